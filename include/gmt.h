@@ -1,0 +1,192 @@
+/*
+ * gmt.h -- C ABI of the GB300 Group Marching Tree (GMT*) planner.
+ *
+ * The planner follows Ichter, Schmerling, Pavone, "Group Marching Tree:
+ * Sampling-Based Approximately Optimal Motion Planning on GPUs" (2017).
+ * Arguments follow the paper's problem statement (Problem 1, Section II: state
+ * space X = [lo, hi], obstacle set X_obs, x_init, goal region X_goal, cost) and
+ * the inputs of Algorithm 1 (n samples, connection radius r, group cost
+ * threshold factor lambda).
+ *
+ * Conventions
+ *  - Plain C: no CUDA, torch or C++ types.  A stream is passed as a
+ *    `gmt_stream`, which is a cudaStream_t (NULL = the legacy default stream).
+ *  - Memory: every array argument says whether it is HOST or DEVICE memory.
+ *    The caller owns every array it passes in and every output array; the
+ *    library owns the opaque handles (gmt_graph, gmt_batch, gmt_model,
+ *    gmt_server) and the device memory inside them, released by *_free.
+ *  - Errors: functions return a gmt_status; no C++ exception crosses the ABI.
+ *    GMT_NO_PATH is a result, not an error (Problem 1: "report failure").
+ *    gmt_last_error() returns a message for the last non-OK status of the
+ *    calling host thread.
+ *  - Device waits inside the kernels are bounded; a wait that runs out returns
+ *    GMT_ERR_TIMEOUT and leaves the CUDA context usable.
+ *  - There is no CPU fallback: every step of the path runs in the library's
+ *    CUDA kernels.  Without a usable GPU, calls return GMT_ERR_CUDA.
+ *  - Arithmetic: IEEE FP32 with round-to-nearest, no FMA contraction, IEEE
+ *    division and square root in every decision, so results are reproducible.
+ *  - Handles are not thread-safe: one handle must not be used by two calls
+ *    at once (on any streams).
+ */
+#ifndef GMT_H
+#define GMT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* gmt_stream;
+
+typedef enum {
+    GMT_OK = 0,
+    GMT_NO_PATH = 1,          /* Alg. 1, Line 12a: V_open became empty */
+    GMT_ERR_INVALID = -1,     /* bad argument, x_init in collision, sampling exhausted */
+    GMT_ERR_OOM = -2,         /* device allocation failed or over the memory budget */
+    GMT_ERR_CUDA = -3,        /* CUDA runtime error (message in gmt_last_error) */
+    GMT_ERR_TIMEOUT = -4,     /* a bounded device wait ran out */
+    GMT_ERR_ITER_LIMIT = -5,  /* more group expansions than gmt_params.max_iters */
+    GMT_ERR_ADMISSION = -6    /* serving: request refused (no slot or memory) */
+} gmt_status;
+
+enum { GMT_COST_EUCLID = 0, GMT_COST_DI = 1 };
+#define GMT_MAX_DIM 10
+
+/* State space X = prod_a [lo[a], hi[a]] (Section II).
+ * kind GMT_COST_EUCLID: geometric planning, cost = Euclidean arc length
+ *   (Section II), dim in [2, GMT_MAX_DIM], pos_dim == dim.
+ * kind GMT_COST_DI: 3D double integrator xdd = u (Section V-A), dim == 6,
+ *   pos_dim == 3, state [p0 p1 p2 v0 v1 v2], cost = arrival time + integral of
+ *   u^T u (the "mixed time/quadratic control effort" cost of Section V-A). */
+typedef struct {
+    int32_t kind;
+    int32_t dim;
+    int32_t pos_dim;
+    float lo[GMT_MAX_DIM];
+    float hi[GMT_MAX_DIM];
+} gmt_space;
+
+/* X_obs: a union of `count` closed axis-aligned boxes in position space
+ * (Section V-B).  lo and hi are DEVICE arrays [count][pos_dim], row-major,
+ * owned by the caller; count == 0 allows NULL pointers. */
+typedef struct {
+    int32_t count;
+    const float* lo;
+    const float* hi;
+} gmt_boxes;
+
+/* X_goal: the closed ball |x - center| <= radius, over the position axes only
+ * (pos_only != 0) or over the whole state (Problem 1). */
+typedef struct {
+    float center[GMT_MAX_DIM];
+    float radius;
+    int32_t pos_only;
+} gmt_goal;
+
+/* Alg. 1 inputs and implementation limits. */
+typedef struct {
+    int32_t n;            /* samples drawn by SampleFree(n); nodes N = n + 1 (node 0 = x_init) */
+    float r;              /* connection radius; <= 0 selects Theorem 1's radius from eta, mu_free */
+    float lambda;         /* group cost threshold factor, in [0, 1]; delta = fl(lambda*r);
+                             0 = the FMT* limit (each group = the open nodes of minimum cost) */
+    uint64_t seed;        /* Philox4x32-10 key of SampleFree */
+    float seg_spacing;    /* geometric edges: collision points every seg_spacing along the segment */
+    int32_t traj_points;  /* double integrator edges: collision points along the trajectory (>= 2) */
+    int32_t max_iters;    /* cap on group expansions; <= 0 means N + 1 */
+    int32_t max_attempts; /* rejection-sampling attempts per node; <= 0 means 65536 */
+    float eta;            /* Theorem 1 tuning parameter (>= 0), used when r <= 0 */
+    float mu_free;        /* Lebesgue measure of X_free (upper bound), used when r <= 0 */
+    int32_t spin_limit;   /* polls of a device-side wait before GMT_ERR_TIMEOUT; <= 0 = default */
+    uint32_t debug_flags; /* GMT_DEBUG_*: test hooks, 0 in normal use */
+} gmt_params;
+
+/* Test hook: the plan kernel's inter-block barrier waits for one more arrival
+ * than there are blocks, so every wait runs out and the call returns
+ * GMT_ERR_TIMEOUT.  Used to test the bounded-wait path without a GPU fault. */
+#define GMT_DEBUG_UNREACHABLE_BARRIER 0x1u
+
+typedef struct gmt_graph gmt_graph;
+
+/* Read-only DEVICE views of a built graph (valid until the next build into, or
+ * the release of, the handle).  Samples are SoA: coordinate a of node v is
+ * X[a * x_pitch + v].  Out-rows list targets in ascending order; in-rows list
+ * sources in ascending order.  For GMT_COST_EUCLID the cost is symmetric and
+ * the in-arrays alias the out-arrays. */
+typedef struct {
+    int32_t kind, dim, pos_dim, N;
+    int32_t x_pitch;
+    int64_t E;
+    float r;
+    const float* X;          /* [dim][x_pitch] */
+    const uint8_t* is_goal;  /* [N], 1 if the sample lies in X_goal */
+    const int32_t* out_row;  /* [N+1] */
+    const int32_t* out_col;  /* [E] */
+    const float* out_cost;   /* [E] c(v, out_col[e]) */
+    const int32_t* in_row;   /* [N+1] */
+    const int32_t* in_col;   /* [E] */
+    const float* in_cost;    /* [E] c(in_col[e], v) */
+} gmt_graph_view;
+
+/* SampleFree and neighbour-set construction (Section III-B; the offline
+ * precomputation of Section V-A).
+ *   V = {x_init} U SampleFree(n): node 0 = x_init (HOST array [dim]), node 1 is
+ *   drawn uniformly in X_goal n X_free, nodes 2..n uniformly in X_free.  Node k,
+ *   attempt t uses Philox4x32-10 with counter (k, t, 0, block) and key (seed low
+ *   32 bits, seed high 32 bits); coordinate a = lo[a] + u*(hi[a]-lo[a]) with
+ *   u = (word >> 8) * 2^-24; the first attempt outside every box is kept.
+ *   Edges: y -> x for y != x with c(y, x) < r (Section III-A), stored as CSR.
+ * *graph: NULL to create a handle, or an existing handle whose device buffers
+ * are reused (grown when needed).  space, boxes, goal, params: HOST structs
+ * (box arrays inside are DEVICE).  Synchronises `stream` once (to size the
+ * edge arrays).  Errors: GMT_ERR_INVALID (arguments; x_init outside X or in
+ * X_obs; a node exhausted max_attempts), GMT_ERR_OOM, GMT_ERR_CUDA. */
+gmt_status gmt_build_graph(const gmt_space* space, const gmt_boxes* boxes, const float* x_init,
+                           const gmt_goal* goal, const gmt_params* params, gmt_graph** graph,
+                           gmt_stream stream);
+
+gmt_status gmt_graph_get_view(const gmt_graph* graph, gmt_graph_view* view);
+void gmt_graph_free(gmt_graph* graph);
+
+/* Per-plan result and counters (host struct). */
+typedef struct {
+    int32_t status;       /* GMT_OK, GMT_NO_PATH or an error */
+    int32_t goal_node;    /* minimum-cost tree node in X_goal (ties: lowest index), -1 if none */
+    float path_cost;      /* cost[goal_node], +inf if none */
+    int32_t path_len;     /* nodes on the path x_init .. goal_node, 0 if none */
+    int64_t iters;        /* group expansions (non-empty groups G) */
+    int64_t final_i;      /* threshold index i of the last expanded group */
+    int64_t push_edges;   /* out-edges scanned from group nodes (Alg. 1, Line 4) */
+    int64_t pull_edges;   /* in-edges scanned for parent selection (Lines 5-6) */
+    int64_t checks;       /* lazy collision checks (Line 7) */
+    int64_t failed;       /* checks that found a collision */
+    int64_t tree_size;    /* nodes with finite cost at termination */
+} gmt_plan_info;
+
+/* Algorithm 1 on a built graph: one persistent kernel runs every wavefront
+ * iteration (group selection, frontier push, lazy parent selection, one
+ * collision check per candidate, set update, termination test) without host
+ * round trips.  V_open in Lines 5-6 is the open set at the start of the
+ * iteration; a candidate whose check fails stays unexplored.
+ *   boxes: obstacles for the collision checks (DEVICE arrays, may differ from
+ *          the ones used at build time).
+ *   parent, cost: DEVICE [N] outputs (parent -1 / cost +inf off the tree).
+ *   path: DEVICE [N] output or NULL; receives x_init .. goal_node.
+ *   info: HOST output.
+ * Synchronises `stream`.  Returns info->status. */
+gmt_status gmt_plan(gmt_graph* graph, const gmt_boxes* boxes, const gmt_params* params, int32_t* parent,
+                    float* cost, int32_t* path, gmt_plan_info* info, gmt_stream stream);
+
+/* Theorem 1's radius r = 4 (1+eta)^(1/d) (1/d)^(1/d) (mu_free/zeta_d)^(1/d)
+ * (log n / n)^(1/d), zeta_d the volume of the unit d-ball, evaluated in double
+ * as 4 * pow((1+eta) * (1/d) * (mu_free/zeta_d) * (log(n)/n), 1/d). */
+double gmt_connection_radius(int32_t n, int32_t d, double eta, double mu_free);
+
+/* Message for the last non-OK status returned to this host thread. */
+const char* gmt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMT_H */

@@ -1,0 +1,753 @@
+// GMT* CPU oracle -- TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow, single-threaded restatement of what the Group Marching Tree
+// hot path computes (Ichter, Schmerling, Pavone, "Group Marching Tree:
+// Sampling-Based Approximately Optimal Motion Planning on GPUs", 2017).
+// Only the test suite, the smoke check and the benchmark's CPU-baseline leg may
+// load this library.  It shares no code, header, table or constant generator
+// with the CUDA path under paper_1705_02403_gb300/csrc/, and includes none of
+// its files.
+//
+// Compile with IEEE semantics and no contraction:
+//   g++ -std=c++17 -O2 -ffp-contract=off -fno-fast-math -shared -fPIC
+//
+// Every function is templated on the real type R (float for the bit-exact
+// parity path, double for the FP64 rerun).  Evaluation order of every
+// floating-point expression is written out explicitly (left to right) and
+// stated in the comment above it; the GPU path follows the same readings.
+//
+// Pins (what checks this file against something other than itself) live in
+// tests/test_oracle_*.py:
+//   philox4x32_10   -> Triton's Philox run in its CPU interpreter (library)
+//   sample_free     -> invariants, chi^2 uniformity, independent rebuild
+//   cost_euclid     -> numpy float64 norm, bitwise symmetry
+//   cost_di         -> closed forms, dense FP64 scan of J, Hermite quadrature,
+//                      Gramian built by numerical integration
+//   edge_free       -> exact slab segment/box test (superset detector),
+//                      hand-placed boxes
+//   build_graph     -> scipy cKDTree pair query (Euclidean), brute force
+//   gmt_plan        -> hand-traced graphs, skip == stepping, lambda=0 == heap
+//                      FMT*, Dijkstra lower bound, (1+2 lambda) upper bound
+//                      without obstacles (Theorem 2), tree invariants
+//   fmt_plan        -> hand-traced graph, Dijkstra lower bound
+//   dijkstra        -> scipy.sparse.csgraph.dijkstra
+//   radius_thm1     -> closed form of Theorem 1 for d = 2, 3
+
+#include <cstdint>
+#include <cstring>
+#include <cmath>
+#include <vector>
+#include <queue>
+#include <limits>
+#include <algorithm>
+
+namespace {
+
+enum { ORC_OK = 0, ORC_NO_PATH = 1, ORC_ERR_INVALID = -1, ORC_ERR_ITER_LIMIT = -5 };
+enum { ORC_EUCLID = 0, ORC_DI = 1 };
+enum { UNEXPLORED = 0, OPEN = 1, CLOSED = 2 };
+const int MAXD = 12;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11 "Parallel random numbers:
+// as easy as 1, 2, 3").  One round maps the counter (c0,c1,c2,c3) with key
+// (k0,k1) to (hi(B*c2)^c1^k0, lo(B*c2), hi(A*c0)^c3^k1, lo(A*c0)) with the
+// round multipliers A = 0xD2511F53, B = 0xCD9E8D57; between rounds the key is
+// bumped by the Weyl constants (0x9E3779B9, 0xBB67AE85).  Ten rounds.
+// ---------------------------------------------------------------------------
+void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    const uint32_t A = 0xD2511F53u, B = 0xCD9E8D57u;
+    const uint32_t WA = 0x9E3779B9u, WB = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t pa = (uint64_t)A * (uint64_t)c0;
+        uint64_t pb = (uint64_t)B * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(pb >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)pb;
+        uint32_t n2 = (uint32_t)(pa >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)pa;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += WA; k1 += WB;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// A 32-bit Philox word becomes a float in [0,1): its top 24 bits times 2^-24
+// (exact in FP32).
+float word_to_unit(uint32_t w) { return (float)(w >> 8) * 0x1p-24f; }
+
+// ---------------------------------------------------------------------------
+// Obstacles: a union of closed axis-aligned boxes in position space
+// (Section V-B: obstacles are unions of axis-aligned bounding boxes).
+// ---------------------------------------------------------------------------
+struct Boxes {
+    int count, dp;
+    const float* lo;  // [count][dp]
+    const float* hi;  // [count][dp]
+};
+
+template <typename R>
+bool point_in_obstacle(const R* p, const Boxes& B) {
+    for (int b = 0; b < B.count; ++b) {
+        bool inside = true;
+        for (int a = 0; a < B.dp; ++a) {
+            R l = (R)B.lo[b * B.dp + a], h = (R)B.hi[b * B.dp + a];
+            if (!(l <= p[a] && p[a] <= h)) { inside = false; break; }
+        }
+        if (inside) return true;
+    }
+    return false;
+}
+
+// Goal region: a closed ball of radius rho around c, over the position axes
+// only (pos_only) or over the whole state.  Membership: sum over axes, in
+// axis order starting from 0, of (x_a - c_a)^2, compared <= rho*rho.
+bool in_goal(const float* x, int gd, const float* c, float rho) {
+    float s = 0.0f;
+    for (int a = 0; a < gd; ++a) {
+        float t = x[a] - c[a];
+        s = s + t * t;
+    }
+    return s <= rho * rho;
+}
+
+// ---------------------------------------------------------------------------
+// Connection costs.
+// ---------------------------------------------------------------------------
+
+// Euclidean arc length (Section II): c = sqrt(((dx0*dx0)+dx1*dx1)+...),
+// dx_a = x_to[a] - x_from[a], summed in axis order from 0.
+template <typename R>
+R cost_euclid(const R* from, const R* to, int d) {
+    R s = 0;
+    for (int a = 0; a < d; ++a) {
+        R t = to[a] - from[a];
+        s = s + t * t;
+    }
+    return std::sqrt(s);
+}
+
+// Double integrator xdd = u in 3 axes, cost = arrival time tau plus control
+// effort, the "mixed time / quadratic control effort" cost of Section V-A.
+// For fixed tau the minimum-effort control gives
+//   J(tau) = tau + a/tau - b/tau^2 + c/tau^3,
+//   a = 4(|v0|^2 + v0.v1 + |v1|^2), b = 12 dp.(v0+v1), c = 12 |dp|^2,
+// and dJ/dtau = 0 is the quartic q(tau) = tau^4 - a tau^2 + 2b tau - 3c.
+// The optimal arrival time is the smallest positive root of q, bracketed on the
+// grid tau_k = r*(k/G), k = 1..G (first k with q(tau_k) >= 0; none -> no edge,
+// because J(tau) >= tau), then refined by `bisect` halvings of
+// [tau_{k-1}, tau_k] (mid = lo + (hi-lo)*0.5; q(mid) < 0 -> lo = mid else hi =
+// mid; tau* = hi).  q is evaluated as ((tau*tau - a)*tau + 2b)*tau - 3c with
+// 2b = 2*b and 3c = 3*c rounded once each; J as ((c/tau - b)/tau + a)/tau + tau.
+// State layout: [p0 p1 p2 v0 v1 v2].
+template <typename R>
+struct DICoeffs { R a, b, c, b2, c3; };
+
+template <typename R>
+DICoeffs<R> di_coeffs(const R* s0, const R* s1) {
+    R n00 = 0, n01 = 0, n11 = 0, bs = 0, cs = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        R p0 = s0[ax], v0 = s0[3 + ax], p1 = s1[ax], v1 = s1[3 + ax];
+        R dp = p1 - p0;
+        n00 = n00 + v0 * v0;
+        n01 = n01 + v0 * v1;
+        n11 = n11 + v1 * v1;
+        bs = bs + dp * (v0 + v1);
+        cs = cs + dp * dp;
+    }
+    DICoeffs<R> k;
+    k.a = (R)4 * ((n00 + n01) + n11);
+    k.b = (R)12 * bs;
+    k.c = (R)12 * cs;
+    k.b2 = (R)2 * k.b;
+    k.c3 = (R)3 * k.c;
+    return k;
+}
+
+template <typename R>
+R di_quartic(const DICoeffs<R>& k, R t) { return ((t * t - k.a) * t + k.b2) * t - k.c3; }
+
+template <typename R>
+R di_J(const DICoeffs<R>& k, R t) { return ((k.c / t - k.b) / t + k.a) / t + t; }
+
+// Returns J (+inf when no root lies in (0, span]) and the arrival time.
+template <typename R>
+R cost_di(const R* s0, const R* s1, R span, int grid, int bisect, R* tau_out) {
+    DICoeffs<R> k = di_coeffs(s0, s1);
+    R prev = 0;
+    int found = 0;
+    R t_hi = 0;
+    for (int g = 1; g <= grid; ++g) {
+        R tg = span * ((R)g / (R)grid);
+        if (di_quartic(k, tg) >= (R)0) { found = g; t_hi = tg; break; }
+        prev = tg;
+    }
+    if (!found) { if (tau_out) *tau_out = std::numeric_limits<R>::infinity(); return std::numeric_limits<R>::infinity(); }
+    R lo = prev, hi = t_hi;
+    for (int s = 0; s < bisect; ++s) {
+        R mid = lo + (hi - lo) * (R)0.5;
+        if (di_quartic(k, mid) < (R)0) lo = mid; else hi = mid;
+    }
+    if (tau_out) *tau_out = hi;
+    return di_J(k, hi);
+}
+
+const int DI_GRID = 32;
+template <typename R> int di_bisect_steps();
+template <> int di_bisect_steps<float>() { return 24; }
+template <> int di_bisect_steps<double>() { return 52; }
+
+// Cost of the directed connection from -> to, both states of dimension d.
+template <typename R>
+R edge_cost(int kind, const R* from, const R* to, int d, R r, R* tau) {
+    if (kind == ORC_EUCLID) { if (tau) *tau = 0; return cost_euclid(from, to, d); }
+    return cost_di(from, to, r, DI_GRID, di_bisect_steps<R>(), tau);
+}
+
+// ---------------------------------------------------------------------------
+// Edge collision check (Alg. 1, Line 7): one connection, checked lazily.
+// Geometric: m = max(2, ceil(L/spacing)+1) points p_k = y + t_k (x - y),
+//   t_k = k/(m-1), endpoints included; a point in a closed box collides.
+// Double integrator: the minimum-effort trajectory is the cubic Hermite curve
+//   p(s) = h00 p0 + h10 tau v0 + h01 p1 + h11 tau v1, s in [0,1],
+//   h00 = 2s^3-3s^2+1, h10 = s^3-2s^2+s, h01 = 3s^2-2s^3, h11 = s^3-s^2,
+//   evaluated at s_k = k/(P-1), k = 0..P-1; a point in a box or outside the
+//   position bounds collides.
+// ---------------------------------------------------------------------------
+template <typename R>
+bool edge_free_geometric(const R* y, const R* x, int dp, R L, R spacing, const Boxes& B) {
+    int m = (int)std::ceil(L / spacing) + 1;
+    if (m < 2) m = 2;
+    R p[MAXD];
+    for (int k = 0; k < m; ++k) {
+        R t = (R)k / (R)(m - 1);
+        for (int a = 0; a < dp; ++a) p[a] = y[a] + t * (x[a] - y[a]);
+        if (point_in_obstacle(p, B)) return false;
+    }
+    return true;
+}
+
+template <typename R>
+void hermite_point(const R* s0, const R* s1, R tau, R s, R* p) {
+    R s2 = s * s;
+    R s3 = s2 * s;
+    R h00 = ((R)2 * s3 - (R)3 * s2) + (R)1;
+    R h10 = (s3 - (R)2 * s2) + s;
+    R h01 = (R)3 * s2 - (R)2 * s3;
+    R h11 = s3 - s2;
+    R h10t = h10 * tau, h11t = h11 * tau;
+    for (int a = 0; a < 3; ++a)
+        p[a] = ((h00 * s0[a] + h10t * s0[3 + a]) + h01 * s1[a]) + h11t * s1[3 + a];
+}
+
+template <typename R>
+bool edge_free_di(const R* y, const R* x, R tau, int points, const float* plo, const float* phi, const Boxes& B) {
+    R p[3];
+    for (int k = 0; k < points; ++k) {
+        R s = (R)k / (R)(points - 1);
+        hermite_point(y, x, tau, s, p);
+        for (int a = 0; a < 3; ++a)
+            if (p[a] < (R)plo[a] || p[a] > (R)phi[a]) return false;
+        if (point_in_obstacle(p, B)) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Neighbour graph: y -> x is an edge iff y != x and c(y,x) < r (Section III-A:
+// neighbours are samples whose connection cost is less than r).  Out-lists are
+// ascending in x, in-lists ascending in y.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Graph {
+    int kind = 0, d = 0, dp = 0, N = 0;
+    R r = 0;
+    std::vector<R> X;            // [d][N]
+    std::vector<uint8_t> goal;   // [N]
+    std::vector<int32_t> out_row, out_col, in_row, in_col;
+    std::vector<R> out_cost, in_cost;
+    void state(int v, R* s) const { for (int a = 0; a < d; ++a) s[a] = X[(size_t)a * N + v]; }
+};
+
+template <typename R>
+Graph<R>* build_graph(int kind, int d, int dp, int N, const float* X, const uint8_t* goal, float r) {
+    Graph<R>* g = new Graph<R>();
+    g->kind = kind; g->d = d; g->dp = dp; g->N = N; g->r = (R)r;
+    g->X.resize((size_t)d * N);
+    for (size_t i = 0; i < (size_t)d * N; ++i) g->X[i] = (R)X[i];
+    g->goal.assign(goal, goal + N);
+    std::vector<std::vector<std::pair<int, R>>> out(N), in(N);
+    R si[MAXD], sj[MAXD];
+    for (int i = 0; i < N; ++i) {
+        g->state(i, si);
+        for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            g->state(j, sj);
+            R c = edge_cost<R>(kind, si, sj, d, g->r, nullptr);
+            if (c < g->r) out[i].push_back({j, c});
+        }
+    }
+    for (int y = 0; y < N; ++y)
+        for (auto& e : out[y]) in[e.first].push_back({y, e.second});
+    auto flatten = [N](const std::vector<std::vector<std::pair<int, R>>>& L,
+                       std::vector<int32_t>& row, std::vector<int32_t>& col, std::vector<R>& cost) {
+        row.assign(N + 1, 0);
+        for (int v = 0; v < N; ++v) row[v + 1] = row[v] + (int32_t)L[v].size();
+        col.clear(); cost.clear();
+        for (int v = 0; v < N; ++v)
+            for (auto& e : L[v]) { col.push_back(e.first); cost.push_back(e.second); }
+    };
+    flatten(out, g->out_row, g->out_col, g->out_cost);
+    flatten(in, g->in_row, g->in_col, g->in_cost);
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// Planner inputs shared by GMT*, FMT* and Dijkstra.
+// ---------------------------------------------------------------------------
+struct PlanCfg {
+    Boxes boxes;
+    const float* pos_lo;   // position bounds (double-integrator wall test)
+    const float* pos_hi;
+    float lambda, seg_spacing;
+    int traj_points, skip_empty, max_iters;
+};
+
+}  // namespace
+
+extern "C" {
+
+struct orc_info {
+    int32_t status, goal_node;
+    double path_cost;
+    int64_t iters, final_i, push_edges, pull_edges, checks, failed, tree_size;
+};
+
+}
+
+namespace {
+
+// Collision verdict for the tree edge parent y -> child x with cost c.
+template <typename R>
+bool check_edge(const Graph<R>& g, int y, int x, R c, const PlanCfg& P) {
+    R sy[MAXD], sx[MAXD];
+    g.state(y, sy); g.state(x, sx);
+    if (g.kind == ORC_EUCLID) return edge_free_geometric(sy, sx, g.dp, c, (R)P.seg_spacing, P.boxes);
+    R tau;
+    cost_di<R>(sy, sx, g.r, DI_GRID, di_bisect_steps<R>(), &tau);
+    return edge_free_di(sy, sx, tau, P.traj_points, P.pos_lo, P.pos_hi, P.boxes);
+}
+
+template <typename R>
+void finish(const Graph<R>& g, const std::vector<R>& cost, bool success, orc_info* info) {
+    info->goal_node = -1;
+    info->path_cost = std::numeric_limits<double>::infinity();
+    if (!success) { info->status = ORC_NO_PATH; return; }
+    // Result (Alg. 1, Line 12b): the minimum-cost tree node in X_goal, ties by index.
+    int best = -1;
+    for (int v = 0; v < g.N; ++v)
+        if (g.goal[v] && cost[v] < std::numeric_limits<R>::infinity())
+            if (best < 0 || cost[v] < cost[best]) best = v;
+    info->status = ORC_OK;
+    info->goal_node = best;
+    info->path_cost = (double)cost[best];
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 (Group Marching Tree), literally, one iteration at a time.
+//   Line 1-2: V_open = {x_init}, tree rooted at x_init, i = 0, delta = lambda r.
+//   Line 3:   G = {v in V_open : cost(v) <= theta_i}, theta_i = fl(fl(i)*delta).
+//             (lambda = 0 is the FMT* limit: G = open nodes at the minimum cost.)
+//   Line 4:   every unexplored out-neighbour x of a node of G, once.
+//   Line 5-6: y* = argmin over in-neighbours y in V_open of (cost(y)+c(y,x), y);
+//             V_open is the set at the start of the iteration.
+//   Line 7-9: if the edge y* -> x is collision-free, add it; x leaves
+//             V_unexplored and enters V_open (visible from iteration i+1).
+//             A failed x stays unexplored and may be retried later.
+//   Line 10:  G moves from V_open to V_closed.
+//   Line 12:  stop with success if G held a goal node, with failure if V_open
+//             is empty; otherwise Line 11, i = i + 1.
+// With skip_empty, the iterations whose group would be empty (no-ops) are
+// skipped: the next i is the smallest i' > i with theta_{i'} >= min open cost.
+// ---------------------------------------------------------------------------
+template <typename R>
+int gmt_plan(const Graph<R>& g, const PlanCfg& P, int32_t* parent_out, R* cost_out, orc_info* info,
+             int64_t* added_i = nullptr, int64_t* closed_i = nullptr) {
+    const int N = g.N;
+    const R INF = std::numeric_limits<R>::infinity();
+    std::memset(info, 0, sizeof(*info));
+    std::vector<int> set(N, UNEXPLORED);
+    std::vector<R> cost(N, INF);
+    std::vector<int32_t> parent(N, -1);
+    set[0] = OPEN;
+    cost[0] = 0;
+    if (added_i) for (int v = 0; v < N; ++v) added_i[v] = v == 0 ? -1 : -2;
+    if (closed_i) for (int v = 0; v < N; ++v) closed_i[v] = -2;
+    const R delta = (R)P.lambda * g.r;    // fl(lambda * r)
+    int64_t i = 0;
+    bool success = false;
+    int status = ORC_OK;
+    std::vector<char> is_near(N, 0);
+    struct Add { int x, y; R c; };
+    for (;;) {
+        // Line 3
+        R theta;
+        if (delta == (R)0) {
+            theta = INF;
+            for (int v = 0; v < N; ++v) if (set[v] == OPEN && cost[v] < theta) theta = cost[v];
+        } else {
+            theta = (R)i * delta;
+        }
+        std::vector<int> G;
+        for (int v = 0; v < N; ++v)
+            if (set[v] == OPEN && cost[v] <= theta) G.push_back(v);
+        if (!G.empty()) {
+            if (info->iters >= P.max_iters) { status = ORC_ERR_ITER_LIMIT; break; }
+            info->iters++;
+        }
+        // Line 4
+        std::vector<int> Xnear;
+        for (int z : G) {
+            info->push_edges += g.out_row[z + 1] - g.out_row[z];
+            for (int e = g.out_row[z]; e < g.out_row[z + 1]; ++e) {
+                int x = g.out_col[e];
+                if (set[x] == UNEXPLORED && !is_near[x]) { is_near[x] = 1; Xnear.push_back(x); }
+            }
+        }
+        std::sort(Xnear.begin(), Xnear.end());
+        // Lines 5-9
+        std::vector<Add> added;
+        for (int x : Xnear) {
+            is_near[x] = 0;
+            info->pull_edges += g.in_row[x + 1] - g.in_row[x];
+            int ybest = -1;
+            R cbest = INF, ebest = 0;
+            for (int e = g.in_row[x]; e < g.in_row[x + 1]; ++e) {
+                int y = g.in_col[e];
+                if (set[y] != OPEN) continue;
+                R c = cost[y] + g.in_cost[e];
+                if (ybest < 0 || c < cbest || (c == cbest && y < ybest)) { ybest = y; cbest = c; ebest = g.in_cost[e]; }
+            }
+            // x was reached from a node of G, which is open, so ybest exists.
+            info->checks++;
+            if (check_edge(g, ybest, x, ebest, P)) added.push_back({x, ybest, cbest});
+            else info->failed++;
+        }
+        for (const Add& a : added) {
+            set[a.x] = OPEN; parent[a.x] = a.y; cost[a.x] = a.c;
+            if (added_i) added_i[a.x] = i;
+        }
+        // Line 10
+        bool goal_in_G = false;
+        for (int z : G) {
+            set[z] = CLOSED;
+            if (g.goal[z]) goal_in_G = true;
+            if (closed_i) closed_i[z] = i;
+        }
+        // Line 12
+        if (goal_in_G) { success = true; break; }
+        R m = INF;
+        for (int v = 0; v < N; ++v) if (set[v] == OPEN && cost[v] < m) m = cost[v];
+        if (m == INF) { success = false; break; }
+        // Line 11
+        if (delta == (R)0 || !P.skip_empty) {
+            i = i + 1;
+            if (i > ((int64_t)1 << 40)) { status = ORC_ERR_ITER_LIMIT; break; }
+        } else {
+            int64_t k = (int64_t)std::ceil(m / delta);
+            if (k < i + 1) k = i + 1;
+            while (k > i + 1 && (R)(k - 1) * delta >= m) --k;
+            while ((R)k * delta < m) ++k;
+            i = k;
+        }
+    }
+    info->final_i = i;
+    int64_t tree = 0;
+    for (int v = 0; v < N; ++v) if (cost[v] < INF) ++tree;
+    info->tree_size = tree;
+    for (int v = 0; v < N; ++v) { parent_out[v] = parent[v]; cost_out[v] = cost[v]; }
+    if (status != ORC_OK) { info->status = status; info->goal_node = -1; info->path_cost = INFINITY; return status; }
+    finish(g, cost, success, info);
+    return info->status;
+}
+
+// ---------------------------------------------------------------------------
+// FMT* (Janson, Schmerling, Clark, Pavone 2015), the comparator of Section III:
+// expand only the single minimum-cost open node z (ties by index) per step,
+// connect each unexplored out-neighbour x of z to argmin over open
+// in-neighbours of cost(y) + c(y,x), lazily checked; stop when z is a goal node
+// or the open set is empty.  Open nodes are kept in a binary heap.
+// ---------------------------------------------------------------------------
+template <typename R>
+int fmt_plan(const Graph<R>& g, const PlanCfg& P, int32_t* parent_out, R* cost_out, orc_info* info) {
+    const int N = g.N;
+    const R INF = std::numeric_limits<R>::infinity();
+    std::memset(info, 0, sizeof(*info));
+    std::vector<int> set(N, UNEXPLORED);
+    std::vector<R> cost(N, INF);
+    std::vector<int32_t> parent(N, -1);
+    typedef std::pair<R, int> Key;
+    std::priority_queue<Key, std::vector<Key>, std::greater<Key>> heap;
+    set[0] = OPEN; cost[0] = 0; heap.push({(R)0, 0});
+    int found = -1;
+    while (!heap.empty()) {
+        Key top = heap.top(); heap.pop();
+        int z = top.second;
+        if (set[z] != OPEN) continue;
+        if (g.goal[z]) { found = z; break; }
+        info->iters++;
+        std::vector<std::pair<int, std::pair<int, R>>> added;
+        info->push_edges += g.out_row[z + 1] - g.out_row[z];
+        for (int e = g.out_row[z]; e < g.out_row[z + 1]; ++e) {
+            int x = g.out_col[e];
+            if (set[x] != UNEXPLORED) continue;
+            info->pull_edges += g.in_row[x + 1] - g.in_row[x];
+            int yb = -1; R cb = INF, eb = 0;
+            for (int f = g.in_row[x]; f < g.in_row[x + 1]; ++f) {
+                int y = g.in_col[f];
+                if (set[y] != OPEN) continue;
+                R c = cost[y] + g.in_cost[f];
+                if (yb < 0 || c < cb || (c == cb && y < yb)) { yb = y; cb = c; eb = g.in_cost[f]; }
+            }
+            info->checks++;
+            if (check_edge(g, yb, x, eb, P)) added.push_back({x, {yb, cb}});
+            else info->failed++;
+        }
+        for (auto& a : added) {
+            set[a.first] = OPEN; parent[a.first] = a.second.first; cost[a.first] = a.second.second;
+            heap.push({cost[a.first], a.first});
+        }
+        set[z] = CLOSED;
+    }
+    int64_t tree = 0;
+    for (int v = 0; v < N; ++v) if (cost[v] < INF) ++tree;
+    info->tree_size = tree;
+    for (int v = 0; v < N; ++v) { parent_out[v] = parent[v]; cost_out[v] = cost[v]; }
+    info->goal_node = -1;
+    info->path_cost = INFINITY;
+    if (found < 0) { info->status = ORC_NO_PATH; return ORC_NO_PATH; }
+    info->status = ORC_OK; info->goal_node = found; info->path_cost = (double)cost[found];
+    return ORC_OK;
+}
+
+// Exact shortest path (Dijkstra) from x_init over the directed r-disk graph
+// restricted to collision-free edges (every edge checked).  dist uses the same
+// recurrence fl(dist(y) + c(y,x)) as the planners.
+template <typename R>
+double dijkstra(const Graph<R>& g, const PlanCfg& P, R* dist_out) {
+    const int N = g.N;
+    const R INF = std::numeric_limits<R>::infinity();
+    std::vector<R> dist(N, INF);
+    std::vector<char> done(N, 0);
+    typedef std::pair<R, int> Key;
+    std::priority_queue<Key, std::vector<Key>, std::greater<Key>> heap;
+    dist[0] = 0; heap.push({(R)0, 0});
+    while (!heap.empty()) {
+        Key t = heap.top(); heap.pop();
+        int y = t.second;
+        if (done[y]) continue;
+        done[y] = 1;
+        for (int e = g.out_row[y]; e < g.out_row[y + 1]; ++e) {
+            int x = g.out_col[e];
+            if (done[x]) continue;
+            R c = dist[y] + g.out_cost[e];
+            if (c < dist[x] && check_edge(g, y, x, g.out_cost[e], P)) { dist[x] = c; heap.push({c, x}); }
+        }
+    }
+    R best = INF;
+    for (int v = 0; v < N; ++v) if (g.goal[v] && dist[v] < best) best = dist[v];
+    if (dist_out) for (int v = 0; v < N; ++v) dist_out[v] = dist[v];
+    return (double)best;
+}
+
+PlanCfg make_cfg(int nbox, int dp, const float* blo, const float* bhi, const float* pos_lo, const float* pos_hi,
+                 float lambda, float seg_spacing, int traj_points, int skip_empty, int max_iters) {
+    PlanCfg P;
+    P.boxes.count = nbox; P.boxes.dp = dp; P.boxes.lo = blo; P.boxes.hi = bhi;
+    P.pos_lo = pos_lo; P.pos_hi = pos_hi;
+    P.lambda = lambda; P.seg_spacing = seg_spacing; P.traj_points = traj_points;
+    P.skip_empty = skip_empty; P.max_iters = max_iters;
+    return P;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C interface (loaded with ctypes by the tests).
+// ===========================================================================
+extern "C" {
+
+void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { philox4x32_10(ctr, key, out); }
+float orc_word_to_unit(uint32_t w) { return word_to_unit(w); }
+
+// SampleFree(n) (Section III-B) with V = {x_init} U SampleFree(n): node 0 is
+// x_init, node 1 is drawn uniformly in X_goal n X_free (so at least one sample
+// lies in the goal region, Alg. 1 input), nodes 2..n uniformly in X_free.
+// Node k, attempt t draws Philox4x32-10 blocks with counter (k, t, stream, blk)
+// and key (seed lo 32 bits, seed hi 32 bits); coordinate a uses word a%4 of
+// block a/4, mapped to lo_a + u*(hi_a - lo_a).  The first attempt that is
+// accepted (not in any closed box; for node 1 also inside the goal ball and the
+// state bounds) is the sample.  For node 1 the goal axes draw from the ball's
+// bounding box [c - rho, c + rho].  Returns 0, or -1 on invalid input or when a
+// node exhausts max_attempts.
+int orc_sample(int d, int dp, const float* lo, const float* hi, int nbox, const float* blo, const float* bhi,
+               const float* x_init, const float* goal_c, float goal_r, int goal_pos_only, int n, uint64_t seed,
+               uint32_t stream, int max_attempts, float* X, uint8_t* is_goal) {
+    if (d < 1 || d > MAXD || dp < 1 || dp > d || n < 1) return ORC_ERR_INVALID;
+    Boxes B{nbox, dp, blo, bhi};
+    const int N = n + 1;
+    const int gd = goal_pos_only ? dp : d;
+    for (int a = 0; a < d; ++a)
+        if (!(lo[a] <= x_init[a] && x_init[a] <= hi[a])) return ORC_ERR_INVALID;
+    if (point_in_obstacle(x_init, B)) return ORC_ERR_INVALID;
+    for (int a = 0; a < d; ++a) X[(size_t)a * N + 0] = x_init[a];
+    const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    float x[MAXD];
+    for (int k = 1; k < N; ++k) {
+        bool ok = false;
+        for (int t = 0; t < max_attempts && !ok; ++t) {
+            uint32_t words[MAXD];
+            for (int blk = 0; blk * 4 < d; ++blk) {
+                uint32_t ctr[4] = {(uint32_t)k, (uint32_t)t, stream, (uint32_t)blk};
+                philox4x32_10(ctr, key, words + 4 * blk);
+            }
+            for (int a = 0; a < d; ++a) {
+                float u = word_to_unit(words[a]);
+                float l = lo[a], h = hi[a];
+                if (k == 1 && a < gd) { l = goal_c[a] - goal_r; h = goal_c[a] + goal_r; }
+                x[a] = l + u * (h - l);
+            }
+            if (k == 1) {
+                bool inb = true;
+                for (int a = 0; a < d; ++a) if (!(lo[a] <= x[a] && x[a] <= hi[a])) inb = false;
+                if (!inb || !in_goal(x, gd, goal_c, goal_r)) continue;
+            }
+            if (point_in_obstacle(x, B)) continue;
+            ok = true;
+        }
+        if (!ok) return ORC_ERR_INVALID;
+        for (int a = 0; a < d; ++a) X[(size_t)a * N + k] = x[a];
+    }
+    for (int k = 0; k < N; ++k) {
+        for (int a = 0; a < d; ++a) x[a] = X[(size_t)a * N + k];
+        is_goal[k] = in_goal(x, gd, goal_c, goal_r) ? 1 : 0;
+    }
+    return ORC_OK;
+}
+
+int orc_in_goal(const float* x, int gd, const float* c, float rho) { return in_goal(x, gd, c, rho) ? 1 : 0; }
+
+float orc_cost_euclid_f32(const float* from, const float* to, int d) { return cost_euclid(from, to, d); }
+double orc_cost_euclid_f64(const double* from, const double* to, int d) { return cost_euclid(from, to, d); }
+
+float orc_cost_di_f32(const float* s0, const float* s1, float r, float* tau) {
+    return cost_di<float>(s0, s1, r, DI_GRID, 24, tau);
+}
+double orc_cost_di_f64(const double* s0, const double* s1, double span, int grid, int bisect, double* tau) {
+    return cost_di<double>(s0, s1, span, grid, bisect, tau);
+}
+void orc_di_coeffs_f64(const double* s0, const double* s1, double* abc) {
+    DICoeffs<double> k = di_coeffs(s0, s1);
+    abc[0] = k.a; abc[1] = k.b; abc[2] = k.c;
+}
+void orc_hermite_point_f64(const double* s0, const double* s1, double tau, double s, double* p) {
+    hermite_point(s0, s1, tau, s, p);
+}
+
+int orc_edge_free_geometric_f32(const float* y, const float* x, int dp, float L, float spacing, int nbox,
+                                const float* blo, const float* bhi) {
+    Boxes B{nbox, dp, blo, bhi};
+    return edge_free_geometric(y, x, dp, L, spacing, B) ? 1 : 0;
+}
+int orc_edge_free_di_f32(const float* y, const float* x, float tau, int points, const float* plo, const float* phi,
+                         int nbox, const float* blo, const float* bhi) {
+    Boxes B{nbox, 3, blo, bhi};
+    return edge_free_di(y, x, tau, points, plo, phi, B) ? 1 : 0;
+}
+
+// Theorem 1 radius r = 4 (1+eta)^(1/d) (1/d)^(1/d) (mu/zeta_d)^(1/d) (log n/n)^(1/d),
+// zeta_d = pi^(d/2) / Gamma(d/2 + 1), evaluated in double as
+// 4 * pow((1+eta) * (1/d) * (mu/zeta_d) * (log(n)/n), 1/d).
+double orc_radius_thm1(int n, int d, double eta, double mu) {
+    const double pi = 3.14159265358979323846;
+    double zeta = std::pow(pi, (double)d / 2.0) / std::tgamma((double)d / 2.0 + 1.0);
+    double base = (1.0 + eta) * (1.0 / (double)d) * (mu / zeta) * (std::log((double)n) / (double)n);
+    return 4.0 * std::pow(base, 1.0 / (double)d);
+}
+
+// ---- graphs ----
+void* orc_graph_build(int precision, int kind, int d, int dp, int N, const float* X, const uint8_t* goal, float r) {
+    if (precision == 64) return build_graph<double>(kind, d, dp, N, X, goal, r);
+    return build_graph<float>(kind, d, dp, N, X, goal, r);
+}
+void orc_graph_free(int precision, void* g) {
+    if (precision == 64) delete (Graph<double>*)g; else delete (Graph<float>*)g;
+}
+int64_t orc_graph_num_edges(int precision, const void* g) {
+    if (precision == 64) return (int64_t)((const Graph<double>*)g)->out_col.size();
+    return (int64_t)((const Graph<float>*)g)->out_col.size();
+}
+// Copies the CSR arrays out; costs are widened to double.
+void orc_graph_copy(int precision, const void* gv, int32_t* out_row, int32_t* out_col, double* out_cost,
+                    int32_t* in_row, int32_t* in_col, double* in_cost) {
+    auto copy = [&](auto* g) {
+        std::copy(g->out_row.begin(), g->out_row.end(), out_row);
+        std::copy(g->out_col.begin(), g->out_col.end(), out_col);
+        for (size_t e = 0; e < g->out_cost.size(); ++e) out_cost[e] = (double)g->out_cost[e];
+        std::copy(g->in_row.begin(), g->in_row.end(), in_row);
+        std::copy(g->in_col.begin(), g->in_col.end(), in_col);
+        for (size_t e = 0; e < g->in_cost.size(); ++e) in_cost[e] = (double)g->in_cost[e];
+    };
+    if (precision == 64) copy((const Graph<double>*)gv); else copy((const Graph<float>*)gv);
+}
+
+// ---- planners ----
+// which: 0 = GMT* (Alg. 1), 1 = FMT*.  cost_out is double regardless of precision.
+// added_i / closed_i (GMT* only, may be NULL): threshold index i of the
+// iteration that added / closed each node (-1 for x_init, -2 never).
+int orc_plan(int precision, int which, const void* gv, int nbox, const float* blo, const float* bhi,
+             const float* pos_lo, const float* pos_hi, float lambda, float seg_spacing, int traj_points,
+             int skip_empty, int max_iters, int32_t* parent, double* cost_out, orc_info* info,
+             int64_t* added_i, int64_t* closed_i) {
+    auto run = [&](auto* g, auto zero) {
+        typedef decltype(zero) R;
+        PlanCfg P = make_cfg(nbox, g->dp, blo, bhi, pos_lo, pos_hi, lambda, seg_spacing, traj_points, skip_empty, max_iters);
+        std::vector<R> c(g->N);
+        int st = which == 0 ? gmt_plan<R>(*g, P, parent, c.data(), info, added_i, closed_i)
+                            : fmt_plan<R>(*g, P, parent, c.data(), info);
+        for (int v = 0; v < g->N; ++v) cost_out[v] = (double)c[v];
+        return st;
+    };
+    if (precision == 64) return run((const Graph<double>*)gv, 0.0);
+    return run((const Graph<float>*)gv, 0.0f);
+}
+
+double orc_dijkstra(int precision, const void* gv, int nbox, const float* blo, const float* bhi,
+                    const float* pos_lo, const float* pos_hi, float seg_spacing, int traj_points, double* dist_out) {
+    auto run = [&](auto* g, auto zero) {
+        typedef decltype(zero) R;
+        PlanCfg P = make_cfg(nbox, g->dp, blo, bhi, pos_lo, pos_hi, 0.0f, seg_spacing, traj_points, 1, 0);
+        std::vector<R> dist(g->N);
+        double best = dijkstra<R>(*g, P, dist.data());
+        if (dist_out) for (int v = 0; v < g->N; ++v) dist_out[v] = (double)dist[v];
+        return best;
+    };
+    if (precision == 64) return run((const Graph<double>*)gv, 0.0);
+    return run((const Graph<float>*)gv, 0.0f);
+}
+
+// Collision verdict of one directed graph edge y -> x of a built graph.
+int orc_graph_edge_free(int precision, const void* gv, int y, int x, double c, int nbox, const float* blo,
+                        const float* bhi, const float* pos_lo, const float* pos_hi, float seg_spacing,
+                        int traj_points) {
+    auto run = [&](auto* g, auto zero) {
+        typedef decltype(zero) R;
+        PlanCfg P = make_cfg(nbox, g->dp, blo, bhi, pos_lo, pos_hi, 0.0f, seg_spacing, traj_points, 1, 0);
+        return check_edge<R>(*g, y, x, (R)c, P) ? 1 : 0;
+    };
+    if (precision == 64) return run((const Graph<double>*)gv, 0.0);
+    return run((const Graph<float>*)gv, 0.0f);
+}
+
+}  // extern "C"

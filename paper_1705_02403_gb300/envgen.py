@@ -1,0 +1,141 @@
+"""Seeded synthetic planning problems (inputs only).
+
+This module draws the environments both the CUDA planner and the CPU oracle
+consume: state bounds, obstacle boxes, x_init, goal ball, n, r, lambda and the
+Philox seed.  It contains none of the planner's arithmetic (no sampling, cost,
+neighbour or wavefront code); the obstacle boxes are drawn with numpy's PCG64
+from the problem seed.
+
+The paper's own workloads (an S3DIS-derived indoor map, a two-level cave and a
+forest, Section V-B) are not available; seeded random-box environments with box
+counts and sample counts in the paper's ranges (Table 3) stand in for them.
+"""
+from __future__ import annotations
+
+import json
+import os
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+EUCLID, DI = 0, 1
+HERE = os.path.dirname(os.path.abspath(__file__))
+CONFIG_DIR = os.path.join(HERE, "configs")
+
+
+@dataclass
+class Problem:
+    """One planning query (Problem 1 of the paper plus Alg. 1's inputs)."""
+    kind: int                 # EUCLID (arc length) or DI (double integrator time + effort)
+    d: int                    # state dimension
+    dp: int                   # position dimension (obstacles live here)
+    lo: np.ndarray            # [d] state lower bounds
+    hi: np.ndarray            # [d] state upper bounds
+    box_lo: np.ndarray        # [B, dp] closed obstacle boxes
+    box_hi: np.ndarray        # [B, dp]
+    x_init: np.ndarray        # [d]
+    goal_center: np.ndarray   # [d] (first dp used when goal_pos_only)
+    goal_radius: float
+    goal_pos_only: bool
+    n: int                    # number of samples; N = n + 1 nodes
+    r: float                  # connection radius (0 = Theorem 1 radius, computed by the planner)
+    lam: float                # group cost threshold factor lambda
+    seed: int                 # Philox key for SampleFree
+    seg_spacing: float = 0.005
+    traj_points: int = 20
+    eta: float = 0.0          # Theorem 1 tuning parameter (only when r == 0)
+    mu_free: float = 1.0      # Lebesgue measure bound used by Theorem 1 (only when r == 0)
+    tag: str = ""
+
+    @property
+    def N(self) -> int:
+        return self.n + 1
+
+    @property
+    def nbox(self) -> int:
+        return int(self.box_lo.shape[0])
+
+    def with_(self, **kw) -> "Problem":
+        return replace(self, **kw)
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def random_boxes(rng, count, dp, x_init_pos, goal_center_pos, goal_radius, side=(0.05, 0.2)):
+    """Boxes with per-axis side lengths U[side] and centres U[0,1]^dp; a box that
+    contains x_init or touches the goal ball is redrawn."""
+    lo = np.zeros((count, dp)); hi = np.zeros((count, dp))
+    k = 0
+    while k < count:
+        s = rng.uniform(side[0], side[1], size=dp)
+        c = rng.uniform(0.0, 1.0, size=dp)
+        bl, bh = c - s / 2, c + s / 2
+        if np.all(bl <= x_init_pos) and np.all(x_init_pos <= bh):
+            continue
+        nearest = np.clip(goal_center_pos, bl, bh)
+        if np.linalg.norm(nearest - goal_center_pos) <= goal_radius:
+            continue
+        lo[k], hi[k] = bl, bh
+        k += 1
+    return _f32(lo), _f32(hi)
+
+
+def geometric(seed: int, d: int = 2, n: int = 1024, nbox: int = 10, r: float = 0.12, lam: float = 0.5,
+              tag: str = "") -> Problem:
+    """Unit hypercube, Euclidean cost, x_init at 0.05, goal ball radius 0.05 at 0.95."""
+    rng = np.random.default_rng([seed, 1705, d])
+    x0 = np.full(d, 0.05)
+    gc = np.full(d, 0.95)
+    bl, bh = random_boxes(rng, nbox, d, x0, gc, 0.05)
+    return Problem(kind=EUCLID, d=d, dp=d, lo=_f32(np.zeros(d)), hi=_f32(np.ones(d)), box_lo=bl, box_hi=bh,
+                   x_init=_f32(x0), goal_center=_f32(gc), goal_radius=0.05, goal_pos_only=False, n=n, r=r,
+                   lam=lam, seed=seed, tag=tag)
+
+
+def load_config(name: str) -> dict:
+    with open(os.path.join(CONFIG_DIR, name + ".json")) as f:
+        return json.load(f)
+
+
+def cfg1_2d(seed: int = 0) -> Problem:
+    """2D geometric GMT*: n=1024, 10 boxes, r=0.12, lambda=0.5."""
+    c = load_config("geometric_2d_n1024")
+    return geometric(seed, d=2, n=c["n"], nbox=c["boxes"], r=c["r"], lam=c["lambda"], tag="geometric_2d_n1024")
+
+
+def di6(seed: int = 0, n: int = 4096, nbox: int = 30, r: float | None = None, lam: float = 0.5) -> Problem:
+    """6D double integrator: position [0,1]^3, velocity [-1,1]^3, x_init at rest
+    at (0.05,0.05,0.05), goal = position ball radius 0.05 at (0.95,0.95,0.95)."""
+    if r is None:
+        r = load_config("double_integrator_6d_n4096")["r"]
+    rng = np.random.default_rng([seed, 1705, 6])
+    x0 = np.array([0.05, 0.05, 0.05, 0.0, 0.0, 0.0])
+    gc = np.array([0.95, 0.95, 0.95, 0.0, 0.0, 0.0])
+    bl, bh = random_boxes(rng, nbox, 3, x0[:3], gc[:3], 0.05)
+    return Problem(kind=DI, d=6, dp=3, lo=_f32([0, 0, 0, -1, -1, -1]), hi=_f32([1, 1, 1, 1, 1, 1]),
+                   box_lo=bl, box_hi=bh, x_init=_f32(x0), goal_center=_f32(gc), goal_radius=0.05,
+                   goal_pos_only=True, n=n, r=float(np.float32(r)), lam=lam, seed=seed,
+                   tag="double_integrator_6d")
+
+
+def cfg2_di6(seed: int = 0) -> Problem:
+    c = load_config("double_integrator_6d_n4096")
+    return di6(seed, n=c["n"], nbox=c["boxes"], r=c["r"], lam=c["lambda"])
+
+
+def batch_queries(seed: int = 0, q: int = 256, n_min: int = 512, n_max: int = 16384, lam: float = 0.5):
+    """Uneven batch: each query 2D or 3D geometric (coin flip), n log-uniform in
+    [n_min, n_max], its own seed, 5..80 boxes; r = 0 asks for the Theorem 1
+    radius (eta = 0, mu(X_free) <= 1)."""
+    rng = np.random.default_rng([seed, 1705, 3])
+    out = []
+    for k in range(q):
+        d = int(rng.integers(2, 4))
+        n = int(round(n_min * (n_max / n_min) ** rng.uniform()))
+        nbox = int(rng.integers(5, 81))
+        qseed = int(rng.integers(0, 2**63 - 1))
+        pb = geometric(qseed, d=d, n=n, nbox=nbox, r=0.0, lam=lam, tag=f"batch{seed}_{k}")
+        out.append(pb)
+    return out
