@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark of the GMT* hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmt|reference] [--workload di6|geo2d]
+
+A step is one pass of the whole hot path over one synthetic problem: SampleFree
+(Philox), the r-disk neighbour CSR (all-pairs cost filter) and the group
+wavefront of Algorithm 1, through the C ABI.  Every step plans a different
+seed.  The default workload is the 6D double integrator (n = 4096, 30 random
+boxes, r frozen for mean out-degree 40, lambda = 0.5).
+
+Metric: edges checked per second (CSR entries scanned by the frontier push and
+the lazy parent selection), beside ms per plan p50/p99.  Inputs are resident in
+HBM before the timed region; L2 is flushed (256 MiB write) between steps and
+the flush is outside the per-step CUDA-event timings.
+
+Under torchrun (N > 1) each rank plans its own seeds (replicas, no collective
+on the data path); value = edges of all ranks / the slowest rank's time.
+
+--impl reference times the CPU oracle (oracle/) as the reference arm on a
+bounded sample of the same workload, on the host cores, single-threaded.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms/plan p50/p99 & edges checked/s; learned+batched vs plain at equal path cost"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gmt", choices=["gmt", "reference"])
+    ap.add_argument("--workload", default="di6", choices=["di6", "geo2d"])
+    ap.add_argument("--seed-base", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_problem(workload, seed):
+    from paper_1705_02403_gb300 import envgen
+    return envgen.cfg2_di6(seed) if workload == "di6" else envgen.cfg1_2d(seed)
+
+
+def workload_config(workload):
+    from paper_1705_02403_gb300 import envgen
+    if workload == "di6":
+        c = envgen.load_config("double_integrator_6d_n4096")
+        return {"workload": "double_integrator_6d_n4096_30boxes", "kind": "double_integrator", "dim": 6,
+                "n": c["n"], "boxes": c["boxes"], "r": c["r"], "lambda": c["lambda"],
+                "traj_points": c["traj_points"]}
+    c = envgen.load_config("geometric_2d_n1024")
+    return {"workload": "geometric_2d_n1024_10boxes", "kind": "euclidean", "dim": 2, "n": c["n"],
+            "boxes": c["boxes"], "r": c["r"], "lambda": c["lambda"], "seg_spacing": c["seg_spacing"]}
+
+
+def pct(a, q):
+    return float(np.percentile(np.asarray(a, dtype=np.float64), q)) if len(a) else None
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"gmt_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- oracle
+class OracleProblem:
+    """A problem with its oracle graph built once (untimed setup)."""
+
+    def __init__(self, O, pb):
+        self.pb = pb
+        self.X, self.goal = O.sample(pb)
+        self.g = O.Graph(pb.kind, pb.d, pb.dp, self.X, self.goal, pb.r)
+
+
+def oracle_step(O, prob, rows_per_step):
+    """One bounded oracle sample of a step: SampleFree of all nodes, the
+    neighbour test of `rows_per_step` rows (time scaled to all N rows) and the
+    full wavefront on the full graph.  Returns (seconds for one full step,
+    edges checked)."""
+    pb = prob.pb
+    t0 = time.perf_counter()
+    O.sample(pb)
+    t1 = time.perf_counter()
+    rows = min(rows_per_step, pb.N)
+    O.count_edges_rows(pb, prob.X, 0, rows)
+    t2 = time.perf_counter()
+    _, _, info = prob.g.plan(pb.box_lo, pb.box_hi, pb.lo[:pb.dp], pb.hi[:pb.dp], pb.lam, pb.seg_spacing,
+                             pb.traj_points)
+    t3 = time.perf_counter()
+    sec = (t1 - t0) + (t2 - t1) * (pb.N / rows) + (t3 - t2)
+    return sec, info["push_edges"] + info["pull_edges"]
+
+
+def cpu_baseline(workload, seeds, rows_per_step):
+    from oracle import oracle as O
+    O.build()
+    tot_s, tot_e = 0.0, 0
+    for s in seeds:
+        sec, edges = oracle_step(O, OracleProblem(O, make_problem(workload, s)), rows_per_step)
+        tot_s += sec
+        tot_e += edges
+    return tot_e / tot_s, tot_s / len(seeds)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cfg = workload_config(args.workload)
+    rows = 64 if args.workload == "di6" else 1025
+    from oracle import oracle as O
+    O.build()
+    pool = [OracleProblem(O, make_problem(args.workload, args.seed_base + k)) for k in range(3)]
+    secs, edges = [], []
+    for k in range(args.warmup + args.steps):
+        sec, e = oracle_step(O, pool[k % len(pool)], rows)
+        if k >= args.warmup:
+            secs.append(sec); edges.append(e)
+    value = float(np.sum(edges) / np.sum(secs))
+    sample = (f"per step: SampleFree of all nodes, the neighbour test of {rows} rows scaled to all N rows, and "
+              f"the full wavefront; problems cycle over seeds {args.seed_base}..{args.seed_base + 2}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": cfg,
+            "ms_per_plan": {"p50": 1e3 * pct(secs, 50), "p99": 1e3 * pct(secs, 99)},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import boxes_on_device, goal_struct, params_struct, space_struct
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    cfg = workload_config(args.workload)
+    total = args.warmup + args.steps
+    seeds = [args.seed_base + 1_000_000 * rank + k for k in range(total)]
+    probs = [make_problem(args.workload, s) for s in seeds]
+    pb0 = probs[0]
+    space, goal = space_struct(pb0), goal_struct(pb0)
+    boxes = [boxes_on_device(pb, dev) for pb in probs]
+    params = [params_struct(pb) for pb in probs]
+    Nn = pb0.N
+    parent = torch.empty(Nn, dtype=torch.int32, device=dev)
+    cost = torch.empty(Nn, dtype=torch.float32, device=dev)
+    path = torch.empty(Nn, dtype=torch.int32, device=dev)
+    graph = N.Graph()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    launches_per_step = 8 if pb0.kind == N.GMT_COST_DI else 5
+
+    def step(k, prof):
+        N.gmt_build_graph(space, boxes[k][0], [float(v) for v in probs[k].x_init], goal, params[k], graph, stream)
+        if k == 0:
+            N.gmt_graph_set_profiling(graph, True)
+        return N.gmt_plan(graph, boxes[k][0], params[k], parent.data_ptr(), cost.data_ptr(), path.data_ptr(),
+                          stream).as_dict()
+
+    # ---- warm-up (untimed)
+    for k in range(args.warmup):
+        step(k, False)
+    torch.cuda.synchronize()
+
+    # ---- timed: inputs resident, L2 flushed between steps (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos, profs = [], []
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for j in range(args.steps):
+        k = args.warmup + j
+        flush.zero_()
+        ev[j][0].record(stream)
+        infos.append(step(k, True))
+        ev[j][1].record(stream)
+        profs.append(N.gmt_graph_get_profile(graph))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    edges = [i["push_edges"] + i["pull_edges"] for i in infos]
+    sum_ms = float(np.sum(step_ms))
+    tot_edges = float(np.sum(edges))
+    if world > 1:
+        t = torch.tensor([sum_ms, tot_edges], dtype=torch.float64, device=dev)
+        mx = t.clone(); torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        sm = t.clone(); torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+        sum_ms_all, tot_edges_all = float(mx[0]), float(sm[1])
+    else:
+        sum_ms_all, tot_edges_all = sum_ms, tot_edges
+    value = tot_edges_all / (sum_ms_all / 1e3)
+
+    # ---- end to end: host inputs (pinned), H2D of the boxes and D2H of the tree each step
+    h_lo = [torch.as_tensor(np.ascontiguousarray(pb.box_lo, np.float32)).pin_memory() for pb in probs]
+    h_hi = [torch.as_tensor(np.ascontiguousarray(pb.box_hi, np.float32)).pin_memory() for pb in probs]
+    d_lo = torch.empty_like(boxes[0][1][0]); d_hi = torch.empty_like(boxes[0][1][1])
+    h_parent = torch.empty(Nn, dtype=torch.int32).pin_memory()
+    h_cost = torch.empty(Nn, dtype=torch.float32).pin_memory()
+    e2e_ms, e2e_edges = [], []
+    bi = bo = 0
+    for j in range(args.steps):
+        k = args.warmup + j
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        d_lo.copy_(h_lo[k], non_blocking=True); d_hi.copy_(h_hi[k], non_blocking=True)
+        bx = N.gmt_boxes(); bx.count = d_lo.shape[0]; bx.lo = d_lo.data_ptr(); bx.hi = d_hi.data_ptr()
+        N.gmt_build_graph(space, bx, [float(v) for v in probs[k].x_init], goal, params[k], graph, stream)
+        info = N.gmt_plan(graph, bx, params[k], parent.data_ptr(), cost.data_ptr(), path.data_ptr(),
+                          stream).as_dict()
+        h_parent.copy_(parent, non_blocking=True); h_cost.copy_(cost, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+        e2e_edges.append(info["push_edges"] + info["pull_edges"])
+        bi = h_lo[k].numel() * 4 + h_hi[k].numel() * 4
+        bo = Nn * 8 + 64
+    e2e_value = float(np.sum(e2e_edges) / (np.sum(e2e_ms) / 1e3))
+    if world > 1:
+        t = torch.tensor([e2e_value], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t)
+        e2e_value = float(t[0])
+
+    # ---- roofline of the dominant kernel
+    kern = {k: float(np.mean([p[k] for p in profs])) for k in
+            ("sample_ms", "pair_ms", "transpose_ms", "scan_ms", "fill_ms", "plan_ms")}
+    dominant = max(kern, key=kern.get)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    d = pb0.d
+    plan_bytes = [8 * i["push_edges"] + 12 * i["pull_edges"] + 8 * d * i["checks"] + 16 * Nn for i in infos]
+    roof = {"kernel": "plan_kernel (wavefront, Alg. 1)", "bound": "hbm",
+            "achieved": float(np.mean(plan_bytes)) / (kern["plan_ms"] / 1e3) / 1e9,
+            "peak": hbm, "unit": "GB/s", "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "traffic": None, "algorithmic_bytes_per_launch": float(np.mean(plan_bytes)),
+            "launch_ms": kern["plan_ms"]}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    if dominant != "plan_ms":
+        roof["note"] = f"dominant stage is {dominant}; plan kernel reported"
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(cfg, seeds=f"{seeds[args.warmup]}..{seeds[-1]} (one seed per step, per rank)",
+                       parallelism=f"replicas x{world}", l2="flushed between steps (256 MiB write)"),
+        "ms_per_plan": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99),
+                        "plan_only_p50": pct([p["plan_ms"] for p in profs], 50),
+                        "plan_only_p99": pct([p["plan_ms"] for p in profs], 99)},
+        "plans_per_s": world * args.steps / (sum_ms_all / 1e3),
+        "kernel_ms_mean": kern,
+        "plan_launch": {"blocks": profs[-1]["plan_blocks"], "threads": profs[-1]["plan_threads"]},
+        "success_rate": float(np.mean([i["status"] == 0 for i in infos])),
+        "mean_edges_checked": float(np.mean(edges)),
+        "wall_s": wall,
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "edges/s", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                "ms_per_plan_p50": pct(e2e_ms, 50)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        seeds_cpu = [seeds[args.warmup + j] for j in range(3)]
+        rows = 256 if args.workload == "di6" else 1025
+        v, sec = cpu_baseline(args.workload, seeds_cpu, rows)
+        line["cpu_baseline"] = {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                "sample": f"3 plans (seeds {seeds_cpu}); per plan: SampleFree, neighbour test of "
+                                          f"{rows} rows scaled to all N rows, full wavefront; "
+                                          f"{1e3 * sec:.0f} ms per full plan"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

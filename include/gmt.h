@@ -177,6 +177,32 @@ typedef struct {
 gmt_status gmt_plan(gmt_graph* graph, const gmt_boxes* boxes, const gmt_params* params, int32_t* parent,
                     float* cost, int32_t* path, gmt_plan_info* info, gmt_stream stream);
 
+/* Launch shape of gmt_plan on this graph (a tuning knob, not a semantic one:
+ * every shape gives the same result).  blocks == 1: one CTA runs the whole
+ * plan with block barriers; blocks > 1: a cooperative grid of that many CTAs
+ * (clamped to what can be co-resident); 0 = automatic (one CTA for N <= 2048,
+ * else one CTA per SM).  threads: CTA size, a multiple of 32 in [64, 1024], or
+ * 0 = automatic. */
+gmt_status gmt_graph_set_launch(gmt_graph* graph, int32_t blocks, int32_t threads);
+
+/* Per-kernel device times of the last gmt_build_graph / gmt_plan on a graph,
+ * recorded with CUDA events on the caller's stream while profiling is on
+ * (milliseconds; 0 for kernels that did not run).  Reading the profile waits
+ * for the recorded events. */
+typedef struct {
+    float sample_ms;     /* SampleFree */
+    float pair_ms;       /* all-pairs cost filter (neighbour bit matrix) */
+    float transpose_ms;  /* in-edge bit matrix (double integrator only) */
+    float scan_ms;       /* row offsets */
+    float fill_ms;       /* CSR columns and costs */
+    float plan_ms;       /* wavefront kernel */
+    int32_t plan_blocks; /* launch shape used by the last plan */
+    int32_t plan_threads;
+} gmt_profile;
+
+gmt_status gmt_graph_set_profiling(gmt_graph* graph, int32_t enable);
+gmt_status gmt_graph_get_profile(gmt_graph* graph, gmt_profile* profile);
+
 /* Theorem 1's radius r = 4 (1+eta)^(1/d) (1/d)^(1/d) (mu_free/zeta_d)^(1/d)
  * (log n / n)^(1/d), zeta_d the volume of the unit d-ball, evaluated in double
  * as 4 * pow((1+eta) * (1/d) * (mu_free/zeta_d) * (log(n)/n), 1/d). */

@@ -451,10 +451,13 @@ int gmt_plan(const Graph<R>& g, const PlanCfg& P, int32_t* parent_out, R* cost_o
         for (int v = 0; v < N; ++v) if (set[v] == OPEN && cost[v] < m) m = cost[v];
         if (m == INF) { success = false; break; }
         // Line 11
+        // The threshold index is kept below 2^24 (exact in FP32); beyond it the
+        // plan stops with an iteration-limit error.
         if (delta == (R)0 || !P.skip_empty) {
             i = i + 1;
-            if (i > ((int64_t)1 << 40)) { status = ORC_ERR_ITER_LIMIT; break; }
+            if (delta != (R)0 && !(m / delta < (R)16777216)) { status = ORC_ERR_ITER_LIMIT; break; }
         } else {
+            if (!(m / delta < (R)16777216)) { status = ORC_ERR_ITER_LIMIT; break; }
             int64_t k = (int64_t)std::ceil(m / delta);
             if (k < i + 1) k = i + 1;
             while (k > i + 1 && (R)(k - 1) * delta >= m) --k;
@@ -700,6 +703,22 @@ void orc_graph_copy(int precision, const void* gv, int32_t* out_row, int32_t* ou
         for (size_t e = 0; e < g->in_cost.size(); ++e) in_cost[e] = (double)g->in_cost[e];
     };
     if (precision == 64) copy((const Graph<double>*)gv); else copy((const Graph<float>*)gv);
+}
+
+// Number of directed edges y -> x with y in rows [row0, row1): the row-slice of
+// the neighbour-set computation, used to time a bounded sample of it.
+int64_t orc_count_edges_rows(int kind, int d, int N, const float* X, float r, int row0, int row1) {
+    int64_t count = 0;
+    float si[MAXD], sj[MAXD];
+    for (int i = row0; i < row1 && i < N; ++i) {
+        for (int a = 0; a < d; ++a) si[a] = X[(size_t)a * N + i];
+        for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            for (int a = 0; a < d; ++a) sj[a] = X[(size_t)a * N + j];
+            if (edge_cost<float>(kind, si, sj, d, r, nullptr) < r) ++count;
+        }
+    }
+    return count;
 }
 
 // ---- planners ----

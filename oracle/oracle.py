@@ -76,6 +76,8 @@ def lib():
         L.orc_dijkstra.argtypes = [I32, P, I32, P, P, P, P, F32, I32, P]; L.orc_dijkstra.restype = F64
         L.orc_graph_edge_free.argtypes = [I32, P, I32, I32, F64, I32, P, P, P, P, F32, I32]
         L.orc_graph_edge_free.restype = I32
+        L.orc_count_edges_rows.argtypes = [I32, I32, I32, P, F32, I32, I32]
+        L.orc_count_edges_rows.restype = I64
         _lib = L
     return _lib
 
@@ -257,6 +259,12 @@ class Graph:
         return bool(lib().orc_graph_edge_free(self.precision, self._h, int(y), int(x), float(c), bl.shape[0],
                                               _p(bl), _p(bh), _p(pl), _p(ph), np.float32(seg_spacing),
                                               traj_points))
+
+
+def count_edges_rows(problem, X, row0, row1):
+    """Edges leaving nodes row0..row1-1 (a slice of the neighbour-set build)."""
+    X = _f32(X)
+    return lib().orc_count_edges_rows(problem.kind, problem.d, X.shape[1], _p(X), np.float32(problem.r), row0, row1)
 
 
 def graph_for(problem, X=None, goal=None, precision=32):

@@ -1,0 +1,190 @@
+"""ctypes binding of libgmt.so: the C ABI of include/gmt.h under the same names.
+
+Argument marshalling only: every step of the planner runs in the library's CUDA
+kernels.  Device arrays are passed as raw pointers (torch tensors' data_ptr());
+the stream is torch's current CUDA stream unless one is given.  There is no CPU
+fallback: if libgmt.so is missing or cannot be loaded, importing this module
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libgmt.so")
+
+GMT_OK, GMT_NO_PATH = 0, 1
+GMT_ERR_INVALID, GMT_ERR_OOM, GMT_ERR_CUDA, GMT_ERR_TIMEOUT, GMT_ERR_ITER_LIMIT, GMT_ERR_ADMISSION = -1, -2, -3, -4, -5, -6
+GMT_COST_EUCLID, GMT_COST_DI = 0, 1
+GMT_MAX_DIM = 10
+GMT_DEBUG_UNREACHABLE_BARRIER = 0x1
+
+STATUS_NAMES = {0: "GMT_OK", 1: "GMT_NO_PATH", -1: "GMT_ERR_INVALID", -2: "GMT_ERR_OOM", -3: "GMT_ERR_CUDA",
+                -4: "GMT_ERR_TIMEOUT", -5: "GMT_ERR_ITER_LIMIT", -6: "GMT_ERR_ADMISSION"}
+
+
+class GmtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class gmt_space(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dim", C.c_int32), ("pos_dim", C.c_int32),
+                ("lo", C.c_float * GMT_MAX_DIM), ("hi", C.c_float * GMT_MAX_DIM)]
+
+
+class gmt_boxes(C.Structure):
+    _fields_ = [("count", C.c_int32), ("lo", C.c_void_p), ("hi", C.c_void_p)]
+
+
+class gmt_goal(C.Structure):
+    _fields_ = [("center", C.c_float * GMT_MAX_DIM), ("radius", C.c_float), ("pos_only", C.c_int32)]
+
+
+class gmt_params(C.Structure):
+    _fields_ = [("n", C.c_int32), ("r", C.c_float), ("lambda_", C.c_float), ("seed", C.c_uint64),
+                ("seg_spacing", C.c_float), ("traj_points", C.c_int32), ("max_iters", C.c_int32),
+                ("max_attempts", C.c_int32), ("eta", C.c_float), ("mu_free", C.c_float),
+                ("spin_limit", C.c_int32), ("debug_flags", C.c_uint32)]
+
+
+class gmt_graph_view(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dim", C.c_int32), ("pos_dim", C.c_int32), ("N", C.c_int32),
+                ("x_pitch", C.c_int32), ("E", C.c_int64), ("r", C.c_float),
+                ("X", C.c_void_p), ("is_goal", C.c_void_p),
+                ("out_row", C.c_void_p), ("out_col", C.c_void_p), ("out_cost", C.c_void_p),
+                ("in_row", C.c_void_p), ("in_col", C.c_void_p), ("in_cost", C.c_void_p)]
+
+
+class gmt_plan_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("goal_node", C.c_int32), ("path_cost", C.c_float), ("path_len", C.c_int32),
+                ("iters", C.c_int64), ("final_i", C.c_int64), ("push_edges", C.c_int64),
+                ("pull_edges", C.c_int64), ("checks", C.c_int64), ("failed", C.c_int64),
+                ("tree_size", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class gmt_profile(C.Structure):
+    _fields_ = [("sample_ms", C.c_float), ("pair_ms", C.c_float), ("transpose_ms", C.c_float),
+                ("scan_ms", C.c_float), ("fill_ms", C.c_float), ("plan_ms", C.c_float),
+                ("plan_blocks", C.c_int32), ("plan_threads", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# Every symbol include/gmt.h declares, with its ctypes signature.
+_P, _I32, _I64, _F32, _F64, _U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double, C.c_uint64
+SIGNATURES = {
+    "gmt_build_graph": (_I32, [C.POINTER(gmt_space), C.POINTER(gmt_boxes), _P, C.POINTER(gmt_goal),
+                               C.POINTER(gmt_params), C.POINTER(C.c_void_p), _P]),
+    "gmt_graph_get_view": (_I32, [_P, C.POINTER(gmt_graph_view)]),
+    "gmt_graph_free": (None, [_P]),
+    "gmt_graph_set_launch": (_I32, [_P, _I32, _I32]),
+    "gmt_plan": (_I32, [_P, C.POINTER(gmt_boxes), C.POINTER(gmt_params), _P, _P, _P, C.POINTER(gmt_plan_info), _P]),
+    "gmt_graph_set_profiling": (_I32, [_P, _I32]),
+    "gmt_graph_get_profile": (_I32, [_P, C.POINTER(gmt_profile)]),
+    "gmt_connection_radius": (_F64, [_I32, _I32, _F64, _F64]),
+    "gmt_last_error": (C.c_char_p, []),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1705_02403_gb300.build` "
+                          "(there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int, allow=(GMT_OK,)):
+    if status not in allow:
+        raise GmtError(status, lib.gmt_last_error().decode())
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ----------------------------------------------------------------- C ABI names
+def gmt_last_error() -> str:
+    return lib.gmt_last_error().decode()
+
+
+def gmt_connection_radius(n: int, d: int, eta: float = 0.0, mu_free: float = 1.0) -> float:
+    return lib.gmt_connection_radius(n, d, eta, mu_free)
+
+
+class Graph:
+    """Owner of a gmt_graph handle (freed with gmt_graph_free)."""
+
+    def __init__(self):
+        self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib.gmt_graph_free(self.handle)
+            self.handle = C.c_void_p(None)
+
+
+def gmt_build_graph(space: gmt_space, boxes: gmt_boxes, x_init, goal: gmt_goal, params: gmt_params,
+                    graph: Graph | None = None, stream=None) -> Graph:
+    """x_init: host sequence of floats (state dimension)."""
+    g = graph if graph is not None else Graph()
+    xi = (C.c_float * GMT_MAX_DIM)(*[float(v) for v in x_init])
+    _check(lib.gmt_build_graph(C.byref(space), C.byref(boxes), C.cast(xi, C.c_void_p), C.byref(goal),
+                               C.byref(params), C.byref(g.handle), _stream(stream)))
+    return g
+
+
+def gmt_graph_get_view(graph: Graph) -> gmt_graph_view:
+    v = gmt_graph_view()
+    _check(lib.gmt_graph_get_view(graph.handle, C.byref(v)))
+    return v
+
+
+def gmt_graph_set_launch(graph: Graph, blocks: int, threads: int) -> None:
+    _check(lib.gmt_graph_set_launch(graph.handle, blocks, threads))
+
+
+def gmt_graph_set_profiling(graph: Graph, enable: bool) -> None:
+    _check(lib.gmt_graph_set_profiling(graph.handle, int(enable)))
+
+
+def gmt_graph_get_profile(graph: Graph) -> dict:
+    p = gmt_profile()
+    _check(lib.gmt_graph_get_profile(graph.handle, C.byref(p)))
+    return p.as_dict()
+
+
+def gmt_graph_free(graph: Graph) -> None:
+    if graph.handle.value:
+        lib.gmt_graph_free(graph.handle)
+        graph.handle = C.c_void_p(None)
+
+
+def gmt_plan(graph: Graph, boxes: gmt_boxes, params: gmt_params, parent_ptr: int, cost_ptr: int,
+             path_ptr: int | None = None, stream=None, allow_errors=False) -> gmt_plan_info:
+    info = gmt_plan_info()
+    st = lib.gmt_plan(graph.handle, C.byref(boxes), C.byref(params), C.c_void_p(parent_ptr), C.c_void_p(cost_ptr),
+                      C.c_void_p(path_ptr or 0), C.byref(info), _stream(stream))
+    if not allow_errors:
+        _check(st, allow=(GMT_OK, GMT_NO_PATH))
+    return info

@@ -1,0 +1,410 @@
+// C ABI of the planner (include/gmt.h): argument checks, device buffers of the
+// opaque handles, and the launch sequence of every entry point.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+using namespace gmtk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+gmt_status fail(gmt_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+gmt_status cuda_fail(cudaError_t e, const char* what) {
+    const gmt_status s = e == cudaErrorMemoryAllocation ? GMT_ERR_OOM : GMT_ERR_CUDA;
+    return fail(s, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define GMT_CUDA(call, what)                              \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+template <typename T>
+cudaError_t grow(T** p, size_t* cap, size_t need) {
+    if (*p && *cap >= need) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (need == 0) need = 1;
+    cudaError_t e = cudaMalloc((void**)p, need * sizeof(T));
+    if (e == cudaSuccess) *cap = need;
+    return e;
+}
+
+// Smallest float t with sqrtf(t) >= r: for s >= 0, sqrtf(s) < r  <=>  s < t,
+// because correctly rounded square root is monotone.
+float euclid_threshold(float r) {
+    float t = r * r;
+    while (t > 0.0f && std::sqrt(t) >= r) t = std::nextafter(t, 0.0f);
+    while (std::sqrt(t) < r) t = std::nextafter(t, INFINITY);
+    return t;
+}
+
+}  // namespace
+
+struct gmt_graph {
+    int kind = 0, d = 0, dp = 0, N = 0, pitch = 0;
+    long long E = 0;
+    float r = 0.0f;
+    float pos_lo[3] = {0, 0, 0}, pos_hi[3] = {0, 0, 0};
+    int plan_blocks = 0, plan_threads = 0;   // 0 = automatic
+    float* X = nullptr;            size_t cap_X = 0;
+    uint8_t* is_goal = nullptr;    size_t cap_is_goal = 0;
+    int* out_row = nullptr;        size_t cap_out_row = 0;
+    int* in_row_own = nullptr;     size_t cap_in_row_own = 0;
+    int* out_count = nullptr;      size_t cap_out_count = 0;
+    int* in_count = nullptr;       size_t cap_in_count = 0;
+    int* out_col = nullptr;        size_t cap_out_col = 0;
+    float* out_cost = nullptr;     size_t cap_out_cost = 0;
+    int* in_col_own = nullptr;     size_t cap_in_col_own = 0;
+    float* in_cost_own = nullptr;  size_t cap_in_cost_own = 0;
+    uint32_t* mask = nullptr;      size_t cap_mask = 0;
+    uint32_t* maskT = nullptr;     size_t cap_maskT = 0;
+    int* flags = nullptr;          size_t cap_flags = 0;
+    // plan workspace
+    float* ocost = nullptr;        size_t cap_ocost = 0;
+    int* stamp = nullptr;          size_t cap_stamp = 0;
+    int* lists = nullptr;          size_t cap_lists = 0;
+    PlanCtl* ctl = nullptr;        size_t cap_ctl = 0;
+    // pinned host mirrors
+    PlanCtl* h_ctl = nullptr;
+    int* h_scalars = nullptr;
+    // profiling: event pairs around each kernel group
+    enum { kSample, kPair, kTranspose, kScan, kFill, kPlan, kStages };
+    bool profiling = false;
+    bool stage_ran[kStages] = {};
+    cudaEvent_t ev[kStages][2] = {};
+    int last_blocks = 0, last_threads = 0;
+
+    cudaError_t mark(int stage, int which, cudaStream_t st) {
+        if (!profiling) return cudaSuccess;
+        if (!ev[stage][which]) {
+            cudaError_t e = cudaEventCreate(&ev[stage][which]);
+            if (e != cudaSuccess) return e;
+        }
+        if (which == 1) stage_ran[stage] = true;
+        return cudaEventRecord(ev[stage][which], st);
+    }
+
+    const int* in_row() const { return kind == GMT_COST_DI ? in_row_own : out_row; }
+    const int* in_col() const { return kind == GMT_COST_DI ? in_col_own : out_col; }
+    const float* in_cost() const { return kind == GMT_COST_DI ? in_cost_own : out_cost; }
+
+    ~gmt_graph() {
+        void* dev[] = {X, is_goal, out_row, in_row_own, out_count, in_count, out_col, out_cost, in_col_own,
+                       in_cost_own, mask, maskT, flags, ocost, stamp, lists, ctl};
+        for (void* p : dev)
+            if (p) cudaFree(p);
+        if (h_ctl) cudaFreeHost(h_ctl);
+        if (h_scalars) cudaFreeHost(h_scalars);
+        for (auto& pair : ev)
+            for (cudaEvent_t e : pair)
+                if (e) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+gmt_status check_space(const gmt_space* sp) {
+    if (!sp) return fail(GMT_ERR_INVALID, "space is NULL");
+    if (sp->kind == GMT_COST_EUCLID) {
+        if (sp->dim < 2 || sp->dim > GMT_MAX_DIM || sp->pos_dim != sp->dim)
+            return fail(GMT_ERR_INVALID, "Euclidean space needs 2 <= dim <= 10 and pos_dim == dim");
+    } else if (sp->kind == GMT_COST_DI) {
+        if (sp->dim != 6 || sp->pos_dim != 3)
+            return fail(GMT_ERR_INVALID, "double-integrator space needs dim == 6, pos_dim == 3");
+    } else {
+        return fail(GMT_ERR_INVALID, "unknown cost kind");
+    }
+    for (int a = 0; a < sp->dim; ++a)
+        if (!(sp->lo[a] < sp->hi[a]) || !std::isfinite(sp->lo[a]) || !std::isfinite(sp->hi[a]))
+            return fail(GMT_ERR_INVALID, "state bounds must be finite with lo < hi");
+    return GMT_OK;
+}
+
+gmt_status check_boxes(const gmt_boxes* b) {
+    if (!b) return fail(GMT_ERR_INVALID, "boxes is NULL");
+    if (b->count < 0) return fail(GMT_ERR_INVALID, "negative box count");
+    if (b->count > 0 && (!b->lo || !b->hi)) return fail(GMT_ERR_INVALID, "box arrays are NULL");
+    return GMT_OK;
+}
+
+float resolve_radius(const gmt_params* p, int d) {
+    if (p->r > 0.0f) return p->r;
+    return (float)gmt_connection_radius(p->n, d, p->eta, p->mu_free);
+}
+
+gmt_status check_params(const gmt_params* p, int d) {
+    if (!p) return fail(GMT_ERR_INVALID, "params is NULL");
+    if (p->n < 1 || p->n > (1 << 24)) return fail(GMT_ERR_INVALID, "n must be in [1, 2^24]");
+    if (!(p->lambda >= 0.0f && p->lambda <= 1.0f)) return fail(GMT_ERR_INVALID, "lambda must be in [0, 1]");
+    if (p->r <= 0.0f && (!(p->eta >= 0.0f) || !(p->mu_free > 0.0f)))
+        return fail(GMT_ERR_INVALID, "r <= 0 needs eta >= 0 and mu_free > 0 (Theorem 1 radius)");
+    const float r = resolve_radius(p, d);
+    if (!(r > 0.0f) || !std::isfinite(r)) return fail(GMT_ERR_INVALID, "connection radius must be positive");
+    if (!(p->seg_spacing > 0.0f)) return fail(GMT_ERR_INVALID, "seg_spacing must be positive");
+    if (p->traj_points < 2) return fail(GMT_ERR_INVALID, "traj_points must be >= 2");
+    return GMT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gmt_last_error(void) { return g_last_error.c_str(); }
+
+double gmt_connection_radius(int32_t n, int32_t d, double eta, double mu_free) {
+    const double pi = 3.14159265358979323846;
+    const double zeta = std::pow(pi, (double)d / 2.0) / std::tgamma((double)d / 2.0 + 1.0);
+    const double base = (1.0 + eta) * (1.0 / (double)d) * (mu_free / zeta) * (std::log((double)n) / (double)n);
+    return 4.0 * std::pow(base, 1.0 / (double)d);
+}
+
+gmt_status gmt_build_graph(const gmt_space* space, const gmt_boxes* boxes, const float* x_init, const gmt_goal* goal,
+                           const gmt_params* params, gmt_graph** graph, gmt_stream stream) {
+    gmt_status s;
+    if ((s = check_space(space)) != GMT_OK) return s;
+    if ((s = check_boxes(boxes)) != GMT_OK) return s;
+    if ((s = check_params(params, space->dim)) != GMT_OK) return s;
+    if (!x_init || !goal || !graph) return fail(GMT_ERR_INVALID, "x_init, goal and graph must be non-NULL");
+    if (!(goal->radius >= 0.0f)) return fail(GMT_ERR_INVALID, "goal radius must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+
+    const bool fresh = *graph == nullptr;
+    gmt_graph* g = fresh ? new gmt_graph() : *graph;
+    auto bail = [&](gmt_status st_) {
+        if (fresh) delete g;
+        return st_;
+    };
+
+    g->kind = space->kind;
+    g->d = space->dim;
+    g->dp = space->pos_dim;
+    g->N = params->n + 1;
+    g->pitch = (g->N + 31) / 32 * 32;
+    g->r = resolve_radius(params, space->dim);
+    g->E = 0;
+    for (int a = 0; a < 3 && a < g->dp; ++a) { g->pos_lo[a] = space->lo[a]; g->pos_hi[a] = space->hi[a]; }
+    const size_t N = (size_t)g->N, P = (size_t)g->pitch, W = (N + 31) / 32;
+
+    SpaceArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
+    sa.kind = g->kind; sa.d = g->d; sa.dp = g->dp; sa.N = g->N; sa.pitch = g->pitch;
+    for (int a = 0; a < g->d; ++a) {
+        sa.lo[a] = space->lo[a]; sa.hi[a] = space->hi[a];
+        sa.x0[a] = x_init[a]; sa.gc[a] = goal->center[a];
+    }
+    sa.grho = goal->radius;
+    sa.gd = goal->pos_only ? g->dp : g->d;
+    sa.key0 = (uint32_t)(params->seed & 0xffffffffu);
+    sa.key1 = (uint32_t)(params->seed >> 32);
+    sa.stream = 0;
+    sa.max_attempts = params->max_attempts > 0 ? params->max_attempts : 65536;
+    sa.r = g->r;
+    sa.r2_threshold = euclid_threshold(g->r);
+    BoxArgs ba{boxes->count, boxes->lo, boxes->hi};
+
+    cudaError_t e;
+#define GROW(ptr, n) if ((e = grow(&g->ptr, &g->cap_##ptr, (n))) != cudaSuccess) return bail(cuda_fail(e, "allocating " #ptr))
+    GROW(X, (size_t)g->d * P);
+    GROW(is_goal, P);
+    GROW(out_row, N + 1);
+    GROW(out_count, N);
+    GROW(mask, W * P);
+    GROW(flags, 4);
+    GROW(ocost, N);
+    GROW(stamp, N);
+    GROW(lists, 5 * N);
+    GROW(ctl, 1);
+    if (g->kind == GMT_COST_DI) {
+        GROW(in_row_own, N + 1);
+        GROW(in_count, N);
+        GROW(maskT, W * P);
+    }
+    if (!g->h_ctl && (e = cudaMallocHost((void**)&g->h_ctl, sizeof(PlanCtl))) != cudaSuccess)
+        return bail(cuda_fail(e, "allocating pinned control block"));
+    if (!g->h_scalars && (e = cudaMallocHost((void**)&g->h_scalars, 4 * sizeof(int))) != cudaSuccess)
+        return bail(cuda_fail(e, "allocating pinned scalars"));
+
+#define LAUNCH(call, what) if ((e = (call)) != cudaSuccess) return bail(cuda_fail(e, what))
+    for (bool& b : g->stage_ran) b = false;
+    LAUNCH(cudaMemsetAsync(g->flags, 0, 4 * sizeof(int), st), "memset");
+    LAUNCH(cudaMemsetAsync(g->out_count, 0, N * sizeof(int), st), "memset");
+    if (g->kind == GMT_COST_DI) LAUNCH(cudaMemsetAsync(g->in_count, 0, N * sizeof(int), st), "memset");
+    LAUNCH(g->mark(gmt_graph::kSample, 0, st), "event");
+    LAUNCH(launch_sample(sa, ba, g->X, g->is_goal, g->flags, st), "sample kernel");
+    LAUNCH(g->mark(gmt_graph::kSample, 1, st), "event");
+    LAUNCH(g->mark(gmt_graph::kPair, 0, st), "event");
+    LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, st), "pair filter kernel");
+    LAUNCH(g->mark(gmt_graph::kPair, 1, st), "event");
+    if (g->kind == GMT_COST_DI) {
+        LAUNCH(g->mark(gmt_graph::kTranspose, 0, st), "event");
+        LAUNCH(launch_transpose(sa, g->mask, g->maskT, g->in_count, st), "transpose kernel");
+        LAUNCH(g->mark(gmt_graph::kTranspose, 1, st), "event");
+    }
+    LAUNCH(g->mark(gmt_graph::kScan, 0, st), "event");
+    LAUNCH(launch_scan(g->out_count, g->out_row, g->N, st), "scan kernel");
+    if (g->kind == GMT_COST_DI) LAUNCH(launch_scan(g->in_count, g->in_row_own, g->N, st), "scan kernel");
+    LAUNCH(g->mark(gmt_graph::kScan, 1, st), "event");
+    LAUNCH(cudaMemcpyAsync(g->h_scalars, g->flags, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
+    LAUNCH(cudaMemcpyAsync(g->h_scalars + 1, g->out_row + N, sizeof(int), cudaMemcpyDeviceToHost, st),
+           "edge count readback");
+    LAUNCH(cudaStreamSynchronize(st), "graph build");
+    const int flags = g->h_scalars[0];
+    if (flags & kSampleBadInit) return bail(fail(GMT_ERR_INVALID, "x_init is outside X or inside an obstacle"));
+    if (flags & kSampleExhausted)
+        return bail(fail(GMT_ERR_INVALID, "a sample exhausted max_attempts (X_free or X_goal n X_free too small)"));
+    g->E = g->h_scalars[1];
+    const size_t E = (size_t)g->E;
+    GROW(out_col, E);
+    GROW(out_cost, E);
+    if (g->kind == GMT_COST_DI) {
+        GROW(in_col_own, E);
+        GROW(in_cost_own, E);
+    }
+    LAUNCH(g->mark(gmt_graph::kFill, 0, st), "event");
+    LAUNCH(launch_fill(sa, g->X, g->mask, g->out_row, g->out_col, g->out_cost, false, st), "fill kernel");
+    if (g->kind == GMT_COST_DI)
+        LAUNCH(launch_fill(sa, g->X, g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own, true, st),
+               "fill kernel");
+    LAUNCH(g->mark(gmt_graph::kFill, 1, st), "event");
+#undef GROW
+#undef LAUNCH
+    *graph = g;
+    return GMT_OK;
+}
+
+gmt_status gmt_graph_get_view(const gmt_graph* g, gmt_graph_view* v) {
+    if (!g || !v) return fail(GMT_ERR_INVALID, "graph and view must be non-NULL");
+    v->kind = g->kind; v->dim = g->d; v->pos_dim = g->dp; v->N = g->N; v->x_pitch = g->pitch;
+    v->E = g->E; v->r = g->r;
+    v->X = g->X; v->is_goal = g->is_goal;
+    v->out_row = g->out_row; v->out_col = g->out_col; v->out_cost = g->out_cost;
+    v->in_row = g->in_row(); v->in_col = g->in_col(); v->in_cost = g->in_cost();
+    return GMT_OK;
+}
+
+void gmt_graph_free(gmt_graph* g) { delete g; }
+
+gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* params, int32_t* parent, float* cost,
+                    int32_t* path, gmt_plan_info* info, gmt_stream stream) {
+    if (!g || g->N == 0) return fail(GMT_ERR_INVALID, "graph is NULL or not built");
+    gmt_status s;
+    if ((s = check_boxes(boxes)) != GMT_OK) return s;
+    if ((s = check_params(params, g->d)) != GMT_OK) return s;
+    if (!parent || !cost || !info) return fail(GMT_ERR_INVALID, "parent, cost and info must be non-NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = g->N;
+
+    PlanArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.kind = g->kind; a.d = g->d; a.dp = g->dp; a.N = N; a.pitch = g->pitch;
+    a.X = g->X; a.is_goal = g->is_goal;
+    a.out_row = g->out_row; a.out_col = g->out_col;
+    a.in_row = g->in_row(); a.in_col = g->in_col(); a.in_cost = g->in_cost();
+    a.boxes = BoxArgs{boxes->count, boxes->lo, boxes->hi};
+    a.r = g->r;
+    a.delta = params->lambda * g->r;
+    a.seg_spacing = params->seg_spacing;
+    a.traj_points = params->traj_points;
+    a.max_iters = params->max_iters > 0 ? params->max_iters : N + 1;
+    a.spin_limit = params->spin_limit;
+    a.debug_flags = params->debug_flags;
+    a.cost = cost; a.parent = parent; a.path = path;
+    a.ocost = g->ocost; a.stamp = g->stamp;
+    a.list_g[0] = g->lists; a.list_g[1] = g->lists + N;
+    a.list_open[0] = g->lists + 2 * (size_t)N; a.list_open[1] = g->lists + 3 * (size_t)N;
+    a.list_cand = g->lists + 4 * (size_t)N;
+    a.ctl = g->ctl;
+    for (int k = 0; k < 3; ++k) { a.pos_lo[k] = g->pos_lo[k]; a.pos_hi[k] = g->pos_hi[k]; }
+
+    int blocks = g->plan_blocks, threads = g->plan_threads;
+    if (threads <= 0) threads = 512;
+    if (blocks <= 0) blocks = N <= 2048 ? 1 : -1;
+    if (blocks == 1) threads = g->plan_threads > 0 ? g->plan_threads : 1024;
+    if (blocks < 0 || blocks > 1) {
+        int dev = 0, sms = 0;
+        GMT_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+        GMT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+        const int maxb = plan_max_coresident_blocks(g->kind, g->dp, threads);
+        if (maxb <= 0) return fail(GMT_ERR_CUDA, "plan kernel cannot be resident with this block size");
+        if (blocks < 0) blocks = sms;
+        if (blocks > maxb) blocks = maxb;
+    }
+    GMT_CUDA(cudaMemsetAsync(g->ctl, 0, sizeof(PlanCtl), st), "memset");
+    g->stage_ran[gmt_graph::kPlan] = false;
+    GMT_CUDA(g->mark(gmt_graph::kPlan, 0, st), "event");
+    GMT_CUDA(launch_plan(a, blocks, threads, st), "plan kernel launch");
+    GMT_CUDA(g->mark(gmt_graph::kPlan, 1, st), "event");
+    g->last_blocks = blocks;
+    g->last_threads = threads;
+    GMT_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(PlanCtl), cudaMemcpyDeviceToHost, st), "control readback");
+    GMT_CUDA(cudaStreamSynchronize(st), "plan kernel");
+    const PlanCtl& c = *g->h_ctl;
+    std::memset(info, 0, sizeof(*info));
+    info->status = c.status;
+    info->goal_node = c.goal_node;
+    info->path_len = c.path_len;
+    info->path_cost = INFINITY;
+    if (c.status == GMT_OK && c.goal_node >= 0) {
+        unsigned bits = (unsigned)(c.goal_key >> 32);
+        std::memcpy(&info->path_cost, &bits, sizeof(float));
+    }
+    info->iters = c.iters;
+    info->final_i = c.final_i;
+    info->push_edges = (int64_t)c.push_edges;
+    info->pull_edges = (int64_t)c.pull_edges;
+    info->checks = (int64_t)c.checks;
+    info->failed = (int64_t)c.failed;
+    info->tree_size = (int64_t)c.tree_size;
+    if (c.status == GMT_ERR_TIMEOUT) return fail(GMT_ERR_TIMEOUT, "a device-side wait ran out (spin limit)");
+    if (c.status == GMT_ERR_ITER_LIMIT) return fail(GMT_ERR_ITER_LIMIT, "group expansions exceeded max_iters");
+    return (gmt_status)c.status;
+}
+
+gmt_status gmt_graph_set_profiling(gmt_graph* g, int32_t enable) {
+    if (!g) return fail(GMT_ERR_INVALID, "graph is NULL");
+    g->profiling = enable != 0;
+    return GMT_OK;
+}
+
+gmt_status gmt_graph_get_profile(gmt_graph* g, gmt_profile* out) {
+    if (!g || !out) return fail(GMT_ERR_INVALID, "graph and profile must be non-NULL");
+    float ms[gmt_graph::kStages] = {};
+    for (int k = 0; k < gmt_graph::kStages; ++k) {
+        if (!g->stage_ran[k] || !g->ev[k][0] || !g->ev[k][1]) continue;
+        GMT_CUDA(cudaEventSynchronize(g->ev[k][1]), "profile event");
+        GMT_CUDA(cudaEventElapsedTime(&ms[k], g->ev[k][0], g->ev[k][1]), "profile event");
+    }
+    out->sample_ms = ms[gmt_graph::kSample];
+    out->pair_ms = ms[gmt_graph::kPair];
+    out->transpose_ms = ms[gmt_graph::kTranspose];
+    out->scan_ms = ms[gmt_graph::kScan];
+    out->fill_ms = ms[gmt_graph::kFill];
+    out->plan_ms = ms[gmt_graph::kPlan];
+    out->plan_blocks = g->last_blocks;
+    out->plan_threads = g->last_threads;
+    return GMT_OK;
+}
+
+gmt_status gmt_graph_set_launch(gmt_graph* g, int32_t blocks, int32_t threads) {
+    if (!g) return fail(GMT_ERR_INVALID, "graph is NULL");
+    if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32 != 0))
+        return fail(GMT_ERR_INVALID, "threads must be 0 or a multiple of 32 in [64, 1024]");
+    if (blocks < 0) return fail(GMT_ERR_INVALID, "blocks must be >= 0");
+    g->plan_blocks = blocks;
+    g->plan_threads = threads;
+    return GMT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,224 @@
+// Device building blocks of the GB300 GMT* planner: Philox4x32-10, the
+// connection costs, point-in-box tests and bounded inter-block waits.
+//
+// All floating-point decisions use IEEE FP32 with round-to-nearest; the
+// library is compiled with -fmad=false -prec-div=true -prec-sqrt=true
+// -ftz=false, and every expression below is written in the evaluation order
+// the planner's specification fixes (left to right), so results are
+// reproducible bit for bit.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gmt.h"
+
+namespace gmtk {
+
+constexpr int kMaxDim = GMT_MAX_DIM;
+constexpr int kWarp = 32;
+
+__device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  A round maps the counter
+// (c0, c1, c2, c3) under key (k0, k1) to
+//   (hi(B c2) ^ c1 ^ k0, lo(B c2), hi(A c0) ^ c3 ^ k1, lo(A c0)),
+// A = 0xD2511F53, B = 0xCD9E8D57; the key advances by (0x9E3779B9, 0xBB67AE85)
+// after every round.  Ten rounds.
+// ---------------------------------------------------------------------------
+struct Ctr4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ Ctr4 philox4x32_10(Ctr4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t hiA = __umulhi(0xD2511F53u, c.x), loA = 0xD2511F53u * c.x;
+        const uint32_t hiB = __umulhi(0xCD9E8D57u, c.z), loB = 0xCD9E8D57u * c.z;
+        c = Ctr4{hiB ^ c.y ^ k0, loB, hiA ^ c.w ^ k1, loA};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Top 24 bits of a word scaled by 2^-24: exact, in [0, 1).
+__device__ __forceinline__ float unit_float(uint32_t w) { return (float)(w >> 8) * 0x1p-24f; }
+
+// ---------------------------------------------------------------------------
+// Obstacles: closed axis-aligned boxes, lo[b*DP + a] <= p[a] <= hi[b*DP + a].
+// ---------------------------------------------------------------------------
+template <int DP>
+__device__ __forceinline__ bool in_box(const float* p, const float* lo, const float* hi, int b) {
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < DP; ++a) inside = inside && (lo[b * DP + a] <= p[a]) && (p[a] <= hi[b * DP + a]);
+    return inside;
+}
+
+template <int DP>
+__device__ __forceinline__ bool in_any_box(const float* p, const float* lo, const float* hi, int nbox) {
+    for (int b = 0; b < nbox; ++b)
+        if (in_box<DP>(p, lo, hi, b)) return true;
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// Euclidean cost: sqrt of sum_a (to_a - from_a)^2 accumulated in axis order.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ float sq_dist(const float* from, const float* to) {
+    float s = 0.0f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const float t = to[a] - from[a];
+        s = s + t * t;
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Double integrator (3 axes, state [p v]): for fixed arrival time tau the
+// minimum-effort cost is J(tau) = tau + a/tau - b/tau^2 + c/tau^3 with
+//   a = 4(|v0|^2 + v0.v1 + |v1|^2), b = 12 dp.(v0+v1), c = 12 |dp|^2;
+// the optimal tau is the smallest positive root of
+//   q(tau) = tau^4 - a tau^2 + 2b tau - 3c = ((tau tau - a) tau + 2b) tau - 3c,
+// bracketed on tau_k = r (k/32), k = 1..32 (first k with q >= 0, none -> no
+// edge since J >= tau) and refined by 24 halvings (q(mid) < 0 -> lo = mid).
+// J is evaluated as ((c/tau - b)/tau + a)/tau + tau.
+// ---------------------------------------------------------------------------
+struct DICoef { float a, b, c, b2, c3; };
+
+__device__ __forceinline__ DICoef di_coef(const float* s0, const float* s1) {
+    float n00 = 0.0f, n01 = 0.0f, n11 = 0.0f, bs = 0.0f, cs = 0.0f;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const float p0 = s0[ax], v0 = s0[3 + ax], p1 = s1[ax], v1 = s1[3 + ax];
+        const float dp = p1 - p0;
+        n00 = n00 + v0 * v0;
+        n01 = n01 + v0 * v1;
+        n11 = n11 + v1 * v1;
+        bs = bs + dp * (v0 + v1);
+        cs = cs + dp * dp;
+    }
+    DICoef k;
+    k.a = 4.0f * ((n00 + n01) + n11);
+    k.b = 12.0f * bs;
+    k.c = 12.0f * cs;
+    k.b2 = 2.0f * k.b;
+    k.c3 = 3.0f * k.c;
+    return k;
+}
+
+__device__ __forceinline__ float di_q(const DICoef& k, float t) { return ((t * t - k.a) * t + k.b2) * t - k.c3; }
+
+constexpr int kDIGrid = 32;
+constexpr int kDIBisect = 24;
+
+// Arrival time tau* (or +inf when no root lies in (0, r]).
+__device__ __forceinline__ float di_tau(const DICoef& k, float r) {
+    float lo = 0.0f, hi = f_inf();
+    for (int g = 1; g <= kDIGrid; ++g) {
+        const float tg = r * ((float)g / (float)kDIGrid);
+        if (di_q(k, tg) >= 0.0f) { hi = tg; break; }
+        lo = tg;
+    }
+    if (hi == f_inf()) return hi;
+    for (int s = 0; s < kDIBisect; ++s) {
+        const float mid = lo + (hi - lo) * 0.5f;
+        if (di_q(k, mid) < 0.0f) lo = mid; else hi = mid;
+    }
+    return hi;
+}
+
+__device__ __forceinline__ float di_J(const DICoef& k, float t) { return ((k.c / t - k.b) / t + k.a) / t + t; }
+
+// Cost from state s0 to state s1 (+inf when no root lies in (0, r]).
+__device__ __forceinline__ float di_cost(const float* s0, const float* s1, float r) {
+    const DICoef k = di_coef(s0, s1);
+    const float t = di_tau(k, r);
+    if (t == f_inf()) return t;
+    return di_J(k, t);
+}
+
+// Conservative rejection of pairs that cannot have J < r (never rejects an
+// edge; the exact test follows).  With s = v0 + v1 the cost is exactly
+//   J(tau) = tau + |v1 - v0|^2 / tau + 3 |2 dp - s tau|^2 / tau^3,
+// so J < r implies (i) 2 |v1 - v0| <= J < r (AM-GM) and (ii) for the arrival
+// time tau < r: |2 dp - s tau| < sqrt((r - tau) tau^3 / 3) <= 3 r^2 / 16, i.e.
+// the point 2 dp lies within 3 r^2/16 of the segment {s tau : 0 <= tau <= r}.
+// Both tests use r inflated by 1% to absorb FP32 rounding.
+__device__ __forceinline__ bool di_may_connect(const float* s0, const float* s1, float r) {
+    const float rr = r * 1.01f;
+    float dv2 = 0.0f, qs = 0.0f, ss = 0.0f, q[3], sv[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const float dv = s1[3 + ax] - s0[3 + ax];
+        dv2 = dv2 + dv * dv;
+        q[ax] = 2.0f * (s1[ax] - s0[ax]);
+        sv[ax] = s0[3 + ax] + s1[3 + ax];
+        qs = qs + q[ax] * sv[ax];
+        ss = ss + sv[ax] * sv[ax];
+    }
+    if (4.0f * dv2 >= rr * rr) return false;
+    float t = ss > 0.0f ? qs / ss : 0.0f;
+    t = fminf(fmaxf(t, 0.0f), rr);
+    float d2 = 0.0f;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const float e = q[ax] - t * sv[ax];
+        d2 = d2 + e * e;
+    }
+    const float bound = 3.0f * rr * rr / 16.0f;
+    return d2 < bound * bound;
+}
+
+// Position of the minimum-effort trajectory (cubic Hermite curve) at s in [0,1]:
+//   p = ((h00 p0 + (h10 tau) v0) + h01 p1) + (h11 tau) v1,
+//   h00 = (2 s^3 - 3 s^2) + 1, h10 = (s^3 - 2 s^2) + s, h01 = 3 s^2 - 2 s^3,
+//   h11 = s^3 - s^2, s^2 = s s, s^3 = s^2 s.
+__device__ __forceinline__ void hermite_point(const float* s0, const float* s1, float tau, float s, float* p) {
+    const float s2 = s * s;
+    const float s3 = s2 * s;
+    const float h00 = (2.0f * s3 - 3.0f * s2) + 1.0f;
+    const float h10 = (s3 - 2.0f * s2) + s;
+    const float h01 = 3.0f * s2 - 2.0f * s3;
+    const float h11 = s3 - s2;
+    const float h10t = h10 * tau, h11t = h11 * tau;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p[a] = ((h00 * s0[a] + h10t * s0[3 + a]) + h01 * s1[a]) + h11t * s1[3 + a];
+}
+
+// ---------------------------------------------------------------------------
+// Memory-ordered global accesses for inter-block synchronisation.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+// Warp-aggregated append: every lane with `want` gets a distinct slot of
+// list[*count], one atomic per warp.  Returns the slot (or -1).
+__device__ __forceinline__ int warp_append_slot(bool want, int* count) {
+    const unsigned mask = __ballot_sync(0xffffffffu, want);
+    if (mask == 0) return -1;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return want ? base + __popc(mask & ((1u << lane) - 1u)) : -1;
+}
+
+__device__ __forceinline__ unsigned float_key(float c) { return __float_as_uint(c); }  // c >= 0
+
+}  // namespace gmtk

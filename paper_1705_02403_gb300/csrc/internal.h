@@ -1,0 +1,101 @@
+// Internal interfaces between the C-ABI layer (capi.cu) and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gmt.h"
+
+namespace gmtk {
+
+constexpr int kMaxDimHost = GMT_MAX_DIM;
+
+// Problem description passed by value to the sampling and graph kernels.
+struct SpaceArgs {
+    int kind, d, dp;
+    int N;        // n + 1 nodes
+    int pitch;    // row pitch of X and of the neighbour bit matrix (N rounded up to 32)
+    float lo[kMaxDimHost], hi[kMaxDimHost];
+    float x0[kMaxDimHost];
+    float gc[kMaxDimHost];
+    float grho;
+    int gd;       // axes of the goal ball
+    uint32_t key0, key1, stream;
+    int max_attempts;
+    float r;
+    float r2_threshold;  // Euclidean: edge iff squared distance < r2_threshold (== sqrt(s) < r)
+};
+
+struct BoxArgs {
+    int count;
+    const float* lo;
+    const float* hi;
+};
+
+// Flags written by the sampling kernel.
+enum { kSampleBadInit = 1, kSampleExhausted = 2 };
+
+// sample.cu / graph.cu
+cudaError_t launch_sample(const SpaceArgs& s, BoxArgs boxes, float* X, uint8_t* is_goal, int* flags,
+                          cudaStream_t st);
+cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* out_count,
+                             cudaStream_t st);
+cudaError_t launch_transpose(const SpaceArgs& s, const uint32_t* mask, uint32_t* maskT, int* in_count,
+                             cudaStream_t st);
+cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st);
+cudaError_t launch_fill(const SpaceArgs& s, const float* X, const uint32_t* mask, const int* row, int* col,
+                        float* cost, bool incoming, cudaStream_t st);
+
+// Workspace and control block of one plan (all device memory).
+struct PlanCtl {
+    unsigned bar_count, bar_gen;
+    int error;
+    int status;
+    int g_count[2];
+    int open_count[2];
+    int keep_count[2];
+    int cand_count;
+    unsigned min_keep[2];
+    unsigned min_new[2];
+    int goal_flag[2];
+    int iters;
+    int final_i;
+    int goal_node;
+    int path_len;
+    unsigned long long goal_key;
+    unsigned long long push_edges, pull_edges, checks, failed, tree_size;
+};
+
+struct PlanArgs {
+    int kind, d, dp, N, pitch;
+    const float* X;
+    const uint8_t* is_goal;
+    const int* out_row;
+    const int* out_col;
+    const int* in_row;
+    const int* in_col;
+    const float* in_cost;
+    BoxArgs boxes;
+    float pos_lo[3], pos_hi[3];
+    float r, delta, seg_spacing;
+    int traj_points, max_iters, spin_limit;
+    unsigned debug_flags;
+    float* cost;
+    int* parent;
+    int* path;
+    float* ocost;
+    int* stamp;
+    int* list_g[2];
+    int* list_open[2];
+    int* list_cand;
+    PlanCtl* ctl;
+};
+
+// plan.cu
+// Launches the wavefront for one plan.  blocks <= 1: a single CTA runs the
+// whole plan with block barriers; otherwise a cooperative grid of `blocks`
+// CTAs synchronises through bounded global barriers.
+cudaError_t launch_plan(const PlanArgs& a, int blocks, int threads, cudaStream_t st);
+int plan_max_coresident_blocks(int kind, int dp, int threads);
+
+}  // namespace gmtk

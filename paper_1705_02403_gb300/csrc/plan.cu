@@ -1,0 +1,462 @@
+// Algorithm 1 (Group Marching Tree) as one persistent CUDA kernel.
+//
+// A "team" of threads runs every wavefront iteration of one plan without
+// returning to the host: either one CTA (block barriers) or a cooperative grid
+// (bounded global barriers, co-residency guaranteed by the cooperative launch).
+// Each iteration i has three phases separated by team barriers:
+//
+//   A  group selection (Line 3): the open list is split into
+//      G_i = {v open : cost(v) <= theta_i} and the nodes that stay open; the
+//      minimum cost of those is reduced for the skip-ahead; the open-set
+//      snapshot `ocost` (cost if open, +inf otherwise) is brought up to date
+//      with the previous iteration's changes (G closed, new nodes opened).
+//   B  frontier push (Line 4): one warp per node of G scans its out-row;
+//      every unexplored neighbour (cost == +inf) is claimed once per iteration
+//      through an atomic stamp and appended to the candidate list.
+//   C  lazy parent (Lines 5-9): one warp per candidate x scans its in-row,
+//      gathers ocost[y] and takes argmin of (ocost[y] + c(y, x), y); the warp
+//      then checks that single edge (points spread over the lanes) and, if it
+//      is free, commits parent/cost and appends x to the next open list.
+//
+// After phase C every thread reads the same totals and decides (Line 12):
+// success if G_i held a goal node, failure if no node stays open, else the
+// next threshold index is the smallest i' > i with theta_{i'} >= min open cost
+// (iterations whose group would be empty are no-ops and are skipped).
+// Lists are appended with one atomic per warp (ballot + popc prefix), the
+// prefix-sum compaction of Section IV.  Counters and lists that the next
+// iteration needs are double-buffered by parity so that resets need no extra
+// barrier.
+#include <climits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gmtk {
+
+constexpr int kDefaultSpinLimit = 1 << 22;
+
+__device__ __forceinline__ int ldcg_i(const int* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned ldcg_u(const unsigned* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldcg_f(const float* p) { return __ldcg(p); }
+
+struct BlockTeam {
+    __device__ __forceinline__ int rank() const { return threadIdx.x; }
+    __device__ __forceinline__ int size() const { return blockDim.x; }
+    __device__ __forceinline__ bool sync(PlanCtl*) const {
+        __syncthreads();
+        return true;
+    }
+};
+
+// Sense-reversing barrier over all CTAs of a cooperative grid.  Every poll is
+// counted; after spin_limit polls (or once another CTA has reported an error)
+// the wait gives up, records GMT_ERR_TIMEOUT and returns false, so the kernel
+// ends with an error status instead of hanging.
+struct GridTeam {
+    unsigned expected;
+    int spin_limit;
+    __device__ __forceinline__ int rank() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ __forceinline__ int size() const { return gridDim.x * blockDim.x; }
+    __device__ bool sync(PlanCtl* ctl) const {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned gen = ld_acquire(&ctl->bar_gen);
+            const unsigned arrived = atom_add_acq_rel(&ctl->bar_count, 1u);
+            if (arrived == expected - 1) {
+                ctl->bar_count = 0;
+                st_release(&ctl->bar_gen, gen + 1);
+            } else {
+                int spins = 0;
+                while (ld_acquire(&ctl->bar_gen) == gen) {
+                    if (ld_volatile(&ctl->error) != 0) break;
+                    if (++spins > spin_limit) {
+                        atomicCAS(&ctl->error, 0, (int)GMT_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        return ld_volatile(&ctl->error) == 0;
+    }
+};
+
+// ---------------------------------------------------------------- edge check
+// Geometric edge y -> x of length L: m = max(2, ceil(L/spacing) + 1) points
+// p_k = y + t_k (x - y), t_k = k/(m-1); collision if one lies in a closed box.
+template <int DP>
+__device__ bool segment_free_warp(const float* y, const float* x, float L, float spacing, const float* blo,
+                                  const float* bhi, int nbox) {
+    const int lane = threadIdx.x & 31;
+    int m = (int)ceilf(L / spacing) + 1;
+    if (m < 2) m = 2;
+    const float denom = (float)(m - 1);
+    for (int k0 = 0; k0 < m; k0 += 32) {
+        const int k = k0 + lane;
+        bool hit = false;
+        if (k < m) {
+            const float t = (float)k / denom;
+            float p[DP];
+#pragma unroll
+            for (int a = 0; a < DP; ++a) p[a] = y[a] + t * (x[a] - y[a]);
+            hit = in_any_box<DP>(p, blo, bhi, nbox);
+        }
+        if (__any_sync(0xffffffffu, hit)) return false;
+    }
+    return true;
+}
+
+// Double-integrator edge: `points` samples of the Hermite trajectory at
+// s_k = k/(points-1); collision if one lies in a box or outside the position
+// bounds.
+__device__ bool trajectory_free_warp(const float* y, const float* x, float r, int points, const float* plo,
+                                     const float* phi, const float* blo, const float* bhi, int nbox) {
+    const int lane = threadIdx.x & 31;
+    const float tau = di_tau(di_coef(y, x), r);
+    const float denom = (float)(points - 1);
+    for (int k0 = 0; k0 < points; k0 += 32) {
+        const int k = k0 + lane;
+        bool hit = false;
+        if (k < points) {
+            const float s = (float)k / denom;
+            float p[3];
+            hermite_point(y, x, tau, s, p);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) hit = hit || p[a] < plo[a] || p[a] > phi[a];
+            hit = hit || in_any_box<3>(p, blo, bhi, nbox);
+        }
+        if (__any_sync(0xffffffffu, hit)) return false;
+    }
+    return true;
+}
+
+// Largest box count staged in shared memory (2 * count * DP floats).
+__host__ __device__ constexpr int smem_box_cap(int dp) { return 4096 / dp; }
+
+// ------------------------------------------------------------------- kernel
+template <class Team, int KIND, int DP>
+__global__ void __launch_bounds__(1024) plan_kernel(PlanArgs A, Team team) {
+    extern __shared__ float sbox[];
+    const int D = KIND == GMT_COST_DI ? 6 : DP;
+    const int nbs = A.boxes.count <= smem_box_cap(DP) ? A.boxes.count : 0;
+    for (int t = threadIdx.x; t < nbs * DP; t += blockDim.x) {
+        sbox[t] = A.boxes.lo[t];
+        sbox[nbs * DP + t] = A.boxes.hi[t];
+    }
+    __syncthreads();
+    const float* blo = nbs ? sbox : A.boxes.lo;
+    const float* bhi = nbs ? sbox + nbs * DP : A.boxes.hi;
+    const int nbox = A.boxes.count;
+
+    PlanCtl* ctl = A.ctl;
+    const int rank = team.rank(), size = team.size();
+    const int lane = threadIdx.x & 31;
+    const int gwarp = rank >> 5, nwarps = size >> 5;
+    const float INF = f_inf();
+    const unsigned INF_KEY = 0x7f800000u;
+    const int N = A.N;
+
+    // Lines 1-2: x_init is the only open node and the root of the tree.
+    for (int v = rank; v < N; v += size) {
+        const float c0 = v == 0 ? 0.0f : INF;
+        A.cost[v] = c0;
+        A.ocost[v] = c0;
+        A.parent[v] = -1;
+        A.stamp[v] = -1;
+    }
+    if (rank == 0) {
+        A.list_open[0][0] = 0;
+        ctl->open_count[0] = 1;
+        ctl->open_count[1] = 0;
+        ctl->g_count[0] = ctl->g_count[1] = 0;
+        ctl->min_keep[0] = ctl->min_keep[1] = INF_KEY;
+        ctl->min_new[0] = ctl->min_new[1] = INF_KEY;
+        ctl->goal_flag[0] = ctl->goal_flag[1] = 0;
+        ctl->cand_count = 0;
+        ctl->goal_key = ~0ull;
+    }
+    bool ok = team.sync(ctl);
+
+    long long i = 0;
+    float theta = 0.0f;
+    int p = 0, q = 0, it = 0;
+    int status = GMT_OK;
+    unsigned long long n_push = 0, n_pull = 0, n_checks = 0, n_failed = 0;
+
+    while (ok) {
+        if (it >= A.max_iters) { status = GMT_ERR_ITER_LIMIT; break; }
+        int* G = A.list_g[p];
+        const int* cur = A.list_open[q];
+        int* nxt = A.list_open[q ^ 1];
+
+        // ---- phase A: snapshot update from the previous iteration, group selection
+        if (it > 0) {
+            const int ng_prev = ldcg_i(&ctl->g_count[p ^ 1]);
+            const int* Gprev = A.list_g[p ^ 1];
+            for (int t = rank; t < ng_prev; t += size) A.ocost[ldcg_i(&Gprev[t])] = INF;
+            const int k0 = ldcg_i(&ctl->keep_count[p ^ 1]), k1 = ldcg_i(&ctl->open_count[q]);
+            for (int t = k0 + rank; t < k1; t += size) {
+                const int x = ldcg_i(&cur[t]);
+                A.ocost[x] = ldcg_f(&A.cost[x]);
+            }
+        }
+        if (rank == 0) ctl->cand_count = 0;
+        {
+            const int ncur = ldcg_i(&ctl->open_count[q]);
+            for (int base = gwarp * 32; base < ncur; base += nwarps * 32) {
+                const int t = base + lane;
+                bool in_g = false, keep = false;
+                int v = -1;
+                float c = INF;
+                if (t < ncur) {
+                    v = ldcg_i(&cur[t]);
+                    c = ldcg_f(&A.cost[v]);
+                    in_g = c <= theta;
+                    keep = !in_g;
+                }
+                const int sg = warp_append_slot(in_g, &ctl->g_count[p]);
+                if (in_g) {
+                    G[sg] = v;
+                    if (A.is_goal[v]) ctl->goal_flag[p] = 1;
+                }
+                const int sk = warp_append_slot(keep, &ctl->open_count[q ^ 1]);
+                if (keep) nxt[sk] = v;
+                const unsigned kmin = __reduce_min_sync(0xffffffffu, keep ? float_key(c) : INF_KEY);
+                if (lane == 0 && kmin != INF_KEY) atomicMin(&ctl->min_keep[p], kmin);
+            }
+        }
+        if (!(ok = team.sync(ctl))) break;
+
+        // ---- phase B: frontier push from G
+        if (rank == 0) {
+            ctl->keep_count[p] = ldcg_i(&ctl->open_count[q ^ 1]);
+            ctl->g_count[p ^ 1] = 0;
+            ctl->min_keep[p ^ 1] = INF_KEY;
+            ctl->min_new[p ^ 1] = INF_KEY;
+            ctl->goal_flag[p ^ 1] = 0;
+            ctl->open_count[q] = 0;
+        }
+        {
+            const int ng = ldcg_i(&ctl->g_count[p]);
+            for (int zi = gwarp; zi < ng; zi += nwarps) {
+                const int z = ldcg_i(&G[zi]);
+                const int e0 = __ldg(&A.out_row[z]), e1 = __ldg(&A.out_row[z + 1]);
+                if (lane == 0) n_push += (unsigned long long)(e1 - e0);
+                for (int eb = e0; eb < e1; eb += 32) {
+                    const int e = eb + lane;
+                    bool want = false;
+                    int x = -1;
+                    if (e < e1) {
+                        x = __ldg(&A.out_col[e]);
+                        if (ldcg_f(&A.cost[x]) == INF) want = atomicExch(&A.stamp[x], it) != it;
+                    }
+                    const int sc = warp_append_slot(want, &ctl->cand_count);
+                    if (want) A.list_cand[sc] = x;
+                }
+            }
+        }
+        if (!(ok = team.sync(ctl))) break;
+
+        // ---- phase C: lazy parent selection, one collision check, commit
+        {
+            const int nc = ldcg_i(&ctl->cand_count);
+            for (int ci = gwarp; ci < nc; ci += nwarps) {
+                const int x = ldcg_i(&A.list_cand[ci]);
+                const int r0 = __ldg(&A.in_row[x]), r1 = __ldg(&A.in_row[x + 1]);
+                float bc = INF;
+                int by = INT_MAX, be = -1;
+                for (int e = r0 + lane; e < r1; e += 32) {
+                    const int y = __ldg(&A.in_col[e]);
+                    const float oc = ldcg_f(&A.ocost[y]);
+                    if (oc < INF) {
+                        const float c = oc + __ldg(&A.in_cost[e]);
+                        if (c < bc || (c == bc && y < by)) { bc = c; by = y; be = e; }
+                    }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const float oc = __shfl_xor_sync(0xffffffffu, bc, off);
+                    const int oy = __shfl_xor_sync(0xffffffffu, by, off);
+                    const int oe = __shfl_xor_sync(0xffffffffu, be, off);
+                    if (oc < bc || (oc == bc && oy < by)) { bc = oc; by = oy; be = oe; }
+                }
+                // The node of G that pushed x is an open in-neighbour, so be >= 0;
+                // the guard only keeps a broken invariant from reading out of bounds.
+                if (be < 0) {
+                    if (lane == 0) { ++n_checks; ++n_failed; atomicCAS(&ctl->error, 0, (int)GMT_ERR_CUDA); }
+                    continue;
+                }
+                float sy[D], sx[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    sy[a] = __ldg(&A.X[(size_t)a * A.pitch + by]);
+                    sx[a] = __ldg(&A.X[(size_t)a * A.pitch + x]);
+                }
+                bool free_edge;
+                if (KIND == GMT_COST_EUCLID)
+                    free_edge = segment_free_warp<DP>(sy, sx, __ldg(&A.in_cost[be]), A.seg_spacing, blo, bhi, nbox);
+                else
+                    free_edge = trajectory_free_warp(sy, sx, A.r, A.traj_points, A.pos_lo, A.pos_hi, blo, bhi, nbox);
+                if (lane == 0) {
+                    n_pull += (unsigned long long)(r1 - r0);
+                    ++n_checks;
+                    if (free_edge) {
+                        A.cost[x] = bc;
+                        A.parent[x] = by;
+                        const int s = atomicAdd(&ctl->open_count[q ^ 1], 1);
+                        nxt[s] = x;
+                        atomicMin(&ctl->min_new[p], float_key(bc));
+                    } else {
+                        ++n_failed;
+                    }
+                }
+            }
+        }
+        if (!(ok = team.sync(ctl))) break;
+
+        // ---- Line 12 / Line 11: termination test, next threshold
+        const int goal = ldcg_i(&ctl->goal_flag[p]);
+        const int n_open = ldcg_i(&ctl->open_count[q ^ 1]);
+        const unsigned mk = min(ldcg_u(&ctl->min_keep[p]), ldcg_u(&ctl->min_new[p]));
+        ++it;
+        if (goal) { status = GMT_OK; break; }
+        if (n_open == 0) { status = GMT_NO_PATH; break; }
+        const float m = __uint_as_float(mk);
+        if (A.delta == 0.0f) {
+            theta = m;
+            i = i + 1;
+        } else {
+            const float qk = m / A.delta;
+            if (!(qk < 16777216.0f)) { status = GMT_ERR_ITER_LIMIT; break; }  // i stays below 2^24
+            long long k = (long long)ceilf(qk);
+            if (k < i + 1) k = i + 1;
+            while (k > i + 1 && (float)(k - 1) * A.delta >= m) --k;
+            while ((float)k * A.delta < m) ++k;
+            i = k;
+            theta = (float)i * A.delta;
+        }
+        p ^= 1;
+        q ^= 1;
+    }
+
+    // ---- result: minimum-cost goal node (ties by index), counters, path
+    if (ok) {
+        unsigned long long tree = 0;
+        for (int v = rank; v < N; v += size) {
+            const float c = ldcg_f(&A.cost[v]);
+            if (c < INF) {
+                ++tree;
+                if (status == GMT_OK && A.is_goal[v])
+                    atomicMin(&ctl->goal_key, ((unsigned long long)float_key(c) << 32) | (unsigned)v);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            n_push += __shfl_xor_sync(0xffffffffu, n_push, off);
+            n_pull += __shfl_xor_sync(0xffffffffu, n_pull, off);
+            n_checks += __shfl_xor_sync(0xffffffffu, n_checks, off);
+            n_failed += __shfl_xor_sync(0xffffffffu, n_failed, off);
+            tree += __shfl_xor_sync(0xffffffffu, tree, off);
+        }
+        if (lane == 0) {
+            atomicAdd(&ctl->push_edges, n_push);
+            atomicAdd(&ctl->pull_edges, n_pull);
+            atomicAdd(&ctl->checks, n_checks);
+            atomicAdd(&ctl->failed, n_failed);
+            atomicAdd(&ctl->tree_size, tree);
+        }
+        ok = team.sync(ctl);
+    }
+    if (rank == 0) {
+        const int err = ld_volatile(&ctl->error);
+        ctl->status = err ? err : status;
+        ctl->iters = it;
+        ctl->final_i = (int)i;
+        ctl->goal_node = -1;
+        ctl->path_len = 0;
+        if (ok && status == GMT_OK) {
+            const int g = (int)(ctl->goal_key & 0xffffffffu);
+            ctl->goal_node = g;
+            int len = 1, v = g;
+            while (v > 0 && len <= N) {
+                v = ldcg_i(&A.parent[v]);
+                ++len;
+            }
+            if (v != 0) len = 0;  // not a chain back to x_init: report no path
+            ctl->path_len = len;
+            if (A.path) {
+                v = g;
+                for (int k = len - 1; k >= 0; --k) {
+                    A.path[k] = v;
+                    if (v > 0) v = ldcg_i(&A.parent[v]);
+                }
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------- launcher
+namespace {
+template <int KIND, int DP>
+cudaError_t plan_t(const PlanArgs& a, int blocks, int threads, cudaStream_t st) {
+    const int nbs = a.boxes.count <= smem_box_cap(DP) ? a.boxes.count : 0;
+    const size_t smem = (size_t)2 * nbs * DP * sizeof(float);
+    if (blocks <= 1) {
+        plan_kernel<BlockTeam, KIND, DP><<<1, threads, smem, st>>>(a, BlockTeam{});
+        return cudaGetLastError();
+    }
+    GridTeam team;
+    team.expected = (unsigned)blocks + ((a.debug_flags & GMT_DEBUG_UNREACHABLE_BARRIER) ? 1u : 0u);
+    team.spin_limit = a.spin_limit > 0 ? a.spin_limit : kDefaultSpinLimit;
+    PlanArgs args = a;
+    void* params[] = {&args, &team};
+    return cudaLaunchCooperativeKernel((const void*)plan_kernel<GridTeam, KIND, DP>, dim3(blocks), dim3(threads),
+                                       params, smem, st);
+}
+
+template <int KIND, int DP>
+int occupancy_t(int threads) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = (size_t)2 * smem_box_cap(DP) * DP * sizeof(float);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel<GridTeam, KIND, DP>, threads, smem);
+    return per_sm * sms;
+}
+}  // namespace
+
+cudaError_t launch_plan(const PlanArgs& a, int blocks, int threads, cudaStream_t st) {
+    if (a.kind == GMT_COST_DI) return plan_t<GMT_COST_DI, 3>(a, blocks, threads, st);
+    switch (a.dp) {
+        case 2: return plan_t<GMT_COST_EUCLID, 2>(a, blocks, threads, st);
+        case 3: return plan_t<GMT_COST_EUCLID, 3>(a, blocks, threads, st);
+        case 4: return plan_t<GMT_COST_EUCLID, 4>(a, blocks, threads, st);
+        case 5: return plan_t<GMT_COST_EUCLID, 5>(a, blocks, threads, st);
+        case 6: return plan_t<GMT_COST_EUCLID, 6>(a, blocks, threads, st);
+        case 7: return plan_t<GMT_COST_EUCLID, 7>(a, blocks, threads, st);
+        case 8: return plan_t<GMT_COST_EUCLID, 8>(a, blocks, threads, st);
+        case 9: return plan_t<GMT_COST_EUCLID, 9>(a, blocks, threads, st);
+        case 10: return plan_t<GMT_COST_EUCLID, 10>(a, blocks, threads, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int plan_max_coresident_blocks(int kind, int dp, int threads) {
+    if (kind == GMT_COST_DI) return occupancy_t<GMT_COST_DI, 3>(threads);
+    switch (dp) {
+        case 2: return occupancy_t<GMT_COST_EUCLID, 2>(threads);
+        case 3: return occupancy_t<GMT_COST_EUCLID, 3>(threads);
+        case 4: return occupancy_t<GMT_COST_EUCLID, 4>(threads);
+        case 5: return occupancy_t<GMT_COST_EUCLID, 5>(threads);
+        case 6: return occupancy_t<GMT_COST_EUCLID, 6>(threads);
+        case 7: return occupancy_t<GMT_COST_EUCLID, 7>(threads);
+        case 8: return occupancy_t<GMT_COST_EUCLID, 8>(threads);
+        case 9: return occupancy_t<GMT_COST_EUCLID, 9>(threads);
+        case 10: return occupancy_t<GMT_COST_EUCLID, 10>(threads);
+        default: return 0;
+    }
+}
+
+}  // namespace gmtk

@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer arrays (CSR, parents, counters) and every FP32 value (samples, edge
+costs, tree costs) must match bit for bit: both sides evaluate the same IEEE
+FP32 expressions in the same order without FMA.  Sizes: the 2D workload at its
+full size (n = 1024) over many seeds; the 6D double integrator at its full size
+(n = 4096) for a few seeds and at n = 600 for more; plus edge cases.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1705_02403_gb300 import envgen
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1705_02403_gb300 import planner
+    return planner
+
+
+def bits(a):
+    return np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+
+
+def gpu_run(P, pb, launch=None, build_only=False, **over):
+    pl = P.Planner(pb).build()
+    v = pl.view()
+    out = {"X": v.X.cpu().numpy(), "goal": v.is_goal.cpu().numpy(), "E": v.E,
+           "out_row": v.out_row.cpu().numpy(), "out_col": v.out_col.cpu().numpy(),
+           "out_cost": v.out_cost.cpu().numpy(), "in_row": v.in_row.cpu().numpy(),
+           "in_col": v.in_col.cpu().numpy(), "in_cost": v.in_cost.cpu().numpy(), "planner": pl}
+    if build_only:
+        return out
+    if launch is not None:
+        pl.set_launch(*launch)
+    info = pl.plan(**over)
+    out.update(parent=pl.parent.cpu().numpy(), cost=pl.cost.cpu().numpy(), info=info,
+               path=pl.path.cpu().numpy()[:info["path_len"]])
+    return out
+
+
+def oracle_run(O, pb, X=None, goal=None, **kw):
+    if X is None:
+        X, goal = O.sample(pb)
+    g = O.Graph(pb.kind, pb.d, pb.dp, X, goal, pb.r if pb.r > 0 else np.float32(O.radius_thm1(pb.n, pb.d)))
+    parent, cost, info = g.plan(pb.box_lo, pb.box_hi, pb.lo[:pb.dp], pb.hi[:pb.dp], pb.lam, pb.seg_spacing,
+                                pb.traj_points, **kw)
+    return X, goal, g, parent, cost, info
+
+
+INFO_KEYS = ["status", "goal_node", "iters", "final_i", "push_edges", "pull_edges", "checks", "failed", "tree_size"]
+
+
+def assert_same(O, G, X, goal, g, parent, cost, info, check_graph=True):
+    assert np.array_equal(bits(G["X"]), bits(X)), "samples differ"
+    assert np.array_equal(G["goal"], goal), "goal flags differ"
+    if check_graph:
+        c = g.csr()
+        assert G["E"] == g.num_edges
+        assert np.array_equal(G["out_row"], c.out_row) and np.array_equal(G["out_col"], c.out_col)
+        assert np.array_equal(bits(G["out_cost"]), bits(c.out_cost))
+        assert np.array_equal(G["in_row"], c.in_row) and np.array_equal(G["in_col"], c.in_col)
+        assert np.array_equal(bits(G["in_cost"]), bits(c.in_cost))
+    assert np.array_equal(G["parent"], parent), "parent arrays differ"
+    assert np.array_equal(bits(G["cost"]), bits(cost)), "cost arrays differ"
+    for k in INFO_KEYS:
+        assert G["info"][k] == info[k], (k, G["info"][k], info[k])
+    if info["status"] == O.OK:
+        assert np.float32(G["info"]["path_cost"]) == np.float32(info["path_cost"])
+        assert list(G["path"]) == O.path_to(parent, info["goal_node"])
+
+
+def test_geometric_2d_full_size_many_seeds(O, P):
+    for seed in range(40):
+        pb = envgen.cfg1_2d(seed)
+        G = gpu_run(P, pb)
+        assert_same(O, G, *oracle_run(O, pb), check_graph=seed < 10)
+
+
+def test_double_integrator_small_many_seeds(O, P):
+    for seed in range(6):
+        pb = envgen.di6(seed=seed, n=600, r=2.8)
+        G = gpu_run(P, pb)
+        assert_same(O, G, *oracle_run(O, pb))
+
+
+def test_double_integrator_full_size(O, P):
+    for seed in (1, 2):
+        pb = envgen.cfg2_di6(seed)
+        G = gpu_run(P, pb)
+        assert_same(O, G, *oracle_run(O, pb))
+
+
+@pytest.mark.parametrize("launch", [(1, 1024), (1, 256), (2, 512), (7, 256), (0, 0), (152, 1024)])
+def test_every_launch_shape_gives_the_same_tree(O, P, launch):
+    for pb in (envgen.cfg1_2d(5), envgen.di6(seed=3, n=600, r=2.8)):
+        G = gpu_run(P, pb, launch=launch)
+        assert_same(O, G, *oracle_run(O, pb), check_graph=False)
+
+
+@pytest.mark.parametrize("d", [3, 4, 10])
+def test_geometric_higher_dimensions(O, P, d):
+    pb = envgen.geometric(seed=d, d=d, n=700, nbox=12, r={3: 0.3, 4: 0.45, 10: 1.0}[d])
+    G = gpu_run(P, pb, launch=(4, 256))
+    assert_same(O, G, *oracle_run(O, pb))
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.2, 1.0])
+def test_lambda_values(O, P, lam):
+    pb = envgen.cfg1_2d(7).with_(lam=lam)
+    assert_same(O, gpu_run(P, pb), *oracle_run(O, pb))
+    pb = envgen.di6(seed=4, n=500, r=2.8, lam=lam)
+    assert_same(O, gpu_run(P, pb, launch=(3, 512)), *oracle_run(O, pb))
+
+
+def test_edge_cases(O, P):
+    # n = 1: x_init plus the goal sample only
+    pb = envgen.geometric(1, d=2, n=1, nbox=3, r=0.12)
+    assert_same(O, gpu_run(P, pb), *oracle_run(O, pb))
+    # no obstacles, ragged N (not a multiple of 32), Theorem 1 radius
+    pb = envgen.geometric(2, d=2, n=777, nbox=0, r=0.0)
+    assert_same(O, gpu_run(P, pb), *oracle_run(O, pb))
+    # x_init inside the goal ball: success at cost 0 after the first group
+    pb = envgen.geometric(3, d=2, n=200, nbox=4, r=0.12).with_(x_init=np.array([0.94, 0.95], np.float32))
+    G = gpu_run(P, pb)
+    assert G["info"]["status"] == O.OK and G["info"]["path_cost"] == 0.0
+    assert_same(O, G, *oracle_run(O, pb))
+    # goal unreachable: a closed wall around the goal ball
+    wall_lo = np.array([[0.8, 0.8]], np.float32)
+    wall_hi = np.array([[1.0, 0.82]], np.float32)
+    wall2_lo = np.array([[0.8, 0.8]], np.float32)
+    wall2_hi = np.array([[0.82, 1.0]], np.float32)
+    pb = envgen.geometric(4, d=2, n=400, nbox=0, r=0.12).with_(
+        box_lo=np.concatenate([wall_lo, wall2_lo]), box_hi=np.concatenate([wall_hi, wall2_hi]))
+    G = gpu_run(P, pb)
+    assert G["info"]["status"] == O.NO_PATH
+    assert_same(O, G, *oracle_run(O, pb))
+    # many boxes: beyond what the plan kernel stages in shared memory
+    rng = np.random.default_rng(0)
+    c = rng.random((3000, 2)); s = rng.uniform(0.001, 0.004, (3000, 2))
+    lo, hi = (c - s).astype(np.float32), (c + s).astype(np.float32)
+    keep = ~(np.all((lo <= 0.05) & (0.05 <= hi), 1) | np.all((lo <= 1.0) & (0.9 <= hi), 1))
+    pb = envgen.geometric(5, d=2, n=900, nbox=0, r=0.1).with_(box_lo=lo[keep], box_hi=hi[keep])
+    assert_same(O, gpu_run(P, pb, launch=(8, 512)), *oracle_run(O, pb))
+
+
+def test_iteration_cap(O, P):
+    pb = envgen.cfg1_2d(0)
+    G = gpu_run(P, pb, allow_errors=True, max_iters=3)
+    assert G["info"]["status"] == -5
+
+
+def test_bad_x_init_is_an_error(O, P):
+    from paper_1705_02403_gb300 import _native as N
+    pb = envgen.cfg1_2d(0)
+    c = (pb.box_lo[0] + pb.box_hi[0]) / 2
+    with pytest.raises(N.GmtError) as e:
+        P.Planner(pb.with_(x_init=c.astype(np.float32))).build()
+    assert e.value.status == N.GMT_ERR_INVALID
+
+
+def test_bounded_barrier_wait_times_out(O, P):
+    # A barrier that waits for one CTA more than the grid has: every wait runs
+    # out after spin_limit polls and the call returns GMT_ERR_TIMEOUT; the
+    # context stays usable and the next plan is correct.
+    from paper_1705_02403_gb300 import _native as N
+    pb = envgen.cfg1_2d(1)
+    pl = P.Planner(pb).build()
+    pl.set_launch(4, 256)
+    info = pl.plan(allow_errors=True, debug_flags=N.GMT_DEBUG_UNREACHABLE_BARRIER, spin_limit=2000)
+    assert info["status"] == N.GMT_ERR_TIMEOUT
+    torch.cuda.synchronize()
+    info = pl.plan()
+    X, goal, g, parent, cost, oinfo = oracle_run(O, pb)
+    assert np.array_equal(pl.parent.cpu().numpy(), parent) and info["goal_node"] == oinfo["goal_node"]
+
+
+def test_fp64_rerun_within_1e5(O, P):
+    # (i) every GPU tree node's cost, re-accumulated in FP64 along the GPU's own
+    # parent pointers with FP64 edge costs, agrees to 1e-5 relative.
+    # (ii) the full FP64 oracle: where its tree equals the FP32 one, the goal
+    # costs agree to 1e-5.
+    for pb in (envgen.cfg1_2d(2), envgen.di6(seed=2, n=600, r=2.8)):
+        G = gpu_run(P, pb)
+        X, parent, cost = G["X"], G["parent"], G["cost"]
+        c64 = np.full(len(parent), np.inf)
+        c64[0] = 0.0
+        order = np.argsort(cost)
+        for v in order:
+            p = parent[v]
+            if p < 0:
+                continue
+            if pb.kind == O.EUCLID:
+                e = np.linalg.norm(X[:, v].astype(np.float64) - X[:, p].astype(np.float64))
+            else:
+                e, _ = O.cost_di_f64(X[:, p].astype(np.float64), X[:, v].astype(np.float64), 2 * pb.r, 64, 60)
+            c64[v] = c64[p] + e
+        fin = np.isfinite(cost)
+        assert np.all(np.abs(cost[fin] - c64[fin]) <= 1e-5 * np.maximum(c64[fin], 1e-30))
+        g64 = O.Graph(pb.kind, pb.d, pb.dp, X, G["goal"], pb.r, precision=64)
+        p64, cst64, i64 = g64.plan(pb.box_lo, pb.box_hi, pb.lo[:pb.dp], pb.hi[:pb.dp], pb.lam, pb.seg_spacing,
+                                   pb.traj_points)
+        if np.array_equal(p64, parent) and i64["status"] == O.OK:
+            assert abs(i64["path_cost"] - G["info"]["path_cost"]) <= 1e-5 * i64["path_cost"]
