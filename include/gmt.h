@@ -185,6 +185,31 @@ gmt_status gmt_plan(gmt_graph* graph, const gmt_boxes* boxes, const gmt_params* 
  * 0 = automatic. */
 gmt_status gmt_graph_set_launch(gmt_graph* graph, int32_t blocks, int32_t threads);
 
+/* Allocation-free planning (an implementation entry point; the paper has no
+ * counterpart).  Runs the same wavefront kernel as gmt_plan, for callers that
+ * must not allocate device memory while they plan: a replanning loop inside a
+ * control cycle (cudaMalloc/cudaFree can synchronise the device and have no
+ * latency bound), code running while a stream is captured into a CUDA graph,
+ * or systems whose memory is fixed at start-up.
+ *   space: HOST struct; its position bounds are used by double-integrator
+ *          trajectory checks and must match the graph's kind and dimensions.
+ *   graph: HOST struct of DEVICE arrays describing the neighbour CSR and the
+ *          samples (layout as gmt_graph_view; e.g. from gmt_graph_get_view or
+ *          the caller's own buffers).  graph->N <= GMT_STATIC_MAX_NODES, else
+ *          GMT_ERR_INVALID.
+ *   boxes, params, parent, cost, path, info, stream: as for gmt_plan.
+ * The kernel's scratch is one fixed __device__ array inside the library
+ * (about 1.8 MB on each GPU that loads it, held until the process exits); no
+ * cudaMalloc, cudaFree or other allocating call is made.  The first call on a
+ * device looks up that array's address; make it before any stream capture.
+ * Every call on a device shares the array (its contents persist between calls;
+ * each call clears the control block it needs), so calls that overlap on the
+ * GPU race: serialise them.  Synchronises `stream`; returns info->status. */
+#define GMT_STATIC_MAX_NODES 65536
+gmt_status gmt_plan_static(const gmt_space* space, const gmt_graph_view* graph, const gmt_boxes* boxes,
+                           const gmt_params* params, int32_t* parent, float* cost, int32_t* path,
+                           gmt_plan_info* info, gmt_stream stream);
+
 /* Per-kernel device times of the last gmt_build_graph / gmt_plan on a graph,
  * recorded with CUDA events on the caller's stream while profiling is on
  * (milliseconds; 0 for kernels that did not run).  Reading the profile waits

@@ -86,6 +86,8 @@ SIGNATURES = {
     "gmt_graph_free": (None, [_P]),
     "gmt_graph_set_launch": (_I32, [_P, _I32, _I32]),
     "gmt_plan": (_I32, [_P, C.POINTER(gmt_boxes), C.POINTER(gmt_params), _P, _P, _P, C.POINTER(gmt_plan_info), _P]),
+    "gmt_plan_static": (_I32, [C.POINTER(gmt_space), C.POINTER(gmt_graph_view), C.POINTER(gmt_boxes),
+                               C.POINTER(gmt_params), _P, _P, _P, C.POINTER(gmt_plan_info), _P]),
     "gmt_graph_set_profiling": (_I32, [_P, _I32]),
     "gmt_graph_get_profile": (_I32, [_P, C.POINTER(gmt_profile)]),
     "gmt_connection_radius": (_F64, [_I32, _I32, _F64, _F64]),
@@ -162,6 +164,19 @@ def gmt_graph_get_view(graph: Graph) -> gmt_graph_view:
 
 def gmt_graph_set_launch(graph: Graph, blocks: int, threads: int) -> None:
     _check(lib.gmt_graph_set_launch(graph.handle, blocks, threads))
+
+
+def gmt_plan_static(space: gmt_space, view: gmt_graph_view, boxes: gmt_boxes, params: gmt_params,
+                    parent_ptr: int, cost_ptr: int, path_ptr: int | None = None, stream=None,
+                    allow_errors=False) -> gmt_plan_info:
+    """Allocation-free plan on caller-described device arrays (see gmt.h)."""
+    info = gmt_plan_info()
+    st = lib.gmt_plan_static(C.byref(space), C.byref(view), C.byref(boxes), C.byref(params), C.c_void_p(parent_ptr),
+                             C.c_void_p(cost_ptr), C.c_void_p(path_ptr or 0), C.byref(info), _stream(stream))
+    if not allow_errors:
+        _check(st, allow=(GMT_OK, GMT_NO_PATH))
+    info.rc = st
+    return info
 
 
 def gmt_graph_set_profiling(graph: Graph, enable: bool) -> None:

@@ -52,6 +52,10 @@ float euclid_threshold(float r) {
 
 }  // namespace
 
+namespace gmtk {
+void record_error(const char* msg) { g_last_error = msg; }
+}  // namespace gmtk
+
 struct gmt_graph {
     int kind = 0, d = 0, dp = 0, N = 0, pitch = 0;
     long long E = 0;

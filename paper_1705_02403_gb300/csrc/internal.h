@@ -91,6 +91,9 @@ struct PlanArgs {
     PlanCtl* ctl;
 };
 
+// capi.cu: sets the message returned by gmt_last_error() on this host thread.
+void record_error(const char* msg);
+
 // plan.cu
 // Launches the wavefront for one plan.  blocks <= 1: a single CTA runs the
 // whole plan with block barriers; otherwise a cooperative grid of `blocks`

@@ -1,0 +1,59 @@
+"""gmt_plan_static, the allocation-free plan entry point, against gmt_plan.
+
+Callers that must not allocate device memory while planning (a replanning loop
+inside a control cycle, work recorded into a CUDA graph, systems whose memory
+is fixed at start-up) use gmt_plan_static: the same wavefront kernel, with its
+scratch in a fixed array inside the library.  Its results must equal
+gmt_plan's bit for bit, on consecutive calls that share that array.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1705_02403_gb300 import envgen
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def plan_both(pb):
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import Planner
+    pl = Planner(pb).build()
+    ref = pl.plan()
+    ref_parent, ref_cost, ref_path = pl.parent.clone(), pl.cost.clone(), pl.path.clone()
+    view = N.gmt_graph_get_view(pl.graph)
+    parent = torch.full_like(ref_parent, -7)
+    cost = torch.full_like(ref_cost, -7.0)
+    path = torch.full_like(ref_path, -7)
+    info = N.gmt_plan_static(pl.space, view, pl.boxes, pl.params, parent.data_ptr(), cost.data_ptr(),
+                             path.data_ptr()).as_dict()
+    torch.cuda.synchronize()
+    return ref, ref_parent, ref_cost, ref_path, info, parent, cost, path
+
+
+def test_static_plan_equals_gmt_plan_on_consecutive_calls():
+    # First call: 6D double integrator, N = 4097 (multi-CTA grid, barrier words
+    # in the static array); second call: 2D, N = 1025 (one CTA), which must not
+    # see anything left over from the first.
+    for pb in (envgen.cfg2_di6(1), envgen.cfg1_2d(3)):
+        ref, rp, rc, rpath, info, parent, cost, path = plan_both(pb)
+        assert torch.equal(parent, rp)
+        assert torch.equal(cost.view(torch.int32), rc.view(torch.int32))   # bit for bit
+        n = ref["path_len"]
+        assert info["path_len"] == n and torch.equal(path[:n], rpath[:n])
+        for k in ("status", "goal_node", "path_cost", "iters", "final_i", "push_edges", "pull_edges", "checks",
+                  "failed", "tree_size"):
+            assert info[k] == ref[k], k
+
+
+def test_static_plan_rejects_graphs_beyond_capacity():
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import Planner
+    pl = Planner(envgen.cfg1_2d(0)).build()
+    view = N.gmt_graph_get_view(pl.graph)
+    view.N = 65537
+    info = N.gmt_plan_static(pl.space, view, pl.boxes, pl.params, pl.parent.data_ptr(), pl.cost.data_ptr(),
+                             None, allow_errors=True)
+    assert info.rc == N.GMT_ERR_INVALID
+    assert "65536" in N.gmt_last_error()
