@@ -126,6 +126,9 @@ typedef struct {
     const int32_t* in_row;   /* [N+1] */
     const int32_t* in_col;   /* [E] */
     const float* in_cost;    /* [E] c(in_col[e], v) */
+    const float* out_tau;    /* [E] double integrator: arrival time of the out-edge; NULL otherwise */
+    const float* in_tau;     /* [E] double integrator: arrival time of the in-edge; NULL otherwise
+                                (gmt_plan_static recomputes it when NULL) */
 } gmt_graph_view;
 
 /* SampleFree and neighbour-set construction (Section III-B; the offline

@@ -55,7 +55,8 @@ class gmt_graph_view(C.Structure):
                 ("x_pitch", C.c_int32), ("E", C.c_int64), ("r", C.c_float),
                 ("X", C.c_void_p), ("is_goal", C.c_void_p),
                 ("out_row", C.c_void_p), ("out_col", C.c_void_p), ("out_cost", C.c_void_p),
-                ("in_row", C.c_void_p), ("in_col", C.c_void_p), ("in_cost", C.c_void_p)]
+                ("in_row", C.c_void_p), ("in_col", C.c_void_p), ("in_cost", C.c_void_p),
+                ("out_tau", C.c_void_p), ("in_tau", C.c_void_p)]
 
 
 class gmt_plan_info(C.Structure):

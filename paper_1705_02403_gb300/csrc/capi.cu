@@ -72,6 +72,8 @@ struct gmt_graph {
     float* out_cost = nullptr;     size_t cap_out_cost = 0;
     int* in_col_own = nullptr;     size_t cap_in_col_own = 0;
     float* in_cost_own = nullptr;  size_t cap_in_cost_own = 0;
+    float* out_tau = nullptr;      size_t cap_out_tau = 0;
+    float* in_tau = nullptr;       size_t cap_in_tau = 0;
     uint32_t* mask = nullptr;      size_t cap_mask = 0;
     uint32_t* maskT = nullptr;     size_t cap_maskT = 0;
     int* flags = nullptr;          size_t cap_flags = 0;
@@ -106,7 +108,7 @@ struct gmt_graph {
 
     ~gmt_graph() {
         void* dev[] = {X, is_goal, out_row, in_row_own, out_count, in_count, out_col, out_cost, in_col_own,
-                       in_cost_own, mask, maskT, flags, ocost, stamp, lists, ctl};
+                       in_cost_own, out_tau, in_tau, mask, maskT, flags, ocost, stamp, lists, ctl};
         for (void* p : dev)
             if (p) cudaFree(p);
         if (h_ctl) cudaFreeHost(h_ctl);
@@ -272,14 +274,20 @@ gmt_status gmt_build_graph(const gmt_space* space, const gmt_boxes* boxes, const
     const size_t E = (size_t)g->E;
     GROW(out_col, E);
     GROW(out_cost, E);
-    if (g->kind == GMT_COST_DI) {
+    const bool di = g->kind == GMT_COST_DI;
+    if (di) {
         GROW(in_col_own, E);
         GROW(in_cost_own, E);
+        GROW(out_tau, E);
+        GROW(in_tau, E);
     }
     LAUNCH(g->mark(gmt_graph::kFill, 0, st), "event");
-    LAUNCH(launch_fill(sa, g->X, g->mask, g->out_row, g->out_col, g->out_cost, false, st), "fill kernel");
-    if (g->kind == GMT_COST_DI)
-        LAUNCH(launch_fill(sa, g->X, g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own, true, st),
+    LAUNCH(launch_fill(sa, g->X, g->mask, g->out_row, g->out_col, g->out_cost, di ? g->out_tau : nullptr, false,
+                       nullptr, nullptr, nullptr, nullptr, st),
+           "fill kernel");
+    if (di)
+        LAUNCH(launch_fill(sa, g->X, g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own, g->in_tau, true,
+                           g->out_row, g->out_col, g->out_cost, g->out_tau, st),
                "fill kernel");
     LAUNCH(g->mark(gmt_graph::kFill, 1, st), "event");
 #undef GROW
@@ -295,6 +303,8 @@ gmt_status gmt_graph_get_view(const gmt_graph* g, gmt_graph_view* v) {
     v->X = g->X; v->is_goal = g->is_goal;
     v->out_row = g->out_row; v->out_col = g->out_col; v->out_cost = g->out_cost;
     v->in_row = g->in_row(); v->in_col = g->in_col(); v->in_cost = g->in_cost();
+    v->out_tau = g->kind == GMT_COST_DI ? g->out_tau : nullptr;
+    v->in_tau = g->kind == GMT_COST_DI ? g->in_tau : nullptr;
     return GMT_OK;
 }
 
@@ -316,6 +326,7 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
     a.X = g->X; a.is_goal = g->is_goal;
     a.out_row = g->out_row; a.out_col = g->out_col;
     a.in_row = g->in_row(); a.in_col = g->in_col(); a.in_cost = g->in_cost();
+    a.in_tau = g->kind == GMT_COST_DI ? g->in_tau : nullptr;
     a.boxes = BoxArgs{boxes->count, boxes->lo, boxes->hi};
     a.r = g->r;
     a.delta = params->lambda * g->r;

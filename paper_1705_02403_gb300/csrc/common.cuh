@@ -141,35 +141,42 @@ __device__ __forceinline__ float di_cost(const float* s0, const float* s1, float
 }
 
 // Conservative rejection of pairs that cannot have J < r (never rejects an
-// edge; the exact test follows).  With s = v0 + v1 the cost is exactly
-//   J(tau) = tau + |v1 - v0|^2 / tau + 3 |2 dp - s tau|^2 / tau^3,
-// so J < r implies (i) 2 |v1 - v0| <= J < r (AM-GM) and (ii) for the arrival
-// time tau < r: |2 dp - s tau| < sqrt((r - tau) tau^3 / 3) <= 3 r^2 / 16, i.e.
-// the point 2 dp lies within 3 r^2/16 of the segment {s tau : 0 <= tau <= r}.
-// Both tests use r inflated by 1% to absorb FP32 rounding.
+// edge; the exact procedure decides the rest).  With s = v0 + v1, dv = v1 - v0
+// the cost is exactly
+//   J(tau) = tau + |dv|^2 / tau + 3 |2 dp - s tau|^2 / tau^3.
+// For tau in (0, r], |2 dp - s tau| >= D, the distance from the point 2 dp to
+// the segment {s t : 0 <= t <= r}, so J(tau) >= f(tau) = tau + A/tau + B/tau^3
+// with A = |dv|^2, B = 3 D^2.  f is convex with f'(t) = 0 at
+// t^2 = (A + sqrt(A^2 + 12 B)) / 2, so min over (0, r] of f is f(min(t, r)).
+// A pair whose bound reaches r (inflated by 1% to absorb FP32 rounding, far
+// above the few-ulp error of either side) cannot be an edge.
 __device__ __forceinline__ bool di_may_connect(const float* s0, const float* s1, float r) {
     const float rr = r * 1.01f;
-    float dv2 = 0.0f, qs = 0.0f, ss = 0.0f, q[3], sv[3];
+    float A = 0.0f, qs = 0.0f, ss = 0.0f, q[3], sv[3];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         const float dv = s1[3 + ax] - s0[3 + ax];
-        dv2 = dv2 + dv * dv;
+        A = A + dv * dv;
         q[ax] = 2.0f * (s1[ax] - s0[ax]);
         sv[ax] = s0[3 + ax] + s1[3 + ax];
         qs = qs + q[ax] * sv[ax];
         ss = ss + sv[ax] * sv[ax];
     }
-    if (4.0f * dv2 >= rr * rr) return false;
+    if (4.0f * A >= rr * rr) return false;  // f >= 2 sqrt(A)
     float t = ss > 0.0f ? qs / ss : 0.0f;
     t = fminf(fmaxf(t, 0.0f), rr);
-    float d2 = 0.0f;
+    float D2 = 0.0f;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         const float e = q[ax] - t * sv[ax];
-        d2 = d2 + e * e;
+        D2 = D2 + e * e;
     }
-    const float bound = 3.0f * rr * rr / 16.0f;
-    return d2 < bound * bound;
+    const float B = 3.0f * D2;
+    float tau = sqrtf(0.5f * (A + sqrtf(A * A + 12.0f * B)));
+    tau = fminf(tau, rr);
+    if (!(tau > 0.0f)) return true;
+    const float f = tau + A / tau + B / (tau * tau * tau);
+    return f < rr;
 }
 
 // Position of the minimum-effort trajectory (cubic Hermite curve) at s in [0,1]:

@@ -8,8 +8,11 @@
 //                     that each warp writes 32 consecutive rows' words
 //   transpose_kernel  32x32 bit-block transpose with warp ballots (in-edges)
 //   scan_kernel       exclusive prefix sum of the per-row counts -> row_ptr
-//   fill_kernel       one warp per row: ballot-free prefix over the row's
-//                     words, costs of the set bits, ascending column order
+//   pair_mask_di_kernel  the same for the double integrator, with a
+//                     conservative lower bound and per-warp compaction of the
+//                     pairs that need the exact root procedure
+//   fill_kernel       one warp per row: prefix over the row's words, column
+//                     list in shared memory, one edge cost per lane
 #include <cstdio>
 
 #include "common.cuh"
@@ -128,6 +131,89 @@ __global__ void __launch_bounds__(kMaskRows) pair_mask_kernel(SpaceArgs s, const
     if (cnt) atomicAdd(&out_count[i], cnt);
 }
 
+// Double-integrator pair filter.  The exact test (root bracketing + 24
+// halvings, ~400 FP32 operations) is needed only for the ~9% of pairs that
+// pass the conservative lower bound, so each warp first evaluates the bound
+// for its 32 rows against every staged column and queues the survivors
+// (row lane, column) in shared memory; whenever 32 are queued, the warp runs
+// the exact test on all of them at once (every lane busy), ORing the verdicts
+// into per-row words kept in shared memory.  Rows are the lanes' own rows, so
+// a queued pair fetches its row state from the owning lane with a shuffle.
+constexpr int kDIRows = 128;   // rows (threads) per block: 4 warps
+constexpr int kDIWords = 4;    // 32-column words per block (128 staged columns)
+
+__global__ void __launch_bounds__(kDIRows) pair_mask_di_kernel(SpaceArgs s, const float* __restrict__ X,
+                                                              uint32_t* __restrict__ mask,
+                                                              int* __restrict__ out_count) {
+    __shared__ float tile[6][kDIWords * 32];
+    __shared__ uint32_t words[kDIRows / 32][kDIWords][32];
+    __shared__ uint16_t queue[kDIRows / 32][64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * kDIRows + threadIdx.x;
+    const int w0 = blockIdx.y * kDIWords;
+    const int j0 = w0 * 32;
+    for (int idx = threadIdx.x; idx < kDIWords * 32; idx += kDIRows) {
+        const int j = j0 + idx;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) tile[a][idx] = j < s.N ? X[(size_t)a * s.pitch + j] : 0.0f;
+    }
+#pragma unroll
+    for (int ww = 0; ww < kDIWords; ++ww) words[warp][ww][lane] = 0u;
+    __syncthreads();
+    const bool row_ok = i < s.N;
+    float xi[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) xi[a] = row_ok ? X[(size_t)a * s.pitch + i] : 0.0f;
+
+    // exact test of up to 32 queued pairs, one per lane
+    auto drain = [&](int count) {
+        const int e = lane < count ? queue[warp][lane] : 0;
+        const int src = e >> 8, jt = e & 255;
+        float a_[6], b_[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            a_[a] = __shfl_sync(0xffffffffu, xi[a], src);
+            b_[a] = tile[a][jt];
+        }
+        if (lane < count && di_cost(a_, b_, s.r) < s.r) atomicOr(&words[warp][jt >> 5][src], 1u << (jt & 31));
+    };
+
+    int qn = 0;
+    const int jend = min(kDIWords * 32, s.N - j0);
+    for (int jt = 0; jt < jend; ++jt) {
+        const int j = j0 + jt;
+        float xj[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) xj[a] = tile[a][jt];
+        const bool pass = row_ok && j != i && di_may_connect(xi, xj, s.r);
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        if (pass) queue[warp][qn + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((lane << 8) | jt);
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+            drain(32);
+            __syncwarp();
+            if (lane < qn - 32) queue[warp][lane] = queue[warp][32 + lane];
+            qn -= 32;
+            __syncwarp();
+        }
+    }
+    if (qn > 0) drain(qn);
+    __syncwarp();
+    if (!row_ok) return;
+    const int W = (s.N + 31) / 32;
+    int cnt = 0;
+#pragma unroll
+    for (int ww = 0; ww < kDIWords; ++ww) {
+        const int w = w0 + ww;
+        if (w >= W) break;
+        const uint32_t bits = words[warp][ww][lane];
+        mask[(size_t)w * s.pitch + i] = bits;
+        cnt += __popc(bits);
+    }
+    if (cnt) atomicAdd(&out_count[i], cnt);
+}
+
 // maskT[u][j] bit l = mask[j/32][32u + l] bit (j%32): the in-neighbour rows.
 __global__ void __launch_bounds__(256) transpose_kernel(int N, int pitch, const uint32_t* __restrict__ mask,
                                                         uint32_t* __restrict__ maskT, int* __restrict__ in_count) {
@@ -184,15 +270,27 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ coun
     if (threadIdx.x == 0) row[N] = carry;
 }
 
-// One warp per row v: words of the row's bits are read 32 at a time, the
-// lanes' edge counts are prefix-summed, and each lane writes the edges of its
-// word (ascending column order overall).
+// One warp per row v.  The row's words are read 32 at a time (one per lane),
+// the lanes' bit counts are prefix-summed, and the columns are written, in
+// ascending order, to a per-warp list in shared memory; the lanes then take
+// the listed edges one each, so the cost evaluations keep every lane busy.
+// Out-rows compute c(v, j).  In-rows of the double integrator look the cost
+// c(j, v) up in the finished out-row of j (binary search), so each edge cost is
+// computed once.
+constexpr int kFillWarps = 8;
+
 template <int KIND, int D, bool INCOMING>
-__global__ void __launch_bounds__(256) fill_kernel(SpaceArgs s, const float* __restrict__ X,
-                                                   const uint32_t* __restrict__ M, const int* __restrict__ row,
-                                                   int* __restrict__ col, float* __restrict__ cost) {
-    const int v = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32);
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kFillWarps * 32) fill_kernel(SpaceArgs s, const float* __restrict__ X,
+                                                               const uint32_t* __restrict__ M,
+                                                               const int* __restrict__ row, int* __restrict__ col,
+                                                               float* __restrict__ cost, float* __restrict__ tau,
+                                                               const int* __restrict__ out_row,
+                                                               const int* __restrict__ out_col,
+                                                               const float* __restrict__ out_cost,
+                                                               const float* __restrict__ out_tau) {
+    __shared__ int list[kFillWarps][1024];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int v = blockIdx.x * kFillWarps + warp;
     if (v >= s.N) return;
     float xv[D];
 #pragma unroll
@@ -209,19 +307,44 @@ __global__ void __launch_bounds__(256) fill_kernel(SpaceArgs s, const float* __r
             const int y = __shfl_up_sync(0xffffffffu, incl, off);
             if (lane >= off) incl += y;
         }
-        int pos = base + incl - n;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int pos = incl - n;
         while (bits) {
             const int b = __ffs(bits) - 1;
             bits &= bits - 1;
-            const int j = 32 * w + b;
-            float xj[D];
-#pragma unroll
-            for (int a = 0; a < D; ++a) xj[a] = X[(size_t)a * s.pitch + j];
-            col[pos] = j;
-            cost[pos] = INCOMING ? edge_cost<KIND, D>(s, xj, xv) : edge_cost<KIND, D>(s, xv, xj);
-            ++pos;
+            list[warp][pos++] = 32 * w + b;
         }
-        base += __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+        for (int t = lane; t < total; t += 32) {
+            const int j = list[warp][t];
+            float c, tj = 0.0f;
+            if (INCOMING && KIND == GMT_COST_DI) {
+                int lo = out_row[j], hi = out_row[j + 1] - 1;   // v is in the out-row of j
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (out_col[mid] < v) lo = mid + 1; else hi = mid;
+                }
+                c = out_cost[lo];
+                tj = out_tau[lo];
+            } else if (KIND == GMT_COST_DI) {
+                float xj[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) xj[a] = X[(size_t)a * s.pitch + j];
+                const DICoef k = di_coef(xv, xj);
+                tj = di_tau(k, s.r);
+                c = di_J(k, tj);
+            } else {
+                float xj[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) xj[a] = X[(size_t)a * s.pitch + j];
+                c = INCOMING ? edge_cost<KIND, D>(s, xj, xv) : edge_cost<KIND, D>(s, xv, xj);
+            }
+            if (KIND == GMT_COST_DI) tau[base + t] = tj;
+            col[base + t] = j;
+            cost[base + t] = c;
+        }
+        base += total;
+        __syncwarp();
     }
 }
 
@@ -241,11 +364,15 @@ cudaError_t mask_t(const SpaceArgs& s, const float* X, uint32_t* mask, int* cnt,
 }
 template <int KIND, int D>
 cudaError_t fill_t(const SpaceArgs& s, const float* X, const uint32_t* M, const int* row, int* col, float* cost,
-                   bool incoming, cudaStream_t st) {
-    const long long threads = (long long)s.N * 32;
-    const int blocks = (int)((threads + 255) / 256);
-    if (incoming) fill_kernel<KIND, D, true><<<blocks, 256, 0, st>>>(s, X, M, row, col, cost);
-    else fill_kernel<KIND, D, false><<<blocks, 256, 0, st>>>(s, X, M, row, col, cost);
+                   float* tau, bool incoming, const int* orow, const int* ocol, const float* ocost,
+                   const float* otau, cudaStream_t st) {
+    const int blocks = (s.N + kFillWarps - 1) / kFillWarps;
+    if (incoming)
+        fill_kernel<KIND, D, true><<<blocks, kFillWarps * 32, 0, st>>>(s, X, M, row, col, cost, tau, orow, ocol,
+                                                                        ocost, otau);
+    else
+        fill_kernel<KIND, D, false><<<blocks, kFillWarps * 32, 0, st>>>(s, X, M, row, col, cost, tau, orow, ocol,
+                                                                         ocost, otau);
     return cudaGetLastError();
 }
 }  // namespace
@@ -281,7 +408,12 @@ cudaError_t launch_sample(const SpaceArgs& s, BoxArgs b, float* X, uint8_t* g, i
 }
 
 cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* cnt, cudaStream_t st) {
-    if (s.kind == GMT_COST_DI) return mask_t<GMT_COST_DI, 6>(s, X, mask, cnt, st);
+    if (s.kind == GMT_COST_DI) {
+        const int W = (s.N + 31) / 32;
+        dim3 grid((s.N + kDIRows - 1) / kDIRows, (W + kDIWords - 1) / kDIWords);
+        pair_mask_di_kernel<<<grid, kDIRows, 0, st>>>(s, X, mask, cnt);
+        return cudaGetLastError();
+    }
     GMT_EUCLID_DIMS(mask_t, s, X, mask, cnt, st)
 }
 
@@ -299,9 +431,11 @@ cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st) {
 }
 
 cudaError_t launch_fill(const SpaceArgs& s, const float* X, const uint32_t* M, const int* row, int* col,
-                        float* cost, bool incoming, cudaStream_t st) {
-    if (s.kind == GMT_COST_DI) return fill_t<GMT_COST_DI, 6>(s, X, M, row, col, cost, incoming, st);
-    GMT_EUCLID_DIMS(fill_t, s, X, M, row, col, cost, incoming, st)
+                        float* cost, float* tau, bool incoming, const int* orow, const int* ocol,
+                        const float* ocost, const float* otau, cudaStream_t st) {
+    if (s.kind == GMT_COST_DI)
+        return fill_t<GMT_COST_DI, 6>(s, X, M, row, col, cost, tau, incoming, orow, ocol, ocost, otau, st);
+    GMT_EUCLID_DIMS(fill_t, s, X, M, row, col, cost, tau, incoming, orow, ocol, ocost, otau, st)
 }
 
 }  // namespace gmtk

@@ -43,8 +43,12 @@ cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask,
 cudaError_t launch_transpose(const SpaceArgs& s, const uint32_t* mask, uint32_t* maskT, int* in_count,
                              cudaStream_t st);
 cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st);
+// incoming: build in-rows from the transposed matrix; double-integrator costs
+// are then looked up in the finished out-CSR (orow, ocol, ocost).
+// tau (double integrator only, may be NULL): arrival time of each edge.
 cudaError_t launch_fill(const SpaceArgs& s, const float* X, const uint32_t* mask, const int* row, int* col,
-                        float* cost, bool incoming, cudaStream_t st);
+                        float* cost, float* tau, bool incoming, const int* orow, const int* ocol,
+                        const float* ocost, const float* otau, cudaStream_t st);
 
 // Workspace and control block of one plan (all device memory).
 struct PlanCtl {
@@ -75,6 +79,7 @@ struct PlanArgs {
     const int* in_row;
     const int* in_col;
     const float* in_cost;
+    const float* in_tau;  // double integrator: arrival time per in-edge (NULL: recompute)
     BoxArgs boxes;
     float pos_lo[3], pos_hi[3];
     float r, delta, seg_spacing;

@@ -111,10 +111,9 @@ __device__ bool segment_free_warp(const float* y, const float* x, float L, float
 // Double-integrator edge: `points` samples of the Hermite trajectory at
 // s_k = k/(points-1); collision if one lies in a box or outside the position
 // bounds.
-__device__ bool trajectory_free_warp(const float* y, const float* x, float r, int points, const float* plo,
+__device__ bool trajectory_free_warp(const float* y, const float* x, float tau, int points, const float* plo,
                                      const float* phi, const float* blo, const float* bhi, int nbox) {
     const int lane = threadIdx.x & 31;
-    const float tau = di_tau(di_coef(y, x), r);
     const float denom = (float)(points - 1);
     for (int k0 = 0; k0 < points; k0 += 32) {
         const int k = k0 + lane;
@@ -297,8 +296,11 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs A, Team team) {
                 bool free_edge;
                 if (KIND == GMT_COST_EUCLID)
                     free_edge = segment_free_warp<DP>(sy, sx, __ldg(&A.in_cost[be]), A.seg_spacing, blo, bhi, nbox);
-                else
-                    free_edge = trajectory_free_warp(sy, sx, A.r, A.traj_points, A.pos_lo, A.pos_hi, blo, bhi, nbox);
+                else {
+                    // arrival time of the edge: stored by the graph build, or recomputed
+                    const float tau = A.in_tau ? __ldg(&A.in_tau[be]) : di_tau(di_coef(sy, sx), A.r);
+                    free_edge = trajectory_free_warp(sy, sx, tau, A.traj_points, A.pos_lo, A.pos_hi, blo, bhi, nbox);
+                }
                 if (lane == 0) {
                     n_pull += (unsigned long long)(r1 - r0);
                     ++n_checks;

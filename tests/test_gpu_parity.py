@@ -88,6 +88,30 @@ def test_double_integrator_small_many_seeds(O, P):
         assert_same(O, G, *oracle_run(O, pb))
 
 
+def test_double_integrator_arrival_times(O, P):
+    # The build stores each edge's arrival time tau*; it must be the oracle's
+    # tau for that pair, bit for bit, on out- and in-edges.
+    pb = envgen.di6(seed=7, n=500, r=2.8)
+    G = gpu_run(P, pb, build_only=True)
+    v = G["planner"].view()
+    raw = v.raw
+    from paper_1705_02403_gb300.planner import wrap_device
+    out_tau = wrap_device(raw.out_tau, (v.E,), "f4", G["planner"].graph).cpu().numpy()
+    in_tau = wrap_device(raw.in_tau, (v.E,), "f4", G["planner"].graph).cpu().numpy()
+    X = G["X"]
+    r = np.float32(pb.r)
+    for y in range(0, pb.N, 7):
+        for e in range(G["out_row"][y], G["out_row"][y + 1]):
+            x = G["out_col"][e]
+            J, tau = O.cost_di(X[:, y], X[:, x], r)
+            assert bits(J) == bits(G["out_cost"][e]) and bits(tau) == bits(out_tau[e])
+    for x in range(0, pb.N, 7):
+        for e in range(G["in_row"][x], G["in_row"][x + 1]):
+            y = G["in_col"][e]
+            J, tau = O.cost_di(X[:, y], X[:, x], r)
+            assert bits(tau) == bits(in_tau[e])
+
+
 def test_double_integrator_full_size(O, P):
     for seed in (1, 2):
         pb = envgen.cfg2_di6(seed)

@@ -16,13 +16,15 @@ pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
 
-def plan_both(pb):
+def plan_both(pb, drop_tau=False):
     from paper_1705_02403_gb300 import _native as N
     from paper_1705_02403_gb300.planner import Planner
     pl = Planner(pb).build()
     ref = pl.plan()
     ref_parent, ref_cost, ref_path = pl.parent.clone(), pl.cost.clone(), pl.path.clone()
     view = N.gmt_graph_get_view(pl.graph)
+    if drop_tau:
+        view.in_tau = view.out_tau = None   # the kernel recomputes arrival times
     parent = torch.full_like(ref_parent, -7)
     cost = torch.full_like(ref_cost, -7.0)
     path = torch.full_like(ref_path, -7)
@@ -35,9 +37,10 @@ def plan_both(pb):
 def test_static_plan_equals_gmt_plan_on_consecutive_calls():
     # First call: 6D double integrator, N = 4097 (multi-CTA grid, barrier words
     # in the static array); second call: 2D, N = 1025 (one CTA), which must not
-    # see anything left over from the first.
-    for pb in (envgen.cfg2_di6(1), envgen.cfg1_2d(3)):
-        ref, rp, rc, rpath, info, parent, cost, path = plan_both(pb)
+    # see anything left over from the first; third: a view without the stored
+    # arrival times.
+    for pb, drop in ((envgen.cfg2_di6(1), False), (envgen.cfg1_2d(3), False), (envgen.di6(2, n=700, r=2.8), True)):
+        ref, rp, rc, rpath, info, parent, cost, path = plan_both(pb, drop)
         assert torch.equal(parent, rp)
         assert torch.equal(cost.view(torch.int32), rc.view(torch.int32))   # bit for bit
         n = ref["path_len"]
