@@ -36,6 +36,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ms/plan p50/p99 & edges checked/s; learned+batched vs plain at equal path cost"
 
+# DRAM bytes (read + write) of one plan_kernel launch on this workload, from the
+# ncu capture summarised in profiles/plan_kernel_double_integrator_6d_n4096.md.
+# Set to None whenever plan_kernel changes until it is captured again.
+PLAN_KERNEL_DRAM_BYTES = {"di6": 2106112, "geo2d": None}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -301,7 +306,8 @@ def run_gpu(args, rank, world, local_rank):
     roof = {"kernel": "plan_kernel (wavefront, Alg. 1)", "bound": "hbm",
             "achieved": float(np.mean(plan_bytes)) / (kern["plan_ms"] / 1e3) / 1e9,
             "peak": hbm, "unit": "GB/s", "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-            "traffic": None, "algorithmic_bytes_per_launch": float(np.mean(plan_bytes)),
+            "traffic": PLAN_KERNEL_DRAM_BYTES.get(args.workload),
+            "algorithmic_bytes_per_launch": float(np.mean(plan_bytes)),
             "launch_ms": kern["plan_ms"]}
     roof["frac"] = roof["achieved"] / roof["peak"]
     if dominant != "plan_ms":

@@ -181,12 +181,14 @@ gmt_status gmt_plan(gmt_graph* graph, const gmt_boxes* boxes, const gmt_params* 
                     float* cost, int32_t* path, gmt_plan_info* info, gmt_stream stream);
 
 /* Launch shape of gmt_plan on this graph (a tuning knob, not a semantic one:
- * every shape gives the same result).  blocks == 1: one CTA runs the whole
- * plan with block barriers; blocks > 1: a cooperative grid of that many CTAs
- * (clamped to what can be co-resident); 0 = automatic (one CTA for N <= 2048,
- * else one CTA per SM).  threads: CTA size, a multiple of 32 in [64, 1024], or
- * 0 = automatic. */
-gmt_status gmt_graph_set_launch(gmt_graph* graph, int32_t blocks, int32_t threads);
+ * every shape gives the same result).  cluster in [2, 16]: one thread-block
+ * cluster of that many CTAs runs the plan with hardware cluster barriers
+ * (blocks ignored); otherwise blocks == 1: one CTA with block barriers;
+ * blocks > 1: a cooperative grid of that many CTAs (clamped to what can be
+ * co-resident) with bounded software barriers; blocks == cluster == 0:
+ * automatic (the largest cluster the GPU can hold, up to 16 CTAs).  threads:
+ * CTA size, a multiple of 32 in [64, 1024], or 0 = automatic. */
+gmt_status gmt_graph_set_launch(gmt_graph* graph, int32_t blocks, int32_t threads, int32_t cluster);
 
 /* Allocation-free planning (an implementation entry point; the paper has no
  * counterpart).  Runs the same wavefront kernel as gmt_plan, for callers that
@@ -224,7 +226,7 @@ typedef struct {
     float scan_ms;       /* row offsets */
     float fill_ms;       /* CSR columns and costs */
     float plan_ms;       /* wavefront kernel */
-    int32_t plan_blocks; /* launch shape used by the last plan */
+    int32_t plan_blocks; /* launch shape used by the last plan (-k: a cluster of k CTAs) */
     int32_t plan_threads;
 } gmt_profile;
 

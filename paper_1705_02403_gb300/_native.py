@@ -85,7 +85,7 @@ SIGNATURES = {
                                C.POINTER(gmt_params), C.POINTER(C.c_void_p), _P]),
     "gmt_graph_get_view": (_I32, [_P, C.POINTER(gmt_graph_view)]),
     "gmt_graph_free": (None, [_P]),
-    "gmt_graph_set_launch": (_I32, [_P, _I32, _I32]),
+    "gmt_graph_set_launch": (_I32, [_P, _I32, _I32, _I32]),
     "gmt_plan": (_I32, [_P, C.POINTER(gmt_boxes), C.POINTER(gmt_params), _P, _P, _P, C.POINTER(gmt_plan_info), _P]),
     "gmt_plan_static": (_I32, [C.POINTER(gmt_space), C.POINTER(gmt_graph_view), C.POINTER(gmt_boxes),
                                C.POINTER(gmt_params), _P, _P, _P, C.POINTER(gmt_plan_info), _P]),
@@ -163,8 +163,8 @@ def gmt_graph_get_view(graph: Graph) -> gmt_graph_view:
     return v
 
 
-def gmt_graph_set_launch(graph: Graph, blocks: int, threads: int) -> None:
-    _check(lib.gmt_graph_set_launch(graph.handle, blocks, threads))
+def gmt_graph_set_launch(graph: Graph, blocks: int, threads: int, cluster: int = 0) -> None:
+    _check(lib.gmt_graph_set_launch(graph.handle, blocks, threads, cluster))
 
 
 def gmt_plan_static(space: gmt_space, view: gmt_graph_view, boxes: gmt_boxes, params: gmt_params,

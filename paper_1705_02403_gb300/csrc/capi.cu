@@ -61,7 +61,8 @@ struct gmt_graph {
     long long E = 0;
     float r = 0.0f;
     float pos_lo[3] = {0, 0, 0}, pos_hi[3] = {0, 0, 0};
-    int plan_blocks = 0, plan_threads = 0;   // 0 = automatic
+    int plan_blocks = 0, plan_threads = 0, plan_cluster = 0;   // 0 = automatic
+    int auto_cluster = -1;                                     // probed once
     float* X = nullptr;            size_t cap_X = 0;
     uint8_t* is_goal = nullptr;    size_t cap_is_goal = 0;
     int* out_row = nullptr;        size_t cap_out_row = 0;
@@ -343,11 +344,20 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
     a.ctl = g->ctl;
     for (int k = 0; k < 3; ++k) { a.pos_lo[k] = g->pos_lo[k]; a.pos_hi[k] = g->pos_hi[k]; }
 
-    int blocks = g->plan_blocks, threads = g->plan_threads;
+    int blocks = g->plan_blocks, threads = g->plan_threads, cluster = g->plan_cluster;
+    if (blocks <= 0 && cluster <= 0) {
+        // automatic: the largest resident thread-block cluster (hardware
+        // barriers; measured fastest on GB300 for N from 1e3 to 4e3), else a
+        // cooperative grid of one CTA per SM
+        if (g->auto_cluster < 0) g->auto_cluster = plan_max_cluster(g->kind, g->dp, N <= 2048 ? 512 : 1024);
+        cluster = g->auto_cluster;
+        if (threads <= 0) threads = N <= 2048 ? 512 : 1024;
+        if (cluster <= 1) blocks = -1;
+    }
     if (threads <= 0) threads = 512;
-    if (blocks <= 0) blocks = N <= 2048 ? 1 : -1;
-    if (blocks == 1) threads = g->plan_threads > 0 ? g->plan_threads : 1024;
-    if (blocks < 0 || blocks > 1) {
+    if (blocks <= 0 && cluster <= 1) blocks = -1;
+    if (blocks == 1 && g->plan_threads <= 0) threads = 1024;
+    if (cluster <= 1 && (blocks < 0 || blocks > 1)) {
         int dev = 0, sms = 0;
         GMT_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
         GMT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
@@ -359,9 +369,9 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
     GMT_CUDA(cudaMemsetAsync(g->ctl, 0, sizeof(PlanCtl), st), "memset");
     g->stage_ran[gmt_graph::kPlan] = false;
     GMT_CUDA(g->mark(gmt_graph::kPlan, 0, st), "event");
-    GMT_CUDA(launch_plan(a, blocks, threads, st), "plan kernel launch");
+    GMT_CUDA(launch_plan(a, blocks, threads, st, cluster), "plan kernel launch");
     GMT_CUDA(g->mark(gmt_graph::kPlan, 1, st), "event");
-    g->last_blocks = blocks;
+    g->last_blocks = cluster > 1 ? -cluster : blocks;
     g->last_threads = threads;
     GMT_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(PlanCtl), cudaMemcpyDeviceToHost, st), "control readback");
     GMT_CUDA(cudaStreamSynchronize(st), "plan kernel");
@@ -412,13 +422,15 @@ gmt_status gmt_graph_get_profile(gmt_graph* g, gmt_profile* out) {
     return GMT_OK;
 }
 
-gmt_status gmt_graph_set_launch(gmt_graph* g, int32_t blocks, int32_t threads) {
+gmt_status gmt_graph_set_launch(gmt_graph* g, int32_t blocks, int32_t threads, int32_t cluster) {
     if (!g) return fail(GMT_ERR_INVALID, "graph is NULL");
     if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32 != 0))
         return fail(GMT_ERR_INVALID, "threads must be 0 or a multiple of 32 in [64, 1024]");
     if (blocks < 0) return fail(GMT_ERR_INVALID, "blocks must be >= 0");
+    if (cluster < 0 || cluster > 16) return fail(GMT_ERR_INVALID, "cluster must be in [0, 16]");
     g->plan_blocks = blocks;
     g->plan_threads = threads;
+    g->plan_cluster = cluster;
     return GMT_OK;
 }
 

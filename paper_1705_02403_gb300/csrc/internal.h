@@ -100,10 +100,12 @@ struct PlanArgs {
 void record_error(const char* msg);
 
 // plan.cu
-// Launches the wavefront for one plan.  blocks <= 1: a single CTA runs the
-// whole plan with block barriers; otherwise a cooperative grid of `blocks`
-// CTAs synchronises through bounded global barriers.
-cudaError_t launch_plan(const PlanArgs& a, int blocks, int threads, cudaStream_t st);
+// Launches the wavefront for one plan.  cluster > 1: one thread-block cluster
+// of that many CTAs with hardware cluster barriers; else blocks <= 1: a single
+// CTA with block barriers; else a cooperative grid of `blocks` CTAs that
+// synchronises through bounded global barriers.
+cudaError_t launch_plan(const PlanArgs& a, int blocks, int threads, cudaStream_t st, int cluster = 0);
 int plan_max_coresident_blocks(int kind, int dp, int threads);
+int plan_max_cluster(int kind, int dp, int threads);
 
 }  // namespace gmtk

@@ -83,6 +83,29 @@ struct GridTeam {
     }
 };
 
+// All CTAs of one thread-block cluster (up to 16 SMs of a GPC).  The barrier
+// is the hardware cluster barrier (arrive.release / wait.acquire at cluster
+// scope); it cannot wait forever because every thread of the cluster reaches
+// every barrier (all exits from the iteration loop are uniform).
+struct ClusterTeam {
+    __device__ __forceinline__ static unsigned cta_rank() {
+        unsigned r;
+        asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+        return r;
+    }
+    __device__ __forceinline__ static unsigned ctas() {
+        unsigned n;
+        asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+        return n;
+    }
+    __device__ __forceinline__ int rank() const { return (int)(cta_rank() * blockDim.x + threadIdx.x); }
+    __device__ __forceinline__ int size() const { return (int)(ctas() * blockDim.x); }
+    __device__ __forceinline__ bool sync(PlanCtl*) const {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        return true;
+    }
+};
+
 // ---------------------------------------------------------------- edge check
 // Geometric edge y -> x of length L: m = max(2, ceil(L/spacing) + 1) points
 // p_k = y + t_k (x - y), t_k = k/(m-1); collision if one lies in a closed box.
@@ -402,9 +425,27 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs A, Team team) {
 // ----------------------------------------------------------------- launcher
 namespace {
 template <int KIND, int DP>
-cudaError_t plan_t(const PlanArgs& a, int blocks, int threads, cudaStream_t st) {
+cudaError_t plan_t(const PlanArgs& a, int blocks, int threads, int cluster, cudaStream_t st) {
     const int nbs = a.boxes.count <= smem_box_cap(DP) ? a.boxes.count : 0;
     const size_t smem = (size_t)2 * nbs * DP * sizeof(float);
+    if (cluster > 1) {
+        auto kern = plan_kernel<ClusterTeam, KIND, DP>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cluster);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kern, a, ClusterTeam{});
+    }
     if (blocks <= 1) {
         plan_kernel<BlockTeam, KIND, DP><<<1, threads, smem, st>>>(a, BlockTeam{});
         return cudaGetLastError();
@@ -429,20 +470,46 @@ int occupancy_t(int threads) {
 }
 }  // namespace
 
-cudaError_t launch_plan(const PlanArgs& a, int blocks, int threads, cudaStream_t st) {
-    if (a.kind == GMT_COST_DI) return plan_t<GMT_COST_DI, 3>(a, blocks, threads, st);
+cudaError_t launch_plan(const PlanArgs& a, int blocks, int threads, cudaStream_t st, int cluster) {
+    if (a.kind == GMT_COST_DI) return plan_t<GMT_COST_DI, 3>(a, blocks, threads, cluster, st);
     switch (a.dp) {
-        case 2: return plan_t<GMT_COST_EUCLID, 2>(a, blocks, threads, st);
-        case 3: return plan_t<GMT_COST_EUCLID, 3>(a, blocks, threads, st);
-        case 4: return plan_t<GMT_COST_EUCLID, 4>(a, blocks, threads, st);
-        case 5: return plan_t<GMT_COST_EUCLID, 5>(a, blocks, threads, st);
-        case 6: return plan_t<GMT_COST_EUCLID, 6>(a, blocks, threads, st);
-        case 7: return plan_t<GMT_COST_EUCLID, 7>(a, blocks, threads, st);
-        case 8: return plan_t<GMT_COST_EUCLID, 8>(a, blocks, threads, st);
-        case 9: return plan_t<GMT_COST_EUCLID, 9>(a, blocks, threads, st);
-        case 10: return plan_t<GMT_COST_EUCLID, 10>(a, blocks, threads, st);
+        case 2: return plan_t<GMT_COST_EUCLID, 2>(a, blocks, threads, cluster, st);
+        case 3: return plan_t<GMT_COST_EUCLID, 3>(a, blocks, threads, cluster, st);
+        case 4: return plan_t<GMT_COST_EUCLID, 4>(a, blocks, threads, cluster, st);
+        case 5: return plan_t<GMT_COST_EUCLID, 5>(a, blocks, threads, cluster, st);
+        case 6: return plan_t<GMT_COST_EUCLID, 6>(a, blocks, threads, cluster, st);
+        case 7: return plan_t<GMT_COST_EUCLID, 7>(a, blocks, threads, cluster, st);
+        case 8: return plan_t<GMT_COST_EUCLID, 8>(a, blocks, threads, cluster, st);
+        case 9: return plan_t<GMT_COST_EUCLID, 9>(a, blocks, threads, cluster, st);
+        case 10: return plan_t<GMT_COST_EUCLID, 10>(a, blocks, threads, cluster, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// Largest cluster size (16, 8, 4, 2) for which one cluster of `threads`-thread
+// CTAs of the plan kernel can be resident; 0 if none.
+int plan_max_cluster(int kind, int dp, int threads) {
+    auto kern = kind == GMT_COST_DI ? plan_kernel<ClusterTeam, GMT_COST_DI, 3>
+                                    : (dp == 2 ? plan_kernel<ClusterTeam, GMT_COST_EUCLID, 2>
+                                               : plan_kernel<ClusterTeam, GMT_COST_EUCLID, 3>);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+    for (int c = 16; c >= 2; c /= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = (size_t)2 * smem_box_cap(3) * 3 * sizeof(float);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0) return c;
+    }
+    cudaGetLastError();
+    return 0;
 }
 
 int plan_max_coresident_blocks(int kind, int dp, int threads) {

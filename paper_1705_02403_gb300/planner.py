@@ -106,8 +106,8 @@ class Planner:
     def view(self) -> GraphView:
         return GraphView(self.graph)
 
-    def set_launch(self, blocks: int, threads: int):
-        N.gmt_graph_set_launch(self.graph, blocks, threads)
+    def set_launch(self, blocks: int, threads: int, cluster: int = 0):
+        N.gmt_graph_set_launch(self.graph, blocks, threads, cluster)
 
     def plan(self, stream=None, allow_errors=False, **param_over) -> dict:
         params = params_struct(self.pb, **param_over) if param_over else self.params

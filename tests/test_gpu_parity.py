@@ -119,7 +119,8 @@ def test_double_integrator_full_size(O, P):
         assert_same(O, G, *oracle_run(O, pb))
 
 
-@pytest.mark.parametrize("launch", [(1, 1024), (1, 256), (2, 512), (7, 256), (0, 0), (152, 1024)])
+@pytest.mark.parametrize("launch", [(1, 1024), (1, 256), (2, 512), (7, 256), (0, 0), (152, 1024), (0, 1024, 2),
+                                    (0, 512, 4), (0, 1024, 8), (0, 1024, 16)])
 def test_every_launch_shape_gives_the_same_tree(O, P, launch):
     for pb in (envgen.cfg1_2d(5), envgen.di6(seed=3, n=600, r=2.8)):
         G = gpu_run(P, pb, launch=launch)
