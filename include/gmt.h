@@ -190,6 +190,56 @@ gmt_status gmt_plan(gmt_graph* graph, const gmt_boxes* boxes, const gmt_params* 
  * CTA size, a multiple of 32 in [64, 1024], or 0 = automatic. */
 gmt_status gmt_graph_set_launch(gmt_graph* graph, int32_t blocks, int32_t threads, int32_t cluster);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent planning problems in one call (an extension of the paper's
+ * single-query method: the same Algorithm 1 on every query).  Supported
+ * queries: double integrator, and geometric with dim 2 or 3. */
+typedef struct {
+    gmt_space space;
+    gmt_boxes boxes;             /* DEVICE arrays, as for gmt_build_graph */
+    float x_init[GMT_MAX_DIM];
+    gmt_goal goal;
+    gmt_params params;           /* r <= 0: Theorem 1 radius for this query's n and dim */
+} gmt_query;
+
+typedef struct gmt_batch gmt_batch;
+
+/* Samples, builds the neighbour CSR of, and plans every query.
+ *   queries: HOST array [q].
+ *   parent, cost: DEVICE outputs of sum_k (n_k + 1) entries; query k's nodes
+ *     start at offset sum_{j<k} (n_j + 1).
+ *   infos: HOST output [q].
+ *   *batch: NULL to create a handle, or the handle of an earlier call, whose
+ *     arena is reused.  If the queries (compared by value, including the box
+ *     pointers) and the output pointers equal the previous call's, the whole
+ *     device sequence is replayed from a CUDA graph captured on the first
+ *     repeat (no host work between kernels); otherwise the batch is prepared
+ *     anew (one host synchronisation to size the edge arrays).
+ * Plan stage: one persistent launch per (kind, dim) group; teams (one CTA or
+ * one cluster, see gmt_batch_set_launch / gmt_batch_autotune) take queries
+ * from a device queue, largest edge count first.  Synchronises `stream`.
+ * Returns GMT_OK, or the first negative per-query status (all infos filled).
+ * A query whose inputs changed in place so that its edge count outgrew the
+ * replayed arena reports GMT_ERR_OOM in its info. */
+gmt_status gmt_plan_batch(int32_t q, const gmt_query* queries, gmt_batch** batch, int32_t* parent, float* cost,
+                          gmt_plan_info* infos, gmt_stream stream);
+
+/* DEVICE views of query k's samples and CSR (and of its path, if `path` is
+ * non-NULL) in the batch arena, valid until the next preparing call. */
+gmt_status gmt_batch_get_view(const gmt_batch* batch, int32_t k, gmt_graph_view* view, int32_t** path);
+
+/* Team shape of the batched plan stage: cluster = CTAs per team (1, 2, 4, 8
+ * or 16; 0 = tuned/automatic), threads per CTA (0 = tuned/automatic). */
+gmt_status gmt_batch_set_launch(gmt_batch* batch, int32_t cluster, int32_t threads);
+
+/* Autotuner: on a batch planned at least once, times the plan stage for every
+ * team shape (cluster 1..16 x 256/512/1024 threads) on `stream`, keeps the
+ * fastest as the automatic shape, and reports it (outputs may be NULL). */
+gmt_status gmt_batch_autotune(gmt_batch* batch, gmt_stream stream, int32_t* best_cluster, int32_t* best_threads,
+                              float* best_ms);
+
+void gmt_batch_free(gmt_batch* batch);
+
 /* Allocation-free planning (an implementation entry point; the paper has no
  * counterpart).  Runs the same wavefront kernel as gmt_plan, for callers that
  * must not allocate device memory while they plan: a replanning loop inside a

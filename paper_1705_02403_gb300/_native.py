@@ -78,6 +78,11 @@ class gmt_profile(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class gmt_query(C.Structure):
+    _fields_ = [("space", gmt_space), ("boxes", gmt_boxes), ("x_init", C.c_float * GMT_MAX_DIM),
+                ("goal", gmt_goal), ("params", gmt_params)]
+
+
 # Every symbol include/gmt.h declares, with its ctypes signature.
 _P, _I32, _I64, _F32, _F64, _U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double, C.c_uint64
 SIGNATURES = {
@@ -91,6 +96,12 @@ SIGNATURES = {
                                C.POINTER(gmt_params), _P, _P, _P, C.POINTER(gmt_plan_info), _P]),
     "gmt_graph_set_profiling": (_I32, [_P, _I32]),
     "gmt_graph_get_profile": (_I32, [_P, C.POINTER(gmt_profile)]),
+    "gmt_plan_batch": (_I32, [_I32, C.POINTER(gmt_query), C.POINTER(C.c_void_p), _P, _P, C.POINTER(gmt_plan_info),
+                              _P]),
+    "gmt_batch_get_view": (_I32, [_P, _I32, C.POINTER(gmt_graph_view), C.POINTER(C.c_void_p)]),
+    "gmt_batch_set_launch": (_I32, [_P, _I32, _I32]),
+    "gmt_batch_autotune": (_I32, [_P, _P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_F32)]),
+    "gmt_batch_free": (None, [_P]),
     "gmt_connection_radius": (_F64, [_I32, _I32, _F64, _F64]),
     "gmt_last_error": (C.c_char_p, []),
 }
@@ -204,3 +215,43 @@ def gmt_plan(graph: Graph, boxes: gmt_boxes, params: gmt_params, parent_ptr: int
     if not allow_errors:
         _check(st, allow=(GMT_OK, GMT_NO_PATH))
     return info
+
+
+class Batch:
+    """Owner of a gmt_batch handle (freed with gmt_batch_free)."""
+
+    def __init__(self):
+        self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib.gmt_batch_free(self.handle)
+            self.handle = C.c_void_p(None)
+
+
+def gmt_plan_batch(queries, batch: Batch, parent_ptr: int, cost_ptr: int, stream=None, allow_errors=False):
+    """queries: a ctypes array of gmt_query.  Returns the list of info dicts."""
+    q = len(queries)
+    infos = (gmt_plan_info * q)()
+    st = lib.gmt_plan_batch(q, queries, C.byref(batch.handle), C.c_void_p(parent_ptr), C.c_void_p(cost_ptr), infos,
+                            _stream(stream))
+    if not allow_errors:
+        _check(st)
+    return [i.as_dict() for i in infos]
+
+
+def gmt_batch_get_view(batch: Batch, k: int):
+    v = gmt_graph_view()
+    path = C.c_void_p()
+    _check(lib.gmt_batch_get_view(batch.handle, k, C.byref(v), C.byref(path)))
+    return v, path.value
+
+
+def gmt_batch_set_launch(batch: Batch, cluster: int, threads: int) -> None:
+    _check(lib.gmt_batch_set_launch(batch.handle, cluster, threads))
+
+
+def gmt_batch_autotune(batch: Batch, stream=None):
+    c, t, ms = C.c_int32(), C.c_int32(), C.c_float()
+    _check(lib.gmt_batch_autotune(batch.handle, _stream(stream), C.byref(c), C.byref(t), C.byref(ms)))
+    return c.value, t.value, ms.value

@@ -1,0 +1,736 @@
+// Batched planning (gmt_plan_batch): hundreds of independent queries of uneven
+// size, each with its own samples, obstacles, radius and seed, run through the
+// same kernels as single plans.
+//
+// Queries are grouped by (cost kind, position dimension) so that each group
+// runs one instantiation of every kernel.  The build kernels cover all queries
+// of a group in one launch: every block (or warp, or thread) finds its query
+// by binary search over per-query prefix offsets of the work units.  The plan
+// stage is one persistent launch per group in which teams (a CTA or a cluster)
+// take queries from a device queue, largest first.  When the same batch is
+// planned again (same descriptors, same outputs), the whole device sequence is
+// replayed from a CUDA graph captured on the previous call.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "graph_body.cuh"
+
+namespace gmtk {
+
+struct QueryDev {
+    SpaceArgs s;
+    BoxArgs boxes;
+    float* X;
+    uint8_t* is_goal;
+    int* flags;
+    uint32_t* mask;
+    uint32_t* maskT;
+    int* out_count;
+    int* in_count;
+    int* out_row;
+    int* in_row;
+    int* out_col;
+    float* out_cost;
+    float* out_tau;
+    int* in_col;
+    float* in_cost;
+    float* in_tau;
+    long long edge_cap;
+};
+
+// index k with off[k] <= t < off[k+1] (off has nq+1 entries, off[0] = 0)
+__device__ __forceinline__ int find_query(const long long* __restrict__ off, int nq, long long t) {
+    int lo = 0, hi = nq - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int D, int DP>
+__global__ void __launch_bounds__(128) batch_sample_kernel(const QueryDev* __restrict__ Q,
+                                                           const long long* __restrict__ off, int nq) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= off[nq]) return;
+    const int k = find_query(off, nq, t);
+    const QueryDev& q = Q[k];
+    sample_node<D, DP>(q.s, q.boxes, q.X, q.is_goal, q.flags, (int)(t - off[k]));
+}
+
+template <int KIND, int D>
+__global__ void __launch_bounds__(kMaskRows) batch_mask_kernel(const QueryDev* __restrict__ Q,
+                                                               const long long* __restrict__ off, int nq) {
+    const long long b = blockIdx.x;
+    const int k = find_query(off, nq, b);
+    const QueryDev& q = Q[k];
+    const int rb = (q.s.N + kMaskRows - 1) / kMaskRows;
+    const int t = (int)(b - off[k]);
+    mask_tile<KIND, D>(q.s, q.X, q.mask, q.out_count, t % rb, t / rb);
+}
+
+__global__ void __launch_bounds__(kDIRows) batch_mask_di_kernel(const QueryDev* __restrict__ Q,
+                                                               const long long* __restrict__ off, int nq) {
+    const long long b = blockIdx.x;
+    const int k = find_query(off, nq, b);
+    const QueryDev& q = Q[k];
+    const int rb = (q.s.N + kDIRows - 1) / kDIRows;
+    const int t = (int)(b - off[k]);
+    mask_di_tile(q.s, q.X, q.mask, q.out_count, t % rb, t / rb);
+}
+
+__global__ void __launch_bounds__(256) batch_transpose_kernel(const QueryDev* __restrict__ Q,
+                                                              const long long* __restrict__ off, int nq) {
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (w >= off[nq]) return;
+    const int k = find_query(off, nq, w);
+    const QueryDev& q = Q[k];
+    transpose_task(q.s.N, q.s.pitch, q.mask, q.maskT, q.in_count, w - off[k]);
+}
+
+__global__ void __launch_bounds__(1024) batch_scan_kernel(const QueryDev* __restrict__ Q, int incoming) {
+    const QueryDev& q = Q[blockIdx.x];
+    if (incoming) scan_rows(q.in_count, q.in_row, q.s.N);
+    else scan_rows(q.out_count, q.out_row, q.s.N);
+}
+
+// One warp per (query, row).  A query whose edge count exceeds the slice it was
+// given (only possible if a replayed batch's inputs changed in place) writes
+// nothing; its plan then reports GMT_ERR_OOM.
+template <int KIND, int D, bool INCOMING>
+__global__ void __launch_bounds__(kFillWarps * 32) batch_fill_kernel(const QueryDev* __restrict__ Q,
+                                                                     const long long* __restrict__ off, int nq) {
+    const long long w = (long long)blockIdx.x * kFillWarps + (threadIdx.x >> 5);
+    if (w >= off[nq]) return;
+    const int k = find_query(off, nq, w);
+    const QueryDev& q = Q[k];
+    const int* row = INCOMING ? q.in_row : q.out_row;
+    if ((long long)row[q.s.N] > q.edge_cap) return;
+    if (INCOMING)
+        fill_row<KIND, D, true>(q.s, q.X, q.maskT, q.in_row, q.in_col, q.in_cost, q.in_tau, q.out_row, q.out_col,
+                                q.out_cost, q.out_tau, (int)(w - off[k]));
+    else
+        fill_row<KIND, D, false>(q.s, q.X, q.mask, q.out_row, q.out_col, q.out_cost, q.out_tau, nullptr, nullptr,
+                                 nullptr, nullptr, (int)(w - off[k]));
+}
+
+namespace {
+template <int D, int DP>
+void sample_g(const QueryDev* Q, const long long* off, int nq, long long total, cudaStream_t st) {
+    batch_sample_kernel<D, DP><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(Q, off, nq);
+}
+template <int KIND, int D>
+void mask_g(const QueryDev* Q, const long long* off, int nq, long long tiles, cudaStream_t st) {
+    if (KIND == GMT_COST_DI) batch_mask_di_kernel<<<(unsigned)tiles, kDIRows, 0, st>>>(Q, off, nq);
+    else batch_mask_kernel<KIND, D><<<(unsigned)tiles, kMaskRows, 0, st>>>(Q, off, nq);
+}
+template <int KIND, int D>
+void fill_g(const QueryDev* Q, const long long* off, int nq, long long rows, bool incoming, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((rows + kFillWarps - 1) / kFillWarps);
+    if (incoming) batch_fill_kernel<KIND, D, true><<<blocks, kFillWarps * 32, 0, st>>>(Q, off, nq);
+    else batch_fill_kernel<KIND, D, false><<<blocks, kFillWarps * 32, 0, st>>>(Q, off, nq);
+}
+}  // namespace
+
+cudaError_t batch_sample(int kind, int d, const QueryDev* Q, const long long* off, int nq, long long total,
+                         cudaStream_t st) {
+    if (kind == GMT_COST_DI) sample_g<6, 3>(Q, off, nq, total, st);
+    else if (d == 2) sample_g<2, 2>(Q, off, nq, total, st);
+    else if (d == 3) sample_g<3, 3>(Q, off, nq, total, st);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+cudaError_t batch_mask(int kind, int d, const QueryDev* Q, const long long* off, int nq, long long tiles,
+                       cudaStream_t st) {
+    if (kind == GMT_COST_DI) mask_g<GMT_COST_DI, 6>(Q, off, nq, tiles, st);
+    else if (d == 2) mask_g<GMT_COST_EUCLID, 2>(Q, off, nq, tiles, st);
+    else if (d == 3) mask_g<GMT_COST_EUCLID, 3>(Q, off, nq, tiles, st);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+cudaError_t batch_fill(int kind, int d, const QueryDev* Q, const long long* off, int nq, long long rows,
+                       bool incoming, cudaStream_t st) {
+    if (kind == GMT_COST_DI) fill_g<GMT_COST_DI, 6>(Q, off, nq, rows, incoming, st);
+    else if (d == 2) fill_g<GMT_COST_EUCLID, 2>(Q, off, nq, rows, incoming, st);
+    else if (d == 3) fill_g<GMT_COST_EUCLID, 3>(Q, off, nq, rows, incoming, st);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+}  // namespace gmtk
+
+// =========================================================================== host
+using namespace gmtk;
+
+namespace {
+
+gmt_status bfail(gmt_status s, const std::string& m) {
+    record_error(m.c_str());
+    return s;
+}
+gmt_status bcuda(cudaError_t e, const char* what) {
+    return bfail(e == cudaErrorMemoryAllocation ? GMT_ERR_OOM : GMT_ERR_CUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define BCUDA(call, what)                                \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return bcuda(e_, what);   \
+    } while (0)
+
+// Device buffer that only grows.
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaError_t need(size_t bytes) {
+        if (p && cap >= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(&p, bytes ? bytes : 1);
+        if (e == cudaSuccess) cap = bytes ? bytes : 1;
+        return e;
+    }
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    template <class T> T* as() const { return (T*)p; }
+};
+
+float euclid_threshold_b(float r) {
+    float t = r * r;
+    while (t > 0.0f && std::sqrt(t) >= r) t = std::nextafter(t, 0.0f);
+    while (std::sqrt(t) < r) t = std::nextafter(t, INFINITY);
+    return t;
+}
+
+constexpr size_t kCtlSlotB = 256;
+
+struct Group {
+    int kind = 0, d = 0, dp = 0;
+    std::vector<int> members;          // query indices
+    long long nodes = 0, tiles = 0, tasks = 0;
+    int max_n = 0, max_boxes = 0;
+    DevBuf desc, off_nodes, off_tiles, off_tasks, off_rows, order, args;
+    std::vector<int> order_h;
+};
+
+}  // namespace
+
+struct gmt_batch {
+    int q = 0;
+    std::vector<gmt_query> queries;
+    std::vector<int> N, pitch;
+    std::vector<long long> node_base;  // offsets into the caller's parent/cost arrays
+    std::vector<long long> E;
+    std::vector<QueryDev> qd;
+    std::vector<float> r;
+    std::vector<Group> groups;
+    // arena
+    DevBuf X, goal, flags, mask, maskT, counts, rows, edges_i, edges_f, path, ctl, next, slot;
+    DevBuf s_ocost, s_stamp, s_lists;
+    PlanCtl* h_ctl = nullptr;
+    int* h_rows = nullptr;
+    size_t h_cap = 0;
+    // launch shape of the plan stage
+    int cluster = 0, threads = 0;      // 0 = automatic / tuned
+    int tuned_cluster = 0, tuned_threads = 0;
+    // captured replay
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int32_t* cap_parent = nullptr;
+    float* cap_cost = nullptr;
+    bool prepared = false;
+    int calls_same = 0;
+    cudaStream_t cap_stream = nullptr;
+
+    ~gmt_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (h_ctl) cudaFreeHost(h_ctl);
+        if (h_rows) cudaFreeHost(h_rows);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+};
+
+namespace {
+
+gmt_status check_query(const gmt_query& Qh, int k) {
+    const gmt_space& sp = Qh.space;
+    const std::string at = " (query " + std::to_string(k) + ")";
+    if (sp.kind == GMT_COST_EUCLID) {
+        if (!(sp.dim == 2 || sp.dim == 3) || sp.pos_dim != sp.dim)
+            return bfail(GMT_ERR_INVALID, "batched geometric queries need dim 2 or 3 and pos_dim == dim" + at);
+    } else if (sp.kind == GMT_COST_DI) {
+        if (sp.dim != 6 || sp.pos_dim != 3) return bfail(GMT_ERR_INVALID, "double integrator needs dim 6, pos_dim 3" + at);
+    } else {
+        return bfail(GMT_ERR_INVALID, "unknown cost kind" + at);
+    }
+    for (int a = 0; a < sp.dim; ++a)
+        if (!(sp.lo[a] < sp.hi[a])) return bfail(GMT_ERR_INVALID, "state bounds need lo < hi" + at);
+    if (Qh.boxes.count < 0 || (Qh.boxes.count > 0 && (!Qh.boxes.lo || !Qh.boxes.hi)))
+        return bfail(GMT_ERR_INVALID, "bad box arrays" + at);
+    const gmt_params& p = Qh.params;
+    if (p.n < 1 || p.n > (1 << 24)) return bfail(GMT_ERR_INVALID, "n must be in [1, 2^24]" + at);
+    if (!(p.lambda >= 0.0f && p.lambda <= 1.0f)) return bfail(GMT_ERR_INVALID, "lambda must be in [0, 1]" + at);
+    if (p.r <= 0.0f && (!(p.eta >= 0.0f) || !(p.mu_free > 0.0f)))
+        return bfail(GMT_ERR_INVALID, "r <= 0 needs eta >= 0 and mu_free > 0" + at);
+    if (!(p.seg_spacing > 0.0f) || p.traj_points < 2)
+        return bfail(GMT_ERR_INVALID, "seg_spacing must be > 0 and traj_points >= 2" + at);
+    if (!(Qh.goal.radius >= 0.0f)) return bfail(GMT_ERR_INVALID, "goal radius must be >= 0" + at);
+    return GMT_OK;
+}
+
+void info_from_ctl(const PlanCtl& c, gmt_plan_info* info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = c.status;
+    info->goal_node = c.goal_node;
+    info->path_len = c.path_len;
+    info->path_cost = INFINITY;
+    if (c.status == GMT_OK && c.goal_node >= 0) {
+        const unsigned bits = (unsigned)(c.goal_key >> 32);
+        std::memcpy(&info->path_cost, &bits, sizeof(float));
+    }
+    info->iters = c.iters;
+    info->final_i = c.final_i;
+    info->push_edges = (int64_t)c.push_edges;
+    info->pull_edges = (int64_t)c.pull_edges;
+    info->checks = (int64_t)c.checks;
+    info->failed = (int64_t)c.failed;
+    info->tree_size = (int64_t)c.tree_size;
+}
+
+// Plan-stage launch shape for a group: (cluster, threads, teams).
+void plan_shape(const gmt_batch* b, const Group& g, int* cluster, int* threads, int* teams) {
+    int c = b->cluster > 0 ? b->cluster : (b->tuned_cluster > 0 ? b->tuned_cluster : 2);
+    int t = b->threads > 0 ? b->threads : (b->tuned_threads > 0 ? b->tuned_threads : 512);
+    int n = plan_batch_max_teams(g.kind, g.dp, t, c);
+    while (n <= 0 && c > 1) {
+        c /= 2;
+        n = plan_batch_max_teams(g.kind, g.dp, t, c);
+    }
+    *cluster = c;
+    *threads = t;
+    *teams = n;
+}
+
+// Everything after the edge counts are known: fill + plan + result copy.
+// Runs on `st`; records nothing that needs the host in between, so it can be
+// captured into a CUDA graph together with the first half (see run_device).
+gmt_status enqueue_build_front(gmt_batch* b, cudaStream_t st) {
+    BCUDA(cudaMemsetAsync(b->flags.p, 0, b->flags.cap, st), "memset");
+    BCUDA(cudaMemsetAsync(b->counts.p, 0, b->counts.cap, st), "memset");
+    for (Group& g : b->groups) {
+        const int nq = (int)g.members.size();
+        const QueryDev* Q = g.desc.as<QueryDev>();
+        BCUDA(batch_sample(g.kind, g.d, Q, g.off_nodes.as<long long>(), nq, g.nodes, st), "batched sample kernel");
+        BCUDA(batch_mask(g.kind, g.d, Q, g.off_tiles.as<long long>(), nq, g.tiles, st), "batched pair filter");
+        if (g.kind == GMT_COST_DI) {
+            const long long warps = g.tasks;
+            batch_transpose_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(Q, g.off_tasks.as<long long>(), nq);
+            BCUDA(cudaGetLastError(), "batched transpose");
+        }
+        batch_scan_kernel<<<nq, 1024, 0, st>>>(Q, 0);
+        if (g.kind == GMT_COST_DI) batch_scan_kernel<<<nq, 1024, 0, st>>>(Q, 1);
+        BCUDA(cudaGetLastError(), "batched scan");
+    }
+    return GMT_OK;
+}
+
+gmt_status enqueue_build_back(gmt_batch* b, int32_t* parent, float* cost, cudaStream_t st) {
+    for (Group& g : b->groups) {
+        const int nq = (int)g.members.size();
+        const QueryDev* Q = g.desc.as<QueryDev>();
+        BCUDA(batch_fill(g.kind, g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, false, st), "batched fill");
+        if (g.kind == GMT_COST_DI)
+            BCUDA(batch_fill(g.kind, g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, true, st), "batched fill");
+    }
+    BCUDA(cudaMemsetAsync(b->ctl.p, 0, b->ctl.cap, st), "memset");
+    BCUDA(cudaMemsetAsync(b->next.p, 0, b->next.cap, st), "memset");
+    int gi = 0;
+    for (Group& g : b->groups) {
+        int cluster, threads, teams;
+        plan_shape(b, g, &cluster, &threads, &teams);
+        if (teams <= 0) return bfail(GMT_ERR_CUDA, "batched plan kernel cannot be resident");
+        BatchScratch sc;
+        sc.ocost = b->s_ocost.as<float>();
+        sc.stamp = b->s_stamp.as<int>();
+        sc.lists = b->s_lists.as<int>();
+        sc.max_nodes = g.max_n;
+        BCUDA(launch_plan_batch(g.kind, g.dp, g.args.as<PlanArgs>(), g.order.as<int>(), (int)g.members.size(),
+                                b->next.as<int>() + gi, b->slot.as<int>(), sc, teams, threads, cluster, g.max_boxes,
+                                st),
+              "batched plan kernel");
+        ++gi;
+    }
+    (void)parent;
+    (void)cost;
+    BCUDA(cudaMemcpyAsync(b->h_ctl, b->ctl.p, (size_t)b->q * kCtlSlotB, cudaMemcpyDeviceToHost, st), "result copy");
+    return GMT_OK;
+}
+
+// Lays out the arena for the queries, runs the front half, reads the edge
+// counts, sizes the edge slices, fills the descriptors and plan arguments.
+gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* parent, float* cost, cudaStream_t st) {
+    b->prepared = false;
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    b->q = q;
+    b->queries.assign(queries, queries + q);
+    b->N.resize(q); b->pitch.resize(q); b->node_base.resize(q + 1); b->E.assign(q, 0); b->qd.resize(q); b->r.resize(q);
+    b->groups.clear();
+    // groups
+    for (int k = 0; k < q; ++k) {
+        const gmt_space& sp = queries[k].space;
+        Group* g = nullptr;
+        for (Group& x : b->groups)
+            if (x.kind == sp.kind && x.d == sp.dim) g = &x;
+        if (!g) {
+            b->groups.emplace_back();
+            g = &b->groups.back();
+            g->kind = sp.kind; g->d = sp.dim; g->dp = sp.pos_dim;
+        }
+        g->members.push_back(k);
+    }
+    // sizes and offsets
+    size_t xs = 0, gs = 0, ms = 0, mts = 0, cs = 0, rs = 0, ps = 0;
+    std::vector<size_t> xo(q), go(q), mo(q), mto(q), co(q), ro(q), po(q);
+    b->node_base[0] = 0;
+    for (int k = 0; k < q; ++k) {
+        const gmt_query& Qh = queries[k];
+        const int N = Qh.params.n + 1;
+        const int P = (N + 31) / 32 * 32, W = (N + 31) / 32;
+        b->N[k] = N; b->pitch[k] = P;
+        b->node_base[k + 1] = b->node_base[k] + N;
+        xo[k] = xs; xs += (size_t)Qh.space.dim * P;
+        go[k] = gs; gs += P;
+        mo[k] = ms; ms += (size_t)W * P;
+        if (Qh.space.kind == GMT_COST_DI) { mto[k] = mts; mts += (size_t)W * P; }
+        co[k] = cs; cs += 2 * (size_t)N;
+        ro[k] = rs; rs += 2 * (size_t)(N + 1);
+        po[k] = ps; ps += N;
+        b->r[k] = Qh.params.r > 0.0f ? Qh.params.r
+                                     : (float)gmt_connection_radius(Qh.params.n, Qh.space.dim, Qh.params.eta,
+                                                                    Qh.params.mu_free);
+    }
+    BCUDA(b->X.need(xs * 4), "arena");
+    BCUDA(b->goal.need(gs), "arena");
+    BCUDA(b->flags.need((size_t)q * 4), "arena");
+    BCUDA(b->mask.need(ms * 4), "arena");
+    BCUDA(b->maskT.need(mts * 4 + 4), "arena");
+    BCUDA(b->counts.need(cs * 4), "arena");
+    BCUDA(b->rows.need(rs * 4), "arena");
+    BCUDA(b->path.need(ps * 4), "arena");
+    BCUDA(b->ctl.need((size_t)q * kCtlSlotB), "arena");
+    BCUDA(b->next.need(b->groups.size() * 4), "arena");
+    if (b->h_cap < (size_t)q) {
+        if (b->h_ctl) cudaFreeHost(b->h_ctl);
+        if (b->h_rows) cudaFreeHost(b->h_rows);
+        b->h_ctl = nullptr; b->h_rows = nullptr; b->h_cap = 0;
+        BCUDA(cudaMallocHost((void**)&b->h_ctl, (size_t)q * kCtlSlotB), "pinned");
+        BCUDA(cudaMallocHost((void**)&b->h_rows, (size_t)q * 2 * sizeof(int)), "pinned");
+        b->h_cap = q;
+    }
+    for (int k = 0; k < q; ++k) {
+        const gmt_query& Qh = queries[k];
+        QueryDev& d = b->qd[k];
+        std::memset(&d, 0, sizeof(d));
+        SpaceArgs& s = d.s;
+        s.kind = Qh.space.kind; s.d = Qh.space.dim; s.dp = Qh.space.pos_dim; s.N = b->N[k]; s.pitch = b->pitch[k];
+        for (int a = 0; a < s.d; ++a) {
+            s.lo[a] = Qh.space.lo[a]; s.hi[a] = Qh.space.hi[a];
+            s.x0[a] = Qh.x_init[a]; s.gc[a] = Qh.goal.center[a];
+        }
+        s.grho = Qh.goal.radius;
+        s.gd = Qh.goal.pos_only ? s.dp : s.d;
+        s.key0 = (uint32_t)(Qh.params.seed & 0xffffffffu);
+        s.key1 = (uint32_t)(Qh.params.seed >> 32);
+        s.stream = 0;
+        s.max_attempts = Qh.params.max_attempts > 0 ? Qh.params.max_attempts : 65536;
+        s.r = b->r[k];
+        s.r2_threshold = euclid_threshold_b(s.r);
+        d.boxes = BoxArgs{Qh.boxes.count, Qh.boxes.lo, Qh.boxes.hi};
+        d.X = b->X.as<float>() + xo[k];
+        d.is_goal = b->goal.as<uint8_t>() + go[k];
+        d.flags = b->flags.as<int>() + k;
+        d.mask = b->mask.as<uint32_t>() + mo[k];
+        d.maskT = s.kind == GMT_COST_DI ? b->maskT.as<uint32_t>() + mto[k] : nullptr;
+        d.out_count = b->counts.as<int>() + co[k];
+        d.in_count = d.out_count + s.N;
+        d.out_row = b->rows.as<int>() + ro[k];
+        d.in_row = s.kind == GMT_COST_DI ? d.out_row + (s.N + 1) : d.out_row;
+        d.edge_cap = 0;
+    }
+    // per-group work offsets and descriptors
+    for (Group& g : b->groups) {
+        const int nq = (int)g.members.size();
+        std::vector<long long> on(nq + 1, 0), ot(nq + 1, 0), ow(nq + 1, 0);
+        std::vector<QueryDev> dq(nq);
+        g.max_n = 0; g.max_boxes = 0;
+        for (int i = 0; i < nq; ++i) {
+            const int k = g.members[i];
+            const int N = b->N[k], W = (N + 31) / 32;
+            const long long tiles = g.kind == GMT_COST_DI
+                                        ? (long long)((N + kDIRows - 1) / kDIRows) * ((W + kDIWords - 1) / kDIWords)
+                                        : (long long)((N + kMaskRows - 1) / kMaskRows) * ((W + kMaskWords - 1) / kMaskWords);
+            on[i + 1] = on[i] + N;
+            ot[i + 1] = ot[i] + tiles;
+            ow[i + 1] = ow[i] + (long long)W * W;
+            g.max_n = std::max(g.max_n, N);
+            g.max_boxes = std::max(g.max_boxes, queries[k].boxes.count);
+            dq[i] = b->qd[k];
+        }
+        g.nodes = on[nq]; g.tiles = ot[nq]; g.tasks = ow[nq];
+        BCUDA(g.desc.need(nq * sizeof(QueryDev)), "descriptors");
+        BCUDA(g.off_nodes.need((nq + 1) * 8), "descriptors");
+        BCUDA(g.off_tiles.need((nq + 1) * 8), "descriptors");
+        BCUDA(g.off_tasks.need((nq + 1) * 8), "descriptors");
+        BCUDA(g.off_rows.need((nq + 1) * 8), "descriptors");
+        BCUDA(cudaMemcpyAsync(g.desc.p, dq.data(), nq * sizeof(QueryDev), cudaMemcpyHostToDevice, st), "upload");
+        BCUDA(cudaMemcpyAsync(g.off_nodes.p, on.data(), (nq + 1) * 8, cudaMemcpyHostToDevice, st), "upload");
+        BCUDA(cudaMemcpyAsync(g.off_tiles.p, ot.data(), (nq + 1) * 8, cudaMemcpyHostToDevice, st), "upload");
+        BCUDA(cudaMemcpyAsync(g.off_tasks.p, ow.data(), (nq + 1) * 8, cudaMemcpyHostToDevice, st), "upload");
+        BCUDA(cudaMemcpyAsync(g.off_rows.p, on.data(), (nq + 1) * 8, cudaMemcpyHostToDevice, st), "upload");
+        BCUDA(cudaStreamSynchronize(st), "upload");  // host vectors go out of scope
+    }
+    gmt_status s = enqueue_build_front(b, st);
+    if (s != GMT_OK) return s;
+    // edge counts: out_row[N] (and in_row[N]) of every query
+    for (int k = 0; k < q; ++k)
+        BCUDA(cudaMemcpyAsync(b->h_rows + k, b->qd[k].out_row + b->N[k], sizeof(int), cudaMemcpyDeviceToHost, st),
+              "edge count readback");
+    std::vector<int> flags(q);
+    BCUDA(cudaMemcpyAsync(flags.data(), b->flags.p, (size_t)q * 4, cudaMemcpyDeviceToHost, st), "flag readback");
+    BCUDA(cudaStreamSynchronize(st), "batched graph build");
+    for (int k = 0; k < q; ++k) {
+        if (flags[k] & kSampleBadInit)
+            return bfail(GMT_ERR_INVALID, "x_init outside X or in an obstacle (query " + std::to_string(k) + ")");
+        if (flags[k] & kSampleExhausted)
+            return bfail(GMT_ERR_INVALID, "sampling exhausted max_attempts (query " + std::to_string(k) + ")");
+    }
+    size_t ei = 0;
+    std::vector<size_t> eo(q);
+    for (int k = 0; k < q; ++k) {
+        b->E[k] = b->h_rows[k];
+        eo[k] = ei;
+        ei += (size_t)b->E[k] * (queries[k].space.kind == GMT_COST_DI ? 2 : 1);
+    }
+    BCUDA(b->edges_i.need(ei * 4 + 4), "edge arena");
+    BCUDA(b->edges_f.need(ei * 2 * 4 + 4), "edge arena");
+    for (int k = 0; k < q; ++k) {
+        QueryDev& d = b->qd[k];
+        const size_t E = (size_t)b->E[k];
+        const bool di = d.s.kind == GMT_COST_DI;
+        d.out_col = b->edges_i.as<int>() + eo[k];
+        d.out_cost = b->edges_f.as<float>() + 2 * eo[k];
+        d.out_tau = di ? d.out_cost + E : nullptr;
+        d.in_col = di ? d.out_col + E : d.out_col;
+        d.in_cost = di ? d.out_cost + 2 * E : d.out_cost;
+        d.in_tau = di ? d.out_cost + 3 * E : nullptr;
+        d.edge_cap = (long long)E;
+    }
+    // plan arguments, order (largest edge count first), scratch
+    int max_n = 0;
+    for (Group& g : b->groups) {
+        const int nq = (int)g.members.size();
+        std::vector<QueryDev> dq(nq);
+        std::vector<PlanArgs> pa(nq);
+        for (int i = 0; i < nq; ++i) {
+            const int k = g.members[i];
+            const QueryDev& d = b->qd[k];
+            const gmt_query& Qh = queries[k];
+            dq[i] = d;
+            PlanArgs& a = pa[i];
+            std::memset(&a, 0, sizeof(a));
+            a.kind = d.s.kind; a.d = d.s.d; a.dp = d.s.dp; a.N = d.s.N; a.pitch = d.s.pitch;
+            a.X = d.X; a.is_goal = d.is_goal;
+            a.out_row = d.out_row; a.out_col = d.out_col;
+            a.in_row = d.in_row; a.in_col = d.in_col; a.in_cost = d.in_cost; a.in_tau = d.in_tau;
+            a.boxes = d.boxes;
+            for (int c = 0; c < 3 && c < d.s.dp; ++c) { a.pos_lo[c] = Qh.space.lo[c]; a.pos_hi[c] = Qh.space.hi[c]; }
+            a.r = d.s.r;
+            a.delta = Qh.params.lambda * d.s.r;
+            a.seg_spacing = Qh.params.seg_spacing;
+            a.traj_points = Qh.params.traj_points;
+            a.max_iters = Qh.params.max_iters > 0 ? Qh.params.max_iters : d.s.N + 1;
+            a.spin_limit = Qh.params.spin_limit;
+            a.debug_flags = 0;
+            a.cost = cost + b->node_base[k];
+            a.parent = parent + b->node_base[k];
+            a.path = b->path.as<int>() + po[k];
+            a.ctl = (PlanCtl*)(b->ctl.as<unsigned char>() + (size_t)k * kCtlSlotB);
+            a.check_edges = 1;
+            a.edge_cap = d.edge_cap;
+        }
+        g.order_h.resize(nq);
+        std::iota(g.order_h.begin(), g.order_h.end(), 0);
+        std::stable_sort(g.order_h.begin(), g.order_h.end(),
+                         [&](int x, int y) { return b->E[g.members[x]] > b->E[g.members[y]]; });
+        BCUDA(cudaMemcpyAsync(g.desc.p, dq.data(), nq * sizeof(QueryDev), cudaMemcpyHostToDevice, st), "upload");
+        BCUDA(g.args.need(nq * sizeof(PlanArgs)), "plan arguments");
+        BCUDA(g.order.need(nq * sizeof(int)), "plan order");
+        BCUDA(cudaMemcpyAsync(g.args.p, pa.data(), nq * sizeof(PlanArgs), cudaMemcpyHostToDevice, st), "upload");
+        BCUDA(cudaMemcpyAsync(g.order.p, g.order_h.data(), nq * sizeof(int), cudaMemcpyHostToDevice, st), "upload");
+        BCUDA(cudaStreamSynchronize(st), "upload");
+        max_n = std::max(max_n, g.max_n);
+    }
+    // scratch for the most teams any shape can run
+    int max_teams = 0;
+    for (Group& g : b->groups)
+        for (int c : {1, 2, 4, 8, 16})
+            for (int t : {256, 512, 1024}) max_teams = std::max(max_teams, plan_batch_max_teams(g.kind, g.dp, t, c));
+    cudaGetLastError();
+    if (max_teams <= 0) return bfail(GMT_ERR_CUDA, "batched plan kernel cannot be resident");
+    BCUDA(b->s_ocost.need((size_t)max_teams * max_n * 4), "scratch");
+    BCUDA(b->s_stamp.need((size_t)max_teams * max_n * 4), "scratch");
+    BCUDA(b->s_lists.need((size_t)max_teams * max_n * 5 * 4), "scratch");
+    BCUDA(b->slot.need((size_t)max_teams * 4), "scratch");
+    // scratch slices are indexed by team id, so every group may use all of it
+    for (Group& g : b->groups) g.max_n = max_n;
+    b->prepared = true;
+    b->cap_parent = parent;
+    b->cap_cost = cost;
+    return GMT_OK;
+}
+
+bool same_request(const gmt_batch* b, int q, const gmt_query* queries, int32_t* parent, float* cost) {
+    return b->prepared && b->q == q && b->cap_parent == parent && b->cap_cost == cost &&
+           std::memcmp(b->queries.data(), queries, (size_t)q * sizeof(gmt_query)) == 0;
+}
+
+gmt_status finish(gmt_batch* b, gmt_plan_info* infos, cudaStream_t st) {
+    BCUDA(cudaStreamSynchronize(st), "batched plan");
+    gmt_status worst = GMT_OK;
+    for (int k = 0; k < b->q; ++k) {
+        const PlanCtl& c = *(const PlanCtl*)((const unsigned char*)b->h_ctl + (size_t)k * kCtlSlotB);
+        info_from_ctl(c, &infos[k]);
+        if (c.status < 0 && worst == GMT_OK) worst = (gmt_status)c.status;
+    }
+    if (worst != GMT_OK) return bfail(worst, "at least one query failed (see its info.status)");
+    return GMT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gmt_status gmt_plan_batch(int32_t q, const gmt_query* queries, gmt_batch** batch, int32_t* parent, float* cost,
+                          gmt_plan_info* infos, gmt_stream stream) {
+    if (q < 1 || !queries || !batch || !parent || !cost || !infos)
+        return bfail(GMT_ERR_INVALID, "q >= 1 and non-NULL queries, batch, parent, cost and infos are required");
+    for (int k = 0; k < q; ++k) {
+        gmt_status s = check_query(queries[k], k);
+        if (s != GMT_OK) return s;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fresh = *batch == nullptr;
+    gmt_batch* b = fresh ? new gmt_batch() : *batch;
+    if (fresh) *batch = b;
+    if (same_request(b, q, queries, parent, cost)) {
+        // replay: capture the device sequence once, then launch the graph
+        if (!b->exec) {
+            if (!b->cap_stream) BCUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream");
+            BCUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+            gmt_status s = enqueue_build_front(b, b->cap_stream);
+            if (s == GMT_OK) s = enqueue_build_back(b, parent, cost, b->cap_stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+            if (s != GMT_OK) { if (g) cudaGraphDestroy(g); return s; }
+            if (e != cudaSuccess) return bcuda(e, "graph capture");
+            b->graph = g;
+            BCUDA(cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
+        }
+        BCUDA(cudaGraphLaunch(b->exec, st), "graph launch");
+        return finish(b, infos, st);
+    }
+    gmt_status s = prepare(b, q, queries, parent, cost, st);
+    if (s != GMT_OK) return s;
+    s = enqueue_build_back(b, parent, cost, st);
+    if (s != GMT_OK) return s;
+    return finish(b, infos, st);
+}
+
+gmt_status gmt_batch_get_view(const gmt_batch* b, int32_t k, gmt_graph_view* v, int32_t** path) {
+    if (!b || !v || !b->prepared || k < 0 || k >= b->q) return bfail(GMT_ERR_INVALID, "no such prepared query");
+    const QueryDev& d = b->qd[k];
+    std::memset(v, 0, sizeof(*v));
+    v->kind = d.s.kind; v->dim = d.s.d; v->pos_dim = d.s.dp; v->N = d.s.N; v->x_pitch = d.s.pitch;
+    v->E = b->E[k]; v->r = d.s.r;
+    v->X = d.X; v->is_goal = d.is_goal;
+    v->out_row = d.out_row; v->out_col = d.out_col; v->out_cost = d.out_cost;
+    v->in_row = d.in_row; v->in_col = d.in_col; v->in_cost = d.in_cost;
+    v->out_tau = d.out_tau; v->in_tau = d.in_tau;
+    if (path) *path = b->path.as<int>() + (b->node_base[k]);
+    return GMT_OK;
+}
+
+gmt_status gmt_batch_set_launch(gmt_batch* b, int32_t cluster, int32_t threads) {
+    if (!b) return bfail(GMT_ERR_INVALID, "batch is NULL");
+    if (cluster < 0 || cluster > 16 || (cluster & (cluster - 1)) != 0)
+        return bfail(GMT_ERR_INVALID, "cluster must be 0 or a power of two up to 16");
+    if (threads != 0 && (threads < 128 || threads > 1024 || threads % 32 != 0))
+        return bfail(GMT_ERR_INVALID, "threads must be 0 or a multiple of 32 in [128, 1024]");
+    b->cluster = cluster;
+    b->threads = threads;
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    return GMT_OK;
+}
+
+gmt_status gmt_batch_autotune(gmt_batch* b, gmt_stream stream, int32_t* best_cluster, int32_t* best_threads,
+                              float* best_ms) {
+    if (!b || !b->prepared) return bfail(GMT_ERR_INVALID, "autotune needs a batch planned once");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int keep_c = b->cluster, keep_t = b->threads;
+    cudaEvent_t e0, e1;
+    BCUDA(cudaEventCreate(&e0), "event");
+    BCUDA(cudaEventCreate(&e1), "event");
+    float best = INFINITY;
+    int bc = 0, bt = 0;
+    for (int c : {1, 2, 4, 8, 16}) {
+        for (int t : {256, 512, 1024}) {
+            b->cluster = c;
+            b->threads = t;
+            int cc, tt, teams;
+            bool ok = true;
+            for (Group& g : b->groups) {
+                plan_shape(b, g, &cc, &tt, &teams);
+                if (cc != c || teams <= 0) ok = false;
+            }
+            cudaGetLastError();
+            if (!ok) continue;
+            float ms_sum = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {
+                BCUDA(cudaEventRecord(e0, st), "event");
+                gmt_status s = enqueue_build_back(b, b->cap_parent, b->cap_cost, st);
+                if (s != GMT_OK) return s;
+                BCUDA(cudaEventRecord(e1, st), "event");
+                BCUDA(cudaEventSynchronize(e1), "event");
+                float ms = 0.0f;
+                BCUDA(cudaEventElapsedTime(&ms, e0, e1), "event");
+                if (rep > 0) ms_sum += ms;
+            }
+            if (ms_sum < best) { best = ms_sum; bc = c; bt = t; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cluster = keep_c;
+    b->threads = keep_t;
+    b->tuned_cluster = bc;
+    b->tuned_threads = bt;
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    if (best_cluster) *best_cluster = bc;
+    if (best_threads) *best_threads = bt;
+    if (best_ms) *best_ms = best;
+    return GMT_OK;
+}
+
+void gmt_batch_free(gmt_batch* b) { delete b; }
+
+}  // extern "C"

@@ -1,0 +1,341 @@
+// Device-function bodies of the SampleFree and neighbour-graph kernels,
+// shared by the single-problem kernels (graph.cu) and the batched ones
+// (batch.cu), so both run the same arithmetic.
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gmtk {
+
+
+// ------------------------------------------------------------------ sampling
+__device__ __forceinline__ bool in_goal_ball(const float* x, int gd, const float* c, float rho) {
+    float s = 0.0f;
+    for (int a = 0; a < gd; ++a) {
+        const float t = x[a] - c[a];
+        s = s + t * t;
+    }
+    return s <= rho * rho;
+}
+
+template <int D, int DP>
+__device__ __forceinline__ void sample_node(const SpaceArgs& s, const BoxArgs& boxes, float* __restrict__ X,
+                                            uint8_t* __restrict__ is_goal, int* __restrict__ flags, int k) {
+    if (k >= s.N) return;
+    float x[D];
+    if (k == 0) {
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            x[a] = s.x0[a];
+            ok = ok && s.lo[a] <= x[a] && x[a] <= s.hi[a];
+        }
+        if (!ok || in_any_box<DP>(x, boxes.lo, boxes.hi, boxes.count)) atomicOr(flags, kSampleBadInit);
+    } else {
+        bool ok = false;
+        for (int t = 0; t < s.max_attempts && !ok; ++t) {
+            uint32_t w[((D + 3) / 4) * 4];
+#pragma unroll
+            for (int blk = 0; blk < (D + 3) / 4; ++blk) {
+                const Ctr4 c = philox4x32_10(Ctr4{(uint32_t)k, (uint32_t)t, s.stream, (uint32_t)blk}, s.key0, s.key1);
+                w[4 * blk + 0] = c.x; w[4 * blk + 1] = c.y; w[4 * blk + 2] = c.z; w[4 * blk + 3] = c.w;
+            }
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float u = unit_float(w[a]);
+                float l = s.lo[a], h = s.hi[a];
+                if (k == 1 && a < s.gd) { l = s.gc[a] - s.grho; h = s.gc[a] + s.grho; }
+                x[a] = l + u * (h - l);
+            }
+            if (k == 1) {
+                bool inb = true;
+#pragma unroll
+                for (int a = 0; a < D; ++a) inb = inb && s.lo[a] <= x[a] && x[a] <= s.hi[a];
+                if (!inb || !in_goal_ball(x, s.gd, s.gc, s.grho)) continue;
+            }
+            if (in_any_box<DP>(x, boxes.lo, boxes.hi, boxes.count)) continue;
+            ok = true;
+        }
+        if (!ok) atomicOr(flags, kSampleExhausted);
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) X[(size_t)a * s.pitch + k] = x[a];
+    is_goal[k] = in_goal_ball(x, s.gd, s.gc, s.grho) ? 1 : 0;
+}
+
+// ------------------------------------------------------------- pair filter
+constexpr int kMaskRows = 256;     // rows (threads) per block
+constexpr int kMaskWords = 8;      // 32-column words per block (256 columns staged in shared memory)
+
+template <int KIND, int D>
+__device__ __forceinline__ bool connects(const SpaceArgs& s, const float* from, const float* to) {
+    if (KIND == GMT_COST_EUCLID) return sq_dist<D>(from, to) < s.r2_threshold;
+    if (!di_may_connect(from, to, s.r)) return false;
+    return di_cost(from, to, s.r) < s.r;
+}
+
+template <int KIND, int D>
+__device__ __forceinline__ float edge_cost(const SpaceArgs& s, const float* from, const float* to) {
+    if (KIND == GMT_COST_EUCLID) return __fsqrt_rn(sq_dist<D>(from, to));
+    return di_cost(from, to, s.r);
+}
+
+// One block of kMaskRows threads: rows bx*kMaskRows.., words by*kMaskWords..
+template <int KIND, int D>
+__device__ __forceinline__ void mask_tile(const SpaceArgs& s, const float* __restrict__ X,
+                                          uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
+                                          int by) {
+    __shared__ float tile[D][kMaskWords * 32];
+    const int i = bx * kMaskRows + threadIdx.x;
+    const int w0 = by * kMaskWords;
+    const int j0 = w0 * 32;
+    for (int idx = threadIdx.x; idx < kMaskWords * 32; idx += kMaskRows) {
+        const int j = j0 + idx;
+#pragma unroll
+        for (int a = 0; a < D; ++a) tile[a][idx] = j < s.N ? X[(size_t)a * s.pitch + j] : 0.0f;
+    }
+    __syncthreads();
+    if (i >= s.N) return;
+    float xi[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) xi[a] = X[(size_t)a * s.pitch + i];
+    const int W = (s.N + 31) / 32;
+    int cnt = 0;
+    for (int ww = 0; ww < kMaskWords; ++ww) {
+        const int w = w0 + ww;
+        if (w >= W) break;
+        uint32_t bits = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int j = w * 32 + b;
+            if (j >= s.N || j == i) continue;
+            float xj[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) xj[a] = tile[a][ww * 32 + b];
+            if (connects<KIND, D>(s, xi, xj)) bits |= 1u << b;
+        }
+        mask[(size_t)w * s.pitch + i] = bits;
+        cnt += __popc(bits);
+    }
+    if (cnt) atomicAdd(&out_count[i], cnt);
+}
+
+// Double-integrator pair filter.  The exact test (root bracketing + 24
+// halvings, ~400 FP32 operations) is needed only for the ~9% of pairs that
+// pass the conservative lower bound, so each warp first evaluates the bound
+// for its 32 rows against every staged column and queues the survivors
+// (row lane, column) in shared memory; whenever 32 are queued, the warp runs
+// the exact test on all of them at once (every lane busy), ORing the verdicts
+// into per-row words kept in shared memory.  Rows are the lanes' own rows, so
+// a queued pair fetches its row state from the owning lane with a shuffle.
+constexpr int kDIRows = 128;   // rows (threads) per block: 4 warps
+constexpr int kDIWords = 4;    // 32-column words per block (128 staged columns)
+
+// One block of kDIRows threads: rows bx*kDIRows.., words by*kDIWords..
+__device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __restrict__ X,
+                                             uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
+                                             int by) {
+    __shared__ float tile[6][kDIWords * 32];
+    __shared__ uint32_t words[kDIRows / 32][kDIWords][32];
+    __shared__ uint16_t queue[kDIRows / 32][64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = bx * kDIRows + threadIdx.x;
+    const int w0 = by * kDIWords;
+    const int j0 = w0 * 32;
+    for (int idx = threadIdx.x; idx < kDIWords * 32; idx += kDIRows) {
+        const int j = j0 + idx;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) tile[a][idx] = j < s.N ? X[(size_t)a * s.pitch + j] : 0.0f;
+    }
+#pragma unroll
+    for (int ww = 0; ww < kDIWords; ++ww) words[warp][ww][lane] = 0u;
+    __syncthreads();
+    const bool row_ok = i < s.N;
+    float xi[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) xi[a] = row_ok ? X[(size_t)a * s.pitch + i] : 0.0f;
+
+    // exact test of up to 32 queued pairs, one per lane
+    auto drain = [&](int count) {
+        const int e = lane < count ? queue[warp][lane] : 0;
+        const int src = e >> 8, jt = e & 255;
+        float a_[6], b_[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            a_[a] = __shfl_sync(0xffffffffu, xi[a], src);
+            b_[a] = tile[a][jt];
+        }
+        if (lane < count && di_cost(a_, b_, s.r) < s.r) atomicOr(&words[warp][jt >> 5][src], 1u << (jt & 31));
+    };
+
+    int qn = 0;
+    const int jend = min(kDIWords * 32, s.N - j0);
+    for (int jt = 0; jt < jend; ++jt) {
+        const int j = j0 + jt;
+        float xj[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) xj[a] = tile[a][jt];
+        const bool pass = row_ok && j != i && di_may_connect(xi, xj, s.r);
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        if (pass) queue[warp][qn + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((lane << 8) | jt);
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+            drain(32);
+            __syncwarp();
+            if (lane < qn - 32) queue[warp][lane] = queue[warp][32 + lane];
+            qn -= 32;
+            __syncwarp();
+        }
+    }
+    if (qn > 0) drain(qn);
+    __syncwarp();
+    if (!row_ok) return;
+    const int W = (s.N + 31) / 32;
+    int cnt = 0;
+#pragma unroll
+    for (int ww = 0; ww < kDIWords; ++ww) {
+        const int w = w0 + ww;
+        if (w >= W) break;
+        const uint32_t bits = words[warp][ww][lane];
+        mask[(size_t)w * s.pitch + i] = bits;
+        cnt += __popc(bits);
+    }
+    if (cnt) atomicAdd(&out_count[i], cnt);
+}
+
+// maskT[u][j] bit l = mask[j/32][32u + l] bit (j%32): the in-neighbour rows.
+// One warp: the 32x32 bit block `task` = (u, w).
+__device__ __forceinline__ void transpose_task(int N, int pitch, const uint32_t* __restrict__ mask,
+                                               uint32_t* __restrict__ maskT, int* __restrict__ in_count,
+                                               long long task) {
+    const int W = (N + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    if (task >= (long long)W * W) return;
+    const int u = (int)(task / W), w = (int)(task % W);
+    const int i = 32 * u + lane;
+    const uint32_t word = i < N ? mask[(size_t)w * pitch + i] : 0u;
+    uint32_t mine = 0;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+        const uint32_t t = __ballot_sync(0xffffffffu, (word >> b) & 1u);
+        if (lane == b) mine = t;
+    }
+    const int j = 32 * w + lane;
+    if (j < N) {
+        maskT[(size_t)u * pitch + j] = mine;
+        if (mine) atomicAdd(&in_count[j], __popc(mine));
+    }
+}
+
+// Exclusive prefix sum: row[v] = sum_{u < v} count[u], row[N] = total.
+// One block of 1024 threads.
+__device__ __forceinline__ void scan_rows(const int* __restrict__ count, int* __restrict__ row, int N) {
+    __shared__ int warp_sum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int carry = 0;
+    for (int base = 0; base < N; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < N ? count[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) warp_sum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int t = warp_sum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, off);
+                if (lane >= off) t += y;
+            }
+            warp_sum[lane] = t;
+        }
+        __syncthreads();
+        if (i < N) row[i] = carry + (warp > 0 ? warp_sum[warp - 1] : 0) + x - v;
+        carry += warp_sum[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) row[N] = carry;
+}
+
+// One warp per row v.  The row's words are read 32 at a time (one per lane),
+// the lanes' bit counts are prefix-summed, and the columns are written, in
+// ascending order, to a per-warp list in shared memory; the lanes then take
+// the listed edges one each, so the cost evaluations keep every lane busy.
+// Out-rows compute c(v, j).  In-rows of the double integrator look the cost
+// c(j, v) up in the finished out-row of j (binary search), so each edge cost is
+// computed once.
+constexpr int kFillWarps = 8;
+
+// One warp: row v (warp w of a block of kFillWarps warps).
+template <int KIND, int D, bool INCOMING>
+__device__ __forceinline__ void fill_row(const SpaceArgs& s, const float* __restrict__ X,
+                                         const uint32_t* __restrict__ M, const int* __restrict__ row,
+                                         int* __restrict__ col, float* __restrict__ cost, float* __restrict__ tau,
+                                         const int* __restrict__ out_row, const int* __restrict__ out_col,
+                                         const float* __restrict__ out_cost, const float* __restrict__ out_tau,
+                                         int v) {
+    __shared__ int list[kFillWarps][1024];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (v >= s.N) return;
+    float xv[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) xv[a] = X[(size_t)a * s.pitch + v];
+    const int W = (s.N + 31) / 32;
+    int base = row[v];
+    for (int c0 = 0; c0 < W; c0 += 32) {
+        const int w = c0 + lane;
+        uint32_t bits = w < W ? M[(size_t)w * s.pitch + v] : 0u;
+        const int n = __popc(bits);
+        int incl = n;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int pos = incl - n;
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            list[warp][pos++] = 32 * w + b;
+        }
+        __syncwarp();
+        for (int t = lane; t < total; t += 32) {
+            const int j = list[warp][t];
+            float c, tj = 0.0f;
+            if (INCOMING && KIND == GMT_COST_DI) {
+                int lo = out_row[j], hi = out_row[j + 1] - 1;   // v is in the out-row of j
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (out_col[mid] < v) lo = mid + 1; else hi = mid;
+                }
+                c = out_cost[lo];
+                tj = out_tau[lo];
+            } else if (KIND == GMT_COST_DI) {
+                float xj[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) xj[a] = X[(size_t)a * s.pitch + j];
+                const DICoef k = di_coef(xv, xj);
+                tj = di_tau(k, s.r);
+                c = di_J(k, tj);
+            } else {
+                float xj[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) xj[a] = X[(size_t)a * s.pitch + j];
+                c = INCOMING ? edge_cost<KIND, D>(s, xj, xv) : edge_cost<KIND, D>(s, xv, xj);
+            }
+            if (KIND == GMT_COST_DI) tau[base + t] = tj;
+            col[base + t] = j;
+            cost[base + t] = c;
+        }
+        base += total;
+        __syncwarp();
+    }
+}
+
+}  // namespace gmtk

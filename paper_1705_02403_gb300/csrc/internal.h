@@ -94,6 +94,20 @@ struct PlanArgs {
     int* list_open[2];
     int* list_cand;
     PlanCtl* ctl;
+    // Set by the batched path: the CSR may only be read if the edge count the
+    // build produced fits the slice that was filled (else GMT_ERR_OOM).
+    int check_edges;
+    long long edge_cap;
+};
+
+// Per-team scratch of the batched wavefront: team t uses the slices
+// [t * max_nodes, (t+1) * max_nodes) of ocost and stamp and
+// [t * 5 max_nodes, (t+1) * 5 max_nodes) of lists.
+struct BatchScratch {
+    float* ocost;
+    int* stamp;
+    int* lists;
+    int max_nodes;
 };
 
 // capi.cu: sets the message returned by gmt_last_error() on this host thread.
@@ -107,5 +121,12 @@ void record_error(const char* msg);
 cudaError_t launch_plan(const PlanArgs& a, int blocks, int threads, cudaStream_t st, int cluster = 0);
 int plan_max_coresident_blocks(int kind, int dp, int threads);
 int plan_max_cluster(int kind, int dp, int threads);
+// Persistent batched wavefront over `nq` queries of one (kind, dp) group, taken
+// in the order `order` from the device counter `next` (zeroed by the caller);
+// `slot` holds one int per team.  cluster <= 1: teams are single CTAs.
+cudaError_t launch_plan_batch(int kind, int dp, const PlanArgs* queries, const int* order, int nq, int* next,
+                              int* slot, const BatchScratch& scratch, int teams, int threads, int cluster,
+                              int max_boxes, cudaStream_t st);
+int plan_batch_max_teams(int kind, int dp, int threads, int cluster);
 
 }  // namespace gmtk

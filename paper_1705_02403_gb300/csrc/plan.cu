@@ -40,6 +40,7 @@ __device__ __forceinline__ unsigned ldcg_u(const unsigned* p) { return __ldcg(p)
 __device__ __forceinline__ float ldcg_f(const float* p) { return __ldcg(p); }
 
 struct BlockTeam {
+    __device__ __forceinline__ int id() const { return blockIdx.x; }
     __device__ __forceinline__ int rank() const { return threadIdx.x; }
     __device__ __forceinline__ int size() const { return blockDim.x; }
     __device__ __forceinline__ bool sync(PlanCtl*) const {
@@ -55,6 +56,7 @@ struct BlockTeam {
 struct GridTeam {
     unsigned expected;
     int spin_limit;
+    __device__ __forceinline__ int id() const { return 0; }
     __device__ __forceinline__ int rank() const { return blockIdx.x * blockDim.x + threadIdx.x; }
     __device__ __forceinline__ int size() const { return gridDim.x * blockDim.x; }
     __device__ bool sync(PlanCtl* ctl) const {
@@ -98,6 +100,7 @@ struct ClusterTeam {
         asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
         return n;
     }
+    __device__ __forceinline__ int id() const { return (int)(blockIdx.x / ctas()); }
     __device__ __forceinline__ int rank() const { return (int)(cta_rank() * blockDim.x + threadIdx.x); }
     __device__ __forceinline__ int size() const { return (int)(ctas() * blockDim.x); }
     __device__ __forceinline__ bool sync(PlanCtl*) const {
@@ -159,8 +162,7 @@ __host__ __device__ constexpr int smem_box_cap(int dp) { return 4096 / dp; }
 
 // ------------------------------------------------------------------- kernel
 template <class Team, int KIND, int DP>
-__global__ void __launch_bounds__(1024) plan_kernel(PlanArgs A, Team team) {
-    extern __shared__ float sbox[];
+__device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
     const int D = KIND == GMT_COST_DI ? 6 : DP;
     const int nbs = A.boxes.count <= smem_box_cap(DP) ? A.boxes.count : 0;
     for (int t = threadIdx.x; t < nbs * DP; t += blockDim.x) {
@@ -174,6 +176,16 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs A, Team team) {
 
     PlanCtl* ctl = A.ctl;
     const int rank = team.rank(), size = team.size();
+    if (A.check_edges) {
+        const long long e = max(__ldcg(&A.out_row[A.N]), __ldcg(&A.in_row[A.N]));
+        if (e > A.edge_cap) {  // uniform across the team: every thread reads the same counts
+            if (rank == 0) {
+                ctl->status = GMT_ERR_OOM;
+                ctl->goal_node = -1;
+            }
+            return;
+        }
+    }
     const int lane = threadIdx.x & 31;
     const int gwarp = rank >> 5, nwarps = size >> 5;
     const float INF = f_inf();
@@ -422,6 +434,42 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs A, Team team) {
     }
 }
 
+template <class Team, int KIND, int DP>
+__global__ void __launch_bounds__(1024) plan_kernel(PlanArgs A, Team team) {
+    extern __shared__ float sbox[];
+    plan_body<Team, KIND, DP>(A, team, sbox);
+}
+
+// Persistent batched wavefront: every team (a CTA, or a cluster) takes the next
+// query from a device queue (queries ordered by decreasing size), runs the
+// plan body on it with its own scratch slice, and repeats until the queue is
+// empty.  Queries never wait for each other, so teams need no co-scheduling
+// beyond their own CTAs.
+template <class Team, int KIND, int DP>
+__global__ void __launch_bounds__(1024) plan_batch_kernel(const PlanArgs* __restrict__ queries,
+                                                          const int* __restrict__ order, int nq,
+                                                          int* __restrict__ next, int* __restrict__ slot,
+                                                          BatchScratch scratch, Team team) {
+    extern __shared__ float sbox[];
+    const int team_id = team.id();
+    for (;;) {
+        if (team.rank() == 0) slot[team_id] = atomicAdd(next, 1);
+        team.sync(nullptr);
+        const int k = __ldcg(&slot[team_id]);
+        if (k >= nq) break;
+        PlanArgs A = queries[order[k]];
+        const size_t nm = (size_t)scratch.max_nodes;
+        A.ocost = scratch.ocost + team_id * nm;
+        A.stamp = scratch.stamp + team_id * nm;
+        int* lists = scratch.lists + team_id * 5 * nm;
+        A.list_g[0] = lists; A.list_g[1] = lists + nm;
+        A.list_open[0] = lists + 2 * nm; A.list_open[1] = lists + 3 * nm;
+        A.list_cand = lists + 4 * nm;
+        plan_body<Team, KIND, DP>(A, team, sbox);
+        team.sync(nullptr);
+    }
+}
+
 // ----------------------------------------------------------------- launcher
 namespace {
 template <int KIND, int DP>
@@ -509,6 +557,91 @@ int plan_max_cluster(int kind, int dp, int threads) {
         if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0) return c;
     }
     cudaGetLastError();
+    return 0;
+}
+
+namespace {
+template <int KIND, int DP>
+cudaError_t plan_batch_t(const PlanArgs* queries, const int* order, int nq, int* next, int* slot,
+                         const BatchScratch& scratch, int teams, int threads, int cluster, int max_boxes,
+                         cudaStream_t st) {
+    const int nbs = max_boxes <= smem_box_cap(DP) ? max_boxes : 0;
+    const size_t smem = (size_t)2 * nbs * DP * sizeof(float);
+    if (cluster <= 1) {
+        plan_batch_kernel<BlockTeam, KIND, DP><<<teams, threads, smem, st>>>(queries, order, nq, next, slot,
+                                                                             scratch, BlockTeam{});
+        return cudaGetLastError();
+    }
+    auto kern = plan_batch_kernel<ClusterTeam, KIND, DP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(teams * cluster);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, queries, order, nq, next, slot, scratch, ClusterTeam{});
+}
+
+template <int KIND, int DP>
+int batch_teams_t(int threads, int cluster) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = (size_t)2 * smem_box_cap(DP) * DP * sizeof(float);
+    if (cluster <= 1) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_batch_kernel<BlockTeam, KIND, DP>, threads, smem);
+        return per_sm * sms;
+    }
+    auto kern = plan_batch_kernel<ClusterTeam, KIND, DP>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+}  // namespace
+
+// The batched path supports the double integrator and 2D/3D geometric queries.
+cudaError_t launch_plan_batch(int kind, int dp, const PlanArgs* queries, const int* order, int nq, int* next,
+                              int* slot, const BatchScratch& scratch, int teams, int threads, int cluster,
+                              int max_boxes, cudaStream_t st) {
+    if (kind == GMT_COST_DI)
+        return plan_batch_t<GMT_COST_DI, 3>(queries, order, nq, next, slot, scratch, teams, threads, cluster, max_boxes, st);
+    if (dp == 2)
+        return plan_batch_t<GMT_COST_EUCLID, 2>(queries, order, nq, next, slot, scratch, teams, threads, cluster,
+                                                max_boxes, st);
+    if (dp == 3)
+        return plan_batch_t<GMT_COST_EUCLID, 3>(queries, order, nq, next, slot, scratch, teams, threads, cluster,
+                                                max_boxes, st);
+    return cudaErrorInvalidValue;
+}
+
+int plan_batch_max_teams(int kind, int dp, int threads, int cluster) {
+    if (kind == GMT_COST_DI) return batch_teams_t<GMT_COST_DI, 3>(threads, cluster);
+    if (dp == 2) return batch_teams_t<GMT_COST_EUCLID, 2>(threads, cluster);
+    if (dp == 3) return batch_teams_t<GMT_COST_EUCLID, 3>(threads, cluster);
     return 0;
 }
 

@@ -114,3 +114,50 @@ class Planner:
         info = N.gmt_plan(self.graph, self.boxes, params, self.parent.data_ptr(), self.cost.data_ptr(),
                           self.path.data_ptr(), stream, allow_errors=allow_errors)
         return info.as_dict()
+
+
+class BatchPlanner:
+    """A batch of problems planned with gmt_plan_batch (one handle, reusable)."""
+
+    def __init__(self, problems, device="cuda"):
+        self.problems = list(problems)
+        self.device = device
+        self._keep = []
+        self.queries = (N.gmt_query * len(self.problems))()
+        for k, pb in enumerate(self.problems):
+            qd = self.queries[k]
+            qd.space = space_struct(pb)
+            b, tens = boxes_on_device(pb, device)
+            self._keep.append(tens)
+            qd.boxes = b
+            for a in range(pb.d):
+                qd.x_init[a] = float(pb.x_init[a])
+            qd.goal = goal_struct(pb)
+            qd.params = params_struct(pb)
+        self.offsets = np.concatenate([[0], np.cumsum([pb.N for pb in self.problems])]).astype(np.int64)
+        total = int(self.offsets[-1])
+        self.parent = torch.empty(total, dtype=torch.int32, device=device)
+        self.cost = torch.empty(total, dtype=torch.float32, device=device)
+        self.batch = N.Batch()
+
+    def plan(self, stream=None, allow_errors=False):
+        return N.gmt_plan_batch(self.queries, self.batch, self.parent.data_ptr(), self.cost.data_ptr(), stream,
+                                allow_errors)
+
+    def result(self, k):
+        a, b = int(self.offsets[k]), int(self.offsets[k + 1])
+        return self.parent[a:b], self.cost[a:b]
+
+    def view(self, k):
+        v, path_ptr = N.gmt_batch_get_view(self.batch, k)
+        out = {"N": v.N, "E": v.E, "r": v.r,
+               "X": wrap_device(v.X, (v.dim, v.x_pitch), "f4", self.batch)[:, :v.N],
+               "is_goal": wrap_device(v.is_goal, (v.N,), "u1", self.batch),
+               "out_row": wrap_device(v.out_row, (v.N + 1,), "i4", self.batch),
+               "out_col": wrap_device(v.out_col, (v.E,), "i4", self.batch),
+               "out_cost": wrap_device(v.out_cost, (v.E,), "f4", self.batch),
+               "in_row": wrap_device(v.in_row, (v.N + 1,), "i4", self.batch),
+               "in_col": wrap_device(v.in_col, (v.E,), "i4", self.batch),
+               "in_cost": wrap_device(v.in_cost, (v.E,), "f4", self.batch),
+               "path": wrap_device(path_ptr, (v.N,), "i4", self.batch)}
+        return out
