@@ -240,6 +240,22 @@ gmt_status gmt_batch_autotune(gmt_batch* batch, gmt_stream stream, int32_t* best
 
 void gmt_batch_free(gmt_batch* batch);
 
+/* ---------------------------------------------------------------- tensor cores
+ * BF16 GEMM on the 5th-generation tensor cores (tcgen05, TMEM accumulator,
+ * TMA loads), the building block of the learned sampling proposal:
+ *   C[M, N] = A[M, K] . B[N, K]^T, FP32 accumulation.
+ * A, B: DEVICE BF16 row-major, 16-byte aligned, K % 8 == 0.
+ * epilogue 0: C (DEVICE FP32 [M, N]) = A.B^T;
+ *          1: C_bf16 (DEVICE BF16 [M, N]) = bf16(relu(A.B^T + bias));
+ *          2: C = A.B^T + bias.   bias: DEVICE FP32 [N] or NULL.
+ * splits > 1 divides K among CTAs (split-K) and needs `workspace` (DEVICE FP32
+ * [splits * M * N]); partial sums are reduced in a fixed order.
+ * error_flag: DEVICE int, set to 1 if a bounded device wait ran out (the
+ * output is then undefined); the caller zeroes it.  Asynchronous on `stream`. */
+gmt_status gmt_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const void* B, int32_t epilogue,
+                         const float* bias, float* C, void* C_bf16, int32_t splits, float* workspace,
+                         int32_t* error_flag, gmt_stream stream);
+
 /* Allocation-free planning (an implementation entry point; the paper has no
  * counterpart).  Runs the same wavefront kernel as gmt_plan, for callers that
  * must not allocate device memory while they plan: a replanning loop inside a

@@ -102,6 +102,7 @@ SIGNATURES = {
     "gmt_batch_set_launch": (_I32, [_P, _I32, _I32]),
     "gmt_batch_autotune": (_I32, [_P, _P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_F32)]),
     "gmt_batch_free": (None, [_P]),
+    "gmt_gemm_bf16": (_I32, [_I32, _I32, _I32, _P, _P, _I32, _P, _P, _P, _I32, _P, _P, _P]),
     "gmt_connection_radius": (_F64, [_I32, _I32, _F64, _F64]),
     "gmt_last_error": (C.c_char_p, []),
 }
@@ -255,3 +256,20 @@ def gmt_batch_autotune(batch: Batch, stream=None):
     c, t, ms = C.c_int32(), C.c_int32(), C.c_float()
     _check(lib.gmt_batch_autotune(batch.handle, _stream(stream), C.byref(c), C.byref(t), C.byref(ms)))
     return c.value, t.value, ms.value
+
+
+def gmt_gemm_bf16(A, B, epilogue=0, bias=None, splits=1, stream=None):
+    """C = A . B^T on the tensor cores (A [M,K], B [N,K] torch bf16 CUDA tensors)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    dev = A.device
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    C = torch.empty(M, N, dtype=torch.float32, device=dev) if epilogue != 1 else None
+    Cb = torch.empty(M, N, dtype=torch.bfloat16, device=dev) if epilogue == 1 else None
+    ws = torch.empty(splits * M * N, dtype=torch.float32, device=dev) if splits > 1 else None
+    _check(lib.gmt_gemm_bf16(M, N, K, A.data_ptr(), B.data_ptr(), epilogue,
+                             bias.data_ptr() if bias is not None else None,
+                             C.data_ptr() if C is not None else None, Cb.data_ptr() if Cb is not None else None,
+                             splits, ws.data_ptr() if ws is not None else None, err.data_ptr(), _stream(stream)))
+    return (C if epilogue != 1 else Cb), err
