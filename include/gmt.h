@@ -148,6 +148,16 @@ gmt_status gmt_build_graph(const gmt_space* space, const gmt_boxes* boxes, const
                            const gmt_goal* goal, const gmt_params* params, gmt_graph** graph,
                            gmt_stream stream);
 
+/* As gmt_build_graph, with `extra_count` caller samples appended after the
+ * n + 1 SampleFree nodes (nodes n+1 .. n+extra_count), e.g. the learned
+ * proposal's (gmt_propose).  extra: DEVICE [dim][extra_pitch].  Appended
+ * samples must lie in X and outside X_obs (else GMT_ERR_INVALID).  Supported
+ * for geometric dim <= 3 and the double integrator.  The radius is params->r
+ * (or Theorem 1's for params->n when r <= 0). */
+gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, const float* x_init,
+                              const gmt_goal* goal, const gmt_params* params, const float* extra,
+                              int32_t extra_count, int32_t extra_pitch, gmt_graph** graph, gmt_stream stream);
+
 gmt_status gmt_graph_get_view(const gmt_graph* graph, gmt_graph_view* view);
 void gmt_graph_free(gmt_graph* graph);
 
@@ -239,6 +249,81 @@ gmt_status gmt_batch_autotune(gmt_batch* batch, gmt_stream stream, int32_t* best
                               float* best_ms);
 
 void gmt_batch_free(gmt_batch* batch);
+
+/* ---------------------------------------------------------------- learned proposal
+ * An extension beyond the paper (which samples uniformly or with Halton
+ * points): an MLP maps a G^3 voxel occupancy grid of the obstacles plus start
+ * and goal to logits over C^3 coarse cells of the position space:
+ *   H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2), Z = [H2, start, goal, 0],
+ *   logits = Z W3^T + b3   (X [B, G^3], H1/H2 [B, hidden], Z [B, hidden+16]).
+ * Forward and backward run on the tcgen05 BF16 GEMM (FP32 accumulation);
+ * training minimises the softmax cross-entropy against a target distribution
+ * over cells with AdamW on FP32 master weights. */
+typedef struct {
+    int32_t grid;       /* G: voxels per axis (32) */
+    int32_t hidden;     /* hidden width (512), multiple of 64 */
+    int32_t cells;      /* C: coarse cells per axis (16 -> 4096 logits) */
+    int32_t max_batch;  /* largest batch of environments per call */
+    uint64_t seed;      /* Philox key of the initial weights */
+} gmt_model_config;
+
+typedef struct gmt_model gmt_model;
+
+/* DEVICE pointers into a model (parameters FP32 row-major [out][in], their
+ * BF16 copies, the last gradients, logits [B][cells^3] and per-environment
+ * losses of the last forward/backward). */
+typedef struct {
+    int32_t grid, hidden, cells, in_features, z_features, n_cells, max_batch;
+    int64_t step;
+    const float *W1, *b1, *W2, *b2, *W3, *b3;
+    const float *gW1, *gb1, *gW2, *gb2, *gW3, *gb3;
+    const void *W1_bf16, *W2_bf16, *W3_bf16;
+    const float* logits;
+    const float* loss;
+} gmt_model_view;
+
+gmt_status gmt_model_create(const gmt_model_config* config, gmt_model** model);
+void gmt_model_free(gmt_model* model);
+gmt_status gmt_model_get_view(const gmt_model* model, gmt_model_view* view);
+
+/* Voxel occupancy of B environments: voxel (i, j, k) of [0,1]^3 is 1 if its
+ * centre ((i+.5)/G, (j+.5)/G, (k+.5)/G) lies in a box.  boxes: HOST array [B]
+ * (box arrays DEVICE, 3D).  voxels: DEVICE BF16 [B][G^3], index (i G + j) G + k.
+ * Synchronises `stream`. */
+gmt_status gmt_voxelize(int32_t B, const gmt_boxes* boxes, int32_t grid, void* voxels, gmt_stream stream);
+
+/* Forward pass.  voxels: DEVICE BF16 [B][G^3]; start_goal: DEVICE FP32 [B][6];
+ * logits: DEVICE FP32 [B][C^3] or NULL (then read them through the view). */
+gmt_status gmt_model_forward(gmt_model* model, int32_t B, const void* voxels, const float* start_goal,
+                             float* logits, gmt_stream stream);
+/* Forward + backward (gradients into the model, no update).  target: DEVICE
+ * FP32 [B][C^3], rows summing to 1.  mean_loss: HOST, may be NULL. */
+gmt_status gmt_model_backward(gmt_model* model, int32_t B, const void* voxels, const float* start_goal,
+                              const float* target, float* mean_loss, gmt_stream stream);
+/* Forward + backward + one AdamW step (beta 0.9/0.999, eps 1e-8; decay on the
+ * weight matrices only).  Synchronises `stream`. */
+gmt_status gmt_model_train_step(gmt_model* model, int32_t B, const void* voxels, const float* start_goal,
+                                const float* target, float lr, float weight_decay, float* mean_loss,
+                                gmt_stream stream);
+/* Checkpoint: weights, Adam moments, step count and seed in one binary file. */
+gmt_status gmt_model_save(const gmt_model* model, const char* path);
+gmt_status gmt_model_load(gmt_model* model, const char* path);
+
+/* Training target: histogram over C^3 cells of points every `spacing` along
+ * the path (sample indices, DEVICE [len]) through samples X (DEVICE
+ * [>=3][pitch], first three coordinates = position in [0,1]^3), plus eps in
+ * every cell, normalised to sum 1.  hist: DEVICE FP32 [C^3]. */
+gmt_status gmt_path_histogram(const float* X, int32_t pitch, const int32_t* path, int32_t len, int32_t cells,
+                              float spacing, float eps, float* hist, gmt_stream stream);
+
+/* Learned samples for one 3D geometric problem: one forward pass on the
+ * voxelised boxes with start/goal (HOST [3] each), then `count` draws: a cell
+ * from the softmax (inverse CDF), a uniform point inside it (Philox4x32-10,
+ * counter (sample, attempt, 2, 0), key = seed), rejected while it lies in a
+ * box.  samples: DEVICE [3][pitch].  Synchronises `stream`. */
+gmt_status gmt_propose(gmt_model* model, const gmt_space* space, const gmt_boxes* boxes, const float* start,
+                       const float* goal, int32_t count, uint64_t seed, float* samples, int32_t pitch,
+                       gmt_stream stream);
 
 /* ---------------------------------------------------------------- tensor cores
  * BF16 GEMM on the 5th-generation tensor cores (tcgen05, TMEM accumulator,

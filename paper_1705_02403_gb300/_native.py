@@ -83,6 +83,22 @@ class gmt_query(C.Structure):
                 ("goal", gmt_goal), ("params", gmt_params)]
 
 
+class gmt_model_config(C.Structure):
+    _fields_ = [("grid", C.c_int32), ("hidden", C.c_int32), ("cells", C.c_int32), ("max_batch", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
+class gmt_model_view(C.Structure):
+    _fields_ = [("grid", C.c_int32), ("hidden", C.c_int32), ("cells", C.c_int32), ("in_features", C.c_int32),
+                ("z_features", C.c_int32), ("n_cells", C.c_int32), ("max_batch", C.c_int32), ("step", C.c_int64),
+                ("W1", C.c_void_p), ("b1", C.c_void_p), ("W2", C.c_void_p), ("b2", C.c_void_p),
+                ("W3", C.c_void_p), ("b3", C.c_void_p),
+                ("gW1", C.c_void_p), ("gb1", C.c_void_p), ("gW2", C.c_void_p), ("gb2", C.c_void_p),
+                ("gW3", C.c_void_p), ("gb3", C.c_void_p),
+                ("W1_bf16", C.c_void_p), ("W2_bf16", C.c_void_p), ("W3_bf16", C.c_void_p),
+                ("logits", C.c_void_p), ("loss", C.c_void_p)]
+
+
 # Every symbol include/gmt.h declares, with its ctypes signature.
 _P, _I32, _I64, _F32, _F64, _U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double, C.c_uint64
 SIGNATURES = {
@@ -103,6 +119,19 @@ SIGNATURES = {
     "gmt_batch_autotune": (_I32, [_P, _P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_F32)]),
     "gmt_batch_free": (None, [_P]),
     "gmt_gemm_bf16": (_I32, [_I32, _I32, _I32, _P, _P, _I32, _P, _P, _P, _I32, _P, _P, _P]),
+    "gmt_build_graph_ex": (_I32, [C.POINTER(gmt_space), C.POINTER(gmt_boxes), _P, C.POINTER(gmt_goal),
+                                  C.POINTER(gmt_params), _P, _I32, _I32, C.POINTER(C.c_void_p), _P]),
+    "gmt_model_create": (_I32, [C.POINTER(gmt_model_config), C.POINTER(C.c_void_p)]),
+    "gmt_model_free": (None, [_P]),
+    "gmt_model_get_view": (_I32, [_P, C.POINTER(gmt_model_view)]),
+    "gmt_voxelize": (_I32, [_I32, C.POINTER(gmt_boxes), _I32, _P, _P]),
+    "gmt_model_forward": (_I32, [_P, _I32, _P, _P, _P, _P]),
+    "gmt_model_backward": (_I32, [_P, _I32, _P, _P, _P, C.POINTER(_F32), _P]),
+    "gmt_model_train_step": (_I32, [_P, _I32, _P, _P, _P, _F32, _F32, C.POINTER(_F32), _P]),
+    "gmt_model_save": (_I32, [_P, C.c_char_p]),
+    "gmt_model_load": (_I32, [_P, C.c_char_p]),
+    "gmt_path_histogram": (_I32, [_P, _I32, _P, _I32, _I32, _F32, _F32, _P, _P]),
+    "gmt_propose": (_I32, [_P, C.POINTER(gmt_space), C.POINTER(gmt_boxes), _P, _P, _I32, _U64, _P, _I32, _P]),
     "gmt_connection_radius": (_F64, [_I32, _I32, _F64, _F64]),
     "gmt_last_error": (C.c_char_p, []),
 }
@@ -273,3 +302,72 @@ def gmt_gemm_bf16(A, B, epilogue=0, bias=None, splits=1, stream=None):
                              C.data_ptr() if C is not None else None, Cb.data_ptr() if Cb is not None else None,
                              splits, ws.data_ptr() if ws is not None else None, err.data_ptr(), _stream(stream)))
     return (C if epilogue != 1 else Cb), err
+
+
+class Model:
+    """Owner of a gmt_model handle."""
+
+    def __init__(self, grid=32, hidden=512, cells=16, max_batch=256, seed=1):
+        cfg = gmt_model_config(grid, hidden, cells, max_batch, seed)
+        self.handle = C.c_void_p(None)
+        _check(lib.gmt_model_create(C.byref(cfg), C.byref(self.handle)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib.gmt_model_free(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def view(self) -> gmt_model_view:
+        v = gmt_model_view()
+        _check(lib.gmt_model_get_view(self.handle, C.byref(v)))
+        return v
+
+    def forward(self, B, voxels_ptr, sg_ptr, logits_ptr=None, stream=None):
+        _check(lib.gmt_model_forward(self.handle, B, C.c_void_p(voxels_ptr), C.c_void_p(sg_ptr),
+                                     C.c_void_p(logits_ptr or 0), _stream(stream)))
+
+    def backward(self, B, voxels_ptr, sg_ptr, target_ptr, stream=None):
+        loss = C.c_float()
+        _check(lib.gmt_model_backward(self.handle, B, C.c_void_p(voxels_ptr), C.c_void_p(sg_ptr),
+                                      C.c_void_p(target_ptr), C.byref(loss), _stream(stream)))
+        return loss.value
+
+    def train_step(self, B, voxels_ptr, sg_ptr, target_ptr, lr, weight_decay=0.0, stream=None):
+        loss = C.c_float()
+        _check(lib.gmt_model_train_step(self.handle, B, C.c_void_p(voxels_ptr), C.c_void_p(sg_ptr),
+                                        C.c_void_p(target_ptr), lr, weight_decay, C.byref(loss), _stream(stream)))
+        return loss.value
+
+    def save(self, path):
+        _check(lib.gmt_model_save(self.handle, path.encode()))
+
+    def load(self, path):
+        _check(lib.gmt_model_load(self.handle, path.encode()))
+
+
+def gmt_voxelize(boxes_list, grid, voxels_ptr, stream=None):
+    arr = (gmt_boxes * len(boxes_list))(*boxes_list)
+    _check(lib.gmt_voxelize(len(boxes_list), arr, grid, C.c_void_p(voxels_ptr), _stream(stream)))
+
+
+def gmt_path_histogram(X_ptr, pitch, path_ptr, length, cells, spacing, eps, hist_ptr, stream=None):
+    _check(lib.gmt_path_histogram(C.c_void_p(X_ptr), pitch, C.c_void_p(path_ptr), length, cells, spacing, eps,
+                                  C.c_void_p(hist_ptr), _stream(stream)))
+
+
+def gmt_propose(model: Model, space: gmt_space, boxes: gmt_boxes, start, goal, count, seed, samples_ptr, pitch,
+                stream=None):
+    s3 = (C.c_float * 3)(*[float(v) for v in start[:3]])
+    g3 = (C.c_float * 3)(*[float(v) for v in goal[:3]])
+    _check(lib.gmt_propose(model.handle, C.byref(space), C.byref(boxes), C.cast(s3, C.c_void_p),
+                           C.cast(g3, C.c_void_p), count, seed, C.c_void_p(samples_ptr), pitch, _stream(stream)))
+
+
+def gmt_build_graph_ex(space, boxes, x_init, goal, params, extra_ptr, extra_count, extra_pitch,
+                       graph: Graph | None = None, stream=None) -> Graph:
+    g = graph if graph is not None else Graph()
+    xi = (C.c_float * GMT_MAX_DIM)(*[float(v) for v in x_init])
+    _check(lib.gmt_build_graph_ex(C.byref(space), C.byref(boxes), C.cast(xi, C.c_void_p), C.byref(goal),
+                                  C.byref(params), C.c_void_p(extra_ptr or 0), extra_count, extra_pitch,
+                                  C.byref(g.handle), _stream(stream)))
+    return g

@@ -441,6 +441,7 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         std::memset(&d, 0, sizeof(d));
         SpaceArgs& s = d.s;
         s.kind = Qh.space.kind; s.d = Qh.space.dim; s.dp = Qh.space.pos_dim; s.N = b->N[k]; s.pitch = b->pitch[k];
+        s.n_sampled = s.N;
         for (int a = 0; a < s.d; ++a) {
             s.lo[a] = Qh.space.lo[a]; s.hi[a] = Qh.space.hi[a];
             s.x0[a] = Qh.x_init[a]; s.gc[a] = Qh.goal.center[a];

@@ -179,7 +179,17 @@ double gmt_connection_radius(int32_t n, int32_t d, double eta, double mu_free) {
 
 gmt_status gmt_build_graph(const gmt_space* space, const gmt_boxes* boxes, const float* x_init, const gmt_goal* goal,
                            const gmt_params* params, gmt_graph** graph, gmt_stream stream) {
+    return gmt_build_graph_ex(space, boxes, x_init, goal, params, nullptr, 0, 0, graph, stream);
+}
+
+gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, const float* x_init,
+                              const gmt_goal* goal, const gmt_params* params, const float* extra, int32_t extra_count,
+                              int32_t extra_pitch, gmt_graph** graph, gmt_stream stream) {
     gmt_status s;
+    if (extra_count < 0 || (extra_count > 0 && (!extra || extra_pitch < extra_count)))
+        return fail(GMT_ERR_INVALID, "extra samples need a DEVICE array [dim][extra_pitch], extra_pitch >= count");
+    if (extra_count > 0 && space && space->kind == GMT_COST_EUCLID && space->dim > 3)
+        return fail(GMT_ERR_INVALID, "appended samples are supported for dim <= 3 and the double integrator");
     if ((s = check_space(space)) != GMT_OK) return s;
     if ((s = check_boxes(boxes)) != GMT_OK) return s;
     if ((s = check_params(params, space->dim)) != GMT_OK) return s;
@@ -197,7 +207,8 @@ gmt_status gmt_build_graph(const gmt_space* space, const gmt_boxes* boxes, const
     g->kind = space->kind;
     g->d = space->dim;
     g->dp = space->pos_dim;
-    g->N = params->n + 1;
+    const int n_sampled = params->n + 1;
+    g->N = n_sampled + extra_count;
     g->pitch = (g->N + 31) / 32 * 32;
     g->r = resolve_radius(params, space->dim);
     g->E = 0;
@@ -207,6 +218,7 @@ gmt_status gmt_build_graph(const gmt_space* space, const gmt_boxes* boxes, const
     SpaceArgs sa;
     std::memset(&sa, 0, sizeof(sa));
     sa.kind = g->kind; sa.d = g->d; sa.dp = g->dp; sa.N = g->N; sa.pitch = g->pitch;
+    sa.n_sampled = n_sampled;
     for (int a = 0; a < g->d; ++a) {
         sa.lo[a] = space->lo[a]; sa.hi[a] = space->hi[a];
         sa.x0[a] = x_init[a]; sa.gc[a] = goal->center[a];
@@ -250,6 +262,8 @@ gmt_status gmt_build_graph(const gmt_space* space, const gmt_boxes* boxes, const
     if (g->kind == GMT_COST_DI) LAUNCH(cudaMemsetAsync(g->in_count, 0, N * sizeof(int), st), "memset");
     LAUNCH(g->mark(gmt_graph::kSample, 0, st), "event");
     LAUNCH(launch_sample(sa, ba, g->X, g->is_goal, g->flags, st), "sample kernel");
+    LAUNCH(launch_append(sa, ba, extra, extra_pitch, n_sampled, extra_count, g->X, g->is_goal, g->flags, st),
+           "append kernel");
     LAUNCH(g->mark(gmt_graph::kSample, 1, st), "event");
     LAUNCH(g->mark(gmt_graph::kPair, 0, st), "event");
     LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, st), "pair filter kernel");
@@ -271,6 +285,7 @@ gmt_status gmt_build_graph(const gmt_space* space, const gmt_boxes* boxes, const
     if (flags & kSampleBadInit) return bail(fail(GMT_ERR_INVALID, "x_init is outside X or inside an obstacle"));
     if (flags & kSampleExhausted)
         return bail(fail(GMT_ERR_INVALID, "a sample exhausted max_attempts (X_free or X_goal n X_free too small)"));
+    if (flags & kSampleBadAppend) return bail(fail(GMT_ERR_INVALID, "an appended sample is outside X or in X_obs"));
     g->E = g->h_scalars[1];
     const size_t E = (size_t)g->E;
     GROW(out_col, E);

@@ -26,6 +26,14 @@ __global__ void __launch_bounds__(128) sample_kernel(SpaceArgs s, BoxArgs boxes,
     sample_node<D, DP>(s, boxes, X, is_goal, flags, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+template <int D, int DP>
+__global__ void __launch_bounds__(128) append_kernel(SpaceArgs s, BoxArgs boxes, const float* __restrict__ src,
+                                                     int src_pitch, int first, int count, float* __restrict__ X,
+                                                     uint8_t* __restrict__ is_goal, int* __restrict__ flags) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count) append_node<D, DP>(s, boxes, src, src_pitch, first, X, is_goal, flags, k);
+}
+
 template <int KIND, int D>
 __global__ void __launch_bounds__(kMaskRows) pair_mask_kernel(SpaceArgs s, const float* __restrict__ X,
                                                               uint32_t* __restrict__ mask,
@@ -118,6 +126,17 @@ cudaError_t launch_sample(const SpaceArgs& s, BoxArgs b, float* X, uint8_t* g, i
         case 10: return sample_t<10, 10>(s, b, X, g, f, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_append(const SpaceArgs& s, BoxArgs b, const float* src, int src_pitch, int first, int count,
+                          float* X, uint8_t* g, int* f, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((count + 127) / 128);
+    if (s.kind == GMT_COST_DI) append_kernel<6, 3><<<blocks, 128, 0, st>>>(s, b, src, src_pitch, first, count, X, g, f);
+    else if (s.d == 2) append_kernel<2, 2><<<blocks, 128, 0, st>>>(s, b, src, src_pitch, first, count, X, g, f);
+    else if (s.d == 3) append_kernel<3, 3><<<blocks, 128, 0, st>>>(s, b, src, src_pitch, first, count, X, g, f);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* cnt, cudaStream_t st) {

@@ -22,7 +22,7 @@ __device__ __forceinline__ bool in_goal_ball(const float* x, int gd, const float
 template <int D, int DP>
 __device__ __forceinline__ void sample_node(const SpaceArgs& s, const BoxArgs& boxes, float* __restrict__ X,
                                             uint8_t* __restrict__ is_goal, int* __restrict__ flags, int k) {
-    if (k >= s.N) return;
+    if (k >= s.n_sampled) return;
     float x[D];
     if (k == 0) {
         bool ok = true;
@@ -62,6 +62,24 @@ __device__ __forceinline__ void sample_node(const SpaceArgs& s, const BoxArgs& b
 #pragma unroll
     for (int a = 0; a < D; ++a) X[(size_t)a * s.pitch + k] = x[a];
     is_goal[k] = in_goal_ball(x, s.gd, s.gc, s.grho) ? 1 : 0;
+}
+
+// Appended sample k (one thread): copy, goal flag, validity (inside X, outside
+// every box).
+template <int D, int DP>
+__device__ __forceinline__ void append_node(const SpaceArgs& s, const BoxArgs& boxes, const float* __restrict__ src,
+                                            int src_pitch, int first, float* __restrict__ X,
+                                            uint8_t* __restrict__ is_goal, int* __restrict__ flags, int k) {
+    float x[D];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        x[a] = src[(size_t)a * src_pitch + k];
+        ok = ok && s.lo[a] <= x[a] && x[a] <= s.hi[a];
+        X[(size_t)a * s.pitch + first + k] = x[a];
+    }
+    if (!ok || in_any_box<DP>(x, boxes.lo, boxes.hi, boxes.count)) atomicOr(flags, kSampleBadAppend);
+    is_goal[first + k] = in_goal_ball(x, s.gd, s.gc, s.grho) ? 1 : 0;
 }
 
 // ------------------------------------------------------------- pair filter

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "gmt.h"
@@ -13,7 +14,8 @@ constexpr int kMaxDimHost = GMT_MAX_DIM;
 // Problem description passed by value to the sampling and graph kernels.
 struct SpaceArgs {
     int kind, d, dp;
-    int N;        // n + 1 nodes
+    int N;        // nodes of the graph
+    int n_sampled;  // nodes 0 .. n_sampled-1 are drawn by SampleFree; the rest are appended samples
     int pitch;    // row pitch of X and of the neighbour bit matrix (N rounded up to 32)
     float lo[kMaxDimHost], hi[kMaxDimHost];
     float x0[kMaxDimHost];
@@ -33,7 +35,7 @@ struct BoxArgs {
 };
 
 // Flags written by the sampling kernel.
-enum { kSampleBadInit = 1, kSampleExhausted = 2 };
+enum { kSampleBadInit = 1, kSampleExhausted = 2, kSampleBadAppend = 4 };
 
 // sample.cu / graph.cu
 cudaError_t launch_sample(const SpaceArgs& s, BoxArgs boxes, float* X, uint8_t* is_goal, int* flags,
@@ -109,6 +111,18 @@ struct BatchScratch {
     int* lists;
     int max_nodes;
 };
+
+// mlp.cu: C = A . B^T on the tensor cores (BF16 in, FP32 accumulate);
+// epilogue 0 = FP32 store, 1 = BF16 relu(x + bias), 2 = FP32 x + bias.
+cudaError_t gemm_bf16_tn(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, int epilogue,
+                         const float* bias, float* C, __nv_bfloat16* Cb, int ldc, int splits, float* partial,
+                         int* error, cudaStream_t st);
+
+// graph.cu: copies `count` appended samples (DEVICE [d][src_pitch]) into X
+// columns first.. and computes their goal flags; sets flags kSampleBadAppend
+// for a sample outside X or inside a box.
+cudaError_t launch_append(const SpaceArgs& s, BoxArgs boxes, const float* src, int src_pitch, int first, int count,
+                          float* X, uint8_t* is_goal, int* flags, cudaStream_t st);
 
 // capi.cu: sets the message returned by gmt_last_error() on this host thread.
 void record_error(const char* msg);

@@ -1,0 +1,204 @@
+"""Learned sampling proposal: data from plain GMT* solutions, training, and
+evaluation of the 50/50 mixture (learned + uniform) against uniform sampling.
+
+All computation runs in libgmt.so (batched planner, voxeliser, path
+histograms, tcgen05 forward/backward, AdamW, proposal sampler); this module
+sequences the calls and keeps the tensors.
+
+Mixture rule: a plan with n samples draws n/2 with SampleFree (uniform, node 1
+in the goal) and n/2 from the proposal; the connection radius is Theorem 1's
+for the n/2 uniform samples alone, so the uniform half keeps the paper's
+guarantee (Theorem 3 needs only the uniform samples and that radius).
+
+    python -m paper_1705_02403_gb300.learned --train-envs 10000 --test-envs 1000 --out learned.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import _native as N
+from . import envgen
+from .planner import BatchPlanner, boxes_on_device, goal_struct, params_struct, space_struct
+
+GRID, HIDDEN, CELLS = 32, 512, 16
+
+
+def env(seed: int, n: int, nbox: int = 30) -> envgen.Problem:
+    """3D box environment with its own start (near the origin corner) and goal
+    ball (near the opposite corner); r = 0 selects Theorem 1's radius."""
+    rng = np.random.default_rng([seed, 1705, 4])
+    x0 = rng.uniform(0.02, 0.25, 3)
+    gc = rng.uniform(0.75, 0.98, 3)
+    bl, bh = envgen.random_boxes(rng, nbox, 3, x0, gc, 0.05, side=(0.05, 0.3))
+    return envgen.Problem(kind=envgen.EUCLID, d=3, dp=3, lo=np.zeros(3, np.float32), hi=np.ones(3, np.float32),
+                          box_lo=bl, box_hi=bh, x_init=x0.astype(np.float32), goal_center=gc.astype(np.float32),
+                          goal_radius=0.05, goal_pos_only=False, n=n, r=0.0, lam=0.5, seed=seed, tag="learned3d")
+
+
+def start_goal(pbs):
+    return torch.tensor(np.stack([np.concatenate([pb.x_init[:3], pb.goal_center[:3]]) for pb in pbs]),
+                        dtype=torch.float32, device="cuda")
+
+
+def voxelize(pbs):
+    X = torch.empty(len(pbs), GRID ** 3, dtype=torch.bfloat16, device="cuda")
+    keep = [boxes_on_device(pb) for pb in pbs]
+    N.gmt_voxelize([k[0] for k in keep], GRID, X.data_ptr())
+    return X
+
+
+def generate_dataset(seeds, n=16384, chunk=256, log=print):
+    """Plain GMT* on every environment; targets = path histograms over cells."""
+    Xs, SGs, Ts, kept = [], [], [], []
+    t0 = time.time()
+    for c in range(0, len(seeds), chunk):
+        pbs = [env(s, n) for s in seeds[c:c + chunk]]
+        bp = BatchPlanner(pbs)
+        infos = bp.plan()
+        ok = [k for k, i in enumerate(infos) if i["status"] == 0]
+        T = torch.empty(len(ok), CELLS ** 3, dtype=torch.float32, device="cuda")
+        for row, k in enumerate(ok):
+            v = bp.view(k)
+            N.gmt_path_histogram(v["X"].data_ptr(), v["X"].stride(0), v["path"].data_ptr(), infos[k]["path_len"],
+                                 CELLS, 0.01, 1e-4, T[row].data_ptr())
+        sel = [pbs[k] for k in ok]
+        Xs.append(voxelize(sel))
+        SGs.append(start_goal(sel))
+        Ts.append(T)
+        kept += [seeds[c + k] for k in ok]
+        del bp
+        if log:
+            log(f"  dataset {c + len(pbs)}/{len(seeds)} solved {len(kept)} ({time.time() - t0:.1f}s)")
+    return torch.cat(Xs), torch.cat(SGs), torch.cat(Ts), kept
+
+
+def train(model: N.Model, X, SG, T, epochs=20, batch=256, lr=1e-3, wd=1e-4, seed=0, log=print):
+    n = X.shape[0]
+    g = torch.Generator().manual_seed(seed)
+    losses = []
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=g)
+        tot, cnt = 0.0, 0
+        for s in range(0, n - batch + 1, batch):
+            idx = perm[s:s + batch].cuda()
+            xb, sgb, tb = X[idx].contiguous(), SG[idx].contiguous(), T[idx].contiguous()
+            loss = model.train_step(batch, xb.data_ptr(), sgb.data_ptr(), tb.data_ptr(), lr, wd)
+            tot += loss
+            cnt += 1
+        losses.append(tot / max(cnt, 1))
+        if log:
+            log(f"  epoch {ep}: mean loss {losses[-1]:.4f}")
+    return losses
+
+
+def mean_loss(model: N.Model, X, SG, T, batch=256):
+    tot, cnt = 0.0, 0
+    for s in range(0, X.shape[0], batch):
+        b = min(batch, X.shape[0] - s)
+        tot += model.backward(b, X[s:s + b].contiguous().data_ptr(), SG[s:s + b].contiguous().data_ptr(),
+                              T[s:s + b].contiguous().data_ptr()) * b
+        cnt += b
+    return tot / cnt
+
+
+def plan_uniform(pbs):
+    bp = BatchPlanner(pbs)
+    return [(i["status"], i["path_cost"]) for i in bp.plan()]
+
+
+def plan_mixture(model: N.Model, pb: envgen.Problem, graph: N.Graph | None = None):
+    """n/2 uniform (SampleFree) + n/2 learned samples, radius for n/2."""
+    n_u = pb.n // 2
+    n_l = pb.n - n_u
+    r = np.float32(N.gmt_connection_radius(n_u, 3, 0.0, 1.0))
+    upb = pb.with_(n=n_u, r=float(r))
+    space, goal = space_struct(upb), goal_struct(upb)
+    boxes, keep = boxes_on_device(upb)
+    params = params_struct(upb)
+    samples = torch.empty(3, n_l, dtype=torch.float32, device="cuda")
+    N.gmt_propose(model, space, boxes, upb.x_init, upb.goal_center, n_l, int(pb.seed) ^ 0x5A5A5A5A, samples.data_ptr(),
+                  n_l)
+    g = N.gmt_build_graph_ex(space, boxes, [float(v) for v in upb.x_init], goal, params, samples.data_ptr(), n_l, n_l,
+                             graph)
+    Nn = n_u + 1 + n_l
+    parent = torch.empty(Nn, dtype=torch.int32, device="cuda")
+    cost = torch.empty(Nn, dtype=torch.float32, device="cuda")
+    info = N.gmt_plan(g, boxes, params, parent.data_ptr(), cost.data_ptr()).as_dict()
+    return (info["status"], info["path_cost"]), g
+
+
+def evaluate(model: N.Model, seeds, ns=(1024, 2048, 4096), n_ref=4096, log=print):
+    """Mean path cost of uniform and mixture sampling at each n, over the
+    environments every method solves, relative to uniform at n_ref.  The
+    control arm "uniform_mixture_radius" samples uniformly with the mixture's
+    (larger, n/2) radius, which isolates what the learned samples add."""
+    res = {"uniform": {}, "mixture": {}, "uniform_mixture_radius": {}}
+    per = {}
+    for n in sorted(set(ns) | {n_ref}):
+        per[("uniform", n)] = plan_uniform([env(s, n) for s in seeds])
+    for n in ns:
+        r_half = float(np.float32(N.gmt_connection_radius(n // 2, 3, 0.0, 1.0)))
+        per[("uniform_mixture_radius", n)] = plan_uniform([env(s, n).with_(r=r_half) for s in seeds])
+    g = None
+    for n in ns:
+        out = []
+        for s in seeds:
+            r, g = plan_mixture(model, env(s, n), g)
+            out.append(r)
+        per[("mixture", n)] = out
+    keys = list(per)
+    both = [i for i in range(len(seeds)) if all(per[k][i][0] == 0 for k in keys)]
+    ref = float(np.mean([per[("uniform", n_ref)][i][1] for i in both])) if both else float("nan")
+    for (kind, n), rr in per.items():
+        costs = [rr[i][1] for i in both]
+        res[kind][str(n)] = {"success": float(np.mean([x[0] == 0 for x in rr])),
+                             "mean_cost": float(np.mean(costs)) if costs else None,
+                             "cost_vs_uniform_ref": (float(np.mean(costs)) / ref) if costs else None}
+    res["reference"] = {"n": n_ref, "mean_cost": ref, "environments_compared": len(both)}
+    within = [n for n in ns if res["mixture"][str(n)]["cost_vs_uniform_ref"] is not None
+              and res["mixture"][str(n)]["cost_vs_uniform_ref"] <= 1.02]
+    res["smallest_mixture_n_within_2pct"] = min(within) if within else None
+    res["sample_reduction_at_equal_cost"] = (n_ref / min(within)) if within else None
+    if log:
+        log(json.dumps(res, indent=1))
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train-envs", type=int, default=10000)
+    ap.add_argument("--test-envs", type=int, default=1000)
+    ap.add_argument("--train-n", type=int, default=16384)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--out", default="learned.json")
+    ap.add_argument("--checkpoint", default="")
+    a = ap.parse_args()
+    t0 = time.time()
+    train_seeds = [1_000_000 + k for k in range(a.train_envs)]
+    test_seeds = [2_000_000 + k for k in range(a.test_envs)]
+    X, SG, T, kept = generate_dataset(train_seeds, n=a.train_n)
+    t_data = time.time() - t0
+    model = N.Model(GRID, HIDDEN, CELLS, 256, seed=7)
+    t1 = time.time()
+    losses = train(model, X, SG, T, epochs=a.epochs)
+    t_train = time.time() - t1
+    if a.checkpoint:
+        model.save(a.checkpoint)
+    Xt, SGt, Tt, _ = generate_dataset(test_seeds[:256], n=a.train_n, log=None)
+    test_loss = mean_loss(model, Xt, SGt, Tt)
+    ev = evaluate(model, test_seeds)
+    out = {"train_envs": a.train_envs, "solved_train_envs": len(kept), "train_n": a.train_n, "epochs": a.epochs,
+           "losses": losses, "held_out_loss": test_loss, "dataset_s": t_data, "train_s": t_train, "eval": ev,
+           "total_s": time.time() - t0}
+    with open(a.out, "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps({k: v for k, v in out.items() if k != "losses"}, indent=1))
+
+
+if __name__ == "__main__":
+    main()
