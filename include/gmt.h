@@ -250,6 +250,65 @@ gmt_status gmt_batch_autotune(gmt_batch* batch, gmt_stream stream, int32_t* best
 
 void gmt_batch_free(gmt_batch* batch);
 
+/* ---------------------------------------------------------------- replanning server
+ * Continuous-batching request loop (an extension for planning inside a
+ * control loop, Sec. V-C's setting): sessions keep samples and the neighbour
+ * CSR resident (connection costs do not depend on the obstacles) plus a
+ * per-edge cache of collision verdicts; each request brings the session's
+ * current boxes, the cache entries of edges whose checked points' bounding box
+ * meets the old or new place of a moved box are cleared, and the wavefront is
+ * re-run (results identical to a fresh plan).  A worker thread admits queued
+ * requests to free slots (CUDA streams with their own plan scratch) as soon as
+ * they free up, so requests overlap on the device; a session has at most one
+ * request running.  Sessions are admitted against a device-memory budget. */
+typedef struct {
+    int32_t slots;         /* concurrent requests (streams), >= 1 */
+    int32_t cluster;       /* CTAs per plan: 0/1 = one CTA, 2..16 = a cluster */
+    int32_t threads;       /* threads per CTA (0 = automatic) */
+    int32_t max_nodes;     /* largest N of any session */
+    int32_t max_boxes;     /* largest box count of any session */
+    uint64_t memory_budget;/* bytes of device memory sessions may hold; 0 = what is free */
+} gmt_server_config;
+
+typedef struct {
+    uint64_t request_id;
+    int32_t session;
+    int32_t status;        /* as gmt_plan_info.status */
+    int32_t goal_node;
+    float path_cost;
+    int64_t iters;
+    int64_t checks;        /* lazy checks (Alg. 1, Line 7) */
+    int64_t checks_computed; /* of those, not answered by the verdict cache */
+    int64_t edges_checked; /* out-edges pushed + in-edges pulled */
+    double queue_ms;       /* submit -> launch */
+    double latency_ms;     /* submit -> plan finished on the device */
+} gmt_server_result;
+
+typedef struct gmt_server gmt_server;
+
+gmt_status gmt_server_create(const gmt_server_config* config, gmt_server** server);
+/* Stops the worker (after running requests finish) and frees everything. */
+void gmt_server_free(gmt_server* server);
+/* Builds a resident session: SampleFree + CSR for the problem (space, x_init,
+ * goal, params as for gmt_build_graph) with `box_count` boxes given as HOST
+ * arrays [box_count][pos_dim].  GMT_ERR_ADMISSION if its estimated device
+ * memory does not fit the budget (or the free memory).  Synchronous. */
+gmt_status gmt_server_open_session(gmt_server* server, const gmt_space* space, const float* x_init,
+                                   const gmt_goal* goal, const gmt_params* params, int32_t box_count,
+                                   const float* box_lo, const float* box_hi, int32_t* session);
+/* Queues a replanning request for the session with its boxes now (HOST
+ * arrays, same count as at open).  parent/cost: DEVICE [N] outputs or NULL
+ * (they must stay valid until the result is polled).  Returns at once. */
+gmt_status gmt_server_submit(gmt_server* server, int32_t session, uint64_t request_id, const float* box_lo,
+                             const float* box_hi, int32_t* parent, float* cost);
+/* Moves up to `max` finished results to `out` (HOST), waiting up to wait_ms
+ * for the first one. */
+gmt_status gmt_server_poll(gmt_server* server, gmt_server_result* out, int32_t max, int32_t* count,
+                           int32_t wait_ms);
+/* Waits for the session's requests, then frees it. */
+gmt_status gmt_server_close_session(gmt_server* server, int32_t session);
+gmt_status gmt_server_session_view(gmt_server* server, int32_t session, gmt_graph_view* view);
+
 /* ---------------------------------------------------------------- learned proposal
  * An extension beyond the paper (which samples uniformly or with Halton
  * points): an MLP maps a G^3 voxel occupancy grid of the obstacles plus start

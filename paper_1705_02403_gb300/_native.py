@@ -99,6 +99,21 @@ class gmt_model_view(C.Structure):
                 ("logits", C.c_void_p), ("loss", C.c_void_p)]
 
 
+class gmt_server_config(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("cluster", C.c_int32), ("threads", C.c_int32), ("max_nodes", C.c_int32),
+                ("max_boxes", C.c_int32), ("memory_budget", C.c_uint64)]
+
+
+class gmt_server_result(C.Structure):
+    _fields_ = [("request_id", C.c_uint64), ("session", C.c_int32), ("status", C.c_int32), ("goal_node", C.c_int32),
+                ("path_cost", C.c_float), ("iters", C.c_int64), ("checks", C.c_int64),
+                ("checks_computed", C.c_int64), ("edges_checked", C.c_int64), ("queue_ms", C.c_double),
+                ("latency_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # Every symbol include/gmt.h declares, with its ctypes signature.
 _P, _I32, _I64, _F32, _F64, _U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double, C.c_uint64
 SIGNATURES = {
@@ -132,6 +147,14 @@ SIGNATURES = {
     "gmt_model_load": (_I32, [_P, C.c_char_p]),
     "gmt_path_histogram": (_I32, [_P, _I32, _P, _I32, _I32, _F32, _F32, _P, _P]),
     "gmt_propose": (_I32, [_P, C.POINTER(gmt_space), C.POINTER(gmt_boxes), _P, _P, _I32, _U64, _P, _I32, _P]),
+    "gmt_server_create": (_I32, [C.POINTER(gmt_server_config), C.POINTER(C.c_void_p)]),
+    "gmt_server_free": (None, [_P]),
+    "gmt_server_open_session": (_I32, [_P, C.POINTER(gmt_space), _P, C.POINTER(gmt_goal), C.POINTER(gmt_params), _I32,
+                                       _P, _P, C.POINTER(_I32)]),
+    "gmt_server_submit": (_I32, [_P, _I32, _U64, _P, _P, _P, _P]),
+    "gmt_server_poll": (_I32, [_P, C.POINTER(gmt_server_result), _I32, C.POINTER(_I32), _I32]),
+    "gmt_server_close_session": (_I32, [_P, _I32]),
+    "gmt_server_session_view": (_I32, [_P, _I32, C.POINTER(gmt_graph_view)]),
     "gmt_connection_radius": (_F64, [_I32, _I32, _F64, _F64]),
     "gmt_last_error": (C.c_char_p, []),
 }
@@ -371,3 +394,55 @@ def gmt_build_graph_ex(space, boxes, x_init, goal, params, extra_ptr, extra_coun
                                   C.byref(params), C.c_void_p(extra_ptr or 0), extra_count, extra_pitch,
                                   C.byref(g.handle), _stream(stream)))
     return g
+
+
+class Server:
+    """Owner of a gmt_server handle."""
+
+    def __init__(self, slots=16, cluster=4, threads=0, max_nodes=8193, max_boxes=64, memory_budget=0):
+        cfg = gmt_server_config(slots, cluster, threads, max_nodes, max_boxes, memory_budget)
+        self.handle = C.c_void_p(None)
+        _check(lib.gmt_server_create(C.byref(cfg), C.byref(self.handle)))
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib.gmt_server_free(self.handle)
+            self.handle = C.c_void_p(None)
+
+    __del__ = close
+
+    def open_session(self, space, x_init, goal, params, box_lo, box_hi, allow_errors=False):
+        import numpy as np
+        lo = np.ascontiguousarray(box_lo, np.float32)
+        hi = np.ascontiguousarray(box_hi, np.float32)
+        xi = (C.c_float * GMT_MAX_DIM)(*[float(v) for v in x_init])
+        sid = C.c_int32()
+        st = lib.gmt_server_open_session(self.handle, C.byref(space), C.cast(xi, C.c_void_p), C.byref(goal),
+                                         C.byref(params), lo.shape[0], lo.ctypes.data_as(C.c_void_p),
+                                         hi.ctypes.data_as(C.c_void_p), C.byref(sid))
+        if allow_errors and st != GMT_OK:
+            return None, st
+        _check(st)
+        return sid.value, st
+
+    def submit(self, session, request_id, box_lo, box_hi, parent_ptr=None, cost_ptr=None):
+        import numpy as np
+        lo = np.ascontiguousarray(box_lo, np.float32)
+        hi = np.ascontiguousarray(box_hi, np.float32)
+        _check(lib.gmt_server_submit(self.handle, session, request_id, lo.ctypes.data_as(C.c_void_p),
+                                     hi.ctypes.data_as(C.c_void_p), C.c_void_p(parent_ptr or 0),
+                                     C.c_void_p(cost_ptr or 0)))
+
+    def poll(self, max_results=1024, wait_ms=0):
+        out = (gmt_server_result * max_results)()
+        n = C.c_int32()
+        _check(lib.gmt_server_poll(self.handle, out, max_results, C.byref(n), wait_ms))
+        return [out[k].as_dict() for k in range(n.value)]
+
+    def close_session(self, session):
+        _check(lib.gmt_server_close_session(self.handle, session))
+
+    def session_view(self, session):
+        v = gmt_graph_view()
+        _check(lib.gmt_server_session_view(self.handle, session, C.byref(v)))
+        return v

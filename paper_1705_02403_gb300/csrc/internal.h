@@ -70,6 +70,7 @@ struct PlanCtl {
     int path_len;
     unsigned long long goal_key;
     unsigned long long push_edges, pull_edges, checks, failed, tree_size;
+    unsigned long long checks_computed;  // checks not answered by the verdict cache
 };
 
 struct PlanArgs {
@@ -96,6 +97,12 @@ struct PlanArgs {
     int* list_open[2];
     int* list_cand;
     PlanCtl* ctl;
+    // Optional per-edge verdict cache (in-CSR order): 0 unknown, 1 free,
+    // 2 collides.  A known verdict answers the check; an unknown one is
+    // computed and stored.  Valid only while the obstacles that could change
+    // the verdict stay where they were (the serving loop clears the entries
+    // that moved boxes touch before every plan).
+    uint8_t* verdict;
     // Set by the batched path: the CSR may only be read if the edge count the
     // build produced fits the slice that was filled (else GMT_ERR_OOM).
     int check_edges;

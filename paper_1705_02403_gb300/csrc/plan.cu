@@ -217,7 +217,7 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
     float theta = 0.0f;
     int p = 0, q = 0, it = 0;
     int status = GMT_OK;
-    unsigned long long n_push = 0, n_pull = 0, n_checks = 0, n_failed = 0;
+    unsigned long long n_push = 0, n_pull = 0, n_checks = 0, n_failed = 0, n_computed = 0;
 
     while (ok) {
         if (it >= A.max_iters) { status = GMT_ERR_ITER_LIMIT; break; }
@@ -329,12 +329,21 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
                     sx[a] = __ldg(&A.X[(size_t)a * A.pitch + x]);
                 }
                 bool free_edge;
-                if (KIND == GMT_COST_EUCLID)
-                    free_edge = segment_free_warp<DP>(sy, sx, __ldg(&A.in_cost[be]), A.seg_spacing, blo, bhi, nbox);
-                else {
-                    // arrival time of the edge: stored by the graph build, or recomputed
-                    const float tau = A.in_tau ? __ldg(&A.in_tau[be]) : di_tau(di_coef(sy, sx), A.r);
-                    free_edge = trajectory_free_warp(sy, sx, tau, A.traj_points, A.pos_lo, A.pos_hi, blo, bhi, nbox);
+                const int cached = A.verdict ? (int)__ldcg(&A.verdict[be]) : 0;
+                if (cached != 0) {
+                    free_edge = cached == 1;
+                } else {
+                    if (KIND == GMT_COST_EUCLID)
+                        free_edge = segment_free_warp<DP>(sy, sx, __ldg(&A.in_cost[be]), A.seg_spacing, blo, bhi, nbox);
+                    else {
+                        // arrival time of the edge: stored by the graph build, or recomputed
+                        const float tau = A.in_tau ? __ldg(&A.in_tau[be]) : di_tau(di_coef(sy, sx), A.r);
+                        free_edge = trajectory_free_warp(sy, sx, tau, A.traj_points, A.pos_lo, A.pos_hi, blo, bhi, nbox);
+                    }
+                    if (lane == 0) {
+                        ++n_computed;
+                        if (A.verdict) A.verdict[be] = free_edge ? 1 : 2;
+                    }
                 }
                 if (lane == 0) {
                     n_pull += (unsigned long long)(r1 - r0);
@@ -395,6 +404,7 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
             n_pull += __shfl_xor_sync(0xffffffffu, n_pull, off);
             n_checks += __shfl_xor_sync(0xffffffffu, n_checks, off);
             n_failed += __shfl_xor_sync(0xffffffffu, n_failed, off);
+            n_computed += __shfl_xor_sync(0xffffffffu, n_computed, off);
             tree += __shfl_xor_sync(0xffffffffu, tree, off);
         }
         if (lane == 0) {
@@ -402,6 +412,7 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
             atomicAdd(&ctl->pull_edges, n_pull);
             atomicAdd(&ctl->checks, n_checks);
             atomicAdd(&ctl->failed, n_failed);
+            atomicAdd(&ctl->checks_computed, n_computed);
             atomicAdd(&ctl->tree_size, tree);
         }
         ok = team.sync(ctl);

@@ -38,7 +38,7 @@ def test_library_exports_every_declared_function(native):
 def test_struct_layout_matches_c(native):
     import ctypes as C
     structs = ["gmt_space", "gmt_boxes", "gmt_goal", "gmt_params", "gmt_graph_view", "gmt_plan_info", "gmt_profile",
-               "gmt_query", "gmt_model_config", "gmt_model_view"]
+               "gmt_query", "gmt_model_config", "gmt_model_view", "gmt_server_config", "gmt_server_result"]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gmt.h"', "int main(void){"]
     for s in structs:
         lines.append(f'printf("{s} %zu\\n", sizeof({s}));')
