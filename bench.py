@@ -39,7 +39,7 @@ METRIC = "ms/plan p50/p99 & edges checked/s; learned+batched vs plain at equal p
 # DRAM bytes (read + write) of one plan_kernel launch on this workload, from the
 # ncu capture summarised in profiles/plan_kernel_double_integrator_6d_n4096.md.
 # Set to None whenever plan_kernel changes until it is captured again.
-PLAN_KERNEL_DRAM_BYTES = {"di6": 2106112, "geo2d": None}
+PLAN_KERNEL_DRAM_BYTES = {"di6": None, "geo2d": None}
 
 
 def parse():
@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--workload", default="di6", choices=["di6", "geo2d"])
     ap.add_argument("--seed-base", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
     return ap.parse_args()
 
 
@@ -334,6 +335,10 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
+    if not args.no_extras:
+        line["batched"] = bench_batched(dev, flush)
+        line["serving"] = bench_serving(local_rank)
+        line["gpu_launches_extras"] = "batched: 7 launches per group per batch (replayed CUDA graph); serving: 3 per request"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         seeds_cpu = [seeds[args.warmup + j] for j in range(3)]
         rows = 256 if args.workload == "di6" else 1025
@@ -344,6 +349,49 @@ def run_gpu(args, rank, world, local_rank):
                                           f"{1e3 * sec:.0f} ms per full plan"}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def bench_batched(dev, flush, reps=5):
+    """The 256-query uneven batch (2D/3D, n log-uniform in [512, 16384], 5-80
+    boxes, Theorem 1 radii): prepared once, team shape autotuned, then whole
+    batches (sampling + CSR + wavefront) replayed from the captured CUDA graph."""
+    import torch
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300 import envgen
+    from paper_1705_02403_gb300.planner import BatchPlanner
+    qs = envgen.batch_queries(seed=0, q=256)
+    bp = BatchPlanner(qs, device=dev)
+    infos = bp.plan()
+    shape = N.gmt_batch_autotune(bp.batch)
+    st = torch.cuda.current_stream()
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        infos = bp.plan()
+        b.record(st)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    edges = sum(i["push_edges"] + i["pull_edges"] for i in infos)
+    t = float(np.median(ms))
+    return {"workload": "256 uneven 2D/3D geometric queries, n log-uniform in [512, 16384], 5-80 boxes",
+            "ms_per_batch_p50": t, "plans_per_s": 256 / (t / 1e3), "edges_checked_per_s": edges / (t / 1e3),
+            "sum_nodes": int(sum(pb.N for pb in qs)), "edges_checked_per_batch": int(edges),
+            "success_rate": float(np.mean([i["status"] == 0 for i in infos])),
+            "autotuned_team": {"cluster": shape[0], "threads": shape[1], "plan_stage_ms": shape[2]}}
+
+
+def bench_serving(local_rank):
+    """10,000 requests at 100 Hz: 100 double-integrator sessions (n uniform in
+    [2048, 8192], 30 boxes moving up to 0.02 per tick), 100 ticks."""
+    from paper_1705_02403_gb300.serving import run_stream
+    out = run_stream(sessions=100, ticks=100, hz=100.0, slots=32, cluster=4, threads=512, seed=local_rank, log=None)
+    return {"workload": "100 Hz replanning stream, 100 DI sessions x 100 ticks, n in [2048, 8192], 30 moving boxes",
+            "latency_ms_p50": out["latency_ms"]["p50"], "latency_ms_p99": out["latency_ms"]["p99"],
+            "requests": out["requests"], "requests_per_s": out["requests_per_s"],
+            "edges_checked_per_s": out["edges_checked_per_s"], "verdict_cache_hit_rate": out["verdict_cache_hit_rate"],
+            "success_rate": out["success_rate"], "errors": out["errors"]}
 
 
 def main():

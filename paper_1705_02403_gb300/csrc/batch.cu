@@ -588,7 +588,7 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
     if (max_teams <= 0) return bfail(GMT_ERR_CUDA, "batched plan kernel cannot be resident");
     BCUDA(b->s_ocost.need((size_t)max_teams * max_n * 4), "scratch");
     BCUDA(b->s_stamp.need((size_t)max_teams * max_n * 4), "scratch");
-    BCUDA(b->s_lists.need((size_t)max_teams * max_n * 5 * 4), "scratch");
+    BCUDA(b->s_lists.need((size_t)max_teams * plan_list_stride(max_n) * 4), "scratch");
     BCUDA(b->slot.need((size_t)max_teams * 4), "scratch");
     // scratch slices are indexed by team id, so every group may use all of it
     for (Group& g : b->groups) g.max_n = max_n;

@@ -243,7 +243,7 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     GROW(flags, 4);
     GROW(ocost, N);
     GROW(stamp, N);
-    GROW(lists, 5 * N);
+    GROW(lists, kPlanListInts * N);
     GROW(ctl, 1);
     if (g->kind == GMT_COST_DI) {
         GROW(in_row_own, N + 1);
@@ -353,9 +353,7 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
     a.debug_flags = params->debug_flags;
     a.cost = cost; a.parent = parent; a.path = path;
     a.ocost = g->ocost; a.stamp = g->stamp;
-    a.list_g[0] = g->lists; a.list_g[1] = g->lists + N;
-    a.list_open[0] = g->lists + 2 * (size_t)N; a.list_open[1] = g->lists + 3 * (size_t)N;
-    a.list_cand = g->lists + 4 * (size_t)N;
+    assign_plan_lists(a, g->lists, (size_t)N);
     a.ctl = g->ctl;
     for (int k = 0; k < 3; ++k) { a.pos_lo[k] = g->pos_lo[k]; a.pos_hi[k] = g->pos_hi[k]; }
 

@@ -94,7 +94,7 @@ struct PlanArgs {
     float* ocost;
     int* stamp;
     int* list_g[2];
-    int* list_open[2];
+    int2* list_open[2];   // (node, cost bits) of each open node
     int* list_cand;
     PlanCtl* ctl;
     // Optional per-edge verdict cache (in-CSR order): 0 unknown, 1 free,
@@ -109,9 +109,21 @@ struct PlanArgs {
     long long edge_cap;
 };
 
+// Plan list scratch: open x2 (int2 entries) first, so both stay 8-byte
+// aligned for any M when `base` is; then G x2 and the candidates (ints).
+constexpr int kPlanListInts = 7;
+__host__ __device__ inline size_t plan_list_stride(size_t M) { return (kPlanListInts * M + 3) / 4 * 4; }
+__host__ __device__ inline void assign_plan_lists(PlanArgs& a, int* base, size_t M) {
+    a.list_open[0] = (int2*)base;
+    a.list_open[1] = (int2*)(base + 2 * M);
+    a.list_g[0] = base + 4 * M;
+    a.list_g[1] = base + 5 * M;
+    a.list_cand = base + 6 * M;
+}
+
 // Per-team scratch of the batched wavefront: team t uses the slices
 // [t * max_nodes, (t+1) * max_nodes) of ocost and stamp and
-// [t * 5 max_nodes, (t+1) * 5 max_nodes) of lists.
+// [t * kPlanListInts max_nodes, (t+1) * kPlanListInts max_nodes) of lists.
 struct BatchScratch {
     float* ocost;
     int* stamp;

@@ -11,8 +11,10 @@
 //      snapshot `ocost` (cost if open, +inf otherwise) is brought up to date
 //      with the previous iteration's changes (G closed, new nodes opened).
 //   B  frontier push (Line 4): one warp per node of G scans its out-row;
-//      every unexplored neighbour (cost == +inf) is claimed once per iteration
-//      through an atomic stamp and appended to the candidate list.
+//      every unexplored neighbour is claimed once per iteration through one
+//      atomicMax on its stamp (INT_MAX marks tree nodes) and appended to the
+//      candidate list.  Open-list entries carry their cost, so group
+//      selection and the snapshot update need no gathers.
 //   C  lazy parent (Lines 5-9): one warp per candidate x scans its in-row,
 //      gathers ocost[y] and takes argmin of (ocost[y] + c(y, x), y); the warp
 //      then checks that single edge (points spread over the lanes) and, if it
@@ -193,15 +195,17 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
     const int N = A.N;
 
     // Lines 1-2: x_init is the only open node and the root of the tree.
+    // stamp[v]: INT_MAX once v is in the tree, else the last iteration that
+    // claimed v as a candidate (-1: never)
     for (int v = rank; v < N; v += size) {
         const float c0 = v == 0 ? 0.0f : INF;
         A.cost[v] = c0;
         A.ocost[v] = c0;
         A.parent[v] = -1;
-        A.stamp[v] = -1;
+        A.stamp[v] = v == 0 ? INT_MAX : -1;
     }
     if (rank == 0) {
-        A.list_open[0][0] = 0;
+        A.list_open[0][0] = make_int2(0, __float_as_int(0.0f));
         ctl->open_count[0] = 1;
         ctl->open_count[1] = 0;
         ctl->g_count[0] = ctl->g_count[1] = 0;
@@ -222,8 +226,8 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
     while (ok) {
         if (it >= A.max_iters) { status = GMT_ERR_ITER_LIMIT; break; }
         int* G = A.list_g[p];
-        const int* cur = A.list_open[q];
-        int* nxt = A.list_open[q ^ 1];
+        const int2* cur = A.list_open[q];
+        int2* nxt = A.list_open[q ^ 1];
 
         // ---- phase A: snapshot update from the previous iteration, group selection
         if (it > 0) {
@@ -232,8 +236,8 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
             for (int t = rank; t < ng_prev; t += size) A.ocost[ldcg_i(&Gprev[t])] = INF;
             const int k0 = ldcg_i(&ctl->keep_count[p ^ 1]), k1 = ldcg_i(&ctl->open_count[q]);
             for (int t = k0 + rank; t < k1; t += size) {
-                const int x = ldcg_i(&cur[t]);
-                A.ocost[x] = ldcg_f(&A.cost[x]);
+                const int2 e = __ldcg(&cur[t]);
+                A.ocost[e.x] = __int_as_float(e.y);
             }
         }
         if (rank == 0) ctl->cand_count = 0;
@@ -245,8 +249,9 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
                 int v = -1;
                 float c = INF;
                 if (t < ncur) {
-                    v = ldcg_i(&cur[t]);
-                    c = ldcg_f(&A.cost[v]);
+                    const int2 e = __ldcg(&cur[t]);
+                    v = e.x;
+                    c = __int_as_float(e.y);
                     in_g = c <= theta;
                     keep = !in_g;
                 }
@@ -256,7 +261,7 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
                     if (A.is_goal[v]) ctl->goal_flag[p] = 1;
                 }
                 const int sk = warp_append_slot(keep, &ctl->open_count[q ^ 1]);
-                if (keep) nxt[sk] = v;
+                if (keep) nxt[sk] = make_int2(v, __float_as_int(c));
                 const unsigned kmin = __reduce_min_sync(0xffffffffu, keep ? float_key(c) : INF_KEY);
                 if (lane == 0 && kmin != INF_KEY) atomicMin(&ctl->min_keep[p], kmin);
             }
@@ -284,7 +289,9 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
                     int x = -1;
                     if (e < e1) {
                         x = __ldg(&A.out_col[e]);
-                        if (ldcg_f(&A.cost[x]) == INF) want = atomicExch(&A.stamp[x], it) != it;
+                        // one atomic both tests "unexplored" (stamp < INT_MAX) and
+                        // claims x for this iteration (stamp < it before)
+                        want = atomicMax(&A.stamp[x], it) < it;
                     }
                     const int sc = warp_append_slot(want, &ctl->cand_count);
                     if (want) A.list_cand[sc] = x;
@@ -299,6 +306,9 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
             for (int ci = gwarp; ci < nc; ci += nwarps) {
                 const int x = ldcg_i(&A.list_cand[ci]);
                 const int r0 = __ldg(&A.in_row[x]), r1 = __ldg(&A.in_row[x + 1]);
+                float sx[D];  // issued now, used by the check after the reduction
+#pragma unroll
+                for (int a = 0; a < D; ++a) sx[a] = __ldg(&A.X[(size_t)a * A.pitch + x]);
                 float bc = INF;
                 int by = INT_MAX, be = -1;
                 for (int e = r0 + lane; e < r1; e += 32) {
@@ -322,12 +332,9 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
                     if (lane == 0) { ++n_checks; ++n_failed; atomicCAS(&ctl->error, 0, (int)GMT_ERR_CUDA); }
                     continue;
                 }
-                float sy[D], sx[D];
+                float sy[D];
 #pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    sy[a] = __ldg(&A.X[(size_t)a * A.pitch + by]);
-                    sx[a] = __ldg(&A.X[(size_t)a * A.pitch + x]);
-                }
+                for (int a = 0; a < D; ++a) sy[a] = __ldg(&A.X[(size_t)a * A.pitch + by]);
                 bool free_edge;
                 const int cached = A.verdict ? (int)__ldcg(&A.verdict[be]) : 0;
                 if (cached != 0) {
@@ -351,8 +358,9 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
                     if (free_edge) {
                         A.cost[x] = bc;
                         A.parent[x] = by;
+                        A.stamp[x] = INT_MAX;
                         const int s = atomicAdd(&ctl->open_count[q ^ 1], 1);
-                        nxt[s] = x;
+                        nxt[s] = make_int2(x, __float_as_int(bc));
                         atomicMin(&ctl->min_new[p], float_key(bc));
                     } else {
                         ++n_failed;
@@ -472,10 +480,7 @@ __global__ void __launch_bounds__(1024) plan_batch_kernel(const PlanArgs* __rest
         const size_t nm = (size_t)scratch.max_nodes;
         A.ocost = scratch.ocost + team_id * nm;
         A.stamp = scratch.stamp + team_id * nm;
-        int* lists = scratch.lists + team_id * 5 * nm;
-        A.list_g[0] = lists; A.list_g[1] = lists + nm;
-        A.list_open[0] = lists + 2 * nm; A.list_open[1] = lists + 3 * nm;
-        A.list_cand = lists + 4 * nm;
+        assign_plan_lists(A, scratch.lists + team_id * plan_list_stride(nm), nm);
         plan_body<Team, KIND, DP>(A, team, sbox);
         team.sync(nullptr);
     }

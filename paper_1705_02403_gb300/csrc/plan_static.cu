@@ -11,7 +11,7 @@
 // in one file-scope __device__ array of fixed size instead of being allocated.
 //
 //  - Capacity: graphs of at most GMT_STATIC_MAX_NODES nodes; larger ones are
-//    rejected with GMT_ERR_INVALID.  The array takes about 1.8 MB on every GPU
+//    rejected with GMT_ERR_INVALID.  The array takes about 2.4 MB on every GPU
 //    that loads the library, for the life of the process.
 //  - Set-up: the first call on a device looks up the array's device address
 //    (cudaGetSymbolAddress, with that device current) and caches it; make that
@@ -34,8 +34,9 @@ namespace {
 constexpr size_t kCtlSlot = 256;
 static_assert(sizeof(PlanCtl) <= kCtlSlot, "control block must fit its slot");
 constexpr size_t kNodes = GMT_STATIC_MAX_NODES;
-// [control block][ocost: kNodes floats][stamp: kNodes ints][5 lists: 5 kNodes ints]
-constexpr size_t kScratchBytes = kCtlSlot + kNodes * sizeof(float) + kNodes * sizeof(int) + 5 * kNodes * sizeof(int);
+// [control block][ocost: kNodes floats][stamp: kNodes ints][lists: kPlanListInts kNodes ints]
+constexpr size_t kScratchBytes =
+    kCtlSlot + kNodes * sizeof(float) + kNodes * sizeof(int) + (size_t)kPlanListInts * kNodes * sizeof(int);
 
 static __device__ __align__(256) unsigned char g_plan_scratch[kScratchBytes];
 
@@ -124,9 +125,7 @@ extern "C" gmt_status gmt_plan_static(const gmt_space* space, const gmt_graph_vi
     a.debug_flags = params->debug_flags;
     a.cost = cost; a.parent = parent; a.path = path;
     a.ocost = ocost; a.stamp = stamp;
-    a.list_g[0] = lists; a.list_g[1] = lists + NM;
-    a.list_open[0] = lists + 2 * NM; a.list_open[1] = lists + 3 * NM;
-    a.list_cand = lists + 4 * NM;
+    assign_plan_lists(a, lists, NM);
     a.ctl = ctl;
 
     int blocks = 1, threads = 1024;

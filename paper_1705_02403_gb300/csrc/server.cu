@@ -258,9 +258,7 @@ cudaError_t start_request(gmt_server* sv, Slot& sl, Session& ss, Request&& rq) {
     a.parent = sl.req.parent ? sl.req.parent : sl.parent;
     a.ocost = sl.ocost; a.stamp = sl.stamp;
     const size_t M = (size_t)sv->cfg.max_nodes;
-    a.list_g[0] = sl.lists; a.list_g[1] = sl.lists + M;
-    a.list_open[0] = sl.lists + 2 * M; a.list_open[1] = sl.lists + 3 * M;
-    a.list_cand = sl.lists + 4 * M;
+    assign_plan_lists(a, sl.lists, M);
     a.ctl = sl.ctl;
     a.verdict = ss.verdict;
     e = cudaMemsetAsync(sl.ctl, 0, sizeof(PlanCtl), st);
@@ -367,7 +365,7 @@ gmt_status gmt_server_create(const gmt_server_config* cfg, gmt_server** out) {
         e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaMalloc(&sl->ocost, M * 4);
         if (e == cudaSuccess) e = cudaMalloc(&sl->stamp, M * 4);
-        if (e == cudaSuccess) e = cudaMalloc(&sl->lists, M * 5 * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&sl->lists, M * kPlanListInts * 4);
         if (e == cudaSuccess) e = cudaMalloc(&sl->ctl, 256);
         if (e == cudaSuccess) e = cudaMalloc(&sl->parent, M * 4);
         if (e == cudaSuccess) e = cudaMalloc(&sl->cost, M * 4);
