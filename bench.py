@@ -190,6 +190,21 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- ranks
+def aggregate_ranks(time_ms, edges, world, device="cpu"):
+    """Whole-job totals across replicas: the slowest rank's time (MAX) and the
+    edges of all ranks (SUM); value = edges / time."""
+    if world <= 1:
+        return time_ms, edges
+    import torch
+    t = torch.tensor([time_ms, edges], dtype=torch.float64, device=device)
+    mx = t.clone()
+    torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+    sm = t.clone()
+    torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 # --------------------------------------------------------------------------- GPU arm
 def run_gpu(args, rank, world, local_rank):
     import torch
@@ -252,13 +267,7 @@ def run_gpu(args, rank, world, local_rank):
     edges = [i["push_edges"] + i["pull_edges"] for i in infos]
     sum_ms = float(np.sum(step_ms))
     tot_edges = float(np.sum(edges))
-    if world > 1:
-        t = torch.tensor([sum_ms, tot_edges], dtype=torch.float64, device=dev)
-        mx = t.clone(); torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        sm = t.clone(); torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-        sum_ms_all, tot_edges_all = float(mx[0]), float(sm[1])
-    else:
-        sum_ms_all, tot_edges_all = sum_ms, tot_edges
+    sum_ms_all, tot_edges_all = aggregate_ranks(sum_ms, tot_edges, world, dev)
     value = tot_edges_all / (sum_ms_all / 1e3)
 
     # ---- end to end: host inputs (pinned), H2D of the boxes and D2H of the tree each step
@@ -286,11 +295,8 @@ def run_gpu(args, rank, world, local_rank):
         e2e_edges.append(info["push_edges"] + info["pull_edges"])
         bi = h_lo[k].numel() * 4 + h_hi[k].numel() * 4
         bo = Nn * 8 + 64
-    e2e_value = float(np.sum(e2e_edges) / (np.sum(e2e_ms) / 1e3))
-    if world > 1:
-        t = torch.tensor([e2e_value], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t)
-        e2e_value = float(t[0])
+    e2e_ms_all, e2e_edges_all = aggregate_ranks(float(np.sum(e2e_ms)), float(np.sum(e2e_edges)), world, dev)
+    e2e_value = e2e_edges_all / (e2e_ms_all / 1e3)
 
     # ---- roofline of the dominant kernel
     kern = {k: float(np.mean([p[k] for p in profs])) for k in
