@@ -20,6 +20,19 @@ constexpr int kWarp = 32;
 
 __device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
 
+// Hardware approximations (a few ulp): used only where a result feeds a
+// conservative filter with ample slack, never in a decision the oracle checks.
+__device__ __forceinline__ float approx_sqrt(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float approx_rcp(float x) {
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  A round maps the counter
 // (c0, c1, c2, c3) under key (k0, k1) to
@@ -149,7 +162,10 @@ __device__ __forceinline__ float di_cost(const float* s0, const float* s1, float
 // with A = |dv|^2, B = 3 D^2.  f is convex with f'(t) = 0 at
 // t^2 = (A + sqrt(A^2 + 12 B)) / 2, so min over (0, r] of f is f(min(t, r)).
 // A pair whose bound reaches r (inflated by 1% to absorb FP32 rounding, far
-// above the few-ulp error of either side) cannot be an edge.
+// above the few-ulp error of either side) cannot be an edge.  The bound only
+// filters (the exact procedure decides every pair it keeps), so it may use the
+// fast reciprocal and square-root approximations: their few-ulp error is far
+// inside the 1% slack.
 __device__ __forceinline__ bool di_may_connect(const float* s0, const float* s1, float r) {
     const float rr = r * 1.01f;
     float A = 0.0f, qs = 0.0f, ss = 0.0f, q[3], sv[3];
@@ -163,7 +179,7 @@ __device__ __forceinline__ bool di_may_connect(const float* s0, const float* s1,
         ss = ss + sv[ax] * sv[ax];
     }
     if (4.0f * A >= rr * rr) return false;  // f >= 2 sqrt(A)
-    float t = ss > 0.0f ? qs / ss : 0.0f;
+    float t = ss > 0.0f ? __fdividef(qs, ss) : 0.0f;
     t = fminf(fmaxf(t, 0.0f), rr);
     float D2 = 0.0f;
 #pragma unroll
@@ -172,10 +188,11 @@ __device__ __forceinline__ bool di_may_connect(const float* s0, const float* s1,
         D2 = D2 + e * e;
     }
     const float B = 3.0f * D2;
-    float tau = sqrtf(0.5f * (A + sqrtf(A * A + 12.0f * B)));
+    float tau = approx_sqrt(0.5f * (A + approx_sqrt(A * A + 12.0f * B)));
     tau = fminf(tau, rr);
     if (!(tau > 0.0f)) return true;
-    const float f = tau + A / tau + B / (tau * tau * tau);
+    const float inv = approx_rcp(tau);
+    const float f = tau + A * inv + B * (inv * inv * inv);
     return f < rr;
 }
 

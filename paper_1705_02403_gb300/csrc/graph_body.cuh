@@ -146,8 +146,14 @@ __device__ __forceinline__ void mask_tile(const SpaceArgs& s, const float* __res
 // the exact test on all of them at once (every lane busy), ORing the verdicts
 // into per-row words kept in shared memory.  Rows are the lanes' own rows, so
 // a queued pair fetches its row state from the owning lane with a shuffle.
-constexpr int kDIRows = 128;   // rows (threads) per block: 4 warps
-constexpr int kDIWords = 4;    // 32-column words per block (128 staged columns)
+#ifndef GMT_DI_ROWS
+#define GMT_DI_ROWS 128
+#endif
+#ifndef GMT_DI_WORDS
+#define GMT_DI_WORDS 1
+#endif
+constexpr int kDIRows = GMT_DI_ROWS;    // rows (threads) per block
+constexpr int kDIWords = GMT_DI_WORDS;  // 32-column words per block (staged columns); 1 measured fastest
 
 // One block of kDIRows threads: rows bx*kDIRows.., words by*kDIWords..
 __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __restrict__ X,
