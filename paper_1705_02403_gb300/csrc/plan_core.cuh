@@ -1,0 +1,140 @@
+// Team synchronisation primitives and the lazy edge checks shared by the
+// wavefront kernels (plan.cu: one query per team; plan_multi.cu: all queries
+// of a batch advancing together).
+#pragma once
+
+#include <climits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gmtk {
+
+constexpr int kDefaultSpinLimit = 1 << 22;
+
+__device__ __forceinline__ int ldcg_i(const int* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned ldcg_u(const unsigned* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldcg_f(const float* p) { return __ldcg(p); }
+
+struct BlockTeam {
+    __device__ __forceinline__ int id() const { return blockIdx.x; }
+    __device__ __forceinline__ int rank() const { return threadIdx.x; }
+    __device__ __forceinline__ int size() const { return blockDim.x; }
+    __device__ __forceinline__ bool sync(PlanCtl*) const {
+        __syncthreads();
+        return true;
+    }
+};
+
+// Sense-reversing barrier over all CTAs of a cooperative grid.  Every poll is
+// counted; after spin_limit polls (or once another CTA has reported an error)
+// the wait gives up, records GMT_ERR_TIMEOUT and returns false, so the kernel
+// ends with an error status instead of hanging.
+struct GridTeam {
+    unsigned expected;
+    int spin_limit;
+    __device__ __forceinline__ int id() const { return 0; }
+    __device__ __forceinline__ int rank() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ __forceinline__ int size() const { return gridDim.x * blockDim.x; }
+    __device__ bool sync(PlanCtl* ctl) const {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned gen = ld_acquire(&ctl->bar_gen);
+            const unsigned arrived = atom_add_acq_rel(&ctl->bar_count, 1u);
+            if (arrived == expected - 1) {
+                ctl->bar_count = 0;
+                st_release(&ctl->bar_gen, gen + 1);
+            } else {
+                int spins = 0;
+                while (ld_acquire(&ctl->bar_gen) == gen) {
+                    if (ld_volatile(&ctl->error) != 0) break;
+                    if (++spins > spin_limit) {
+                        atomicCAS(&ctl->error, 0, (int)GMT_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        return ld_volatile(&ctl->error) == 0;
+    }
+};
+
+// All CTAs of one thread-block cluster (up to 16 SMs of a GPC).  The barrier
+// is the hardware cluster barrier (arrive.release / wait.acquire at cluster
+// scope); it cannot wait forever because every thread of the cluster reaches
+// every barrier (all exits from the iteration loop are uniform).
+struct ClusterTeam {
+    __device__ __forceinline__ static unsigned cta_rank() {
+        unsigned r;
+        asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+        return r;
+    }
+    __device__ __forceinline__ static unsigned ctas() {
+        unsigned n;
+        asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+        return n;
+    }
+    __device__ __forceinline__ int id() const { return (int)(blockIdx.x / ctas()); }
+    __device__ __forceinline__ int rank() const { return (int)(cta_rank() * blockDim.x + threadIdx.x); }
+    __device__ __forceinline__ int size() const { return (int)(ctas() * blockDim.x); }
+    __device__ __forceinline__ bool sync(PlanCtl*) const {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        return true;
+    }
+};
+
+// ---------------------------------------------------------------- edge check
+// Geometric edge y -> x of length L: m = max(2, ceil(L/spacing) + 1) points
+// p_k = y + t_k (x - y), t_k = k/(m-1); collision if one lies in a closed box.
+template <int DP>
+__device__ bool segment_free_warp(const float* y, const float* x, float L, float spacing, const float* blo,
+                                  const float* bhi, int nbox) {
+    const int lane = threadIdx.x & 31;
+    int m = (int)ceilf(L / spacing) + 1;
+    if (m < 2) m = 2;
+    const float denom = (float)(m - 1);
+    for (int k0 = 0; k0 < m; k0 += 32) {
+        const int k = k0 + lane;
+        bool hit = false;
+        if (k < m) {
+            const float t = (float)k / denom;
+            float p[DP];
+#pragma unroll
+            for (int a = 0; a < DP; ++a) p[a] = y[a] + t * (x[a] - y[a]);
+            hit = in_any_box<DP>(p, blo, bhi, nbox);
+        }
+        if (__any_sync(0xffffffffu, hit)) return false;
+    }
+    return true;
+}
+
+// Double-integrator edge: `points` samples of the Hermite trajectory at
+// s_k = k/(points-1); collision if one lies in a box or outside the position
+// bounds.
+__device__ bool trajectory_free_warp(const float* y, const float* x, float tau, int points, const float* plo,
+                                     const float* phi, const float* blo, const float* bhi, int nbox) {
+    const int lane = threadIdx.x & 31;
+    const float denom = (float)(points - 1);
+    for (int k0 = 0; k0 < points; k0 += 32) {
+        const int k = k0 + lane;
+        bool hit = false;
+        if (k < points) {
+            const float s = (float)k / denom;
+            float p[3];
+            hermite_point(y, x, tau, s, p);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) hit = hit || p[a] < plo[a] || p[a] > phi[a];
+            hit = hit || in_any_box<3>(p, blo, bhi, nbox);
+        }
+        if (__any_sync(0xffffffffu, hit)) return false;
+    }
+    return true;
+}
+
+// Largest box count staged in shared memory (2 * count * DP floats).
+__host__ __device__ constexpr int smem_box_cap(int dp) { return 4096 / dp; }
+
+}  // namespace gmtk
