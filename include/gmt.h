@@ -225,9 +225,11 @@ typedef struct gmt_batch gmt_batch;
  *     device sequence is replayed from a CUDA graph captured on the first
  *     repeat (no host work between kernels); otherwise the batch is prepared
  *     anew (one host synchronisation to size the edge arrays).
- * Plan stage: one persistent launch per (kind, dim) group; teams (one CTA or
- * one cluster, see gmt_batch_set_launch / gmt_batch_autotune) take queries
- * from a device queue, largest edge count first.  Synchronises `stream`.
+ * Plan stage (see gmt_batch_set_mode): per (kind, dim) group, either one
+ * persistent launch whose teams (one CTA or one cluster) take queries from a
+ * device queue, largest edge count first, or one cooperative launch per 512
+ * queries in which all queries advance one iteration per grid step.  Both
+ * give every query the result of a single gmt_plan.  Synchronises `stream`.
  * Returns GMT_OK, or the first negative per-query status (all infos filled).
  * A query whose inputs changed in place so that its edge count outgrew the
  * replayed arena reports GMT_ERR_OOM in its info. */
@@ -238,15 +240,38 @@ gmt_status gmt_plan_batch(int32_t q, const gmt_query* queries, gmt_batch** batch
  * non-NULL) in the batch arena, valid until the next preparing call. */
 gmt_status gmt_batch_get_view(const gmt_batch* batch, int32_t k, gmt_graph_view* view, int32_t** path);
 
-/* Team shape of the batched plan stage: cluster = CTAs per team (1, 2, 4, 8
- * or 16; 0 = tuned/automatic), threads per CTA (0 = tuned/automatic). */
+/* Plan-stage scheme of a batch.
+ *   GMT_BATCH_TEAMS: one persistent launch per group; a team (a CTA or a
+ *     cluster) runs one query at a time with team barriers.
+ *   GMT_BATCH_LOCKSTEP: one cooperative grid runs up to 512 queries at once,
+ *     one Algorithm 1 iteration of every live query per grid step (two
+ *     bounded grid barriers per step), so small groups of many queries fill
+ *     the GPU together.
+ *   GMT_BATCH_AUTO: the autotuner's choice; before tuning, lockstep when the
+ *     queries average at most 2048 nodes, else teams. */
+typedef enum { GMT_BATCH_AUTO = 0, GMT_BATCH_TEAMS = 1, GMT_BATCH_LOCKSTEP = 2 } gmt_batch_mode;
+gmt_status gmt_batch_set_mode(gmt_batch* batch, int32_t mode);
+
+/* Launch shape of the batched plan stage: cluster = CTAs per team (teams
+ * scheme only: 1, 2, 4, 8 or 16; 0 = tuned/automatic), threads per CTA (both
+ * schemes; 0 = tuned/automatic). */
 gmt_status gmt_batch_set_launch(gmt_batch* batch, int32_t cluster, int32_t threads);
 
+/* The scheme and shape the next plan stage will use (outputs may be NULL);
+ * cluster is 0 under the lockstep scheme. */
+gmt_status gmt_batch_get_launch(const gmt_batch* batch, int32_t* mode, int32_t* cluster, int32_t* threads);
+
 /* Autotuner: on a batch planned at least once, times the plan stage for every
- * team shape (cluster 1..16 x 256/512/1024 threads) on `stream`, keeps the
- * fastest as the automatic shape, and reports it (outputs may be NULL). */
+ * team shape (cluster 1..16 x 256/512/1024 threads) and every lockstep shape
+ * (256/512/1024 threads) on `stream`, keeps the fastest as the automatic
+ * scheme and shape, and reports it (outputs may be NULL; best_cluster is 0
+ * when lockstep wins, see gmt_batch_get_launch). */
 gmt_status gmt_batch_autotune(gmt_batch* batch, gmt_stream stream, int32_t* best_cluster, int32_t* best_threads,
                               float* best_ms);
+
+/* Device time of the plan stage (all plan launches, without the graph build)
+ * of the last completed gmt_plan_batch or autotune call, in milliseconds. */
+gmt_status gmt_batch_last_plan_ms(const gmt_batch* batch, float* ms);
 
 void gmt_batch_free(gmt_batch* batch);
 

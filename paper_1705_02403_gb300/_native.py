@@ -130,7 +130,10 @@ SIGNATURES = {
     "gmt_plan_batch": (_I32, [_I32, C.POINTER(gmt_query), C.POINTER(C.c_void_p), _P, _P, C.POINTER(gmt_plan_info),
                               _P]),
     "gmt_batch_get_view": (_I32, [_P, _I32, C.POINTER(gmt_graph_view), C.POINTER(C.c_void_p)]),
+    "gmt_batch_set_mode": (_I32, [_P, _I32]),
     "gmt_batch_set_launch": (_I32, [_P, _I32, _I32]),
+    "gmt_batch_get_launch": (_I32, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
+    "gmt_batch_last_plan_ms": (_I32, [_P, C.POINTER(_F32)]),
     "gmt_batch_autotune": (_I32, [_P, _P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_F32)]),
     "gmt_batch_free": (None, [_P]),
     "gmt_gemm_bf16": (_I32, [_I32, _I32, _I32, _P, _P, _I32, _P, _P, _P, _I32, _P, _P, _P]),
@@ -300,8 +303,29 @@ def gmt_batch_get_view(batch: Batch, k: int):
     return v, path.value
 
 
+BATCH_AUTO, BATCH_TEAMS, BATCH_LOCKSTEP = 0, 1, 2
+
+
+def gmt_batch_set_mode(batch: Batch, mode: int) -> None:
+    _check(lib.gmt_batch_set_mode(batch.handle, mode))
+
+
 def gmt_batch_set_launch(batch: Batch, cluster: int, threads: int) -> None:
     _check(lib.gmt_batch_set_launch(batch.handle, cluster, threads))
+
+
+def gmt_batch_get_launch(batch: Batch):
+    """(mode, cluster, threads) of the next plan stage."""
+    m, c, t = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib.gmt_batch_get_launch(batch.handle, C.byref(m), C.byref(c), C.byref(t)))
+    return m.value, c.value, t.value
+
+
+def gmt_batch_last_plan_ms(batch: Batch) -> float:
+    """Device time of the last call's plan stage (ms)."""
+    ms = C.c_float()
+    _check(lib.gmt_batch_last_plan_ms(batch.handle, C.byref(ms)))
+    return ms.value
 
 
 def gmt_batch_autotune(batch: Batch, stream=None):

@@ -217,6 +217,10 @@ struct Group {
     int max_n = 0, max_boxes = 0;
     DevBuf desc, off_nodes, off_tiles, off_tasks, off_rows, order, args;
     std::vector<int> order_h;
+    // lockstep scheme: members [chunk_start[c], chunk_start[c] + chunk_count[c])
+    // run in one launch; their node offsets start at lock_base + chunk_base[c]
+    std::vector<int> chunk_start, chunk_count, chunk_nodes, chunk_base, chunk_ctl;
+    DevBuf lock_base;
 };
 
 }  // namespace
@@ -233,12 +237,16 @@ struct gmt_batch {
     // arena
     DevBuf X, goal, flags, mask, maskT, counts, rows, edges_i, edges_f, path, ctl, next, slot;
     DevBuf s_ocost, s_stamp, s_lists;
+    DevBuf l_open, l_glist, l_ocost, l_stamp, l_ctl;
+    int lock_chunks = 0;
+    cudaEvent_t ev_plan[2] = {nullptr, nullptr};  // around the plan stage of every call
     PlanCtl* h_ctl = nullptr;
     int* h_rows = nullptr;
     size_t h_cap = 0;
-    // launch shape of the plan stage
+    // scheme and launch shape of the plan stage
+    int mode = GMT_BATCH_AUTO;
     int cluster = 0, threads = 0;      // 0 = automatic / tuned
-    int tuned_cluster = 0, tuned_threads = 0;
+    int tuned_mode = GMT_BATCH_AUTO, tuned_cluster = 0, tuned_threads = 0;
     // captured replay
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -254,6 +262,8 @@ struct gmt_batch {
         if (h_ctl) cudaFreeHost(h_ctl);
         if (h_rows) cudaFreeHost(h_rows);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        for (cudaEvent_t e : ev_plan)
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -304,6 +314,35 @@ void info_from_ctl(const PlanCtl& c, gmt_plan_info* info) {
     info->tree_size = (int64_t)c.tree_size;
 }
 
+// Under stream capture an event record becomes a graph node only with the
+// external flag; outside capture it is an ordinary record.
+cudaError_t record_plan_event(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t err = cudaStreamIsCapturing(st, &cs);
+    if (err != cudaSuccess) return err;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal)
+                                               : cudaEventRecord(e, st);
+}
+
+// Untuned choice: lockstep pays two grid barriers per step but keeps the whole
+// GPU busy when every query is small; teams win once queries are large enough
+// to fill a team each (measured crossover: a few thousand nodes per query).
+constexpr long long kLockstepMeanNodes = 2048;
+
+int plan_mode(const gmt_batch* b) {
+    if (b->mode != GMT_BATCH_AUTO) return b->mode;
+    if (b->tuned_mode != GMT_BATCH_AUTO) return b->tuned_mode;
+    if (b->node_base.empty()) return GMT_BATCH_LOCKSTEP;
+    return b->node_base.back() <= kLockstepMeanNodes * b->q ? GMT_BATCH_LOCKSTEP : GMT_BATCH_TEAMS;
+}
+
+// Lockstep launch shape for a group: (threads, co-resident blocks).
+void lock_shape(const gmt_batch* b, const Group& g, int* threads, int* blocks) {
+    const int t = b->threads > 0 ? b->threads : (b->tuned_threads > 0 ? b->tuned_threads : 512);
+    *threads = t;
+    *blocks = plan_lockstep_max_blocks(g.kind, g.dp, t);
+}
+
 // Plan-stage launch shape for a group: (cluster, threads, teams).
 void plan_shape(const gmt_batch* b, const Group& g, int* cluster, int* threads, int* teams) {
     int c = b->cluster > 0 ? b->cluster : (b->tuned_cluster > 0 ? b->tuned_cluster : 2);
@@ -350,6 +389,36 @@ gmt_status enqueue_build_back(gmt_batch* b, int32_t* parent, float* cost, cudaSt
             BCUDA(batch_fill(g.kind, g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, true, st), "batched fill");
     }
     BCUDA(cudaMemsetAsync(b->ctl.p, 0, b->ctl.cap, st), "memset");
+    for (cudaEvent_t& e : b->ev_plan)
+        if (!e) BCUDA(cudaEventCreate(&e), "event");
+    BCUDA(record_plan_event(b->ev_plan[0], st), "event");
+    if (plan_mode(b) == GMT_BATCH_LOCKSTEP) {
+        BCUDA(cudaMemsetAsync(b->l_ctl.p, 0, b->l_ctl.cap, st), "memset");
+        for (Group& g : b->groups) {
+            int threads, blocks;
+            lock_shape(b, g, &threads, &blocks);
+            if (blocks <= 0) return bfail(GMT_ERR_CUDA, "lockstep plan kernel cannot be resident");
+            for (size_t c = 0; c < g.chunk_start.size(); ++c) {
+                LockScratch sc;
+                sc.ctl = b->l_ctl.as<LockCtl>() + g.chunk_ctl[c];
+                sc.open[0] = b->l_open.as<int4>();
+                sc.open[1] = sc.open[0] + g.chunk_nodes[c];
+                sc.glist[0] = b->l_glist.as<int2>();
+                sc.glist[1] = sc.glist[0] + g.chunk_nodes[c];
+                sc.ocost = b->l_ocost.as<float>();
+                sc.stamp = b->l_stamp.as<int>();
+                sc.base = g.lock_base.as<int>() + g.chunk_base[c];
+                sc.nodes = g.chunk_nodes[c];
+                BCUDA(launch_plan_lockstep(g.kind, g.dp, g.args.as<PlanArgs>() + g.chunk_start[c], g.chunk_count[c], sc,
+                                           blocks, threads, st),
+                      "lockstep plan kernel");
+            }
+        }
+        BCUDA(record_plan_event(b->ev_plan[1], st), "event");
+        BCUDA(cudaMemcpyAsync(b->h_ctl, b->ctl.p, (size_t)b->q * kCtlSlotB, cudaMemcpyDeviceToHost, st),
+              "result copy");
+        return GMT_OK;
+    }
     BCUDA(cudaMemsetAsync(b->next.p, 0, b->next.cap, st), "memset");
     int gi = 0;
     for (Group& g : b->groups) {
@@ -367,6 +436,7 @@ gmt_status enqueue_build_back(gmt_batch* b, int32_t* parent, float* cost, cudaSt
               "batched plan kernel");
         ++gi;
     }
+    BCUDA(record_plan_event(b->ev_plan[1], st), "event");
     (void)parent;
     (void)cost;
     BCUDA(cudaMemcpyAsync(b->h_ctl, b->ctl.p, (size_t)b->q * kCtlSlotB, cudaMemcpyDeviceToHost, st), "result copy");
@@ -579,6 +649,39 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         BCUDA(cudaStreamSynchronize(st), "upload");
         max_n = std::max(max_n, g.max_n);
     }
+    // lockstep chunks: up to kLockMaxQueries members per launch
+    size_t lock_nodes = 1;
+    int chunks = 0;
+    for (Group& g : b->groups) {
+        const int nq = (int)g.members.size();
+        g.chunk_start.clear(); g.chunk_count.clear(); g.chunk_nodes.clear(); g.chunk_base.clear(); g.chunk_ctl.clear();
+        std::vector<int> base;
+        for (int c0 = 0; c0 < nq; c0 += kLockMaxQueries) {
+            const int cnt = std::min(kLockMaxQueries, nq - c0);
+            g.chunk_start.push_back(c0);
+            g.chunk_count.push_back(cnt);
+            g.chunk_base.push_back((int)base.size());
+            g.chunk_ctl.push_back(chunks++);
+            long long acc = 0;
+            for (int i = 0; i < cnt; ++i) {
+                base.push_back((int)acc);
+                acc += b->N[g.members[c0 + i]];
+            }
+            if (acc > (1ll << 30)) return bfail(GMT_ERR_INVALID, "too many nodes in one lockstep launch");
+            base.push_back((int)acc);
+            g.chunk_nodes.push_back((int)acc);
+            lock_nodes = std::max(lock_nodes, (size_t)acc);
+        }
+        BCUDA(g.lock_base.need(base.size() * 4), "lockstep offsets");
+        BCUDA(cudaMemcpyAsync(g.lock_base.p, base.data(), base.size() * 4, cudaMemcpyHostToDevice, st), "upload");
+        BCUDA(cudaStreamSynchronize(st), "upload");
+    }
+    BCUDA(b->l_open.need(2 * lock_nodes * sizeof(int4)), "lockstep scratch");
+    BCUDA(b->l_glist.need(2 * lock_nodes * sizeof(int2)), "lockstep scratch");
+    BCUDA(b->l_ocost.need(lock_nodes * 4), "lockstep scratch");
+    BCUDA(b->l_stamp.need(lock_nodes * 4), "lockstep scratch");
+    BCUDA(b->l_ctl.need((size_t)chunks * sizeof(LockCtl)), "lockstep scratch");
+    b->lock_chunks = chunks;
     // scratch for the most teams any shape can run
     int max_teams = 0;
     for (Group& g : b->groups)
@@ -669,6 +772,16 @@ gmt_status gmt_batch_get_view(const gmt_batch* b, int32_t k, gmt_graph_view* v, 
     return GMT_OK;
 }
 
+gmt_status gmt_batch_set_mode(gmt_batch* b, int32_t mode) {
+    if (!b) return bfail(GMT_ERR_INVALID, "batch is NULL");
+    if (mode != GMT_BATCH_AUTO && mode != GMT_BATCH_TEAMS && mode != GMT_BATCH_LOCKSTEP)
+        return bfail(GMT_ERR_INVALID, "mode must be GMT_BATCH_AUTO, GMT_BATCH_TEAMS or GMT_BATCH_LOCKSTEP");
+    b->mode = mode;
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    return GMT_OK;
+}
+
 gmt_status gmt_batch_set_launch(gmt_batch* b, int32_t cluster, int32_t threads) {
     if (!b) return bfail(GMT_ERR_INVALID, "batch is NULL");
     if (cluster < 0 || cluster > 16 || (cluster & (cluster - 1)) != 0)
@@ -682,46 +795,79 @@ gmt_status gmt_batch_set_launch(gmt_batch* b, int32_t cluster, int32_t threads) 
     return GMT_OK;
 }
 
+gmt_status gmt_batch_get_launch(const gmt_batch* b, int32_t* mode, int32_t* cluster, int32_t* threads) {
+    if (!b) return bfail(GMT_ERR_INVALID, "batch is NULL");
+    const int m = plan_mode(b);
+    int c = 0, t = 0;
+    if (m == GMT_BATCH_LOCKSTEP) {
+        t = b->threads > 0 ? b->threads : (b->tuned_threads > 0 ? b->tuned_threads : 512);
+    } else {
+        c = b->cluster > 0 ? b->cluster : (b->tuned_cluster > 0 ? b->tuned_cluster : 2);
+        t = b->threads > 0 ? b->threads : (b->tuned_threads > 0 ? b->tuned_threads : 512);
+    }
+    if (mode) *mode = m;
+    if (cluster) *cluster = c;
+    if (threads) *threads = t;
+    return GMT_OK;
+}
+
 gmt_status gmt_batch_autotune(gmt_batch* b, gmt_stream stream, int32_t* best_cluster, int32_t* best_threads,
                               float* best_ms) {
     if (!b || !b->prepared) return bfail(GMT_ERR_INVALID, "autotune needs a batch planned once");
     cudaStream_t st = (cudaStream_t)stream;
-    const int keep_c = b->cluster, keep_t = b->threads;
+    const int keep_m = b->mode, keep_c = b->cluster, keep_t = b->threads;
     cudaEvent_t e0, e1;
     BCUDA(cudaEventCreate(&e0), "event");
     BCUDA(cudaEventCreate(&e1), "event");
     float best = INFINITY;
-    int bc = 0, bt = 0;
-    for (int c : {1, 2, 4, 8, 16}) {
-        for (int t : {256, 512, 1024}) {
-            b->cluster = c;
-            b->threads = t;
-            int cc, tt, teams;
-            bool ok = true;
-            for (Group& g : b->groups) {
+    int bm = GMT_BATCH_AUTO, bc = 0, bt = 0;
+    struct Shape { int mode, cluster, threads; };
+    std::vector<Shape> shapes;
+    for (int t : {256, 512, 1024}) shapes.push_back({GMT_BATCH_LOCKSTEP, 0, t});
+    for (int c : {1, 2, 4, 8, 16})
+        for (int t : {256, 512, 1024}) shapes.push_back({GMT_BATCH_TEAMS, c, t});
+    gmt_status fail = GMT_OK;
+    for (const Shape& sh : shapes) {
+        b->mode = sh.mode;
+        b->cluster = sh.cluster;
+        b->threads = sh.threads;
+        bool ok = true;
+        for (Group& g : b->groups) {
+            if (sh.mode == GMT_BATCH_LOCKSTEP) {
+                int tt, blocks;
+                lock_shape(b, g, &tt, &blocks);
+                if (blocks <= 0) ok = false;
+            } else {
+                int cc, tt, teams;
                 plan_shape(b, g, &cc, &tt, &teams);
-                if (cc != c || teams <= 0) ok = false;
+                if (cc != sh.cluster || teams <= 0) ok = false;
             }
-            cudaGetLastError();
-            if (!ok) continue;
-            float ms_sum = 0.0f;
-            for (int rep = 0; rep < 2; ++rep) {
-                BCUDA(cudaEventRecord(e0, st), "event");
-                gmt_status s = enqueue_build_back(b, b->cap_parent, b->cap_cost, st);
-                if (s != GMT_OK) return s;
-                BCUDA(cudaEventRecord(e1, st), "event");
-                BCUDA(cudaEventSynchronize(e1), "event");
-                float ms = 0.0f;
-                BCUDA(cudaEventElapsedTime(&ms, e0, e1), "event");
-                if (rep > 0) ms_sum += ms;
-            }
-            if (ms_sum < best) { best = ms_sum; bc = c; bt = t; }
         }
+        cudaGetLastError();
+        if (!ok) continue;
+        float ms_sum = 0.0f;
+        for (int rep = 0; rep < 2 && fail == GMT_OK; ++rep) {
+            cudaError_t e = cudaEventRecord(e0, st);
+            if (e != cudaSuccess) { fail = bcuda(e, "event"); break; }
+            fail = enqueue_build_back(b, b->cap_parent, b->cap_cost, st);
+            if (fail != GMT_OK) break;
+            e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) { fail = bcuda(e, "event"); break; }
+            if (rep > 0) ms_sum += ms;
+        }
+        if (fail != GMT_OK) break;
+        if (ms_sum < best) { best = ms_sum; bm = sh.mode; bc = sh.cluster; bt = sh.threads; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    b->mode = keep_m;
     b->cluster = keep_c;
     b->threads = keep_t;
+    if (fail != GMT_OK) return fail;
+    b->tuned_mode = bm;
     b->tuned_cluster = bc;
     b->tuned_threads = bt;
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
@@ -729,6 +875,12 @@ gmt_status gmt_batch_autotune(gmt_batch* b, gmt_stream stream, int32_t* best_clu
     if (best_cluster) *best_cluster = bc;
     if (best_threads) *best_threads = bt;
     if (best_ms) *best_ms = best;
+    return GMT_OK;
+}
+
+gmt_status gmt_batch_last_plan_ms(const gmt_batch* b, float* ms) {
+    if (!b || !ms || !b->ev_plan[0] || !b->ev_plan[1]) return bfail(GMT_ERR_INVALID, "no plan stage has run");
+    BCUDA(cudaEventElapsedTime(ms, b->ev_plan[0], b->ev_plan[1]), "event");
     return GMT_OK;
 }
 

@@ -131,6 +131,34 @@ struct BatchScratch {
     int max_nodes;
 };
 
+// Lockstep batched wavefront (plan_multi.cu).  At most kLockMaxQueries
+// queries per launch; every block queues up to kLockQueue candidates per
+// super-iteration in shared memory (further claims are pulled at once by the
+// warp that made them).
+constexpr int kLockMaxQueries = 512;
+constexpr int kLockQueue = 1024;
+
+// Grid-wide counters of one lockstep launch (zeroed by the caller).  Open
+// list j holds its kept entries in [0, keep) and its newly opened ones in
+// [nodes - new_total[j], nodes).  gk[j] packs two counters that grow in the
+// same phase: the low half counts group list j, the high half the kept
+// entries of open list j ^ 1.
+struct LockCtl {
+    PlanCtl team;  // barrier and error flag
+    unsigned long long gk[2];
+    int new_total[2];
+};
+
+struct LockScratch {
+    LockCtl* ctl;
+    int4* open[2];    // (node, cost bits, query, 0); `nodes` entries each
+    int2* glist[2];   // (query, node); `nodes` entries each
+    float* ocost;     // open-snapshot cost of every node of every query
+    int* stamp;       // claim stamp of every node (INT_MAX: in the tree)
+    const int* base;  // nq + 1 node offsets: query k owns [base[k], base[k+1])
+    int nodes;        // base[nq]
+};
+
 // mlp.cu: C = A . B^T on the tensor cores (BF16 in, FP32 accumulate);
 // epilogue 0 = FP32 store, 1 = BF16 relu(x + bias), 2 = FP32 x + bias.
 cudaError_t gemm_bf16_tn(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, int epilogue,
@@ -161,5 +189,11 @@ cudaError_t launch_plan_batch(int kind, int dp, const PlanArgs* queries, const i
                               int* slot, const BatchScratch& scratch, int teams, int threads, int cluster,
                               int max_boxes, cudaStream_t st);
 int plan_batch_max_teams(int kind, int dp, int threads, int cluster);
+// plan_multi.cu: one cooperative grid of `blocks` CTAs advances all `nq`
+// queries of one (kind, dp) group together (nq <= kLockMaxQueries).  The
+// queries' PlanCtl blocks must be zeroed before the launch.
+cudaError_t launch_plan_lockstep(int kind, int dp, const PlanArgs* queries, int nq, const LockScratch& s, int blocks,
+                                 int threads, cudaStream_t st);
+int plan_lockstep_max_blocks(int kind, int dp, int threads);
 
 }  // namespace gmtk

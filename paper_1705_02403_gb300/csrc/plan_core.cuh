@@ -87,8 +87,26 @@ struct ClusterTeam {
 };
 
 // ---------------------------------------------------------------- edge check
+// Both checks first keep only the boxes that meet an axis-aligned bound of
+// every point the check will evaluate (one box per lane, 32 at a time), then
+// test the points against those boxes alone.  The bound is inflated by far
+// more than the rounding of the point formulas, so a box that holds one of
+// the computed points is never dropped: the verdict equals testing every
+// point against every box.
+
+// Does box b meet [lo, hi] (closed intervals on all DP axes)?
+template <int DP>
+__device__ __forceinline__ bool box_meets(const float* blo, const float* bhi, int b, const float* lo,
+                                          const float* hi) {
+    bool m = true;
+#pragma unroll
+    for (int a = 0; a < DP; ++a) m = m && blo[b * DP + a] <= hi[a] && lo[a] <= bhi[b * DP + a];
+    return m;
+}
+
 // Geometric edge y -> x of length L: m = max(2, ceil(L/spacing) + 1) points
 // p_k = y + t_k (x - y), t_k = k/(m-1); collision if one lies in a closed box.
+// Every computed p_k lies within a few ulps of the segment's bounding box.
 template <int DP>
 __device__ bool segment_free_warp(const float* y, const float* x, float L, float spacing, const float* blo,
                                   const float* bhi, int nbox) {
@@ -96,38 +114,68 @@ __device__ bool segment_free_warp(const float* y, const float* x, float L, float
     int m = (int)ceilf(L / spacing) + 1;
     if (m < 2) m = 2;
     const float denom = (float)(m - 1);
-    for (int k0 = 0; k0 < m; k0 += 32) {
-        const int k = k0 + lane;
-        bool hit = false;
-        if (k < m) {
-            const float t = (float)k / denom;
-            float p[DP];
+    float lo[DP], hi[DP];
 #pragma unroll
-            for (int a = 0; a < DP; ++a) p[a] = y[a] + t * (x[a] - y[a]);
-            hit = in_any_box<DP>(p, blo, bhi, nbox);
+    for (int a = 0; a < DP; ++a) {
+        const float e = 1e-5f * (fabsf(x[a]) + fabsf(y[a])) + 1e-30f;
+        lo[a] = fminf(x[a], y[a]) - e;
+        hi[a] = fmaxf(x[a], y[a]) + e;
+    }
+    for (int b0 = 0; b0 < nbox; b0 += 32) {
+        const int b = b0 + lane;
+        const unsigned near = __ballot_sync(0xffffffffu, b < nbox && box_meets<DP>(blo, bhi, b, lo, hi));
+        if (!near) continue;
+        for (int k0 = 0; k0 < m; k0 += 32) {
+            const int k = k0 + lane;
+            bool hit = false;
+            if (k < m) {
+                const float t = (float)k / denom;
+                float p[DP];
+#pragma unroll
+                for (int a = 0; a < DP; ++a) p[a] = y[a] + t * (x[a] - y[a]);
+                for (unsigned w = near; w; w &= w - 1) hit = hit || in_box<DP>(p, blo, bhi, b0 + __ffs(w) - 1);
+            }
+            if (__any_sync(0xffffffffu, hit)) return false;
         }
-        if (__any_sync(0xffffffffu, hit)) return false;
     }
     return true;
 }
 
 // Double-integrator edge: `points` samples of the Hermite trajectory at
 // s_k = k/(points-1); collision if one lies in a box or outside the position
-// bounds.
-__device__ bool trajectory_free_warp(const float* y, const float* x, float tau, int points, const float* plo,
+// bounds.  The cubic lies in the convex hull of its Bezier control points
+// p0, p0 + tau v0 / 3, p1 - tau v1 / 3, p1, whose bounding box (inflated)
+// selects the boxes.
+__device__ inline bool trajectory_free_warp(const float* y, const float* x, float tau, int points, const float* plo,
                                      const float* phi, const float* blo, const float* bhi, int nbox) {
     const int lane = threadIdx.x & 31;
     const float denom = (float)(points - 1);
+    float lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float c1 = y[a] + tau * y[3 + a] / 3.0f, c2 = x[a] - tau * x[3 + a] / 3.0f;
+        const float e = 1e-5f * (fabsf(y[a]) + fabsf(x[a]) + tau * (fabsf(y[3 + a]) + fabsf(x[3 + a]))) + 1e-30f;
+        lo[a] = fminf(fminf(y[a], x[a]), fminf(c1, c2)) - e;
+        hi[a] = fmaxf(fmaxf(y[a], x[a]), fmaxf(c1, c2)) + e;
+    }
+    unsigned near_first = 0;  // boxes 0..31, reused by the first chunk of points
+    if (nbox > 0) near_first = __ballot_sync(0xffffffffu, lane < nbox && box_meets<3>(blo, bhi, lane, lo, hi));
     for (int k0 = 0; k0 < points; k0 += 32) {
         const int k = k0 + lane;
         bool hit = false;
+        float p[3];
         if (k < points) {
             const float s = (float)k / denom;
-            float p[3];
             hermite_point(y, x, tau, s, p);
 #pragma unroll
             for (int a = 0; a < 3; ++a) hit = hit || p[a] < plo[a] || p[a] > phi[a];
-            hit = hit || in_any_box<3>(p, blo, bhi, nbox);
+        }
+        for (int b0 = 0; b0 < nbox; b0 += 32) {
+            const unsigned near =
+                b0 == 0 ? near_first
+                        : __ballot_sync(0xffffffffu, b0 + lane < nbox && box_meets<3>(blo, bhi, b0 + lane, lo, hi));
+            if (k < points)
+                for (unsigned w = near; w; w &= w - 1) hit = hit || in_box<3>(p, blo, bhi, b0 + __ffs(w) - 1);
         }
         if (__any_sync(0xffffffffu, hit)) return false;
     }

@@ -3,8 +3,9 @@
 Every query of a mixed batch (2D and 3D geometric, double integrator; uneven
 n, own seeds, own boxes, Theorem 1 radii) must produce the same samples, CSR,
 parents, costs and counters as the oracle on that query alone; a repeated call
-(replayed from the captured CUDA graph) must give the same bits again; every
-team shape gives the same trees.
+(replayed from the captured CUDA graph) must give the same bits again; both
+plan-stage schemes (teams, lockstep) and every launch shape give the same
+trees.
 """
 import numpy as np
 import pytest
@@ -75,6 +76,8 @@ def test_mixed_batch_matches_oracle_and_replays(O):
     # a third call replays the same graph again
     infos3 = bp.plan()
     assert infos3 == infos2
+    from paper_1705_02403_gb300 import _native as N
+    assert N.gmt_batch_last_plan_ms(bp.batch) > 0.0
 
 
 @pytest.mark.parametrize("shape", [(1, 256), (1, 1024), (2, 512), (4, 512), (8, 1024), (16, 512)])
@@ -82,12 +85,100 @@ def test_every_team_shape_gives_the_same_trees(O, shape):
     from paper_1705_02403_gb300 import _native as N
     from paper_1705_02403_gb300.planner import BatchPlanner
     bp = BatchPlanner(mixed_batch(seed=1, q=10))
-    N.gmt_batch_set_launch(bp.batch, *shape) if bp.batch.handle.value else None
     infos = bp.plan()
+    N.gmt_batch_set_mode(bp.batch, N.BATCH_TEAMS)
     N.gmt_batch_set_launch(bp.batch, *shape)
+    assert N.gmt_batch_get_launch(bp.batch) == (N.BATCH_TEAMS, shape[0], shape[1])
     infos = bp.plan()            # prepared once; this call replays with the shape
     for k in range(len(bp.problems)):
         check_query(O, bp, k, infos)
+
+
+@pytest.mark.parametrize("threads", [256, 512, 1024])
+def test_every_lockstep_shape_gives_the_same_trees(O, threads):
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import BatchPlanner
+    bp = BatchPlanner(mixed_batch(seed=4, q=12))
+    bp.plan()
+    N.gmt_batch_set_mode(bp.batch, N.BATCH_LOCKSTEP)
+    N.gmt_batch_set_launch(bp.batch, 0, threads)
+    assert N.gmt_batch_get_launch(bp.batch) == (N.BATCH_LOCKSTEP, 0, threads)
+    infos = bp.plan()
+    for k in range(len(bp.problems)):
+        check_query(O, bp, k, infos)
+
+
+def test_lockstep_and_teams_agree_bit_for_bit(O):
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import BatchPlanner
+    bp = BatchPlanner(mixed_batch(seed=3, q=16))
+    N_ = N
+    infos_l = bp.plan()
+    assert N_.gmt_batch_get_launch(bp.batch)[0] == N.BATCH_LOCKSTEP   # the untuned default for small queries
+    for k in range(len(bp.problems)):
+        check_query(O, bp, k, infos_l)
+    p_l, c_l = bp.parent.clone(), bp.cost.clone()
+    N.gmt_batch_set_mode(bp.batch, N.BATCH_TEAMS)
+    bp.parent.fill_(-9)
+    bp.cost.fill_(-9.0)
+    infos_t = bp.plan()
+    assert infos_t == infos_l
+    assert torch.equal(bp.parent, p_l)
+    assert torch.equal(bp.cost.view(torch.int32), c_l.view(torch.int32))
+
+
+def test_lockstep_runs_more_than_512_queries_in_chunks(O):
+    # 600 small queries: the lockstep scheme runs them as two launches
+    from paper_1705_02403_gb300.planner import BatchPlanner
+    qs = envgen.batch_queries(seed=5, q=600, n_min=16, n_max=200)
+    bp = BatchPlanner(qs)
+    infos = bp.plan()
+    for k in range(len(qs)):
+        check_query(O, bp, k, infos)
+
+
+def test_lockstep_candidate_queue_overflow(O):
+    # Nearly complete graphs: x_init alone claims more candidates in its first
+    # iteration than a block's shared-memory queue holds, so the pushing warp
+    # pulls the rest itself.
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import BatchPlanner
+    qs = [envgen.geometric(600 + k, d=2, n=1500, nbox=4, r=1.0) for k in range(2)]
+    qs += [envgen.geometric(610, d=3, n=1400, nbox=6, r=1.2)]
+    qs += envgen.batch_queries(seed=6, q=5, n_min=200, n_max=800)
+    bp = BatchPlanner(qs)
+    bp.plan()
+    N.gmt_batch_set_mode(bp.batch, N.BATCH_LOCKSTEP)
+    infos = bp.plan()
+    for k in range(len(qs)):
+        check_query(O, bp, k, infos)
+    assert max(bp.view(k)["E"] / qs[k].N for k in range(3)) > 1024
+
+
+@pytest.mark.parametrize("mode", ["lockstep", "teams"])
+def test_iteration_limit_per_query(O, mode):
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import BatchPlanner
+    qs = mixed_batch(seed=7, q=10)
+    bp = BatchPlanner(qs)
+    limits = {1: 1, 3: 4, 5: 2, 8: 6}
+    for k, m in limits.items():
+        bp.queries[k].params.max_iters = m
+    bp.plan(allow_errors=True)
+    N.gmt_batch_set_mode(bp.batch, N.BATCH_LOCKSTEP if mode == "lockstep" else N.BATCH_TEAMS)
+    infos = bp.plan(allow_errors=True)
+    for k, pb in enumerate(qs):
+        X, goal = O.sample(pb)
+        r = pb.r if pb.r > 0 else np.float32(O.radius_thm1(pb.n, pb.d))
+        g = O.Graph(pb.kind, pb.d, pb.dp, X, goal, r)
+        parent, cost, info = g.plan(pb.box_lo, pb.box_hi, pb.lo[:pb.dp], pb.hi[:pb.dp], pb.lam, pb.seg_spacing,
+                                    pb.traj_points, max_iters=limits.get(k))
+        p, c = bp.result(k)
+        assert np.array_equal(p.cpu().numpy(), parent), k
+        assert np.array_equal(bits(c.cpu().numpy()), bits(cost)), k
+        for key in INFO_KEYS:
+            assert infos[k][key] == info[key], (k, key)
+    assert any(infos[k]["status"] == N.GMT_ERR_ITER_LIMIT for k in limits)
 
 
 def test_autotune_keeps_results(O):
@@ -96,20 +187,28 @@ def test_autotune_keeps_results(O):
     bp = BatchPlanner(mixed_batch(seed=2, q=12))
     infos = bp.plan()
     c, t, ms = N.gmt_batch_autotune(bp.batch)
-    assert c in (1, 2, 4, 8, 16) and t in (256, 512, 1024) and ms > 0
+    mode, c2, t2 = N.gmt_batch_get_launch(bp.batch)
+    assert mode in (N.BATCH_TEAMS, N.BATCH_LOCKSTEP) and t2 == t and c2 == c
+    assert (c == 0) == (mode == N.BATCH_LOCKSTEP)
+    assert c in (0, 1, 2, 4, 8, 16) and t in (256, 512, 1024) and ms > 0
     infos2 = bp.plan()
     for k in range(len(bp.problems)):
         check_query(O, bp, k, infos2)
 
 
-def test_full_size_batch_sampled_queries(O):
+@pytest.mark.parametrize("mode", ["default", "lockstep"])
+def test_full_size_batch_sampled_queries(O, mode):
     # The 256-query workload (n up to 16384): every query's tree is checked for
     # the paper's invariants on the GPU result, and a sample of queries, the
     # largest included, against the oracle bit for bit.
+    from paper_1705_02403_gb300 import _native as N
     from paper_1705_02403_gb300.planner import BatchPlanner
     qs = envgen.batch_queries(seed=0, q=256)
     bp = BatchPlanner(qs)
     infos = bp.plan()
+    if mode == "lockstep":
+        N.gmt_batch_set_mode(bp.batch, N.BATCH_LOCKSTEP)
+        infos = bp.plan()
     sizes = np.array([pb.n for pb in qs])
     pick = sorted(set([int(np.argmax(sizes)), int(np.argmin(sizes))] + list(range(0, 256, 37))))
     for k in pick:
