@@ -39,7 +39,7 @@ METRIC = "ms/plan p50/p99 & edges checked/s; learned+batched vs plain at equal p
 # DRAM bytes (read + write) of one plan_kernel launch on this workload, from the
 # ncu capture summarised in profiles/plan_kernel_double_integrator_6d_n4096.md.
 # Set to None whenever plan_kernel changes until it is captured again.
-PLAN_KERNEL_DRAM_BYTES = {"di6": 2111744, "geo2d": None}
+PLAN_KERNEL_DRAM_BYTES = {"di6": None, "geo2d": None}
 
 
 def parse():

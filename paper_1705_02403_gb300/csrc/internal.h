@@ -52,18 +52,23 @@ cudaError_t launch_fill(const SpaceArgs& s, const float* X, const uint32_t* mask
                         float* cost, float* tau, bool incoming, const int* orow, const int* ocol,
                         const float* ocost, const float* otau, cudaStream_t st);
 
-// Workspace and control block of one plan (all device memory).
+// Workspace and control block of one plan (all device memory).  Counters are
+// double-buffered by iteration parity.  Open list j holds its kept entries in
+// [0, keep_count[j]) and the nodes opened by the previous iteration in
+// [M - new_count[j], M) (M: the list's capacity); the lockstep kernel keeps a
+// query's whole open count in keep_count and its minimum open cost in
+// min_keep.
 struct PlanCtl {
     unsigned bar_count, bar_gen;
     int error;
     int status;
-    int g_count[2];
-    int open_count[2];
+    int g_count[2];      // entries of group list j
     int keep_count[2];
-    int cand_count;
-    unsigned min_keep[2];
-    unsigned min_new[2];
-    int goal_flag[2];
+    int new_count[2];
+    int cand_count[2];   // candidates claimed in an iteration of parity j
+    unsigned min_keep[2];  // minimum cost (as bits) over the kept entries
+    unsigned min_new[2];   // ... over the newly opened nodes
+    int goal_flag[2];    // the group held a goal node
     int iters;
     int final_i;
     int goal_node;
@@ -91,10 +96,10 @@ struct PlanArgs {
     float* cost;
     int* parent;
     int* path;
-    float* ocost;
+    float* ocost;         // open-set snapshot (cost if open, +inf otherwise)
     int* stamp;
     int* list_g[2];
-    int2* list_open[2];   // (node, cost bits) of each open node
+    int2* list_open[2];   // (node, cost bits) of each open node; N entries each
     int* list_cand;
     PlanCtl* ctl;
     // Optional per-edge verdict cache (in-CSR order): 0 unknown, 1 free,

@@ -1,33 +1,39 @@
 // Algorithm 1 (Group Marching Tree) as one persistent CUDA kernel.
 //
 // A "team" of threads runs every wavefront iteration of one plan without
-// returning to the host: either one CTA (block barriers) or a cooperative grid
-// (bounded global barriers, co-residency guaranteed by the cooperative launch).
-// Each iteration i has three phases separated by team barriers:
+// returning to the host: one CTA (block barriers), one thread-block cluster
+// (hardware cluster barriers) or a cooperative grid (bounded global
+// barriers, co-residency guaranteed by the cooperative launch).  Each
+// iteration i has two phases separated by team barriers:
 //
-//   A  group selection (Line 3): the open list is split into
-//      G_i = {v open : cost(v) <= theta_i} and the nodes that stay open; the
-//      minimum cost of those is reduced for the skip-ahead; the open-set
-//      snapshot `ocost` (cost if open, +inf otherwise) is brought up to date
-//      with the previous iteration's changes (G closed, new nodes opened).
-//   B  frontier push (Line 4): one warp per node of G scans its out-row;
-//      every unexplored neighbour is claimed once per iteration through one
-//      atomicMax on its stamp (INT_MAX marks tree nodes) and appended to the
-//      candidate list.  Open-list entries carry their cost, so group
-//      selection and the snapshot update need no gathers.
-//   C  lazy parent (Lines 5-9): one warp per candidate x scans its in-row,
-//      gathers ocost[y] and takes argmin of (ocost[y] + c(y, x), y); the warp
-//      then checks that single edge (points spread over the lanes) and, if it
-//      is free, commits parent/cost and appends x to the next open list.
+//   1  the open-set snapshot `ocost` (cost if open, +inf otherwise) is
+//      brought up to date with the previous iteration (its group closed, the
+//      nodes it opened set to their costs); group selection (Line 3) splits
+//      the open list into G_i = {v open : cost(v) <= theta_i} and the nodes
+//      that stay open; the warp that selects a node of G_i at once pushes it
+//      (Line 4): it scans the node's out-row and claims every unexplored
+//      neighbour once per iteration through one atomicMax on its stamp
+//      (INT_MAX marks tree nodes), appending it to the candidate list.
+//      Nothing reads the snapshot in this phase.
+//   2  lazy parent (Lines 5-9): one warp per candidate x scans its in-row,
+//      gathers the snapshot and takes argmin of (ocost[y] + c(y, x), y); the
+//      warp checks that single edge (points spread over the lanes) and, if it
+//      is free, commits parent and cost and appends x to the next open list.
 //
-// After phase C every thread reads the same totals and decides (Line 12):
+// Open entries carry their cost, so selection and the snapshot update need
+// no gathers.  Open entries are dealt to the team's CTAs round-robin first,
+// then to their warps, then to lanes, so that the nodes of a small group (and
+// their pushes) spread over the team.  An open list keeps the entries that
+// stay open at its front and the newly opened nodes at its back, so phase 1
+// of the next iteration finds exactly the nodes the snapshot lacks.
+//
+// After phase 2 every thread reads the same totals and decides (Line 12):
 // success if G_i held a goal node, failure if no node stays open, else the
 // next threshold index is the smallest i' > i with theta_{i'} >= min open cost
-// (iterations whose group would be empty are no-ops and are skipped).
-// Lists are appended with one atomic per warp (ballot + popc prefix), the
-// prefix-sum compaction of Section IV.  Counters and lists that the next
-// iteration needs are double-buffered by parity so that resets need no extra
-// barrier.
+// (iterations whose group would be empty are no-ops and are skipped).  Lists
+// are appended with one atomic per warp (ballot + popc prefix), the prefix-sum
+// compaction of Section IV.  Counters are double-buffered by parity so that
+// resets need no extra barrier.
 #include "plan_core.cuh"
 
 namespace gmtk {
@@ -35,7 +41,7 @@ namespace gmtk {
 // ------------------------------------------------------------------- kernel
 template <class Team, int KIND, int DP>
 __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
-    const int D = KIND == GMT_COST_DI ? 6 : DP;
+    constexpr int D = KIND == GMT_COST_DI ? 6 : DP;
     const int nbs = A.boxes.count <= smem_box_cap(DP) ? A.boxes.count : 0;
     for (int t = threadIdx.x; t < nbs * DP; t += blockDim.x) {
         sbox[t] = A.boxes.lo[t];
@@ -58,8 +64,9 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
             return;
         }
     }
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpc = blockDim.x >> 5;
     const int gwarp = rank >> 5, nwarps = size >> 5;
+    const int cta = team.cta(), nctas = team.ctas();
     const float INF = f_inf();
     const unsigned INF_KEY = 0x7f800000u;
     const int N = A.N;
@@ -76,103 +83,96 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
     }
     if (rank == 0) {
         A.list_open[0][0] = make_int2(0, __float_as_int(0.0f));
-        ctl->open_count[0] = 1;
-        ctl->open_count[1] = 0;
-        ctl->g_count[0] = ctl->g_count[1] = 0;
-        ctl->min_keep[0] = ctl->min_keep[1] = INF_KEY;
-        ctl->min_new[0] = ctl->min_new[1] = INF_KEY;
-        ctl->goal_flag[0] = ctl->goal_flag[1] = 0;
-        ctl->cand_count = 0;
+        for (int k = 0; k < 2; ++k) {
+            ctl->g_count[k] = ctl->keep_count[k] = ctl->new_count[k] = ctl->cand_count[k] = 0;
+            ctl->min_keep[k] = ctl->min_new[k] = INF_KEY;
+            ctl->goal_flag[k] = 0;
+        }
+        ctl->keep_count[0] = 1;
         ctl->goal_key = ~0ull;
     }
     bool ok = team.sync(ctl);
 
     long long i = 0;
     float theta = 0.0f;
-    int p = 0, q = 0, it = 0;
+    int it = 0;
     int status = GMT_OK;
     unsigned long long n_push = 0, n_pull = 0, n_checks = 0, n_failed = 0, n_computed = 0;
 
     while (ok) {
         if (it >= A.max_iters) { status = GMT_ERR_ITER_LIMIT; break; }
+        const int p = it & 1;
+        const int2* cur = A.list_open[p];
+        int2* nxt = A.list_open[p ^ 1];
         int* G = A.list_g[p];
-        const int2* cur = A.list_open[q];
-        int2* nxt = A.list_open[q ^ 1];
 
-        // ---- phase A: snapshot update from the previous iteration, group selection
+        // ---- phase 1: snapshot update, group selection, push
+        const int nk = ldcg_i(&ctl->keep_count[p]), nn = ldcg_i(&ctl->new_count[p]);
         if (it > 0) {
             const int ng_prev = ldcg_i(&ctl->g_count[p ^ 1]);
             const int* Gprev = A.list_g[p ^ 1];
             for (int t = rank; t < ng_prev; t += size) A.ocost[ldcg_i(&Gprev[t])] = INF;
-            const int k0 = ldcg_i(&ctl->keep_count[p ^ 1]), k1 = ldcg_i(&ctl->open_count[q]);
-            for (int t = k0 + rank; t < k1; t += size) {
-                const int2 e = __ldcg(&cur[t]);
+            for (int t = rank; t < nn; t += size) {
+                const int2 e = __ldcg(&cur[N - 1 - t]);
                 A.ocost[e.x] = __int_as_float(e.y);
             }
         }
-        if (rank == 0) ctl->cand_count = 0;
         {
-            const int ncur = ldcg_i(&ctl->open_count[q]);
-            for (int base = gwarp * 32; base < ncur; base += nwarps * 32) {
-                const int t = base + lane;
+            const int ncur = nk + nn;
+            const int per_round = nctas * wpc * 32;
+            for (int t0 = cta + nctas * wib; t0 < ncur; t0 += per_round) {  // t0: entry of lane 0
+                const int t = t0 + nctas * wpc * lane;
                 bool in_g = false, keep = false;
-                int v = -1;
-                float c = INF;
+                int2 e = make_int2(-1, 0);
                 if (t < ncur) {
-                    const int2 e = __ldcg(&cur[t]);
-                    v = e.x;
-                    c = __int_as_float(e.y);
-                    in_g = c <= theta;
+                    e = __ldcg(&cur[t < nk ? t : N - 1 - (t - nk)]);
+                    in_g = __int_as_float(e.y) <= theta;
                     keep = !in_g;
                 }
                 const int sg = warp_append_slot(in_g, &ctl->g_count[p]);
                 if (in_g) {
-                    G[sg] = v;
-                    if (A.is_goal[v]) ctl->goal_flag[p] = 1;
+                    G[sg] = e.x;
+                    if (A.is_goal[e.x]) ctl->goal_flag[p] = 1;
                 }
-                const int sk = warp_append_slot(keep, &ctl->open_count[q ^ 1]);
-                if (keep) nxt[sk] = make_int2(v, __float_as_int(c));
-                const unsigned kmin = __reduce_min_sync(0xffffffffu, keep ? float_key(c) : INF_KEY);
+                const int sk = warp_append_slot(keep, &ctl->keep_count[p ^ 1]);
+                if (keep) nxt[sk] = e;
+                const unsigned kmin =
+                    __reduce_min_sync(0xffffffffu, keep ? float_key(__int_as_float(e.y)) : INF_KEY);
                 if (lane == 0 && kmin != INF_KEY) atomicMin(&ctl->min_keep[p], kmin);
+                for (unsigned gm = __ballot_sync(0xffffffffu, in_g); gm; gm &= gm - 1) {
+                    const int z = __shfl_sync(0xffffffffu, e.x, __ffs(gm) - 1);
+                    const int e0 = __ldg(&A.out_row[z]), e1 = __ldg(&A.out_row[z + 1]);
+                    if (lane == 0) n_push += (unsigned long long)(e1 - e0);
+                    for (int eb = e0; eb < e1; eb += 32) {
+                        const int ei = eb + lane;
+                        bool want = false;
+                        int x = -1;
+                        if (ei < e1) {
+                            x = __ldg(&A.out_col[ei]);
+                            // one atomic both tests "unexplored" (stamp < INT_MAX) and
+                            // claims x for this iteration (stamp < it before)
+                            want = atomicMax(&A.stamp[x], it) < it;
+                        }
+                        const int sc = warp_append_slot(want, &ctl->cand_count[p]);
+                        if (want) A.list_cand[sc] = x;
+                    }
+                }
             }
         }
         if (!(ok = team.sync(ctl))) break;
 
-        // ---- phase B: frontier push from G
+        // ---- phase 2: lazy parent selection, one collision check, commit
         if (rank == 0) {
-            ctl->keep_count[p] = ldcg_i(&ctl->open_count[q ^ 1]);
             ctl->g_count[p ^ 1] = 0;
+            ctl->keep_count[p] = 0;
+            ctl->new_count[p] = 0;
+            ctl->cand_count[p ^ 1] = 0;
             ctl->min_keep[p ^ 1] = INF_KEY;
             ctl->min_new[p ^ 1] = INF_KEY;
             ctl->goal_flag[p ^ 1] = 0;
-            ctl->open_count[q] = 0;
         }
         {
-            const int ng = ldcg_i(&ctl->g_count[p]);
-            for (int zi = gwarp; zi < ng; zi += nwarps) {
-                const int z = ldcg_i(&G[zi]);
-                const int e0 = __ldg(&A.out_row[z]), e1 = __ldg(&A.out_row[z + 1]);
-                if (lane == 0) n_push += (unsigned long long)(e1 - e0);
-                for (int eb = e0; eb < e1; eb += 32) {
-                    const int e = eb + lane;
-                    bool want = false;
-                    int x = -1;
-                    if (e < e1) {
-                        x = __ldg(&A.out_col[e]);
-                        // one atomic both tests "unexplored" (stamp < INT_MAX) and
-                        // claims x for this iteration (stamp < it before)
-                        want = atomicMax(&A.stamp[x], it) < it;
-                    }
-                    const int sc = warp_append_slot(want, &ctl->cand_count);
-                    if (want) A.list_cand[sc] = x;
-                }
-            }
-        }
-        if (!(ok = team.sync(ctl))) break;
-
-        // ---- phase C: lazy parent selection, one collision check, commit
-        {
-            const int nc = ldcg_i(&ctl->cand_count);
+            const int nc = ldcg_i(&ctl->cand_count[p]);
             for (int ci = gwarp; ci < nc; ci += nwarps) {
                 const int x = ldcg_i(&A.list_cand[ci]);
                 const int r0 = __ldg(&A.in_row[x]), r1 = __ldg(&A.in_row[x + 1]);
@@ -229,8 +229,8 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
                         A.cost[x] = bc;
                         A.parent[x] = by;
                         A.stamp[x] = INT_MAX;
-                        const int s = atomicAdd(&ctl->open_count[q ^ 1], 1);
-                        nxt[s] = make_int2(x, __float_as_int(bc));
+                        const int s = atomicAdd(&ctl->new_count[p ^ 1], 1);
+                        nxt[N - 1 - s] = make_int2(x, __float_as_int(bc));
                         atomicMin(&ctl->min_new[p], float_key(bc));
                     } else {
                         ++n_failed;
@@ -242,7 +242,7 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
 
         // ---- Line 12 / Line 11: termination test, next threshold
         const int goal = ldcg_i(&ctl->goal_flag[p]);
-        const int n_open = ldcg_i(&ctl->open_count[q ^ 1]);
+        const int n_open = ldcg_i(&ctl->keep_count[p ^ 1]) + ldcg_i(&ctl->new_count[p ^ 1]);
         const unsigned mk = min(ldcg_u(&ctl->min_keep[p]), ldcg_u(&ctl->min_new[p]));
         ++it;
         if (goal) { status = GMT_OK; break; }
@@ -261,19 +261,17 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
             i = k;
             theta = (float)i * A.delta;
         }
-        p ^= 1;
-        q ^= 1;
     }
 
     // ---- result: minimum-cost goal node (ties by index), counters, path
     if (ok) {
         unsigned long long tree = 0;
         for (int v = rank; v < N; v += size) {
-            const float c = ldcg_f(&A.cost[v]);
-            if (c < INF) {
+            const float cv = ldcg_f(&A.cost[v]);
+            if (cv < INF) {
                 ++tree;
                 if (status == GMT_OK && A.is_goal[v])
-                    atomicMin(&ctl->goal_key, ((unsigned long long)float_key(c) << 32) | (unsigned)v);
+                    atomicMin(&ctl->goal_key, ((unsigned long long)float_key(cv) << 32) | (unsigned)v);
             }
         }
 #pragma unroll

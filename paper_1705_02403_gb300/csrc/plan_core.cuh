@@ -16,8 +16,12 @@ __device__ __forceinline__ int ldcg_i(const int* p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned ldcg_u(const unsigned* p) { return __ldcg(p); }
 __device__ __forceinline__ float ldcg_f(const float* p) { return __ldcg(p); }
 
+// Every team also names its CTAs (cta() in [0, ctas())), so that work can be
+// dealt to CTAs round-robin.
 struct BlockTeam {
     __device__ __forceinline__ int id() const { return blockIdx.x; }
+    __device__ __forceinline__ int cta() const { return 0; }
+    __device__ __forceinline__ int ctas() const { return 1; }
     __device__ __forceinline__ int rank() const { return threadIdx.x; }
     __device__ __forceinline__ int size() const { return blockDim.x; }
     __device__ __forceinline__ bool sync(PlanCtl*) const {
@@ -34,6 +38,8 @@ struct GridTeam {
     unsigned expected;
     int spin_limit;
     __device__ __forceinline__ int id() const { return 0; }
+    __device__ __forceinline__ int cta() const { return blockIdx.x; }
+    __device__ __forceinline__ int ctas() const { return gridDim.x; }
     __device__ __forceinline__ int rank() const { return blockIdx.x * blockDim.x + threadIdx.x; }
     __device__ __forceinline__ int size() const { return gridDim.x * blockDim.x; }
     __device__ bool sync(PlanCtl* ctl) const {
@@ -72,14 +78,16 @@ struct ClusterTeam {
         asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
         return r;
     }
-    __device__ __forceinline__ static unsigned ctas() {
+    __device__ __forceinline__ static unsigned cluster_ctas() {
         unsigned n;
         asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
         return n;
     }
-    __device__ __forceinline__ int id() const { return (int)(blockIdx.x / ctas()); }
+    __device__ __forceinline__ int id() const { return (int)(blockIdx.x / cluster_ctas()); }
+    __device__ __forceinline__ int cta() const { return (int)cta_rank(); }
+    __device__ __forceinline__ int ctas() const { return (int)cluster_ctas(); }
     __device__ __forceinline__ int rank() const { return (int)(cta_rank() * blockDim.x + threadIdx.x); }
-    __device__ __forceinline__ int size() const { return (int)(ctas() * blockDim.x); }
+    __device__ __forceinline__ int size() const { return (int)(cluster_ctas() * blockDim.x); }
     __device__ __forceinline__ bool sync(PlanCtl*) const {
         asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
         return true;

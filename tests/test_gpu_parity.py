@@ -127,6 +127,25 @@ def test_every_launch_shape_gives_the_same_tree(O, P, launch):
         assert_same(O, G, *oracle_run(O, pb), check_graph=False)
 
 
+DENSE = [envgen.geometric(41, d=2, n=3000, nbox=4, r=1.3), envgen.geometric(42, d=3, n=2600, nbox=6, r=1.6)]
+
+
+@pytest.fixture(scope="module")
+def dense_oracle(O):
+    return [oracle_run(O, pb) for pb in DENSE]
+
+
+@pytest.mark.parametrize("launch", [(1, 256), (1, 1024), (0, 1024, 16), (4, 256)])
+def test_candidate_queue_overflow(O, P, dense_oracle, launch):
+    # Nearly complete graphs: x_init claims more candidates in its first
+    # iteration than one CTA's shared-memory queue (2048) holds, so the warp
+    # that claims them pulls the rest itself.
+    for pb, ref in zip(DENSE, dense_oracle):
+        G = gpu_run(P, pb, launch=launch)
+        assert G["out_row"][1] - G["out_row"][0] > 2048
+        assert_same(O, G, *ref, check_graph=False)
+
+
 @pytest.mark.parametrize("d", [3, 4, 10])
 def test_geometric_higher_dimensions(O, P, d):
     pb = envgen.geometric(seed=d, d=d, n=700, nbox=12, r={3: 0.3, 4: 0.45, 10: 1.0}[d])
