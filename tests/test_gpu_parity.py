@@ -136,10 +136,10 @@ def dense_oracle(O):
 
 
 @pytest.mark.parametrize("launch", [(1, 256), (1, 1024), (0, 1024, 16), (4, 256)])
-def test_candidate_queue_overflow(O, P, dense_oracle, launch):
-    # Nearly complete graphs: x_init claims more candidates in its first
-    # iteration than one CTA's shared-memory queue (2048) holds, so the warp
-    # that claims them pulls the rest itself.
+def test_nearly_complete_graphs(O, P, dense_oracle, launch):
+    # Nearly complete graphs: one warp's push of x_init claims thousands of
+    # candidates in the first iteration, and every in-row scan spans many
+    # warp-wide chunks.
     for pb, ref in zip(DENSE, dense_oracle):
         G = gpu_run(P, pb, launch=launch)
         assert G["out_row"][1] - G["out_row"][0] > 2048
