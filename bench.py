@@ -37,9 +37,10 @@ sys.path.insert(0, ROOT)
 METRIC = "ms/plan p50/p99 & edges checked/s; learned+batched vs plain at equal path cost"
 
 # DRAM bytes (read + write) of one plan_kernel launch on this workload, from the
-# ncu capture summarised in profiles/plan_kernel_double_integrator_6d_n4096.md.
+# ncu captures summarised in profiles/plan_kernel_double_integrator_6d_n4096.md
+# and profiles/plan_kernel_geometric_2d_n1024.md.
 # Set to None whenever plan_kernel changes until it is captured again.
-PLAN_KERNEL_DRAM_BYTES = {"di6": None, "geo2d": None}
+PLAN_KERNEL_DRAM_BYTES = {"di6": 2112768, "geo2d": 418816}
 
 
 def parse():
@@ -368,9 +369,10 @@ def bench_batched(dev, flush, reps=5):
     qs = envgen.batch_queries(seed=0, q=256)
     bp = BatchPlanner(qs, device=dev)
     infos = bp.plan()
-    shape = N.gmt_batch_autotune(bp.batch)
+    N.gmt_batch_autotune(bp.batch)
+    mode, cluster, threads = N.gmt_batch_get_launch(bp.batch)
     st = torch.cuda.current_stream()
-    ms = []
+    ms, plan_ms = [], []
     for _ in range(reps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -379,13 +381,31 @@ def bench_batched(dev, flush, reps=5):
         b.record(st)
         b.synchronize()
         ms.append(a.elapsed_time(b))
+        plan_ms.append(N.gmt_batch_last_plan_ms(bp.batch))
     edges = sum(i["push_edges"] + i["pull_edges"] for i in infos)
     t = float(np.median(ms))
+    tp = float(np.median(plan_ms))
+    # plan-stage roofline: algorithmic bytes of every query's wavefront (the
+    # per-plan formula of the main line) over the plan-stage time
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    plan_bytes = sum(8 * i["push_edges"] + 12 * i["pull_edges"] + 8 * pb.d * i["checks"] + 16 * pb.N
+                     for i, pb in zip(infos, qs))
+    achieved = plan_bytes / (tp / 1e3) / 1e9
     return {"workload": "256 uneven 2D/3D geometric queries, n log-uniform in [512, 16384], 5-80 boxes",
             "ms_per_batch_p50": t, "plans_per_s": 256 / (t / 1e3), "edges_checked_per_s": edges / (t / 1e3),
             "sum_nodes": int(sum(pb.N for pb in qs)), "edges_checked_per_batch": int(edges),
             "success_rate": float(np.mean([i["status"] == 0 for i in infos])),
-            "autotuned_team": {"cluster": shape[0], "threads": shape[1], "plan_stage_ms": shape[2]}}
+            "plan_stage_ms_p50": tp,
+            "autotuned": {"scheme": {N.BATCH_TEAMS: "teams", N.BATCH_LOCKSTEP: "lockstep"}.get(mode, str(mode)),
+                          "cluster": cluster, "threads": threads},
+            "plan_stage_roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                                    "frac": achieved / hbm, "algorithmic_bytes": plan_bytes, "traffic": None}}
 
 
 def bench_serving(local_rank):

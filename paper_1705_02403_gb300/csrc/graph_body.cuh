@@ -294,6 +294,7 @@ __device__ __forceinline__ void scan_rows(const int* __restrict__ count, int* __
 // c(j, v) up in the finished out-row of j (binary search), so each edge cost is
 // computed once.
 constexpr int kFillWarps = 8;
+constexpr int kFillList = 1024;  // column list per warp (a 32-word chunk holds at most 1024)
 
 // One warp: row v (warp w of a block of kFillWarps warps).
 template <int KIND, int D, bool INCOMING>
@@ -303,7 +304,7 @@ __device__ __forceinline__ void fill_row(const SpaceArgs& s, const float* __rest
                                          const int* __restrict__ out_row, const int* __restrict__ out_col,
                                          const float* __restrict__ out_cost, const float* __restrict__ out_tau,
                                          int v) {
-    __shared__ int list[kFillWarps][1024];
+    __shared__ int list[kFillWarps][kFillList];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (v >= s.N) return;
     float xv[D];
@@ -311,25 +312,13 @@ __device__ __forceinline__ void fill_row(const SpaceArgs& s, const float* __rest
     for (int a = 0; a < D; ++a) xv[a] = X[(size_t)a * s.pitch + v];
     const int W = (s.N + 31) / 32;
     int base = row[v];
-    for (int c0 = 0; c0 < W; c0 += 32) {
-        const int w = c0 + lane;
-        uint32_t bits = w < W ? M[(size_t)w * s.pitch + v] : 0u;
-        const int n = __popc(bits);
-        int incl = n;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        int pos = incl - n;
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            list[warp][pos++] = 32 * w + b;
-        }
+    // Columns are gathered in the warp's list (ascending) and their costs
+    // computed 32 at a time once the list is full or the row ends, so that
+    // the lanes stay busy when a row's edges spread over many words.
+    int cnt = 0;
+    auto flush = [&]() {
         __syncwarp();
-        for (int t = lane; t < total; t += 32) {
+        for (int t = lane; t < cnt; t += 32) {
             const int j = list[warp][t];
             float c, tj = 0.0f;
             if (INCOMING && KIND == GMT_COST_DI) {
@@ -357,9 +346,31 @@ __device__ __forceinline__ void fill_row(const SpaceArgs& s, const float* __rest
             col[base + t] = j;
             cost[base + t] = c;
         }
-        base += total;
+        base += cnt;
+        cnt = 0;
         __syncwarp();
+    };
+    for (int c0 = 0; c0 < W; c0 += 32) {
+        const int w = c0 + lane;
+        uint32_t bits = w < W ? M[(size_t)w * s.pitch + v] : 0u;
+        const int n = __popc(bits);
+        int incl = n;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);  // at most 1024
+        if (cnt + total > kFillList) flush();
+        int pos = cnt + incl - n;
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            list[warp][pos++] = 32 * w + b;
+        }
+        cnt += total;
     }
+    flush();
 }
 
 }  // namespace gmtk
