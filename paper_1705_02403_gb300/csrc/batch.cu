@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kMaskRows) batch_mask_kernel(const QueryDev* _
     mask_tile<KIND, D>(q.s, q.X, q.mask, q.out_count, t % rb, t / rb);
 }
 
-__global__ void __launch_bounds__(kDIRows) batch_mask_di_kernel(const QueryDev* __restrict__ Q,
+__global__ void __launch_bounds__(kDIRows, 8) batch_mask_di_kernel(const QueryDev* __restrict__ Q,
                                                                const long long* __restrict__ off, int nq) {
     const long long b = blockIdx.x;
     const int k = find_query(off, nq, b);

@@ -196,6 +196,44 @@ __device__ __forceinline__ bool di_may_connect(const float* s0, const float* s1,
     return f < rr;
 }
 
+// Second filter stage, for the pairs di_may_connect keeps.  With R = 1.01 r,
+// q(tau) = tau^3 (J(tau) - R) = tau^4 - R tau^3 + a tau^2 - b tau + c.  The exact
+// procedure only reports an edge when J(tau*) < r at a root tau* in (0, r], and
+// J(tau*) >= min of J over (0, r], so an edge needs q <= 0 somewhere in (0, r].
+// On each quarter [lo, lo + h] of [0, r] the Bernstein coefficients of q
+// (degree 4) bound q from below; if every coefficient of every quarter exceeds
+// T = 1e-4 S (S = |c| + |b| r + a r^2 + R r^3 + r^4 bounds every term's size, and
+// the FP32 rounding of these few operations stays below 1e-5 S), q > 0 on
+// (0, r] and the pair cannot be an edge.  The 1% slack covers the rounding of
+// the exact procedure's J, as for the bound above.
+__device__ __forceinline__ bool di_bern_may_connect(const float* s0, const float* s1, float r) {
+    const DICoef k = di_coef(s0, s1);
+    const float R = r * 1.01f;
+    const float a = k.a, b = k.b, c = k.c;
+    const float r2 = r * r;
+    const float S = fabsf(c) + fabsf(b) * r + fabsf(a) * r2 + R * r2 * r + r2 * r2;
+    const float T = 1e-4f * S;
+    const float h = 0.25f * r;
+    const float h2 = h * h;
+    const float d4 = h2 * h2;
+#pragma unroll
+    for (int qtr = 0; qtr < 4; ++qtr) {
+        const float lo = (float)qtr * h;
+        // Taylor coefficients of q at lo times powers of h: q(lo + h s) = sum d_k s^k
+        const float d0 = (((lo - R) * lo + a) * lo - b) * lo + c;
+        const float d1 = (((4.0f * lo - 3.0f * R) * lo + 2.0f * a) * lo - b) * h;
+        const float d2 = ((6.0f * lo - 3.0f * R) * lo + a) * h2;
+        const float d3 = (4.0f * lo - R) * h2 * h;
+        // Bernstein coefficients: beta_i = sum_{k <= i} C(i,k) / C(4,k) d_k
+        const float b1 = d0 + 0.25f * d1;
+        const float b2 = (d0 + 0.5f * d1) + d2 * (1.0f / 6.0f);
+        const float b3 = ((d0 + 0.75f * d1) + 0.5f * d2) + 0.25f * d3;
+        const float b4 = (((d0 + d1) + d2) + d3) + d4;
+        if (!(d0 > T && b1 > T && b2 > T && b3 > T && b4 > T)) return true;
+    }
+    return false;
+}
+
 // Position of the minimum-effort trajectory (cubic Hermite curve) at s in [0,1]:
 //   p = ((h00 p0 + (h10 tau) v0) + h01 p1) + (h11 tau) v1,
 //   h00 = (2 s^3 - 3 s^2) + 1, h10 = (s^3 - 2 s^2) + s, h01 = 3 s^2 - 2 s^3,

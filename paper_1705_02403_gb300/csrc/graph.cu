@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kMaskRows) pair_mask_kernel(SpaceArgs s, const
     mask_tile<KIND, D>(s, X, mask, out_count, blockIdx.x, blockIdx.y);
 }
 
-__global__ void __launch_bounds__(kDIRows) pair_mask_di_kernel(SpaceArgs s, const float* __restrict__ X,
+__global__ void __launch_bounds__(kDIRows, 8) pair_mask_di_kernel(SpaceArgs s, const float* __restrict__ X,
                                                               uint32_t* __restrict__ mask,
                                                               int* __restrict__ out_count) {
     mask_di_tile(s, X, mask, out_count, blockIdx.x, blockIdx.y);

@@ -161,7 +161,7 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
                                              int by) {
     __shared__ float tile[6][kDIWords * 32];
     __shared__ uint32_t words[kDIRows / 32][kDIWords][32];
-    __shared__ uint16_t queue[kDIRows / 32][64];
+    __shared__ uint16_t queue[kDIRows / 32][3][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = bx * kDIRows + threadIdx.x;
     const int w0 = by * kDIWords;
@@ -179,40 +179,82 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
 #pragma unroll
     for (int a = 0; a < 6; ++a) xi[a] = row_ok ? X[(size_t)a * s.pitch + i] : 0.0f;
 
-    // exact test of up to 32 queued pairs, one per lane
-    auto drain = [&](int count) {
-        const int e = lane < count ? queue[warp][lane] : 0;
+    // Four tests of increasing cost and strength: the velocity test of
+    // di_may_connect alone (every pair), di_may_connect, di_bern_may_connect,
+    // and the exact cost.  Pairs that pass a test wait in that stage's queue;
+    // 32 at a time (one per lane) they take the next test, so every lane stays
+    // busy although fewer pairs reach each stage.  An entry is
+    // (row lane << 8) | column.
+    const float rr = s.r * 1.01f;
+    int qn0 = 0, qn1 = 0, qn2 = 0;
+    auto state = [&](int e, float* a_, float* b_) {
         const int src = e >> 8, jt = e & 255;
-        float a_[6], b_[6];
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
             a_[a] = __shfl_sync(0xffffffffu, xi[a], src);
             b_[a] = tile[a][jt];
         }
+    };
+    // appends the lanes that pass to queue k; returns the new length
+    auto enqueue = [&](int k, bool pass, int e, int qn) {
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        if (pass) queue[warp][k][qn + __popc(m & ((1u << lane) - 1u))] = (uint16_t)e;
+        __syncwarp();
+        return qn + __popc(m);
+    };
+    auto shift = [&](int k, int qn) {  // drops the 32 entries just taken
+        __syncwarp();
+        if (lane < qn - 32) queue[warp][k][lane] = queue[warp][k][32 + lane];
+        __syncwarp();
+        return qn - 32;
+    };
+    auto drain2 = [&](int count) {  // exact test
+        const int e = lane < count ? queue[warp][2][lane] : 0;
+        float a_[6], b_[6];
+        state(e, a_, b_);
+        const int src = e >> 8, jt = e & 255;
         if (lane < count && di_cost(a_, b_, s.r) < s.r) atomicOr(&words[warp][jt >> 5][src], 1u << (jt & 31));
     };
+    auto drain1 = [&](int count) {  // second bound
+        const int e = lane < count ? queue[warp][1][lane] : 0;
+        float a_[6], b_[6];
+        state(e, a_, b_);
+        qn2 = enqueue(2, lane < count && di_bern_may_connect(a_, b_, s.r), e, qn2);
+        if (qn2 >= 32) {
+            drain2(32);
+            qn2 = shift(2, qn2);
+        }
+    };
+    auto drain0 = [&](int count) {  // first bound
+        const int e = lane < count ? queue[warp][0][lane] : 0;
+        float a_[6], b_[6];
+        state(e, a_, b_);
+        qn1 = enqueue(1, lane < count && di_may_connect(a_, b_, s.r), e, qn1);
+        if (qn1 >= 32) {
+            drain1(32);
+            qn1 = shift(1, qn1);
+        }
+    };
 
-    int qn = 0;
     const int jend = min(kDIWords * 32, s.N - j0);
     for (int jt = 0; jt < jend; ++jt) {
         const int j = j0 + jt;
-        float xj[6];
+        // velocity test: J >= tau + |v1 - v0|^2 / tau >= 2 |v1 - v0|
+        float A = 0.0f;
 #pragma unroll
-        for (int a = 0; a < 6; ++a) xj[a] = tile[a][jt];
-        const bool pass = row_ok && j != i && di_may_connect(xi, xj, s.r);
-        const unsigned m = __ballot_sync(0xffffffffu, pass);
-        if (pass) queue[warp][qn + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((lane << 8) | jt);
-        qn += __popc(m);
-        __syncwarp();
-        if (qn >= 32) {
-            drain(32);
-            __syncwarp();
-            if (lane < qn - 32) queue[warp][lane] = queue[warp][32 + lane];
-            qn -= 32;
-            __syncwarp();
+        for (int a = 3; a < 6; ++a) {
+            const float dv = tile[a][jt] - xi[a];
+            A = A + dv * dv;
+        }
+        qn0 = enqueue(0, row_ok && j != i && 4.0f * A < rr * rr, (lane << 8) | jt, qn0);
+        if (qn0 >= 32) {
+            drain0(32);
+            qn0 = shift(0, qn0);
         }
     }
-    if (qn > 0) drain(qn);
+    if (qn0 > 0) drain0(qn0);
+    if (qn1 > 0) drain1(qn1);
+    if (qn2 > 0) drain2(qn2);
     __syncwarp();
     if (!row_ok) return;
     const int W = (s.N + 31) / 32;
