@@ -101,21 +101,20 @@ __global__ void __launch_bounds__(1024) batch_scan_kernel(const QueryDev* __rest
 // One warp per (query, row).  A query whose edge count exceeds the slice it was
 // given (only possible if a replayed batch's inputs changed in place) writes
 // nothing; its plan then reports GMT_ERR_OOM.
-template <int KIND, int D, bool INCOMING>
+template <int KIND, int D>
 __global__ void __launch_bounds__(kFillWarps * 32) batch_fill_kernel(const QueryDev* __restrict__ Q,
                                                                      const long long* __restrict__ off, int nq) {
     const long long w = (long long)blockIdx.x * kFillWarps + (threadIdx.x >> 5);
     if (w >= off[nq]) return;
     const int k = find_query(off, nq, w);
     const QueryDev& q = Q[k];
-    const int* row = INCOMING ? q.in_row : q.out_row;
+    const bool incoming = blockIdx.y == 1;  // in-rows (double integrator)
+    const int* row = incoming ? q.in_row : q.out_row;
     if ((long long)row[q.s.N] > q.edge_cap) return;
-    if (INCOMING)
-        fill_row<KIND, D, true>(q.s, q.X, q.maskT, q.in_row, q.in_col, q.in_cost, q.in_tau, q.out_row, q.out_col,
-                                q.out_cost, q.out_tau, (int)(w - off[k]));
+    if (incoming)
+        fill_row<KIND, D, true>(q.s, q.X, q.maskT, q.in_row, q.in_col, q.in_cost, q.in_tau, (int)(w - off[k]));
     else
-        fill_row<KIND, D, false>(q.s, q.X, q.mask, q.out_row, q.out_col, q.out_cost, q.out_tau, nullptr, nullptr,
-                                 nullptr, nullptr, (int)(w - off[k]));
+        fill_row<KIND, D, false>(q.s, q.X, q.mask, q.out_row, q.out_col, q.out_cost, q.out_tau, (int)(w - off[k]));
 }
 
 namespace {
@@ -129,10 +128,9 @@ void mask_g(const QueryDev* Q, const long long* off, int nq, long long tiles, cu
     else batch_mask_kernel<KIND, D><<<(unsigned)tiles, kMaskRows, 0, st>>>(Q, off, nq);
 }
 template <int KIND, int D>
-void fill_g(const QueryDev* Q, const long long* off, int nq, long long rows, bool incoming, cudaStream_t st) {
-    const unsigned blocks = (unsigned)((rows + kFillWarps - 1) / kFillWarps);
-    if (incoming) batch_fill_kernel<KIND, D, true><<<blocks, kFillWarps * 32, 0, st>>>(Q, off, nq);
-    else batch_fill_kernel<KIND, D, false><<<blocks, kFillWarps * 32, 0, st>>>(Q, off, nq);
+void fill_g(const QueryDev* Q, const long long* off, int nq, long long rows, cudaStream_t st) {
+    const dim3 grid((unsigned)((rows + kFillWarps - 1) / kFillWarps), KIND == GMT_COST_DI ? 2 : 1);
+    batch_fill_kernel<KIND, D><<<grid, kFillWarps * 32, 0, st>>>(Q, off, nq);
 }
 }  // namespace
 
@@ -153,10 +151,10 @@ cudaError_t batch_mask(int kind, int d, const QueryDev* Q, const long long* off,
     return cudaGetLastError();
 }
 cudaError_t batch_fill(int kind, int d, const QueryDev* Q, const long long* off, int nq, long long rows,
-                       bool incoming, cudaStream_t st) {
-    if (kind == GMT_COST_DI) fill_g<GMT_COST_DI, 6>(Q, off, nq, rows, incoming, st);
-    else if (d == 2) fill_g<GMT_COST_EUCLID, 2>(Q, off, nq, rows, incoming, st);
-    else if (d == 3) fill_g<GMT_COST_EUCLID, 3>(Q, off, nq, rows, incoming, st);
+                       cudaStream_t st) {
+    if (kind == GMT_COST_DI) fill_g<GMT_COST_DI, 6>(Q, off, nq, rows, st);
+    else if (d == 2) fill_g<GMT_COST_EUCLID, 2>(Q, off, nq, rows, st);
+    else if (d == 3) fill_g<GMT_COST_EUCLID, 3>(Q, off, nq, rows, st);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -384,9 +382,7 @@ gmt_status enqueue_build_back(gmt_batch* b, int32_t* parent, float* cost, cudaSt
     for (Group& g : b->groups) {
         const int nq = (int)g.members.size();
         const QueryDev* Q = g.desc.as<QueryDev>();
-        BCUDA(batch_fill(g.kind, g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, false, st), "batched fill");
-        if (g.kind == GMT_COST_DI)
-            BCUDA(batch_fill(g.kind, g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, true, st), "batched fill");
+        BCUDA(batch_fill(g.kind, g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, st), "batched fill");
     }
     BCUDA(cudaMemsetAsync(b->ctl.p, 0, b->ctl.cap, st), "memset");
     for (cudaEvent_t& e : b->ev_plan)

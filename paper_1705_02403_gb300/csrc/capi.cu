@@ -298,13 +298,10 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
         GROW(in_tau, E);
     }
     LAUNCH(g->mark(gmt_graph::kFill, 0, st), "event");
-    LAUNCH(launch_fill(sa, g->X, g->mask, g->out_row, g->out_col, g->out_cost, di ? g->out_tau : nullptr, false,
-                       nullptr, nullptr, nullptr, nullptr, st),
-           "fill kernel");
-    if (di)
-        LAUNCH(launch_fill(sa, g->X, g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own, g->in_tau, true,
-                           g->out_row, g->out_col, g->out_cost, g->out_tau, st),
-               "fill kernel");
+    const FillDir out_dir{g->mask, g->out_row, g->out_col, g->out_cost, di ? g->out_tau : nullptr};
+    const FillDir in_dir = di ? FillDir{g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own, g->in_tau}
+                              : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr};
+    LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, st), "fill kernel");
     LAUNCH(g->mark(gmt_graph::kFill, 1, st), "event");
 #undef GROW
 #undef LAUNCH

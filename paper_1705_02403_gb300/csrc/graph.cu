@@ -8,11 +8,12 @@
 //                     that each warp writes 32 consecutive rows' words
 //   transpose_kernel  32x32 bit-block transpose with warp ballots (in-edges)
 //   scan_kernel       exclusive prefix sum of the per-row counts -> row_ptr
-//   pair_mask_di_kernel  the same for the double integrator, with a
-//                     conservative lower bound and per-warp compaction of the
-//                     pairs that need the exact root procedure
+//   pair_mask_di_kernel  the same for the double integrator: three
+//                     conservative tests of increasing cost, then the exact
+//                     root procedure, with per-warp compaction between stages
 //   fill_kernel       one warp per row: prefix over the row's words, column
-//                     list in shared memory, one edge cost per lane
+//                     list in shared memory, one edge cost per lane; out- and
+//                     in-rows in one launch
 #include <cstdio>
 
 #include "graph_body.cuh"
@@ -20,9 +21,24 @@
 namespace gmtk {
 
 // ------------------------------------------------------------------ kernels
+constexpr int kSampleThreads = 64;  // small blocks spread the few thousand nodes over more SMs
+
+// Boxes are staged in shared memory when `staged` (2 * count * DP floats): the
+// rejection loop then tests them without a global-memory round trip per box.
 template <int D, int DP>
-__global__ void __launch_bounds__(128) sample_kernel(SpaceArgs s, BoxArgs boxes, float* __restrict__ X,
-                                                     uint8_t* __restrict__ is_goal, int* __restrict__ flags) {
+__global__ void __launch_bounds__(kSampleThreads) sample_kernel(SpaceArgs s, BoxArgs boxes, float* __restrict__ X,
+                                                                uint8_t* __restrict__ is_goal,
+                                                                int* __restrict__ flags, int staged) {
+    extern __shared__ float sbox[];
+    if (staged) {
+        for (int t = threadIdx.x; t < boxes.count * DP; t += blockDim.x) {
+            sbox[t] = boxes.lo[t];
+            sbox[boxes.count * DP + t] = boxes.hi[t];
+        }
+        __syncthreads();
+        boxes.lo = sbox;
+        boxes.hi = sbox + boxes.count * DP;
+    }
     sample_node<D, DP>(s, boxes, X, is_goal, flags, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -56,24 +72,23 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ coun
     scan_rows(count, row, N);
 }
 
-template <int KIND, int D, bool INCOMING>
-__global__ void __launch_bounds__(kFillWarps * 32) fill_kernel(SpaceArgs s, const float* __restrict__ X,
-                                                               const uint32_t* __restrict__ M,
-                                                               const int* __restrict__ row, int* __restrict__ col,
-                                                               float* __restrict__ cost, float* __restrict__ tau,
-                                                               const int* __restrict__ out_row,
-                                                               const int* __restrict__ out_col,
-                                                               const float* __restrict__ out_cost,
-                                                               const float* __restrict__ out_tau) {
-    fill_row<KIND, D, INCOMING>(s, X, M, row, col, cost, tau, out_row, out_col, out_cost, out_tau,
-                                blockIdx.x * kFillWarps + (threadIdx.x >> 5));
+// blockIdx.y = 0: out-rows; 1: in-rows (double integrator).
+template <int KIND, int D>
+__global__ void __launch_bounds__(kFillWarps * 32) fill_kernel(SpaceArgs s, const float* __restrict__ X, FillDir out,
+                                                               FillDir in) {
+    const int v = blockIdx.x * kFillWarps + (threadIdx.x >> 5);
+    if (blockIdx.y == 0) fill_row<KIND, D, false>(s, X, out.mask, out.row, out.col, out.cost, out.tau, v);
+    else fill_row<KIND, D, true>(s, X, in.mask, in.row, in.col, in.cost, in.tau, v);
 }
 
 // ------------------------------------------------------------------ launchers
 namespace {
 template <int D, int DP>
 cudaError_t sample_t(const SpaceArgs& s, BoxArgs b, float* X, uint8_t* g, int* f, cudaStream_t st) {
-    sample_kernel<D, DP><<<(s.N + 127) / 128, 128, 0, st>>>(s, b, X, g, f);
+    const int staged = b.count > 0 && b.count <= 4096 / DP;
+    const size_t smem = staged ? (size_t)2 * b.count * DP * sizeof(float) : 0;
+    sample_kernel<D, DP><<<(s.N + kSampleThreads - 1) / kSampleThreads, kSampleThreads, smem, st>>>(s, b, X, g, f,
+                                                                                                     staged);
     return cudaGetLastError();
 }
 template <int KIND, int D>
@@ -84,16 +99,9 @@ cudaError_t mask_t(const SpaceArgs& s, const float* X, uint32_t* mask, int* cnt,
     return cudaGetLastError();
 }
 template <int KIND, int D>
-cudaError_t fill_t(const SpaceArgs& s, const float* X, const uint32_t* M, const int* row, int* col, float* cost,
-                   float* tau, bool incoming, const int* orow, const int* ocol, const float* ocost,
-                   const float* otau, cudaStream_t st) {
-    const int blocks = (s.N + kFillWarps - 1) / kFillWarps;
-    if (incoming)
-        fill_kernel<KIND, D, true><<<blocks, kFillWarps * 32, 0, st>>>(s, X, M, row, col, cost, tau, orow, ocol,
-                                                                        ocost, otau);
-    else
-        fill_kernel<KIND, D, false><<<blocks, kFillWarps * 32, 0, st>>>(s, X, M, row, col, cost, tau, orow, ocol,
-                                                                         ocost, otau);
+cudaError_t fill_t(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, cudaStream_t st) {
+    const dim3 grid((s.N + kFillWarps - 1) / kFillWarps, in.mask ? 2 : 1);
+    fill_kernel<KIND, D><<<grid, kFillWarps * 32, 0, st>>>(s, X, out, in);
     return cudaGetLastError();
 }
 }  // namespace
@@ -162,12 +170,9 @@ cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill(const SpaceArgs& s, const float* X, const uint32_t* M, const int* row, int* col,
-                        float* cost, float* tau, bool incoming, const int* orow, const int* ocol,
-                        const float* ocost, const float* otau, cudaStream_t st) {
-    if (s.kind == GMT_COST_DI)
-        return fill_t<GMT_COST_DI, 6>(s, X, M, row, col, cost, tau, incoming, orow, ocol, ocost, otau, st);
-    GMT_EUCLID_DIMS(fill_t, s, X, M, row, col, cost, tau, incoming, orow, ocol, ocost, otau, st)
+cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, cudaStream_t st) {
+    if (s.kind == GMT_COST_DI) return fill_t<GMT_COST_DI, 6>(s, X, out, in, st);
+    GMT_EUCLID_DIMS(fill_t, s, X, out, in, st)
 }
 
 }  // namespace gmtk

@@ -332,9 +332,9 @@ __device__ __forceinline__ void scan_rows(const int* __restrict__ count, int* __
 // the lanes' bit counts are prefix-summed, and the columns are written, in
 // ascending order, to a per-warp list in shared memory; the lanes then take
 // the listed edges one each, so the cost evaluations keep every lane busy.
-// Out-rows compute c(v, j).  In-rows of the double integrator look the cost
-// c(j, v) up in the finished out-row of j (binary search), so each edge cost is
-// computed once.
+// Out-rows compute c(v, j), in-rows c(j, v), with the same formulas on the
+// same states, so an edge's cost (and arrival time) is the same bits in both
+// CSRs and the two directions need not wait for each other.
 constexpr int kFillWarps = 8;
 constexpr int kFillList = 1024;  // column list per warp (a 32-word chunk holds at most 1024)
 
@@ -343,8 +343,6 @@ template <int KIND, int D, bool INCOMING>
 __device__ __forceinline__ void fill_row(const SpaceArgs& s, const float* __restrict__ X,
                                          const uint32_t* __restrict__ M, const int* __restrict__ row,
                                          int* __restrict__ col, float* __restrict__ cost, float* __restrict__ tau,
-                                         const int* __restrict__ out_row, const int* __restrict__ out_col,
-                                         const float* __restrict__ out_cost, const float* __restrict__ out_tau,
                                          int v) {
     __shared__ int list[kFillWarps][kFillList];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -363,19 +361,13 @@ __device__ __forceinline__ void fill_row(const SpaceArgs& s, const float* __rest
         for (int t = lane; t < cnt; t += 32) {
             const int j = list[warp][t];
             float c, tj = 0.0f;
-            if (INCOMING && KIND == GMT_COST_DI) {
-                int lo = out_row[j], hi = out_row[j + 1] - 1;   // v is in the out-row of j
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (out_col[mid] < v) lo = mid + 1; else hi = mid;
-                }
-                c = out_cost[lo];
-                tj = out_tau[lo];
-            } else if (KIND == GMT_COST_DI) {
+            if (KIND == GMT_COST_DI) {
+                // the same formulas on the same states as the edge's out-row:
+                // identical bits in both directions
                 float xj[D];
 #pragma unroll
                 for (int a = 0; a < D; ++a) xj[a] = X[(size_t)a * s.pitch + j];
-                const DICoef k = di_coef(xv, xj);
+                const DICoef k = INCOMING ? di_coef(xj, xv) : di_coef(xv, xj);
                 tj = di_tau(k, s.r);
                 c = di_J(k, tj);
             } else {

@@ -45,12 +45,18 @@ cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask,
 cudaError_t launch_transpose(const SpaceArgs& s, const uint32_t* mask, uint32_t* maskT, int* in_count,
                              cudaStream_t st);
 cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st);
-// incoming: build in-rows from the transposed matrix; double-integrator costs
-// are then looked up in the finished out-CSR (orow, ocol, ocost).
-// tau (double integrator only, may be NULL): arrival time of each edge.
-cudaError_t launch_fill(const SpaceArgs& s, const float* X, const uint32_t* mask, const int* row, int* col,
-                        float* cost, float* tau, bool incoming, const int* orow, const int* ocol,
-                        const float* ocost, const float* otau, cudaStream_t st);
+// One CSR direction for the fill: the bit matrix rows come from (mask for
+// out-rows, its transpose for in-rows), row offsets, and the outputs; tau
+// (double integrator only, may be NULL) receives each edge's arrival time.
+struct FillDir {
+    const uint32_t* mask;
+    const int* row;
+    int* col;
+    float* cost;
+    float* tau;
+};
+// Fills the out-CSR, and the in-CSR in the same launch when in.mask != NULL.
+cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, cudaStream_t st);
 
 // Workspace and control block of one plan (all device memory).  Counters are
 // double-buffered by iteration parity.  Open list j holds its kept entries in

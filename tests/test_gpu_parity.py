@@ -119,6 +119,51 @@ def test_double_integrator_full_size(O, P):
         assert_same(O, G, *oracle_run(O, pb))
 
 
+def test_double_integrator_filters_keep_every_edge_on_adversarial_states(O, P):
+    # The pair filter tests every pair with conservative bounds before the exact
+    # procedure.  States appended in tight families (tiny position changes,
+    # equal or nearly equal velocities, slow motion, exact duplicates of the
+    # position) stress the bounds where their margins are thinnest; the CSR must
+    # still equal the oracle's, which evaluates the definition for every pair.
+    import torch
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import GraphView, boxes_on_device, goal_struct, params_struct, space_struct
+    pb = envgen.di6(seed=11, n=200, nbox=0, r=2.0)
+    rng = np.random.default_rng(5)
+    states = []
+    for b in np.concatenate([rng.uniform(0.2, 0.8, (40, 3)), rng.uniform(-0.8, 0.8, (40, 3))], axis=1):
+        for kind in range(10):
+            s = b.copy()
+            if kind in (0, 1, 2):
+                s[:3] += rng.uniform(-1e-3, 1e-3, 3)
+                s[3:] = rng.uniform(-1, 1, 3)
+            elif kind in (3, 4):
+                s[:3] += rng.uniform(-0.1, 0.1, 3)
+                s[3:] += rng.uniform(-1e-4, 1e-4, 3)
+            elif kind == 5:
+                s[3:] = rng.uniform(-1, 1, 3)
+            elif kind in (6, 7):
+                s[:3] += rng.uniform(-0.05, 0.05, 3)
+                s[3:] = rng.uniform(-0.02, 0.02, 3)
+            else:
+                s[:3] += rng.uniform(-1e-5, 1e-5, 3)
+                s[3:] += rng.uniform(-1e-5, 1e-5, 3)
+            states.append(np.clip(s, [0, 0, 0, -1, -1, -1], [1, 1, 1, 1, 1, 1]))
+    extra = torch.tensor(np.array(states, np.float32).T.copy(), device="cuda")
+    boxes, keep = boxes_on_device(pb)
+    g = N.gmt_build_graph_ex(space_struct(pb), boxes, [float(v) for v in pb.x_init], goal_struct(pb), params_struct(pb),
+                             extra.data_ptr(), len(states), len(states))
+    v = GraphView(g)
+    X, goal = v.X.cpu().numpy(), v.is_goal.cpu().numpy()
+    og = O.Graph(pb.kind, pb.d, pb.dp, X, goal, np.float32(pb.r))
+    c = og.csr()
+    assert v.E == og.num_edges and v.E > 0
+    assert np.array_equal(v.out_row.cpu().numpy(), c.out_row) and np.array_equal(v.out_col.cpu().numpy(), c.out_col)
+    assert np.array_equal(bits(v.out_cost.cpu().numpy()), bits(c.out_cost))
+    assert np.array_equal(v.in_row.cpu().numpy(), c.in_row) and np.array_equal(v.in_col.cpu().numpy(), c.in_col)
+    assert np.array_equal(bits(v.in_cost.cpu().numpy()), bits(c.in_cost))
+
+
 @pytest.mark.parametrize("launch", [(1, 1024), (1, 256), (2, 512), (7, 256), (0, 0), (152, 1024), (0, 1024, 2),
                                     (0, 512, 4), (0, 1024, 8), (0, 1024, 16)])
 def test_every_launch_shape_gives_the_same_tree(O, P, launch):
