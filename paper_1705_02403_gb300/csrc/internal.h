@@ -60,18 +60,20 @@ cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, 
 
 // Workspace and control block of one plan (all device memory).  Counters are
 // double-buffered by iteration parity.  Open list j holds its kept entries in
-// [0, keep_count[j]) and the nodes opened by the previous iteration in
-// [M - new_count[j], M) (M: the list's capacity); the lockstep kernel keeps a
-// query's whole open count in keep_count and its minimum open cost in
-// min_keep.
+// [0, kept) and the nodes opened by the previous iteration in
+// [M - new_count[j], M) (M: the list's capacity).  gk[j] packs two counters
+// that grow in the same phase, so one atomic reserves both: the low half
+// counts group list j, the high half the kept entries of open list j ^ 1.
+// The lockstep kernel keeps a query's whole open count in open_count and its
+// minimum open cost in min_keep.
 struct PlanCtl {
     unsigned bar_count, bar_gen;
     int error;
     int status;
-    int g_count[2];      // entries of group list j
-    int keep_count[2];
+    unsigned long long gk[2];
     int new_count[2];
     int cand_count[2];   // candidates claimed in an iteration of parity j
+    int open_count[2];
     unsigned min_keep[2];  // minimum cost (as bits) over the kept entries
     unsigned min_new[2];   // ... over the newly opened nodes
     int goal_flag[2];    // the group held a goal node

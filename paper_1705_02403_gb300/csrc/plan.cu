@@ -84,11 +84,12 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
     if (rank == 0) {
         A.list_open[0][0] = make_int2(0, __float_as_int(0.0f));
         for (int k = 0; k < 2; ++k) {
-            ctl->g_count[k] = ctl->keep_count[k] = ctl->new_count[k] = ctl->cand_count[k] = 0;
+            ctl->gk[k] = 0ull;
+            ctl->new_count[k] = ctl->cand_count[k] = 0;
             ctl->min_keep[k] = ctl->min_new[k] = INF_KEY;
             ctl->goal_flag[k] = 0;
         }
-        ctl->keep_count[0] = 1;
+        ctl->gk[1] = 1ull << 32;  // one kept entry in open list 0
         ctl->goal_key = ~0ull;
     }
     bool ok = team.sync(ctl);
@@ -107,9 +108,10 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
         int* G = A.list_g[p];
 
         // ---- phase 1: snapshot update, group selection, push
-        const int nk = ldcg_i(&ctl->keep_count[p]), nn = ldcg_i(&ctl->new_count[p]);
+        const unsigned long long gk_prev = __ldcg(&ctl->gk[p ^ 1]);
+        const int nk = (int)(gk_prev >> 32), nn = ldcg_i(&ctl->new_count[p]);
         if (it > 0) {
-            const int ng_prev = ldcg_i(&ctl->g_count[p ^ 1]);
+            const int ng_prev = (int)(gk_prev & 0xffffffffu);
             const int* Gprev = A.list_g[p ^ 1];
             for (int t = rank; t < ng_prev; t += size) A.ocost[ldcg_i(&Gprev[t])] = INF;
             for (int t = rank; t < nn; t += size) {
@@ -129,13 +131,18 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
                     in_g = __int_as_float(e.y) <= theta;
                     keep = !in_g;
                 }
-                const int sg = warp_append_slot(in_g, &ctl->g_count[p]);
+                // one atomic reserves the warp's group entries and kept entries
+                const unsigned mg = __ballot_sync(0xffffffffu, in_g), mkeep = __ballot_sync(0xffffffffu, keep);
+                unsigned long long base = 0;
+                if (lane == 0 && (mg | mkeep))
+                    base = atomicAdd(&ctl->gk[p], ((unsigned long long)__popc(mkeep) << 32) | __popc(mg));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                const unsigned below = (1u << lane) - 1u;
                 if (in_g) {
-                    G[sg] = e.x;
+                    G[(int)(base & 0xffffffffu) + __popc(mg & below)] = e.x;
                     if (A.is_goal[e.x]) ctl->goal_flag[p] = 1;
                 }
-                const int sk = warp_append_slot(keep, &ctl->keep_count[p ^ 1]);
-                if (keep) nxt[sk] = e;
+                if (keep) nxt[(int)(base >> 32) + __popc(mkeep & below)] = e;
                 const unsigned kmin =
                     __reduce_min_sync(0xffffffffu, keep ? float_key(__int_as_float(e.y)) : INF_KEY);
                 if (lane == 0 && kmin != INF_KEY) atomicMin(&ctl->min_keep[p], kmin);
@@ -163,8 +170,7 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
 
         // ---- phase 2: lazy parent selection, one collision check, commit
         if (rank == 0) {
-            ctl->g_count[p ^ 1] = 0;
-            ctl->keep_count[p] = 0;
+            ctl->gk[p ^ 1] = 0ull;  // previous group list, kept entries of this iteration's open list
             ctl->new_count[p] = 0;
             ctl->cand_count[p ^ 1] = 0;
             ctl->min_keep[p ^ 1] = INF_KEY;
@@ -242,7 +248,7 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
 
         // ---- Line 12 / Line 11: termination test, next threshold
         const int goal = ldcg_i(&ctl->goal_flag[p]);
-        const int n_open = ldcg_i(&ctl->keep_count[p ^ 1]) + ldcg_i(&ctl->new_count[p ^ 1]);
+        const int n_open = (int)(__ldcg(&ctl->gk[p]) >> 32) + ldcg_i(&ctl->new_count[p ^ 1]);
         const unsigned mk = min(ldcg_u(&ctl->min_keep[p]), ldcg_u(&ctl->min_new[p]));
         ++it;
         if (goal) { status = GMT_OK; break; }

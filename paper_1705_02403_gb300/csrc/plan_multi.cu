@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(1024) plan_lockstep_kernel(const PlanArgs* __r
             PlanCtl* ctl = QA[k].ctl;
             ctl->min_keep[p ^ 1] = INF_KEY;
             ctl->goal_flag[p ^ 1] = 0;
-            ctl->keep_count[p] = 0;
+            ctl->open_count[p] = 0;
         }
         if (tid == 0) {
             sm.nqueue = 0;
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(1024) plan_lockstep_kernel(const PlanArgs* __r
                 if (n_open == 0 && sm.acc_goal[k] == 0 && sm.acc_push[k] == 0 && sm.acc_checks[k] == 0) continue;
                 PlanCtl* ctl = QA[k].ctl;
                 if (n_open) {
-                    atomicAdd(&ctl->keep_count[p ^ 1], n_open);
+                    atomicAdd(&ctl->open_count[p ^ 1], n_open);
                     atomicMin(&ctl->min_keep[p], sm.acc_min[k]);
                 }
                 if (sm.acc_goal[k]) ctl->goal_flag[p] = 1;
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(1024) plan_lockstep_kernel(const PlanArgs* __r
             const PlanArgs* A = &QA[k];
             PlanCtl* ctl = A->ctl;
             const int goal = ldcg_i(&ctl->goal_flag[p]);
-            const int n_open = ldcg_i(&ctl->keep_count[p ^ 1]);
+            const int n_open = ldcg_i(&ctl->open_count[p ^ 1]);
             const unsigned mk = ldcg_u(&ctl->min_keep[p]);
             int st = kRunning;
             if (goal) {
