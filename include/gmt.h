@@ -105,6 +105,13 @@ typedef struct {
  * than there are blocks, so every wait runs out and the call returns
  * GMT_ERR_TIMEOUT.  Used to test the bounded-wait path without a GPU fault. */
 #define GMT_DEBUG_UNREACHABLE_BARRIER 0x1u
+/* Test hooks for the neighbour build of 2D/3D geometric graphs, which picks
+ * a cell list (candidates from the grid cells around each node) when the
+ * radius is small against the domain and the all-pairs test otherwise; both
+ * give the same CSR.  PAIRS_ALL forces the all-pairs test, PAIRS_CELLS the cell
+ * list (rows with more than 1024 neighbours still fall back to all pairs). */
+#define GMT_DEBUG_PAIRS_ALL 0x2u
+#define GMT_DEBUG_PAIRS_CELLS 0x4u
 
 typedef struct gmt_graph gmt_graph;
 

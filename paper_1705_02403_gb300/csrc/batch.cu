@@ -17,7 +17,7 @@
 #include <string>
 #include <vector>
 
-#include "graph_body.cuh"
+#include "cells_body.cuh"
 
 namespace gmtk {
 
@@ -40,6 +40,14 @@ struct QueryDev {
     float* in_cost;
     float* in_tau;
     long long edge_cap;
+    // cell-list neighbour build (2D/3D geometric queries with a small radius)
+    CellGrid cg;
+    int use_cells;
+    int* cell_of;
+    int* cell_sorted;
+    int* cell_cnt;
+    int* cell_start;
+    int* cell_info;  // [longest row, a row overflowed the fill's list]
 };
 
 // index k with off[k] <= t < off[k+1] (off has nq+1 entries, off[0] = 0)
@@ -98,6 +106,49 @@ __global__ void __launch_bounds__(1024) batch_scan_kernel(const QueryDev* __rest
     else scan_rows(q.out_count, q.out_row, q.s.N);
 }
 
+// ---- cell-list neighbour build (queries with use_cells; the others return)
+template <int D>
+__global__ void __launch_bounds__(256) batch_cells_count_kernel(const QueryDev* __restrict__ Q,
+                                                                const long long* __restrict__ off, int nq) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= off[nq]) return;
+    const int k = find_query(off, nq, t);
+    const QueryDev& q = Q[k];
+    if (q.use_cells) cell_count_node<D>(q.s, q.X, q.cg, q.cell_of, q.cell_cnt, (int)(t - off[k]));
+}
+
+__global__ void __launch_bounds__(1024) batch_cells_scan_kernel(const QueryDev* __restrict__ Q) {
+    const QueryDev& q = Q[blockIdx.x];
+    if (q.use_cells) scan_rows(q.cell_cnt, q.cell_start, q.cg.ncells);
+}
+
+__global__ void __launch_bounds__(256) batch_cells_scatter_kernel(const QueryDev* __restrict__ Q,
+                                                                  const long long* __restrict__ off, int nq) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= off[nq]) return;
+    const int k = find_query(off, nq, t);
+    const QueryDev& q = Q[k];
+    if (q.use_cells) cell_scatter_node(q.s.N, q.cell_of, q.cell_start, q.cell_cnt, q.cell_sorted, (int)(t - off[k]));
+}
+
+// One warp per (query, row).  Fill pass: a query whose longest row outgrew
+// the sort list (only possible if a replayed batch's inputs changed in place)
+// gets an edge count its plan rejects (GMT_ERR_OOM); so does one whose edge
+// count outgrew its slice.
+template <int D, bool FILL>
+__global__ void __launch_bounds__(kCellWarps * 32) batch_cells_rows_kernel(const QueryDev* __restrict__ Q,
+                                                                           const long long* __restrict__ off, int nq) {
+    const long long w = (long long)blockIdx.x * kCellWarps + (threadIdx.x >> 5);
+    if (w >= off[nq]) return;
+    const int k = find_query(off, nq, w);
+    const QueryDev& q = Q[k];
+    if (!q.use_cells) return;
+    if (FILL && (long long)q.out_row[q.s.N] > q.edge_cap) return;
+    cell_row<D, FILL>(q.s, q.X, q.cg, q.cell_of, q.cell_start, q.cell_sorted, q.out_count, q.cell_info, q.out_row,
+                      q.out_col, q.out_cost, q.cell_info + 1, (int)(w - off[k]));
+    if (FILL && (threadIdx.x & 31) == 0 && __ldcg(&q.cell_info[1]) != 0) q.out_row[q.s.N] = INT_MAX;
+}
+
 // One warp per (query, row).  A query whose edge count exceeds the slice it was
 // given (only possible if a replayed batch's inputs changed in place) writes
 // nothing; its plan then reports GMT_ERR_OOM.
@@ -108,6 +159,7 @@ __global__ void __launch_bounds__(kFillWarps * 32) batch_fill_kernel(const Query
     if (w >= off[nq]) return;
     const int k = find_query(off, nq, w);
     const QueryDev& q = Q[k];
+    if (q.use_cells) return;
     const bool incoming = blockIdx.y == 1;  // in-rows (double integrator)
     const int* row = incoming ? q.in_row : q.out_row;
     if ((long long)row[q.s.N] > q.edge_cap) return;
@@ -144,9 +196,31 @@ cudaError_t batch_sample(int kind, int d, const QueryDev* Q, const long long* of
 }
 cudaError_t batch_mask(int kind, int d, const QueryDev* Q, const long long* off, int nq, long long tiles,
                        cudaStream_t st) {
+    if (tiles == 0) return cudaSuccess;  // every query of the group uses the cell list
     if (kind == GMT_COST_DI) mask_g<GMT_COST_DI, 6>(Q, off, nq, tiles, st);
     else if (d == 2) mask_g<GMT_COST_EUCLID, 2>(Q, off, nq, tiles, st);
     else if (d == 3) mask_g<GMT_COST_EUCLID, 3>(Q, off, nq, tiles, st);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+// Cell-list stages before the row scan: cell counts, per-query cell scan,
+// scatter, row counts (queries without use_cells return at once).
+cudaError_t batch_cells_front(int d, const QueryDev* Q, const long long* off, int nq, long long nodes,
+                              cudaStream_t st) {
+    const unsigned tb = (unsigned)((nodes + 255) / 256), wb = (unsigned)((nodes + kCellWarps - 1) / kCellWarps);
+    if (d == 2) batch_cells_count_kernel<2><<<tb, 256, 0, st>>>(Q, off, nq);
+    else if (d == 3) batch_cells_count_kernel<3><<<tb, 256, 0, st>>>(Q, off, nq);
+    else return cudaErrorInvalidValue;
+    batch_cells_scan_kernel<<<nq, 1024, 0, st>>>(Q);
+    batch_cells_scatter_kernel<<<tb, 256, 0, st>>>(Q, off, nq);
+    if (d == 2) batch_cells_rows_kernel<2, false><<<wb, kCellWarps * 32, 0, st>>>(Q, off, nq);
+    else batch_cells_rows_kernel<3, false><<<wb, kCellWarps * 32, 0, st>>>(Q, off, nq);
+    return cudaGetLastError();
+}
+cudaError_t batch_cells_fill(int d, const QueryDev* Q, const long long* off, int nq, long long rows, cudaStream_t st) {
+    const unsigned wb = (unsigned)((rows + kCellWarps - 1) / kCellWarps);
+    if (d == 2) batch_cells_rows_kernel<2, true><<<wb, kCellWarps * 32, 0, st>>>(Q, off, nq);
+    else if (d == 3) batch_cells_rows_kernel<3, true><<<wb, kCellWarps * 32, 0, st>>>(Q, off, nq);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -219,6 +293,7 @@ struct Group {
     // run in one launch; their node offsets start at lock_base + chunk_base[c]
     std::vector<int> chunk_start, chunk_count, chunk_nodes, chunk_base, chunk_ctl;
     DevBuf lock_base;
+    bool any_cells = false;  // some member builds its neighbours with the cell list
 };
 
 }  // namespace
@@ -234,6 +309,7 @@ struct gmt_batch {
     std::vector<Group> groups;
     // arena
     DevBuf X, goal, flags, mask, maskT, counts, rows, edges_i, edges_f, path, ctl, next, slot;
+    DevBuf cells, cell_info;
     DevBuf s_ocost, s_stamp, s_lists;
     DevBuf l_open, l_glist, l_ocost, l_stamp, l_ctl;
     int lock_chunks = 0;
@@ -361,11 +437,14 @@ void plan_shape(const gmt_batch* b, const Group& g, int* cluster, int* threads, 
 gmt_status enqueue_build_front(gmt_batch* b, cudaStream_t st) {
     BCUDA(cudaMemsetAsync(b->flags.p, 0, b->flags.cap, st), "memset");
     BCUDA(cudaMemsetAsync(b->counts.p, 0, b->counts.cap, st), "memset");
+    BCUDA(cudaMemsetAsync(b->cells.p, 0, b->cells.cap, st), "memset");
+    BCUDA(cudaMemsetAsync(b->cell_info.p, 0, b->cell_info.cap, st), "memset");
     for (Group& g : b->groups) {
         const int nq = (int)g.members.size();
         const QueryDev* Q = g.desc.as<QueryDev>();
         BCUDA(batch_sample(g.kind, g.d, Q, g.off_nodes.as<long long>(), nq, g.nodes, st), "batched sample kernel");
         BCUDA(batch_mask(g.kind, g.d, Q, g.off_tiles.as<long long>(), nq, g.tiles, st), "batched pair filter");
+        if (g.any_cells) BCUDA(batch_cells_front(g.d, Q, g.off_nodes.as<long long>(), nq, g.nodes, st), "batched cells");
         if (g.kind == GMT_COST_DI) {
             const long long warps = g.tasks;
             batch_transpose_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(Q, g.off_tasks.as<long long>(), nq);
@@ -383,6 +462,7 @@ gmt_status enqueue_build_back(gmt_batch* b, int32_t* parent, float* cost, cudaSt
         const int nq = (int)g.members.size();
         const QueryDev* Q = g.desc.as<QueryDev>();
         BCUDA(batch_fill(g.kind, g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, st), "batched fill");
+        if (g.any_cells) BCUDA(batch_cells_fill(g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, st), "batched cells");
     }
     BCUDA(cudaMemsetAsync(b->ctl.p, 0, b->ctl.cap, st), "memset");
     for (cudaEvent_t& e : b->ev_plan)
@@ -441,7 +521,10 @@ gmt_status enqueue_build_back(gmt_batch* b, int32_t* parent, float* cost, cudaSt
 
 // Lays out the arena for the queries, runs the front half, reads the edge
 // counts, sizes the edge slices, fills the descriptors and plan arguments.
-gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* parent, float* cost, cudaStream_t st) {
+// force_pairs[k] != 0: query k uses the all-pairs test even where the cell list
+// would apply (set after a row outgrew the cell list's sort buffer).
+gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* parent, float* cost, cudaStream_t st,
+                   const std::vector<char>& force_pairs = {}) {
     b->prepared = false;
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -463,8 +546,10 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         g->members.push_back(k);
     }
     // sizes and offsets
-    size_t xs = 0, gs = 0, ms = 0, mts = 0, cs = 0, rs = 0, ps = 0;
-    std::vector<size_t> xo(q), go(q), mo(q), mto(q), co(q), ro(q), po(q);
+    size_t xs = 0, gs = 0, ms = 0, mts = 0, cs = 0, rs = 0, ps = 0, cls = 0;
+    std::vector<size_t> xo(q), go(q), mo(q), mto(q), co(q), ro(q), po(q), clo(q);
+    std::vector<CellGrid> cgs(q);
+    std::vector<char> use_cells(q, 0);
     b->node_base[0] = 0;
     for (int k = 0; k < q; ++k) {
         const gmt_query& Qh = queries[k];
@@ -472,21 +557,34 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         const int P = (N + 31) / 32 * 32, W = (N + 31) / 32;
         b->N[k] = N; b->pitch[k] = P;
         b->node_base[k + 1] = b->node_base[k] + N;
+        b->r[k] = Qh.params.r > 0.0f ? Qh.params.r
+                                     : (float)gmt_connection_radius(Qh.params.n, Qh.space.dim, Qh.params.eta,
+                                                                    Qh.params.mu_free);
+        bool pays = false;
+        const unsigned dbg = Qh.params.debug_flags;
+        const bool applies = make_cell_grid(Qh.space.kind, Qh.space.dim, Qh.space.lo, Qh.space.hi, b->r[k], N,
+                                            &cgs[k], &pays);
+        use_cells[k] = applies && !(dbg & GMT_DEBUG_PAIRS_ALL) && (pays || (dbg & GMT_DEBUG_PAIRS_CELLS)) &&
+                       !(k < (int)force_pairs.size() && force_pairs[k]);
         xo[k] = xs; xs += (size_t)Qh.space.dim * P;
         go[k] = gs; gs += P;
-        mo[k] = ms; ms += (size_t)W * P;
+        if (use_cells[k]) {
+            clo[k] = cls;
+            cls += 2 * (size_t)N + 2 * (size_t)cgs[k].ncells + 1;
+        } else {
+            mo[k] = ms; ms += (size_t)W * P;
+        }
         if (Qh.space.kind == GMT_COST_DI) { mto[k] = mts; mts += (size_t)W * P; }
         co[k] = cs; cs += 2 * (size_t)N;
         ro[k] = rs; rs += 2 * (size_t)(N + 1);
         po[k] = ps; ps += N;
-        b->r[k] = Qh.params.r > 0.0f ? Qh.params.r
-                                     : (float)gmt_connection_radius(Qh.params.n, Qh.space.dim, Qh.params.eta,
-                                                                    Qh.params.mu_free);
     }
     BCUDA(b->X.need(xs * 4), "arena");
     BCUDA(b->goal.need(gs), "arena");
     BCUDA(b->flags.need((size_t)q * 4), "arena");
-    BCUDA(b->mask.need(ms * 4), "arena");
+    BCUDA(b->mask.need(ms * 4 + 4), "arena");
+    BCUDA(b->cells.need(cls * 4 + 4), "arena");
+    BCUDA(b->cell_info.need((size_t)q * 2 * 4), "arena");
     BCUDA(b->maskT.need(mts * 4 + 4), "arena");
     BCUDA(b->counts.need(cs * 4), "arena");
     BCUDA(b->rows.need(rs * 4), "arena");
@@ -524,7 +622,17 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         d.X = b->X.as<float>() + xo[k];
         d.is_goal = b->goal.as<uint8_t>() + go[k];
         d.flags = b->flags.as<int>() + k;
-        d.mask = b->mask.as<uint32_t>() + mo[k];
+        d.mask = use_cells[k] ? nullptr : b->mask.as<uint32_t>() + mo[k];
+        d.use_cells = use_cells[k];
+        d.cg = cgs[k];
+        if (use_cells[k]) {
+            const size_t N = (size_t)s.N;
+            d.cell_of = b->cells.as<int>() + clo[k];
+            d.cell_sorted = d.cell_of + N;
+            d.cell_cnt = d.cell_sorted + N;
+            d.cell_start = d.cell_cnt + cgs[k].ncells;
+        }
+        d.cell_info = b->cell_info.as<int>() + 2 * k;
         d.maskT = s.kind == GMT_COST_DI ? b->maskT.as<uint32_t>() + mto[k] : nullptr;
         d.out_count = b->counts.as<int>() + co[k];
         d.in_count = d.out_count + s.N;
@@ -538,10 +646,13 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         std::vector<long long> on(nq + 1, 0), ot(nq + 1, 0), ow(nq + 1, 0);
         std::vector<QueryDev> dq(nq);
         g.max_n = 0; g.max_boxes = 0;
+        g.any_cells = false;
         for (int i = 0; i < nq; ++i) {
             const int k = g.members[i];
             const int N = b->N[k], W = (N + 31) / 32;
-            const long long tiles = g.kind == GMT_COST_DI
+            g.any_cells = g.any_cells || use_cells[k];
+            const long long tiles = use_cells[k] ? 0
+                                    : g.kind == GMT_COST_DI
                                         ? (long long)((N + kDIRows - 1) / kDIRows) * ((W + kDIWords - 1) / kDIWords)
                                         : (long long)((N + kMaskRows - 1) / kMaskRows) * ((W + kMaskWords - 1) / kMaskWords);
             on[i + 1] = on[i] + N;
@@ -570,9 +681,24 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
     for (int k = 0; k < q; ++k)
         BCUDA(cudaMemcpyAsync(b->h_rows + k, b->qd[k].out_row + b->N[k], sizeof(int), cudaMemcpyDeviceToHost, st),
               "edge count readback");
-    std::vector<int> flags(q);
+    std::vector<int> flags(q), cell_info(2 * (size_t)q);
     BCUDA(cudaMemcpyAsync(flags.data(), b->flags.p, (size_t)q * 4, cudaMemcpyDeviceToHost, st), "flag readback");
+    BCUDA(cudaMemcpyAsync(cell_info.data(), b->cell_info.p, (size_t)q * 8, cudaMemcpyDeviceToHost, st),
+          "cell readback");
     BCUDA(cudaStreamSynchronize(st), "batched graph build");
+    {
+        // a row too long for the cell list's sort buffer: that query takes the
+        // all-pairs test instead, and the batch is prepared again
+        std::vector<char> force(force_pairs);
+        force.resize(q, 0);
+        bool again = false;
+        for (int k = 0; k < q; ++k)
+            if (use_cells[k] && cell_info[2 * k] > kCellList) {
+                force[k] = 1;
+                again = true;
+            }
+        if (again) return prepare(b, q, queries, parent, cost, st, force);
+    }
     for (int k = 0; k < q; ++k) {
         if (flags[k] & kSampleBadInit)
             return bfail(GMT_ERR_INVALID, "x_init outside X or in an obstacle (query " + std::to_string(k) + ")");

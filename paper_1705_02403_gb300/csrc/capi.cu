@@ -77,7 +77,13 @@ struct gmt_graph {
     float* in_tau = nullptr;       size_t cap_in_tau = 0;
     uint32_t* mask = nullptr;      size_t cap_mask = 0;
     uint32_t* maskT = nullptr;     size_t cap_maskT = 0;
-    int* flags = nullptr;          size_t cap_flags = 0;
+    int* flags = nullptr;          size_t cap_flags = 0;   // [sample flags, max row length, row overflow, -]
+    // cell-list neighbour build
+    int* cell_of = nullptr;        size_t cap_cell_of = 0;
+    int* cell_sorted = nullptr;    size_t cap_cell_sorted = 0;
+    int* cell_cnt = nullptr;       size_t cap_cell_cnt = 0;
+    int* cell_start = nullptr;     size_t cap_cell_start = 0;
+    bool used_cells = false;
     // plan workspace
     float* ocost = nullptr;        size_t cap_ocost = 0;
     int* stamp = nullptr;          size_t cap_stamp = 0;
@@ -109,7 +115,8 @@ struct gmt_graph {
 
     ~gmt_graph() {
         void* dev[] = {X, is_goal, out_row, in_row_own, out_count, in_count, out_col, out_cost, in_col_own,
-                       in_cost_own, out_tau, in_tau, mask, maskT, flags, ocost, stamp, lists, ctl};
+                       in_cost_own, out_tau, in_tau, mask, maskT, flags, cell_of, cell_sorted, cell_cnt,
+                       cell_start, ocost, stamp, lists, ctl};
         for (void* p : dev)
             if (p) cudaFree(p);
         if (h_ctl) cudaFreeHost(h_ctl);
@@ -239,7 +246,6 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     GROW(is_goal, P);
     GROW(out_row, N + 1);
     GROW(out_count, N);
-    GROW(mask, W * P);
     GROW(flags, 4);
     GROW(ocost, N);
     GROW(stamp, N);
@@ -265,8 +271,31 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     LAUNCH(launch_append(sa, ba, extra, extra_pitch, n_sampled, extra_count, g->X, g->is_goal, g->flags, st),
            "append kernel");
     LAUNCH(g->mark(gmt_graph::kSample, 1, st), "event");
+    // neighbour test: cell list for 2D/3D geometric graphs with a small radius
+    // (or when forced), else all pairs; both give the same CSR
+    CellGrid cg;
+    bool cells_pay = false;
+    bool cells = make_cell_grid(g->kind, g->d, space->lo, space->hi, g->r, g->N, &cg, &cells_pay);
+    if (params->debug_flags & GMT_DEBUG_PAIRS_ALL) cells = false;
+    else if (!(params->debug_flags & GMT_DEBUG_PAIRS_CELLS)) cells = cells && cells_pay;
     LAUNCH(g->mark(gmt_graph::kPair, 0, st), "event");
-    LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, st), "pair filter kernel");
+    if (cells) {
+        GROW(cell_of, N);
+        GROW(cell_sorted, N);
+        GROW(cell_cnt, (size_t)cg.ncells);
+        GROW(cell_start, (size_t)cg.ncells + 1);
+        LAUNCH(cudaMemsetAsync(g->cell_cnt, 0, (size_t)cg.ncells * sizeof(int), st), "memset");
+        LAUNCH(launch_cells_count(sa, g->X, cg, g->cell_of, g->cell_cnt, st), "cell count kernel");
+        LAUNCH(launch_scan(g->cell_cnt, g->cell_start, cg.ncells, st), "scan kernel");
+        LAUNCH(launch_cells_scatter(g->N, g->cell_of, g->cell_start, g->cell_cnt, g->cell_sorted, st),
+               "cell scatter kernel");
+        LAUNCH(launch_cells_rows(sa, g->X, cg, g->cell_of, g->cell_start, g->cell_sorted, false, g->out_count,
+                                 g->flags + 1, nullptr, nullptr, nullptr, nullptr, st),
+               "cell row kernel");
+    } else {
+        GROW(mask, W * P);
+        LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, st), "pair filter kernel");
+    }
     LAUNCH(g->mark(gmt_graph::kPair, 1, st), "event");
     if (g->kind == GMT_COST_DI) {
         LAUNCH(g->mark(gmt_graph::kTranspose, 0, st), "event");
@@ -277,16 +306,28 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     LAUNCH(launch_scan(g->out_count, g->out_row, g->N, st), "scan kernel");
     if (g->kind == GMT_COST_DI) LAUNCH(launch_scan(g->in_count, g->in_row_own, g->N, st), "scan kernel");
     LAUNCH(g->mark(gmt_graph::kScan, 1, st), "event");
-    LAUNCH(cudaMemcpyAsync(g->h_scalars, g->flags, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
-    LAUNCH(cudaMemcpyAsync(g->h_scalars + 1, g->out_row + N, sizeof(int), cudaMemcpyDeviceToHost, st),
+    LAUNCH(cudaMemcpyAsync(g->h_scalars, g->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
+    LAUNCH(cudaMemcpyAsync(g->h_scalars + 2, g->out_row + N, sizeof(int), cudaMemcpyDeviceToHost, st),
            "edge count readback");
     LAUNCH(cudaStreamSynchronize(st), "graph build");
+    if (cells && g->h_scalars[1] > kCellList) {
+        // a row too long to sort in shared memory: the all-pairs test instead
+        cells = false;
+        GROW(mask, W * P);
+        LAUNCH(cudaMemsetAsync(g->out_count, 0, N * sizeof(int), st), "memset");
+        LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, st), "pair filter kernel");
+        LAUNCH(launch_scan(g->out_count, g->out_row, g->N, st), "scan kernel");
+        LAUNCH(cudaMemcpyAsync(g->h_scalars + 2, g->out_row + N, sizeof(int), cudaMemcpyDeviceToHost, st),
+               "edge count readback");
+        LAUNCH(cudaStreamSynchronize(st), "graph build");
+    }
+    g->used_cells = cells;
     const int flags = g->h_scalars[0];
     if (flags & kSampleBadInit) return bail(fail(GMT_ERR_INVALID, "x_init is outside X or inside an obstacle"));
     if (flags & kSampleExhausted)
         return bail(fail(GMT_ERR_INVALID, "a sample exhausted max_attempts (X_free or X_goal n X_free too small)"));
     if (flags & kSampleBadAppend) return bail(fail(GMT_ERR_INVALID, "an appended sample is outside X or in X_obs"));
-    g->E = g->h_scalars[1];
+    g->E = g->h_scalars[2];
     const size_t E = (size_t)g->E;
     GROW(out_col, E);
     GROW(out_cost, E);
@@ -298,10 +339,16 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
         GROW(in_tau, E);
     }
     LAUNCH(g->mark(gmt_graph::kFill, 0, st), "event");
-    const FillDir out_dir{g->mask, g->out_row, g->out_col, g->out_cost, di ? g->out_tau : nullptr};
-    const FillDir in_dir = di ? FillDir{g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own, g->in_tau}
-                              : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr};
-    LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, st), "fill kernel");
+    if (cells) {
+        LAUNCH(launch_cells_rows(sa, g->X, cg, g->cell_of, g->cell_start, g->cell_sorted, true, nullptr, nullptr,
+                                 g->out_row, g->out_col, g->out_cost, g->flags + 2, st),
+               "cell row kernel");
+    } else {
+        const FillDir out_dir{g->mask, g->out_row, g->out_col, g->out_cost, di ? g->out_tau : nullptr};
+        const FillDir in_dir = di ? FillDir{g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own, g->in_tau}
+                                  : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr};
+        LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, st), "fill kernel");
+    }
     LAUNCH(g->mark(gmt_graph::kFill, 1, st), "event");
 #undef GROW
 #undef LAUNCH

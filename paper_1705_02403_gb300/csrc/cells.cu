@@ -1,0 +1,105 @@
+// Cell-list neighbour build for one graph (kernels in cells_body.cuh).
+#include <cmath>
+
+#include "cells_body.cuh"
+
+namespace gmtk {
+
+template <int D>
+__global__ void __launch_bounds__(256) cells_count_kernel(SpaceArgs s, const float* __restrict__ X, CellGrid cg,
+                                                          int* __restrict__ cell_of, int* __restrict__ cnt) {
+    cell_count_node<D>(s, X, cg, cell_of, cnt, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(256) cells_scatter_kernel(int N, const int* __restrict__ cell_of,
+                                                            const int* __restrict__ start, int* __restrict__ cnt,
+                                                            int* __restrict__ sorted) {
+    cell_scatter_node(N, cell_of, start, cnt, sorted, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <int D, bool FILL>
+__global__ void __launch_bounds__(kCellWarps * 32) cells_rows_kernel(SpaceArgs s, const float* __restrict__ X,
+                                                                     CellGrid cg, const int* __restrict__ cell_of,
+                                                                     const int* __restrict__ start,
+                                                                     const int* __restrict__ sorted,
+                                                                     int* __restrict__ out_count,
+                                                                     int* __restrict__ max_deg,
+                                                                     const int* __restrict__ row,
+                                                                     int* __restrict__ col, float* __restrict__ cost,
+                                                                     int* __restrict__ overflow) {
+    cell_row<D, FILL>(s, X, cg, cell_of, start, sorted, out_count, max_deg, row, col, cost, overflow,
+                      blockIdx.x * kCellWarps + (threadIdx.x >> 5));
+}
+
+bool make_cell_grid(int kind, int d, const float* lo, const float* hi, float r, int N, CellGrid* cg, bool* pays) {
+    if (kind != GMT_COST_EUCLID || (d != 2 && d != 3) || !(r > 0.0f)) return false;
+    // cell side: at least 1.01 r, and coarse enough for at most 2^16 cells
+    double h = (double)r * 1.01;
+    for (;;) {
+        double cells = 1.0;
+        for (int a = 0; a < d; ++a) cells *= std::floor(((double)hi[a] - (double)lo[a]) / h) + 1.0;
+        if (cells <= 65536.0) break;
+        h *= 1.25;
+    }
+    double frac = 1.0;
+    long long ncells = 1;
+    for (int a = 0; a < 3; ++a) {
+        cg->g[a] = 1;
+        cg->lo[a] = 0.0f;
+        if (a >= d) continue;
+        const double L = (double)hi[a] - (double)lo[a];
+        cg->g[a] = (int)std::floor(L / h) + 1;
+        cg->lo[a] = lo[a];
+        frac *= std::min(1.0, 3.0 * h / L);
+        ncells *= cg->g[a];
+    }
+    // keep h >= 1.01 r for the rounded reciprocal too
+    cg->inv_h = (float)(1.0 / h);
+    while ((double)r * 1.01 * (double)cg->inv_h > 1.0) cg->inv_h = std::nextafter(cg->inv_h, 0.0f);
+    cg->ncells = (int)ncells;
+    *pays = frac <= 0.25 && N >= 4096;
+    return true;
+}
+
+namespace {
+template <int D>
+cudaError_t rows_t(const SpaceArgs& s, const float* X, const CellGrid& cg, const int* cell_of, const int* start,
+                   const int* sorted, bool fill, int* out_count, int* max_deg, const int* row, int* col, float* cost,
+                   int* overflow, cudaStream_t st) {
+    const int blocks = (s.N + kCellWarps - 1) / kCellWarps;
+    if (fill)
+        cells_rows_kernel<D, true><<<blocks, kCellWarps * 32, 0, st>>>(s, X, cg, cell_of, start, sorted, out_count,
+                                                                        max_deg, row, col, cost, overflow);
+    else
+        cells_rows_kernel<D, false><<<blocks, kCellWarps * 32, 0, st>>>(s, X, cg, cell_of, start, sorted, out_count,
+                                                                         max_deg, row, col, cost, overflow);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_cells_count(const SpaceArgs& s, const float* X, const CellGrid& cg, int* cell_of, int* cell_cnt,
+                               cudaStream_t st) {
+    const int blocks = (s.N + 255) / 256;
+    if (s.d == 2) cells_count_kernel<2><<<blocks, 256, 0, st>>>(s, X, cg, cell_of, cell_cnt);
+    else if (s.d == 3) cells_count_kernel<3><<<blocks, 256, 0, st>>>(s, X, cg, cell_of, cell_cnt);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cells_scatter(int N, const int* cell_of, const int* cell_start, int* cell_cnt, int* sorted,
+                                 cudaStream_t st) {
+    cells_scatter_kernel<<<(N + 255) / 256, 256, 0, st>>>(N, cell_of, cell_start, cell_cnt, sorted);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cells_rows(const SpaceArgs& s, const float* X, const CellGrid& cg, const int* cell_of,
+                              const int* cell_start, const int* sorted, bool fill, int* out_count, int* max_deg,
+                              const int* row, int* col, float* cost, int* overflow, cudaStream_t st) {
+    if (s.d == 2)
+        return rows_t<2>(s, X, cg, cell_of, cell_start, sorted, fill, out_count, max_deg, row, col, cost, overflow, st);
+    if (s.d == 3)
+        return rows_t<3>(s, X, cg, cell_of, cell_start, sorted, fill, out_count, max_deg, row, col, cost, overflow, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace gmtk

@@ -58,6 +58,37 @@ struct FillDir {
 // Fills the out-CSR, and the in-CSR in the same launch when in.mask != NULL.
 cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, cudaStream_t st);
 
+// Cell-list neighbour search (geometric graphs, 2 or 3 dimensions): a uniform
+// grid over the position bounds whose cell side h is at least 1.01 r, so a
+// pair closer than r by the FP32 edge predicate lies in the same or adjacent
+// cells on every axis however the cell coordinates round (with at most 2^16
+// cells, the rounding of (x - lo) / h stays below 10^-4 cell, against a 1%
+// margin).  Cell index: ((c2 g1) + c1) g0 + c0.
+struct CellGrid {
+    int g[3];      // cells per axis (1 on unused axes)
+    float lo[3];
+    float inv_h;   // 1 / h
+    int ncells;
+};
+// Neighbours of one row that the fill sorts in shared memory; a row with more
+// falls back to the all-pairs build.
+constexpr int kCellList = 1024;
+// Returns false when the cell list does not apply (not a 2D/3D geometric
+// graph); *pays is false when the 3^d cells around a node would hold more than
+// a quarter of the domain.
+bool make_cell_grid(int kind, int d, const float* lo, const float* hi, float r, int N, CellGrid* cg, bool* pays);
+cudaError_t launch_cells_count(const SpaceArgs& s, const float* X, const CellGrid& cg, int* cell_of, int* cell_cnt,
+                               cudaStream_t st);
+// cell_cnt returns to zero.
+cudaError_t launch_cells_scatter(int N, const int* cell_of, const int* cell_start, int* cell_cnt, int* sorted,
+                                 cudaStream_t st);
+// fill = false: out_count[v] = neighbours of v, max_deg = their maximum; fill
+// = true: columns (ascending) and costs of every row at row[v]; a row longer
+// than kCellList sets *overflow and writes nothing.
+cudaError_t launch_cells_rows(const SpaceArgs& s, const float* X, const CellGrid& cg, const int* cell_of,
+                              const int* cell_start, const int* sorted, bool fill, int* out_count, int* max_deg,
+                              const int* row, int* col, float* cost, int* overflow, cudaStream_t st);
+
 // Workspace and control block of one plan (all device memory).  Counters are
 // double-buffered by iteration parity.  Open list j holds its kept entries in
 // [0, kept) and the nodes opened by the previous iteration in

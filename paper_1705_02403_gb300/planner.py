@@ -98,8 +98,9 @@ class Planner:
         self.cost = torch.empty(pb.N, dtype=torch.float32, device=device)
         self.path = torch.empty(pb.N, dtype=torch.int32, device=device)
 
-    def build(self, stream=None):
-        N.gmt_build_graph(self.space, self.boxes, [float(v) for v in self.pb.x_init], self.goal, self.params,
+    def build(self, stream=None, debug_flags=0):
+        params = params_struct(self.pb, debug_flags=debug_flags) if debug_flags else self.params
+        N.gmt_build_graph(self.space, self.boxes, [float(v) for v in self.pb.x_init], self.goal, params,
                           self.graph, stream)
         return self
 

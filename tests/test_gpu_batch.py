@@ -127,6 +127,28 @@ def test_lockstep_and_teams_agree_bit_for_bit(O):
     assert torch.equal(bp.cost.view(torch.int32), c_l.view(torch.int32))
 
 
+@pytest.mark.parametrize("flags", ["cells", "pairs"])
+def test_neighbour_build_choice_gives_the_same_queries(O, flags):
+    # Every geometric query forced onto the cell-list neighbour build (or onto
+    # the all-pairs test), small queries, a dense one whose rows outgrow the cell
+    # list's sort buffer (the batch is prepared again with all pairs for it) and
+    # double-integrator queries beside them: each equals the oracle.
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import BatchPlanner
+    qs = mixed_batch(seed=8, q=12) + [envgen.geometric(41, d=2, n=3000, nbox=4, r=1.3),
+                                      envgen.geometric(56, d=3, n=5000, nbox=20, r=0.0)]
+    bp = BatchPlanner(qs)
+    f = N.GMT_DEBUG_PAIRS_CELLS if flags == "cells" else N.GMT_DEBUG_PAIRS_ALL
+    for k, pb in enumerate(qs):
+        if pb.kind == envgen.EUCLID:
+            bp.queries[k].params.debug_flags = f
+    infos = bp.plan()
+    for k in range(len(qs)):
+        check_query(O, bp, k, infos)
+    infos2 = bp.plan()          # replayed
+    assert infos2 == infos
+
+
 def test_lockstep_runs_more_than_512_queries_in_chunks(O):
     # 600 small queries: the lockstep scheme runs them as two launches
     from paper_1705_02403_gb300.planner import BatchPlanner

@@ -119,6 +119,43 @@ def test_double_integrator_full_size(O, P):
         assert_same(O, G, *oracle_run(O, pb))
 
 
+def csr_of(P, pb, flags):
+    v = P.Planner(pb).build(debug_flags=flags).view()
+    return {k: getattr(v, k).cpu().numpy() for k in ("out_row", "out_col", "out_cost", "in_row", "in_col", "in_cost")}
+
+
+def same_csr(a, b):
+    return all(np.array_equal(a[k] if "cost" not in k else bits(a[k]), b[k] if "cost" not in k else bits(b[k]))
+               for k in a)
+
+
+@pytest.mark.parametrize("case", ["2d_small_r", "2d_ragged", "3d_thm1", "3d_boxes", "2d_dense_fallback",
+                                  "3d_dense_fallback", "2d_two_nodes"])
+def test_cell_list_and_all_pairs_give_the_oracle_csr(O, P, case):
+    # The 2D/3D geometric neighbour build picks a cell list when the radius is
+    # small against the domain.  Forced either way, it must give the oracle's
+    # CSR bit for bit; rows longer than the cell list's sort buffer (dense
+    # graphs) fall back to the all-pairs test.
+    from paper_1705_02403_gb300 import _native as N
+    pb = {"2d_small_r": envgen.geometric(51, d=2, n=3000, nbox=8, r=0.03),
+          "2d_ragged": envgen.geometric(52, d=2, n=1777, nbox=5, r=0.05),
+          "3d_thm1": envgen.geometric(53, d=3, n=4000, nbox=12, r=0.0),
+          "3d_boxes": envgen.geometric(54, d=3, n=2500, nbox=40, r=0.11),
+          "2d_dense_fallback": DENSE[0],
+          "3d_dense_fallback": DENSE[1],
+          "2d_two_nodes": envgen.geometric(55, d=2, n=1, nbox=0, r=0.05)}[case]
+    cells = csr_of(P, pb, N.GMT_DEBUG_PAIRS_CELLS)
+    pairs = csr_of(P, pb, N.GMT_DEBUG_PAIRS_ALL)
+    auto = csr_of(P, pb, 0)
+    assert same_csr(cells, pairs) and same_csr(auto, pairs)
+    X, goal = O.sample(pb)
+    r = pb.r if pb.r > 0 else np.float32(O.radius_thm1(pb.n, pb.d))
+    c = O.Graph(pb.kind, pb.d, pb.dp, X, goal, r).csr()
+    ref = {"out_row": c.out_row, "out_col": c.out_col, "out_cost": c.out_cost, "in_row": c.in_row,
+           "in_col": c.in_col, "in_cost": c.in_cost}
+    assert same_csr(cells, ref)
+
+
 def test_double_integrator_filters_keep_every_edge_on_adversarial_states(O, P):
     # The pair filter tests every pair with conservative bounds before the exact
     # procedure.  States appended in tight families (tiny position changes,
