@@ -109,9 +109,13 @@ typedef struct {
  * a cell list (candidates from the grid cells around each node) when the
  * radius is small against the domain and the all-pairs test otherwise; both
  * give the same CSR.  PAIRS_ALL forces the all-pairs test, PAIRS_CELLS the cell
- * list (rows with more than 1024 neighbours still fall back to all pairs). */
+ * list.  The cell list orders a row's columns with a bitmap of the row when
+ * the graph has at most 32768 nodes, else by sorting a list of at most 1024
+ * (a longer row falls back to the all-pairs test); CELLS_LIST forces the list
+ * at any size. */
 #define GMT_DEBUG_PAIRS_ALL 0x2u
 #define GMT_DEBUG_PAIRS_CELLS 0x4u
+#define GMT_DEBUG_CELLS_LIST 0x8u
 
 typedef struct gmt_graph gmt_graph;
 

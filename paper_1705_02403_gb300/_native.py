@@ -19,7 +19,7 @@ GMT_ERR_INVALID, GMT_ERR_OOM, GMT_ERR_CUDA, GMT_ERR_TIMEOUT, GMT_ERR_ITER_LIMIT,
 GMT_COST_EUCLID, GMT_COST_DI = 0, 1
 GMT_MAX_DIM = 10
 GMT_DEBUG_UNREACHABLE_BARRIER = 0x1
-GMT_DEBUG_PAIRS_ALL, GMT_DEBUG_PAIRS_CELLS = 0x2, 0x4
+GMT_DEBUG_PAIRS_ALL, GMT_DEBUG_PAIRS_CELLS, GMT_DEBUG_CELLS_LIST = 0x2, 0x4, 0x8
 
 STATUS_NAMES = {0: "GMT_OK", 1: "GMT_NO_PATH", -1: "GMT_ERR_INVALID", -2: "GMT_ERR_OOM", -3: "GMT_ERR_CUDA",
                 -4: "GMT_ERR_TIMEOUT", -5: "GMT_ERR_ITER_LIMIT", -6: "GMT_ERR_ADMISSION"}

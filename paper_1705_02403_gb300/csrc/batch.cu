@@ -137,7 +137,9 @@ __global__ void __launch_bounds__(256) batch_cells_scatter_kernel(const QueryDev
 // count outgrew its slice.
 template <int D, bool FILL>
 __global__ void __launch_bounds__(kCellWarps * 32) batch_cells_rows_kernel(const QueryDev* __restrict__ Q,
-                                                                           const long long* __restrict__ off, int nq) {
+                                                                           const long long* __restrict__ off, int nq,
+                                                                           int words) {
+    extern __shared__ int cell_buf[];
     const long long w = (long long)blockIdx.x * kCellWarps + (threadIdx.x >> 5);
     if (w >= off[nq]) return;
     const int k = find_query(off, nq, w);
@@ -145,7 +147,8 @@ __global__ void __launch_bounds__(kCellWarps * 32) batch_cells_rows_kernel(const
     if (!q.use_cells) return;
     if (FILL && (long long)q.out_row[q.s.N] > q.edge_cap) return;
     cell_row<D, FILL>(q.s, q.X, q.cg, q.cell_of, q.cell_start, q.cell_sorted, q.out_count, q.cell_info, q.out_row,
-                      q.out_col, q.out_cost, q.cell_info + 1, (int)(w - off[k]));
+                      q.out_col, q.out_cost, q.cell_info + 1, cell_buf + (threadIdx.x >> 5) * words,
+                      (int)(w - off[k]));
     if (FILL && (threadIdx.x & 31) == 0 && __ldcg(&q.cell_info[1]) != 0) q.out_row[q.s.N] = INT_MAX;
 }
 
@@ -213,14 +216,17 @@ cudaError_t batch_cells_front(int d, const QueryDev* Q, const long long* off, in
     else return cudaErrorInvalidValue;
     batch_cells_scan_kernel<<<nq, 1024, 0, st>>>(Q);
     batch_cells_scatter_kernel<<<tb, 256, 0, st>>>(Q, off, nq);
-    if (d == 2) batch_cells_rows_kernel<2, false><<<wb, kCellWarps * 32, 0, st>>>(Q, off, nq);
-    else batch_cells_rows_kernel<3, false><<<wb, kCellWarps * 32, 0, st>>>(Q, off, nq);
+    if (d == 2) batch_cells_rows_kernel<2, false><<<wb, kCellWarps * 32, 0, st>>>(Q, off, nq, 0);
+    else batch_cells_rows_kernel<3, false><<<wb, kCellWarps * 32, 0, st>>>(Q, off, nq, 0);
     return cudaGetLastError();
 }
-cudaError_t batch_cells_fill(int d, const QueryDev* Q, const long long* off, int nq, long long rows, cudaStream_t st) {
+// words: the largest cell_fill_words of the group's cell-list queries
+cudaError_t batch_cells_fill(int d, const QueryDev* Q, const long long* off, int nq, long long rows, int words,
+                             cudaStream_t st) {
     const unsigned wb = (unsigned)((rows + kCellWarps - 1) / kCellWarps);
-    if (d == 2) batch_cells_rows_kernel<2, true><<<wb, kCellWarps * 32, 0, st>>>(Q, off, nq);
-    else if (d == 3) batch_cells_rows_kernel<3, true><<<wb, kCellWarps * 32, 0, st>>>(Q, off, nq);
+    const size_t smem = (size_t)kCellWarps * words * sizeof(int);
+    if (d == 2) batch_cells_rows_kernel<2, true><<<wb, kCellWarps * 32, smem, st>>>(Q, off, nq, words);
+    else if (d == 3) batch_cells_rows_kernel<3, true><<<wb, kCellWarps * 32, smem, st>>>(Q, off, nq, words);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -294,6 +300,7 @@ struct Group {
     std::vector<int> chunk_start, chunk_count, chunk_nodes, chunk_base, chunk_ctl;
     DevBuf lock_base;
     bool any_cells = false;  // some member builds its neighbours with the cell list
+    int cell_words = 0;      // largest fill buffer (words per warp) of those members
 };
 
 }  // namespace
@@ -462,7 +469,9 @@ gmt_status enqueue_build_back(gmt_batch* b, int32_t* parent, float* cost, cudaSt
         const int nq = (int)g.members.size();
         const QueryDev* Q = g.desc.as<QueryDev>();
         BCUDA(batch_fill(g.kind, g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, st), "batched fill");
-        if (g.any_cells) BCUDA(batch_cells_fill(g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, st), "batched cells");
+        if (g.any_cells)
+            BCUDA(batch_cells_fill(g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, g.cell_words, st),
+                  "batched cells");
     }
     BCUDA(cudaMemsetAsync(b->ctl.p, 0, b->ctl.cap, st), "memset");
     for (cudaEvent_t& e : b->ev_plan)
@@ -564,6 +573,7 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         const unsigned dbg = Qh.params.debug_flags;
         const bool applies = make_cell_grid(Qh.space.kind, Qh.space.dim, Qh.space.lo, Qh.space.hi, b->r[k], N,
                                             &cgs[k], &pays);
+        if (dbg & GMT_DEBUG_CELLS_LIST) cgs[k].list_only = 1;
         use_cells[k] = applies && !(dbg & GMT_DEBUG_PAIRS_ALL) && (pays || (dbg & GMT_DEBUG_PAIRS_CELLS)) &&
                        !(k < (int)force_pairs.size() && force_pairs[k]);
         xo[k] = xs; xs += (size_t)Qh.space.dim * P;
@@ -647,10 +657,12 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         std::vector<QueryDev> dq(nq);
         g.max_n = 0; g.max_boxes = 0;
         g.any_cells = false;
+        g.cell_words = 0;
         for (int i = 0; i < nq; ++i) {
             const int k = g.members[i];
             const int N = b->N[k], W = (N + 31) / 32;
             g.any_cells = g.any_cells || use_cells[k];
+            if (use_cells[k]) g.cell_words = std::max(g.cell_words, cell_fill_words(cgs[k], N));
             const long long tiles = use_cells[k] ? 0
                                     : g.kind == GMT_COST_DI
                                         ? (long long)((N + kDIRows - 1) / kDIRows) * ((W + kDIWords - 1) / kDIWords)
@@ -693,7 +705,7 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         force.resize(q, 0);
         bool again = false;
         for (int k = 0; k < q; ++k)
-            if (use_cells[k] && cell_info[2 * k] > kCellList) {
+            if (use_cells[k] && !cell_fill_fits(cgs[k], b->N[k], cell_info[2 * k])) {
                 force[k] = 1;
                 again = true;
             }

@@ -276,6 +276,7 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     CellGrid cg;
     bool cells_pay = false;
     bool cells = make_cell_grid(g->kind, g->d, space->lo, space->hi, g->r, g->N, &cg, &cells_pay);
+    if (params->debug_flags & GMT_DEBUG_CELLS_LIST) cg.list_only = 1;
     if (params->debug_flags & GMT_DEBUG_PAIRS_ALL) cells = false;
     else if (!(params->debug_flags & GMT_DEBUG_PAIRS_CELLS)) cells = cells && cells_pay;
     LAUNCH(g->mark(gmt_graph::kPair, 0, st), "event");
@@ -310,7 +311,7 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     LAUNCH(cudaMemcpyAsync(g->h_scalars + 2, g->out_row + N, sizeof(int), cudaMemcpyDeviceToHost, st),
            "edge count readback");
     LAUNCH(cudaStreamSynchronize(st), "graph build");
-    if (cells && g->h_scalars[1] > kCellList) {
+    if (cells && !cell_fill_fits(cg, g->N, g->h_scalars[1])) {
         // a row too long to sort in shared memory: the all-pairs test instead
         cells = false;
         GROW(mask, W * P);

@@ -26,9 +26,10 @@ __global__ void __launch_bounds__(kCellWarps * 32) cells_rows_kernel(SpaceArgs s
                                                                      int* __restrict__ max_deg,
                                                                      const int* __restrict__ row,
                                                                      int* __restrict__ col, float* __restrict__ cost,
-                                                                     int* __restrict__ overflow) {
+                                                                     int* __restrict__ overflow, int words) {
+    extern __shared__ int cell_buf[];
     cell_row<D, FILL>(s, X, cg, cell_of, start, sorted, out_count, max_deg, row, col, cost, overflow,
-                      blockIdx.x * kCellWarps + (threadIdx.x >> 5));
+                      cell_buf + (threadIdx.x >> 5) * words, blockIdx.x * kCellWarps + (threadIdx.x >> 5));
 }
 
 bool make_cell_grid(int kind, int d, const float* lo, const float* hi, float r, int N, CellGrid* cg, bool* pays) {
@@ -57,7 +58,11 @@ bool make_cell_grid(int kind, int d, const float* lo, const float* hi, float r, 
     cg->inv_h = (float)(1.0 / h);
     while ((double)r * 1.01 * (double)cg->inv_h > 1.0) cg->inv_h = std::nextafter(cg->inv_h, 0.0f);
     cg->ncells = (int)ncells;
-    *pays = frac <= 0.25 && N >= 4096;
+    cg->list_only = 0;
+    // measured on one GB300 (Theorem 1 radii): in 2D the cell list overtakes
+    // the all-pairs test near 4096 nodes; in 3D, with 27 cells of candidates
+    // per row, only beyond 16384
+    *pays = frac <= 0.25 && N >= (d == 2 ? 4096 : 32768);
     return true;
 }
 
@@ -67,12 +72,13 @@ cudaError_t rows_t(const SpaceArgs& s, const float* X, const CellGrid& cg, const
                    const int* sorted, bool fill, int* out_count, int* max_deg, const int* row, int* col, float* cost,
                    int* overflow, cudaStream_t st) {
     const int blocks = (s.N + kCellWarps - 1) / kCellWarps;
+    const int words = cell_fill_words(cg, s.N);
     if (fill)
-        cells_rows_kernel<D, true><<<blocks, kCellWarps * 32, 0, st>>>(s, X, cg, cell_of, start, sorted, out_count,
-                                                                        max_deg, row, col, cost, overflow);
+        cells_rows_kernel<D, true><<<blocks, kCellWarps * 32, (size_t)kCellWarps * words * sizeof(int), st>>>(
+            s, X, cg, cell_of, start, sorted, out_count, max_deg, row, col, cost, overflow, words);
     else
         cells_rows_kernel<D, false><<<blocks, kCellWarps * 32, 0, st>>>(s, X, cg, cell_of, start, sorted, out_count,
-                                                                         max_deg, row, col, cost, overflow);
+                                                                         max_deg, row, col, cost, overflow, 0);
     return cudaGetLastError();
 }
 }  // namespace

@@ -69,9 +69,15 @@ struct CellGrid {
     float lo[3];
     float inv_h;   // 1 / h
     int ncells;
+    int list_only;  // the fill sorts a list even where a bitmap would fit (test hook)
 };
-// Neighbours of one row that the fill sorts in shared memory; a row with more
-// falls back to the all-pairs build.
+// Shared-memory words per warp of the cell-list fill: a bitmap of the row's
+// columns for graphs of at most 32 kCellList nodes, else a list of at most
+// kCellList neighbours to sort (a longer row falls back to the all-pairs
+// build).  cell_fill_fits says whether a longest row of max_deg fits.
+__host__ __device__ inline bool cell_fill_fits(const CellGrid& cg, int N, int max_deg) {
+    return (!cg.list_only && (N + 31) / 32 <= 1024) || max_deg <= 1024;
+}
 constexpr int kCellList = 1024;
 // Returns false when the cell list does not apply (not a 2D/3D geometric
 // graph); *pays is false when the 3^d cells around a node would hold more than

@@ -127,7 +127,7 @@ def test_lockstep_and_teams_agree_bit_for_bit(O):
     assert torch.equal(bp.cost.view(torch.int32), c_l.view(torch.int32))
 
 
-@pytest.mark.parametrize("flags", ["cells", "pairs"])
+@pytest.mark.parametrize("flags", ["cells", "cells_list", "pairs"])
 def test_neighbour_build_choice_gives_the_same_queries(O, flags):
     # Every geometric query forced onto the cell-list neighbour build (or onto
     # the all-pairs test), small queries, a dense one whose rows outgrow the cell
@@ -138,7 +138,8 @@ def test_neighbour_build_choice_gives_the_same_queries(O, flags):
     qs = mixed_batch(seed=8, q=12) + [envgen.geometric(41, d=2, n=3000, nbox=4, r=1.3),
                                       envgen.geometric(56, d=3, n=5000, nbox=20, r=0.0)]
     bp = BatchPlanner(qs)
-    f = N.GMT_DEBUG_PAIRS_CELLS if flags == "cells" else N.GMT_DEBUG_PAIRS_ALL
+    f = {"cells": N.GMT_DEBUG_PAIRS_CELLS, "cells_list": N.GMT_DEBUG_PAIRS_CELLS | N.GMT_DEBUG_CELLS_LIST,
+         "pairs": N.GMT_DEBUG_PAIRS_ALL}[flags]
     for k, pb in enumerate(qs):
         if pb.kind == envgen.EUCLID:
             bp.queries[k].params.debug_flags = f

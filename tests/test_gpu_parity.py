@@ -133,9 +133,10 @@ def same_csr(a, b):
                                   "3d_dense_fallback", "2d_two_nodes"])
 def test_cell_list_and_all_pairs_give_the_oracle_csr(O, P, case):
     # The 2D/3D geometric neighbour build picks a cell list when the radius is
-    # small against the domain.  Forced either way, it must give the oracle's
-    # CSR bit for bit; rows longer than the cell list's sort buffer (dense
-    # graphs) fall back to the all-pairs test.
+    # small against the domain.  Forced either way, and with either way of
+    # ordering a row (bitmap or sorted list), it must give the oracle's CSR bit
+    # for bit; rows longer than the list (dense graphs) fall back to the
+    # all-pairs test.
     from paper_1705_02403_gb300 import _native as N
     pb = {"2d_small_r": envgen.geometric(51, d=2, n=3000, nbox=8, r=0.03),
           "2d_ragged": envgen.geometric(52, d=2, n=1777, nbox=5, r=0.05),
@@ -145,9 +146,10 @@ def test_cell_list_and_all_pairs_give_the_oracle_csr(O, P, case):
           "3d_dense_fallback": DENSE[1],
           "2d_two_nodes": envgen.geometric(55, d=2, n=1, nbox=0, r=0.05)}[case]
     cells = csr_of(P, pb, N.GMT_DEBUG_PAIRS_CELLS)
+    listed = csr_of(P, pb, N.GMT_DEBUG_PAIRS_CELLS | N.GMT_DEBUG_CELLS_LIST)
     pairs = csr_of(P, pb, N.GMT_DEBUG_PAIRS_ALL)
     auto = csr_of(P, pb, 0)
-    assert same_csr(cells, pairs) and same_csr(auto, pairs)
+    assert same_csr(cells, pairs) and same_csr(listed, pairs) and same_csr(auto, pairs)
     X, goal = O.sample(pb)
     r = pb.r if pb.r > 0 else np.float32(O.radius_thm1(pb.n, pb.d))
     c = O.Graph(pb.kind, pb.d, pb.dp, X, goal, r).csr()
