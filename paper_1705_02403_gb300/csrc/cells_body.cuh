@@ -1,6 +1,6 @@
-// Cell-list neighbour search for geometric graphs in 2 and 3 dimensions (an
-// acceleration of the all-pairs neighbour test of Section III-A; Section VI
-// names spatial data structures as the way to large sample counts).  Nodes are
+// Cell-list neighbour search for geometric graphs in 2 and 3 dimensions: a
+// faster way to the same neighbour sets (Section III-A's r-disk neighbours,
+// precomputed in Section V-A), not a change of the method.  Nodes are
 // counting-sorted by grid cell; a row's candidates are the nodes of the 3^d
 // cells around its own, which lie in 3^(d-1) runs of consecutive cells along
 // axis 0.  Every candidate takes the same FP32 edge predicate as the all-pairs
