@@ -639,6 +639,88 @@ int orc_sample(int d, int dp, const float* lo, const float* hi, int nbox, const 
     return ORC_OK;
 }
 
+// ---- Halton SampleFree (the low-dispersion sequence of Sec. V, "Halton
+// sequence"; our reading of how it meets SampleFree's contract) ----
+// Point k >= 1 of the Halton sequence has coordinate a equal to the radical
+// inverse of k in the a-th prime base: writing k = sum_i d_i p^i, it is
+// sum_i d_i p^-(i+1).  It is evaluated exactly as the fraction R / p^m (R the
+// digits of k reversed, m their count), rounded to double and then to float.
+static const uint32_t kHaltonPrimes[MAXD] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29};
+
+float halton_unit(uint32_t k, uint32_t p) {
+    uint64_t R = 0, P = 1;
+    while (k > 0) {
+        R = R * p + k % p;
+        P *= p;
+        k /= p;
+    }
+    return (float)((double)R / (double)P);
+}
+
+// Node 0 = x_init.  Node 1 = the first Halton point (k = 1, 2, ...), mapped into
+// the goal ball's bounding box on the goal axes and into X on the others, that
+// lies in X, in the goal ball and outside every box.  Nodes 2..n = the Halton
+// points mapped into X that lie outside every box, in the order of k.  At most
+// max_candidates points are tried for node 1 and for nodes 2..n each.
+int orc_sample_halton(int d, int dp, const float* lo, const float* hi, int nbox, const float* blo, const float* bhi,
+                      const float* x_init, const float* goal_c, float goal_r, int goal_pos_only, int n,
+                      long long max_candidates, float* X, uint8_t* is_goal) {
+    if (d < 1 || d > MAXD || dp < 1 || dp > d || n < 1) return ORC_ERR_INVALID;
+    Boxes B{nbox, dp, blo, bhi};
+    const int N = n + 1;
+    const int gd = goal_pos_only ? dp : d;
+    for (int a = 0; a < d; ++a)
+        if (!(lo[a] <= x_init[a] && x_init[a] <= hi[a])) return ORC_ERR_INVALID;
+    if (point_in_obstacle(x_init, B)) return ORC_ERR_INVALID;
+    for (int a = 0; a < d; ++a) X[(size_t)a * N + 0] = x_init[a];
+    float x[MAXD];
+    if (N > 1) {
+        bool found = false;
+        for (long long k = 1; k <= max_candidates && !found; ++k) {
+            for (int a = 0; a < d; ++a) {
+                const float u = halton_unit((uint32_t)k, kHaltonPrimes[a]);
+                float l = lo[a], h = hi[a];
+                if (a < gd) { l = goal_c[a] - goal_r; h = goal_c[a] + goal_r; }
+                x[a] = l + u * (h - l);
+            }
+            bool inb = true;
+            for (int a = 0; a < d; ++a) if (!(lo[a] <= x[a] && x[a] <= hi[a])) inb = false;
+            if (!inb || !in_goal(x, gd, goal_c, goal_r) || point_in_obstacle(x, B)) continue;
+            for (int a = 0; a < d; ++a) X[(size_t)a * N + 1] = x[a];
+            found = true;
+        }
+        if (!found) return ORC_ERR_INVALID;
+    }
+    int v = 2;
+    for (long long k = 1; v < N; ++k) {
+        if (k > max_candidates) return ORC_ERR_INVALID;
+        for (int a = 0; a < d; ++a) {
+            const float u = halton_unit((uint32_t)k, kHaltonPrimes[a]);
+            x[a] = lo[a] + u * (hi[a] - lo[a]);
+        }
+        if (point_in_obstacle(x, B)) continue;
+        for (int a = 0; a < d; ++a) X[(size_t)a * N + v] = x[a];
+        ++v;
+    }
+    for (int k = 0; k < N; ++k) {
+        for (int a = 0; a < d; ++a) x[a] = X[(size_t)a * N + k];
+        is_goal[k] = in_goal(x, gd, goal_c, goal_r) ? 1 : 0;
+    }
+    return ORC_OK;
+}
+
+float orc_halton_unit(uint32_t k, uint32_t p) { return halton_unit(k, p); }
+
+// Connection radius for low-dispersion samples (Sec. III-B: a smaller r than
+// Theorem 1's may be used; our reading drops Theorem 1's log n factor):
+// 4 ((1 + eta) (1/d) (mu / zeta_d) (1/n))^(1/d).
+double orc_radius_halton(int n, int d, double eta, double mu) {
+    const double pi = 3.14159265358979323846;
+    double zeta = std::pow(pi, (double)d / 2.0) / std::tgamma((double)d / 2.0 + 1.0);
+    double base = (1.0 + eta) * (1.0 / (double)d) * (mu / zeta) * (1.0 / (double)n);
+    return 4.0 * std::pow(base, 1.0 / (double)d);
+}
+
 int orc_in_goal(const float* x, int gd, const float* c, float rho) { return in_goal(x, gd, c, rho) ? 1 : 0; }
 
 float orc_cost_euclid_f32(const float* from, const float* to, int d) { return cost_euclid(from, to, d); }

@@ -67,6 +67,10 @@ def lib():
         L.orc_edge_free_di_f32.argtypes = [P, P, F32, I32, P, P, I32, P, P]
         L.orc_edge_free_di_f32.restype = I32
         L.orc_radius_thm1.argtypes = [I32, I32, F64, F64]; L.orc_radius_thm1.restype = F64
+        L.orc_radius_halton.argtypes = [I32, I32, F64, F64]; L.orc_radius_halton.restype = F64
+        L.orc_halton_unit.argtypes = [C.c_uint32, C.c_uint32]; L.orc_halton_unit.restype = F32
+        L.orc_sample_halton.argtypes = [I32, I32, P, P, I32, P, P, P, P, F32, I32, I32, C.c_int64, P, P]
+        L.orc_sample_halton.restype = I32
         L.orc_graph_build.argtypes = [I32, I32, I32, I32, I32, P, P, F32]; L.orc_graph_build.restype = P
         L.orc_graph_free.argtypes = [I32, P]
         L.orc_graph_num_edges.argtypes = [I32, P]; L.orc_graph_num_edges.restype = I64
@@ -155,6 +159,32 @@ def edge_free_di(y, x, tau, points, pos_lo, pos_hi, box_lo, box_hi):
 
 def radius_thm1(n: int, d: int, eta: float = 0.0, mu: float = 1.0) -> float:
     return lib().orc_radius_thm1(n, d, eta, mu)
+
+
+def radius_halton(n: int, d: int, eta: float = 0.0, mu: float = 1.0) -> float:
+    return lib().orc_radius_halton(n, d, eta, mu)
+
+
+def halton_unit(k: int, p: int) -> float:
+    return lib().orc_halton_unit(k, p)
+
+
+def sample_halton(problem, max_candidates: int | None = None):
+    """Halton SampleFree for a problem: (X [d][N] float32, is_goal [N] uint8)."""
+    pb = problem
+    d, dp, n = pb.d, pb.dp, pb.n
+    N = n + 1
+    X = np.zeros((d, N), dtype=np.float32)
+    goal = np.zeros(N, dtype=np.uint8)
+    lo, hi = _f32(pb.lo), _f32(pb.hi)
+    bl, bh = _f32(pb.box_lo).reshape(-1, dp), _f32(pb.box_hi).reshape(-1, dp)
+    xi, gc = _f32(pb.x_init), _f32(pb.goal_center)
+    cap = max_candidates if max_candidates is not None else 64 * N + 65536
+    st = lib().orc_sample_halton(d, dp, _p(lo), _p(hi), bl.shape[0], _p(bl), _p(bh), _p(xi), _p(gc),
+                                 np.float32(pb.goal_radius), int(pb.goal_pos_only), n, cap, _p(X), _p(goal))
+    if st != OK:
+        raise ValueError(f"oracle Halton sampling failed with status {st}")
+    return X, goal
 
 
 def in_goal(x, gd, c, rho):
