@@ -99,7 +99,23 @@ typedef struct {
     float mu_free;        /* Lebesgue measure of X_free (upper bound), used when r <= 0 */
     int32_t spin_limit;   /* polls of a device-side wait before GMT_ERR_TIMEOUT; <= 0 = default */
     uint32_t debug_flags; /* GMT_DEBUG_*: test hooks, 0 in normal use */
+    int32_t sampler;      /* GMT_SAMPLER_*: how SampleFree draws its n samples */
 } gmt_params;
+
+/* SampleFree variants.
+ *   GMT_SAMPLER_PHILOX: i.i.d. uniform samples (Philox4x32-10 keyed by seed);
+ *     node 1 uniform in X_goal n X_free, nodes 2..n uniform in X_free, by
+ *     rejection (max_attempts per node).
+ *   GMT_SAMPLER_HALTON: the deterministic low-dispersion Halton sequence that
+ *     the paper's experiments use (Sec. V): point k >= 1 has coordinate a equal
+ *     to the radical inverse of k in the a-th prime base (2, 3, 5, 7, ...),
+ *     mapped affinely onto X.  Node 1 is the first point mapped into the goal
+ *     ball's bounding box (goal axes) that lies in X_goal n X_free; nodes 2..n
+ *     are the points of X_free in the order of k.  seed is unused; at most
+ *     max_attempts + 64 N points are tried per sequence (max_attempts <= 0:
+ *     65536); r <= 0 selects gmt_connection_radius_halton. */
+#define GMT_SAMPLER_PHILOX 0
+#define GMT_SAMPLER_HALTON 1
 
 /* Test hook: the plan kernel's inter-block barrier waits for one more arrival
  * than there are blocks, so every wait runs out and the call returns
@@ -483,6 +499,12 @@ gmt_status gmt_graph_get_profile(gmt_graph* graph, gmt_profile* profile);
  * (log n / n)^(1/d), zeta_d the volume of the unit d-ball, evaluated in double
  * as 4 * pow((1+eta) * (1/d) * (mu_free/zeta_d) * (log(n)/n), 1/d). */
 double gmt_connection_radius(int32_t n, int32_t d, double eta, double mu_free);
+
+/* Radius for low-dispersion (Halton) samples.  Sec. III-B allows a smaller r
+ * than Theorem 1's for such sequences without fixing one; this library's
+ * reading drops Theorem 1's log n factor: 4 * pow((1+eta) * (1/d) *
+ * (mu_free/zeta_d) * (1/n), 1/d). */
+double gmt_connection_radius_halton(int32_t n, int32_t d, double eta, double mu_free);
 
 /* Message for the last non-OK status returned to this host thread. */
 const char* gmt_last_error(void);

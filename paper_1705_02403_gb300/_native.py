@@ -20,6 +20,7 @@ GMT_COST_EUCLID, GMT_COST_DI = 0, 1
 GMT_MAX_DIM = 10
 GMT_DEBUG_UNREACHABLE_BARRIER = 0x1
 GMT_DEBUG_PAIRS_ALL, GMT_DEBUG_PAIRS_CELLS, GMT_DEBUG_CELLS_LIST = 0x2, 0x4, 0x8
+GMT_SAMPLER_PHILOX, GMT_SAMPLER_HALTON = 0, 1
 
 STATUS_NAMES = {0: "GMT_OK", 1: "GMT_NO_PATH", -1: "GMT_ERR_INVALID", -2: "GMT_ERR_OOM", -3: "GMT_ERR_CUDA",
                 -4: "GMT_ERR_TIMEOUT", -5: "GMT_ERR_ITER_LIMIT", -6: "GMT_ERR_ADMISSION"}
@@ -48,7 +49,7 @@ class gmt_params(C.Structure):
     _fields_ = [("n", C.c_int32), ("r", C.c_float), ("lambda_", C.c_float), ("seed", C.c_uint64),
                 ("seg_spacing", C.c_float), ("traj_points", C.c_int32), ("max_iters", C.c_int32),
                 ("max_attempts", C.c_int32), ("eta", C.c_float), ("mu_free", C.c_float),
-                ("spin_limit", C.c_int32), ("debug_flags", C.c_uint32)]
+                ("spin_limit", C.c_int32), ("debug_flags", C.c_uint32), ("sampler", C.c_int32)]
 
 
 class gmt_graph_view(C.Structure):
@@ -160,6 +161,7 @@ SIGNATURES = {
     "gmt_server_close_session": (_I32, [_P, _I32]),
     "gmt_server_session_view": (_I32, [_P, _I32, C.POINTER(gmt_graph_view)]),
     "gmt_connection_radius": (_F64, [_I32, _I32, _F64, _F64]),
+    "gmt_connection_radius_halton": (_F64, [_I32, _I32, _F64, _F64]),
     "gmt_last_error": (C.c_char_p, []),
 }
 
@@ -201,6 +203,10 @@ def gmt_last_error() -> str:
 
 def gmt_connection_radius(n: int, d: int, eta: float = 0.0, mu_free: float = 1.0) -> float:
     return lib.gmt_connection_radius(n, d, eta, mu_free)
+
+
+def gmt_connection_radius_halton(n: int, d: int, eta: float = 0.0, mu_free: float = 1.0) -> float:
+    return lib.gmt_connection_radius_halton(n, d, eta, mu_free)
 
 
 class Graph:

@@ -67,7 +67,16 @@ __global__ void __launch_bounds__(128) batch_sample_kernel(const QueryDev* __res
     if (t >= off[nq]) return;
     const int k = find_query(off, nq, t);
     const QueryDev& q = Q[k];
+    if (q.s.sampler == GMT_SAMPLER_HALTON) return;  // batch_halton_kernel
     sample_node<D, DP>(q.s, q.boxes, q.X, q.is_goal, q.flags, (int)(t - off[k]));
+}
+
+// One block per query of the group; queries that sample with Philox return.
+template <int D, int DP>
+__global__ void __launch_bounds__(kHaltonThreads) batch_halton_kernel(const QueryDev* __restrict__ Q) {
+    const QueryDev& q = Q[blockIdx.x];
+    if (q.s.sampler != GMT_SAMPLER_HALTON) return;
+    halton_sample_block<D, DP>(q.s, q.boxes, q.X, q.is_goal, q.flags);
 }
 
 template <int KIND, int D>
@@ -174,8 +183,9 @@ __global__ void __launch_bounds__(kFillWarps * 32) batch_fill_kernel(const Query
 
 namespace {
 template <int D, int DP>
-void sample_g(const QueryDev* Q, const long long* off, int nq, long long total, cudaStream_t st) {
+void sample_g(const QueryDev* Q, const long long* off, int nq, long long total, bool halton, cudaStream_t st) {
     batch_sample_kernel<D, DP><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(Q, off, nq);
+    if (halton) batch_halton_kernel<D, DP><<<nq, kHaltonThreads, 0, st>>>(Q);
 }
 template <int KIND, int D>
 void mask_g(const QueryDev* Q, const long long* off, int nq, long long tiles, cudaStream_t st) {
@@ -190,10 +200,10 @@ void fill_g(const QueryDev* Q, const long long* off, int nq, long long rows, cud
 }  // namespace
 
 cudaError_t batch_sample(int kind, int d, const QueryDev* Q, const long long* off, int nq, long long total,
-                         cudaStream_t st) {
-    if (kind == GMT_COST_DI) sample_g<6, 3>(Q, off, nq, total, st);
-    else if (d == 2) sample_g<2, 2>(Q, off, nq, total, st);
-    else if (d == 3) sample_g<3, 3>(Q, off, nq, total, st);
+                         bool halton, cudaStream_t st) {
+    if (kind == GMT_COST_DI) sample_g<6, 3>(Q, off, nq, total, halton, st);
+    else if (d == 2) sample_g<2, 2>(Q, off, nq, total, halton, st);
+    else if (d == 3) sample_g<3, 3>(Q, off, nq, total, halton, st);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -301,6 +311,7 @@ struct Group {
     DevBuf lock_base;
     bool any_cells = false;  // some member builds its neighbours with the cell list
     int cell_words = 0;      // largest fill buffer (words per warp) of those members
+    bool any_halton = false; // some member samples with the Halton sequence
 };
 
 }  // namespace
@@ -368,6 +379,8 @@ gmt_status check_query(const gmt_query& Qh, int k) {
     const gmt_params& p = Qh.params;
     if (p.n < 1 || p.n > (1 << 24)) return bfail(GMT_ERR_INVALID, "n must be in [1, 2^24]" + at);
     if (!(p.lambda >= 0.0f && p.lambda <= 1.0f)) return bfail(GMT_ERR_INVALID, "lambda must be in [0, 1]" + at);
+    if (p.sampler != GMT_SAMPLER_PHILOX && p.sampler != GMT_SAMPLER_HALTON)
+        return bfail(GMT_ERR_INVALID, "sampler must be GMT_SAMPLER_PHILOX or GMT_SAMPLER_HALTON" + at);
     if (p.r <= 0.0f && (!(p.eta >= 0.0f) || !(p.mu_free > 0.0f)))
         return bfail(GMT_ERR_INVALID, "r <= 0 needs eta >= 0 and mu_free > 0" + at);
     if (!(p.seg_spacing > 0.0f) || p.traj_points < 2)
@@ -449,7 +462,8 @@ gmt_status enqueue_build_front(gmt_batch* b, cudaStream_t st) {
     for (Group& g : b->groups) {
         const int nq = (int)g.members.size();
         const QueryDev* Q = g.desc.as<QueryDev>();
-        BCUDA(batch_sample(g.kind, g.d, Q, g.off_nodes.as<long long>(), nq, g.nodes, st), "batched sample kernel");
+        BCUDA(batch_sample(g.kind, g.d, Q, g.off_nodes.as<long long>(), nq, g.nodes, g.any_halton, st),
+              "batched sample kernel");
         BCUDA(batch_mask(g.kind, g.d, Q, g.off_tiles.as<long long>(), nq, g.tiles, st), "batched pair filter");
         if (g.any_cells) BCUDA(batch_cells_front(g.d, Q, g.off_nodes.as<long long>(), nq, g.nodes, st), "batched cells");
         if (g.kind == GMT_COST_DI) {
@@ -567,8 +581,9 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         b->N[k] = N; b->pitch[k] = P;
         b->node_base[k + 1] = b->node_base[k] + N;
         b->r[k] = Qh.params.r > 0.0f ? Qh.params.r
-                                     : (float)gmt_connection_radius(Qh.params.n, Qh.space.dim, Qh.params.eta,
-                                                                    Qh.params.mu_free);
+                  : Qh.params.sampler == GMT_SAMPLER_HALTON
+                      ? (float)gmt_connection_radius_halton(Qh.params.n, Qh.space.dim, Qh.params.eta, Qh.params.mu_free)
+                      : (float)gmt_connection_radius(Qh.params.n, Qh.space.dim, Qh.params.eta, Qh.params.mu_free);
         bool pays = false;
         const unsigned dbg = Qh.params.debug_flags;
         const bool applies = make_cell_grid(Qh.space.kind, Qh.space.dim, Qh.space.lo, Qh.space.hi, b->r[k], N,
@@ -626,6 +641,8 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         s.key1 = (uint32_t)(Qh.params.seed >> 32);
         s.stream = 0;
         s.max_attempts = Qh.params.max_attempts > 0 ? Qh.params.max_attempts : 65536;
+        s.sampler = Qh.params.sampler;
+        s.halton_cap = (long long)s.max_attempts + 64LL * s.N;
         s.r = b->r[k];
         s.r2_threshold = euclid_threshold_b(s.r);
         d.boxes = BoxArgs{Qh.boxes.count, Qh.boxes.lo, Qh.boxes.hi};
@@ -658,10 +675,12 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         g.max_n = 0; g.max_boxes = 0;
         g.any_cells = false;
         g.cell_words = 0;
+        g.any_halton = false;
         for (int i = 0; i < nq; ++i) {
             const int k = g.members[i];
             const int N = b->N[k], W = (N + 31) / 32;
             g.any_cells = g.any_cells || use_cells[k];
+            g.any_halton = g.any_halton || queries[k].params.sampler == GMT_SAMPLER_HALTON;
             if (use_cells[k]) g.cell_words = std::max(g.cell_words, cell_fill_words(cgs[k], N));
             const long long tiles = use_cells[k] ? 0
                                     : g.kind == GMT_COST_DI

@@ -155,13 +155,16 @@ gmt_status check_boxes(const gmt_boxes* b) {
 
 float resolve_radius(const gmt_params* p, int d) {
     if (p->r > 0.0f) return p->r;
-    return (float)gmt_connection_radius(p->n, d, p->eta, p->mu_free);
+    return (float)(p->sampler == GMT_SAMPLER_HALTON ? gmt_connection_radius_halton(p->n, d, p->eta, p->mu_free)
+                                                    : gmt_connection_radius(p->n, d, p->eta, p->mu_free));
 }
 
 gmt_status check_params(const gmt_params* p, int d) {
     if (!p) return fail(GMT_ERR_INVALID, "params is NULL");
     if (p->n < 1 || p->n > (1 << 24)) return fail(GMT_ERR_INVALID, "n must be in [1, 2^24]");
     if (!(p->lambda >= 0.0f && p->lambda <= 1.0f)) return fail(GMT_ERR_INVALID, "lambda must be in [0, 1]");
+    if (p->sampler != GMT_SAMPLER_PHILOX && p->sampler != GMT_SAMPLER_HALTON)
+        return fail(GMT_ERR_INVALID, "sampler must be GMT_SAMPLER_PHILOX or GMT_SAMPLER_HALTON");
     if (p->r <= 0.0f && (!(p->eta >= 0.0f) || !(p->mu_free > 0.0f)))
         return fail(GMT_ERR_INVALID, "r <= 0 needs eta >= 0 and mu_free > 0 (Theorem 1 radius)");
     const float r = resolve_radius(p, d);
@@ -176,6 +179,13 @@ gmt_status check_params(const gmt_params* p, int d) {
 extern "C" {
 
 const char* gmt_last_error(void) { return g_last_error.c_str(); }
+
+double gmt_connection_radius_halton(int32_t n, int32_t d, double eta, double mu_free) {
+    const double pi = 3.14159265358979323846;
+    const double zeta = std::pow(pi, (double)d / 2.0) / std::tgamma((double)d / 2.0 + 1.0);
+    const double base = (1.0 + eta) * (1.0 / (double)d) * (mu_free / zeta) * (1.0 / (double)n);
+    return 4.0 * std::pow(base, 1.0 / (double)d);
+}
 
 double gmt_connection_radius(int32_t n, int32_t d, double eta, double mu_free) {
     const double pi = 3.14159265358979323846;
@@ -236,6 +246,8 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     sa.key1 = (uint32_t)(params->seed >> 32);
     sa.stream = 0;
     sa.max_attempts = params->max_attempts > 0 ? params->max_attempts : 65536;
+    sa.sampler = params->sampler;
+    sa.halton_cap = (long long)sa.max_attempts + 64LL * n_sampled;
     sa.r = g->r;
     sa.r2_threshold = euclid_threshold(g->r);
     BoxArgs ba{boxes->count, boxes->lo, boxes->hi};

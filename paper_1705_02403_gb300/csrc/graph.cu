@@ -2,6 +2,7 @@
 // precomputation of Section V-A), as CUDA kernels for sm_103a.
 //
 //   sample_kernel     one thread per node: Philox4x32-10 rejection sampling
+//   halton_kernel     one block: the free Halton points in order
 //   pair_mask_kernel  all ordered pairs (i, j): bit j of row i is set iff
 //                     c(i, j) < r; rows staged through shared memory; the bit
 //                     matrix is word-major (word w of every row contiguous) so
@@ -40,6 +41,13 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(SpaceArgs s, Box
         boxes.hi = sbox + boxes.count * DP;
     }
     sample_node<D, DP>(s, boxes, X, is_goal, flags, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <int D, int DP>
+__global__ void __launch_bounds__(kHaltonThreads) halton_kernel(SpaceArgs s, BoxArgs boxes, float* __restrict__ X,
+                                                                uint8_t* __restrict__ is_goal,
+                                                                int* __restrict__ flags) {
+    halton_sample_block<D, DP>(s, boxes, X, is_goal, flags);
 }
 
 template <int D, int DP>
@@ -85,6 +93,10 @@ __global__ void __launch_bounds__(kFillWarps * 32) fill_kernel(SpaceArgs s, cons
 namespace {
 template <int D, int DP>
 cudaError_t sample_t(const SpaceArgs& s, BoxArgs b, float* X, uint8_t* g, int* f, cudaStream_t st) {
+    if (s.sampler == GMT_SAMPLER_HALTON) {
+        halton_kernel<D, DP><<<1, kHaltonThreads, 0, st>>>(s, b, X, g, f);
+        return cudaGetLastError();
+    }
     const int staged = b.count > 0 && b.count <= 4096 / DP;
     const size_t smem = staged ? (size_t)2 * b.count * DP * sizeof(float) : 0;
     sample_kernel<D, DP><<<(s.N + kSampleThreads - 1) / kSampleThreads, kSampleThreads, smem, st>>>(s, b, X, g, f,

@@ -64,6 +64,117 @@ __device__ __forceinline__ void sample_node(const SpaceArgs& s, const BoxArgs& b
     is_goal[k] = in_goal_ball(x, s.gd, s.gc, s.grho) ? 1 : 0;
 }
 
+// ------------------------------------------------------------ Halton
+// Radical inverse of k in base p, exactly: the digits of k reversed (R) over
+// p^m (m digits), rounded to double and then to float (R, p^m < 2^35).
+__host__ __device__ __forceinline__ float halton_unit(uint32_t k, uint32_t p) {
+    unsigned long long R = 0, P = 1;
+    while (k > 0) {
+        R = R * p + k % p;
+        P *= p;
+        k /= p;
+    }
+    return (float)((double)R / (double)P);
+}
+
+__host__ __device__ __forceinline__ uint32_t halton_prime(int a) {
+    const uint32_t primes[10] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29};
+    return primes[a];
+}
+
+constexpr int kHaltonThreads = 512;
+
+// Halton SampleFree of one graph, run by a whole block of kHaltonThreads:
+// node 0 = x_init; node 1 = the first goal-mapped point (smallest k) in X, in
+// the goal ball and outside the boxes; nodes 2..n_sampled-1 = the free points
+// in the order of k (block-wide prefix sums keep that order).
+template <int D, int DP>
+__device__ void halton_sample_block(const SpaceArgs& s, const BoxArgs& boxes, float* __restrict__ X,
+                                    uint8_t* __restrict__ is_goal, int* __restrict__ flags) {
+    __shared__ int s_warp[kHaltonThreads / 32];
+    __shared__ int s_best;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int N = s.n_sampled;
+    if (tid == 0) sample_node<D, DP>(s, boxes, X, is_goal, flags, 0);  // x_init and its checks
+    // node 1
+    if (tid == 0) s_best = INT_MAX;
+    __syncthreads();
+    for (long long base = 1; base <= s.halton_cap; base += blockDim.x) {
+        const long long k = base + tid;
+        if (k <= s.halton_cap) {
+            float x[D];
+            bool ok = true;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float u = halton_unit((uint32_t)k, halton_prime(a));
+                float l = s.lo[a], h = s.hi[a];
+                if (a < s.gd) { l = s.gc[a] - s.grho; h = s.gc[a] + s.grho; }
+                x[a] = l + u * (h - l);
+                ok = ok && s.lo[a] <= x[a] && x[a] <= s.hi[a];
+            }
+            if (ok && in_goal_ball(x, s.gd, s.gc, s.grho) && !in_any_box<DP>(x, boxes.lo, boxes.hi, boxes.count))
+                atomicMin(&s_best, (int)k);
+        }
+        __syncthreads();
+        const bool found = s_best != INT_MAX;
+        __syncthreads();
+        if (found) break;
+    }
+    if (tid == 0) {
+        if (s_best == INT_MAX) {
+            atomicOr(flags, kSampleExhausted);
+        } else {
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float u = halton_unit((uint32_t)s_best, halton_prime(a));
+                float l = s.lo[a], h = s.hi[a];
+                if (a < s.gd) { l = s.gc[a] - s.grho; h = s.gc[a] + s.grho; }
+                X[(size_t)a * s.pitch + 1] = l + u * (h - l);
+            }
+        }
+    }
+    // nodes 2..N-1
+    int got = 0;
+    for (long long base = 1; got < N - 2; base += blockDim.x) {
+        if (base > s.halton_cap) {
+            if (tid == 0) atomicOr(flags, kSampleExhausted);
+            break;
+        }
+        const long long k = base + tid;
+        float x[D];
+        bool ok = false;
+        if (k <= s.halton_cap) {
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                x[a] = s.lo[a] + halton_unit((uint32_t)k, halton_prime(a)) * (s.hi[a] - s.lo[a]);
+            ok = !in_any_box<DP>(x, boxes.lo, boxes.hi, boxes.count);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (lane == 0) s_warp[warp] = __popc(m);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            const int c = s_warp[w];
+            before += w < warp ? c : 0;
+            total += c;
+        }
+        const int rank = before + __popc(m & ((1u << lane) - 1u));
+        if (ok && got + rank < N - 2) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) X[(size_t)a * s.pitch + 2 + got + rank] = x[a];
+        }
+        got += total;
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int v = tid; v < N; v += blockDim.x) {
+        float x[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) x[a] = X[(size_t)a * s.pitch + v];
+        is_goal[v] = in_goal_ball(x, s.gd, s.gc, s.grho) ? 1 : 0;
+    }
+}
+
 // Appended sample k (one thread): copy, goal flag, validity (inside X, outside
 // every box).
 template <int D, int DP>

@@ -26,6 +26,8 @@ struct SpaceArgs {
     int max_attempts;
     float r;
     float r2_threshold;  // Euclidean: edge iff squared distance < r2_threshold (== sqrt(s) < r)
+    int sampler;         // GMT_SAMPLER_PHILOX or GMT_SAMPLER_HALTON
+    long long halton_cap;  // Halton points tried per sequence
 };
 
 struct BoxArgs {
@@ -38,6 +40,8 @@ struct BoxArgs {
 enum { kSampleBadInit = 1, kSampleExhausted = 2, kSampleBadAppend = 4 };
 
 // sample.cu / graph.cu
+// SampleFree with s.sampler's method (Halton: one block compacts the free
+// points in order).
 cudaError_t launch_sample(const SpaceArgs& s, BoxArgs boxes, float* X, uint8_t* is_goal, int* flags,
                           cudaStream_t st);
 cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* out_count,

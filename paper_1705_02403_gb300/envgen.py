@@ -46,6 +46,7 @@ class Problem:
     eta: float = 0.0          # Theorem 1 tuning parameter (only when r == 0)
     mu_free: float = 1.0      # Lebesgue measure bound used by Theorem 1 (only when r == 0)
     tag: str = ""
+    sampler: int = 0          # 0: Philox i.i.d. uniform; 1: Halton sequence (seed unused)
 
     @property
     def N(self) -> int:

@@ -52,6 +52,7 @@ def params_struct(pb: Problem, **over) -> N.gmt_params:
     p.max_iters, p.max_attempts = 0, 0
     p.eta, p.mu_free = float(pb.eta), float(pb.mu_free)
     p.spin_limit, p.debug_flags = 0, 0
+    p.sampler = int(pb.sampler)
     for k, v in over.items():
         setattr(p, k, v)
     return p

@@ -31,8 +31,9 @@ def mixed_batch(seed=0, q=14, n_max=1500):
 
 
 def oracle_of(O, pb):
-    X, goal = O.sample(pb)
-    r = pb.r if pb.r > 0 else np.float32(O.radius_thm1(pb.n, pb.d))
+    X, goal = O.sample_halton(pb) if pb.sampler == 1 else O.sample(pb)
+    r0 = O.radius_halton(pb.n, pb.d) if pb.sampler == 1 else O.radius_thm1(pb.n, pb.d)
+    r = pb.r if pb.r > 0 else np.float32(r0)
     g = O.Graph(pb.kind, pb.d, pb.dp, X, goal, r)
     parent, cost, info = g.plan(pb.box_lo, pb.box_hi, pb.lo[:pb.dp], pb.hi[:pb.dp], pb.lam, pb.seg_spacing,
                                 pb.traj_points)
@@ -148,6 +149,19 @@ def test_neighbour_build_choice_gives_the_same_queries(O, flags):
         check_query(O, bp, k, infos)
     infos2 = bp.plan()          # replayed
     assert infos2 == infos
+
+
+def test_halton_queries_in_a_batch(O):
+    # Halton and Philox queries side by side (2D, 3D, double integrator, one
+    # large enough for the cell list): each equals the oracle on its own.
+    from paper_1705_02403_gb300.planner import BatchPlanner
+    qs = mixed_batch(seed=9, q=10)
+    qs = [pb.with_(sampler=k % 2) for k, pb in enumerate(qs)]
+    qs.append(envgen.geometric(76, d=2, n=6000, nbox=20, r=0.0).with_(sampler=1))
+    bp = BatchPlanner(qs)
+    infos = bp.plan()
+    for k in range(len(qs)):
+        check_query(O, bp, k, infos)
 
 
 def test_lockstep_runs_more_than_512_queries_in_chunks(O):

@@ -45,8 +45,9 @@ def gpu_run(P, pb, launch=None, build_only=False, **over):
 
 def oracle_run(O, pb, X=None, goal=None, **kw):
     if X is None:
-        X, goal = O.sample(pb)
-    g = O.Graph(pb.kind, pb.d, pb.dp, X, goal, pb.r if pb.r > 0 else np.float32(O.radius_thm1(pb.n, pb.d)))
+        X, goal = O.sample_halton(pb) if pb.sampler == 1 else O.sample(pb)
+    r0 = O.radius_halton(pb.n, pb.d) if pb.sampler == 1 else O.radius_thm1(pb.n, pb.d)
+    g = O.Graph(pb.kind, pb.d, pb.dp, X, goal, pb.r if pb.r > 0 else np.float32(r0))
     parent, cost, info = g.plan(pb.box_lo, pb.box_hi, pb.lo[:pb.dp], pb.hi[:pb.dp], pb.lam, pb.seg_spacing,
                                 pb.traj_points, **kw)
     return X, goal, g, parent, cost, info
@@ -228,6 +229,19 @@ def test_nearly_complete_graphs(O, P, dense_oracle, launch):
         G = gpu_run(P, pb, launch=launch)
         assert G["out_row"][1] - G["out_row"][0] > 2048
         assert_same(O, G, *ref, check_graph=False)
+
+
+@pytest.mark.parametrize("case", ["2d", "3d_thm", "di6", "4d", "ragged_small"])
+def test_halton_sampling_matches_the_oracle(O, P, case):
+    # Halton SampleFree (the paper's sampler): samples, goal flags, CSR and tree
+    # equal the oracle's; r = 0 selects the low-dispersion radius.
+    pb = {"2d": envgen.geometric(71, d=2, n=2000, nbox=10, r=0.05),
+          "3d_thm": envgen.geometric(72, d=3, n=3000, nbox=30, r=0.0),
+          "di6": envgen.di6(seed=73, n=600, r=2.8),
+          "4d": envgen.geometric(74, d=4, n=1500, nbox=6, r=0.0),
+          "ragged_small": envgen.geometric(75, d=2, n=37, nbox=3, r=0.3)}[case].with_(sampler=1)
+    G = gpu_run(P, pb)
+    assert_same(O, G, *oracle_run(O, pb))
 
 
 @pytest.mark.parametrize("d", [3, 4, 10])
