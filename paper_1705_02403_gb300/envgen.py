@@ -140,3 +140,92 @@ def batch_queries(seed: int = 0, q: int = 256, n_min: int = 512, n_max: int = 16
         pb = geometric(qseed, d=d, n=n, nbox=nbox, r=0.0, lam=lam, tag=f"batch{seed}_{k}")
         out.append(pb)
     return out
+
+# ---------------------------------------------------------------- sweeps
+# Synthetic analogues of the environments of Tables 1 and 3 (the paper gives
+# their figures, not their geometry).
+
+def rectangles(seed: int, d: int, n: int = 5000, nbox: int = 10, lam: float = 0.5) -> Problem:
+    """Table 1 "Rectangles" analogue: the unit d-cube with nbox rectangles in the
+    first two axes (sides U[0.1, 0.3], centres U[0.15, 0.85]^2) extruded over
+    every other axis, so they obstruct equally in every dimension; x_init at
+    0.05, goal ball radius 0.05 at 0.95; Theorem 1 radius."""
+    rng = np.random.default_rng([seed, 1705, 100 + d])
+    x0, gc = np.full(d, 0.05), np.full(d, 0.95)
+    lo = np.zeros((nbox, d)); hi = np.ones((nbox, d))
+    k = 0
+    while k < nbox:
+        c = rng.uniform(0.15, 0.85, 2)
+        s = rng.uniform(0.1, 0.3, 2)
+        bl, bh = c - s / 2, c + s / 2
+        if np.all(bl <= x0[:2]) and np.all(x0[:2] <= bh):
+            continue                                   # would contain x_init
+        if np.linalg.norm(np.clip(gc[:2], bl, bh) - gc[:2]) <= 0.05:
+            continue                                   # would touch the goal ball
+        lo[k, :2], hi[k, :2] = bl, bh
+        k += 1
+    return Problem(kind=EUCLID, d=d, dp=d, lo=_f32(np.zeros(d)), hi=_f32(np.ones(d)), box_lo=_f32(lo),
+                   box_hi=_f32(hi), x_init=_f32(x0), goal_center=_f32(gc), goal_radius=0.05, goal_pos_only=False,
+                   n=n, r=0.0, lam=lam, seed=seed, tag=f"rectangles_{d}d")
+
+
+def maze(seed: int, d: int, n: int = 5000, walls: int = 3, door: float = 0.25, lam: float = 0.5) -> Problem:
+    """Table 1 "Maze" analogue: walls of thickness 0.05 across axis 0 at
+    x0 = k / (walls + 1), each spanning every other axis except one square door
+    (side `door` in axes 1 and 2, at a random place), as 4 boxes per wall
+    around the door; d >= 3."""
+    rng = np.random.default_rng([seed, 1705, 200 + d])
+    x0, gc = np.full(d, 0.05), np.full(d, 0.95)
+    lo, hi = [], []
+    for w in range(walls):
+        xc = (w + 1) / (walls + 1)
+        dc = rng.uniform(door / 2 + 0.05, 1 - door / 2 - 0.05, 2)
+        d_lo, d_hi = dc - door / 2, dc + door / 2
+        for part in range(4):
+            bl, bh = np.zeros(d), np.ones(d)
+            bl[0], bh[0] = xc - 0.025, xc + 0.025
+            if part == 0: bh[1] = d_lo[0]                               # below the door in axis 1
+            elif part == 1: bl[1] = d_hi[0]                             # above it
+            elif part == 2: bl[1], bh[1], bh[2] = d_lo[0], d_hi[0], d_lo[1]
+            else: bl[1], bh[1], bl[2] = d_lo[0], d_hi[0], d_hi[1]
+            lo.append(bl); hi.append(bh)
+    return Problem(kind=EUCLID, d=d, dp=d, lo=_f32(np.zeros(d)), hi=_f32(np.ones(d)), box_lo=_f32(np.array(lo)),
+                   box_hi=_f32(np.array(hi)), x_init=_f32(x0), goal_center=_f32(gc), goal_radius=0.05,
+                   goal_pos_only=False, n=n, r=0.0, lam=lam, seed=seed, tag=f"maze_{d}d")
+
+
+def forest_boxes(seed: int, trunks: int, strips: int):
+    """Table 3 obstacle-resolution analogue: `trunks` vertical cylinders in
+    the unit cube (radius U[0.03, 0.06], axis at U[0.15, 0.8]^2, full height),
+    each cross-section approximated by `strips` axis-aligned strips (each as
+    wide as the disk's chord at the strip's edge nearest the axis, so the union
+    covers the disk); the same trunks at every resolution."""
+    rng = np.random.default_rng([seed, 1705, 300])
+    lo, hi = [], []
+    for _ in range(trunks):
+        c = rng.uniform(0.15, 0.8, 2)
+        rad = rng.uniform(0.03, 0.06)
+        for k in range(strips):
+            y0 = -rad + 2 * rad * k / strips
+            y1 = -rad + 2 * rad * (k + 1) / strips
+            yo = min(abs(y0), abs(y1)) if y0 * y1 > 0 else 0.0   # the strip's edge nearest the centre
+            half = np.sqrt(max(rad * rad - yo * yo, 0.0))
+            lo.append([c[0] - half, c[1] + y0, 0.0])
+            hi.append([c[0] + half, c[1] + y1, 1.0])
+    return _f32(np.array(lo)), _f32(np.array(hi))
+
+
+def di6_scaled(seed: int, n: int, nbox: int = 300, lam: float = 0.5, boxes=None) -> Problem:
+    """Table 3 analogue for the double integrator: the bench workload's setting
+    at sample count n with the radius scaled as r_4096 (4096 / n)^(1/6) (about
+    the same mean out-degree); boxes: `nbox` random boxes (sides U[0.02, 0.08])
+    or the given (lo, hi) arrays."""
+    c = load_config("double_integrator_6d_n4096")
+    r = float(np.float32(c["r"] * (4096.0 / n) ** (1.0 / 6.0)))
+    pb = di6(seed, n=n, nbox=0, r=r, lam=lam)
+    if boxes is None:
+        rng = np.random.default_rng([seed, 1705, 400])
+        bl, bh = random_boxes(rng, nbox, 3, pb.x_init[:3], pb.goal_center[:3], 0.05, side=(0.02, 0.08))
+    else:
+        bl, bh = boxes
+    return pb.with_(box_lo=bl, box_hi=bh, tag=f"di6_n{n}_b{bl.shape[0]}")
