@@ -84,6 +84,12 @@ struct gmt_graph {
     int* cell_cnt = nullptr;       size_t cap_cell_cnt = 0;
     int* cell_start = nullptr;     size_t cap_cell_start = 0;
     bool used_cells = false;
+    // box grid of the last plan (many boxes)
+    int* grid_cnt = nullptr;       size_t cap_grid_cnt = 0;
+    int* grid_start = nullptr;     size_t cap_grid_start = 0;
+    int* grid_list = nullptr;      size_t cap_grid_list = 0;
+    int* grid_cell_of = nullptr;   size_t cap_grid_cell_of = 0;
+    float* grid_ext = nullptr;     size_t cap_grid_ext = 0;
     // plan workspace
     float* ocost = nullptr;        size_t cap_ocost = 0;
     int* stamp = nullptr;          size_t cap_stamp = 0;
@@ -116,7 +122,8 @@ struct gmt_graph {
     ~gmt_graph() {
         void* dev[] = {X, is_goal, out_row, in_row_own, out_count, in_count, out_col, out_cost, in_col_own,
                        in_cost_own, out_tau, in_tau, mask, maskT, flags, cell_of, cell_sorted, cell_cnt,
-                       cell_start, ocost, stamp, lists, ctl};
+                       cell_start, grid_cnt, grid_start, grid_list, grid_cell_of, grid_ext, ocost, stamp,
+                       lists, ctl};
         for (void* p : dev)
             if (p) cudaFree(p);
         if (h_ctl) cudaFreeHost(h_ctl);
@@ -439,6 +446,34 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
     GMT_CUDA(cudaMemsetAsync(g->ctl, 0, sizeof(PlanCtl), st), "memset");
     g->stage_ran[gmt_graph::kPlan] = false;
     GMT_CUDA(g->mark(gmt_graph::kPlan, 0, st), "event");
+    if (g->dp >= 2 && boxes->count >= kBoxGridMinBoxes) {
+        // many boxes: bin them on a grid over the first two position axes
+        const int G = box_grid_cells(boxes->count);
+        const size_t B = (size_t)boxes->count, cells = (size_t)G * G;
+        cudaError_t e;
+#define GROWP(ptr, n) if ((e = grow(&g->ptr, &g->cap_##ptr, (n))) != cudaSuccess) return cuda_fail(e, "allocating " #ptr)
+        GROWP(grid_cnt, cells);
+        GROWP(grid_start, cells + 1);
+        GROWP(grid_list, B);
+        GROWP(grid_cell_of, B);
+        GROWP(grid_ext, 2);
+#undef GROWP
+        BoxGridArgs& gr = a.grid;
+        gr.use = 1;
+        gr.g = G;
+        for (int k = 0; k < 2; ++k) {
+            gr.lo[k] = g->pos_lo[k];
+            gr.inv_h[k] = (float)((double)G / ((double)g->pos_hi[k] - (double)g->pos_lo[k]));
+        }
+        gr.ext = g->grid_ext;
+        gr.start = g->grid_start;
+        gr.list = g->grid_list;
+        GMT_CUDA(cudaMemsetAsync(g->grid_cnt, 0, cells * sizeof(int), st), "memset");
+        GMT_CUDA(cudaMemsetAsync(g->grid_ext, 0, 2 * sizeof(float), st), "memset");
+        GMT_CUDA(launch_box_grid(g->dp, a.boxes, gr, g->grid_cnt, g->grid_start, g->grid_list, g->grid_cell_of,
+                                 g->grid_ext, st),
+                 "box grid kernels");
+    }
     GMT_CUDA(launch_plan(a, blocks, threads, st, cluster), "plan kernel launch");
     GMT_CUDA(g->mark(gmt_graph::kPlan, 1, st), "event");
     g->last_blocks = cluster > 1 ? -cluster : blocks;

@@ -32,6 +32,47 @@ __global__ void __launch_bounds__(kCellWarps * 32) cells_rows_kernel(SpaceArgs s
                       cell_buf + (threadIdx.x >> 5) * words, blockIdx.x * kCellWarps + (threadIdx.x >> 5));
 }
 
+// ---- box grid (checks against many boxes)
+__device__ __forceinline__ int box_grid_cell(const BoxGridArgs& g, float x, int a) {
+    const int k = (int)floorf((x - g.lo[a]) * g.inv_h[a]);
+    return min(max(k, 0), g.g - 1);
+}
+
+__global__ void __launch_bounds__(256) box_grid_count_kernel(BoxArgs boxes, int dp, BoxGridArgs grid,
+                                                             int* __restrict__ cnt, int* __restrict__ cell_of,
+                                                             float* __restrict__ ext) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= boxes.count) return;
+    const float* lo = boxes.lo + (size_t)b * dp;
+    const float* hi = boxes.hi + (size_t)b * dp;
+    const int c = box_grid_cell(grid, lo[1], 1) * grid.g + box_grid_cell(grid, lo[0], 0);
+    cell_of[b] = c;
+    atomicAdd(&cnt[c], 1);
+    // sides are >= 0 (a box with lo > hi meets nothing), so their bits order as ints
+    atomicMax((int*)&ext[0], __float_as_int(fmaxf(hi[0] - lo[0], 0.0f)));
+    atomicMax((int*)&ext[1], __float_as_int(fmaxf(hi[1] - lo[1], 0.0f)));
+}
+
+__global__ void __launch_bounds__(256) box_grid_scatter_kernel(int count, const int* __restrict__ cell_of,
+                                                               const int* __restrict__ start, int* __restrict__ cnt,
+                                                               int* __restrict__ list) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= count) return;
+    const int c = cell_of[b];
+    list[start[c] + atomicSub(&cnt[c], 1) - 1] = b;
+}
+
+cudaError_t launch_box_grid(int dp, BoxArgs boxes, const BoxGridArgs& grid, int* cnt, int* start, int* list,
+                            int* cell_of, float* ext, cudaStream_t st) {
+    if (dp < 2 || boxes.count < 1) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)((boxes.count + 255) / 256);
+    box_grid_count_kernel<<<blocks, 256, 0, st>>>(boxes, dp, grid, cnt, cell_of, ext);
+    cudaError_t e = launch_scan(cnt, start, grid.g * grid.g, st);
+    if (e != cudaSuccess) return e;
+    box_grid_scatter_kernel<<<blocks, 256, 0, st>>>(boxes.count, cell_of, start, cnt, list);
+    return cudaGetLastError();
+}
+
 bool make_cell_grid(int kind, int d, const float* lo, const float* hi, float r, int N, CellGrid* cg, bool* pays) {
     if (kind != GMT_COST_EUCLID || (d != 2 && d != 3) || !(r > 0.0f)) return false;
     // cell side: at least 1.01 r, and coarse enough for at most 2^16 cells

@@ -217,11 +217,13 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
                     free_edge = cached == 1;
                 } else {
                     if (KIND == GMT_COST_EUCLID)
-                        free_edge = segment_free_warp<DP>(sy, sx, __ldg(&A.in_cost[be]), A.seg_spacing, blo, bhi, nbox);
+                        free_edge = segment_free_warp<DP>(sy, sx, __ldg(&A.in_cost[be]), A.seg_spacing, blo, bhi,
+                                                          nbox, A.grid);
                     else {
                         // arrival time of the edge: stored by the graph build, or recomputed
                         const float tau = A.in_tau ? __ldg(&A.in_tau[be]) : di_tau(di_coef(sy, sx), A.r);
-                        free_edge = trajectory_free_warp(sy, sx, tau, A.traj_points, A.pos_lo, A.pos_hi, blo, bhi, nbox);
+                        free_edge = trajectory_free_warp(sy, sx, tau, A.traj_points, A.pos_lo, A.pos_hi, blo, bhi, nbox,
+                                                         A.grid);
                     }
                     if (lane == 0) {
                         ++n_computed;

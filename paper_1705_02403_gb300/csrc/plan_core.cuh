@@ -112,12 +112,40 @@ __device__ __forceinline__ bool box_meets(const float* blo, const float* bhi, in
     return m;
 }
 
+// Calls visit(bi) on chunks of candidate boxes, one per lane (bi = -1 for an
+// empty lane), until visit returns true (it must return the same value in
+// every lane); returns whether it did.  Candidates: every box, or with the
+// grid, the boxes listed in the cells that can hold a box meeting [lo, hi].
+template <class F>
+__device__ __forceinline__ bool for_box_chunks(const float* lo, const float* hi, int nbox, const BoxGridArgs& grid,
+                                               F&& visit) {
+    const int lane = threadIdx.x & 31;
+    if (!grid.use) {
+        for (int b0 = 0; b0 < nbox; b0 += 32)
+            if (visit(b0 + lane < nbox ? b0 + lane : -1)) return true;
+        return false;
+    }
+    const float ex = __ldg(&grid.ext[0]), ey = __ldg(&grid.ext[1]);
+    auto cell = [&](float x, int a) {
+        const int k = (int)floorf((x - grid.lo[a]) * grid.inv_h[a]);
+        return min(max(k, 0), grid.g - 1);
+    };
+    const int cx0 = max(cell(lo[0] - ex, 0) - 1, 0), cx1 = min(cell(hi[0], 0) + 1, grid.g - 1);
+    const int cy0 = max(cell(lo[1] - ey, 1) - 1, 0), cy1 = min(cell(hi[1], 1) + 1, grid.g - 1);
+    for (int cy = cy0; cy <= cy1; ++cy) {
+        const int s = __ldg(&grid.start[cy * grid.g + cx0]), e = __ldg(&grid.start[cy * grid.g + cx1 + 1]);
+        for (int t0 = s; t0 < e; t0 += 32)
+            if (visit(t0 + lane < e ? __ldg(&grid.list[t0 + lane]) : -1)) return true;
+    }
+    return false;
+}
+
 // Geometric edge y -> x of length L: m = max(2, ceil(L/spacing) + 1) points
 // p_k = y + t_k (x - y), t_k = k/(m-1); collision if one lies in a closed box.
 // Every computed p_k lies within a few ulps of the segment's bounding box.
 template <int DP>
 __device__ bool segment_free_warp(const float* y, const float* x, float L, float spacing, const float* blo,
-                                  const float* bhi, int nbox) {
+                                  const float* bhi, int nbox, const BoxGridArgs& grid) {
     const int lane = threadIdx.x & 31;
     int m = (int)ceilf(L / spacing) + 1;
     if (m < 2) m = 2;
@@ -129,24 +157,27 @@ __device__ bool segment_free_warp(const float* y, const float* x, float L, float
         lo[a] = fminf(x[a], y[a]) - e;
         hi[a] = fmaxf(x[a], y[a]) + e;
     }
-    for (int b0 = 0; b0 < nbox; b0 += 32) {
-        const int b = b0 + lane;
-        const unsigned near = __ballot_sync(0xffffffffu, b < nbox && box_meets<DP>(blo, bhi, b, lo, hi));
-        if (!near) continue;
+    const bool hit_any = for_box_chunks(lo, hi, nbox, grid, [&](int bi) {
+        const unsigned near = __ballot_sync(0xffffffffu, bi >= 0 && box_meets<DP>(blo, bhi, bi, lo, hi));
+        if (!near) return false;
         for (int k0 = 0; k0 < m; k0 += 32) {
             const int k = k0 + lane;
-            bool hit = false;
+            float p[DP];
             if (k < m) {
                 const float t = (float)k / denom;
-                float p[DP];
 #pragma unroll
                 for (int a = 0; a < DP; ++a) p[a] = y[a] + t * (x[a] - y[a]);
-                for (unsigned w = near; w; w &= w - 1) hit = hit || in_box<DP>(p, blo, bhi, b0 + __ffs(w) - 1);
             }
-            if (__any_sync(0xffffffffu, hit)) return false;
+            bool hit = false;
+            for (unsigned w = near; w; w &= w - 1) {
+                const int bb = __shfl_sync(0xffffffffu, bi, __ffs(w) - 1);
+                if (k < m) hit = hit || in_box<DP>(p, blo, bhi, bb);
+            }
+            if (__any_sync(0xffffffffu, hit)) return true;
         }
-    }
-    return true;
+        return false;
+    });
+    return !hit_any;
 }
 
 // Double-integrator edge: `points` samples of the Hermite trajectory at
@@ -155,7 +186,8 @@ __device__ bool segment_free_warp(const float* y, const float* x, float L, float
 // p0, p0 + tau v0 / 3, p1 - tau v1 / 3, p1, whose bounding box (inflated)
 // selects the boxes.
 __device__ inline bool trajectory_free_warp(const float* y, const float* x, float tau, int points, const float* plo,
-                                     const float* phi, const float* blo, const float* bhi, int nbox) {
+                                            const float* phi, const float* blo, const float* bhi, int nbox,
+                                            const BoxGridArgs& grid) {
     const int lane = threadIdx.x & 31;
     const float denom = (float)(points - 1);
     float lo[3], hi[3];
@@ -166,8 +198,6 @@ __device__ inline bool trajectory_free_warp(const float* y, const float* x, floa
         lo[a] = fminf(fminf(y[a], x[a]), fminf(c1, c2)) - e;
         hi[a] = fmaxf(fmaxf(y[a], x[a]), fmaxf(c1, c2)) + e;
     }
-    unsigned near_first = 0;  // boxes 0..31, reused by the first chunk of points
-    if (nbox > 0) near_first = __ballot_sync(0xffffffffu, lane < nbox && box_meets<3>(blo, bhi, lane, lo, hi));
     for (int k0 = 0; k0 < points; k0 += 32) {
         const int k = k0 + lane;
         bool hit = false;
@@ -178,14 +208,17 @@ __device__ inline bool trajectory_free_warp(const float* y, const float* x, floa
 #pragma unroll
             for (int a = 0; a < 3; ++a) hit = hit || p[a] < plo[a] || p[a] > phi[a];
         }
-        for (int b0 = 0; b0 < nbox; b0 += 32) {
-            const unsigned near =
-                b0 == 0 ? near_first
-                        : __ballot_sync(0xffffffffu, b0 + lane < nbox && box_meets<3>(blo, bhi, b0 + lane, lo, hi));
-            if (k < points)
-                for (unsigned w = near; w; w &= w - 1) hit = hit || in_box<3>(p, blo, bhi, b0 + __ffs(w) - 1);
-        }
         if (__any_sync(0xffffffffu, hit)) return false;
+        const bool hit_box = for_box_chunks(lo, hi, nbox, grid, [&](int bi) {
+            const unsigned near = __ballot_sync(0xffffffffu, bi >= 0 && box_meets<3>(blo, bhi, bi, lo, hi));
+            bool h = false;
+            for (unsigned w = near; w; w &= w - 1) {
+                const int bb = __shfl_sync(0xffffffffu, bi, __ffs(w) - 1);
+                if (k < points) h = h || in_box<3>(p, blo, bhi, bb);
+            }
+            return __any_sync(0xffffffffu, h);
+        });
+        if (hit_box) return false;
     }
     return true;
 }

@@ -128,10 +128,12 @@ __device__ bool pull_candidate(const PlanArgs* __restrict__ Ap, LockSmem& sm, in
         free_edge = cached == 1;
     } else {
         if (KIND == GMT_COST_EUCLID) {
-            free_edge = segment_free_warp<DP>(sy, sx, __ldg(&in_cost[be]), Ap->seg_spacing, blo, bhi, nbox);
+            free_edge =
+                segment_free_warp<DP>(sy, sx, __ldg(&in_cost[be]), Ap->seg_spacing, blo, bhi, nbox, Ap->grid);
         } else {
             const float tau = Ap->in_tau ? __ldg(&Ap->in_tau[be]) : di_tau(di_coef(sy, sx), Ap->r);
-            free_edge = trajectory_free_warp(sy, sx, tau, Ap->traj_points, Ap->pos_lo, Ap->pos_hi, blo, bhi, nbox);
+            free_edge = trajectory_free_warp(sy, sx, tau, Ap->traj_points, Ap->pos_lo, Ap->pos_hi, blo, bhi, nbox,
+                                             Ap->grid);
         }
         if (lane == 0) {
             atomicAdd(&sm.acc_computed[q], 1u);

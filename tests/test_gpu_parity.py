@@ -244,6 +244,35 @@ def test_halton_sampling_matches_the_oracle(O, P, case):
     assert_same(O, G, *oracle_run(O, pb))
 
 
+@pytest.mark.parametrize("case", ["2d_600", "3d_300", "di_forest_1500", "2d_outside"])
+def test_many_boxes_use_the_box_grid(O, P, case):
+    # From 128 boxes the plan bins them on a grid over the first two position
+    # axes; the checks gather candidates from the grid and the tree must stay
+    # the oracle's.
+    rng = np.random.default_rng(81)
+    if case == "2d_600":
+        pb = envgen.geometric(81, d=2, n=2000, nbox=0, r=0.06)
+        bl, bh = envgen.random_boxes(rng, 600, 2, pb.x_init, pb.goal_center, 0.05, side=(0.005, 0.03))
+    elif case == "3d_300":
+        pb = envgen.geometric(82, d=3, n=2500, nbox=0, r=0.12)
+        bl, bh = envgen.random_boxes(rng, 300, 3, pb.x_init, pb.goal_center, 0.05, side=(0.01, 0.06))
+    elif case == "di_forest_1500":
+        pb = envgen.di6(seed=83, n=700, nbox=0, r=2.8)
+        bl, bh = envgen.forest_boxes(83, 10, 150)
+    else:  # boxes reaching outside the domain on both sides
+        pb = envgen.geometric(84, d=2, n=1500, nbox=0, r=0.07)
+        bl, bh = envgen.random_boxes(rng, 300, 2, pb.x_init, pb.goal_center, 0.05, side=(0.01, 0.05))
+        bl = bl.copy(); bh = bh.copy()
+        bl[:20] -= 0.3; bh[20:40] += 0.3
+        keep = ~(np.all(bl <= pb.x_init, axis=1) & np.all(pb.x_init <= bh, axis=1))
+        bl, bh = bl[keep], bh[keep]
+    pb = pb.with_(box_lo=bl, box_hi=bh)
+    assert pb.nbox >= 128
+    G = gpu_run(P, pb)
+    assert_same(O, G, *oracle_run(O, pb), check_graph=False)
+    assert G["info"]["checks"] > 0
+
+
 @pytest.mark.parametrize("d", [3, 4, 10])
 def test_geometric_higher_dimensions(O, P, d):
     pb = envgen.geometric(seed=d, d=d, n=700, nbox=12, r={3: 0.3, 4: 0.45, 10: 1.0}[d])
