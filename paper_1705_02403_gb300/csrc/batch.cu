@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(128) batch_sample_kernel(const QueryDev* __res
     const int k = find_query(off, nq, t);
     const QueryDev& q = Q[k];
     if (q.s.sampler == GMT_SAMPLER_HALTON) return;  // batch_halton_kernel
-    sample_node<D, DP>(q.s, q.boxes, q.X, q.is_goal, q.flags, (int)(t - off[k]));
+    const BoxGridArgs no_grid{};
+    sample_node<D, DP>(q.s, q.boxes, no_grid, q.X, q.is_goal, q.flags, (int)(t - off[k]));
 }
 
 // One block per query of the group; queries that sample with Philox return.
@@ -76,7 +77,8 @@ template <int D, int DP>
 __global__ void __launch_bounds__(kHaltonThreads) batch_halton_kernel(const QueryDev* __restrict__ Q) {
     const QueryDev& q = Q[blockIdx.x];
     if (q.s.sampler != GMT_SAMPLER_HALTON) return;
-    halton_sample_block<D, DP>(q.s, q.boxes, q.X, q.is_goal, q.flags);
+    const BoxGridArgs no_grid{};
+    halton_sample_block<D, DP>(q.s, q.boxes, no_grid, q.X, q.is_goal, q.flags);
 }
 
 template <int KIND, int D>

@@ -201,6 +201,36 @@ double gmt_connection_radius(int32_t n, int32_t d, double eta, double mu_free) {
     return 4.0 * std::pow(base, 1.0 / (double)d);
 }
 
+namespace {
+// Box grid over the first two position axes of the graph's space, for at
+// least kBoxGridMinBoxes boxes (use = 0 otherwise).
+cudaError_t build_box_grid(gmt_graph* g, const BoxArgs& boxes, BoxGridArgs* gr, cudaStream_t st) {
+    std::memset(gr, 0, sizeof(*gr));
+    if (g->dp < 2 || boxes.count < kBoxGridMinBoxes) return cudaSuccess;
+    const int G = box_grid_cells(boxes.count);
+    const size_t B = (size_t)boxes.count, cells = (size_t)G * G;
+    cudaError_t e;
+    if ((e = grow(&g->grid_cnt, &g->cap_grid_cnt, cells)) != cudaSuccess) return e;
+    if ((e = grow(&g->grid_start, &g->cap_grid_start, cells + 1)) != cudaSuccess) return e;
+    if ((e = grow(&g->grid_list, &g->cap_grid_list, B)) != cudaSuccess) return e;
+    if ((e = grow(&g->grid_cell_of, &g->cap_grid_cell_of, B)) != cudaSuccess) return e;
+    if ((e = grow(&g->grid_ext, &g->cap_grid_ext, (size_t)2)) != cudaSuccess) return e;
+    gr->use = 1;
+    gr->g = G;
+    for (int k = 0; k < 2; ++k) {
+        gr->lo[k] = g->pos_lo[k];
+        gr->inv_h[k] = (float)((double)G / ((double)g->pos_hi[k] - (double)g->pos_lo[k]));
+    }
+    gr->ext = g->grid_ext;
+    gr->start = g->grid_start;
+    gr->list = g->grid_list;
+    if ((e = cudaMemsetAsync(g->grid_cnt, 0, cells * sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(g->grid_ext, 0, 2 * sizeof(float), st)) != cudaSuccess) return e;
+    return launch_box_grid(g->dp, boxes, *gr, g->grid_cnt, g->grid_start, g->grid_list, g->grid_cell_of, g->grid_ext,
+                           st);
+}
+}  // namespace
+
 gmt_status gmt_build_graph(const gmt_space* space, const gmt_boxes* boxes, const float* x_init, const gmt_goal* goal,
                            const gmt_params* params, gmt_graph** graph, gmt_stream stream) {
     return gmt_build_graph_ex(space, boxes, x_init, goal, params, nullptr, 0, 0, graph, stream);
@@ -286,7 +316,9 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     LAUNCH(cudaMemsetAsync(g->out_count, 0, N * sizeof(int), st), "memset");
     if (g->kind == GMT_COST_DI) LAUNCH(cudaMemsetAsync(g->in_count, 0, N * sizeof(int), st), "memset");
     LAUNCH(g->mark(gmt_graph::kSample, 0, st), "event");
-    LAUNCH(launch_sample(sa, ba, g->X, g->is_goal, g->flags, st), "sample kernel");
+    BoxGridArgs grid;
+    LAUNCH(build_box_grid(g, ba, &grid, st), "box grid kernels");
+    LAUNCH(launch_sample(sa, ba, grid, g->X, g->is_goal, g->flags, st), "sample kernel");
     LAUNCH(launch_append(sa, ba, extra, extra_pitch, n_sampled, extra_count, g->X, g->is_goal, g->flags, st),
            "append kernel");
     LAUNCH(g->mark(gmt_graph::kSample, 1, st), "event");
@@ -446,34 +478,8 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
     GMT_CUDA(cudaMemsetAsync(g->ctl, 0, sizeof(PlanCtl), st), "memset");
     g->stage_ran[gmt_graph::kPlan] = false;
     GMT_CUDA(g->mark(gmt_graph::kPlan, 0, st), "event");
-    if (g->dp >= 2 && boxes->count >= kBoxGridMinBoxes) {
-        // many boxes: bin them on a grid over the first two position axes
-        const int G = box_grid_cells(boxes->count);
-        const size_t B = (size_t)boxes->count, cells = (size_t)G * G;
-        cudaError_t e;
-#define GROWP(ptr, n) if ((e = grow(&g->ptr, &g->cap_##ptr, (n))) != cudaSuccess) return cuda_fail(e, "allocating " #ptr)
-        GROWP(grid_cnt, cells);
-        GROWP(grid_start, cells + 1);
-        GROWP(grid_list, B);
-        GROWP(grid_cell_of, B);
-        GROWP(grid_ext, 2);
-#undef GROWP
-        BoxGridArgs& gr = a.grid;
-        gr.use = 1;
-        gr.g = G;
-        for (int k = 0; k < 2; ++k) {
-            gr.lo[k] = g->pos_lo[k];
-            gr.inv_h[k] = (float)((double)G / ((double)g->pos_hi[k] - (double)g->pos_lo[k]));
-        }
-        gr.ext = g->grid_ext;
-        gr.start = g->grid_start;
-        gr.list = g->grid_list;
-        GMT_CUDA(cudaMemsetAsync(g->grid_cnt, 0, cells * sizeof(int), st), "memset");
-        GMT_CUDA(cudaMemsetAsync(g->grid_ext, 0, 2 * sizeof(float), st), "memset");
-        GMT_CUDA(launch_box_grid(g->dp, a.boxes, gr, g->grid_cnt, g->grid_start, g->grid_list, g->grid_cell_of,
-                                 g->grid_ext, st),
-                 "box grid kernels");
-    }
+    // many boxes: bin them on a grid over the first two position axes
+    GMT_CUDA(build_box_grid(g, a.boxes, &a.grid, st), "box grid kernels");
     GMT_CUDA(launch_plan(a, blocks, threads, st, cluster), "plan kernel launch");
     GMT_CUDA(g->mark(gmt_graph::kPlan, 1, st), "event");
     g->last_blocks = cluster > 1 ? -cluster : blocks;

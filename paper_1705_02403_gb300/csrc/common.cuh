@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "gmt.h"
+#include "internal.h"
 
 namespace gmtk {
 
@@ -73,6 +74,35 @@ __device__ __forceinline__ bool in_any_box(const float* p, const float* lo, cons
     for (int b = 0; b < nbox; ++b)
         if (in_box<DP>(p, lo, hi, b)) return true;
     return false;
+}
+
+// Does point p lie in a box?  With the grid, only the boxes listed in the
+// cells from (p - ext) to p on axes 0 and 1 (widened by one cell each way) can
+// hold it; each is tested exactly.  One thread.
+template <int DP>
+__device__ __forceinline__ bool in_any_box_grid(const float* p, const float* blo, const float* bhi,
+                                                const BoxGridArgs& grid) {
+    const float ex = __ldg(&grid.ext[0]), ey = __ldg(&grid.ext[1]);
+    auto cell = [&](float v, int a) {
+        const int k = (int)floorf((v - grid.lo[a]) * grid.inv_h[a]);
+        return min(max(k, 0), grid.g - 1);
+    };
+    const int cx0 = max(cell(p[0] - ex, 0) - 1, 0), cx1 = min(cell(p[0], 0) + 1, grid.g - 1);
+    const int cy0 = max(cell(p[1] - ey, 1) - 1, 0), cy1 = min(cell(p[1], 1) + 1, grid.g - 1);
+    for (int cy = cy0; cy <= cy1; ++cy) {
+        const int e = __ldg(&grid.start[cy * grid.g + cx1 + 1]);
+        for (int t = __ldg(&grid.start[cy * grid.g + cx0]); t < e; ++t)
+            if (in_box<DP>(p, blo, bhi, __ldg(&grid.list[t]))) return true;
+    }
+    return false;
+}
+
+// Is p in any box: through the grid when the caller built one, else by
+// scanning every box.
+template <int DP>
+__device__ __forceinline__ bool point_in_boxes(const float* p, const gmtk::BoxArgs& boxes,
+                                               const gmtk::BoxGridArgs& grid) {
+    return grid.use ? in_any_box_grid<DP>(p, boxes.lo, boxes.hi, grid) : in_any_box<DP>(p, boxes.lo, boxes.hi, boxes.count);
 }
 
 // ---------------------------------------------------------------------------

@@ -27,8 +27,8 @@ constexpr int kSampleThreads = 64;  // small blocks spread the few thousand node
 // Boxes are staged in shared memory when `staged` (2 * count * DP floats): the
 // rejection loop then tests them without a global-memory round trip per box.
 template <int D, int DP>
-__global__ void __launch_bounds__(kSampleThreads) sample_kernel(SpaceArgs s, BoxArgs boxes, float* __restrict__ X,
-                                                                uint8_t* __restrict__ is_goal,
+__global__ void __launch_bounds__(kSampleThreads) sample_kernel(SpaceArgs s, BoxArgs boxes, BoxGridArgs grid,
+                                                                float* __restrict__ X, uint8_t* __restrict__ is_goal,
                                                                 int* __restrict__ flags, int staged) {
     extern __shared__ float sbox[];
     if (staged) {
@@ -40,14 +40,14 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(SpaceArgs s, Box
         boxes.lo = sbox;
         boxes.hi = sbox + boxes.count * DP;
     }
-    sample_node<D, DP>(s, boxes, X, is_goal, flags, blockIdx.x * blockDim.x + threadIdx.x);
+    sample_node<D, DP>(s, boxes, grid, X, is_goal, flags, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <int D, int DP>
-__global__ void __launch_bounds__(kHaltonThreads) halton_kernel(SpaceArgs s, BoxArgs boxes, float* __restrict__ X,
-                                                                uint8_t* __restrict__ is_goal,
+__global__ void __launch_bounds__(kHaltonThreads) halton_kernel(SpaceArgs s, BoxArgs boxes, BoxGridArgs grid,
+                                                                float* __restrict__ X, uint8_t* __restrict__ is_goal,
                                                                 int* __restrict__ flags) {
-    halton_sample_block<D, DP>(s, boxes, X, is_goal, flags);
+    halton_sample_block<D, DP>(s, boxes, grid, X, is_goal, flags);
 }
 
 template <int D, int DP>
@@ -92,15 +92,16 @@ __global__ void __launch_bounds__(kFillWarps * 32) fill_kernel(SpaceArgs s, cons
 // ------------------------------------------------------------------ launchers
 namespace {
 template <int D, int DP>
-cudaError_t sample_t(const SpaceArgs& s, BoxArgs b, float* X, uint8_t* g, int* f, cudaStream_t st) {
+cudaError_t sample_t(const SpaceArgs& s, BoxArgs b, const BoxGridArgs& grid, float* X, uint8_t* g, int* f,
+                     cudaStream_t st) {
     if (s.sampler == GMT_SAMPLER_HALTON) {
-        halton_kernel<D, DP><<<1, kHaltonThreads, 0, st>>>(s, b, X, g, f);
+        halton_kernel<D, DP><<<1, kHaltonThreads, 0, st>>>(s, b, grid, X, g, f);
         return cudaGetLastError();
     }
     const int staged = b.count > 0 && b.count <= 4096 / DP;
     const size_t smem = staged ? (size_t)2 * b.count * DP * sizeof(float) : 0;
-    sample_kernel<D, DP><<<(s.N + kSampleThreads - 1) / kSampleThreads, kSampleThreads, smem, st>>>(s, b, X, g, f,
-                                                                                                     staged);
+    sample_kernel<D, DP><<<(s.N + kSampleThreads - 1) / kSampleThreads, kSampleThreads, smem, st>>>(
+        s, b, grid, X, g, f, staged);
     return cudaGetLastError();
 }
 template <int KIND, int D>
@@ -132,18 +133,19 @@ cudaError_t fill_t(const SpaceArgs& s, const float* X, const FillDir& out, const
         default: return cudaErrorInvalidValue;                       \
     }
 
-cudaError_t launch_sample(const SpaceArgs& s, BoxArgs b, float* X, uint8_t* g, int* f, cudaStream_t st) {
-    if (s.kind == GMT_COST_DI) return sample_t<6, 3>(s, b, X, g, f, st);
+cudaError_t launch_sample(const SpaceArgs& s, BoxArgs b, const BoxGridArgs& grid, float* X, uint8_t* g, int* f,
+                          cudaStream_t st) {
+    if (s.kind == GMT_COST_DI) return sample_t<6, 3>(s, b, grid, X, g, f, st);
     switch (s.d) {
-        case 2: return sample_t<2, 2>(s, b, X, g, f, st);
-        case 3: return sample_t<3, 3>(s, b, X, g, f, st);
-        case 4: return sample_t<4, 4>(s, b, X, g, f, st);
-        case 5: return sample_t<5, 5>(s, b, X, g, f, st);
-        case 6: return sample_t<6, 6>(s, b, X, g, f, st);
-        case 7: return sample_t<7, 7>(s, b, X, g, f, st);
-        case 8: return sample_t<8, 8>(s, b, X, g, f, st);
-        case 9: return sample_t<9, 9>(s, b, X, g, f, st);
-        case 10: return sample_t<10, 10>(s, b, X, g, f, st);
+        case 2: return sample_t<2, 2>(s, b, grid, X, g, f, st);
+        case 3: return sample_t<3, 3>(s, b, grid, X, g, f, st);
+        case 4: return sample_t<4, 4>(s, b, grid, X, g, f, st);
+        case 5: return sample_t<5, 5>(s, b, grid, X, g, f, st);
+        case 6: return sample_t<6, 6>(s, b, grid, X, g, f, st);
+        case 7: return sample_t<7, 7>(s, b, grid, X, g, f, st);
+        case 8: return sample_t<8, 8>(s, b, grid, X, g, f, st);
+        case 9: return sample_t<9, 9>(s, b, grid, X, g, f, st);
+        case 10: return sample_t<10, 10>(s, b, grid, X, g, f, st);
         default: return cudaErrorInvalidValue;
     }
 }

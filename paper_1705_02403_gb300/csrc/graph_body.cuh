@@ -20,8 +20,9 @@ __device__ __forceinline__ bool in_goal_ball(const float* x, int gd, const float
 }
 
 template <int D, int DP>
-__device__ __forceinline__ void sample_node(const SpaceArgs& s, const BoxArgs& boxes, float* __restrict__ X,
-                                            uint8_t* __restrict__ is_goal, int* __restrict__ flags, int k) {
+__device__ __forceinline__ void sample_node(const SpaceArgs& s, const BoxArgs& boxes, const BoxGridArgs& grid,
+                                            float* __restrict__ X, uint8_t* __restrict__ is_goal,
+                                            int* __restrict__ flags, int k) {
     if (k >= s.n_sampled) return;
     float x[D];
     if (k == 0) {
@@ -54,7 +55,7 @@ __device__ __forceinline__ void sample_node(const SpaceArgs& s, const BoxArgs& b
                 for (int a = 0; a < D; ++a) inb = inb && s.lo[a] <= x[a] && x[a] <= s.hi[a];
                 if (!inb || !in_goal_ball(x, s.gd, s.gc, s.grho)) continue;
             }
-            if (in_any_box<DP>(x, boxes.lo, boxes.hi, boxes.count)) continue;
+            if (point_in_boxes<DP>(x, boxes, grid)) continue;
             ok = true;
         }
         if (!ok) atomicOr(flags, kSampleExhausted);
@@ -89,13 +90,13 @@ constexpr int kHaltonThreads = 512;
 // the goal ball and outside the boxes; nodes 2..n_sampled-1 = the free points
 // in the order of k (block-wide prefix sums keep that order).
 template <int D, int DP>
-__device__ void halton_sample_block(const SpaceArgs& s, const BoxArgs& boxes, float* __restrict__ X,
-                                    uint8_t* __restrict__ is_goal, int* __restrict__ flags) {
+__device__ void halton_sample_block(const SpaceArgs& s, const BoxArgs& boxes, const BoxGridArgs& grid,
+                                    float* __restrict__ X, uint8_t* __restrict__ is_goal, int* __restrict__ flags) {
     __shared__ int s_warp[kHaltonThreads / 32];
     __shared__ int s_best;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int N = s.n_sampled;
-    if (tid == 0) sample_node<D, DP>(s, boxes, X, is_goal, flags, 0);  // x_init and its checks
+    if (tid == 0) sample_node<D, DP>(s, boxes, grid, X, is_goal, flags, 0);  // x_init and its checks
     // node 1
     if (tid == 0) s_best = INT_MAX;
     __syncthreads();
@@ -112,7 +113,7 @@ __device__ void halton_sample_block(const SpaceArgs& s, const BoxArgs& boxes, fl
                 x[a] = l + u * (h - l);
                 ok = ok && s.lo[a] <= x[a] && x[a] <= s.hi[a];
             }
-            if (ok && in_goal_ball(x, s.gd, s.gc, s.grho) && !in_any_box<DP>(x, boxes.lo, boxes.hi, boxes.count))
+            if (ok && in_goal_ball(x, s.gd, s.gc, s.grho) && !point_in_boxes<DP>(x, boxes, grid))
                 atomicMin(&s_best, (int)k);
         }
         __syncthreads();
@@ -147,7 +148,7 @@ __device__ void halton_sample_block(const SpaceArgs& s, const BoxArgs& boxes, fl
 #pragma unroll
             for (int a = 0; a < D; ++a)
                 x[a] = s.lo[a] + halton_unit((uint32_t)k, halton_prime(a)) * (s.hi[a] - s.lo[a]);
-            ok = !in_any_box<DP>(x, boxes.lo, boxes.hi, boxes.count);
+            ok = !point_in_boxes<DP>(x, boxes, grid);
         }
         const unsigned m = __ballot_sync(0xffffffffu, ok);
         if (lane == 0) s_warp[warp] = __popc(m);

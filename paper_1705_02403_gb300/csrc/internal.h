@@ -36,14 +36,42 @@ struct BoxArgs {
     const float* hi;
 };
 
+// Grid over the first two position axes for checks against many boxes: box b
+// is listed in the cell of its minimum corner.  Every box that holds a point
+// p has its minimum corner within [p - ext, p] on both axes (ext: the largest
+// box side per axis), so the cells from (p - ext) to p, widened by one cell
+// each way against rounding, list every candidate; the exact box test then
+// decides as without the grid.
+struct BoxGridArgs {
+    int use;           // 0: scan every box
+    int g;             // cells per axis
+    float lo[2], inv_h[2];
+    const float* ext;  // [2], device: largest box side along axes 0 and 1
+    const int* start;  // [g * g + 1] first list entry of each cell
+    const int* list;   // box indices, grouped by cell
+};
+// Boxes from which the plan builds a grid (fewer are scanned directly).
+constexpr int kBoxGridMinBoxes = 128;
+// Cells per axis for `count` boxes.
+inline int box_grid_cells(int count) {
+    int g = 1;
+    while (g < 64 && g * g < count) g *= 2;
+    return g;
+}
+// Builds the grid: cnt [g*g] and ext [2] must be zeroed; start [g*g + 1],
+// list [count], cell_of [count].
+cudaError_t launch_box_grid(int dp, BoxArgs boxes, const BoxGridArgs& grid, int* cnt, int* start, int* list,
+                            int* cell_of, float* ext, cudaStream_t st);
+
 // Flags written by the sampling kernel.
 enum { kSampleBadInit = 1, kSampleExhausted = 2, kSampleBadAppend = 4 };
 
 // sample.cu / graph.cu
 // SampleFree with s.sampler's method (Halton: one block compacts the free
 // points in order).
-cudaError_t launch_sample(const SpaceArgs& s, BoxArgs boxes, float* X, uint8_t* is_goal, int* flags,
-                          cudaStream_t st);
+// grid: a box grid of `boxes` (use = 0 to scan them).
+cudaError_t launch_sample(const SpaceArgs& s, BoxArgs boxes, const BoxGridArgs& grid, float* X, uint8_t* is_goal,
+                          int* flags, cudaStream_t st);
 cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* out_count,
                              cudaStream_t st);
 cudaError_t launch_transpose(const SpaceArgs& s, const uint32_t* mask, uint32_t* maskT, int* in_count,
@@ -98,33 +126,6 @@ cudaError_t launch_cells_scatter(int N, const int* cell_of, const int* cell_star
 cudaError_t launch_cells_rows(const SpaceArgs& s, const float* X, const CellGrid& cg, const int* cell_of,
                               const int* cell_start, const int* sorted, bool fill, int* out_count, int* max_deg,
                               const int* row, int* col, float* cost, int* overflow, cudaStream_t st);
-
-// Grid over the first two position axes for checks against many boxes: box b
-// is listed in the cell of its minimum corner.  Every box that meets a query
-// box [lo, hi] has its minimum corner within [lo - ext, hi] on both axes (ext:
-// the largest box side per axis), so the cells from (lo - ext) to hi, widened
-// by one cell each way against rounding, list every candidate; the exact box
-// test then decides as without the grid.
-struct BoxGridArgs {
-    int use;           // 0: scan every box
-    int g;             // cells per axis
-    float lo[2], inv_h[2];
-    const float* ext;  // [2], device: largest box side along axes 0 and 1
-    const int* start;  // [g * g + 1] first list entry of each cell
-    const int* list;   // box indices, grouped by cell
-};
-// Boxes from which the plan builds a grid (fewer are scanned directly).
-constexpr int kBoxGridMinBoxes = 128;
-// Cells per axis for `count` boxes.
-inline int box_grid_cells(int count) {
-    int g = 1;
-    while (g < 64 && g * g < count) g *= 2;
-    return g;
-}
-// Builds the grid: cnt [g*g] and ext [2] must be zeroed; start [g*g + 1],
-// list [count], cell_of [count].
-cudaError_t launch_box_grid(int dp, BoxArgs boxes, const BoxGridArgs& grid, int* cnt, int* start, int* list,
-                            int* cell_of, float* ext, cudaStream_t st);
 
 // Workspace and control block of one plan (all device memory).  Counters are
 // double-buffered by iteration parity.  Open list j holds its kept entries in

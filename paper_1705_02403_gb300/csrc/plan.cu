@@ -40,7 +40,7 @@ namespace gmtk {
 
 // ------------------------------------------------------------------- kernel
 template <class Team, int KIND, int DP>
-__device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
+__device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
     constexpr int D = KIND == GMT_COST_DI ? 6 : DP;
     const int nbs = A.boxes.count <= smem_box_cap(DP) ? A.boxes.count : 0;
     for (int t = threadIdx.x; t < nbs * DP; t += blockDim.x) {
@@ -330,7 +330,7 @@ __device__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
 }
 
 template <class Team, int KIND, int DP>
-__global__ void __launch_bounds__(1024) plan_kernel(PlanArgs A, Team team) {
+__global__ void __launch_bounds__(1024, 1) plan_kernel(PlanArgs A, Team team) {
     extern __shared__ float sbox[];
     plan_body<Team, KIND, DP>(A, team, sbox);
 }
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs A, Team team) {
 // empty.  Queries never wait for each other, so teams need no co-scheduling
 // beyond their own CTAs.
 template <class Team, int KIND, int DP>
-__global__ void __launch_bounds__(1024) plan_batch_kernel(const PlanArgs* __restrict__ queries,
+__global__ void __launch_bounds__(1024, 1) plan_batch_kernel(const PlanArgs* __restrict__ queries,
                                                           const int* __restrict__ order, int nq,
                                                           int* __restrict__ next, int* __restrict__ slot,
                                                           BatchScratch scratch, Team team) {

@@ -112,44 +112,32 @@ __device__ __forceinline__ bool box_meets(const float* blo, const float* bhi, in
     return m;
 }
 
-// Calls visit(bi) on chunks of candidate boxes, one per lane (bi = -1 for an
-// empty lane), until visit returns true (it must return the same value in
-// every lane); returns whether it did.  Candidates: every box, or with the
-// grid, the boxes listed in the cells that can hold a box meeting [lo, hi].
-template <class F>
-__device__ __forceinline__ bool for_box_chunks(const float* lo, const float* hi, int nbox, const BoxGridArgs& grid,
-                                               F&& visit) {
-    const int lane = threadIdx.x & 31;
-    if (!grid.use) {
-        for (int b0 = 0; b0 < nbox; b0 += 32)
-            if (visit(b0 + lane < nbox ? b0 + lane : -1)) return true;
-        return false;
-    }
-    const float ex = __ldg(&grid.ext[0]), ey = __ldg(&grid.ext[1]);
-    auto cell = [&](float x, int a) {
-        const int k = (int)floorf((x - grid.lo[a]) * grid.inv_h[a]);
-        return min(max(k, 0), grid.g - 1);
-    };
-    const int cx0 = max(cell(lo[0] - ex, 0) - 1, 0), cx1 = min(cell(hi[0], 0) + 1, grid.g - 1);
-    const int cy0 = max(cell(lo[1] - ey, 1) - 1, 0), cy1 = min(cell(hi[1], 1) + 1, grid.g - 1);
-    for (int cy = cy0; cy <= cy1; ++cy) {
-        const int s = __ldg(&grid.start[cy * grid.g + cx0]), e = __ldg(&grid.start[cy * grid.g + cx1 + 1]);
-        for (int t0 = s; t0 < e; t0 += 32)
-            if (visit(t0 + lane < e ? __ldg(&grid.list[t0 + lane]) : -1)) return true;
-    }
-    return false;
-}
-
 // Geometric edge y -> x of length L: m = max(2, ceil(L/spacing) + 1) points
 // p_k = y + t_k (x - y), t_k = k/(m-1); collision if one lies in a closed box.
-// Every computed p_k lies within a few ulps of the segment's bounding box.
+// Without the grid, boxes that do not meet the segment's bounding box (every
+// computed p_k lies within a few ulps of it) are set aside 32 at a time first.
 template <int DP>
-__device__ bool segment_free_warp(const float* y, const float* x, float L, float spacing, const float* blo,
+__device__ __forceinline__ bool segment_free_warp(const float* y, const float* x, float L, float spacing, const float* blo,
                                   const float* bhi, int nbox, const BoxGridArgs& grid) {
     const int lane = threadIdx.x & 31;
     int m = (int)ceilf(L / spacing) + 1;
     if (m < 2) m = 2;
     const float denom = (float)(m - 1);
+    if (grid.use) {
+        for (int k0 = 0; k0 < m; k0 += 32) {
+            const int k = k0 + lane;
+            bool hit = false;
+            if (k < m) {
+                const float t = (float)k / denom;
+                float p[DP];
+#pragma unroll
+                for (int a = 0; a < DP; ++a) p[a] = y[a] + t * (x[a] - y[a]);
+                hit = in_any_box_grid<DP>(p, blo, bhi, grid);
+            }
+            if (__any_sync(0xffffffffu, hit)) return false;
+        }
+        return true;
+    }
     float lo[DP], hi[DP];
 #pragma unroll
     for (int a = 0; a < DP; ++a) {
@@ -157,46 +145,48 @@ __device__ bool segment_free_warp(const float* y, const float* x, float L, float
         lo[a] = fminf(x[a], y[a]) - e;
         hi[a] = fmaxf(x[a], y[a]) + e;
     }
-    const bool hit_any = for_box_chunks(lo, hi, nbox, grid, [&](int bi) {
-        const unsigned near = __ballot_sync(0xffffffffu, bi >= 0 && box_meets<DP>(blo, bhi, bi, lo, hi));
-        if (!near) return false;
+    for (int b0 = 0; b0 < nbox; b0 += 32) {
+        const int b = b0 + lane;
+        const unsigned near = __ballot_sync(0xffffffffu, b < nbox && box_meets<DP>(blo, bhi, b, lo, hi));
+        if (!near) continue;
         for (int k0 = 0; k0 < m; k0 += 32) {
             const int k = k0 + lane;
-            float p[DP];
+            bool hit = false;
             if (k < m) {
                 const float t = (float)k / denom;
+                float p[DP];
 #pragma unroll
                 for (int a = 0; a < DP; ++a) p[a] = y[a] + t * (x[a] - y[a]);
+                for (unsigned w = near; w; w &= w - 1) hit = hit || in_box<DP>(p, blo, bhi, b0 + __ffs(w) - 1);
             }
-            bool hit = false;
-            for (unsigned w = near; w; w &= w - 1) {
-                const int bb = __shfl_sync(0xffffffffu, bi, __ffs(w) - 1);
-                if (k < m) hit = hit || in_box<DP>(p, blo, bhi, bb);
-            }
-            if (__any_sync(0xffffffffu, hit)) return true;
+            if (__any_sync(0xffffffffu, hit)) return false;
         }
-        return false;
-    });
-    return !hit_any;
+    }
+    return true;
 }
 
 // Double-integrator edge: `points` samples of the Hermite trajectory at
 // s_k = k/(points-1); collision if one lies in a box or outside the position
-// bounds.  The cubic lies in the convex hull of its Bezier control points
-// p0, p0 + tau v0 / 3, p1 - tau v1 / 3, p1, whose bounding box (inflated)
-// selects the boxes.
-__device__ inline bool trajectory_free_warp(const float* y, const float* x, float tau, int points, const float* plo,
+// bounds.  Without the grid, the boxes are first filtered against the
+// bounding box of the cubic's Bezier control points p0, p0 + tau v0 / 3,
+// p1 - tau v1 / 3, p1 (the curve lies in their convex hull), inflated.
+__device__ __forceinline__ bool trajectory_free_warp(const float* y, const float* x, float tau, int points, const float* plo,
                                             const float* phi, const float* blo, const float* bhi, int nbox,
                                             const BoxGridArgs& grid) {
     const int lane = threadIdx.x & 31;
     const float denom = (float)(points - 1);
     float lo[3], hi[3];
+    unsigned near_first = 0;  // boxes 0..31, reused by the first chunk of points
+    if (!grid.use) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float c1 = y[a] + tau * y[3 + a] / 3.0f, c2 = x[a] - tau * x[3 + a] / 3.0f;
-        const float e = 1e-5f * (fabsf(y[a]) + fabsf(x[a]) + tau * (fabsf(y[3 + a]) + fabsf(x[3 + a]))) + 1e-30f;
-        lo[a] = fminf(fminf(y[a], x[a]), fminf(c1, c2)) - e;
-        hi[a] = fmaxf(fmaxf(y[a], x[a]), fmaxf(c1, c2)) + e;
+        for (int a = 0; a < 3; ++a) {
+            const float c1 = y[a] + tau * y[3 + a] / 3.0f, c2 = x[a] - tau * x[3 + a] / 3.0f;
+            const float e =
+                1e-5f * (fabsf(y[a]) + fabsf(x[a]) + tau * (fabsf(y[3 + a]) + fabsf(x[3 + a]))) + 1e-30f;
+            lo[a] = fminf(fminf(y[a], x[a]), fminf(c1, c2)) - e;
+            hi[a] = fmaxf(fmaxf(y[a], x[a]), fmaxf(c1, c2)) + e;
+        }
+        if (nbox > 0) near_first = __ballot_sync(0xffffffffu, lane < nbox && box_meets<3>(blo, bhi, lane, lo, hi));
     }
     for (int k0 = 0; k0 < points; k0 += 32) {
         const int k = k0 + lane;
@@ -207,18 +197,18 @@ __device__ inline bool trajectory_free_warp(const float* y, const float* x, floa
             hermite_point(y, x, tau, s, p);
 #pragma unroll
             for (int a = 0; a < 3; ++a) hit = hit || p[a] < plo[a] || p[a] > phi[a];
+            if (grid.use && !hit) hit = in_any_box_grid<3>(p, blo, bhi, grid);
+        }
+        if (!grid.use) {
+            for (int b0 = 0; b0 < nbox; b0 += 32) {
+                const unsigned near =
+                    b0 == 0 ? near_first
+                            : __ballot_sync(0xffffffffu, b0 + lane < nbox && box_meets<3>(blo, bhi, b0 + lane, lo, hi));
+                if (k < points)
+                    for (unsigned w = near; w; w &= w - 1) hit = hit || in_box<3>(p, blo, bhi, b0 + __ffs(w) - 1);
+            }
         }
         if (__any_sync(0xffffffffu, hit)) return false;
-        const bool hit_box = for_box_chunks(lo, hi, nbox, grid, [&](int bi) {
-            const unsigned near = __ballot_sync(0xffffffffu, bi >= 0 && box_meets<3>(blo, bhi, bi, lo, hi));
-            bool h = false;
-            for (unsigned w = near; w; w &= w - 1) {
-                const int bb = __shfl_sync(0xffffffffu, bi, __ffs(w) - 1);
-                if (k < points) h = h || in_box<3>(p, blo, bhi, bb);
-            }
-            return __any_sync(0xffffffffu, h);
-        });
-        if (hit_box) return false;
     }
     return true;
 }
