@@ -44,7 +44,7 @@
 namespace {
 
 enum { ORC_OK = 0, ORC_NO_PATH = 1, ORC_ERR_INVALID = -1, ORC_ERR_ITER_LIMIT = -5 };
-enum { ORC_EUCLID = 0, ORC_DI = 1 };
+enum { ORC_EUCLID = 0, ORC_DI = 1, ORC_DUBINS = 2 };
 enum { UNEXPLORED = 0, OPEN = 1, CLOSED = 2 };
 const int MAXD = 12;
 
@@ -198,10 +198,253 @@ template <typename R> int di_bisect_steps();
 template <> int di_bisect_steps<float>() { return 24; }
 template <> int di_bisect_steps<double>() { return 52; }
 
+// ---------------------------------------------------------------------------
+// Dubins airplane (Sec. V-A): a planar Dubins car of turning radius rho with a
+// single integrator in altitude (unbounded climb rate) and the Euclidean
+// length of the trajectory as cost.  State (x, y, z, theta).  Reading: the
+// trajectory follows the shortest planar Dubins path (the best of the words
+// LSL, RSR, LSR, RSL, RLR, LRL; Dubins 1957) with altitude linear in planar arc
+// length, so its length is sqrt(L^2 + dz^2) with L the planar path length: the
+// shortest trajectory, because any altitude profile over a planar path of
+// length L is at least that long and the bound grows with L.
+//
+// Sine, cosine and arctangent are this file's own (range reduction and Taylor
+// series evaluated in a fixed order), so results do not depend on a math
+// library; the float and double instantiations use their own constants.
+// ---------------------------------------------------------------------------
+template <typename R> struct DubK;
+template <> struct DubK<float> {
+    static constexpr float pi = 3.14159265358979f, two_pi = 6.28318530717959f, pi_2 = 1.57079632679490f,
+                           pi_4 = 0.785398163397448f;
+    static constexpr float pi_2_hi = 1.57079637050628662109375f;  // fl(pi/2)
+    static constexpr float pi_2_lo = -4.37113900018624e-8f;       // pi/2 - fl(pi/2)
+    static constexpr float two_over_pi = 0.636619772367581f, tan_pi_8 = 0.414213562373095f;
+};
+template <> struct DubK<double> {
+    static constexpr double pi = 3.14159265358979323846, two_pi = 6.28318530717958647692,
+                            pi_2 = 1.57079632679489661923, pi_4 = 0.785398163397448309616;
+    static constexpr double pi_2_hi = 1.57079632679489655800;  // fl64(pi/2)
+    static constexpr double pi_2_lo = 6.12323399573676603587e-17;
+    static constexpr double two_over_pi = 0.636619772367581343076, tan_pi_8 = 0.414213562373095048802;
+};
+
+// sin r, cos r for |r| <= pi/4 (+ rounding): Taylor polynomials through r^11
+// and r^12, Horner form.
+template <typename R> R dub_sin_poly(R r) {
+    const R r2 = r * r;
+    return r + r * (r2 * ((R)(-1.0 / 6) + r2 * ((R)(1.0 / 120) + r2 * ((R)(-1.0 / 5040) +
+                    r2 * ((R)(1.0 / 362880) + r2 * (R)(-1.0 / 39916800))))));
+}
+template <typename R> R dub_cos_poly(R r) {
+    const R r2 = r * r;
+    return (R)1 + r2 * ((R)(-1.0 / 2) + r2 * ((R)(1.0 / 24) + r2 * ((R)(-1.0 / 720) +
+                  r2 * ((R)(1.0 / 40320) + r2 * ((R)(-1.0 / 3628800) + r2 * (R)(1.0 / 479001600))))));
+}
+// x = k pi/2 + r with k the nearest integer to 2x/pi (ties to even); the
+// quadrant k mod 4 picks +-sin r or +-cos r.
+template <typename R> void dub_sincos(R x, R* s, R* c) {
+    const R kf = std::nearbyint(x * DubK<R>::two_over_pi);
+    const R r = (x - kf * DubK<R>::pi_2_hi) - kf * DubK<R>::pi_2_lo;
+    const R sr = dub_sin_poly(r), cr = dub_cos_poly(r);
+    const int q = (int)((long long)kf & 3);
+    if (q == 0) { *s = sr; *c = cr; }
+    else if (q == 1) { *s = cr; *c = -sr; }
+    else if (q == 2) { *s = -sr; *c = -cr; }
+    else { *s = -cr; *c = sr; }
+}
+template <typename R> R dub_cos(R x) { R s, c; dub_sincos(x, &s, &c); return c; }
+// atan z, 0 <= z <= 1: above tan(pi/8), atan z = pi/4 + atan u with
+// u = (z - 1)/(z + 1); then the series u - u^3/3 + u^5/5 - ... through u^21
+// (|u| <= tan(pi/8)).
+template <typename R> R dub_atan01(R z) {
+    R base = 0, u = z;
+    if (z > DubK<R>::tan_pi_8) { base = DubK<R>::pi_4; u = (z - (R)1) / (z + (R)1); }
+    const R u2 = u * u;
+    R poly = (R)(-1.0 / 21);
+    poly = (R)(1.0 / 19) + u2 * poly;
+    poly = (R)(-1.0 / 17) + u2 * poly;
+    poly = (R)(1.0 / 15) + u2 * poly;
+    poly = (R)(-1.0 / 13) + u2 * poly;
+    poly = (R)(1.0 / 11) + u2 * poly;
+    poly = (R)(-1.0 / 9) + u2 * poly;
+    poly = (R)(1.0 / 7) + u2 * poly;
+    poly = (R)(-1.0 / 5) + u2 * poly;
+    poly = (R)(1.0 / 3) + u2 * poly;
+    poly = -(u2 * poly);
+    return base + (u + u * poly);
+}
+// Angle of (x, y) in (-pi, pi]; (0, 0) -> 0.
+template <typename R> R dub_atan2(R y, R x) {
+    const R ax = std::fabs(x), ay = std::fabs(y);
+    if (ax == (R)0 && ay == (R)0) return 0;
+    R a = ay <= ax ? dub_atan01(ay / ax) : DubK<R>::pi_2 - dub_atan01(ax / ay);
+    if (x < (R)0) a = DubK<R>::pi - a;
+    return y < (R)0 ? -a : a;
+}
+template <typename R> R dub_acos(R x) { return dub_atan2(std::sqrt(((R)1 - x) * ((R)1 + x)), x); }
+template <typename R> R dub_mod2pi(R a) { return a - DubK<R>::two_pi * std::floor(a / DubK<R>::two_pi); }
+// An end turn (t or q) within 2^-13 of a full circle is the small negative
+// turn it differs by: a full loop is never part of a shortest path, and the
+// turn is that close to 2 pi only when its exact value is a rounding error
+// away from 0.
+template <typename R> R dub_end_turn(R a) {
+    return a > DubK<R>::two_pi - (R)(1.0 / 8192) ? a - DubK<R>::two_pi : a;
+}
+
+enum { DUB_LSL = 0, DUB_RSR, DUB_LSR, DUB_RSL, DUB_RLR, DUB_LRL, DUB_NONE };
+
+template <typename R>
+struct DubinsPath { int word; R t, p, q; R L; };   // t, p, q: segment lengths / rho; L = rho ((t + p) + q)
+
+// Lengths of all six words (+inf where a word does not exist), in the order of
+// the enum.  Frame: the line from start to end, scaled by 1/rho: the start is
+// at the origin with heading alpha, the end at (d, 0) with heading beta.  A CSC
+// word's straight part is the common tangent of its two turning circles; a CCC
+// word's middle circle touches both (it exists only for circles at most 4 rho
+// apart).
+template <typename R>
+void dubins_words(R x0, R y0, R th0, R x1, R y1, R th1, R rho, DubinsPath<R> out[6]) {
+    const R dx = x1 - x0, dy = y1 - y0;
+    const R D = std::sqrt(dx * dx + dy * dy);
+    const R d = D / rho;
+    const R phi = dub_atan2(dy, dx);
+    const R al = dub_mod2pi(th0 - phi), be = dub_mod2pi(th1 - phi);
+    R sa, ca, sb, cb;
+    dub_sincos(al, &sa, &ca);
+    dub_sincos(be, &sb, &cb);
+    const R cab = dub_cos(al - be);
+    const R dd = d * d;
+    const R inf = std::numeric_limits<R>::infinity();
+    for (int w = 0; w < 6; ++w) out[w] = DubinsPath<R>{w, 0, 0, 0, inf};
+    auto set = [&](int w, R t, R p, R q) {
+        t = dub_end_turn(t);
+        q = dub_end_turn(q);
+        out[w] = DubinsPath<R>{w, t, p, q, ((t + p) + q) * rho};
+    };
+    {   // LSL
+        const R p2 = (((R)2 + dd) - (R)2 * cab) + ((R)2 * d) * (sa - sb);
+        if (p2 >= (R)0) {
+            const R psi = dub_atan2(cb - ca, (d + sa) - sb);
+            set(DUB_LSL, dub_mod2pi(psi - al), std::sqrt(p2), dub_mod2pi(be - psi));
+        }
+    }
+    {   // RSR
+        const R p2 = (((R)2 + dd) - (R)2 * cab) + ((R)2 * d) * (sb - sa);
+        if (p2 >= (R)0) {
+            const R psi = dub_atan2(ca - cb, (d - sa) + sb);
+            set(DUB_RSR, dub_mod2pi(al - psi), std::sqrt(p2), dub_mod2pi(psi - be));
+        }
+    }
+    {   // LSR
+        const R p2 = ((dd - (R)2) + (R)2 * cab) + ((R)2 * d) * (sa + sb);
+        if (p2 >= (R)0) {
+            const R p = std::sqrt(p2);
+            const R psi = dub_atan2(-ca - cb, (d + sa) + sb) - dub_atan2((R)-2, p);
+            set(DUB_LSR, dub_mod2pi(psi - al), p, dub_mod2pi(psi - be));
+        }
+    }
+    {   // RSL
+        const R p2 = ((dd - (R)2) + (R)2 * cab) - ((R)2 * d) * (sa + sb);
+        if (p2 >= (R)0) {
+            const R p = std::sqrt(p2);
+            const R psi = dub_atan2(ca + cb, (d - sa) - sb) - dub_atan2((R)2, p);
+            set(DUB_RSL, dub_mod2pi(al - psi), p, dub_mod2pi(be - psi));
+        }
+    }
+    {   // RLR
+        const R c = ((((R)6 - dd) + (R)2 * cab) + ((R)2 * d) * (sa - sb)) / (R)8;
+        if (std::fabs(c) <= (R)1) {
+            const R p = dub_mod2pi(DubK<R>::two_pi - dub_acos(c));
+            const R t = dub_mod2pi((al - dub_atan2(ca - cb, (d - sa) + sb)) + p / (R)2);
+            set(DUB_RLR, t, p, dub_mod2pi(((al - be) - t) + p));
+        }
+    }
+    {   // LRL
+        const R c = ((((R)6 - dd) + (R)2 * cab) + ((R)2 * d) * (sb - sa)) / (R)8;
+        if (std::fabs(c) <= (R)1) {
+            const R p = dub_mod2pi(DubK<R>::two_pi - dub_acos(c));
+            const R t = dub_mod2pi(((-al) - dub_atan2(ca - cb, (d + sa) - sb)) + p / (R)2);
+            set(DUB_LRL, t, p, dub_mod2pi(((be - al) - t) + p));
+        }
+    }
+}
+
+// The shortest word (ties: the earliest in enum order).
+template <typename R>
+DubinsPath<R> dubins_path(const R* s0, const R* s1, R rho) {
+    DubinsPath<R> w[6];
+    dubins_words(s0[0], s0[1], s0[3], s1[0], s1[1], s1[3], rho, w);
+    DubinsPath<R> best{DUB_NONE, 0, 0, 0, std::numeric_limits<R>::infinity()};
+    for (int k = 0; k < 6; ++k)
+        if (w[k].L < best.L) best = w[k];
+    return best;
+}
+
+// Prefilter: the cost is at least the 3D distance, so a pair whose squared
+// distance reaches (1 + 2^-6) r^2 has no edge; the margin keeps the test from
+// deciding any pair the rounded cost could put below r.
+template <typename R>
+bool dubins_near(const R* s0, const R* s1, R r) {
+    const R dx = s1[0] - s0[0], dy = s1[1] - s0[1], dz = s1[2] - s0[2];
+    return ((dx * dx + dy * dy) + dz * dz) < (r * r) * (R)1.015625;
+}
+
+template <typename R>
+R cost_dubins(const R* s0, const R* s1, R rho) {
+    const DubinsPath<R> P = dubins_path(s0, s1, rho);
+    const R dz = s1[2] - s0[2];
+    return std::sqrt(P.L * P.L + dz * dz);
+}
+
+// Pose at fraction s of the trajectory: planar arc length ell = s L walked
+// through the word's segments (a left turn by angle a from heading th moves by
+// rho (sin(th + a) - sin th, cos th - cos(th + a)), a right turn by
+// rho (sin th - sin(th - a), cos(th - a) - cos th), a straight part of length l
+// by l (cos th, sin th)); altitude z0 + s dz.
+template <typename R>
+void dubins_point(const R* s0, const R* s1, const DubinsPath<R>& P, R rho, R s, R* out) {
+    static const int kSeg[6][3] = {{0, 1, 0}, {2, 1, 2}, {0, 1, 2}, {2, 1, 0}, {2, 0, 2}, {0, 2, 0}};  // 0 L, 1 S, 2 R
+    R x = s0[0], y = s0[1], th = s0[3];
+    R ell = s * P.L;
+    const R len[3] = {P.t * rho, P.p * rho, P.q * rho};
+    for (int k = 0; k < 3; ++k) {
+        const R a = ell < len[k] ? ell : len[k];
+        const int type = kSeg[P.word][k];
+        R s_th, c_th;
+        dub_sincos(th, &s_th, &c_th);
+        if (type == 1) {
+            x = x + a * c_th;
+            y = y + a * s_th;
+        } else {
+            const R ang = a / rho;
+            const R th2 = type == 0 ? th + ang : th - ang;
+            R s_2, c_2;
+            dub_sincos(th2, &s_2, &c_2);
+            if (type == 0) {
+                x = x + rho * (s_2 - s_th);
+                y = y + rho * (c_th - c_2);
+            } else {
+                x = x + rho * (s_th - s_2);
+                y = y + rho * (c_2 - c_th);
+            }
+            th = th2;
+        }
+        ell = ell - a;
+    }
+    out[0] = x;
+    out[1] = y;
+    out[2] = s0[2] + s * (s1[2] - s0[2]);
+    out[3] = th;
+}
+
 // Cost of the directed connection from -> to, both states of dimension d.
 template <typename R>
-R edge_cost(int kind, const R* from, const R* to, int d, R r, R* tau) {
+R edge_cost(int kind, const R* from, const R* to, int d, R r, R* tau, R rho = 0) {
     if (kind == ORC_EUCLID) { if (tau) *tau = 0; return cost_euclid(from, to, d); }
+    if (kind == ORC_DUBINS) {
+        if (tau) *tau = 0;
+        return dubins_near(from, to, r) ? cost_dubins(from, to, rho) : std::numeric_limits<R>::infinity();
+    }
     return cost_di(from, to, r, DI_GRID, di_bisect_steps<R>(), tau);
 }
 
@@ -254,6 +497,26 @@ bool edge_free_di(const R* y, const R* x, R tau, int points, const float* plo, c
     return true;
 }
 
+// Dubins airplane edge of cost c: m = max(2, ceil(c/spacing)+1) points at
+// s_k = k/(m-1) of the path; a point in a box or outside the position bounds
+// collides.
+template <typename R>
+bool edge_free_dubins(const R* y, const R* x, R c, R rho, R spacing, const float* plo, const float* phi,
+                      const Boxes& B) {
+    const DubinsPath<R> P = dubins_path(y, x, rho);
+    int m = (int)std::ceil(c / spacing) + 1;
+    if (m < 2) m = 2;
+    R q[4];
+    for (int k = 0; k < m; ++k) {
+        const R s = (R)k / (R)(m - 1);
+        dubins_point(y, x, P, rho, s, q);
+        for (int a = 0; a < 3; ++a)
+            if (q[a] < (R)plo[a] || q[a] > (R)phi[a]) return false;
+        if (point_in_obstacle(q, B)) return false;
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // Neighbour graph: y -> x is an edge iff y != x and c(y,x) < r (Section III-A:
 // neighbours are samples whose connection cost is less than r).  Out-lists are
@@ -263,6 +526,7 @@ template <typename R>
 struct Graph {
     int kind = 0, d = 0, dp = 0, N = 0;
     R r = 0;
+    R rho = 0;   // Dubins airplane: turning radius
     std::vector<R> X;            // [d][N]
     std::vector<uint8_t> goal;   // [N]
     std::vector<int32_t> out_row, out_col, in_row, in_col;
@@ -271,9 +535,10 @@ struct Graph {
 };
 
 template <typename R>
-Graph<R>* build_graph(int kind, int d, int dp, int N, const float* X, const uint8_t* goal, float r) {
+Graph<R>* build_graph(int kind, int d, int dp, int N, const float* X, const uint8_t* goal, float r, float rho = 0.0f) {
     Graph<R>* g = new Graph<R>();
     g->kind = kind; g->d = d; g->dp = dp; g->N = N; g->r = (R)r;
+    g->rho = (R)rho;
     g->X.resize((size_t)d * N);
     for (size_t i = 0; i < (size_t)d * N; ++i) g->X[i] = (R)X[i];
     g->goal.assign(goal, goal + N);
@@ -284,7 +549,7 @@ Graph<R>* build_graph(int kind, int d, int dp, int N, const float* X, const uint
         for (int j = 0; j < N; ++j) {
             if (j == i) continue;
             g->state(j, sj);
-            R c = edge_cost<R>(kind, si, sj, d, g->r, nullptr);
+            R c = edge_cost<R>(kind, si, sj, d, g->r, nullptr, g->rho);
             if (c < g->r) out[i].push_back({j, c});
         }
     }
@@ -334,6 +599,8 @@ bool check_edge(const Graph<R>& g, int y, int x, R c, const PlanCfg& P) {
     R sy[MAXD], sx[MAXD];
     g.state(y, sy); g.state(x, sx);
     if (g.kind == ORC_EUCLID) return edge_free_geometric(sy, sx, g.dp, c, (R)P.seg_spacing, P.boxes);
+    if (g.kind == ORC_DUBINS)
+        return edge_free_dubins(sy, sx, c, g.rho, (R)P.seg_spacing, P.pos_lo, P.pos_hi, P.boxes);
     R tau;
     cost_di<R>(sy, sx, g.r, DI_GRID, di_bisect_steps<R>(), &tau);
     return edge_free_di(sy, sx, tau, P.traj_points, P.pos_lo, P.pos_hi, P.boxes);
@@ -762,6 +1029,69 @@ double orc_radius_thm1(int n, int d, double eta, double mu) {
 }
 
 // ---- graphs ----
+void* orc_graph_build_dubins(int precision, int N, const float* X, const uint8_t* goal, float r, float rho) {
+    if (precision == 64) return build_graph<double>(ORC_DUBINS, 4, 3, N, X, goal, r, rho);
+    return build_graph<float>(ORC_DUBINS, 4, 3, N, X, goal, r, rho);
+}
+
+// Dubins words of a pair (float or double, by `precision`): six entries of
+// (word, t, p, q, L) in enum order; returns the index of the shortest (6 if
+// none exists).  States are (x, y, z, theta).
+int orc_dubins_words(int precision, const double* s0, const double* s1, double rho, double* out) {
+    auto run = [&](auto zero) {
+        typedef decltype(zero) R;
+        const R a[4] = {(R)s0[0], (R)s0[1], (R)s0[2], (R)s0[3]}, b[4] = {(R)s1[0], (R)s1[1], (R)s1[2], (R)s1[3]};
+        DubinsPath<R> w[6];
+        dubins_words(a[0], a[1], a[3], b[0], b[1], b[3], (R)rho, w);
+        for (int k = 0; k < 6; ++k) {
+            out[5 * k + 0] = w[k].word; out[5 * k + 1] = w[k].t; out[5 * k + 2] = w[k].p;
+            out[5 * k + 3] = w[k].q; out[5 * k + 4] = w[k].L;
+        }
+        return dubins_path(a, b, (R)rho).word;
+    };
+    return precision == 64 ? run(0.0) : run(0.0f);
+}
+// Cost of the connection s0 -> s1 (r: the prefilter's radius; +inf when the
+// prefilter rejects the pair).
+double orc_cost_dubins(int precision, const double* s0, const double* s1, double rho, double r) {
+    auto run = [&](auto zero) {
+        typedef decltype(zero) R;
+        const R a[4] = {(R)s0[0], (R)s0[1], (R)s0[2], (R)s0[3]}, b[4] = {(R)s1[0], (R)s1[1], (R)s1[2], (R)s1[3]};
+        return (double)edge_cost<R>(ORC_DUBINS, a, b, 4, (R)r, nullptr, (R)rho);
+    };
+    return precision == 64 ? run(0.0) : run(0.0f);
+}
+// Pose at fraction s of the trajectory s0 -> s1.
+void orc_dubins_point(int precision, const double* s0, const double* s1, double rho, double s, double* out) {
+    auto run = [&](auto zero) {
+        typedef decltype(zero) R;
+        const R a[4] = {(R)s0[0], (R)s0[1], (R)s0[2], (R)s0[3]}, b[4] = {(R)s1[0], (R)s1[1], (R)s1[2], (R)s1[3]};
+        R q[4];
+        dubins_point(a, b, dubins_path(a, b, (R)rho), (R)rho, (R)s, q);
+        for (int k = 0; k < 4; ++k) out[k] = (double)q[k];
+    };
+    if (precision == 64) run(0.0); else run(0.0f);
+}
+// The trigonometric building blocks over arrays (float or double).
+void orc_dub_trig(int precision, int which, int n, const double* x, const double* y, double* out0, double* out1) {
+    for (int i = 0; i < n; ++i) {
+        if (precision == 64) {
+            if (which == 0) dub_sincos(x[i], &out0[i], &out1[i]);
+            else out0[i] = which == 1 ? dub_atan2(y[i], x[i]) : dub_acos(x[i]);
+        } else {
+            float a, b;
+            if (which == 0) { dub_sincos((float)x[i], &a, &b); out0[i] = a; out1[i] = b; }
+            else out0[i] = which == 1 ? dub_atan2((float)y[i], (float)x[i]) : dub_acos((float)x[i]);
+        }
+    }
+}
+// Collision verdict of the trajectory s0 -> s1 of cost c (float).
+int orc_edge_free_dubins_f32(const float* s0, const float* s1, float c, float rho, float spacing, const float* pos_lo,
+                             const float* pos_hi, int nbox, const float* blo, const float* bhi) {
+    Boxes B{nbox, 3, blo, bhi};
+    return edge_free_dubins<float>(s0, s1, c, rho, spacing, pos_lo, pos_hi, B) ? 1 : 0;
+}
+
 void* orc_graph_build(int precision, int kind, int d, int dp, int N, const float* X, const uint8_t* goal, float r) {
     if (precision == 64) return build_graph<double>(kind, d, dp, N, X, goal, r);
     return build_graph<float>(kind, d, dp, N, X, goal, r);

@@ -20,7 +20,7 @@ SRC = os.path.join(HERE, "gmt_oracle.cpp")
 LIB = os.path.join(HERE, "liboracle.so")
 
 OK, NO_PATH, ERR_INVALID, ERR_ITER_LIMIT = 0, 1, -1, -5
-EUCLID, DI = 0, 1
+EUCLID, DI, DUBINS = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -72,6 +72,13 @@ def lib():
         L.orc_sample_halton.argtypes = [I32, I32, P, P, I32, P, P, P, P, F32, I32, I32, C.c_int64, P, P]
         L.orc_sample_halton.restype = I32
         L.orc_graph_build.argtypes = [I32, I32, I32, I32, I32, P, P, F32]; L.orc_graph_build.restype = P
+        L.orc_graph_build_dubins.argtypes = [I32, I32, P, P, F32, F32]; L.orc_graph_build_dubins.restype = P
+        L.orc_dubins_words.argtypes = [I32, P, P, F64, P]; L.orc_dubins_words.restype = I32
+        L.orc_cost_dubins.argtypes = [I32, P, P, F64, F64]; L.orc_cost_dubins.restype = F64
+        L.orc_dubins_point.argtypes = [I32, P, P, F64, F64, P]
+        L.orc_dub_trig.argtypes = [I32, I32, I32, P, P, P, P]
+        L.orc_edge_free_dubins_f32.argtypes = [P, P, F32, F32, F32, P, P, I32, P, P]
+        L.orc_edge_free_dubins_f32.restype = I32
         L.orc_graph_free.argtypes = [I32, P]
         L.orc_graph_num_edges.argtypes = [I32, P]; L.orc_graph_num_edges.restype = I64
         L.orc_graph_copy.argtypes = [I32, P, P, P, P, P, P, P]
@@ -187,6 +194,55 @@ def sample_halton(problem, max_candidates: int | None = None):
     return X, goal
 
 
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+# --------------------------------------------------------------------------- Dubins airplane
+DUBINS_WORDS = ("LSL", "RSR", "LSR", "RSL", "RLR", "LRL")
+
+
+def dubins_words(s0, s1, rho, precision=32):
+    """All six Dubins words of the pair (x, y, z, theta) -> (x, y, z, theta):
+    array [6][5] of (word, t, p, q, L) (+inf L where a word does not exist) and
+    the index of the shortest.  precision 32 computes in float."""
+    a, b = _f64(s0), _f64(s1)
+    out = np.zeros((6, 5), np.float64)
+    best = lib().orc_dubins_words(precision, _p(a), _p(b), float(rho), _p(out))
+    return out, best
+
+
+def cost_dubins(s0, s1, rho, r, precision=32):
+    """Edge cost of s0 -> s1 (+inf when the distance prefilter rejects it)."""
+    a, b = _f64(s0), _f64(s1)
+    return lib().orc_cost_dubins(precision, _p(a), _p(b), float(rho), float(r))
+
+
+def dubins_point(s0, s1, rho, s, precision=32):
+    a, b = _f64(s0), _f64(s1)
+    out = np.zeros(4, np.float64)
+    lib().orc_dubins_point(precision, _p(a), _p(b), float(rho), float(s), _p(out))
+    return out
+
+
+def dub_trig(which, x, y=None, precision=32):
+    """The oracle's own trigonometry over arrays: which 0 = (sin, cos) of x,
+    1 = atan2(y, x), 2 = acos(x)."""
+    x = _f64(x).ravel()
+    y = _f64(y).ravel() if y is not None else np.zeros_like(x)
+    o0, o1 = np.zeros_like(x), np.zeros_like(x)
+    lib().orc_dub_trig(precision, which, x.size, _p(x), _p(y), _p(o0), _p(o1))
+    return (o0, o1) if which == 0 else o0
+
+
+def edge_free_dubins(s0, s1, c, rho, spacing, pos_lo, pos_hi, box_lo, box_hi):
+    a, b = _f32(s0), _f32(s1)
+    bl, bh = _f32(box_lo).reshape(-1, 3), _f32(box_hi).reshape(-1, 3)
+    pl, ph = _f32(pos_lo), _f32(pos_hi)
+    return bool(lib().orc_edge_free_dubins_f32(_p(a), _p(b), np.float32(c), np.float32(rho), np.float32(spacing),
+                                               _p(pl), _p(ph), bl.shape[0], _p(bl), _p(bh)))
+
+
 def in_goal(x, gd, c, rho):
     x = _f32(x); c = _f32(c)
     return bool(lib().orc_in_goal(_p(x), gd, _p(c), np.float32(rho)))
@@ -226,11 +282,17 @@ class CSR:
 class Graph:
     """Brute-force r-disk neighbour graph of a sample set (FP32 or FP64)."""
 
-    def __init__(self, kind, d, dp, X, goal, r, precision=32):
+    def __init__(self, kind, d, dp, X, goal, r, precision=32, rho=0.0):
         X = _f32(X)
         self.kind, self.d, self.dp, self.N, self.r, self.precision = kind, d, dp, X.shape[1], float(np.float32(r)), precision
         self.X, self.goal = X, np.ascontiguousarray(goal, dtype=np.uint8)
-        self._h = lib().orc_graph_build(precision, kind, d, dp, self.N, _p(X), _p(self.goal), np.float32(r))
+        if kind == DUBINS:
+            if (d, dp) != (4, 3) or not rho > 0:
+                raise ValueError("Dubins airplane graphs need d = 4, dp = 3 and a turning radius > 0")
+            self._h = lib().orc_graph_build_dubins(precision, self.N, _p(X), _p(self.goal), np.float32(r),
+                                                   np.float32(rho))
+        else:
+            self._h = lib().orc_graph_build(precision, kind, d, dp, self.N, _p(X), _p(self.goal), np.float32(r))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -294,13 +356,15 @@ class Graph:
 def count_edges_rows(problem, X, row0, row1):
     """Edges leaving nodes row0..row1-1 (a slice of the neighbour-set build)."""
     X = _f32(X)
+    if problem.kind == DUBINS:
+        raise ValueError("count_edges_rows covers the Euclidean and double-integrator costs")
     return lib().orc_count_edges_rows(problem.kind, problem.d, X.shape[1], _p(X), np.float32(problem.r), row0, row1)
 
 
 def graph_for(problem, X=None, goal=None, precision=32):
     if X is None:
         X, goal = sample(problem)
-    return Graph(problem.kind, problem.d, problem.dp, X, goal, problem.r, precision)
+    return Graph(problem.kind, problem.d, problem.dp, X, goal, problem.r, precision, rho=getattr(problem, "rho", 0.0))
 
 
 def plan_problem(problem, X=None, goal=None, precision=32, **kw):

@@ -18,7 +18,7 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-EUCLID, DI = 0, 1
+EUCLID, DI, DUBINS = 0, 1, 2
 HERE = os.path.dirname(os.path.abspath(__file__))
 CONFIG_DIR = os.path.join(HERE, "configs")
 
@@ -26,7 +26,7 @@ CONFIG_DIR = os.path.join(HERE, "configs")
 @dataclass
 class Problem:
     """One planning query (Problem 1 of the paper plus Alg. 1's inputs)."""
-    kind: int                 # EUCLID (arc length) or DI (double integrator time + effort)
+    kind: int                 # EUCLID (arc length), DI (double integrator time + effort) or DUBINS (airplane path length)
     d: int                    # state dimension
     dp: int                   # position dimension (obstacles live here)
     lo: np.ndarray            # [d] state lower bounds
@@ -47,6 +47,7 @@ class Problem:
     mu_free: float = 1.0      # Lebesgue measure bound used by Theorem 1 (only when r == 0)
     tag: str = ""
     sampler: int = 0          # 0: Philox i.i.d. uniform; 1: Halton sequence (seed unused)
+    rho: float = 0.0          # Dubins airplane turning radius (DUBINS only)
 
     @property
     def N(self) -> int:
@@ -229,3 +230,18 @@ def di6_scaled(seed: int, n: int, nbox: int = 300, lam: float = 0.5, boxes=None)
     else:
         bl, bh = boxes
     return pb.with_(box_lo=bl, box_hi=bh, tag=f"di6_n{n}_b{bl.shape[0]}")
+
+
+def dubins_forest(seed: int, n: int = 5000, trunks: int = 10, strips: int = 15, rho: float = 0.05,
+                  r: float = 0.2, lam: float = 1.0, sampler: int = 0) -> Problem:
+    """Dubins airplane in a forest (the Sec. V-B forest analogue): state
+    (x, y, z, heading), position in the unit cube, heading in [-pi, pi];
+    obstacles: forest_boxes(seed, trunks, strips) (full-height trunks); x_init
+    at (0.05, 0.05, 0.2) heading 0; goal = position ball radius 0.05 at
+    (0.95, 0.95, 0.8); turning radius rho; lambda = 1 as in Sec. V."""
+    bl, bh = forest_boxes(seed, trunks, strips) if trunks > 0 else (_f32(np.zeros((0, 3))), _f32(np.zeros((0, 3))))
+    pi = float(np.float32(np.pi))
+    return Problem(kind=DUBINS, d=4, dp=3, lo=_f32([0, 0, 0, -pi]), hi=_f32([1, 1, 1, pi]), box_lo=bl, box_hi=bh,
+                   x_init=_f32([0.05, 0.05, 0.2, 0.0]), goal_center=_f32([0.95, 0.95, 0.8, 0.0]), goal_radius=0.05,
+                   goal_pos_only=True, n=n, r=float(np.float32(r)), lam=lam, seed=seed, sampler=sampler,
+                   rho=float(np.float32(rho)), tag=f"dubins_forest_n{n}_b{bl.shape[0]}")
