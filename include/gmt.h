@@ -50,7 +50,7 @@ typedef enum {
     GMT_ERR_ADMISSION = -6    /* serving: request refused (no slot or memory) */
 } gmt_status;
 
-enum { GMT_COST_EUCLID = 0, GMT_COST_DI = 1 };
+enum { GMT_COST_EUCLID = 0, GMT_COST_DI = 1, GMT_COST_DUBINS = 2 };
 #define GMT_MAX_DIM 10
 
 /* State space X = prod_a [lo[a], hi[a]] (Section II).
@@ -58,7 +58,15 @@ enum { GMT_COST_EUCLID = 0, GMT_COST_DI = 1 };
  *   (Section II), dim in [2, GMT_MAX_DIM], pos_dim == dim.
  * kind GMT_COST_DI: 3D double integrator xdd = u (Section V-A), dim == 6,
  *   pos_dim == 3, state [p0 p1 p2 v0 v1 v2], cost = arrival time + integral of
- *   u^T u (the "mixed time/quadratic control effort" cost of Section V-A). */
+ *   u^T u (the "mixed time/quadratic control effort" cost of Section V-A).
+ * kind GMT_COST_DUBINS: Dubins airplane (Section V-A: a planar Dubins car of
+ *   turning radius gmt_params.turn_radius with a single integrator in
+ *   altitude), dim == 4, pos_dim == 3, state [x y z heading]; the trajectory
+ *   is the shortest planar Dubins path with altitude linear in its arc length
+ *   and the cost is its Euclidean length sqrt(L^2 + dz^2).  Pairs whose squared
+ *   3D distance is at least (1 + 2^-6) r^2 are never connected (the cost is at
+ *   least that distance).  An end turn of a word that computes within 2^-13
+ *   rad of a full circle counts as the small negative turn it differs by. */
 typedef struct {
     int32_t kind;
     int32_t dim;
@@ -91,7 +99,8 @@ typedef struct {
     float lambda;         /* group cost threshold factor, in [0, 1]; delta = fl(lambda*r);
                              0 = the FMT* limit (each group = the open nodes of minimum cost) */
     uint64_t seed;        /* Philox4x32-10 key of SampleFree */
-    float seg_spacing;    /* geometric edges: collision points every seg_spacing along the segment */
+    float seg_spacing;    /* geometric and Dubins airplane edges: a cost-c edge is checked at
+                             max(2, ceil(c / seg_spacing) + 1) equally spaced points */
     int32_t traj_points;  /* double integrator edges: collision points along the trajectory (>= 2) */
     int32_t max_iters;    /* cap on group expansions; <= 0 means N + 1 */
     int32_t max_attempts; /* rejection-sampling attempts per node; <= 0 means 65536 */
@@ -100,6 +109,8 @@ typedef struct {
     int32_t spin_limit;   /* polls of a device-side wait before GMT_ERR_TIMEOUT; <= 0 = default */
     uint32_t debug_flags; /* GMT_DEBUG_*: test hooks, 0 in normal use */
     int32_t sampler;      /* GMT_SAMPLER_*: how SampleFree draws its n samples */
+    float turn_radius;    /* GMT_COST_DUBINS: turning radius rho (> 0); such graphs
+                             need r > 0 (Theorem 1's radius is for the geometric cost) */
 } gmt_params;
 
 /* SampleFree variants.
@@ -139,7 +150,7 @@ typedef struct gmt_graph gmt_graph;
  * the release of, the handle).  Samples are SoA: coordinate a of node v is
  * X[a * x_pitch + v].  Out-rows list targets in ascending order; in-rows list
  * sources in ascending order.  For GMT_COST_EUCLID the cost is symmetric and
- * the in-arrays alias the out-arrays. */
+ * the in-arrays alias the out-arrays; the other kinds have their own in-CSR. */
 typedef struct {
     int32_t kind, dim, pos_dim, N;
     int32_t x_pitch;
@@ -156,6 +167,7 @@ typedef struct {
     const float* out_tau;    /* [E] double integrator: arrival time of the out-edge; NULL otherwise */
     const float* in_tau;     /* [E] double integrator: arrival time of the in-edge; NULL otherwise
                                 (gmt_plan_static recomputes it when NULL) */
+    float turn_radius;       /* Dubins airplane: the turning radius the costs were built with; 0 otherwise */
 } gmt_graph_view;
 
 /* SampleFree and neighbour-set construction (Section III-B; the offline

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(PKG, "libgmt.so")
 
 GMT_OK, GMT_NO_PATH = 0, 1
 GMT_ERR_INVALID, GMT_ERR_OOM, GMT_ERR_CUDA, GMT_ERR_TIMEOUT, GMT_ERR_ITER_LIMIT, GMT_ERR_ADMISSION = -1, -2, -3, -4, -5, -6
-GMT_COST_EUCLID, GMT_COST_DI = 0, 1
+GMT_COST_EUCLID, GMT_COST_DI, GMT_COST_DUBINS = 0, 1, 2
 GMT_MAX_DIM = 10
 GMT_DEBUG_UNREACHABLE_BARRIER = 0x1
 GMT_DEBUG_PAIRS_ALL, GMT_DEBUG_PAIRS_CELLS, GMT_DEBUG_CELLS_LIST = 0x2, 0x4, 0x8
@@ -49,7 +49,8 @@ class gmt_params(C.Structure):
     _fields_ = [("n", C.c_int32), ("r", C.c_float), ("lambda_", C.c_float), ("seed", C.c_uint64),
                 ("seg_spacing", C.c_float), ("traj_points", C.c_int32), ("max_iters", C.c_int32),
                 ("max_attempts", C.c_int32), ("eta", C.c_float), ("mu_free", C.c_float),
-                ("spin_limit", C.c_int32), ("debug_flags", C.c_uint32), ("sampler", C.c_int32)]
+                ("spin_limit", C.c_int32), ("debug_flags", C.c_uint32), ("sampler", C.c_int32),
+                ("turn_radius", C.c_float)]
 
 
 class gmt_graph_view(C.Structure):
@@ -58,7 +59,7 @@ class gmt_graph_view(C.Structure):
                 ("X", C.c_void_p), ("is_goal", C.c_void_p),
                 ("out_row", C.c_void_p), ("out_col", C.c_void_p), ("out_cost", C.c_void_p),
                 ("in_row", C.c_void_p), ("in_col", C.c_void_p), ("in_cost", C.c_void_p),
-                ("out_tau", C.c_void_p), ("in_tau", C.c_void_p)]
+                ("out_tau", C.c_void_p), ("in_tau", C.c_void_p), ("turn_radius", C.c_float)]
 
 
 class gmt_plan_info(C.Structure):

@@ -372,7 +372,7 @@ gmt_status check_query(const gmt_query& Qh, int k) {
     } else if (sp.kind == GMT_COST_DI) {
         if (sp.dim != 6 || sp.pos_dim != 3) return bfail(GMT_ERR_INVALID, "double integrator needs dim 6, pos_dim 3" + at);
     } else {
-        return bfail(GMT_ERR_INVALID, "unknown cost kind" + at);
+        return bfail(GMT_ERR_INVALID, "batched queries are geometric or double integrator" + at);
     }
     for (int a = 0; a < sp.dim; ++a)
         if (!(sp.lo[a] < sp.hi[a])) return bfail(GMT_ERR_INVALID, "state bounds need lo < hi" + at);

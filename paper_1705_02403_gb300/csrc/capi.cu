@@ -60,6 +60,7 @@ struct gmt_graph {
     int kind = 0, d = 0, dp = 0, N = 0, pitch = 0;
     long long E = 0;
     float r = 0.0f;
+    float rho = 0.0f;   // Dubins airplane turning radius the costs were built with
     float pos_lo[3] = {0, 0, 0}, pos_hi[3] = {0, 0, 0};
     int plan_blocks = 0, plan_threads = 0, plan_cluster = 0;   // 0 = automatic
     int auto_cluster = -1;                                     // probed once
@@ -115,9 +116,12 @@ struct gmt_graph {
         return cudaEventRecord(ev[stage][which], st);
     }
 
-    const int* in_row() const { return kind == GMT_COST_DI ? in_row_own : out_row; }
-    const int* in_col() const { return kind == GMT_COST_DI ? in_col_own : out_col; }
-    const float* in_cost() const { return kind == GMT_COST_DI ? in_cost_own : out_cost; }
+    // costs that are not symmetric (double integrator, Dubins airplane) keep
+    // their own in-CSR
+    bool directed() const { return kind != GMT_COST_EUCLID; }
+    const int* in_row() const { return directed() ? in_row_own : out_row; }
+    const int* in_col() const { return directed() ? in_col_own : out_col; }
+    const float* in_cost() const { return directed() ? in_cost_own : out_cost; }
 
     ~gmt_graph() {
         void* dev[] = {X, is_goal, out_row, in_row_own, out_count, in_count, out_col, out_cost, in_col_own,
@@ -144,6 +148,9 @@ gmt_status check_space(const gmt_space* sp) {
     } else if (sp->kind == GMT_COST_DI) {
         if (sp->dim != 6 || sp->pos_dim != 3)
             return fail(GMT_ERR_INVALID, "double-integrator space needs dim == 6, pos_dim == 3");
+    } else if (sp->kind == GMT_COST_DUBINS) {
+        if (sp->dim != 4 || sp->pos_dim != 3)
+            return fail(GMT_ERR_INVALID, "Dubins airplane space needs dim == 4, pos_dim == 3");
     } else {
         return fail(GMT_ERR_INVALID, "unknown cost kind");
     }
@@ -243,10 +250,13 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     if (extra_count < 0 || (extra_count > 0 && (!extra || extra_pitch < extra_count)))
         return fail(GMT_ERR_INVALID, "extra samples need a DEVICE array [dim][extra_pitch], extra_pitch >= count");
     if (extra_count > 0 && space && space->kind == GMT_COST_EUCLID && space->dim > 3)
-        return fail(GMT_ERR_INVALID, "appended samples are supported for dim <= 3 and the double integrator");
+        return fail(GMT_ERR_INVALID, "appended samples are supported for dim <= 3 and the kinodynamic spaces");
     if ((s = check_space(space)) != GMT_OK) return s;
     if ((s = check_boxes(boxes)) != GMT_OK) return s;
     if ((s = check_params(params, space->dim)) != GMT_OK) return s;
+    if (space->kind == GMT_COST_DUBINS &&
+        (!(params->turn_radius > 0.0f) || !std::isfinite(params->turn_radius) || !(params->r > 0.0f)))
+        return fail(GMT_ERR_INVALID, "a Dubins airplane graph needs turn_radius > 0 and r > 0");
     if (!x_init || !goal || !graph) return fail(GMT_ERR_INVALID, "x_init, goal and graph must be non-NULL");
     if (!(goal->radius >= 0.0f)) return fail(GMT_ERR_INVALID, "goal radius must be >= 0");
     cudaStream_t st = (cudaStream_t)stream;
@@ -265,6 +275,7 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     g->N = n_sampled + extra_count;
     g->pitch = (g->N + 31) / 32 * 32;
     g->r = resolve_radius(params, space->dim);
+    g->rho = space->kind == GMT_COST_DUBINS ? params->turn_radius : 0.0f;
     g->E = 0;
     for (int a = 0; a < 3 && a < g->dp; ++a) { g->pos_lo[a] = space->lo[a]; g->pos_hi[a] = space->hi[a]; }
     const size_t N = (size_t)g->N, P = (size_t)g->pitch, W = (N + 31) / 32;
@@ -287,6 +298,7 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     sa.halton_cap = (long long)sa.max_attempts + 64LL * n_sampled;
     sa.r = g->r;
     sa.r2_threshold = euclid_threshold(g->r);
+    sa.rho = g->rho;
     BoxArgs ba{boxes->count, boxes->lo, boxes->hi};
 
     cudaError_t e;
@@ -300,7 +312,7 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     GROW(stamp, N);
     GROW(lists, kPlanListInts * N);
     GROW(ctl, 1);
-    if (g->kind == GMT_COST_DI) {
+    if (g->directed()) {
         GROW(in_row_own, N + 1);
         GROW(in_count, N);
         GROW(maskT, W * P);
@@ -314,7 +326,7 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     for (bool& b : g->stage_ran) b = false;
     LAUNCH(cudaMemsetAsync(g->flags, 0, 4 * sizeof(int), st), "memset");
     LAUNCH(cudaMemsetAsync(g->out_count, 0, N * sizeof(int), st), "memset");
-    if (g->kind == GMT_COST_DI) LAUNCH(cudaMemsetAsync(g->in_count, 0, N * sizeof(int), st), "memset");
+    if (g->directed()) LAUNCH(cudaMemsetAsync(g->in_count, 0, N * sizeof(int), st), "memset");
     LAUNCH(g->mark(gmt_graph::kSample, 0, st), "event");
     BoxGridArgs grid;
     LAUNCH(build_box_grid(g, ba, &grid, st), "box grid kernels");
@@ -349,14 +361,14 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
         LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, st), "pair filter kernel");
     }
     LAUNCH(g->mark(gmt_graph::kPair, 1, st), "event");
-    if (g->kind == GMT_COST_DI) {
+    if (g->directed()) {
         LAUNCH(g->mark(gmt_graph::kTranspose, 0, st), "event");
         LAUNCH(launch_transpose(sa, g->mask, g->maskT, g->in_count, st), "transpose kernel");
         LAUNCH(g->mark(gmt_graph::kTranspose, 1, st), "event");
     }
     LAUNCH(g->mark(gmt_graph::kScan, 0, st), "event");
     LAUNCH(launch_scan(g->out_count, g->out_row, g->N, st), "scan kernel");
-    if (g->kind == GMT_COST_DI) LAUNCH(launch_scan(g->in_count, g->in_row_own, g->N, st), "scan kernel");
+    if (g->directed()) LAUNCH(launch_scan(g->in_count, g->in_row_own, g->N, st), "scan kernel");
     LAUNCH(g->mark(gmt_graph::kScan, 1, st), "event");
     LAUNCH(cudaMemcpyAsync(g->h_scalars, g->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
     LAUNCH(cudaMemcpyAsync(g->h_scalars + 2, g->out_row + N, sizeof(int), cudaMemcpyDeviceToHost, st),
@@ -383,10 +395,12 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     const size_t E = (size_t)g->E;
     GROW(out_col, E);
     GROW(out_cost, E);
-    const bool di = g->kind == GMT_COST_DI;
-    if (di) {
+    const bool di = g->kind == GMT_COST_DI, directed = g->directed();
+    if (directed) {
         GROW(in_col_own, E);
         GROW(in_cost_own, E);
+    }
+    if (di) {
         GROW(out_tau, E);
         GROW(in_tau, E);
     }
@@ -397,8 +411,9 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
                "cell row kernel");
     } else {
         const FillDir out_dir{g->mask, g->out_row, g->out_col, g->out_cost, di ? g->out_tau : nullptr};
-        const FillDir in_dir = di ? FillDir{g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own, g->in_tau}
-                                  : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr};
+        const FillDir in_dir = directed ? FillDir{g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own,
+                                                  di ? g->in_tau : nullptr}
+                                        : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr};
         LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, st), "fill kernel");
     }
     LAUNCH(g->mark(gmt_graph::kFill, 1, st), "event");
@@ -417,6 +432,7 @@ gmt_status gmt_graph_get_view(const gmt_graph* g, gmt_graph_view* v) {
     v->in_row = g->in_row(); v->in_col = g->in_col(); v->in_cost = g->in_cost();
     v->out_tau = g->kind == GMT_COST_DI ? g->out_tau : nullptr;
     v->in_tau = g->kind == GMT_COST_DI ? g->in_tau : nullptr;
+    v->turn_radius = g->rho;
     return GMT_OK;
 }
 
@@ -443,6 +459,7 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
     a.r = g->r;
     a.delta = params->lambda * g->r;
     a.seg_spacing = params->seg_spacing;
+    a.rho = g->rho;
     a.traj_points = params->traj_points;
     a.max_iters = params->max_iters > 0 ? params->max_iters : N + 1;
     a.spin_limit = params->spin_limit;

@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dubins.cuh"
 #include "gmt.h"
 #include "internal.h"
 

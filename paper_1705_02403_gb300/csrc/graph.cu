@@ -12,6 +12,8 @@
 //   pair_mask_di_kernel  the same for the double integrator: three
 //                     conservative tests of increasing cost, then the exact
 //                     root procedure, with per-warp compaction between stages
+//   pair_mask_dubins_kernel  the same for the Dubins airplane: distance
+//                     prefilter, then the shortest-word cost from a queue
 //   fill_kernel       one warp per row: prefix over the row's words, column
 //                     list in shared memory, one edge cost per lane; out- and
 //                     in-rows in one launch
@@ -71,6 +73,12 @@ __global__ void __launch_bounds__(kDIRows, 8) pair_mask_di_kernel(SpaceArgs s, c
     mask_di_tile(s, X, mask, out_count, blockIdx.x, blockIdx.y);
 }
 
+__global__ void __launch_bounds__(kDubRows) pair_mask_dubins_kernel(SpaceArgs s, const float* __restrict__ X,
+                                                                  uint32_t* __restrict__ mask,
+                                                                  int* __restrict__ out_count) {
+    mask_dubins_tile(s, X, mask, out_count, blockIdx.x, blockIdx.y);
+}
+
 __global__ void __launch_bounds__(256) transpose_kernel(int N, int pitch, const uint32_t* __restrict__ mask,
                                                         uint32_t* __restrict__ maskT, int* __restrict__ in_count) {
     transpose_task(N, pitch, mask, maskT, in_count, ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32);
@@ -80,7 +88,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ coun
     scan_rows(count, row, N);
 }
 
-// blockIdx.y = 0: out-rows; 1: in-rows (double integrator).
+// blockIdx.y = 0: out-rows; 1: in-rows (double integrator, Dubins airplane).
 template <int KIND, int D>
 __global__ void __launch_bounds__(kFillWarps * 32) fill_kernel(SpaceArgs s, const float* __restrict__ X, FillDir out,
                                                                FillDir in) {
@@ -136,6 +144,7 @@ cudaError_t fill_t(const SpaceArgs& s, const float* X, const FillDir& out, const
 cudaError_t launch_sample(const SpaceArgs& s, BoxArgs b, const BoxGridArgs& grid, float* X, uint8_t* g, int* f,
                           cudaStream_t st) {
     if (s.kind == GMT_COST_DI) return sample_t<6, 3>(s, b, grid, X, g, f, st);
+    if (s.kind == GMT_COST_DUBINS) return sample_t<4, 3>(s, b, grid, X, g, f, st);
     switch (s.d) {
         case 2: return sample_t<2, 2>(s, b, grid, X, g, f, st);
         case 3: return sample_t<3, 3>(s, b, grid, X, g, f, st);
@@ -155,6 +164,8 @@ cudaError_t launch_append(const SpaceArgs& s, BoxArgs b, const float* src, int s
     if (count <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((count + 127) / 128);
     if (s.kind == GMT_COST_DI) append_kernel<6, 3><<<blocks, 128, 0, st>>>(s, b, src, src_pitch, first, count, X, g, f);
+    else if (s.kind == GMT_COST_DUBINS)
+        append_kernel<4, 3><<<blocks, 128, 0, st>>>(s, b, src, src_pitch, first, count, X, g, f);
     else if (s.d == 2) append_kernel<2, 2><<<blocks, 128, 0, st>>>(s, b, src, src_pitch, first, count, X, g, f);
     else if (s.d == 3) append_kernel<3, 3><<<blocks, 128, 0, st>>>(s, b, src, src_pitch, first, count, X, g, f);
     else return cudaErrorInvalidValue;
@@ -166,6 +177,12 @@ cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask,
         const int W = (s.N + 31) / 32;
         dim3 grid((s.N + kDIRows - 1) / kDIRows, (W + kDIWords - 1) / kDIWords);
         pair_mask_di_kernel<<<grid, kDIRows, 0, st>>>(s, X, mask, cnt);
+        return cudaGetLastError();
+    }
+    if (s.kind == GMT_COST_DUBINS) {
+        const int W = (s.N + 31) / 32;
+        dim3 grid((s.N + kDubRows - 1) / kDubRows, (W + kDubWords - 1) / kDubWords);
+        pair_mask_dubins_kernel<<<grid, kDubRows, 0, st>>>(s, X, mask, cnt);
         return cudaGetLastError();
     }
     GMT_EUCLID_DIMS(mask_t, s, X, mask, cnt, st)
@@ -186,6 +203,7 @@ cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st) {
 
 cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, cudaStream_t st) {
     if (s.kind == GMT_COST_DI) return fill_t<GMT_COST_DI, 6>(s, X, out, in, st);
+    if (s.kind == GMT_COST_DUBINS) return fill_t<GMT_COST_DUBINS, 4>(s, X, out, in, st);
     GMT_EUCLID_DIMS(fill_t, s, X, out, in, st)
 }
 

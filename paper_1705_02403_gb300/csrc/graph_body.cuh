@@ -201,6 +201,7 @@ constexpr int kMaskWords = 8;      // 32-column words per block (256 columns sta
 template <int KIND, int D>
 __device__ __forceinline__ bool connects(const SpaceArgs& s, const float* from, const float* to) {
     if (KIND == GMT_COST_EUCLID) return sq_dist<D>(from, to) < s.r2_threshold;
+    if (KIND == GMT_COST_DUBINS) return dubins_near(from, to, s.r) && dubins_cost(from, to, s.rho) < s.r;
     if (!di_may_connect(from, to, s.r)) return false;
     return di_cost(from, to, s.r) < s.r;
 }
@@ -208,6 +209,7 @@ __device__ __forceinline__ bool connects(const SpaceArgs& s, const float* from, 
 template <int KIND, int D>
 __device__ __forceinline__ float edge_cost(const SpaceArgs& s, const float* from, const float* to) {
     if (KIND == GMT_COST_EUCLID) return __fsqrt_rn(sq_dist<D>(from, to));
+    if (KIND == GMT_COST_DUBINS) return dubins_cost(from, to, s.rho);
     return di_cost(from, to, s.r);
 }
 
@@ -374,6 +376,80 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
 #pragma unroll
     for (int ww = 0; ww < kDIWords; ++ww) {
         const int w = w0 + ww;
+        if (w >= W) break;
+        const uint32_t bits = words[warp][ww][lane];
+        mask[(size_t)w * s.pitch + i] = bits;
+        cnt += __popc(bits);
+    }
+    if (cnt) atomicAdd(&out_count[i], cnt);
+}
+
+// Dubins airplane pair filter: the 3D-distance prefilter for every pair, then
+// the shortest-word cost for the ~3% that pass, 32 at a time from a per-warp
+// queue (entry (row lane << 8) | column) so that every lane computes one.
+constexpr int kDubRows = 128;  // rows (threads) per block
+constexpr int kDubWords = 1;   // 32-column words per block
+
+__device__ __forceinline__ void mask_dubins_tile(const SpaceArgs& s, const float* __restrict__ X,
+                                                 uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
+                                                 int by) {
+    __shared__ float tile[4][kDubWords * 32];
+    __shared__ uint32_t words[kDubRows / 32][kDubWords][32];
+    __shared__ uint16_t queue[kDubRows / 32][64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = bx * kDubRows + threadIdx.x;
+    const int j0 = by * kDubWords * 32;
+    for (int idx = threadIdx.x; idx < kDubWords * 32; idx += kDubRows) {
+        const int j = j0 + idx;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) tile[a][idx] = j < s.N ? X[(size_t)a * s.pitch + j] : 0.0f;
+    }
+#pragma unroll
+    for (int ww = 0; ww < kDubWords; ++ww) words[warp][ww][lane] = 0u;
+    __syncthreads();
+    const bool row_ok = i < s.N;
+    float xi[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) xi[a] = row_ok ? X[(size_t)a * s.pitch + i] : 0.0f;
+    int qn = 0;
+    auto drain = [&](int count) {
+        const int e = lane < count ? queue[warp][lane] : 0;
+        const int src = e >> 8, jt = e & 255;
+        float a_[4], b_[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            a_[a] = __shfl_sync(0xffffffffu, xi[a], src);
+            b_[a] = tile[a][jt];
+        }
+        if (lane < count && dubins_cost(a_, b_, s.rho) < s.r) atomicOr(&words[warp][jt >> 5][src], 1u << (jt & 31));
+    };
+    const int jend = min(kDubWords * 32, s.N - j0);
+    for (int jt = 0; jt < jend; ++jt) {
+        const int j = j0 + jt;
+        float b_[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) b_[a] = tile[a][jt];
+        const bool pass = row_ok && j != i && dubins_near(xi, b_, s.r);
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        if (pass) queue[warp][qn + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((lane << 8) | jt);
+        __syncwarp();
+        qn += __popc(m);
+        if (qn >= 32) {
+            drain(32);
+            __syncwarp();
+            if (lane < qn - 32) queue[warp][lane] = queue[warp][32 + lane];
+            __syncwarp();
+            qn -= 32;
+        }
+    }
+    if (qn > 0) drain(qn);
+    __syncwarp();
+    if (!row_ok) return;
+    const int W = (s.N + 31) / 32;
+    int cnt = 0;
+#pragma unroll
+    for (int ww = 0; ww < kDubWords; ++ww) {
+        const int w = by * kDubWords + ww;
         if (w >= W) break;
         const uint32_t bits = words[warp][ww][lane];
         mask[(size_t)w * s.pitch + i] = bits;

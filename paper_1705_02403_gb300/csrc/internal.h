@@ -26,6 +26,7 @@ struct SpaceArgs {
     int max_attempts;
     float r;
     float r2_threshold;  // Euclidean: edge iff squared distance < r2_threshold (== sqrt(s) < r)
+    float rho;           // Dubins airplane: turning radius
     int sampler;         // GMT_SAMPLER_PHILOX or GMT_SAMPLER_HALTON
     long long halton_cap;  // Halton points tried per sequence
 };
@@ -169,6 +170,7 @@ struct PlanArgs {
     BoxGridArgs grid;  // use = 0 unless the plan built one
     float pos_lo[3], pos_hi[3];
     float r, delta, seg_spacing;
+    float rho;            // Dubins airplane: turning radius
     int traj_points, max_iters, spin_limit;
     unsigned debug_flags;
     float* cost;

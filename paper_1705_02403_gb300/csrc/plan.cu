@@ -41,7 +41,7 @@ namespace gmtk {
 // ------------------------------------------------------------------- kernel
 template <class Team, int KIND, int DP>
 __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
-    constexpr int D = KIND == GMT_COST_DI ? 6 : DP;
+    constexpr int D = KIND == GMT_COST_DI ? 6 : (KIND == GMT_COST_DUBINS ? 4 : DP);
     const int nbs = A.boxes.count <= smem_box_cap(DP) ? A.boxes.count : 0;
     for (int t = threadIdx.x; t < nbs * DP; t += blockDim.x) {
         sbox[t] = A.boxes.lo[t];
@@ -219,6 +219,9 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
                     if (KIND == GMT_COST_EUCLID)
                         free_edge = segment_free_warp<DP>(sy, sx, __ldg(&A.in_cost[be]), A.seg_spacing, blo, bhi,
                                                           nbox, A.grid);
+                    else if (KIND == GMT_COST_DUBINS)
+                        free_edge = dubins_free_warp(sy, sx, __ldg(&A.in_cost[be]), A.seg_spacing, A.rho, A.pos_lo,
+                                                     A.pos_hi, blo, bhi, nbox, A.grid);
                     else {
                         // arrival time of the edge: stored by the graph build, or recomputed
                         const float tau = A.in_tau ? __ldg(&A.in_tau[be]) : di_tau(di_coef(sy, sx), A.r);
@@ -412,6 +415,7 @@ int occupancy_t(int threads) {
 
 cudaError_t launch_plan(const PlanArgs& a, int blocks, int threads, cudaStream_t st, int cluster) {
     if (a.kind == GMT_COST_DI) return plan_t<GMT_COST_DI, 3>(a, blocks, threads, cluster, st);
+    if (a.kind == GMT_COST_DUBINS) return plan_t<GMT_COST_DUBINS, 3>(a, blocks, threads, cluster, st);
     switch (a.dp) {
         case 2: return plan_t<GMT_COST_EUCLID, 2>(a, blocks, threads, cluster, st);
         case 3: return plan_t<GMT_COST_EUCLID, 3>(a, blocks, threads, cluster, st);
@@ -429,9 +433,10 @@ cudaError_t launch_plan(const PlanArgs& a, int blocks, int threads, cudaStream_t
 // Largest cluster size (16, 8, 4, 2) for which one cluster of `threads`-thread
 // CTAs of the plan kernel can be resident; 0 if none.
 int plan_max_cluster(int kind, int dp, int threads) {
-    auto kern = kind == GMT_COST_DI ? plan_kernel<ClusterTeam, GMT_COST_DI, 3>
-                                    : (dp == 2 ? plan_kernel<ClusterTeam, GMT_COST_EUCLID, 2>
-                                               : plan_kernel<ClusterTeam, GMT_COST_EUCLID, 3>);
+    auto kern = kind == GMT_COST_DI       ? plan_kernel<ClusterTeam, GMT_COST_DI, 3>
+                : kind == GMT_COST_DUBINS ? plan_kernel<ClusterTeam, GMT_COST_DUBINS, 3>
+                : dp == 2                 ? plan_kernel<ClusterTeam, GMT_COST_EUCLID, 2>
+                                          : plan_kernel<ClusterTeam, GMT_COST_EUCLID, 3>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
     for (int c = 16; c >= 2; c /= 2) {
         cudaLaunchConfig_t cfg = {};
@@ -515,10 +520,12 @@ int batch_teams_t(int threads, int cluster) {
 }
 }  // namespace
 
-// The batched path supports the double integrator and 2D/3D geometric queries.
+// The batched path supports the double integrator and 2D/3D geometric queries
+// (not the Dubins airplane).
 cudaError_t launch_plan_batch(int kind, int dp, const PlanArgs* queries, const int* order, int nq, int* next,
                               int* slot, const BatchScratch& scratch, int teams, int threads, int cluster,
                               int max_boxes, cudaStream_t st) {
+    if (kind == GMT_COST_DUBINS) return cudaErrorInvalidValue;
     if (kind == GMT_COST_DI)
         return plan_batch_t<GMT_COST_DI, 3>(queries, order, nq, next, slot, scratch, teams, threads, cluster, max_boxes, st);
     if (dp == 2)
@@ -531,6 +538,7 @@ cudaError_t launch_plan_batch(int kind, int dp, const PlanArgs* queries, const i
 }
 
 int plan_batch_max_teams(int kind, int dp, int threads, int cluster) {
+    if (kind == GMT_COST_DUBINS) return 0;
     if (kind == GMT_COST_DI) return batch_teams_t<GMT_COST_DI, 3>(threads, cluster);
     if (dp == 2) return batch_teams_t<GMT_COST_EUCLID, 2>(threads, cluster);
     if (dp == 3) return batch_teams_t<GMT_COST_EUCLID, 3>(threads, cluster);
@@ -539,6 +547,7 @@ int plan_batch_max_teams(int kind, int dp, int threads, int cluster) {
 
 int plan_max_coresident_blocks(int kind, int dp, int threads) {
     if (kind == GMT_COST_DI) return occupancy_t<GMT_COST_DI, 3>(threads);
+    if (kind == GMT_COST_DUBINS) return occupancy_t<GMT_COST_DUBINS, 3>(threads);
     switch (dp) {
         case 2: return occupancy_t<GMT_COST_EUCLID, 2>(threads);
         case 3: return occupancy_t<GMT_COST_EUCLID, 3>(threads);

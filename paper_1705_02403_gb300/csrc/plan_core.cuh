@@ -213,6 +213,59 @@ __device__ __forceinline__ bool trajectory_free_warp(const float* y, const float
     return true;
 }
 
+// Dubins airplane edge y -> x of cost c: m = max(2, ceil(c / spacing) + 1)
+// trajectory points at fractions k / (m - 1); a point in a box or outside the
+// position bounds collides.  Every lane computes the (same) shortest word and
+// then its own points.  Without the box grid, boxes are first tested against
+// a bound of the whole trajectory: its planar part stays within c/2 of the
+// midpoint of y and x (a point at arc length l is within l of y and L - l of x,
+// L <= c), its altitude between the two end altitudes.
+__device__ __forceinline__ bool dubins_free_warp(const float* y, const float* x, float c, float spacing, float rho,
+                                                 const float* plo, const float* phi, const float* blo,
+                                                 const float* bhi, int nbox, const BoxGridArgs& grid) {
+    const int lane = threadIdx.x & 31;
+    const DubPath P = dubins_path(y, x, rho);
+    int m = (int)ceilf(c / spacing) + 1;
+    if (m < 2) m = 2;
+    const float denom = (float)(m - 1);
+    float lo[3], hi[3];
+    unsigned near_first = 0;
+    if (!grid.use) {
+        const float e = 1e-3f * c + 1e-5f * (fabsf(y[0]) + fabsf(y[1]) + fabsf(y[2]) + rho) + 1e-30f;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const float mid = 0.5f * (y[a] + x[a]);
+            lo[a] = mid - 0.5f * c - e;
+            hi[a] = mid + 0.5f * c + e;
+        }
+        lo[2] = fminf(y[2], x[2]) - e;
+        hi[2] = fmaxf(y[2], x[2]) + e;
+        if (nbox > 0) near_first = __ballot_sync(0xffffffffu, lane < nbox && box_meets<3>(blo, bhi, lane, lo, hi));
+    }
+    for (int k0 = 0; k0 < m; k0 += 32) {
+        const int k = k0 + lane;
+        bool hit = false;
+        float p[3];
+        if (k < m) {
+            dubins_point(y, x, P, rho, (float)k / denom, p);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) hit = hit || p[a] < plo[a] || p[a] > phi[a];
+            if (grid.use && !hit) hit = in_any_box_grid<3>(p, blo, bhi, grid);
+        }
+        if (!grid.use) {
+            for (int b0 = 0; b0 < nbox; b0 += 32) {
+                const unsigned near =
+                    b0 == 0 ? near_first
+                            : __ballot_sync(0xffffffffu, b0 + lane < nbox && box_meets<3>(blo, bhi, b0 + lane, lo, hi));
+                if (k < m)
+                    for (unsigned w = near; w; w &= w - 1) hit = hit || in_box<3>(p, blo, bhi, b0 + __ffs(w) - 1);
+            }
+        }
+        if (__any_sync(0xffffffffu, hit)) return false;
+    }
+    return true;
+}
+
 // Largest box count staged in shared memory (2 * count * DP floats).
 __host__ __device__ constexpr int smem_box_cap(int dp) { return 4096 / dp; }
 

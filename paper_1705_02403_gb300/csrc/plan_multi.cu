@@ -541,7 +541,7 @@ int lockstep_blocks_t(int threads) {
 
 cudaError_t launch_plan_lockstep(int kind, int dp, const PlanArgs* queries, int nq, const LockScratch& s, int blocks,
                                  int threads, cudaStream_t st) {
-    if (nq < 1 || nq > kLockMaxQueries || blocks < 1) return cudaErrorInvalidValue;
+    if (nq < 1 || nq > kLockMaxQueries || blocks < 1 || kind == GMT_COST_DUBINS) return cudaErrorInvalidValue;
     if (kind == GMT_COST_DI) return lockstep_t<GMT_COST_DI, 3>(queries, nq, s, blocks, threads, st);
     if (dp == 2) return lockstep_t<GMT_COST_EUCLID, 2>(queries, nq, s, blocks, threads, st);
     if (dp == 3) return lockstep_t<GMT_COST_EUCLID, 3>(queries, nq, s, blocks, threads, st);
@@ -549,6 +549,7 @@ cudaError_t launch_plan_lockstep(int kind, int dp, const PlanArgs* queries, int 
 }
 
 int plan_lockstep_max_blocks(int kind, int dp, int threads) {
+    if (kind == GMT_COST_DUBINS) return 0;
     if (kind == GMT_COST_DI) return lockstep_blocks_t<GMT_COST_DI, 3>(threads);
     if (dp == 2) return lockstep_blocks_t<GMT_COST_EUCLID, 2>(threads);
     if (dp == 3) return lockstep_blocks_t<GMT_COST_EUCLID, 3>(threads);

@@ -83,10 +83,12 @@ extern "C" gmt_status gmt_plan_static(const gmt_space* space, const gmt_graph_vi
                                          std::to_string(GMT_STATIC_MAX_NODES));
     if (g->kind != space->kind || g->dim != space->dim || g->pos_dim != space->pos_dim)
         return fail(GMT_ERR_INVALID, "graph view and space disagree on kind or dimensions");
-    if (g->kind != GMT_COST_EUCLID && g->kind != GMT_COST_DI) return fail(GMT_ERR_INVALID, "unknown cost kind");
-    if (g->kind == GMT_COST_DI ? (g->dim != 6 || g->pos_dim != 3)
-                               : (g->dim < 2 || g->dim > GMT_MAX_DIM || g->pos_dim != g->dim))
-        return fail(GMT_ERR_INVALID, "unsupported dimensions");
+    if (g->kind != GMT_COST_EUCLID && g->kind != GMT_COST_DI && g->kind != GMT_COST_DUBINS)
+        return fail(GMT_ERR_INVALID, "unknown cost kind");
+    if (g->kind == GMT_COST_DI       ? (g->dim != 6 || g->pos_dim != 3)
+        : g->kind == GMT_COST_DUBINS ? (g->dim != 4 || g->pos_dim != 3 || !(g->turn_radius > 0.0f))
+                                     : (g->dim < 2 || g->dim > GMT_MAX_DIM || g->pos_dim != g->dim))
+        return fail(GMT_ERR_INVALID, "unsupported dimensions (or a Dubins view without a turning radius)");
     if (g->x_pitch < g->N || g->E < 0 || !g->X || !g->is_goal || !g->out_row || !g->in_row ||
         (g->E > 0 && (!g->out_col || !g->in_col || !g->in_cost)))
         return fail(GMT_ERR_INVALID, "graph view has missing arrays or a bad pitch");
@@ -119,6 +121,7 @@ extern "C" gmt_status gmt_plan_static(const gmt_space* space, const gmt_graph_vi
     a.r = g->r;
     a.delta = params->lambda * g->r;
     a.seg_spacing = params->seg_spacing;
+    a.rho = g->kind == GMT_COST_DUBINS ? g->turn_radius : 0.0f;
     a.traj_points = params->traj_points;
     a.max_iters = params->max_iters > 0 ? params->max_iters : g->N + 1;
     a.spin_limit = params->spin_limit;

@@ -53,6 +53,7 @@ def params_struct(pb: Problem, **over) -> N.gmt_params:
     p.eta, p.mu_free = float(pb.eta), float(pb.mu_free)
     p.spin_limit, p.debug_flags = 0, 0
     p.sampler = int(pb.sampler)
+    p.turn_radius = float(getattr(pb, "rho", 0.0))
     for k, v in over.items():
         setattr(p, k, v)
     return p

@@ -47,7 +47,7 @@ def oracle_run(O, pb, X=None, goal=None, **kw):
     if X is None:
         X, goal = O.sample_halton(pb) if pb.sampler == 1 else O.sample(pb)
     r0 = O.radius_halton(pb.n, pb.d) if pb.sampler == 1 else O.radius_thm1(pb.n, pb.d)
-    g = O.Graph(pb.kind, pb.d, pb.dp, X, goal, pb.r if pb.r > 0 else np.float32(r0))
+    g = O.Graph(pb.kind, pb.d, pb.dp, X, goal, pb.r if pb.r > 0 else np.float32(r0), rho=pb.rho)
     parent, cost, info = g.plan(pb.box_lo, pb.box_hi, pb.lo[:pb.dp], pb.hi[:pb.dp], pb.lam, pb.seg_spacing,
                                 pb.traj_points, **kw)
     return X, goal, g, parent, cost, info
