@@ -168,6 +168,9 @@ typedef struct {
     const float* in_tau;     /* [E] double integrator: arrival time of the in-edge; NULL otherwise
                                 (gmt_plan_static recomputes it when NULL) */
     float turn_radius;       /* Dubins airplane: the turning radius the costs were built with; 0 otherwise */
+    const float* in_path;    /* [E][4] Dubins airplane: the in-edge's shortest planar word as (t, p, q, word),
+                                word = LSL 0, RSR 1, LSR 2, RSL 3, RLR 4, LRL 5 stored as int32 bits;
+                                NULL otherwise (gmt_plan_static recomputes it when NULL) */
 } gmt_graph_view;
 
 /* SampleFree and neighbour-set construction (Section III-B; the offline

@@ -59,7 +59,8 @@ class gmt_graph_view(C.Structure):
                 ("X", C.c_void_p), ("is_goal", C.c_void_p),
                 ("out_row", C.c_void_p), ("out_col", C.c_void_p), ("out_cost", C.c_void_p),
                 ("in_row", C.c_void_p), ("in_col", C.c_void_p), ("in_cost", C.c_void_p),
-                ("out_tau", C.c_void_p), ("in_tau", C.c_void_p), ("turn_radius", C.c_float)]
+                ("out_tau", C.c_void_p), ("in_tau", C.c_void_p), ("turn_radius", C.c_float),
+                ("in_path", C.c_void_p)]
 
 
 class gmt_plan_info(C.Structure):

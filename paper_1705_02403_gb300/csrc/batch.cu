@@ -178,9 +178,10 @@ __global__ void __launch_bounds__(kFillWarps * 32) batch_fill_kernel(const Query
     const int* row = incoming ? q.in_row : q.out_row;
     if ((long long)row[q.s.N] > q.edge_cap) return;
     if (incoming)
-        fill_row<KIND, D, true>(q.s, q.X, q.maskT, q.in_row, q.in_col, q.in_cost, q.in_tau, (int)(w - off[k]));
+        fill_row<KIND, D, true>(q.s, q.X, q.maskT, q.in_row, q.in_col, q.in_cost, q.in_tau, nullptr, (int)(w - off[k]));
     else
-        fill_row<KIND, D, false>(q.s, q.X, q.mask, q.out_row, q.out_col, q.out_cost, q.out_tau, (int)(w - off[k]));
+        fill_row<KIND, D, false>(q.s, q.X, q.mask, q.out_row, q.out_col, q.out_cost, q.out_tau, nullptr,
+                                 (int)(w - off[k]));
 }
 
 namespace {

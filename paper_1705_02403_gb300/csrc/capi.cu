@@ -76,6 +76,7 @@ struct gmt_graph {
     float* in_cost_own = nullptr;  size_t cap_in_cost_own = 0;
     float* out_tau = nullptr;      size_t cap_out_tau = 0;
     float* in_tau = nullptr;       size_t cap_in_tau = 0;
+    float* in_path = nullptr;      size_t cap_in_path = 0;   // Dubins airplane: [E][4] (t, p, q, word bits)
     uint32_t* mask = nullptr;      size_t cap_mask = 0;
     uint32_t* maskT = nullptr;     size_t cap_maskT = 0;
     int* flags = nullptr;          size_t cap_flags = 0;   // [sample flags, max row length, row overflow, -]
@@ -125,7 +126,7 @@ struct gmt_graph {
 
     ~gmt_graph() {
         void* dev[] = {X, is_goal, out_row, in_row_own, out_count, in_count, out_col, out_cost, in_col_own,
-                       in_cost_own, out_tau, in_tau, mask, maskT, flags, cell_of, cell_sorted, cell_cnt,
+                       in_cost_own, out_tau, in_tau, in_path, mask, maskT, flags, cell_of, cell_sorted, cell_cnt,
                        cell_start, grid_cnt, grid_start, grid_list, grid_cell_of, grid_ext, ocost, stamp,
                        lists, ctl};
         for (void* p : dev)
@@ -404,16 +405,18 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
         GROW(out_tau, E);
         GROW(in_tau, E);
     }
+    const bool dubins = g->kind == GMT_COST_DUBINS;
+    if (dubins) GROW(in_path, 4 * E);
     LAUNCH(g->mark(gmt_graph::kFill, 0, st), "event");
     if (cells) {
         LAUNCH(launch_cells_rows(sa, g->X, cg, g->cell_of, g->cell_start, g->cell_sorted, true, nullptr, nullptr,
                                  g->out_row, g->out_col, g->out_cost, g->flags + 2, st),
                "cell row kernel");
     } else {
-        const FillDir out_dir{g->mask, g->out_row, g->out_col, g->out_cost, di ? g->out_tau : nullptr};
+        const FillDir out_dir{g->mask, g->out_row, g->out_col, g->out_cost, di ? g->out_tau : nullptr, nullptr};
         const FillDir in_dir = directed ? FillDir{g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own,
-                                                  di ? g->in_tau : nullptr}
-                                        : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr};
+                                                  di ? g->in_tau : nullptr, dubins ? g->in_path : nullptr}
+                                        : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
         LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, st), "fill kernel");
     }
     LAUNCH(g->mark(gmt_graph::kFill, 1, st), "event");
@@ -433,6 +436,7 @@ gmt_status gmt_graph_get_view(const gmt_graph* g, gmt_graph_view* v) {
     v->out_tau = g->kind == GMT_COST_DI ? g->out_tau : nullptr;
     v->in_tau = g->kind == GMT_COST_DI ? g->in_tau : nullptr;
     v->turn_radius = g->rho;
+    v->in_path = g->kind == GMT_COST_DUBINS ? g->in_path : nullptr;
     return GMT_OK;
 }
 
@@ -455,6 +459,7 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
     a.out_row = g->out_row; a.out_col = g->out_col;
     a.in_row = g->in_row(); a.in_col = g->in_col(); a.in_cost = g->in_cost();
     a.in_tau = g->kind == GMT_COST_DI ? g->in_tau : nullptr;
+    a.in_path = g->kind == GMT_COST_DUBINS ? g->in_path : nullptr;
     a.boxes = BoxArgs{boxes->count, boxes->lo, boxes->hi};
     a.r = g->r;
     a.delta = params->lambda * g->r;

@@ -53,7 +53,7 @@ __device__ __forceinline__ void dub_sincos(float x, float* s, float* c) {
     const float kf = rintf(x * dub::kTwoOverPi);
     const float r = (x - kf * dub::kPi2Hi) - kf * dub::kPi2Lo;
     const float sr = dub_sin_poly(r), cr = dub_cos_poly(r);
-    const int q = (int)((long long)kf & 3);
+    const int q = __float2int_rz(kf) & 3;  // kf is integral and small: its quadrant mod 4
     if (q == 0) { *s = sr; *c = cr; }
     else if (q == 1) { *s = cr; *c = -sr; }
     else if (q == 2) { *s = -sr; *c = -cr; }
@@ -194,42 +194,87 @@ __device__ __forceinline__ float dubins_cost(const float* s0, const float* s1, f
     return dubins_length(dubins_path(s0, s1, rho), s0, s1);
 }
 
-// Position at fraction s of the trajectory: planar arc length s L walked
-// through the word's segments (left turn by a: rho (sin(th + a) - sin th,
-// cos th - cos(th + a)); right turn: rho (sin th - sin(th - a),
-// cos(th - a) - cos th); straight part: l (cos th, sin th)), altitude linear.
-__device__ __forceinline__ void dubins_point(const float* s0, const float* s1, const DubPath& P, float rho, float s,
-                                             float* out) {
-    // segment types by word, 2 bits each (0 L, 1 S, 2 R): LSL RSR LSR RSL RLR LRL
+// Trajectory points.  The pose at fraction s walks planar arc length s L
+// through the word's segments: segment k advances by a_k = min(ell_k, len_k)
+// with ell_0 = s L and ell_{k+1} = ell_k - a_k (a left turn by a from heading
+// th moves by rho (sin(th + a) - sin th, cos th - cos(th + a)), a right turn by
+// rho (sin th - sin(th - a), cos(th - a) - cos th), a straight part by
+// a (cos th, sin th)); the altitude is z0 + s dz.  DubSegs holds the pose at
+// the start of each segment (the segments before it walked in full), so a
+// point costs one partial segment: after it, a segment of length >= 0 advances
+// by exactly 0, and only a negative last turn (an end turn taken as a small
+// negative turn) still applies in full.
+struct DubSegs {
+    float x[3], y[3], th[3], sn[3], cs[3];  // start pose of each segment, sin and cos of its heading
+    float len[3];                           // segment lengths (rho t, rho p, rho q)
+    unsigned types;                         // 2 bits per segment: 0 L, 1 S, 2 R
+    float L, rho;
+};
+
+// the partial (or full) segment of type `type` from a pose
+__device__ __forceinline__ void dub_advance(unsigned type, float a, float rho, float& x, float& y, float& th, float s_th,
+                                            float c_th) {
+    if (type == 1u) {
+        x = x + a * c_th;
+        y = y + a * s_th;
+    } else {
+        const float ang = a / rho;
+        const float th2 = type == 0u ? th + ang : th - ang;
+        float s_2, c_2;
+        dub_sincos(th2, &s_2, &c_2);
+        if (type == 0u) {
+            x = x + rho * (s_2 - s_th);
+            y = y + rho * (c_th - c_2);
+        } else {
+            x = x + rho * (s_th - s_2);
+            y = y + rho * (c_2 - c_th);
+        }
+        th = th2;
+    }
+}
+
+__device__ __forceinline__ DubSegs dubins_segments(const float* s0, const DubPath& P, float rho) {
+    // segment types by word, 2 bits each: LSL RSR LSR RSL RLR LRL
     constexpr unsigned kSeg[6] = {0u | 1u << 2 | 0u << 4, 2u | 1u << 2 | 2u << 4, 0u | 1u << 2 | 2u << 4,
                                   2u | 1u << 2 | 0u << 4, 2u | 0u << 2 | 2u << 4, 0u | 2u << 2 | 0u << 4};
+    DubSegs G;
+    G.types = kSeg[P.word < 6 ? P.word : 0];
+    G.len[0] = P.t * rho;
+    G.len[1] = P.p * rho;
+    G.len[2] = P.q * rho;
+    G.L = P.L;
+    G.rho = rho;
     float x = s0[0], y = s0[1], th = s0[3];
-    float ell = s * P.L;
-    const float len[3] = {P.t * rho, P.p * rho, P.q * rho};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float a = ell < len[k] ? ell : len[k];
-        const unsigned type = (kSeg[P.word] >> (2 * k)) & 3u;
         float s_th, c_th;
         dub_sincos(th, &s_th, &c_th);
-        if (type == 1u) {
-            x = x + a * c_th;
-            y = y + a * s_th;
-        } else {
-            const float ang = a / rho;
-            const float th2 = type == 0u ? th + ang : th - ang;
-            float s_2, c_2;
-            dub_sincos(th2, &s_2, &c_2);
-            if (type == 0u) {
-                x = x + rho * (s_2 - s_th);
-                y = y + rho * (c_th - c_2);
-            } else {
-                x = x + rho * (s_th - s_2);
-                y = y + rho * (c_2 - c_th);
-            }
-            th = th2;
+        G.x[k] = x; G.y[k] = y; G.th[k] = th; G.sn[k] = s_th; G.cs[k] = c_th;
+        if (k < 2) dub_advance((G.types >> (2 * k)) & 3u, G.len[k], rho, x, y, th, s_th, c_th);
+    }
+    return G;
+}
+
+__device__ __forceinline__ void dubins_point(const float* s0, const float* s1, const DubSegs& G, float s, float* out) {
+    float ell = s * G.L;
+    int k = 0;
+    float a = ell;
+    if (!(ell < G.len[0])) {      // segment 0 walked in full
+        ell = ell - G.len[0];
+        k = 1;
+        a = ell;
+        if (!(ell < G.len[1])) {  // segment 1 walked in full
+            ell = ell - G.len[1];
+            k = 2;
+            a = ell < G.len[2] ? ell : G.len[2];
         }
-        ell = ell - a;
+    }
+    float x = G.x[k], y = G.y[k], th = G.th[k];
+    dub_advance((G.types >> (2 * k)) & 3u, a, G.rho, x, y, th, G.sn[k], G.cs[k]);
+    if (k < 2 && G.len[2] < 0.0f) {  // a negative last turn applies whatever the point
+        float s_th, c_th;
+        dub_sincos(th, &s_th, &c_th);
+        dub_advance((G.types >> 4) & 3u, G.len[2], G.rho, x, y, th, s_th, c_th);
     }
     out[0] = x;
     out[1] = y;

@@ -531,7 +531,7 @@ template <int KIND, int D, bool INCOMING>
 __device__ __forceinline__ void fill_row(const SpaceArgs& s, const float* __restrict__ X,
                                          const uint32_t* __restrict__ M, const int* __restrict__ row,
                                          int* __restrict__ col, float* __restrict__ cost, float* __restrict__ tau,
-                                         int v) {
+                                         float* __restrict__ path, int v) {
     __shared__ int list[kFillWarps][kFillList];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (v >= s.N) return;
@@ -549,7 +549,17 @@ __device__ __forceinline__ void fill_row(const SpaceArgs& s, const float* __rest
         for (int t = lane; t < cnt; t += 32) {
             const int j = list[warp][t];
             float c, tj = 0.0f;
-            if (KIND == GMT_COST_DI) {
+            if (KIND == GMT_COST_DUBINS) {
+                float xj[D];
+#pragma unroll
+                for (int a = 0; a < D; ++a) xj[a] = X[(size_t)a * s.pitch + j];
+                const float* from = INCOMING ? xj : xv;
+                const float* to = INCOMING ? xv : xj;
+                const DubPath P = dubins_path(from, to, s.rho);
+                c = dubins_length(P, from, to);
+                if (path)
+                    reinterpret_cast<float4*>(path)[base + t] = make_float4(P.t, P.p, P.q, __int_as_float(P.word));
+            } else if (KIND == GMT_COST_DI) {
                 // the same formulas on the same states as the edge's out-row:
                 // identical bits in both directions
                 float xj[D];

@@ -80,13 +80,16 @@ cudaError_t launch_transpose(const SpaceArgs& s, const uint32_t* mask, uint32_t*
 cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st);
 // One CSR direction for the fill: the bit matrix rows come from (mask for
 // out-rows, its transpose for in-rows), row offsets, and the outputs; tau
-// (double integrator only, may be NULL) receives each edge's arrival time.
+// (double integrator only, may be NULL) receives each edge's arrival time,
+// path (Dubins airplane only, may be NULL) each edge's shortest word as
+// (t, p, q, word bits) in 4 floats.
 struct FillDir {
     const uint32_t* mask;
     const int* row;
     int* col;
     float* cost;
     float* tau;
+    float* path;
 };
 // Fills the out-CSR, and the in-CSR in the same launch when in.mask != NULL.
 cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, cudaStream_t st);
@@ -166,6 +169,7 @@ struct PlanArgs {
     const int* in_col;
     const float* in_cost;
     const float* in_tau;  // double integrator: arrival time per in-edge (NULL: recompute)
+    const float* in_path; // Dubins airplane: (t, p, q, word bits) per in-edge (NULL: recompute)
     BoxArgs boxes;
     BoxGridArgs grid;  // use = 0 unless the plan built one
     float pos_lo[3], pos_hi[3];

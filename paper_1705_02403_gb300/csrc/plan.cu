@@ -219,9 +219,18 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
                     if (KIND == GMT_COST_EUCLID)
                         free_edge = segment_free_warp<DP>(sy, sx, __ldg(&A.in_cost[be]), A.seg_spacing, blo, bhi,
                                                           nbox, A.grid);
-                    else if (KIND == GMT_COST_DUBINS)
-                        free_edge = dubins_free_warp(sy, sx, __ldg(&A.in_cost[be]), A.seg_spacing, A.rho, A.pos_lo,
-                                                     A.pos_hi, blo, bhi, nbox, A.grid);
+                    else if (KIND == GMT_COST_DUBINS) {
+                        // the edge's shortest word: stored by the graph build, or recomputed
+                        DubPath P;
+                        if (A.in_path) {
+                            const float4 w = __ldg(reinterpret_cast<const float4*>(A.in_path) + be);
+                            P = DubPath{__float_as_int(w.w), w.x, w.y, w.z, ((w.x + w.y) + w.z) * A.rho};
+                        } else {
+                            P = dubins_path(sy, sx, A.rho);
+                        }
+                        free_edge = dubins_free_warp(sy, sx, P, __ldg(&A.in_cost[be]), A.seg_spacing, A.rho,
+                                                     A.pos_lo, A.pos_hi, blo, bhi, nbox, A.grid);
+                    }
                     else {
                         // arrival time of the edge: stored by the graph build, or recomputed
                         const float tau = A.in_tau ? __ldg(&A.in_tau[be]) : di_tau(di_coef(sy, sx), A.r);

@@ -213,18 +213,21 @@ __device__ __forceinline__ bool trajectory_free_warp(const float* y, const float
     return true;
 }
 
-// Dubins airplane edge y -> x of cost c: m = max(2, ceil(c / spacing) + 1)
-// trajectory points at fractions k / (m - 1); a point in a box or outside the
-// position bounds collides.  Every lane computes the (same) shortest word and
-// then its own points.  Without the box grid, boxes are first tested against
-// a bound of the whole trajectory: its planar part stays within c/2 of the
-// midpoint of y and x (a point at arc length l is within l of y and L - l of x,
-// L <= c), its altitude between the two end altitudes.
-__device__ __forceinline__ bool dubins_free_warp(const float* y, const float* x, float c, float spacing, float rho,
-                                                 const float* plo, const float* phi, const float* blo,
-                                                 const float* bhi, int nbox, const BoxGridArgs& grid) {
+// Dubins airplane edge y -> x of cost c along its shortest word P:
+// m = max(2, ceil(c / spacing) + 1) trajectory points at fractions k / (m - 1);
+// a point in a box or outside the position bounds collides.  Every lane walks
+// the segment start poses once, then its own points.  Without the box grid,
+// boxes are first tested against a bound of the whole trajectory: its planar
+// part stays within c/2 of the midpoint of y and x (a point at arc length l is
+// within l of y and L - l of x, L <= c), its altitude between the two end
+// altitudes.
+__device__ __forceinline__ bool dubins_free_warp(const float* y, const float* x, const DubPath& P, float c,
+                                                 float spacing, float rho, const float* plo, const float* phi,
+                                                 const float* blo, const float* bhi, int nbox,
+                                                 const BoxGridArgs& grid) {
     const int lane = threadIdx.x & 31;
-    const DubPath P = dubins_path(y, x, rho);
+    if (P.word >= kDubNone) return false;  // no word: never an edge (its cost would be +inf)
+    const DubSegs G = dubins_segments(y, P, rho);
     int m = (int)ceilf(c / spacing) + 1;
     if (m < 2) m = 2;
     const float denom = (float)(m - 1);
@@ -247,7 +250,7 @@ __device__ __forceinline__ bool dubins_free_warp(const float* y, const float* x,
         bool hit = false;
         float p[3];
         if (k < m) {
-            dubins_point(y, x, P, rho, (float)k / denom, p);
+            dubins_point(y, x, G, (float)k / denom, p);
 #pragma unroll
             for (int a = 0; a < 3; ++a) hit = hit || p[a] < plo[a] || p[a] > phi[a];
             if (grid.use && !hit) hit = in_any_box_grid<3>(p, blo, bhi, grid);

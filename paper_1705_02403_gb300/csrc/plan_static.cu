@@ -116,6 +116,7 @@ extern "C" gmt_status gmt_plan_static(const gmt_space* space, const gmt_graph_vi
     a.out_row = g->out_row; a.out_col = g->out_col;
     a.in_row = g->in_row; a.in_col = g->in_col; a.in_cost = g->in_cost;
     a.in_tau = g->kind == GMT_COST_DI ? g->in_tau : nullptr;
+    a.in_path = g->kind == GMT_COST_DUBINS ? g->in_path : nullptr;
     a.boxes = BoxArgs{boxes->count, boxes->lo, boxes->hi};
     for (int k = 0; k < 3 && k < g->pos_dim; ++k) { a.pos_lo[k] = space->lo[k]; a.pos_hi[k] = space->hi[k]; }
     a.r = g->r;

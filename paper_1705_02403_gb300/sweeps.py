@@ -1,12 +1,14 @@
 """Synthetic sweeps in the manner of Table 1 (cost error of GMT* against FMT*
 over lambda and dimension) and Table 3 (time and cost against sample count
-and obstacle resolution), run on the GPU planner.
+and obstacle resolution, double integrator and Dubins airplane), run on the
+GPU planner.
 
 FMT* is GMT* at lambda = 0 (the limit of Sec. III: every group is the set of
 open nodes of minimum cost; the oracle tests pin this against a heap FMT*), so
 both arms run through the same library on the same graph.  The environments
 are synthetic analogues (envgen.rectangles, envgen.maze, envgen.forest_boxes,
-envgen.di6_scaled); the paper gives their figures, not their geometry.
+envgen.di6_scaled, envgen.dubins_forest); the paper gives their figures, not
+their geometry.
 
     python -m paper_1705_02403_gb300.sweeps --out sweeps.json
 """
@@ -108,19 +110,45 @@ def table3(runs: int = 20, lam: float = 1.0, log=print):
     return rows
 
 
+def table3_dubins(runs: int = 20, lam: float = 1.0, sampler: int = 1, log=print):
+    """Dubins airplane in the forest analogue (lambda = 1, Halton samples as in
+    Sec. V): time against the number of boxes at n = 5000 (150, 500, 1500,
+    5000: the same ten trunks cut into 15, 50, 150, 500 strips, Table 3's box
+    counts), then n = 10000 with 150 boxes (radius scaled for about the same
+    mean out-degree)."""
+    rows = []
+    for n, strips in ((5000, 15), (5000, 50), (5000, 150), (5000, 500), (10000, 15)):
+        r = float(np.float32(0.2 * (5000.0 / n) ** 0.2))
+        probs = [envgen.dubins_forest(seed, n=n, r=r, strips=strips, sampler=sampler) for seed in range(runs)]
+        res = _timed_runs(probs, lam)
+        res.update({"sweep": "boxes" if n == 5000 else "samples", "n": n, "boxes": 10 * strips, "r": r})
+        rows.append(res)
+        if log:
+            log(f"  n={n}, {10 * strips} boxes: plan {res['plan_ms_p50']:.3f} ms (p99 {res['plan_ms_p99']:.3f}), "
+                f"build {res['build_ms_p50']:.3f} ms, success {res['success']:.2f}, mean cost {res['mean_cost']}")
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--runs1", type=int, default=50, help="runs per Table 1 cell")
     ap.add_argument("--runs3", type=int, default=20, help="problems per Table 3 row")
     ap.add_argument("--out", default="sweeps.json")
+    ap.add_argument("--only", choices=["table1", "table3", "dubins"], default=None)
     a = ap.parse_args()
     t0 = time.time()
-    print("Table 1 analogue (cost error of GMT* against FMT* = GMT* at lambda 0, n = 5000):")
-    t1 = table1(a.runs1)
-    print("Table 3 analogue (double integrator, lambda = 1):")
-    t3 = table3(a.runs3)
-    out = {"table1": t1, "table3": t3, "wall_s": time.time() - t0,
-           "device": torch.cuda.get_device_name(0) if torch.cuda.is_available() else None}
+    out = {}
+    if a.only in (None, "table1"):
+        print("Table 1 analogue (cost error of GMT* against FMT* = GMT* at lambda 0, n = 5000):")
+        out["table1"] = table1(a.runs1)
+    if a.only in (None, "table3"):
+        print("Table 3 analogue (double integrator, lambda = 1):")
+        out["table3"] = table3(a.runs3)
+    if a.only in (None, "dubins"):
+        print("Table 3 analogue (Dubins airplane in the forest, lambda = 1, Halton samples):")
+        out["table3_dubins"] = table3_dubins(a.runs3)
+    out.update({"wall_s": time.time() - t0,
+           "device": torch.cuda.get_device_name(0) if torch.cuda.is_available() else None})
     with open(a.out, "w") as f:
         json.dump(out, f, indent=1)
 

@@ -105,3 +105,74 @@ def test_bad_arguments(O, P):
     with pytest.raises(N.GmtError) as e:
         bp.plan()
     assert e.value.status == N.GMT_ERR_INVALID
+
+
+def test_aligned_states_and_recomputed_words(O, P):
+    # Families of states along their own heading (a straight path whose end
+    # turns round to near-full loops and are taken as small negative turns),
+    # near-duplicates and pure sideways offsets, appended to a sparse forest
+    # sample set; the CSR (every cost), the stored words (through the plan's
+    # checks) and a plan that recomputes the words must all equal the oracle.
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import GraphView, boxes_on_device, goal_struct, params_struct, space_struct
+    pb = envgen.dubins_forest(21, n=300, r=0.3, trunks=3)
+    rng = np.random.default_rng(8)
+    states = []
+    for _ in range(60):
+        b = np.array([*rng.uniform(0.15, 0.85, 3), rng.uniform(-3.1, 3.1)])
+        for kind in range(8):
+            s = b.copy()
+            if kind < 4:        # along the heading, same heading
+                u = rng.uniform(0.005, 0.2)
+                s[0] += u * np.cos(b[3]); s[1] += u * np.sin(b[3]); s[2] += rng.uniform(-0.05, 0.05)
+            elif kind < 6:      # near-duplicates
+                s[:3] += rng.uniform(-1e-4, 1e-4, 3); s[3] += rng.uniform(-1e-4, 1e-4)
+            else:               # sideways, same heading
+                u = rng.uniform(-0.1, 0.1)
+                s[0] -= u * np.sin(b[3]); s[1] += u * np.cos(b[3])
+            s = np.clip(s, pb.lo, pb.hi).astype(np.float32)
+            if not np.any(np.all((pb.box_lo <= s[:3]) & (s[:3] <= pb.box_hi), axis=1)):
+                states.append(s)
+    extra = torch.tensor(np.array(states, np.float32).T.copy(), device="cuda")
+    boxes, keep = boxes_on_device(pb)
+    params = params_struct(pb)
+    g = N.gmt_build_graph_ex(space_struct(pb), boxes, [float(v) for v in pb.x_init], goal_struct(pb), params,
+                             extra.data_ptr(), len(states), len(states))
+    v = GraphView(g)
+    X, goal = v.X.cpu().numpy(), v.is_goal.cpu().numpy()
+    og = O.Graph(pb.kind, pb.d, pb.dp, X, goal, np.float32(pb.r), rho=pb.rho)
+    c = og.csr()
+    assert v.E == og.num_edges and v.E > 0
+    assert np.array_equal(v.out_row.cpu().numpy(), c.out_row) and np.array_equal(v.out_col.cpu().numpy(), c.out_col)
+    assert np.array_equal(bits(v.out_cost.cpu().numpy()), bits(c.out_cost))
+    assert np.array_equal(v.in_row.cpu().numpy(), c.in_row) and np.array_equal(v.in_col.cpu().numpy(), c.in_col)
+    assert np.array_equal(bits(v.in_cost.cpu().numpy()), bits(c.in_cost))
+    # stored words: the oracle's shortest word for every in-edge
+    raw = v.raw
+    words = P.wrap_device(raw.in_path, (v.E, 4), "f4", g).cpu().numpy()
+    wid = words[:, 3].copy().view(np.int32)
+    neg = 0
+    for x in range(v.N):
+        for e in range(c.in_row[x], c.in_row[x + 1]):
+            y = int(c.in_col[e])
+            ref, best = O.dubins_words(X[:, y], X[:, x], pb.rho, precision=32)
+            assert wid[e] == best and np.array_equal(bits(words[e, :3]), bits(ref[best, 1:4]))
+            neg += int(ref[best, 1] < 0 or ref[best, 3] < 0)
+    assert neg > 0, "some stored words carry a negative end turn"
+    # plans: stored words (gmt_plan) and recomputed ones (a view without them)
+    n_total = v.N
+    parent = torch.empty(n_total, dtype=torch.int32, device="cuda")
+    cost = torch.empty(n_total, dtype=torch.float32, device="cuda")
+    ref_parent, ref_cost, ref_info = og.plan(pb.box_lo, pb.box_hi, pb.lo[:3], pb.hi[:3], pb.lam, pb.seg_spacing)
+    for recompute in (False, True):
+        view = N.gmt_graph_get_view(g)
+        if recompute:
+            view.in_path = None
+            info = N.gmt_plan_static(space_struct(pb), view, boxes, params, parent.data_ptr(), cost.data_ptr(),
+                                     None).as_dict()
+        else:
+            info = N.gmt_plan(g, boxes, params, parent.data_ptr(), cost.data_ptr(), None).as_dict()
+        torch.cuda.synchronize()
+        assert np.array_equal(parent.cpu().numpy(), ref_parent)
+        assert np.array_equal(bits(cost.cpu().numpy()), bits(ref_cost))
+        assert info["checks"] == ref_info["checks"] and info["failed"] == ref_info["failed"]

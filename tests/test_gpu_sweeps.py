@@ -24,3 +24,12 @@ def test_table3_small():
     rows = sweeps.table3(runs=2, log=None)
     assert [r["boxes"] for r in rows] == [300, 300, 300, 300, 150, 500, 1500, 5000]
     assert all(r["plan_ms_p50"] > 0 and r["build_ms_p50"] > 0 for r in rows)
+
+
+def test_table3_dubins_small():
+    from paper_1705_02403_gb300 import sweeps
+    rows = sweeps.table3_dubins(runs=1, log=None)
+    assert [(r["n"], r["boxes"]) for r in rows] == [(5000, 150), (5000, 500), (5000, 1500), (5000, 5000),
+                                                    (10000, 150)]
+    assert all(r["plan_ms_p50"] > 0 and r["build_ms_p50"] > 0 for r in rows)
+    assert all(r["success"] == 1.0 for r in rows)

@@ -57,3 +57,16 @@ def test_forest_strips_cover_each_disk():
             for k in range(strips):
                 covered |= inside(p, L[k], H[k])
             assert covered.all()
+
+
+def test_dubins_forest():
+    for seed in range(10):
+        for strips in (15, 500):
+            pb = envgen.dubins_forest(seed, n=100, strips=strips)
+            assert (pb.kind, pb.d, pb.dp) == (envgen.DUBINS, 4, 3) and pb.rho > 0
+            assert pb.box_lo.shape == (10 * strips, 3)
+            assert not inside(pb.x_init[:3], pb.box_lo, pb.box_hi).any()
+            near = np.clip(pb.goal_center[:3], pb.box_lo, pb.box_hi)
+            assert np.all(np.linalg.norm(near - pb.goal_center[:3], axis=1) > pb.goal_radius)
+            assert np.all(pb.box_lo[:, 2] == 0) and np.all(pb.box_hi[:, 2] == 1)   # full-height trunks
+            assert pb.lo[3] < -3.14 and pb.hi[3] > 3.14                              # every heading
