@@ -90,8 +90,7 @@ struct gmt_graph {
     int* grid_cnt = nullptr;       size_t cap_grid_cnt = 0;
     int* grid_start = nullptr;     size_t cap_grid_start = 0;
     int* grid_list = nullptr;      size_t cap_grid_list = 0;
-    int* grid_cell_of = nullptr;   size_t cap_grid_cell_of = 0;
-    float* grid_ext = nullptr;     size_t cap_grid_ext = 0;
+    int* grid_big = nullptr;       size_t cap_grid_big = 0;
     // plan workspace
     float* ocost = nullptr;        size_t cap_ocost = 0;
     int* stamp = nullptr;          size_t cap_stamp = 0;
@@ -127,7 +126,7 @@ struct gmt_graph {
     ~gmt_graph() {
         void* dev[] = {X, is_goal, out_row, in_row_own, out_count, in_count, out_col, out_cost, in_col_own,
                        in_cost_own, out_tau, in_tau, in_path, mask, maskT, flags, cell_of, cell_sorted, cell_cnt,
-                       cell_start, grid_cnt, grid_start, grid_list, grid_cell_of, grid_ext, ocost, stamp,
+                       cell_start, grid_cnt, grid_start, grid_list, grid_big, ocost, stamp,
                        lists, ctl};
         for (void* p : dev)
             if (p) cudaFree(p);
@@ -218,24 +217,23 @@ cudaError_t build_box_grid(gmt_graph* g, const BoxArgs& boxes, BoxGridArgs* gr, 
     const int G = box_grid_cells(boxes.count);
     const size_t B = (size_t)boxes.count, cells = (size_t)G * G;
     cudaError_t e;
-    if ((e = grow(&g->grid_cnt, &g->cap_grid_cnt, cells)) != cudaSuccess) return e;
+    if ((e = grow(&g->grid_cnt, &g->cap_grid_cnt, cells + 1)) != cudaSuccess) return e;  // + the big-box count
     if ((e = grow(&g->grid_start, &g->cap_grid_start, cells + 1)) != cudaSuccess) return e;
-    if ((e = grow(&g->grid_list, &g->cap_grid_list, B)) != cudaSuccess) return e;
-    if ((e = grow(&g->grid_cell_of, &g->cap_grid_cell_of, B)) != cudaSuccess) return e;
-    if ((e = grow(&g->grid_ext, &g->cap_grid_ext, (size_t)2)) != cudaSuccess) return e;
+    if ((e = grow(&g->grid_list, &g->cap_grid_list, B * kBoxGridMaxCells)) != cudaSuccess) return e;
+    if ((e = grow(&g->grid_big, &g->cap_grid_big, B)) != cudaSuccess) return e;
     gr->use = 1;
     gr->g = G;
     for (int k = 0; k < 2; ++k) {
         gr->lo[k] = g->pos_lo[k];
         gr->inv_h[k] = (float)((double)G / ((double)g->pos_hi[k] - (double)g->pos_lo[k]));
     }
-    gr->ext = g->grid_ext;
     gr->start = g->grid_start;
     gr->list = g->grid_list;
-    if ((e = cudaMemsetAsync(g->grid_cnt, 0, cells * sizeof(int), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(g->grid_ext, 0, 2 * sizeof(float), st)) != cudaSuccess) return e;
-    return launch_box_grid(g->dp, boxes, *gr, g->grid_cnt, g->grid_start, g->grid_list, g->grid_cell_of, g->grid_ext,
-                           st);
+    gr->big = g->grid_big;
+    gr->nbig = g->grid_cnt + cells;
+    if ((e = cudaMemsetAsync(g->grid_cnt, 0, (cells + 1) * sizeof(int), st)) != cudaSuccess) return e;
+    return launch_box_grid(g->dp, boxes, *gr, g->grid_cnt, g->grid_start, g->grid_list, g->grid_big,
+                           g->grid_cnt + cells, st);
 }
 }  // namespace
 

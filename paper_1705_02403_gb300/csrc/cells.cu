@@ -33,43 +33,59 @@ __global__ void __launch_bounds__(kCellWarps * 32) cells_rows_kernel(SpaceArgs s
 }
 
 // ---- box grid (checks against many boxes)
-__device__ __forceinline__ int box_grid_cell(const BoxGridArgs& g, float x, int a) {
-    const int k = (int)floorf((x - g.lo[a]) * g.inv_h[a]);
-    return min(max(k, 0), g.g - 1);
+// The cell range [c0, c1] of box b on the grid's axes (empty when lo > hi).
+__device__ __forceinline__ void box_grid_range(const BoxGridArgs& g, const float* lo, const float* hi, int* c0,
+                                               int* c1) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        c0[a] = box_grid_cell(g, lo[a], a);
+        c1[a] = box_grid_cell(g, hi[a], a);
+    }
 }
 
+// One thread per box: counts it in each cell it overlaps, or lists it as big.
 __global__ void __launch_bounds__(256) box_grid_count_kernel(BoxArgs boxes, int dp, BoxGridArgs grid,
-                                                             int* __restrict__ cnt, int* __restrict__ cell_of,
-                                                             float* __restrict__ ext) {
+                                                             int* __restrict__ cnt, int* __restrict__ big,
+                                                             int* __restrict__ nbig) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= boxes.count) return;
-    const float* lo = boxes.lo + (size_t)b * dp;
-    const float* hi = boxes.hi + (size_t)b * dp;
-    const int c = box_grid_cell(grid, lo[1], 1) * grid.g + box_grid_cell(grid, lo[0], 0);
-    cell_of[b] = c;
-    atomicAdd(&cnt[c], 1);
-    // sides are >= 0 (a box with lo > hi meets nothing), so their bits order as ints
-    atomicMax((int*)&ext[0], __float_as_int(fmaxf(hi[0] - lo[0], 0.0f)));
-    atomicMax((int*)&ext[1], __float_as_int(fmaxf(hi[1] - lo[1], 0.0f)));
+    int c0[2], c1[2];
+    box_grid_range(grid, boxes.lo + (size_t)b * dp, boxes.hi + (size_t)b * dp, c0, c1);
+    if (c0[0] > c1[0] || c0[1] > c1[1]) return;  // lo > hi: the box holds no point
+    if ((c1[0] - c0[0] + 1) * (c1[1] - c0[1] + 1) > kBoxGridMaxCells) {
+        big[atomicAdd(nbig, 1)] = b;
+        return;
+    }
+    for (int cy = c0[1]; cy <= c1[1]; ++cy)
+        for (int cx = c0[0]; cx <= c1[0]; ++cx) atomicAdd(&cnt[cy * grid.g + cx], 1);
 }
 
-__global__ void __launch_bounds__(256) box_grid_scatter_kernel(int count, const int* __restrict__ cell_of,
+// One thread per box: writes it into each of its cells' lists (cnt counts
+// back down to 0).
+__global__ void __launch_bounds__(256) box_grid_scatter_kernel(BoxArgs boxes, int dp, BoxGridArgs grid,
                                                                const int* __restrict__ start, int* __restrict__ cnt,
                                                                int* __restrict__ list) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= count) return;
-    const int c = cell_of[b];
-    list[start[c] + atomicSub(&cnt[c], 1) - 1] = b;
+    if (b >= boxes.count) return;
+    int c0[2], c1[2];
+    box_grid_range(grid, boxes.lo + (size_t)b * dp, boxes.hi + (size_t)b * dp, c0, c1);
+    if (c0[0] > c1[0] || c0[1] > c1[1]) return;
+    if ((c1[0] - c0[0] + 1) * (c1[1] - c0[1] + 1) > kBoxGridMaxCells) return;
+    for (int cy = c0[1]; cy <= c1[1]; ++cy)
+        for (int cx = c0[0]; cx <= c1[0]; ++cx) {
+            const int c = cy * grid.g + cx;
+            list[start[c] + atomicSub(&cnt[c], 1) - 1] = b;
+        }
 }
 
 cudaError_t launch_box_grid(int dp, BoxArgs boxes, const BoxGridArgs& grid, int* cnt, int* start, int* list,
-                            int* cell_of, float* ext, cudaStream_t st) {
+                            int* big, int* nbig, cudaStream_t st) {
     if (dp < 2 || boxes.count < 1) return cudaErrorInvalidValue;
     const unsigned blocks = (unsigned)((boxes.count + 255) / 256);
-    box_grid_count_kernel<<<blocks, 256, 0, st>>>(boxes, dp, grid, cnt, cell_of, ext);
+    box_grid_count_kernel<<<blocks, 256, 0, st>>>(boxes, dp, grid, cnt, big, nbig);
     cudaError_t e = launch_scan(cnt, start, grid.g * grid.g, st);
     if (e != cudaSuccess) return e;
-    box_grid_scatter_kernel<<<blocks, 256, 0, st>>>(boxes.count, cell_of, start, cnt, list);
+    box_grid_scatter_kernel<<<blocks, 256, 0, st>>>(boxes, dp, grid, start, cnt, list);
     return cudaGetLastError();
 }
 

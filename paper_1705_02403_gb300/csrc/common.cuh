@@ -77,24 +77,24 @@ __device__ __forceinline__ bool in_any_box(const float* p, const float* lo, cons
     return false;
 }
 
-// Does point p lie in a box?  With the grid, only the boxes listed in the
-// cells from (p - ext) to p on axes 0 and 1 (widened by one cell each way) can
-// hold it; each is tested exactly.  One thread.
+// Grid cell of coordinate x on grid axis a, clamped to the grid.
+__device__ __forceinline__ int box_grid_cell(const BoxGridArgs& g, float x, int a) {
+    const int k = (int)floorf((x - g.lo[a]) * g.inv_h[a]);
+    return min(max(k, 0), g.g - 1);
+}
+
+// Does point p lie in a box?  With the grid, only the boxes listed in p's
+// cell and the big boxes can hold it; each is tested exactly.  One thread.
 template <int DP>
 __device__ __forceinline__ bool in_any_box_grid(const float* p, const float* blo, const float* bhi,
                                                 const BoxGridArgs& grid) {
-    const float ex = __ldg(&grid.ext[0]), ey = __ldg(&grid.ext[1]);
-    auto cell = [&](float v, int a) {
-        const int k = (int)floorf((v - grid.lo[a]) * grid.inv_h[a]);
-        return min(max(k, 0), grid.g - 1);
-    };
-    const int cx0 = max(cell(p[0] - ex, 0) - 1, 0), cx1 = min(cell(p[0], 0) + 1, grid.g - 1);
-    const int cy0 = max(cell(p[1] - ey, 1) - 1, 0), cy1 = min(cell(p[1], 1) + 1, grid.g - 1);
-    for (int cy = cy0; cy <= cy1; ++cy) {
-        const int e = __ldg(&grid.start[cy * grid.g + cx1 + 1]);
-        for (int t = __ldg(&grid.start[cy * grid.g + cx0]); t < e; ++t)
-            if (in_box<DP>(p, blo, bhi, __ldg(&grid.list[t]))) return true;
-    }
+    const int c = box_grid_cell(grid, p[1], 1) * grid.g + box_grid_cell(grid, p[0], 0);
+    const int e = __ldg(&grid.start[c + 1]);
+    for (int t = __ldg(&grid.start[c]); t < e; ++t)
+        if (in_box<DP>(p, blo, bhi, __ldg(&grid.list[t]))) return true;
+    const int nb = __ldg(grid.nbig);
+    for (int t = 0; t < nb; ++t)
+        if (in_box<DP>(p, blo, bhi, __ldg(&grid.big[t]))) return true;
     return false;
 }
 

@@ -38,31 +38,36 @@ struct BoxArgs {
 };
 
 // Grid over the first two position axes for checks against many boxes: box b
-// is listed in the cell of its minimum corner.  Every box that holds a point
-// p has its minimum corner within [p - ext, p] on both axes (ext: the largest
-// box side per axis), so the cells from (p - ext) to p, widened by one cell
-// each way against rounding, list every candidate; the exact box test then
-// decides as without the grid.
+// is listed in every cell its [lo, hi] overlaps on those axes (cells from
+// cell(lo) to cell(hi), cell(x) = clamp(floor((x - lo_grid) * inv_h))), or, if
+// that is more than kBoxGridMaxCells cells, in a list of big boxes.  A box
+// that holds a point p is listed in p's cell: lo <= p <= hi gives
+// cell(lo) <= cell(p) <= cell(hi), since every step of cell() is monotone in
+// IEEE arithmetic.  A query tests the boxes of p's cell and the big boxes
+// exactly, so its verdict equals testing every box.
 struct BoxGridArgs {
-    int use;           // 0: scan every box
-    int g;             // cells per axis
+    int use;            // 0: scan every box
+    int g;              // cells per axis
     float lo[2], inv_h[2];
-    const float* ext;  // [2], device: largest box side along axes 0 and 1
-    const int* start;  // [g * g + 1] first list entry of each cell
-    const int* list;   // box indices, grouped by cell
+    const int* start;   // [g * g + 1] first list entry of each cell
+    const int* list;    // box indices, grouped by cell
+    const int* big;     // indices of the boxes over more than kBoxGridMaxCells cells
+    const int* nbig;    // [1] their count
 };
 // Boxes from which the plan builds a grid (fewer are scanned directly).
 constexpr int kBoxGridMinBoxes = 128;
+// Cells a box may be listed in before it goes to the big-box list.
+constexpr int kBoxGridMaxCells = 32;
 // Cells per axis for `count` boxes.
 inline int box_grid_cells(int count) {
     int g = 1;
     while (g < 64 && g * g < count) g *= 2;
     return g;
 }
-// Builds the grid: cnt [g*g] and ext [2] must be zeroed; start [g*g + 1],
-// list [count], cell_of [count].
+// Builds the grid: cnt [g*g] and nbig [1] must be zeroed; start [g*g + 1],
+// list [count * kBoxGridMaxCells], big [count].
 cudaError_t launch_box_grid(int dp, BoxArgs boxes, const BoxGridArgs& grid, int* cnt, int* start, int* list,
-                            int* cell_of, float* ext, cudaStream_t st);
+                            int* big, int* nbig, cudaStream_t st);
 
 // Flags written by the sampling kernel.
 enum { kSampleBadInit = 1, kSampleExhausted = 2, kSampleBadAppend = 4 };

@@ -244,11 +244,12 @@ def test_halton_sampling_matches_the_oracle(O, P, case):
     assert_same(O, G, *oracle_run(O, pb))
 
 
-@pytest.mark.parametrize("case", ["2d_600", "3d_300", "di_forest_1500", "2d_outside"])
+@pytest.mark.parametrize("case", ["2d_600", "3d_300", "di_forest_1500", "2d_outside", "2d_big_and_degenerate"])
 def test_many_boxes_use_the_box_grid(O, P, case):
-    # From 128 boxes the plan bins them on a grid over the first two position
-    # axes; the checks gather candidates from the grid and the tree must stay
-    # the oracle's.
+    # From 128 boxes the plan and SampleFree list each box in the grid cells
+    # it overlaps on the first two position axes (boxes over more than 32
+    # cells in a list scanned for every point); samples and tree must stay the
+    # oracle's.
     rng = np.random.default_rng(81)
     if case == "2d_600":
         pb = envgen.geometric(81, d=2, n=2000, nbox=0, r=0.06)
@@ -259,6 +260,20 @@ def test_many_boxes_use_the_box_grid(O, P, case):
     elif case == "di_forest_1500":
         pb = envgen.di6(seed=83, n=700, nbox=0, r=2.8)
         bl, bh = envgen.forest_boxes(83, 10, 150)
+    elif case == "2d_big_and_degenerate":
+        # 200 small boxes (16 x 16 cells), 4 boxes over ~40 cells each (the
+        # big-box list), zero-width boxes (lo == hi on an axis: they still hold
+        # the points on them) and empty ones (lo > hi: they hold nothing)
+        pb = envgen.geometric(85, d=2, n=2500, nbox=0, r=0.06)
+        bl, bh = envgen.random_boxes(rng, 200, 2, pb.x_init, pb.goal_center, 0.05, side=(0.01, 0.04))
+        big_lo = np.array([[0.2, 0.3], [0.55, 0.1], [0.1, 0.6], [0.5, 0.5]], np.float32)
+        big_hi = big_lo + np.array([[0.38, 0.36], [0.36, 0.37], [0.35, 0.2], [0.37, 0.36]], np.float32)
+        flat_lo = np.array([[0.3, 0.05], [0.05, 0.9]], np.float32)
+        flat_hi = np.array([[0.3, 0.3], [0.4, 0.9]], np.float32)          # x == 0.3 and y == 0.9 segments
+        empty_lo = np.array([[0.6, 0.6], [0.1, 0.2]], np.float32)
+        empty_hi = np.array([[0.5, 0.9], [0.3, 0.1]], np.float32)
+        bl = np.concatenate([bl, big_lo, flat_lo, empty_lo])
+        bh = np.concatenate([bh, big_hi, flat_hi, empty_hi])
     else:  # boxes reaching outside the domain on both sides
         pb = envgen.geometric(84, d=2, n=1500, nbox=0, r=0.07)
         bl, bh = envgen.random_boxes(rng, 300, 2, pb.x_init, pb.goal_center, 0.05, side=(0.01, 0.05))
