@@ -91,6 +91,7 @@ struct gmt_graph {
     int* grid_start = nullptr;     size_t cap_grid_start = 0;
     int* grid_list = nullptr;      size_t cap_grid_list = 0;
     int* grid_big = nullptr;       size_t cap_grid_big = 0;
+    int* halton = nullptr;         size_t cap_halton = 0;    // multi-block Halton sampler scratch (ints)
     // plan workspace
     float* ocost = nullptr;        size_t cap_ocost = 0;
     int* stamp = nullptr;          size_t cap_stamp = 0;
@@ -126,7 +127,7 @@ struct gmt_graph {
     ~gmt_graph() {
         void* dev[] = {X, is_goal, out_row, in_row_own, out_count, in_count, out_col, out_cost, in_col_own,
                        in_cost_own, out_tau, in_tau, in_path, mask, maskT, flags, cell_of, cell_sorted, cell_cnt,
-                       cell_start, grid_cnt, grid_start, grid_list, grid_big, ocost, stamp,
+                       cell_start, grid_cnt, grid_start, grid_list, grid_big, halton, ocost, stamp,
                        lists, ctl};
         for (void* p : dev)
             if (p) cudaFree(p);
@@ -329,7 +330,15 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     LAUNCH(g->mark(gmt_graph::kSample, 0, st), "event");
     BoxGridArgs grid;
     LAUNCH(build_box_grid(g, ba, &grid, st), "box grid kernels");
-    LAUNCH(launch_sample(sa, ba, grid, g->X, g->is_goal, g->flags, st), "sample kernel");
+    void* halton_scratch = nullptr;
+    if (sa.sampler == GMT_SAMPLER_HALTON) {
+        const size_t bytes = halton_scratch_bytes(sa.halton_cap);
+        GROW(halton, bytes / sizeof(int));
+        LAUNCH(cudaMemsetAsync(g->halton, 0, bytes, st), "memset");
+        LAUNCH(cudaMemsetAsync(g->halton + 1, 0x7f, sizeof(int), st), "memset");  // no chunk has stopped the rest
+        halton_scratch = g->halton;
+    }
+    LAUNCH(launch_sample(sa, ba, grid, halton_scratch, g->X, g->is_goal, g->flags, st), "sample kernel");
     LAUNCH(launch_append(sa, ba, extra, extra_pitch, n_sampled, extra_count, g->X, g->is_goal, g->flags, st),
            "append kernel");
     LAUNCH(g->mark(gmt_graph::kSample, 1, st), "event");
@@ -390,6 +399,7 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     if (flags & kSampleExhausted)
         return bail(fail(GMT_ERR_INVALID, "a sample exhausted max_attempts (X_free or X_goal n X_free too small)"));
     if (flags & kSampleBadAppend) return bail(fail(GMT_ERR_INVALID, "an appended sample is outside X or in X_obs"));
+    if (flags & kSampleTimeout) return bail(fail(GMT_ERR_TIMEOUT, "the Halton sampler's bounded wait ran out"));
     g->E = g->h_scalars[2];
     const size_t E = (size_t)g->E;
     GROW(out_col, E);

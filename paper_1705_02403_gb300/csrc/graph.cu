@@ -3,6 +3,9 @@
 //
 //   sample_kernel     one thread per node: Philox4x32-10 rejection sampling
 //   halton_kernel     one block: the free Halton points in order
+//   halton_head_kernel + halton_free_kernel  the same split: nodes 0 and 1
+//                     in one block, the free points over many blocks (chunks
+//                     in ticket order, running totals by look-back)
 //   pair_mask_kernel  all ordered pairs (i, j): bit j of row i is set iff
 //                     c(i, j) < r; rows staged through shared memory; the bit
 //                     matrix is word-major (word w of every row contiguous) so
@@ -53,6 +56,101 @@ __global__ void __launch_bounds__(kHaltonThreads) halton_kernel(SpaceArgs s, Box
 }
 
 template <int D, int DP>
+__global__ void __launch_bounds__(kHaltonThreads) halton_head_kernel(SpaceArgs s, BoxArgs boxes, BoxGridArgs grid,
+                                                                     float* __restrict__ X,
+                                                                     uint8_t* __restrict__ is_goal,
+                                                                     int* __restrict__ flags) {
+    halton_head_block<D, DP>(s, boxes, grid, X, is_goal, flags);
+}
+
+// Nodes 2..n_sampled-1 of the Halton SampleFree: the free points in the order
+// of k.  A block takes chunk c (points 1 + c*kHaltonChunk ..) from the ticket,
+// counts its free points, publishes the count (flag 1), adds the counts or the
+// running total (flag 2) of the chunks before it, walking back until one has a
+// running total, and publishes its own; its free points then go to nodes
+// 2 + (total before it) + (rank within the chunk).  Chunks are taken in ticket
+// order by running blocks, so every chunk a block waits on is held by a
+// running block; the first chunk whose total reaches the count stops the rest
+// (a chunk after it that finds a predecessor unpublished gives up once it sees
+// the stop).  Every wait is bounded (kSampleTimeout).
+constexpr long long kHaltonSpinLimit = 1ll << 22;
+
+template <int D, int DP>
+__global__ void __launch_bounds__(kHaltonChunk) halton_free_kernel(SpaceArgs s, BoxArgs boxes, BoxGridArgs grid,
+                                                                   int* __restrict__ scratch,
+                                                                   float* __restrict__ X,
+                                                                   uint8_t* __restrict__ is_goal,
+                                                                   int* __restrict__ flags) {
+    __shared__ int s_chunk, s_quit, s_before, s_go;
+    __shared__ int s_warp[kHaltonChunk / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int* ticket = scratch;
+    int* stop = scratch + 1;
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(scratch + 4);
+    const long long need = (long long)s.n_sampled - 2;
+    const long long nchunks = (s.halton_cap + kHaltonChunk - 1) / kHaltonChunk;
+    constexpr unsigned long long kAgg = 1ull << 62, kInc = 2ull << 62, kVal = (1ull << 62) - 1;
+    for (;;) {
+        if (tid == 0) {
+            s_chunk = atomicAdd(ticket, 1);
+            s_quit = s_chunk >= nchunks || *(volatile int*)stop < s_chunk;
+        }
+        __syncthreads();
+        const int c = s_chunk;
+        if (s_quit) break;  // the same decision for the whole block
+        const long long k = 1 + (long long)c * kHaltonChunk + tid;
+        float x[D];
+        const bool ok = k <= s.halton_cap && halton_free_point<D, DP>(s, boxes, grid, k, x);
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (lane == 0) s_warp[warp] = __popc(m);
+        __syncthreads();
+        if (tid == 0) {
+            int count = 0;
+            for (int w = 0; w < kHaltonChunk / 32; ++w) count += s_warp[w];
+            long long before = 0;
+            int go = 1;
+            if (c > 0) {
+                __threadfence();
+                atomicExch(&status[c], kAgg | (unsigned long long)count);
+                long long spins = 0;
+                for (int j = c - 1; j >= 0;) {
+                    const unsigned long long v = atomicAdd(&status[j], 0ull);
+                    if ((v >> 62) == 0) {  // not published yet
+                        if (*(volatile int*)stop < c) { go = 0; break; }
+                        if (++spins > kHaltonSpinLimit) { atomicOr(flags, kSampleTimeout); go = 0; break; }
+                        continue;
+                    }
+                    before += (long long)(v & kVal);
+                    if ((v >> 62) == 2) break;
+                    --j;
+                }
+            }
+            if (go) {
+                const long long total = before + count;
+                __threadfence();
+                atomicExch(&status[c], kInc | (unsigned long long)total);
+                if (total >= need) atomicMin(stop, c);
+                else if (c == nchunks - 1) atomicOr(flags, kSampleExhausted);
+            }
+            s_before = (int)before;
+            s_go = go;
+        }
+        __syncthreads();
+        if (s_go && ok) {
+            int rank = __popc(m & ((1u << lane) - 1u));
+            for (int w = 0; w < warp; ++w) rank += s_warp[w];
+            const long long v = 2 + (long long)s_before + rank;
+            if (v < s.n_sampled) {
+#pragma unroll
+                for (int a = 0; a < D; ++a) X[(size_t)a * s.pitch + v] = x[a];
+                is_goal[v] = in_goal_ball(x, s.gd, s.gc, s.grho) ? 1 : 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int D, int DP>
 __global__ void __launch_bounds__(128) append_kernel(SpaceArgs s, BoxArgs boxes, const float* __restrict__ src,
                                                      int src_pitch, int first, int count, float* __restrict__ X,
                                                      uint8_t* __restrict__ is_goal, int* __restrict__ flags) {
@@ -100,10 +198,23 @@ __global__ void __launch_bounds__(kFillWarps * 32) fill_kernel(SpaceArgs s, cons
 // ------------------------------------------------------------------ launchers
 namespace {
 template <int D, int DP>
-cudaError_t sample_t(const SpaceArgs& s, BoxArgs b, const BoxGridArgs& grid, float* X, uint8_t* g, int* f,
-                     cudaStream_t st) {
+cudaError_t sample_t(const SpaceArgs& s, BoxArgs b, const BoxGridArgs& grid, void* scratch, float* X, uint8_t* g,
+                     int* f, cudaStream_t st) {
     if (s.sampler == GMT_SAMPLER_HALTON) {
-        halton_kernel<D, DP><<<1, kHaltonThreads, 0, st>>>(s, b, grid, X, g, f);
+        if (!scratch) {
+            halton_kernel<D, DP><<<1, kHaltonThreads, 0, st>>>(s, b, grid, X, g, f);
+            return cudaGetLastError();
+        }
+        halton_head_kernel<D, DP><<<1, kHaltonThreads, 0, st>>>(s, b, grid, X, g, f);
+        const long long need = (long long)s.n_sampled - 2;
+        if (need <= 0) return cudaGetLastError();
+        // about twice the chunks the nodes need when most points are free;
+        // blocks loop for more chunks when they are not
+        const long long nchunks = (s.halton_cap + kHaltonChunk - 1) / kHaltonChunk;
+        long long blocks = 2 * ((need + kHaltonChunk - 1) / kHaltonChunk) + 8;
+        if (blocks > nchunks) blocks = nchunks;
+        if (blocks > 1024) blocks = 1024;
+        halton_free_kernel<D, DP><<<(unsigned)blocks, kHaltonChunk, 0, st>>>(s, b, grid, (int*)scratch, X, g, f);
         return cudaGetLastError();
     }
     const int staged = b.count > 0 && b.count <= 4096 / DP;
@@ -141,20 +252,20 @@ cudaError_t fill_t(const SpaceArgs& s, const float* X, const FillDir& out, const
         default: return cudaErrorInvalidValue;                       \
     }
 
-cudaError_t launch_sample(const SpaceArgs& s, BoxArgs b, const BoxGridArgs& grid, float* X, uint8_t* g, int* f,
-                          cudaStream_t st) {
-    if (s.kind == GMT_COST_DI) return sample_t<6, 3>(s, b, grid, X, g, f, st);
-    if (s.kind == GMT_COST_DUBINS) return sample_t<4, 3>(s, b, grid, X, g, f, st);
+cudaError_t launch_sample(const SpaceArgs& s, BoxArgs b, const BoxGridArgs& grid, void* scratch, float* X,
+                          uint8_t* g, int* f, cudaStream_t st) {
+    if (s.kind == GMT_COST_DI) return sample_t<6, 3>(s, b, grid, scratch, X, g, f, st);
+    if (s.kind == GMT_COST_DUBINS) return sample_t<4, 3>(s, b, grid, scratch, X, g, f, st);
     switch (s.d) {
-        case 2: return sample_t<2, 2>(s, b, grid, X, g, f, st);
-        case 3: return sample_t<3, 3>(s, b, grid, X, g, f, st);
-        case 4: return sample_t<4, 4>(s, b, grid, X, g, f, st);
-        case 5: return sample_t<5, 5>(s, b, grid, X, g, f, st);
-        case 6: return sample_t<6, 6>(s, b, grid, X, g, f, st);
-        case 7: return sample_t<7, 7>(s, b, grid, X, g, f, st);
-        case 8: return sample_t<8, 8>(s, b, grid, X, g, f, st);
-        case 9: return sample_t<9, 9>(s, b, grid, X, g, f, st);
-        case 10: return sample_t<10, 10>(s, b, grid, X, g, f, st);
+        case 2: return sample_t<2, 2>(s, b, grid, scratch, X, g, f, st);
+        case 3: return sample_t<3, 3>(s, b, grid, scratch, X, g, f, st);
+        case 4: return sample_t<4, 4>(s, b, grid, scratch, X, g, f, st);
+        case 5: return sample_t<5, 5>(s, b, grid, scratch, X, g, f, st);
+        case 6: return sample_t<6, 6>(s, b, grid, scratch, X, g, f, st);
+        case 7: return sample_t<7, 7>(s, b, grid, scratch, X, g, f, st);
+        case 8: return sample_t<8, 8>(s, b, grid, scratch, X, g, f, st);
+        case 9: return sample_t<9, 9>(s, b, grid, scratch, X, g, f, st);
+        case 10: return sample_t<10, 10>(s, b, grid, scratch, X, g, f, st);
         default: return cudaErrorInvalidValue;
     }
 }

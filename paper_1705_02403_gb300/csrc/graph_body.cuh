@@ -85,18 +85,24 @@ __host__ __device__ __forceinline__ uint32_t halton_prime(int a) {
 
 constexpr int kHaltonThreads = 512;
 
-// Halton SampleFree of one graph, run by a whole block of kHaltonThreads:
-// node 0 = x_init; node 1 = the first goal-mapped point (smallest k) in X, in
-// the goal ball and outside the boxes; nodes 2..n_sampled-1 = the free points
-// in the order of k (block-wide prefix sums keep that order).
+// Halton point k mapped onto X, and whether it is free (outside every box).
 template <int D, int DP>
-__device__ void halton_sample_block(const SpaceArgs& s, const BoxArgs& boxes, const BoxGridArgs& grid,
-                                    float* __restrict__ X, uint8_t* __restrict__ is_goal, int* __restrict__ flags) {
-    __shared__ int s_warp[kHaltonThreads / 32];
+__device__ __forceinline__ bool halton_free_point(const SpaceArgs& s, const BoxArgs& boxes, const BoxGridArgs& grid,
+                                                  long long k, float* x) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) x[a] = s.lo[a] + halton_unit((uint32_t)k, halton_prime(a)) * (s.hi[a] - s.lo[a]);
+    return !point_in_boxes<DP>(x, boxes, grid);
+}
+
+// Nodes 0 and 1 of a Halton SampleFree, run by a whole block: node 0 =
+// x_init (and its checks); node 1 = the first goal-mapped point (smallest k)
+// in X, in the goal ball and outside the boxes.  Writes their goal flags.
+template <int D, int DP>
+__device__ void halton_head_block(const SpaceArgs& s, const BoxArgs& boxes, const BoxGridArgs& grid,
+                                  float* __restrict__ X, uint8_t* __restrict__ is_goal, int* __restrict__ flags) {
     __shared__ int s_best;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const int N = s.n_sampled;
-    if (tid == 0) sample_node<D, DP>(s, boxes, grid, X, is_goal, flags, 0);  // x_init and its checks
+    const int tid = threadIdx.x;
+    if (tid == 0) sample_node<D, DP>(s, boxes, grid, X, is_goal, flags, 0);  // x_init, its checks and goal flag
     // node 1
     if (tid == 0) s_best = INT_MAX;
     __syncthreads();
@@ -125,15 +131,30 @@ __device__ void halton_sample_block(const SpaceArgs& s, const BoxArgs& boxes, co
         if (s_best == INT_MAX) {
             atomicOr(flags, kSampleExhausted);
         } else {
+            float x[D];
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 const float u = halton_unit((uint32_t)s_best, halton_prime(a));
                 float l = s.lo[a], h = s.hi[a];
                 if (a < s.gd) { l = s.gc[a] - s.grho; h = s.gc[a] + s.grho; }
-                X[(size_t)a * s.pitch + 1] = l + u * (h - l);
+                x[a] = l + u * (h - l);
+                X[(size_t)a * s.pitch + 1] = x[a];
             }
+            is_goal[1] = in_goal_ball(x, s.gd, s.gc, s.grho) ? 1 : 0;
         }
     }
+}
+
+// Halton SampleFree of one graph, run by a whole block of kHaltonThreads:
+// nodes 0 and 1 as halton_head_block; nodes 2..n_sampled-1 = the free points
+// in the order of k (block-wide prefix sums keep that order).
+template <int D, int DP>
+__device__ void halton_sample_block(const SpaceArgs& s, const BoxArgs& boxes, const BoxGridArgs& grid,
+                                    float* __restrict__ X, uint8_t* __restrict__ is_goal, int* __restrict__ flags) {
+    __shared__ int s_warp[kHaltonThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int N = s.n_sampled;
+    halton_head_block<D, DP>(s, boxes, grid, X, is_goal, flags);
     // nodes 2..N-1
     int got = 0;
     for (long long base = 1; got < N - 2; base += blockDim.x) {
@@ -144,12 +165,7 @@ __device__ void halton_sample_block(const SpaceArgs& s, const BoxArgs& boxes, co
         const long long k = base + tid;
         float x[D];
         bool ok = false;
-        if (k <= s.halton_cap) {
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-                x[a] = s.lo[a] + halton_unit((uint32_t)k, halton_prime(a)) * (s.hi[a] - s.lo[a]);
-            ok = !point_in_boxes<DP>(x, boxes, grid);
-        }
+        if (k <= s.halton_cap) ok = halton_free_point<D, DP>(s, boxes, grid, k, x);
         const unsigned m = __ballot_sync(0xffffffffu, ok);
         if (lane == 0) s_warp[warp] = __popc(m);
         __syncthreads();

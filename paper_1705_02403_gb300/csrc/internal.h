@@ -70,13 +70,28 @@ cudaError_t launch_box_grid(int dp, BoxArgs boxes, const BoxGridArgs& grid, int*
                             int* big, int* nbig, cudaStream_t st);
 
 // Flags written by the sampling kernel.
-enum { kSampleBadInit = 1, kSampleExhausted = 2, kSampleBadAppend = 4 };
+enum { kSampleBadInit = 1, kSampleExhausted = 2, kSampleBadAppend = 4, kSampleTimeout = 8 };
+
+// Halton SampleFree over several blocks: chunks of kHaltonChunk consecutive
+// points, taken in order from a ticket; each publishes its count of free
+// points, then (looking back over its predecessors) the running total, so its
+// free points land at nodes 2 + total-before-it + rank, in the order of k.
+constexpr int kHaltonChunk = 256;
+// Scratch of the multi-block sampler: [0] ticket, [1] first chunk whose running
+// total reaches the node count (INT_MAX before), then one 64-bit status word
+// per chunk (8-byte aligned).  Zeroed, with [1] set high, before each launch.
+inline size_t halton_scratch_bytes(long long cap) {
+    return 16 + (size_t)((cap + kHaltonChunk - 1) / kHaltonChunk) * 8;
+}
 
 // sample.cu / graph.cu
 // SampleFree with s.sampler's method (Halton: one block compacts the free
 // points in order).
 // grid: a box grid of `boxes` (use = 0 to scan them).
-cudaError_t launch_sample(const SpaceArgs& s, BoxArgs boxes, const BoxGridArgs& grid, float* X, uint8_t* is_goal,
+// scratch: halton_scratch_bytes(s.halton_cap) bytes prepared as described
+// there (Halton sampler only; NULL runs the single-block sampler).
+cudaError_t launch_sample(const SpaceArgs& s, BoxArgs boxes, const BoxGridArgs& grid, void* scratch, float* X,
+                          uint8_t* is_goal,
                           int* flags, cudaStream_t st);
 cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* out_count,
                              cudaStream_t st);

@@ -244,6 +244,35 @@ def test_halton_sampling_matches_the_oracle(O, P, case):
     assert_same(O, G, *oracle_run(O, pb))
 
 
+def test_halton_free_points_over_many_chunks(O, P):
+    # The free Halton points are gathered over many blocks, a chunk of 256
+    # points each, in the order of k.  A box over 64% of the square leaves
+    # about one point in three free, so the blocks loop for more chunks; the
+    # samples must still be the oracle's, node for node.
+    from paper_1705_02403_gb300 import _native as N
+    box = (np.array([[0.1, 0.1]], np.float32), np.array([[0.9, 0.9]], np.float32))
+    pb = envgen.geometric(76, d=2, n=60000, nbox=0, r=0.004).with_(box_lo=box[0], box_hi=box[1], sampler=1)
+    G = gpu_run(P, pb, build_only=True)
+    X, goal = O.sample_halton(pb)
+    assert np.array_equal(bits(G["X"]), bits(X)) and np.array_equal(G["goal"], goal)
+    # n = 1 and 2: x_init and the goal node only, then one free point
+    for n in (1, 2):
+        pb = envgen.geometric(77, d=2, n=n, nbox=4, r=0.5).with_(sampler=1)
+        G = gpu_run(P, pb, build_only=True)
+        X, goal = O.sample_halton(pb)
+        assert np.array_equal(bits(G["X"]), bits(X)) and np.array_equal(G["goal"], goal)
+    # too few free points within the attempt cap: an error on both sides
+    pb = envgen.geometric(78, d=2, n=5000, nbox=0, r=0.05).with_(
+        box_lo=np.array([[0.001, 0.0]], np.float32), box_hi=np.array([[1.0, 1.0]], np.float32),
+        x_init=np.array([0.0005, 0.5], np.float32), goal_center=np.array([0.0005, 0.9], np.float32),
+        goal_radius=0.0004, sampler=1)
+    with pytest.raises(ValueError):
+        O.sample_halton(pb)
+    with pytest.raises(N.GmtError) as e:
+        P.Planner(pb).build()
+    assert e.value.status == N.GMT_ERR_INVALID
+
+
 @pytest.mark.parametrize("case", ["2d_600", "3d_300", "di_forest_1500", "2d_outside", "2d_big_and_degenerate"])
 def test_many_boxes_use_the_box_grid(O, P, case):
     # From 128 boxes the plan and SampleFree list each box in the grid cells
