@@ -32,7 +32,7 @@ __device__ __forceinline__ void sample_node(const SpaceArgs& s, const BoxArgs& b
             x[a] = s.x0[a];
             ok = ok && s.lo[a] <= x[a] && x[a] <= s.hi[a];
         }
-        if (!ok || in_any_box<DP>(x, boxes.lo, boxes.hi, boxes.count)) atomicOr(flags, kSampleBadInit);
+        if (!ok || point_in_boxes<DP>(x, boxes, grid)) atomicOr(flags, kSampleBadInit);
     } else {
         bool ok = false;
         for (int t = 0; t < s.max_attempts && !ok; ++t) {
