@@ -40,7 +40,7 @@ METRIC = "ms/plan p50/p99 & edges checked/s; learned+batched vs plain at equal p
 # ncu captures summarised in profiles/plan_kernel_double_integrator_6d_n4096.md
 # and profiles/plan_kernel_geometric_2d_n1024.md.
 # Set to None whenever plan_kernel changes until it is captured again.
-PLAN_KERNEL_DRAM_BYTES = {"di6": 2112768, "geo2d": 419328}
+PLAN_KERNEL_DRAM_BYTES = {"di6": None, "geo2d": None}
 
 
 def parse():
@@ -345,7 +345,9 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_extras:
         line["batched"] = bench_batched(dev, flush)
         line["serving"] = bench_serving(local_rank)
-        line["gpu_launches_extras"] = "batched: 7 launches per group per batch (replayed CUDA graph); serving: 3 per request"
+        line["dubins"] = bench_dubins(dev, flush)
+        line["gpu_launches_extras"] = ("batched: 7 launches per group per batch (replayed CUDA graph); serving: 3 per "
+                                       "request; dubins: 9-10 per build, 1 per plan")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         seeds_cpu = [seeds[args.warmup + j] for j in range(3)]
         rows = 256 if args.workload == "di6" else 1025
@@ -406,6 +408,37 @@ def bench_batched(dev, flush, reps=5):
                           "cluster": cluster, "threads": threads},
             "plan_stage_roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                                     "frac": achieved / hbm, "algorithmic_bytes": plan_bytes, "traffic": None}}
+
+
+def bench_dubins(dev, flush, reps=20):
+    """Dubins airplane forest (n = 5000, lambda = 1, Halton samples, rho = 0.05,
+    r = 0.2; ten trunks as 150 and as 5000 boxes): per repetition the L2 is
+    flushed, then the graph is built and planned; library event times of the
+    build stages and of the plan kernel, p50 over the repetitions."""
+    import torch
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300 import envgen
+    from paper_1705_02403_gb300.planner import Planner
+    out = {"workload": "Dubins airplane forest, n=5000, lambda=1, Halton, rho=0.05, r=0.2"}
+    for strips in (15, 500):
+        pb = envgen.dubins_forest(0, n=5000, strips=strips, sampler=1)
+        pl = Planner(pb, device=dev).build()
+        N.gmt_graph_set_profiling(pl.graph, True)
+        plan_ms, build_ms, infos = [], [], []
+        for _ in range(reps):
+            flush.zero_()
+            pl.build()
+            infos.append(pl.plan())
+            torch.cuda.synchronize()
+            p = N.gmt_graph_get_profile(pl.graph)
+            plan_ms.append(p["plan_ms"])
+            build_ms.append(p["sample_ms"] + p["pair_ms"] + p["transpose_ms"] + p["scan_ms"] + p["fill_ms"])
+        edges = float(np.mean([i["push_edges"] + i["pull_edges"] for i in infos]))
+        out[f"boxes_{10 * strips}"] = {
+            "plan_ms_p50": pct(plan_ms, 50), "plan_ms_p99": pct(plan_ms, 99), "build_ms_p50": pct(build_ms, 50),
+            "edges_checked_per_s_plan": edges / (pct(plan_ms, 50) / 1e3), "E": int(pl.view().E),
+            "path_cost": float(infos[-1]["path_cost"]), "status": int(infos[-1]["status"])}
+    return out
 
 
 def bench_serving(local_rank):

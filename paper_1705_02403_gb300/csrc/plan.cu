@@ -150,18 +150,31 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
                     const int z = __shfl_sync(0xffffffffu, e.x, __ffs(gm) - 1);
                     const int e0 = __ldg(&A.out_row[z]), e1 = __ldg(&A.out_row[z + 1]);
                     if (lane == 0) n_push += (unsigned long long)(e1 - e0);
-                    for (int eb = e0; eb < e1; eb += 32) {
-                        const int ei = eb + lane;
-                        bool want = false;
-                        int x = -1;
-                        if (ei < e1) {
-                            x = __ldg(&A.out_col[ei]);
+                    // two chunks of 32 at a time: their column loads, their claims,
+                    // and one slot reservation, each issued together
+                    for (int eb = e0; eb < e1; eb += 2 * 32) {
+                        int xs[2];
+                        bool want[2];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int ei = eb + 32 * u + lane;
+                            xs[u] = ei < e1 ? __ldg(&A.out_col[ei]) : -1;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 2; ++u)
                             // one atomic both tests "unexplored" (stamp < INT_MAX) and
                             // claims x for this iteration (stamp < it before)
-                            want = atomicMax(&A.stamp[x], it) < it;
-                        }
-                        const int sc = warp_append_slot(want, &ctl->cand_count[p]);
-                        if (want) A.list_cand[sc] = x;
+                            want[u] = xs[u] >= 0 && atomicMax(&A.stamp[xs[u]], it) < it;
+                        const unsigned m0 = __ballot_sync(0xffffffffu, want[0]);
+                        const unsigned m1 = __ballot_sync(0xffffffffu, want[1]);
+                        const int n0 = __popc(m0), total = n0 + __popc(m1);
+                        if (total == 0) continue;
+                        int slot = 0;
+                        if (lane == 0) slot = atomicAdd(&ctl->cand_count[p], total);
+                        slot = __shfl_sync(0xffffffffu, slot, 0);
+                        const unsigned below = (1u << lane) - 1u;
+                        if (want[0]) A.list_cand[slot + __popc(m0 & below)] = xs[0];
+                        if (want[1]) A.list_cand[slot + n0 + __popc(m1 & below)] = xs[1];
                     }
                 }
             }
@@ -185,14 +198,29 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
                 float sx[D];  // issued now, used by the check after the reduction
 #pragma unroll
                 for (int a = 0; a < D; ++a) sx[a] = __ldg(&A.X[(size_t)a * A.pitch + x]);
+                // Each lane keeps the minimum (cost, index) of its entries: a
+                // total order, so the order of the entries does not matter.
+                // Four chunks of 32 at a time: their column and cost loads, then
+                // their snapshot gathers, each issued together.
                 float bc = INF;
                 int by = INT_MAX, be = -1;
-                for (int e = r0 + lane; e < r1; e += 32) {
-                    const int y = __ldg(&A.in_col[e]);
-                    const float oc = ldcg_f(&A.ocost[y]);
-                    if (oc < INF) {
-                        const float c = oc + __ldg(&A.in_cost[e]);
-                        if (c < bc || (c == bc && y < by)) { bc = c; by = y; be = e; }
+                for (int eb = r0; eb < r1; eb += 4 * 32) {
+                    int ys[4];
+                    float ic[4], oc[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int e = eb + 32 * u + lane;
+                        ys[u] = e < r1 ? __ldg(&A.in_col[e]) : -1;
+                        ic[u] = e < r1 ? __ldg(&A.in_cost[e]) : 0.0f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) oc[u] = ys[u] >= 0 ? ldcg_f(&A.ocost[ys[u]]) : INF;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (oc[u] < INF) {
+                            const float c = oc[u] + ic[u];
+                            if (c < bc || (c == bc && ys[u] < by)) { bc = c; by = ys[u]; be = eb + 32 * u + lane; }
+                        }
                     }
                 }
 #pragma unroll
