@@ -245,7 +245,8 @@ gmt_status gmt_graph_set_launch(gmt_graph* graph, int32_t blocks, int32_t thread
 /* ---------------------------------------------------------------- batches
  * Many independent planning problems in one call (an extension of the paper's
  * single-query method: the same Algorithm 1 on every query).  Supported
- * queries: double integrator, and geometric with dim 2 or 3. */
+ * queries: double integrator, Dubins airplane (turn_radius > 0, r > 0), and
+ * geometric with dim 2 or 3. */
 typedef struct {
     gmt_space space;
     gmt_boxes boxes;             /* DEVICE arrays, as for gmt_build_graph */

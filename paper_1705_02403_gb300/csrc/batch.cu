@@ -39,6 +39,7 @@ struct QueryDev {
     int* in_col;
     float* in_cost;
     float* in_tau;
+    float* in_path;  // Dubins airplane: (t, p, q, word) per in-edge, 16-byte aligned
     long long edge_cap;
     // cell-list neighbour build (2D/3D geometric queries with a small radius)
     CellGrid cg;
@@ -100,6 +101,16 @@ __global__ void __launch_bounds__(kDIRows, 8) batch_mask_di_kernel(const QueryDe
     const int rb = (q.s.N + kDIRows - 1) / kDIRows;
     const int t = (int)(b - off[k]);
     mask_di_tile(q.s, q.X, q.mask, q.out_count, t % rb, t / rb);
+}
+
+__global__ void __launch_bounds__(kDubRows) batch_mask_dubins_kernel(const QueryDev* __restrict__ Q,
+                                                                    const long long* __restrict__ off, int nq) {
+    const long long b = blockIdx.x;
+    const int k = find_query(off, nq, b);
+    const QueryDev& q = Q[k];
+    const int rb = (q.s.N + kDubRows - 1) / kDubRows;
+    const int t = (int)(b - off[k]);
+    mask_dubins_tile(q.s, q.X, q.mask, q.out_count, t % rb, t / rb);
 }
 
 __global__ void __launch_bounds__(256) batch_transpose_kernel(const QueryDev* __restrict__ Q,
@@ -174,11 +185,12 @@ __global__ void __launch_bounds__(kFillWarps * 32) batch_fill_kernel(const Query
     const int k = find_query(off, nq, w);
     const QueryDev& q = Q[k];
     if (q.use_cells) return;
-    const bool incoming = blockIdx.y == 1;  // in-rows (double integrator)
+    const bool incoming = blockIdx.y == 1;  // in-rows (double integrator, Dubins airplane)
     const int* row = incoming ? q.in_row : q.out_row;
     if ((long long)row[q.s.N] > q.edge_cap) return;
     if (incoming)
-        fill_row<KIND, D, true>(q.s, q.X, q.maskT, q.in_row, q.in_col, q.in_cost, q.in_tau, nullptr, (int)(w - off[k]));
+        fill_row<KIND, D, true>(q.s, q.X, q.maskT, q.in_row, q.in_col, q.in_cost, q.in_tau, q.in_path,
+                                (int)(w - off[k]));
     else
         fill_row<KIND, D, false>(q.s, q.X, q.mask, q.out_row, q.out_col, q.out_cost, q.out_tau, nullptr,
                                  (int)(w - off[k]));
@@ -193,11 +205,12 @@ void sample_g(const QueryDev* Q, const long long* off, int nq, long long total, 
 template <int KIND, int D>
 void mask_g(const QueryDev* Q, const long long* off, int nq, long long tiles, cudaStream_t st) {
     if (KIND == GMT_COST_DI) batch_mask_di_kernel<<<(unsigned)tiles, kDIRows, 0, st>>>(Q, off, nq);
+    else if (KIND == GMT_COST_DUBINS) batch_mask_dubins_kernel<<<(unsigned)tiles, kDubRows, 0, st>>>(Q, off, nq);
     else batch_mask_kernel<KIND, D><<<(unsigned)tiles, kMaskRows, 0, st>>>(Q, off, nq);
 }
 template <int KIND, int D>
 void fill_g(const QueryDev* Q, const long long* off, int nq, long long rows, cudaStream_t st) {
-    const dim3 grid((unsigned)((rows + kFillWarps - 1) / kFillWarps), KIND == GMT_COST_DI ? 2 : 1);
+    const dim3 grid((unsigned)((rows + kFillWarps - 1) / kFillWarps), KIND == GMT_COST_EUCLID ? 1 : 2);
     batch_fill_kernel<KIND, D><<<grid, kFillWarps * 32, 0, st>>>(Q, off, nq);
 }
 }  // namespace
@@ -205,6 +218,7 @@ void fill_g(const QueryDev* Q, const long long* off, int nq, long long rows, cud
 cudaError_t batch_sample(int kind, int d, const QueryDev* Q, const long long* off, int nq, long long total,
                          bool halton, cudaStream_t st) {
     if (kind == GMT_COST_DI) sample_g<6, 3>(Q, off, nq, total, halton, st);
+    else if (kind == GMT_COST_DUBINS) sample_g<4, 3>(Q, off, nq, total, halton, st);
     else if (d == 2) sample_g<2, 2>(Q, off, nq, total, halton, st);
     else if (d == 3) sample_g<3, 3>(Q, off, nq, total, halton, st);
     else return cudaErrorInvalidValue;
@@ -214,6 +228,7 @@ cudaError_t batch_mask(int kind, int d, const QueryDev* Q, const long long* off,
                        cudaStream_t st) {
     if (tiles == 0) return cudaSuccess;  // every query of the group uses the cell list
     if (kind == GMT_COST_DI) mask_g<GMT_COST_DI, 6>(Q, off, nq, tiles, st);
+    else if (kind == GMT_COST_DUBINS) mask_g<GMT_COST_DUBINS, 4>(Q, off, nq, tiles, st);
     else if (d == 2) mask_g<GMT_COST_EUCLID, 2>(Q, off, nq, tiles, st);
     else if (d == 3) mask_g<GMT_COST_EUCLID, 3>(Q, off, nq, tiles, st);
     else return cudaErrorInvalidValue;
@@ -246,6 +261,7 @@ cudaError_t batch_cells_fill(int d, const QueryDev* Q, const long long* off, int
 cudaError_t batch_fill(int kind, int d, const QueryDev* Q, const long long* off, int nq, long long rows,
                        cudaStream_t st) {
     if (kind == GMT_COST_DI) fill_g<GMT_COST_DI, 6>(Q, off, nq, rows, st);
+    else if (kind == GMT_COST_DUBINS) fill_g<GMT_COST_DUBINS, 4>(Q, off, nq, rows, st);
     else if (d == 2) fill_g<GMT_COST_EUCLID, 2>(Q, off, nq, rows, st);
     else if (d == 3) fill_g<GMT_COST_EUCLID, 3>(Q, off, nq, rows, st);
     else return cudaErrorInvalidValue;
@@ -372,8 +388,12 @@ gmt_status check_query(const gmt_query& Qh, int k) {
             return bfail(GMT_ERR_INVALID, "batched geometric queries need dim 2 or 3 and pos_dim == dim" + at);
     } else if (sp.kind == GMT_COST_DI) {
         if (sp.dim != 6 || sp.pos_dim != 3) return bfail(GMT_ERR_INVALID, "double integrator needs dim 6, pos_dim 3" + at);
+    } else if (sp.kind == GMT_COST_DUBINS) {
+        if (sp.dim != 4 || sp.pos_dim != 3) return bfail(GMT_ERR_INVALID, "Dubins airplane needs dim 4, pos_dim 3" + at);
+        if (!(Qh.params.turn_radius > 0.0f) || !std::isfinite(Qh.params.turn_radius) || !(Qh.params.r > 0.0f))
+            return bfail(GMT_ERR_INVALID, "a Dubins airplane query needs turn_radius > 0 and r > 0" + at);
     } else {
-        return bfail(GMT_ERR_INVALID, "batched queries are geometric or double integrator" + at);
+        return bfail(GMT_ERR_INVALID, "unknown cost kind" + at);
     }
     for (int a = 0; a < sp.dim; ++a)
         if (!(sp.lo[a] < sp.hi[a])) return bfail(GMT_ERR_INVALID, "state bounds need lo < hi" + at);
@@ -469,13 +489,13 @@ gmt_status enqueue_build_front(gmt_batch* b, cudaStream_t st) {
               "batched sample kernel");
         BCUDA(batch_mask(g.kind, g.d, Q, g.off_tiles.as<long long>(), nq, g.tiles, st), "batched pair filter");
         if (g.any_cells) BCUDA(batch_cells_front(g.d, Q, g.off_nodes.as<long long>(), nq, g.nodes, st), "batched cells");
-        if (g.kind == GMT_COST_DI) {
+        if (g.kind != GMT_COST_EUCLID) {  // directed costs: the in-neighbour bit matrix and rows
             const long long warps = g.tasks;
             batch_transpose_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(Q, g.off_tasks.as<long long>(), nq);
             BCUDA(cudaGetLastError(), "batched transpose");
         }
         batch_scan_kernel<<<nq, 1024, 0, st>>>(Q, 0);
-        if (g.kind == GMT_COST_DI) batch_scan_kernel<<<nq, 1024, 0, st>>>(Q, 1);
+        if (g.kind != GMT_COST_EUCLID) batch_scan_kernel<<<nq, 1024, 0, st>>>(Q, 1);
         BCUDA(cudaGetLastError(), "batched scan");
     }
     return GMT_OK;
@@ -602,7 +622,7 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         } else {
             mo[k] = ms; ms += (size_t)W * P;
         }
-        if (Qh.space.kind == GMT_COST_DI) { mto[k] = mts; mts += (size_t)W * P; }
+        if (Qh.space.kind != GMT_COST_EUCLID) { mto[k] = mts; mts += (size_t)W * P; }
         co[k] = cs; cs += 2 * (size_t)N;
         ro[k] = rs; rs += 2 * (size_t)(N + 1);
         po[k] = ps; ps += N;
@@ -648,6 +668,7 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         s.halton_cap = (long long)s.max_attempts + 64LL * s.N;
         s.r = b->r[k];
         s.r2_threshold = euclid_threshold_b(s.r);
+        s.rho = s.kind == GMT_COST_DUBINS ? Qh.params.turn_radius : 0.0f;
         d.boxes = BoxArgs{Qh.boxes.count, Qh.boxes.lo, Qh.boxes.hi};
         d.X = b->X.as<float>() + xo[k];
         d.is_goal = b->goal.as<uint8_t>() + go[k];
@@ -663,11 +684,11 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
             d.cell_start = d.cell_cnt + cgs[k].ncells;
         }
         d.cell_info = b->cell_info.as<int>() + 2 * k;
-        d.maskT = s.kind == GMT_COST_DI ? b->maskT.as<uint32_t>() + mto[k] : nullptr;
+        d.maskT = s.kind != GMT_COST_EUCLID ? b->maskT.as<uint32_t>() + mto[k] : nullptr;
         d.out_count = b->counts.as<int>() + co[k];
         d.in_count = d.out_count + s.N;
         d.out_row = b->rows.as<int>() + ro[k];
-        d.in_row = s.kind == GMT_COST_DI ? d.out_row + (s.N + 1) : d.out_row;
+        d.in_row = s.kind != GMT_COST_EUCLID ? d.out_row + (s.N + 1) : d.out_row;
         d.edge_cap = 0;
     }
     // per-group work offsets and descriptors
@@ -685,10 +706,13 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
             g.any_cells = g.any_cells || use_cells[k];
             g.any_halton = g.any_halton || queries[k].params.sampler == GMT_SAMPLER_HALTON;
             if (use_cells[k]) g.cell_words = std::max(g.cell_words, cell_fill_words(cgs[k], N));
-            const long long tiles = use_cells[k] ? 0
-                                    : g.kind == GMT_COST_DI
-                                        ? (long long)((N + kDIRows - 1) / kDIRows) * ((W + kDIWords - 1) / kDIWords)
-                                        : (long long)((N + kMaskRows - 1) / kMaskRows) * ((W + kMaskWords - 1) / kMaskWords);
+            const long long tiles =
+                use_cells[k] ? 0
+                : g.kind == GMT_COST_DI
+                    ? (long long)((N + kDIRows - 1) / kDIRows) * ((W + kDIWords - 1) / kDIWords)
+                : g.kind == GMT_COST_DUBINS
+                    ? (long long)((N + kDubRows - 1) / kDubRows) * ((W + kDubWords - 1) / kDubWords)
+                    : (long long)((N + kMaskRows - 1) / kMaskRows) * ((W + kMaskWords - 1) / kMaskWords);
             on[i + 1] = on[i] + N;
             ot[i + 1] = ot[i] + tiles;
             ow[i + 1] = ow[i] + (long long)W * W;
@@ -739,25 +763,35 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         if (flags[k] & kSampleExhausted)
             return bfail(GMT_ERR_INVALID, "sampling exhausted max_attempts (query " + std::to_string(k) + ")");
     }
-    size_t ei = 0;
-    std::vector<size_t> eo(q);
+    // edge slices: ints (columns) and floats; a Dubins query's float slice
+    // starts with its in-edge words (4 floats each), kept 16-byte aligned
+    size_t ei = 0, ef = 0;
+    std::vector<size_t> eo(q), fo(q);
     for (int k = 0; k < q; ++k) {
         b->E[k] = b->h_rows[k];
+        const size_t E = (size_t)b->E[k];
+        const int kind = queries[k].space.kind;
         eo[k] = ei;
-        ei += (size_t)b->E[k] * (queries[k].space.kind == GMT_COST_DI ? 2 : 1);
+        ei += E * (kind == GMT_COST_EUCLID ? 1 : 2);
+        fo[k] = ef;
+        ef += (kind == GMT_COST_EUCLID ? E : kind == GMT_COST_DI ? 4 * E : 6 * E);
+        ef = (ef + 3) / 4 * 4;
     }
     BCUDA(b->edges_i.need(ei * 4 + 4), "edge arena");
-    BCUDA(b->edges_f.need(ei * 2 * 4 + 4), "edge arena");
+    BCUDA(b->edges_f.need(ef * 4 + 16), "edge arena");
     for (int k = 0; k < q; ++k) {
         QueryDev& d = b->qd[k];
         const size_t E = (size_t)b->E[k];
-        const bool di = d.s.kind == GMT_COST_DI;
+        const bool di = d.s.kind == GMT_COST_DI, dub = d.s.kind == GMT_COST_DUBINS, directed = di || dub;
+        float* f = b->edges_f.as<float>() + fo[k];
+        d.in_path = dub ? f : nullptr;
+        if (dub) f += 4 * E;
         d.out_col = b->edges_i.as<int>() + eo[k];
-        d.out_cost = b->edges_f.as<float>() + 2 * eo[k];
-        d.out_tau = di ? d.out_cost + E : nullptr;
-        d.in_col = di ? d.out_col + E : d.out_col;
-        d.in_cost = di ? d.out_cost + 2 * E : d.out_cost;
-        d.in_tau = di ? d.out_cost + 3 * E : nullptr;
+        d.out_cost = f;
+        d.out_tau = di ? f + E : nullptr;
+        d.in_col = directed ? d.out_col + E : d.out_col;
+        d.in_cost = di ? f + 2 * E : dub ? f + E : d.out_cost;
+        d.in_tau = di ? f + 3 * E : nullptr;
         d.edge_cap = (long long)E;
     }
     // plan arguments, order (largest edge count first), scratch
@@ -777,6 +811,8 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
             a.X = d.X; a.is_goal = d.is_goal;
             a.out_row = d.out_row; a.out_col = d.out_col;
             a.in_row = d.in_row; a.in_col = d.in_col; a.in_cost = d.in_cost; a.in_tau = d.in_tau;
+            a.in_path = d.in_path;
+            a.rho = d.s.rho;
             a.boxes = d.boxes;
             for (int c = 0; c < 3 && c < d.s.dp; ++c) { a.pos_lo[c] = Qh.space.lo[c]; a.pos_hi[c] = Qh.space.hi[c]; }
             a.r = d.s.r;
@@ -924,6 +960,8 @@ gmt_status gmt_batch_get_view(const gmt_batch* b, int32_t k, gmt_graph_view* v, 
     v->out_row = d.out_row; v->out_col = d.out_col; v->out_cost = d.out_cost;
     v->in_row = d.in_row; v->in_col = d.in_col; v->in_cost = d.in_cost;
     v->out_tau = d.out_tau; v->in_tau = d.in_tau;
+    v->turn_radius = d.s.rho;
+    v->in_path = d.in_path;
     if (path) *path = b->path.as<int>() + (b->node_base[k]);
     return GMT_OK;
 }

@@ -557,14 +557,16 @@ int batch_teams_t(int threads, int cluster) {
 }
 }  // namespace
 
-// The batched path supports the double integrator and 2D/3D geometric queries
-// (not the Dubins airplane).
+// The batched path supports the double integrator, the Dubins airplane and
+// 2D/3D geometric queries.
 cudaError_t launch_plan_batch(int kind, int dp, const PlanArgs* queries, const int* order, int nq, int* next,
                               int* slot, const BatchScratch& scratch, int teams, int threads, int cluster,
                               int max_boxes, cudaStream_t st) {
-    if (kind == GMT_COST_DUBINS) return cudaErrorInvalidValue;
     if (kind == GMT_COST_DI)
         return plan_batch_t<GMT_COST_DI, 3>(queries, order, nq, next, slot, scratch, teams, threads, cluster, max_boxes, st);
+    if (kind == GMT_COST_DUBINS)
+        return plan_batch_t<GMT_COST_DUBINS, 3>(queries, order, nq, next, slot, scratch, teams, threads, cluster,
+                                                max_boxes, st);
     if (dp == 2)
         return plan_batch_t<GMT_COST_EUCLID, 2>(queries, order, nq, next, slot, scratch, teams, threads, cluster,
                                                 max_boxes, st);
@@ -575,8 +577,8 @@ cudaError_t launch_plan_batch(int kind, int dp, const PlanArgs* queries, const i
 }
 
 int plan_batch_max_teams(int kind, int dp, int threads, int cluster) {
-    if (kind == GMT_COST_DUBINS) return 0;
     if (kind == GMT_COST_DI) return batch_teams_t<GMT_COST_DI, 3>(threads, cluster);
+    if (kind == GMT_COST_DUBINS) return batch_teams_t<GMT_COST_DUBINS, 3>(threads, cluster);
     if (dp == 2) return batch_teams_t<GMT_COST_EUCLID, 2>(threads, cluster);
     if (dp == 3) return batch_teams_t<GMT_COST_EUCLID, 3>(threads, cluster);
     return 0;

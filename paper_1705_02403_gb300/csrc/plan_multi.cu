@@ -76,7 +76,7 @@ __device__ __forceinline__ int find_node_query(const int* base, int nq, int g) {
 template <int KIND, int DP>
 __device__ bool pull_candidate(const PlanArgs* __restrict__ Ap, LockSmem& sm, int q, const float* __restrict__ ocost,
                                int* stamp, int x, PlanCtl* team_ctl, float* out_cost) {
-    constexpr int D = KIND == GMT_COST_DI ? 6 : DP;
+    constexpr int D = KIND == GMT_COST_DI ? 6 : (KIND == GMT_COST_DUBINS ? 4 : DP);
     const int lane = threadIdx.x & 31;
     const float INF = f_inf();
     const int* in_row = Ap->in_row;
@@ -88,14 +88,27 @@ __device__ bool pull_candidate(const PlanArgs* __restrict__ Ap, LockSmem& sm, in
     float sx[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) sx[a] = __ldg(&X[(size_t)a * pitch + x]);
+    // each lane's minimum (cost, index) over its entries (a total order);
+    // four chunks' loads, then their snapshot gathers, issued together
     float bc = INF;
     int by = INT_MAX, be = -1;
-    for (int e = r0 + lane; e < r1; e += 32) {
-        const int y = __ldg(&in_col[e]);
-        const float oc = ldcg_f(&ocost[y]);
-        if (oc < INF) {
-            const float c = oc + __ldg(&in_cost[e]);
-            if (c < bc || (c == bc && y < by)) { bc = c; by = y; be = e; }
+    for (int eb = r0; eb < r1; eb += 4 * 32) {
+        int ys[4];
+        float ic[4], oc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = eb + 32 * u + lane;
+            ys[u] = e < r1 ? __ldg(&in_col[e]) : -1;
+            ic[u] = e < r1 ? __ldg(&in_cost[e]) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) oc[u] = ys[u] >= 0 ? ldcg_f(&ocost[ys[u]]) : INF;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (oc[u] < INF) {
+                const float c = oc[u] + ic[u];
+                if (c < bc || (c == bc && ys[u] < by)) { bc = c; by = ys[u]; be = eb + 32 * u + lane; }
+            }
         }
     }
 #pragma unroll
@@ -130,6 +143,16 @@ __device__ bool pull_candidate(const PlanArgs* __restrict__ Ap, LockSmem& sm, in
         if (KIND == GMT_COST_EUCLID) {
             free_edge =
                 segment_free_warp<DP>(sy, sx, __ldg(&in_cost[be]), Ap->seg_spacing, blo, bhi, nbox, Ap->grid);
+        } else if (KIND == GMT_COST_DUBINS) {
+            DubPath P;
+            if (Ap->in_path) {
+                const float4 w = __ldg(reinterpret_cast<const float4*>(Ap->in_path) + be);
+                P = DubPath{__float_as_int(w.w), w.x, w.y, w.z, ((w.x + w.y) + w.z) * Ap->rho};
+            } else {
+                P = dubins_path(sy, sx, Ap->rho);
+            }
+            free_edge = dubins_free_warp(sy, sx, P, __ldg(&in_cost[be]), Ap->seg_spacing, Ap->rho, Ap->pos_lo,
+                                         Ap->pos_hi, blo, bhi, nbox, Ap->grid);
         } else {
             const float tau = Ap->in_tau ? __ldg(&Ap->in_tau[be]) : di_tau(di_coef(sy, sx), Ap->r);
             free_edge = trajectory_free_warp(sy, sx, tau, Ap->traj_points, Ap->pos_lo, Ap->pos_hi, blo, bhi, nbox,
@@ -541,16 +564,17 @@ int lockstep_blocks_t(int threads) {
 
 cudaError_t launch_plan_lockstep(int kind, int dp, const PlanArgs* queries, int nq, const LockScratch& s, int blocks,
                                  int threads, cudaStream_t st) {
-    if (nq < 1 || nq > kLockMaxQueries || blocks < 1 || kind == GMT_COST_DUBINS) return cudaErrorInvalidValue;
+    if (nq < 1 || nq > kLockMaxQueries || blocks < 1) return cudaErrorInvalidValue;
     if (kind == GMT_COST_DI) return lockstep_t<GMT_COST_DI, 3>(queries, nq, s, blocks, threads, st);
+    if (kind == GMT_COST_DUBINS) return lockstep_t<GMT_COST_DUBINS, 3>(queries, nq, s, blocks, threads, st);
     if (dp == 2) return lockstep_t<GMT_COST_EUCLID, 2>(queries, nq, s, blocks, threads, st);
     if (dp == 3) return lockstep_t<GMT_COST_EUCLID, 3>(queries, nq, s, blocks, threads, st);
     return cudaErrorInvalidValue;
 }
 
 int plan_lockstep_max_blocks(int kind, int dp, int threads) {
-    if (kind == GMT_COST_DUBINS) return 0;
     if (kind == GMT_COST_DI) return lockstep_blocks_t<GMT_COST_DI, 3>(threads);
+    if (kind == GMT_COST_DUBINS) return lockstep_blocks_t<GMT_COST_DUBINS, 3>(threads);
     if (dp == 2) return lockstep_blocks_t<GMT_COST_EUCLID, 2>(threads);
     if (dp == 3) return lockstep_blocks_t<GMT_COST_EUCLID, 3>(threads);
     return 0;

@@ -34,7 +34,7 @@ def oracle_of(O, pb):
     X, goal = O.sample_halton(pb) if pb.sampler == 1 else O.sample(pb)
     r0 = O.radius_halton(pb.n, pb.d) if pb.sampler == 1 else O.radius_thm1(pb.n, pb.d)
     r = pb.r if pb.r > 0 else np.float32(r0)
-    g = O.Graph(pb.kind, pb.d, pb.dp, X, goal, r)
+    g = O.Graph(pb.kind, pb.d, pb.dp, X, goal, r, rho=pb.rho)
     parent, cost, info = g.plan(pb.box_lo, pb.box_hi, pb.lo[:pb.dp], pb.hi[:pb.dp], pb.lam, pb.seg_spacing,
                                 pb.traj_points)
     return X, goal, g, parent, cost, info
@@ -162,6 +162,28 @@ def test_halton_queries_in_a_batch(O):
     infos = bp.plan()
     for k in range(len(qs)):
         check_query(O, bp, k, infos)
+
+
+@pytest.mark.parametrize("mode", ["teams", "lockstep"])
+def test_dubins_queries_in_a_batch(O, mode):
+    # Dubins airplane queries (Philox and Halton, 30 to 500 boxes, two turning
+    # radii) next to geometric and double-integrator ones, under both plan-stage
+    # schemes: each equals the oracle on its own.
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import BatchPlanner
+    qs = mixed_batch(seed=11, q=8)
+    qs += [envgen.dubins_forest(31, n=900, r=0.3, trunks=3, strips=10),
+           envgen.dubins_forest(32, n=1400, r=0.28, strips=15, sampler=1),
+           envgen.dubins_forest(33, n=700, r=0.35, rho=0.1, strips=50),
+           envgen.dubins_forest(34, n=64, r=0.6, trunks=2)]
+    bp = BatchPlanner(qs)
+    bp.plan()
+    N.gmt_batch_set_mode(bp.batch, N.BATCH_TEAMS if mode == "teams" else N.BATCH_LOCKSTEP)
+    infos = bp.plan()
+    for k in range(len(qs)):
+        check_query(O, bp, k, infos)
+    v, _ = N.gmt_batch_get_view(bp.batch, len(qs) - 1)
+    assert v.turn_radius == np.float32(qs[-1].rho) and v.in_path is not None
 
 
 def test_lockstep_runs_more_than_512_queries_in_chunks(O):

@@ -100,8 +100,8 @@ def test_bad_arguments(O, P):
         with pytest.raises(N.GmtError) as e:
             P.Planner(bad).build()
         assert e.value.status == N.GMT_ERR_INVALID
-    # the batched path covers geometric and double-integrator queries only
-    bp = P.BatchPlanner([pb])
+    # the batched path checks the same
+    bp = P.BatchPlanner([pb, pb.with_(rho=0.0)])
     with pytest.raises(N.GmtError) as e:
         bp.plan()
     assert e.value.status == N.GMT_ERR_INVALID
