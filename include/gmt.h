@@ -359,8 +359,10 @@ gmt_status gmt_server_create(const gmt_server_config* config, gmt_server** serve
 void gmt_server_free(gmt_server* server);
 /* Builds a resident session: SampleFree + CSR for the problem (space, x_init,
  * goal, params as for gmt_build_graph) with `box_count` boxes given as HOST
- * arrays [box_count][pos_dim].  GMT_ERR_ADMISSION if its estimated device
- * memory does not fit the budget (or the free memory).  Synchronous. */
+ * arrays [box_count][pos_dim].  Spaces: double integrator, Dubins airplane,
+ * geometric with dim 2 or 3 (else GMT_ERR_INVALID).  GMT_ERR_ADMISSION if its
+ * estimated device memory does not fit the budget (or the free memory).
+ * Synchronous. */
 gmt_status gmt_server_open_session(gmt_server* server, const gmt_space* space, const float* x_init,
                                    const gmt_goal* goal, const gmt_params* params, int32_t box_count,
                                    const float* box_lo, const float* box_hi, int32_t* session);

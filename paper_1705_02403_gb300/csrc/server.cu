@@ -34,18 +34,19 @@
 namespace gmtk {
 
 // Bounding box (over the position axes) of the points the lazy check of in-edge
-// e tests: the m segment points (geometric) or the trajectory points (double
-// integrator), computed with the same expressions as the check.
+// e tests: the m segment points (geometric), the trajectory points (double
+// integrator) or the points along the stored shortest word (Dubins airplane),
+// computed with the same expressions as the check.
 template <int KIND, int DP>
 __global__ void edge_aabb_kernel(int N, int pitch, const float* __restrict__ X, const int* __restrict__ in_row,
                                  const int* __restrict__ in_col, const float* __restrict__ in_cost,
-                                 const float* __restrict__ in_tau, float seg_spacing, int traj_points,
-                                 float* __restrict__ aabb) {
+                                 const float* __restrict__ in_tau, const float* __restrict__ in_path, float rho,
+                                 float seg_spacing, int traj_points, float* __restrict__ aabb) {
     const int x = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (x >= N) return;
-    constexpr int D = KIND == GMT_COST_DI ? 6 : DP;
-    constexpr int P = KIND == GMT_COST_DI ? 3 : DP;
+    constexpr int D = KIND == GMT_COST_DI ? 6 : (KIND == GMT_COST_DUBINS ? 4 : DP);
+    constexpr int P = KIND == GMT_COST_EUCLID ? DP : 3;
     float sx[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) sx[a] = X[(size_t)a * pitch + x];
@@ -57,7 +58,22 @@ __global__ void edge_aabb_kernel(int N, int pitch, const float* __restrict__ X, 
         float lo[P], hi[P];
 #pragma unroll
         for (int a = 0; a < P; ++a) { lo[a] = f_inf(); hi[a] = -f_inf(); }
-        if (KIND == GMT_COST_EUCLID) {
+        if (KIND == GMT_COST_DUBINS) {
+            const float4 w = reinterpret_cast<const float4*>(in_path)[e];
+            const DubPath Pw{__float_as_int(w.w), w.x, w.y, w.z, ((w.x + w.y) + w.z) * rho};
+            if (Pw.word < kDubNone) {
+                const DubSegs G = dubins_segments(sy, Pw, rho);
+                int m = (int)ceilf(in_cost[e] / seg_spacing) + 1;
+                if (m < 2) m = 2;
+                const float denom = (float)(m - 1);
+                for (int k = 0; k < m; ++k) {
+                    float p[3];
+                    dubins_point(sy, sx, G, (float)k / denom, p);
+#pragma unroll
+                    for (int a = 0; a < P; ++a) { lo[a] = fminf(lo[a], p[a]); hi[a] = fmaxf(hi[a], p[a]); }
+                }
+            }
+        } else if (KIND == GMT_COST_EUCLID) {
             int m = (int)ceilf(in_cost[e] / seg_spacing) + 1;
             if (m < 2) m = 2;
             const float denom = (float)(m - 1);
@@ -246,6 +262,8 @@ cudaError_t start_request(gmt_server* sv, Slot& sl, Session& ss, Request&& rq) {
     a.kind = v.kind; a.d = v.dim; a.dp = v.pos_dim; a.N = v.N; a.pitch = v.x_pitch;
     a.X = v.X; a.is_goal = v.is_goal; a.out_row = v.out_row; a.out_col = v.out_col;
     a.in_row = v.in_row; a.in_col = v.in_col; a.in_cost = v.in_cost; a.in_tau = v.in_tau;
+    a.in_path = v.in_path;
+    a.rho = v.turn_radius;
     a.boxes = BoxArgs{nb, ss.d_lo, ss.d_hi};
     for (int k = 0; k < 3 && k < v.pos_dim; ++k) { a.pos_lo[k] = ss.space.lo[k]; a.pos_hi[k] = ss.space.hi[k]; }
     a.r = v.r;
@@ -339,8 +357,10 @@ void worker_loop(gmt_server* sv) {
 size_t session_bytes_estimate(int N, int kind) {
     const size_t P = (size_t)(N + 31) / 32 * 32, W = (size_t)(N + 31) / 32;
     const size_t E = (size_t)N * 256;  // upper estimate of edges per node
-    const size_t mask = W * P * 4 * (kind == GMT_COST_DI ? 2 : 1);
-    return mask + E * (kind == GMT_COST_DI ? 44 : 33) + (size_t)N * 64;
+    const size_t mask = W * P * 4 * (kind == GMT_COST_EUCLID ? 1 : 2);
+    // per edge: CSR columns and costs (both directions for directed costs),
+    // arrival times (DI) or stored words (Dubins), point box, verdict
+    return mask + E * (kind == GMT_COST_DI ? 44 : kind == GMT_COST_DUBINS ? 57 : 33) + (size_t)N * 64;
 }
 
 }  // namespace
@@ -423,8 +443,10 @@ gmt_status gmt_server_open_session(gmt_server* sv, const gmt_space* space, const
         return sfail(GMT_ERR_INVALID, "bad session arguments");
     if (box_count > sv->cfg.max_boxes) return sfail(GMT_ERR_INVALID, "more boxes than the server's max_boxes");
     if (params->n + 1 > sv->cfg.max_nodes) return sfail(GMT_ERR_INVALID, "more nodes than the server's max_nodes");
-    if (!(space->kind == GMT_COST_DI || (space->kind == GMT_COST_EUCLID && (space->dim == 2 || space->dim == 3))))
-        return sfail(GMT_ERR_INVALID, "sessions support the double integrator and 2D/3D geometric spaces");
+    if (!(space->kind == GMT_COST_DI || space->kind == GMT_COST_DUBINS ||
+          (space->kind == GMT_COST_EUCLID && (space->dim == 2 || space->dim == 3))))
+        return sfail(GMT_ERR_INVALID,
+                     "sessions support the double integrator, the Dubins airplane and 2D/3D geometric spaces");
     // admission by device memory: the configured budget and what is free now
     const size_t need = session_bytes_estimate(params->n + 1, space->kind);
     size_t free_b = 0, total_b = 0;
@@ -476,15 +498,19 @@ gmt_status gmt_server_open_session(gmt_server* sv, const gmt_space* space, const
         if (space->kind == GMT_COST_DI)
             edge_aabb_kernel<GMT_COST_DI, 3><<<blocks, 256, 0, sv->setup>>>(
                 s.view.N, s.view.x_pitch, s.view.X, s.view.in_row, s.view.in_col, s.view.in_cost, s.view.in_tau,
-                params->seg_spacing, params->traj_points, s.aabb);
+                nullptr, 0.0f, params->seg_spacing, params->traj_points, s.aabb);
+        else if (space->kind == GMT_COST_DUBINS)
+            edge_aabb_kernel<GMT_COST_DUBINS, 3><<<blocks, 256, 0, sv->setup>>>(
+                s.view.N, s.view.x_pitch, s.view.X, s.view.in_row, s.view.in_col, s.view.in_cost, nullptr,
+                s.view.in_path, s.view.turn_radius, params->seg_spacing, params->traj_points, s.aabb);
         else if (space->dim == 2)
             edge_aabb_kernel<GMT_COST_EUCLID, 2><<<blocks, 256, 0, sv->setup>>>(
                 s.view.N, s.view.x_pitch, s.view.X, s.view.in_row, s.view.in_col, s.view.in_cost, nullptr,
-                params->seg_spacing, params->traj_points, s.aabb);
+                nullptr, 0.0f, params->seg_spacing, params->traj_points, s.aabb);
         else
             edge_aabb_kernel<GMT_COST_EUCLID, 3><<<blocks, 256, 0, sv->setup>>>(
                 s.view.N, s.view.x_pitch, s.view.X, s.view.in_row, s.view.in_col, s.view.in_cost, nullptr,
-                params->seg_spacing, params->traj_points, s.aabb);
+                nullptr, 0.0f, params->seg_spacing, params->traj_points, s.aabb);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(sv->setup);

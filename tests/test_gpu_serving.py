@@ -1,5 +1,6 @@
 """The replanning server: every request's tree is the same alone and in a mix
-of overlapping requests (bit for bit, verdict cache included), sessions are
+of overlapping requests (bit for bit, verdict cache included; geometric,
+double-integrator and Dubins-airplane sessions with moving boxes), sessions are
 admitted by device memory, and the verdict cache only recomputes what moved
 boxes can change."""
 import numpy as np
@@ -37,7 +38,9 @@ def test_same_alone_and_in_the_mix():
     from paper_1705_02403_gb300.serving import MovingBoxes
     pbs = [envgen.di6(seed=1, n=700, r=2.8), envgen.geometric(2, d=2, n=900, nbox=10, r=0.12),
            envgen.di6(seed=3, n=1200, r=2.6), envgen.geometric(4, d=3, n=800, nbox=12, r=0.3),
-           envgen.di6(seed=5, n=2500, r=2.5)]
+           envgen.di6(seed=5, n=2500, r=2.5),
+           envgen.dubins_forest(6, n=800, r=0.3, trunks=3, strips=10),
+           envgen.dubins_forest(7, n=1500, r=0.28, trunks=2, strips=15, sampler=1)]
     server = N.Server(slots=3, cluster=2, threads=512, max_nodes=2501, max_boxes=30)
     sids = [server.open_session(*structs(pb)[:1], pb.x_init, *structs(pb)[1:], pb.box_lo, pb.box_hi)[0] for pb in pbs]
     movers = [MovingBoxes(pb, k, vmax=0.05) if pb.dp == 3 else None for k, pb in enumerate(pbs)]
