@@ -110,6 +110,12 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
         // ---- phase 1: snapshot update, group selection, push
         const unsigned long long gk_prev = __ldcg(&ctl->gk[p ^ 1]);
         const int nk = (int)(gk_prev >> 32), nn = ldcg_i(&ctl->new_count[p]);
+        // the lane's first open entry, loaded now so that its latency overlaps
+        // the snapshot update below (which writes ocost only, never cur)
+        const int ncur = nk + nn;
+        const int t_first = cta + nctas * wib + nctas * wpc * lane;
+        int2 e_first = make_int2(-1, 0);
+        if (t_first < ncur) e_first = __ldcg(&cur[t_first < nk ? t_first : N - 1 - (t_first - nk)]);
         if (it > 0) {
             const int ng_prev = (int)(gk_prev & 0xffffffffu);
             const int* Gprev = A.list_g[p ^ 1];
@@ -120,14 +126,13 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
             }
         }
         {
-            const int ncur = nk + nn;
             const int per_round = nctas * wpc * 32;
             for (int t0 = cta + nctas * wib; t0 < ncur; t0 += per_round) {  // t0: entry of lane 0
                 const int t = t0 + nctas * wpc * lane;
                 bool in_g = false, keep = false;
                 int2 e = make_int2(-1, 0);
                 if (t < ncur) {
-                    e = __ldcg(&cur[t < nk ? t : N - 1 - (t - nk)]);
+                    e = t0 == cta + nctas * wib ? e_first : __ldcg(&cur[t < nk ? t : N - 1 - (t - nk)]);
                     in_g = __int_as_float(e.y) <= theta;
                     keep = !in_g;
                 }
@@ -191,9 +196,12 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
             ctl->goal_flag[p ^ 1] = 0;
         }
         {
+            // the warp's first candidate slot, loaded with the count (the list
+            // holds at least N entries; the value is used only if ci < nc)
+            const int x_first = gwarp < N ? ldcg_i(&A.list_cand[gwarp]) : -1;
             const int nc = ldcg_i(&ctl->cand_count[p]);
             for (int ci = gwarp; ci < nc; ci += nwarps) {
-                const int x = ldcg_i(&A.list_cand[ci]);
+                const int x = ci == gwarp ? x_first : ldcg_i(&A.list_cand[ci]);
                 const int r0 = __ldg(&A.in_row[x]), r1 = __ldg(&A.in_row[x + 1]);
                 float sx[D];  // issued now, used by the check after the reduction
 #pragma unroll
