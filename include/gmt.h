@@ -377,6 +377,15 @@ gmt_status gmt_server_poll(gmt_server* server, gmt_server_result* out, int32_t m
                            int32_t wait_ms);
 /* Waits for the session's requests, then frees it. */
 gmt_status gmt_server_close_session(gmt_server* server, int32_t session);
+/* The robot has moved: node 0 of the session becomes x_init (HOST [dim]).
+ * Waits (up to 30 s, else GMT_ERR_TIMEOUT) for the requests submitted
+ * before, then builds the session's graph again (same seed, the boxes of its
+ * last request; node 0's rows are part of every other row's neighbours, so
+ * the CSR is rebuilt rather than patched) with a cleared verdict cache;
+ * requests submitted meanwhile wait and then plan on the new graph.
+ * GMT_ERR_INVALID if x_init is outside X or inside one of those boxes; on any
+ * error the session keeps its previous graph.  Synchronous. */
+gmt_status gmt_server_move_start(gmt_server* server, int32_t session, const float* x_init);
 gmt_status gmt_server_session_view(gmt_server* server, int32_t session, gmt_graph_view* view);
 
 /* ---------------------------------------------------------------- learned proposal

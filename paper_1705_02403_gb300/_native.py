@@ -161,6 +161,7 @@ SIGNATURES = {
     "gmt_server_submit": (_I32, [_P, _I32, _U64, _P, _P, _P, _P]),
     "gmt_server_poll": (_I32, [_P, C.POINTER(gmt_server_result), _I32, C.POINTER(_I32), _I32]),
     "gmt_server_close_session": (_I32, [_P, _I32]),
+    "gmt_server_move_start": (_I32, [_P, _I32, _P]),
     "gmt_server_session_view": (_I32, [_P, _I32, C.POINTER(gmt_graph_view)]),
     "gmt_connection_radius": (_F64, [_I32, _I32, _F64, _F64]),
     "gmt_connection_radius_halton": (_F64, [_I32, _I32, _F64, _F64]),
@@ -474,6 +475,10 @@ class Server:
 
     def close_session(self, session):
         _check(lib.gmt_server_close_session(self.handle, session))
+
+    def move_start(self, session, x_init):
+        xi = (C.c_float * GMT_MAX_DIM)(*[float(v) for v in x_init])
+        _check(lib.gmt_server_move_start(self.handle, session, C.cast(xi, C.c_void_p)))
 
     def session_view(self, session):
         v = gmt_graph_view()

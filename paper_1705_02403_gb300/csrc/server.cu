@@ -150,6 +150,7 @@ struct Session {
     size_t bytes = 0;
     bool busy = false;
     bool closing = false;
+    bool moving = false;  // a start move is rebuilding the graph: requests wait in the queue
 };
 
 struct Request {
@@ -324,7 +325,7 @@ void worker_loop(gmt_server* sv) {
             if (sl.busy) continue;
             auto qit = std::find_if(sv->queue.begin(), sv->queue.end(), [&](const Request& q) {
                 auto s = sv->sessions.find(q.session);
-                return s != sv->sessions.end() && !s->second.busy;
+                return s != sv->sessions.end() && !s->second.busy && !s->second.moving;
             });
             if (qit == sv->queue.end()) break;
             Session& ss = sv->sessions[qit->session];
@@ -435,6 +436,40 @@ void gmt_server_free(gmt_server* sv) {
     delete sv;
 }
 
+namespace {
+// Allocates and fills a session's per-edge point boxes and clears its verdict
+// cache (all unknown) for the graph `v`.
+cudaError_t edge_cache_setup(const gmt_graph_view& v, const gmt_space& space, const gmt_params& params, float** aabb,
+                             uint8_t** verdict, cudaStream_t st) {
+    const long long E = v.E;
+    const int P = space.pos_dim;
+    cudaError_t e = cudaMalloc(aabb, std::max(1ll, E) * 2 * P * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(verdict, std::max(1ll, E));
+    if (e == cudaSuccess) e = cudaMemsetAsync(*verdict, 0, std::max(1ll, E), st);
+    if (e == cudaSuccess && E > 0) {
+        const unsigned blocks = (unsigned)((v.N + 7) / 8);
+        if (space.kind == GMT_COST_DI)
+            edge_aabb_kernel<GMT_COST_DI, 3><<<blocks, 256, 0, st>>>(
+                v.N, v.x_pitch, v.X, v.in_row, v.in_col, v.in_cost, v.in_tau, nullptr, 0.0f, params.seg_spacing,
+                params.traj_points, *aabb);
+        else if (space.kind == GMT_COST_DUBINS)
+            edge_aabb_kernel<GMT_COST_DUBINS, 3><<<blocks, 256, 0, st>>>(
+                v.N, v.x_pitch, v.X, v.in_row, v.in_col, v.in_cost, nullptr, v.in_path, v.turn_radius,
+                params.seg_spacing, params.traj_points, *aabb);
+        else if (space.dim == 2)
+            edge_aabb_kernel<GMT_COST_EUCLID, 2><<<blocks, 256, 0, st>>>(
+                v.N, v.x_pitch, v.X, v.in_row, v.in_col, v.in_cost, nullptr, nullptr, 0.0f, params.seg_spacing,
+                params.traj_points, *aabb);
+        else
+            edge_aabb_kernel<GMT_COST_EUCLID, 3><<<blocks, 256, 0, st>>>(
+                v.N, v.x_pitch, v.X, v.in_row, v.in_col, v.in_cost, nullptr, nullptr, 0.0f, params.seg_spacing,
+                params.traj_points, *aabb);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+}  // namespace
+
 gmt_status gmt_server_open_session(gmt_server* sv, const gmt_space* space, const float* x_init, const gmt_goal* goal,
                                    const gmt_params* params, int32_t box_count, const float* box_lo,
                                    const float* box_hi, int32_t* session) {
@@ -489,30 +524,7 @@ gmt_status gmt_server_open_session(gmt_server* sv, const gmt_space* space, const
     gmt_status st = gmt_build_graph(space, &bx, x_init, goal, params, &s.graph, sv->setup);
     if (st != GMT_OK) return undo(st, std::string("session graph: ") + gmt_last_error());
     gmt_graph_get_view(s.graph, &s.view);
-    const long long E = s.view.E;
-    e = cudaMalloc(&s.aabb, std::max(1ll, E) * 2 * P * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&s.verdict, std::max(1ll, E));
-    if (e == cudaSuccess) e = cudaMemsetAsync(s.verdict, 0, std::max(1ll, E), sv->setup);
-    if (e == cudaSuccess && E > 0) {
-        const unsigned blocks = (unsigned)((s.view.N + 7) / 8);
-        if (space->kind == GMT_COST_DI)
-            edge_aabb_kernel<GMT_COST_DI, 3><<<blocks, 256, 0, sv->setup>>>(
-                s.view.N, s.view.x_pitch, s.view.X, s.view.in_row, s.view.in_col, s.view.in_cost, s.view.in_tau,
-                nullptr, 0.0f, params->seg_spacing, params->traj_points, s.aabb);
-        else if (space->kind == GMT_COST_DUBINS)
-            edge_aabb_kernel<GMT_COST_DUBINS, 3><<<blocks, 256, 0, sv->setup>>>(
-                s.view.N, s.view.x_pitch, s.view.X, s.view.in_row, s.view.in_col, s.view.in_cost, nullptr,
-                s.view.in_path, s.view.turn_radius, params->seg_spacing, params->traj_points, s.aabb);
-        else if (space->dim == 2)
-            edge_aabb_kernel<GMT_COST_EUCLID, 2><<<blocks, 256, 0, sv->setup>>>(
-                s.view.N, s.view.x_pitch, s.view.X, s.view.in_row, s.view.in_col, s.view.in_cost, nullptr,
-                nullptr, 0.0f, params->seg_spacing, params->traj_points, s.aabb);
-        else
-            edge_aabb_kernel<GMT_COST_EUCLID, 3><<<blocks, 256, 0, sv->setup>>>(
-                s.view.N, s.view.x_pitch, s.view.X, s.view.in_row, s.view.in_col, s.view.in_cost, nullptr,
-                nullptr, 0.0f, params->seg_spacing, params->traj_points, s.aabb);
-        e = cudaGetLastError();
-    }
+    e = edge_cache_setup(s.view, *space, *params, &s.aabb, &s.verdict, sv->setup);
     if (e == cudaSuccess) e = cudaStreamSynchronize(sv->setup);
     if (e != cudaSuccess) return undo(GMT_ERR_CUDA, std::string("session setup: ") + cudaGetErrorString(e));
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -569,7 +581,7 @@ gmt_status gmt_server_close_session(gmt_server* sv, int32_t session) {
         const bool idle = sv->cv.wait_for(lk, std::chrono::seconds(30), [&] {
             bool queued = false;
             for (auto& q : sv->queue) queued = queued || q.session == session;
-            return !queued && !sv->sessions[session].busy;
+            return !queued && !sv->sessions[session].busy && !sv->sessions[session].moving;
         });
         if (!idle) {
             sv->sessions[session].closing = false;
@@ -584,6 +596,97 @@ gmt_status gmt_server_close_session(gmt_server* sv, int32_t session) {
     for (void* p : d)
         if (p) cudaFree(p);
     return GMT_OK;
+}
+
+gmt_status gmt_server_move_start(gmt_server* sv, int32_t session, const float* x_init) {
+    if (!sv || !x_init) return sfail(GMT_ERR_INVALID, "server and x_init must be non-NULL");
+    gmt_space space;
+    gmt_goal goal;
+    gmt_params params;
+    std::vector<float> lo, hi;
+    gmt_boxes bx;
+    {
+        std::unique_lock<std::mutex> lk(sv->mu);
+        auto it = sv->sessions.find(session);
+        if (it == sv->sessions.end() || it->second.closing) return sfail(GMT_ERR_INVALID, "no such session");
+        if (it->second.moving) return sfail(GMT_ERR_INVALID, "the session's start is already being moved");
+        // wait (bounded) until the requests submitted before the move are done
+        const bool idle = sv->cv.wait_for(lk, std::chrono::seconds(30), [&] {
+            bool queued = false;
+            for (auto& q : sv->queue) queued = queued || q.session == session;
+            auto s = sv->sessions.find(session);
+            return s == sv->sessions.end() || (!queued && !s->second.busy);
+        });
+        it = sv->sessions.find(session);
+        if (it == sv->sessions.end()) return sfail(GMT_ERR_INVALID, "the session was closed");
+        if (!idle) return sfail(GMT_ERR_TIMEOUT, "session still busy after 30 s");
+        Session& s = it->second;
+        s.moving = true;  // requests submitted from now on wait for the new graph
+        space = s.space; goal = s.goal; params = s.params;
+        lo = s.cur_lo; hi = s.cur_hi;
+        bx = gmt_boxes{s.nbox, s.d_lo, s.d_hi};
+    }
+    auto finish = [&](gmt_status st, const std::string& m) {
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            auto it = sv->sessions.find(session);
+            if (it != sv->sessions.end()) it->second.moving = false;
+        }
+        sv->cv.notify_all();
+        return st == GMT_OK ? GMT_OK : sfail(st, m);
+    };
+    // the new start must lie in X and outside the boxes the session has now
+    for (int a = 0; a < space.dim; ++a)
+        if (!(space.lo[a] <= x_init[a] && x_init[a] <= space.hi[a]))
+            return finish(GMT_ERR_INVALID, "the new start is outside the state bounds");
+    const int P = space.pos_dim;
+    for (int b = 0; b < bx.count; ++b) {
+        bool in = true;
+        for (int a = 0; a < P; ++a) in = in && lo[(size_t)b * P + a] <= x_init[a] && x_init[a] <= hi[(size_t)b * P + a];
+        if (in) return finish(GMT_ERR_INVALID, "the new start is inside a box");
+    }
+    // a new graph (same seed, the current boxes) in a handle of its own, so a
+    // failure leaves the session as it was
+    gmt_graph* ng = nullptr;
+    gmt_status st = gmt_build_graph(&space, &bx, x_init, &goal, &params, &ng, sv->setup);
+    if (st != GMT_OK) {
+        const std::string m = std::string("start move: ") + gmt_last_error();
+        if (ng) gmt_graph_free(ng);
+        return finish(st, m);
+    }
+    gmt_graph_view nv;
+    gmt_graph_get_view(ng, &nv);
+    float* naabb = nullptr;
+    uint8_t* nverdict = nullptr;
+    cudaError_t e = edge_cache_setup(nv, space, params, &naabb, &nverdict, sv->setup);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sv->setup);
+    if (e != cudaSuccess) {
+        gmt_graph_free(ng);
+        if (naabb) cudaFree(naabb);
+        if (nverdict) cudaFree(nverdict);
+        return finish(GMT_ERR_CUDA, std::string("start move: ") + cudaGetErrorString(e));
+    }
+    gmt_graph* og = nullptr;
+    float* oaabb = nullptr;
+    uint8_t* overdict = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->sessions.find(session);
+        if (it == sv->sessions.end()) {  // closing waits for the move, so this does not happen
+            gmt_graph_free(ng);
+            cudaFree(naabb);
+            cudaFree(nverdict);
+            return sfail(GMT_ERR_INVALID, "the session was closed");
+        }
+        Session& s = it->second;
+        og = s.graph; oaabb = s.aabb; overdict = s.verdict;
+        s.graph = ng; s.view = nv; s.aabb = naabb; s.verdict = nverdict;
+        std::memcpy(s.x_init, x_init, space.dim * sizeof(float));
+    }
+    gmt_graph_free(og);
+    cudaFree(oaabb);
+    cudaFree(overdict);
+    return finish(GMT_OK, "");
 }
 
 gmt_status gmt_server_session_view(gmt_server* sv, int32_t session, gmt_graph_view* view) {

@@ -117,3 +117,67 @@ def test_verdict_cache_reuse():
     info, _, _ = alone(server, sid, pb, lo, hi)
     assert r2["status"] == info["status"] and r2["goal_node"] == info["goal_node"]
     server.close()
+
+
+@pytest.mark.parametrize("kind", ["di", "dubins"])
+def test_start_move_rebuilds_the_session(kind):
+    # After gmt_server_move_start the session plans exactly as a graph built
+    # fresh at the new start (same seed, the boxes of its last request) and
+    # planned with the request's boxes; a move into a box is refused and the
+    # session keeps planning on its previous graph.
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import Planner, boxes_on_device
+    from paper_1705_02403_gb300.serving import MovingBoxes
+    pb = envgen.di6(seed=8, n=900, r=2.8) if kind == "di" else envgen.dubins_forest(8, n=900, r=0.3, trunks=3,
+                                                                                      strips=10)
+    server = N.Server(slots=2, cluster=2, threads=512, max_nodes=pb.N, max_boxes=pb.nbox)
+    sid, _ = server.open_session(*structs(pb)[:1], pb.x_init, *structs(pb)[1:], pb.box_lo, pb.box_hi)
+    mover = MovingBoxes(pb, 3, vmax=0.03)
+
+    def request(rid, lo, hi):
+        parent = torch.full((pb.N,), -7, dtype=torch.int32, device="cuda")
+        cost = torch.full((pb.N,), -7.0, dtype=torch.float32, device="cuda")
+        server.submit(sid, rid, lo, hi, parent.data_ptr(), cost.data_ptr())
+        while True:
+            got = server.poll(8, 200)
+            if got:
+                assert len(got) == 1 and got[0]["request_id"] == rid
+                torch.cuda.synchronize()
+                return got[0], parent, cost
+
+    lo1, hi1 = mover.step()
+    request(0, lo1, hi1)
+    # a start inside one of the current boxes is refused
+    inside = (lo1[0] + hi1[0]) / 2
+    x_bad = pb.x_init.copy()
+    x_bad[:3] = inside[:3]
+    with pytest.raises(N.GmtError) as e:
+        server.move_start(sid, x_bad)
+    assert e.value.status == N.GMT_ERR_INVALID
+    r, parent, cost = request(1, lo1, hi1)
+    info, p2, c2 = alone(server, sid, pb, lo1, hi1)
+    assert torch.equal(parent, p2) and torch.equal(cost.view(torch.int32), c2.view(torch.int32))
+    # a valid move, then requests with moving boxes
+    x_new = None
+    for cand in ([0.03, 0.04, 0.3], [0.1, 0.03, 0.2], [0.04, 0.12, 0.1], [0.2, 0.05, 0.05]):
+        c = np.array(cand, np.float32)
+        if not np.any(np.all((lo1 <= c) & (c <= hi1), axis=1)):
+            x_new = pb.x_init.copy()
+            x_new[:3] = c
+            break
+    assert x_new is not None
+    server.move_start(sid, x_new)
+    fresh = Planner(pb.with_(x_init=x_new, box_lo=lo1, box_hi=hi1)).build()
+    for rid in (2, 3):
+        lo, hi = mover.step()
+        r, parent, cost = request(rid, lo, hi)
+        b, keep = boxes_on_device(pb.with_(box_lo=lo, box_hi=hi))
+        fresh.boxes = b
+        ref = fresh.plan()
+        torch.cuda.synchronize()
+        assert r["status"] == ref["status"] and r["goal_node"] == ref["goal_node"]
+        assert torch.equal(parent, fresh.parent)
+        assert torch.equal(cost.view(torch.int32), fresh.cost.view(torch.int32))
+    v = server.session_view(sid)
+    assert v.X is not None
+    server.close()
