@@ -200,6 +200,19 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
                               const gmt_goal* goal, const gmt_params* params, const float* extra,
                               int32_t extra_count, int32_t extra_pitch, gmt_graph** graph, gmt_stream stream);
 
+/* As gmt_build_graph, without the host synchronisation: when the handle's edge
+ * arrays from earlier builds are at least as large as needed, the whole build
+ * is only queued on `stream`, and its edge count and sampling status are read
+ * by the next gmt_plan (or gmt_graph_get_view) on this handle, which returns
+ * the errors gmt_build_graph would have returned.  If the edges do not fit
+ * those arrays, that call rebuilds synchronously and the result is the same.
+ * A new handle, the cell-list neighbour build or appended samples take the
+ * synchronous path.  `boxes` (the struct's DEVICE arrays) must stay valid
+ * until that plan or view. */
+gmt_status gmt_build_graph_async(const gmt_space* space, const gmt_boxes* boxes, const float* x_init,
+                                 const gmt_goal* goal, const gmt_params* params, gmt_graph** graph,
+                                 gmt_stream stream);
+
 gmt_status gmt_graph_get_view(const gmt_graph* graph, gmt_graph_view* view);
 void gmt_graph_free(gmt_graph* graph);
 

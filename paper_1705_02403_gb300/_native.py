@@ -143,6 +143,8 @@ SIGNATURES = {
     "gmt_gemm_bf16": (_I32, [_I32, _I32, _I32, _P, _P, _I32, _P, _P, _P, _I32, _P, _P, _P]),
     "gmt_build_graph_ex": (_I32, [C.POINTER(gmt_space), C.POINTER(gmt_boxes), _P, C.POINTER(gmt_goal),
                                   C.POINTER(gmt_params), _P, _I32, _I32, C.POINTER(C.c_void_p), _P]),
+    "gmt_build_graph_async": (_I32, [C.POINTER(gmt_space), C.POINTER(gmt_boxes), _P, C.POINTER(gmt_goal),
+                                     C.POINTER(gmt_params), C.POINTER(C.c_void_p), _P]),
     "gmt_model_create": (_I32, [C.POINTER(gmt_model_config), C.POINTER(C.c_void_p)]),
     "gmt_model_free": (None, [_P]),
     "gmt_model_get_view": (_I32, [_P, C.POINTER(gmt_model_view)]),
@@ -231,6 +233,17 @@ def gmt_build_graph(space: gmt_space, boxes: gmt_boxes, x_init, goal: gmt_goal, 
     xi = (C.c_float * GMT_MAX_DIM)(*[float(v) for v in x_init])
     _check(lib.gmt_build_graph(C.byref(space), C.byref(boxes), C.cast(xi, C.c_void_p), C.byref(goal),
                                C.byref(params), C.byref(g.handle), _stream(stream)))
+    return g
+
+
+def gmt_build_graph_async(space: gmt_space, boxes: gmt_boxes, x_init, goal: gmt_goal, params: gmt_params,
+                          graph: Graph | None = None, stream=None) -> Graph:
+    """gmt_build_graph without the host synchronisation (confirmed by the next
+    gmt_plan or view on the handle); `boxes`' arrays must stay valid until then."""
+    g = graph if graph is not None else Graph()
+    xi = (C.c_float * GMT_MAX_DIM)(*[float(v) for v in x_init])
+    _check(lib.gmt_build_graph_async(C.byref(space), C.byref(boxes), C.cast(xi, C.c_void_p), C.byref(goal),
+                                     C.byref(params), C.byref(g.handle), _stream(stream)))
     return g
 
 

@@ -100,6 +100,18 @@ struct gmt_graph {
     // pinned host mirrors
     PlanCtl* h_ctl = nullptr;
     int* h_scalars = nullptr;
+    // An asynchronous build (gmt_build_graph_async) not yet confirmed: its fill
+    // wrote into the edge arrays of earlier builds (`pending_cap` edges); the
+    // flags and edge count are read by the next plan or view, which rebuilds
+    // synchronously from the kept inputs if the edges did not fit.
+    bool pending = false;
+    long long pending_cap = 0;
+    cudaStream_t pending_stream = nullptr;
+    gmt_space p_space;
+    gmt_boxes p_boxes;
+    float p_x_init[GMT_MAX_DIM];
+    gmt_goal p_goal;
+    gmt_params p_params;
     // profiling: event pairs around each kernel group
     enum { kSample, kPair, kTranspose, kScan, kFill, kPlan, kStages };
     bool profiling = false;
@@ -243,9 +255,60 @@ gmt_status gmt_build_graph(const gmt_space* space, const gmt_boxes* boxes, const
     return gmt_build_graph_ex(space, boxes, x_init, goal, params, nullptr, 0, 0, graph, stream);
 }
 
+namespace {
+// Edges every edge array of the handle holds now (0 if one is missing).
+long long edge_capacity(const gmt_graph* g) {
+    long long c = (long long)std::min(g->cap_out_col, g->cap_out_cost);
+    if (g->directed()) c = std::min(c, (long long)std::min(g->cap_in_col_own, g->cap_in_cost_own));
+    if (g->kind == GMT_COST_DI) c = std::min(c, (long long)std::min(g->cap_out_tau, g->cap_in_tau));
+    if (g->kind == GMT_COST_DUBINS) c = std::min(c, (long long)(g->cap_in_path / 4));
+    return c;
+}
+
+gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const float* x_init, const gmt_goal* goal,
+                      const gmt_params* params, const float* extra, int32_t extra_count, int32_t extra_pitch,
+                      gmt_graph** graph, gmt_stream stream, bool async);
+
+// Confirms an asynchronous build once its stream has reached the flag and
+// edge-count readback: reports sampling errors as the synchronous build does,
+// and rebuilds synchronously if the edges outgrew the arrays the fill used.
+gmt_status resolve_pending(gmt_graph* g, bool* rebuilt) {
+    *rebuilt = false;
+    if (!g->pending) return GMT_OK;
+    GMT_CUDA(cudaStreamSynchronize(g->pending_stream), "graph build");
+    g->pending = false;
+    const int flags = g->h_scalars[0];
+    g->E = g->h_scalars[2];
+    if (flags & kSampleBadInit) return fail(GMT_ERR_INVALID, "x_init is outside X or inside an obstacle");
+    if (flags & kSampleExhausted)
+        return fail(GMT_ERR_INVALID, "a sample exhausted max_attempts (X_free or X_goal n X_free too small)");
+    if (flags & kSampleTimeout) return fail(GMT_ERR_TIMEOUT, "the Halton sampler's bounded wait ran out");
+    if (g->E > g->pending_cap) {
+        *rebuilt = true;
+        gmt_graph* h = g;
+        return build_impl(&g->p_space, &g->p_boxes, g->p_x_init, &g->p_goal, &g->p_params, nullptr, 0, 0, &h,
+                          (gmt_stream)g->pending_stream, false);
+    }
+    return GMT_OK;
+}
+}  // namespace
+
 gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, const float* x_init,
                               const gmt_goal* goal, const gmt_params* params, const float* extra, int32_t extra_count,
                               int32_t extra_pitch, gmt_graph** graph, gmt_stream stream) {
+    return build_impl(space, boxes, x_init, goal, params, extra, extra_count, extra_pitch, graph, stream, false);
+}
+
+gmt_status gmt_build_graph_async(const gmt_space* space, const gmt_boxes* boxes, const float* x_init,
+                                 const gmt_goal* goal, const gmt_params* params, gmt_graph** graph,
+                                 gmt_stream stream) {
+    return build_impl(space, boxes, x_init, goal, params, nullptr, 0, 0, graph, stream, true);
+}
+
+namespace {
+gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const float* x_init, const gmt_goal* goal,
+                      const gmt_params* params, const float* extra, int32_t extra_count, int32_t extra_pitch,
+                      gmt_graph** graph, gmt_stream stream, bool async) {
     gmt_status s;
     if (extra_count < 0 || (extra_count > 0 && (!extra || extra_pitch < extra_count)))
         return fail(GMT_ERR_INVALID, "extra samples need a DEVICE array [dim][extra_pitch], extra_pitch >= count");
@@ -381,6 +444,34 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     LAUNCH(cudaMemcpyAsync(g->h_scalars, g->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
     LAUNCH(cudaMemcpyAsync(g->h_scalars + 2, g->out_row + N, sizeof(int), cudaMemcpyDeviceToHost, st),
            "edge count readback");
+    g->pending = false;
+    const long long cap_now = edge_capacity(g);
+    if (async && !cells && extra_count == 0 && cap_now > 0) {
+        // no host wait: fill into the arrays of earlier builds; the next plan
+        // (or view) confirms the edge count and rebuilds if it did not fit
+        const bool di_a = g->kind == GMT_COST_DI, dub_a = g->kind == GMT_COST_DUBINS;
+        LAUNCH(g->mark(gmt_graph::kFill, 0, st), "event");
+        const FillDir out_dir{g->mask, g->out_row, g->out_col, g->out_cost, di_a ? g->out_tau : nullptr, nullptr,
+                              cap_now};
+        const FillDir in_dir = g->directed() ? FillDir{g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own,
+                                                       di_a ? g->in_tau : nullptr, dub_a ? g->in_path : nullptr,
+                                                       cap_now}
+                                             : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+        LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, st), "fill kernel");
+        LAUNCH(g->mark(gmt_graph::kFill, 1, st), "event");
+        g->used_cells = false;
+        g->E = -1;
+        g->pending = true;
+        g->pending_cap = cap_now;
+        g->pending_stream = st;
+        g->p_space = *space;
+        g->p_boxes = *boxes;
+        std::memcpy(g->p_x_init, x_init, space->dim * sizeof(float));
+        g->p_goal = *goal;
+        g->p_params = *params;
+        *graph = g;
+        return GMT_OK;
+    }
     LAUNCH(cudaStreamSynchronize(st), "graph build");
     if (cells && !cell_fill_fits(cg, g->N, g->h_scalars[1])) {
         // a row too long to sort in shared memory: the all-pairs test instead
@@ -402,29 +493,32 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     if (flags & kSampleTimeout) return bail(fail(GMT_ERR_TIMEOUT, "the Halton sampler's bounded wait ran out"));
     g->E = g->h_scalars[2];
     const size_t E = (size_t)g->E;
-    GROW(out_col, E);
-    GROW(out_cost, E);
+    // edge arrays that have to grow get a quarter of headroom, so that the
+    // next asynchronous builds of similar graphs fit them
+    const size_t Eg = edge_capacity(g) >= (long long)E ? E : E + E / 4 + 1024;
+    GROW(out_col, Eg);
+    GROW(out_cost, Eg);
     const bool di = g->kind == GMT_COST_DI, directed = g->directed();
     if (directed) {
-        GROW(in_col_own, E);
-        GROW(in_cost_own, E);
+        GROW(in_col_own, Eg);
+        GROW(in_cost_own, Eg);
     }
     if (di) {
-        GROW(out_tau, E);
-        GROW(in_tau, E);
+        GROW(out_tau, Eg);
+        GROW(in_tau, Eg);
     }
     const bool dubins = g->kind == GMT_COST_DUBINS;
-    if (dubins) GROW(in_path, 4 * E);
+    if (dubins) GROW(in_path, 4 * Eg);
     LAUNCH(g->mark(gmt_graph::kFill, 0, st), "event");
     if (cells) {
         LAUNCH(launch_cells_rows(sa, g->X, cg, g->cell_of, g->cell_start, g->cell_sorted, true, nullptr, nullptr,
                                  g->out_row, g->out_col, g->out_cost, g->flags + 2, st),
                "cell row kernel");
     } else {
-        const FillDir out_dir{g->mask, g->out_row, g->out_col, g->out_cost, di ? g->out_tau : nullptr, nullptr};
+        const FillDir out_dir{g->mask, g->out_row, g->out_col, g->out_cost, di ? g->out_tau : nullptr, nullptr, 0};
         const FillDir in_dir = directed ? FillDir{g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own,
-                                                  di ? g->in_tau : nullptr, dubins ? g->in_path : nullptr}
-                                        : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+                                                  di ? g->in_tau : nullptr, dubins ? g->in_path : nullptr, 0}
+                                        : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
         LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, st), "fill kernel");
     }
     LAUNCH(g->mark(gmt_graph::kFill, 1, st), "event");
@@ -434,8 +528,14 @@ gmt_status gmt_build_graph_ex(const gmt_space* space, const gmt_boxes* boxes, co
     return GMT_OK;
 }
 
-gmt_status gmt_graph_get_view(const gmt_graph* g, gmt_graph_view* v) {
-    if (!g || !v) return fail(GMT_ERR_INVALID, "graph and view must be non-NULL");
+}  // namespace
+
+gmt_status gmt_graph_get_view(const gmt_graph* gc, gmt_graph_view* v) {
+    if (!gc || !v) return fail(GMT_ERR_INVALID, "graph and view must be non-NULL");
+    gmt_graph* g = const_cast<gmt_graph*>(gc);  // confirming a pending build completes it, nothing else
+    bool rebuilt = false;
+    const gmt_status ps = resolve_pending(g, &rebuilt);
+    if (ps != GMT_OK) return ps;
     v->kind = g->kind; v->dim = g->d; v->pos_dim = g->dp; v->N = g->N; v->x_pitch = g->pitch;
     v->E = g->E; v->r = g->r;
     v->X = g->X; v->is_goal = g->is_goal;
@@ -482,6 +582,10 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
     assign_plan_lists(a, g->lists, (size_t)N);
     a.ctl = g->ctl;
     for (int k = 0; k < 3; ++k) { a.pos_lo[k] = g->pos_lo[k]; a.pos_hi[k] = g->pos_hi[k]; }
+    if (g->pending) {  // an asynchronous build: the kernel reads the CSR only if its edges fit
+        a.check_edges = 1;
+        a.edge_cap = g->pending_cap;
+    }
 
     int blocks = g->plan_blocks, threads = g->plan_threads, cluster = g->plan_cluster;
     if (blocks <= 0 && cluster <= 0) {
@@ -516,6 +620,11 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
     g->last_threads = threads;
     GMT_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(PlanCtl), cudaMemcpyDeviceToHost, st), "control readback");
     GMT_CUDA(cudaStreamSynchronize(st), "plan kernel");
+    if (g->pending) {
+        bool rebuilt = false;
+        if ((s = resolve_pending(g, &rebuilt)) != GMT_OK) return s;
+        if (rebuilt) return gmt_plan(g, boxes, params, parent, cost, path, info, stream);
+    }
     const PlanCtl& c = *g->h_ctl;
     std::memset(info, 0, sizeof(*info));
     info->status = c.status;

@@ -191,6 +191,8 @@ template <int KIND, int D>
 __global__ void __launch_bounds__(kFillWarps * 32) fill_kernel(SpaceArgs s, const float* __restrict__ X, FillDir out,
                                                                FillDir in) {
     const int v = blockIdx.x * kFillWarps + (threadIdx.x >> 5);
+    const FillDir& f = blockIdx.y == 0 ? out : in;
+    if (f.cap > 0 && (long long)__ldg(&f.row[s.N]) > f.cap) return;  // does not fit: the caller rebuilds
     if (blockIdx.y == 0) fill_row<KIND, D, false>(s, X, out.mask, out.row, out.col, out.cost, out.tau, out.path, v);
     else fill_row<KIND, D, true>(s, X, in.mask, in.row, in.col, in.cost, in.tau, in.path, v);
 }

@@ -110,6 +110,7 @@ struct FillDir {
     float* cost;
     float* tau;
     float* path;
+    long long cap;  // > 0: the arrays hold `cap` edges; a larger edge count writes nothing
 };
 // Fills the out-CSR, and the in-CSR in the same launch when in.mask != NULL.
 cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, cudaStream_t st);

@@ -100,10 +100,12 @@ class Planner:
         self.cost = torch.empty(pb.N, dtype=torch.float32, device=device)
         self.path = torch.empty(pb.N, dtype=torch.int32, device=device)
 
-    def build(self, stream=None, debug_flags=0):
+    def build(self, stream=None, debug_flags=0, asynchronous=False):
+        """gmt_build_graph; asynchronous=True queues the build without a host
+        wait (gmt_build_graph_async; confirmed by the next plan or view)."""
         params = params_struct(self.pb, debug_flags=debug_flags) if debug_flags else self.params
-        N.gmt_build_graph(self.space, self.boxes, [float(v) for v in self.pb.x_init], self.goal, params,
-                          self.graph, stream)
+        fn = N.gmt_build_graph_async if asynchronous else N.gmt_build_graph
+        fn(self.space, self.boxes, [float(v) for v in self.pb.x_init], self.goal, params, self.graph, stream)
         return self
 
     def view(self) -> GraphView:

@@ -421,3 +421,47 @@ def test_fp64_rerun_within_1e5(O, P):
                                    pb.traj_points)
         if np.array_equal(p64, parent) and i64["status"] == O.OK:
             assert abs(i64["path_cost"] - G["info"]["path_cost"]) <= 1e-5 * i64["path_cost"]
+
+
+def test_asynchronous_builds(O, P):
+    # gmt_build_graph_async on a reused handle: no host wait in the build; the
+    # plan confirms the edge count.  A graph with more edges than the arrays of
+    # earlier builds is rebuilt synchronously by the plan; a bad x_init is
+    # reported by the plan; a view confirms the build too.  Every result equals
+    # the synchronous build's and the oracle's.
+    from paper_1705_02403_gb300 import _native as N
+    small = envgen.di6(seed=31, n=300, r=2.4)
+    big = envgen.di6(seed=32, n=900, r=2.8)
+    geo = envgen.geometric(33, d=2, n=700, nbox=8, r=0.1)
+    pl = P.Planner(small).build()                       # sizes the edge arrays (synchronous)
+    for pb in (big, small, big):                        # grows past them, then fits, then fits
+        pl.pb = pb
+        pl.space, pl.goal, pl.params = P.space_struct(pb), P.goal_struct(pb), P.params_struct(pb)
+        pl.boxes, pl._box_tensors = P.boxes_on_device(pb)
+        pl.parent = torch.empty(pb.N, dtype=torch.int32, device="cuda")
+        pl.cost = torch.empty(pb.N, dtype=torch.float32, device="cuda")
+        pl.path = torch.empty(pb.N, dtype=torch.int32, device="cuda")
+        pl.build(asynchronous=True)
+        info = pl.plan()
+        G = {"parent": pl.parent.cpu().numpy(), "cost": pl.cost.cpu().numpy(), "info": info,
+             "path": pl.path.cpu().numpy()[:info["path_len"]]}
+        v = pl.view()
+        G.update(X=v.X.cpu().numpy(), goal=v.is_goal.cpu().numpy(), E=v.E, out_row=v.out_row.cpu().numpy(),
+                 out_col=v.out_col.cpu().numpy(), out_cost=v.out_cost.cpu().numpy(), in_row=v.in_row.cpu().numpy(),
+                 in_col=v.in_col.cpu().numpy(), in_cost=v.in_cost.cpu().numpy())
+        assert_same(O, G, *oracle_run(O, pb))
+    # a view right after an asynchronous build confirms it
+    g2 = P.Planner(geo).build()
+    g2.build(asynchronous=True)
+    v = g2.view()
+    ref = gpu_run(P, geo, build_only=True)
+    assert v.E == ref["E"] and np.array_equal(v.out_col.cpu().numpy(), ref["out_col"])
+    # x_init in a box: the plan reports what the synchronous build would have
+    bad = big.with_(x_init=((big.box_lo[0] + big.box_hi[0]) / 2).tolist() + [0.0, 0.0, 0.0])
+    pl.pb = bad
+    pl.space, pl.goal, pl.params = P.space_struct(bad), P.goal_struct(bad), P.params_struct(bad)
+    pl.build(asynchronous=True)
+    with pytest.raises(N.GmtError) as e:
+        pl.plan()
+    assert e.value.status == N.GMT_ERR_INVALID
+
