@@ -532,6 +532,8 @@ typedef struct {
     int32_t plan_threads;
 } gmt_profile;
 
+/* enable: 0 off, 1 every stage (two events around each), 2 the plan kernel
+ * only (events cost the device a few microseconds each). */
 gmt_status gmt_graph_set_profiling(gmt_graph* graph, int32_t enable);
 gmt_status gmt_graph_get_profile(gmt_graph* graph, gmt_profile* profile);
 

@@ -114,13 +114,13 @@ struct gmt_graph {
     gmt_params p_params;
     // profiling: event pairs around each kernel group
     enum { kSample, kPair, kTranspose, kScan, kFill, kPlan, kStages };
-    bool profiling = false;
+    int profiling = 0;  // 0 off, 1 every stage, 2 the plan kernel only
     bool stage_ran[kStages] = {};
     cudaEvent_t ev[kStages][2] = {};
     int last_blocks = 0, last_threads = 0;
 
     cudaError_t mark(int stage, int which, cudaStream_t st) {
-        if (!profiling) return cudaSuccess;
+        if (!profiling || (profiling == 2 && stage != kPlan)) return cudaSuccess;
         if (!ev[stage][which]) {
             cudaError_t e = cudaEventCreate(&ev[stage][which]);
             if (e != cudaSuccess) return e;
@@ -649,7 +649,8 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
 
 gmt_status gmt_graph_set_profiling(gmt_graph* g, int32_t enable) {
     if (!g) return fail(GMT_ERR_INVALID, "graph is NULL");
-    g->profiling = enable != 0;
+    if (enable < 0 || enable > 2) return fail(GMT_ERR_INVALID, "profiling must be 0, 1 or 2");
+    g->profiling = enable;
     return GMT_OK;
 }
 
