@@ -349,6 +349,18 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
         }
         ok = team.sync(ctl);
     }
+    // Line 12b's path is walked by rank 0 from the goal node back to x_init.
+    // The wavefront is over and the staged boxes are no longer needed, so CTA 0
+    // first copies the parent array into that shared memory when it fits:
+    // each hop is then a shared-memory read instead of an L2 round trip.
+    unsigned dyn_smem;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
+    int* const spar = reinterpret_cast<int*>(sbox);
+    const bool par_in_smem = ok && status == GMT_OK && (size_t)N * sizeof(int) <= dyn_smem;
+    if (par_in_smem && team.cta() == 0) {  // uniform over CTA 0
+        for (int v = threadIdx.x; v < N; v += blockDim.x) spar[v] = ldcg_i(&A.parent[v]);
+        __syncthreads();
+    }
     if (rank == 0) {
         const int err = ld_volatile(&ctl->error);
         ctl->status = err ? err : status;
@@ -359,9 +371,10 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
         if (ok && status == GMT_OK) {
             const int g = (int)(ctl->goal_key & 0xffffffffu);
             ctl->goal_node = g;
+            auto parent_of = [&](int v) { return par_in_smem ? spar[v] : ldcg_i(&A.parent[v]); };
             int len = 1, v = g;
             while (v > 0 && len <= N) {
-                v = ldcg_i(&A.parent[v]);
+                v = parent_of(v);
                 ++len;
             }
             if (v != 0) len = 0;  // not a chain back to x_init: report no path
@@ -370,7 +383,7 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
                 v = g;
                 for (int k = len - 1; k >= 0; --k) {
                     A.path[k] = v;
-                    if (v > 0) v = ldcg_i(&A.parent[v]);
+                    if (v > 0) v = parent_of(v);
                 }
             }
         }
@@ -415,7 +428,7 @@ namespace {
 template <int KIND, int DP>
 cudaError_t plan_t(const PlanArgs& a, int blocks, int threads, int cluster, cudaStream_t st) {
     const int nbs = a.boxes.count <= smem_box_cap(DP) ? a.boxes.count : 0;
-    const size_t smem = (size_t)2 * nbs * DP * sizeof(float);
+    const size_t smem = plan_smem_bytes(nbs, DP, a.N);
     if (cluster > 1) {
         auto kern = plan_kernel<ClusterTeam, KIND, DP>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -452,7 +465,7 @@ int occupancy_t(int threads) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = (size_t)2 * smem_box_cap(DP) * DP * sizeof(float);
+    const size_t smem = plan_smem_bytes(smem_box_cap(DP), DP, 12 * 1024);  // the most a launch asks for
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel<GridTeam, KIND, DP>, threads, smem);
     return per_sm * sms;
 }
@@ -487,7 +500,7 @@ int plan_max_cluster(int kind, int dp, int threads) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(c);
         cfg.blockDim = dim3(threads);
-        cfg.dynamicSmemBytes = (size_t)2 * smem_box_cap(3) * 3 * sizeof(float);
+        cfg.dynamicSmemBytes = plan_smem_bytes(smem_box_cap(3), 3, 12 * 1024);
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = c;
@@ -508,7 +521,7 @@ cudaError_t plan_batch_t(const PlanArgs* queries, const int* order, int nq, int*
                          const BatchScratch& scratch, int teams, int threads, int cluster, int max_boxes,
                          cudaStream_t st) {
     const int nbs = max_boxes <= smem_box_cap(DP) ? max_boxes : 0;
-    const size_t smem = (size_t)2 * nbs * DP * sizeof(float);
+    const size_t smem = plan_smem_bytes(nbs, DP, scratch.max_nodes);
     if (cluster <= 1) {
         plan_batch_kernel<BlockTeam, KIND, DP><<<teams, threads, smem, st>>>(queries, order, nq, next, slot,
                                                                              scratch, BlockTeam{});
@@ -537,7 +550,7 @@ int batch_teams_t(int threads, int cluster) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = (size_t)2 * smem_box_cap(DP) * DP * sizeof(float);
+    const size_t smem = plan_smem_bytes(smem_box_cap(DP), DP, 12 * 1024);  // the most a launch asks for
     if (cluster <= 1) {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_batch_kernel<BlockTeam, KIND, DP>, threads, smem);
