@@ -90,7 +90,8 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
             ctl->goal_flag[k] = 0;
         }
         ctl->gk[1] = 1ull << 32;  // one kept entry in open list 0
-        ctl->goal_key = ~0ull;
+        // the minimum (cost, index) goal node of the tree so far: x_init at cost 0 if it is one
+        ctl->goal_key = A.is_goal[0] ? 0ull : ~0ull;
     }
     bool ok = team.sync(ctl);
 
@@ -98,7 +99,9 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
     float theta = 0.0f;
     int it = 0;
     int status = GMT_OK;
-    unsigned long long n_push = 0, n_pull = 0, n_checks = 0, n_failed = 0, n_computed = 0;
+    unsigned long long n_push = 0, n_pull = 0;       // edges: may exceed 2^32 over a dense graph
+    unsigned n_checks = 0, n_failed = 0, n_computed = 0;  // per thread at most N each
+    unsigned n_tree = rank == 0 ? 1u : 0u;  // tree nodes: x_init, then one per commit
 
     while (ok) {
         if (it >= A.max_iters) { status = GMT_ERR_ITER_LIMIT; break; }
@@ -203,6 +206,7 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
             for (int ci = gwarp; ci < nc; ci += nwarps) {
                 const int x = ci == gwarp ? x_first : ldcg_i(&A.list_cand[ci]);
                 const int r0 = __ldg(&A.in_row[x]), r1 = __ldg(&A.in_row[x + 1]);
+                const bool x_goal = A.is_goal[x] != 0;
                 float sx[D];  // issued now, used by the check after the reduction
 #pragma unroll
                 for (int a = 0; a < D; ++a) sx[a] = __ldg(&A.X[(size_t)a * A.pitch + x]);
@@ -288,6 +292,10 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
                         const int s = atomicAdd(&ctl->new_count[p ^ 1], 1);
                         nxt[N - 1 - s] = make_int2(x, __float_as_int(bc));
                         atomicMin(&ctl->min_new[p], float_key(bc));
+                        // a tree node's cost never changes, so the minimum goal
+                        // node over commits is Line 12b's minimum over the tree
+                        ++n_tree;
+                        if (x_goal) atomicMin(&ctl->goal_key, ((unsigned long long)float_key(bc) << 32) | (unsigned)x);
                     } else {
                         ++n_failed;
                     }
@@ -319,35 +327,27 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
         }
     }
 
-    // ---- result: minimum-cost goal node (ties by index), counters, path
+    // ---- result: counters (the goal node was tracked at each commit; the loop
+    // ended after a team barrier, so every commit is visible), path
     if (ok) {
-        unsigned long long tree = 0;
-        for (int v = rank; v < N; v += size) {
-            const float cv = ldcg_f(&A.cost[v]);
-            if (cv < INF) {
-                ++tree;
-                if (status == GMT_OK && A.is_goal[v])
-                    atomicMin(&ctl->goal_key, ((unsigned long long)float_key(cv) << 32) | (unsigned)v);
-            }
-        }
+        unsigned long long checks = n_checks, failed = n_failed, computed = n_computed, tree = n_tree;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             n_push += __shfl_xor_sync(0xffffffffu, n_push, off);
             n_pull += __shfl_xor_sync(0xffffffffu, n_pull, off);
-            n_checks += __shfl_xor_sync(0xffffffffu, n_checks, off);
-            n_failed += __shfl_xor_sync(0xffffffffu, n_failed, off);
-            n_computed += __shfl_xor_sync(0xffffffffu, n_computed, off);
+            checks += __shfl_xor_sync(0xffffffffu, checks, off);
+            failed += __shfl_xor_sync(0xffffffffu, failed, off);
+            computed += __shfl_xor_sync(0xffffffffu, computed, off);
             tree += __shfl_xor_sync(0xffffffffu, tree, off);
         }
         if (lane == 0) {
             atomicAdd(&ctl->push_edges, n_push);
             atomicAdd(&ctl->pull_edges, n_pull);
-            atomicAdd(&ctl->checks, n_checks);
-            atomicAdd(&ctl->failed, n_failed);
-            atomicAdd(&ctl->checks_computed, n_computed);
+            atomicAdd(&ctl->checks, checks);
+            atomicAdd(&ctl->failed, failed);
+            atomicAdd(&ctl->checks_computed, computed);
             atomicAdd(&ctl->tree_size, tree);
         }
-        ok = team.sync(ctl);
     }
     // Line 12b's path is walked by rank 0 from the goal node back to x_init.
     // The wavefront is over and the staged boxes are no longer needed, so CTA 0
