@@ -229,7 +229,8 @@ def run_gpu(args, rank, world, local_rank):
     path = torch.empty(Nn, dtype=torch.int32, device=dev)
     graph = N.Graph()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    launches_per_step = 8 if pb0.kind == N.GMT_COST_DI else 5
+    # sample, pair filter, (transpose, in-row scan,) row scan, fill, plan
+    launches_per_step = 7 if pb0.kind == N.GMT_COST_DI else 5
 
     def step(k, level):
         # the build is queued without a host wait (gmt_plan confirms it; the
