@@ -465,3 +465,14 @@ def test_asynchronous_builds(O, P):
         pl.plan()
     assert e.value.status == N.GMT_ERR_INVALID
 
+
+
+def test_large_graph(O, P):
+    # 40001 nodes in 2D (Theorem 1 radius, 5.4 M edges, about 100 group
+    # expansions): the cell-list build, a wavefront over a large graph and the
+    # path walk from global memory (the parent array exceeds the 48 KB of
+    # shared memory); everything equals the oracle
+    pb = envgen.geometric(91, d=2, n=40000, nbox=40, r=0.0)
+    G = gpu_run(P, pb)
+    assert G["E"] > 5_000_000 and G["info"]["iters"] > 50
+    assert_same(O, G, *oracle_run(O, pb))
