@@ -39,8 +39,22 @@
 namespace gmtk {
 
 // ------------------------------------------------------------------- kernel
-template <class Team, int KIND, int DP>
-__device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, float* sbox) {
+// Loads of the wavefront's mutable state (snapshot, lists, control block):
+// from L2 (ld.global.cg) when the team spans several SMs, plain loads when a
+// single CTA keeps that state in its shared memory (SM = true).
+template <bool SM> __device__ __forceinline__ int st_i(const int* p) { if (SM) return *p; return __ldcg(p); }
+template <bool SM> __device__ __forceinline__ unsigned st_u(const unsigned* p) { if (SM) return *p; return __ldcg(p); }
+template <bool SM> __device__ __forceinline__ float st_f(const float* p) { if (SM) return *p; return __ldcg(p); }
+template <bool SM> __device__ __forceinline__ int2 st_i2(const int2* p) { if (SM) return *p; return __ldcg(p); }
+template <bool SM> __device__ __forceinline__ unsigned long long st_ull(const unsigned long long* p) {
+    if (SM) return *p;
+    return __ldcg(p);
+}
+
+// sbox_bytes: shared memory at sbox for staged boxes and, once the wavefront is
+// over, the copy of the parent array.
+template <class Team, int KIND, int DP, bool SM = false>
+__device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, float* sbox, size_t sbox_bytes) {
     constexpr int D = KIND == GMT_COST_DI ? 6 : (KIND == GMT_COST_DUBINS ? 4 : DP);
     const int nbs = A.boxes.count <= smem_box_cap(DP) ? A.boxes.count : 0;
     for (int t = threadIdx.x; t < nbs * DP; t += blockDim.x) {
@@ -111,20 +125,20 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
         int* G = A.list_g[p];
 
         // ---- phase 1: snapshot update, group selection, push
-        const unsigned long long gk_prev = __ldcg(&ctl->gk[p ^ 1]);
-        const int nk = (int)(gk_prev >> 32), nn = ldcg_i(&ctl->new_count[p]);
+        const unsigned long long gk_prev = st_ull<SM>(&ctl->gk[p ^ 1]);
+        const int nk = (int)(gk_prev >> 32), nn = st_i<SM>(&ctl->new_count[p]);
         // the lane's first open entry, loaded now so that its latency overlaps
         // the snapshot update below (which writes ocost only, never cur)
         const int ncur = nk + nn;
         const int t_first = cta + nctas * wib + nctas * wpc * lane;
         int2 e_first = make_int2(-1, 0);
-        if (t_first < ncur) e_first = __ldcg(&cur[t_first < nk ? t_first : N - 1 - (t_first - nk)]);
+        if (t_first < ncur) e_first = st_i2<SM>(&cur[t_first < nk ? t_first : N - 1 - (t_first - nk)]);
         if (it > 0) {
             const int ng_prev = (int)(gk_prev & 0xffffffffu);
             const int* Gprev = A.list_g[p ^ 1];
-            for (int t = rank; t < ng_prev; t += size) A.ocost[ldcg_i(&Gprev[t])] = INF;
+            for (int t = rank; t < ng_prev; t += size) A.ocost[st_i<SM>(&Gprev[t])] = INF;
             for (int t = rank; t < nn; t += size) {
-                const int2 e = __ldcg(&cur[N - 1 - t]);
+                const int2 e = st_i2<SM>(&cur[N - 1 - t]);
                 A.ocost[e.x] = __int_as_float(e.y);
             }
         }
@@ -135,7 +149,7 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
                 bool in_g = false, keep = false;
                 int2 e = make_int2(-1, 0);
                 if (t < ncur) {
-                    e = t0 == cta + nctas * wib ? e_first : __ldcg(&cur[t < nk ? t : N - 1 - (t - nk)]);
+                    e = t0 == cta + nctas * wib ? e_first : st_i2<SM>(&cur[t < nk ? t : N - 1 - (t - nk)]);
                     in_g = __int_as_float(e.y) <= theta;
                     keep = !in_g;
                 }
@@ -201,10 +215,10 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
         {
             // the warp's first candidate slot, loaded with the count (the list
             // holds at least N entries; the value is used only if ci < nc)
-            const int x_first = gwarp < N ? ldcg_i(&A.list_cand[gwarp]) : -1;
-            const int nc = ldcg_i(&ctl->cand_count[p]);
+            const int x_first = gwarp < N ? st_i<SM>(&A.list_cand[gwarp]) : -1;
+            const int nc = st_i<SM>(&ctl->cand_count[p]);
             for (int ci = gwarp; ci < nc; ci += nwarps) {
-                const int x = ci == gwarp ? x_first : ldcg_i(&A.list_cand[ci]);
+                const int x = ci == gwarp ? x_first : st_i<SM>(&A.list_cand[ci]);
                 const int r0 = __ldg(&A.in_row[x]), r1 = __ldg(&A.in_row[x + 1]);
                 const bool x_goal = A.is_goal[x] != 0;
                 float sx[D];  // issued now, used by the check after the reduction
@@ -226,7 +240,7 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
                         ic[u] = e < r1 ? __ldg(&A.in_cost[e]) : 0.0f;
                     }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) oc[u] = ys[u] >= 0 ? ldcg_f(&A.ocost[ys[u]]) : INF;
+                    for (int u = 0; u < 4; ++u) oc[u] = ys[u] >= 0 ? st_f<SM>(&A.ocost[ys[u]]) : INF;
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         if (oc[u] < INF) {
@@ -305,9 +319,9 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
         if (!(ok = team.sync(ctl))) break;
 
         // ---- Line 12 / Line 11: termination test, next threshold
-        const int goal = ldcg_i(&ctl->goal_flag[p]);
-        const int n_open = (int)(__ldcg(&ctl->gk[p]) >> 32) + ldcg_i(&ctl->new_count[p ^ 1]);
-        const unsigned mk = min(ldcg_u(&ctl->min_keep[p]), ldcg_u(&ctl->min_new[p]));
+        const int goal = st_i<SM>(&ctl->goal_flag[p]);
+        const int n_open = (int)(st_ull<SM>(&ctl->gk[p]) >> 32) + st_i<SM>(&ctl->new_count[p ^ 1]);
+        const unsigned mk = min(st_u<SM>(&ctl->min_keep[p]), st_u<SM>(&ctl->min_new[p]));
         ++it;
         if (goal) { status = GMT_OK; break; }
         if (n_open == 0) { status = GMT_NO_PATH; break; }
@@ -353,10 +367,8 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
     // The wavefront is over and the staged boxes are no longer needed, so CTA 0
     // first copies the parent array into that shared memory when it fits:
     // each hop is then a shared-memory read instead of an L2 round trip.
-    unsigned dyn_smem;
-    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
     int* const spar = reinterpret_cast<int*>(sbox);
-    const bool par_in_smem = ok && status == GMT_OK && (size_t)N * sizeof(int) <= dyn_smem;
+    const bool par_in_smem = ok && status == GMT_OK && (size_t)N * sizeof(int) <= sbox_bytes;
     if (par_in_smem && team.cta() == 0) {  // uniform over CTA 0
         for (int v = threadIdx.x; v < N; v += blockDim.x) spar[v] = ldcg_i(&A.parent[v]);
         __syncthreads();
@@ -393,7 +405,37 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
 template <class Team, int KIND, int DP>
 __global__ void __launch_bounds__(1024, 1) plan_kernel(PlanArgs A, Team team) {
     extern __shared__ float sbox[];
-    plan_body<Team, KIND, DP>(A, team, sbox);
+    unsigned dyn_smem;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
+    plan_body<Team, KIND, DP>(A, team, sbox, dyn_smem);
+}
+
+// One CTA whose wavefront state lives in its shared memory: after the region
+// of staged boxes / parent copy (region0 bytes) come the control block, the
+// snapshot (ocost), the stamps and the lists (plan_smem_state_bytes).  Every
+// step of the body then touches L2 only for the read-only CSR, the samples and
+// the outputs.  The control block is copied out for the host at the end.
+template <int KIND, int DP>
+__global__ void __launch_bounds__(1024, 1) plan_kernel_smem(PlanArgs A, unsigned region0) {
+    extern __shared__ __align__(16) float smem[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(smem);
+    PlanCtl* gctl = A.ctl;
+    PlanCtl* sctl = reinterpret_cast<PlanCtl*>(base + region0);
+    const size_t N = (size_t)A.N;
+    float* socost = reinterpret_cast<float*>(base + region0 + kSmemCtlBytes);
+    int* sstamp = reinterpret_cast<int*>(socost + N);
+    int* slists = reinterpret_cast<int*>(base + region0 + kSmemCtlBytes + smem_round16(8 * N));
+    for (int t = threadIdx.x; t < (int)(sizeof(PlanCtl) / sizeof(int)); t += blockDim.x)
+        reinterpret_cast<int*>(sctl)[t] = 0;
+    __syncthreads();
+    A.ctl = sctl;
+    A.ocost = socost;
+    A.stamp = sstamp;
+    assign_plan_lists(A, slists, N);
+    plan_body<BlockTeam, KIND, DP, true>(A, BlockTeam{}, smem, region0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < (int)(sizeof(PlanCtl) / sizeof(int)); t += blockDim.x)
+        reinterpret_cast<int*>(gctl)[t] = reinterpret_cast<const int*>(sctl)[t];
 }
 
 // Persistent batched wavefront: every team (a CTA, or a cluster) takes the next
@@ -418,7 +460,9 @@ __global__ void __launch_bounds__(1024, 1) plan_batch_kernel(const PlanArgs* __r
         A.ocost = scratch.ocost + team_id * nm;
         A.stamp = scratch.stamp + team_id * nm;
         assign_plan_lists(A, scratch.lists + team_id * plan_list_stride(nm), nm);
-        plan_body<Team, KIND, DP>(A, team, sbox);
+        unsigned dyn_smem;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
+        plan_body<Team, KIND, DP>(A, team, sbox, dyn_smem);
         team.sync(nullptr);
     }
 }
@@ -448,6 +492,19 @@ cudaError_t plan_t(const PlanArgs& a, int blocks, int threads, int cluster, cuda
         return cudaLaunchKernelEx(&cfg, kern, a, ClusterTeam{});
     }
     if (blocks <= 1) {
+        // one CTA: the wavefront state goes to shared memory when it fits
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const size_t region0 = smem_round16(smem);
+        const size_t total = plan_smem_state_bytes(region0, a.N);
+        if (total <= (size_t)optin) {
+            auto kern = plan_kernel_smem<KIND, DP>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total);
+            if (e != cudaSuccess) return e;
+            kern<<<1, threads, total, st>>>(a, (unsigned)region0);
+            return cudaGetLastError();
+        }
         plan_kernel<BlockTeam, KIND, DP><<<1, threads, smem, st>>>(a, BlockTeam{});
         return cudaGetLastError();
     }

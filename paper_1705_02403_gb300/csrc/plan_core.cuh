@@ -280,4 +280,14 @@ inline size_t plan_smem_bytes(int staged_boxes, int dp, int N) {
     return parents <= 48 * 1024 && parents > boxes ? parents : boxes;
 }
 
+// Shared-memory layout of the single-CTA kernel that keeps the wavefront state
+// on chip (plan_kernel_smem): region0 (boxes / parent copy), the control
+// block, ocost and stamp (N each), the lists.
+__host__ __device__ constexpr size_t smem_round16(size_t b) { return (b + 15) / 16 * 16; }
+constexpr size_t kSmemCtlBytes = smem_round16(sizeof(PlanCtl));
+inline size_t plan_smem_state_bytes(size_t region0, int N) {
+    return smem_round16(region0) + kSmemCtlBytes + smem_round16((size_t)8 * N) +
+           smem_round16(plan_list_stride((size_t)N) * sizeof(int));
+}
+
 }  // namespace gmtk
