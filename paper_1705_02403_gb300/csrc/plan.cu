@@ -39,18 +39,6 @@
 namespace gmtk {
 
 // ------------------------------------------------------------------- kernel
-// Loads of the wavefront's mutable state (snapshot, lists, control block):
-// from L2 (ld.global.cg) when the team spans several SMs, plain loads when a
-// single CTA keeps that state in its shared memory (SM = true).
-template <bool SM> __device__ __forceinline__ int st_i(const int* p) { if (SM) return *p; return __ldcg(p); }
-template <bool SM> __device__ __forceinline__ unsigned st_u(const unsigned* p) { if (SM) return *p; return __ldcg(p); }
-template <bool SM> __device__ __forceinline__ float st_f(const float* p) { if (SM) return *p; return __ldcg(p); }
-template <bool SM> __device__ __forceinline__ int2 st_i2(const int2* p) { if (SM) return *p; return __ldcg(p); }
-template <bool SM> __device__ __forceinline__ unsigned long long st_ull(const unsigned long long* p) {
-    if (SM) return *p;
-    return __ldcg(p);
-}
-
 // sbox_bytes: shared memory at sbox for staged boxes and, once the wavefront is
 // over, the copy of the parent array.
 template <class Team, int KIND, int DP, bool SM = false>
@@ -224,31 +212,9 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
                 float sx[D];  // issued now, used by the check after the reduction
 #pragma unroll
                 for (int a = 0; a < D; ++a) sx[a] = __ldg(&A.X[(size_t)a * A.pitch + x]);
-                // Each lane keeps the minimum (cost, index) of its entries: a
-                // total order, so the order of the entries does not matter.
-                // Four chunks of 32 at a time: their column and cost loads, then
-                // their snapshot gathers, each issued together.
-                float bc = INF;
-                int by = INT_MAX, be = -1;
-                for (int eb = r0; eb < r1; eb += 4 * 32) {
-                    int ys[4];
-                    float ic[4], oc[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int e = eb + 32 * u + lane;
-                        ys[u] = e < r1 ? __ldg(&A.in_col[e]) : -1;
-                        ic[u] = e < r1 ? __ldg(&A.in_cost[e]) : 0.0f;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) oc[u] = ys[u] >= 0 ? st_f<SM>(&A.ocost[ys[u]]) : INF;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (oc[u] < INF) {
-                            const float c = oc[u] + ic[u];
-                            if (c < bc || (c == bc && ys[u] < by)) { bc = c; by = ys[u]; be = eb + 32 * u + lane; }
-                        }
-                    }
-                }
+                float bc;
+                int by, be;
+                lane_parent_min<SM>(A.in_col, A.in_cost, A.ocost, r0, r1, lane, &bc, &by, &be);
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
                     const float oc = __shfl_xor_sync(0xffffffffu, bc, off);

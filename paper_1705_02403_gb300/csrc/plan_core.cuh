@@ -269,6 +269,55 @@ __device__ __forceinline__ bool dubins_free_warp(const float* y, const float* x,
     return true;
 }
 
+// Loads of the wavefront's mutable state (snapshot, lists, control block):
+// from L2 (ld.global.cg) when the team spans several SMs, plain loads when a
+// single CTA keeps that state in its shared memory (SM = true).
+template <bool SM> __device__ __forceinline__ int st_i(const int* p) { if (SM) return *p; return __ldcg(p); }
+template <bool SM> __device__ __forceinline__ unsigned st_u(const unsigned* p) { if (SM) return *p; return __ldcg(p); }
+template <bool SM> __device__ __forceinline__ float st_f(const float* p) { if (SM) return *p; return __ldcg(p); }
+template <bool SM> __device__ __forceinline__ int2 st_i2(const int2* p) { if (SM) return *p; return __ldcg(p); }
+template <bool SM> __device__ __forceinline__ unsigned long long st_ull(const unsigned long long* p) {
+    if (SM) return *p;
+    return __ldcg(p);
+}
+
+// Lazy parent (Alg. 1, Lines 5-6), one lane's share: over the in-row entries
+// r0 + lane, r0 + lane + 32, ... the minimum (cost, index) of
+// fl(ocost[y] + in_cost[e]) among open y (ocost < +inf); *be = its edge, -1
+// if none.  (cost, index) is a total order, so the order of the entries does
+// not matter: four chunks of 32 are taken at a time, their column and cost
+// loads issued together, then their snapshot gathers.
+template <bool SM>
+__device__ __forceinline__ void lane_parent_min(const int* __restrict__ in_col, const float* __restrict__ in_cost,
+                                                const float* ocost, int r0, int r1, int lane, float* bc_out,
+                                                int* by_out, int* be_out) {
+    const float INF = f_inf();
+    float bc = INF;
+    int by = INT_MAX, be = -1;
+    for (int eb = r0; eb < r1; eb += 4 * 32) {
+        int ys[4];
+        float ic[4], oc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = eb + 32 * u + lane;
+            ys[u] = e < r1 ? __ldg(&in_col[e]) : -1;
+            ic[u] = e < r1 ? __ldg(&in_cost[e]) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) oc[u] = ys[u] >= 0 ? st_f<SM>(&ocost[ys[u]]) : INF;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (oc[u] < INF) {
+                const float c = oc[u] + ic[u];
+                if (c < bc || (c == bc && ys[u] < by)) { bc = c; by = ys[u]; be = eb + 32 * u + lane; }
+            }
+        }
+    }
+    *bc_out = bc;
+    *by_out = by;
+    *be_out = be;
+}
+
 // Largest box count staged in shared memory (2 * count * DP floats).
 __host__ __device__ constexpr int smem_box_cap(int dp) { return 4096 / dp; }
 // Dynamic shared memory of a plan launch: the staged boxes, or, when it is

@@ -88,29 +88,9 @@ __device__ bool pull_candidate(const PlanArgs* __restrict__ Ap, LockSmem& sm, in
     float sx[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) sx[a] = __ldg(&X[(size_t)a * pitch + x]);
-    // each lane's minimum (cost, index) over its entries (a total order);
-    // four chunks' loads, then their snapshot gathers, issued together
-    float bc = INF;
-    int by = INT_MAX, be = -1;
-    for (int eb = r0; eb < r1; eb += 4 * 32) {
-        int ys[4];
-        float ic[4], oc[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = eb + 32 * u + lane;
-            ys[u] = e < r1 ? __ldg(&in_col[e]) : -1;
-            ic[u] = e < r1 ? __ldg(&in_cost[e]) : 0.0f;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) oc[u] = ys[u] >= 0 ? ldcg_f(&ocost[ys[u]]) : INF;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (oc[u] < INF) {
-                const float c = oc[u] + ic[u];
-                if (c < bc || (c == bc && ys[u] < by)) { bc = c; by = ys[u]; be = eb + 32 * u + lane; }
-            }
-        }
-    }
+    float bc;
+    int by, be;
+    lane_parent_min<false>(in_col, in_cost, ocost, r0, r1, lane, &bc, &by, &be);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const float oc = __shfl_xor_sync(kFull, bc, off);
