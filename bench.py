@@ -40,7 +40,7 @@ METRIC = "ms/plan p50/p99 & edges checked/s; learned+batched vs plain at equal p
 # ncu captures summarised in profiles/plan_kernel_double_integrator_6d_n4096.md
 # and profiles/plan_kernel_geometric_2d_n1024.md.
 # Set to None whenever plan_kernel changes until it is captured again.
-PLAN_KERNEL_DRAM_BYTES = {"di6": 2220032, "geo2d": 420352}
+PLAN_KERNEL_DRAM_BYTES = {"di6": 2220288, "geo2d": 419840}
 
 
 def parse():
@@ -229,8 +229,9 @@ def run_gpu(args, rank, world, local_rank):
     path = torch.empty(Nn, dtype=torch.int32, device=dev)
     graph = N.Graph()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    # sample, pair filter, (transpose, in-row scan,) row scan, fill, plan
-    launches_per_step = 7 if pb0.kind == N.GMT_COST_DI else 5
+    # sample, pair filter, (transpose,) row scans (both directions in one
+    # launch), fill, plan
+    launches_per_step = 6 if pb0.kind == N.GMT_COST_DI else 5
 
     def step(k, level):
         # the build is queued without a host wait (gmt_plan confirms it; the
@@ -363,7 +364,7 @@ def run_gpu(args, rank, world, local_rank):
         line["serving"] = bench_serving(local_rank)
         line["dubins"] = bench_dubins(dev, flush)
         line["gpu_launches_extras"] = ("batched: 7 launches per group per batch (replayed CUDA graph); serving: 3 per "
-                                       "request; dubins: 9-10 per build, 1 per plan")
+                                       "request; dubins: 8-9 per build, 1 per plan")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         seeds_cpu = [seeds[args.warmup + j] for j in range(3)]
         rows = 256 if args.workload == "di6" else 1025

@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(kCellWarps * 32) batch_cells_rows_kernel(const
 template <int KIND, int D>
 __global__ void __launch_bounds__(kFillWarps * 32) batch_fill_kernel(const QueryDev* __restrict__ Q,
                                                                      const long long* __restrict__ off, int nq) {
+    __shared__ int list[kFillWarps][kFillList];
     const long long w = (long long)blockIdx.x * kFillWarps + (threadIdx.x >> 5);
     if (w >= off[nq]) return;
     const int k = find_query(off, nq, w);
@@ -190,10 +191,10 @@ __global__ void __launch_bounds__(kFillWarps * 32) batch_fill_kernel(const Query
     if ((long long)row[q.s.N] > q.edge_cap) return;
     if (incoming)
         fill_row<KIND, D, true>(q.s, q.X, q.maskT, q.in_row, q.in_col, q.in_cost, q.in_tau, q.in_path,
-                                (int)(w - off[k]));
+                                (int)(w - off[k]), list[threadIdx.x >> 5]);
     else
         fill_row<KIND, D, false>(q.s, q.X, q.mask, q.out_row, q.out_col, q.out_cost, q.out_tau, nullptr,
-                                 (int)(w - off[k]));
+                                 (int)(w - off[k]), list[threadIdx.x >> 5]);
 }
 
 namespace {

@@ -79,7 +79,7 @@ struct gmt_graph {
     float* in_path = nullptr;      size_t cap_in_path = 0;   // Dubins airplane: [E][4] (t, p, q, word bits)
     uint32_t* mask = nullptr;      size_t cap_mask = 0;
     uint32_t* maskT = nullptr;     size_t cap_maskT = 0;
-    int* flags = nullptr;          size_t cap_flags = 0;   // [sample flags, max row length, row overflow, -]
+    int* flags = nullptr;          size_t cap_flags = 0;   // [sample flags, max row length, row overflow, fill ticket]
     // cell-list neighbour build
     int* cell_of = nullptr;        size_t cap_cell_of = 0;
     int* cell_sorted = nullptr;    size_t cap_cell_sorted = 0;
@@ -438,8 +438,9 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
         LAUNCH(g->mark(gmt_graph::kTranspose, 1, st), "event");
     }
     LAUNCH(g->mark(gmt_graph::kScan, 0, st), "event");
-    LAUNCH(launch_scan(g->out_count, g->out_row, g->N, st), "scan kernel");
-    if (g->directed()) LAUNCH(launch_scan(g->in_count, g->in_row_own, g->N, st), "scan kernel");
+    LAUNCH(launch_scan2(g->out_count, g->out_row, g->directed() ? g->in_count : nullptr,
+                        g->directed() ? g->in_row_own : nullptr, g->N, st),
+           "scan kernel");
     LAUNCH(g->mark(gmt_graph::kScan, 1, st), "event");
     LAUNCH(cudaMemcpyAsync(g->h_scalars, g->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
     LAUNCH(cudaMemcpyAsync(g->h_scalars + 2, g->out_row + N, sizeof(int), cudaMemcpyDeviceToHost, st),
@@ -457,7 +458,7 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
                                                        di_a ? g->in_tau : nullptr, dub_a ? g->in_path : nullptr,
                                                        cap_now}
                                              : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
-        LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, st), "fill kernel");
+        LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, g->flags + 3, st), "fill kernel");
         LAUNCH(g->mark(gmt_graph::kFill, 1, st), "event");
         g->used_cells = false;
         g->E = -1;
@@ -519,7 +520,7 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
         const FillDir in_dir = directed ? FillDir{g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own,
                                                   di ? g->in_tau : nullptr, dubins ? g->in_path : nullptr, 0}
                                         : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
-        LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, st), "fill kernel");
+        LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, g->flags + 3, st), "fill kernel");
     }
     LAUNCH(g->mark(gmt_graph::kFill, 1, st), "event");
 #undef GROW

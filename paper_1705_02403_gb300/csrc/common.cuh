@@ -174,6 +174,40 @@ __device__ __forceinline__ float di_tau(const DICoef& k, float r) {
     return hi;
 }
 
+// Two arrival times at once, each bit-identical to di_tau: the same grid
+// points and the same halvings, with the two searches interleaved so that
+// their dependent chains overlap.  The grid is scanned two points per step
+// (the first point with q >= 0 wins, as in the one-point scan).
+__device__ __forceinline__ void di_tau2(const DICoef& k0, const DICoef& k1, float r, float& t0, float& t1) {
+    static_assert(kDIGrid % 2 == 0, "two grid points per step");
+    // g0, g1: the first grid index with q >= 0 (0 while none is found)
+    int g0 = 0, g1 = 0;
+    for (int g = 1; g <= kDIGrid; g += 2) {
+        const float ta = r * ((float)g / (float)kDIGrid), tb = r * ((float)(g + 1) / (float)kDIGrid);
+        const bool a0 = di_q(k0, ta) >= 0.0f, b0 = di_q(k0, tb) >= 0.0f;
+        const bool a1 = di_q(k1, ta) >= 0.0f, b1 = di_q(k1, tb) >= 0.0f;
+        if (g0 == 0) g0 = a0 ? g : b0 ? g + 1 : 0;
+        if (g1 == 0) g1 = a1 ? g : b1 ? g + 1 : 0;
+        if (g0 != 0 && g1 != 0) break;
+    }
+    // the bracket [tau_{g-1}, tau_g] (tau_0 = 0); an edge without a root in
+    // (0, r] takes lo = hi = 0, so its halvings stay finite, and +inf
+    float lo0 = g0 > 1 ? r * ((float)(g0 - 1) / (float)kDIGrid) : 0.0f;
+    float hi0 = g0 > 0 ? r * ((float)g0 / (float)kDIGrid) : 0.0f;
+    float lo1 = g1 > 1 ? r * ((float)(g1 - 1) / (float)kDIGrid) : 0.0f;
+    float hi1 = g1 > 0 ? r * ((float)g1 / (float)kDIGrid) : 0.0f;
+    for (int s = 0; s < kDIBisect; ++s) {
+        const float m0 = lo0 + (hi0 - lo0) * 0.5f, m1 = lo1 + (hi1 - lo1) * 0.5f;
+        const bool n0 = di_q(k0, m0) < 0.0f, n1 = di_q(k1, m1) < 0.0f;
+        lo0 = n0 ? m0 : lo0;
+        hi0 = n0 ? hi0 : m0;
+        lo1 = n1 ? m1 : lo1;
+        hi1 = n1 ? hi1 : m1;
+    }
+    t0 = g0 > 0 ? hi0 : f_inf();
+    t1 = g1 > 0 ? hi1 : f_inf();
+}
+
 __device__ __forceinline__ float di_J(const DICoef& k, float t) { return ((k.c / t - k.b) / t + k.a) / t + t; }
 
 // Cost from state s0 to state s1 (+inf when no root lies in (0, r]).

@@ -17,9 +17,12 @@
 //                     root procedure, with per-warp compaction between stages
 //   pair_mask_dubins_kernel  the same for the Dubins airplane: distance
 //                     prefilter, then the shortest-word cost from a queue
-//   fill_kernel       one warp per row: prefix over the row's words, column
-//                     list in shared memory, one edge cost per lane; out- and
-//                     in-rows in one launch
+//   scan2_kernel      both directions' row offsets (one block each)
+//   fill_kernel       persistent blocks, eight rows at a time: each warp
+//                     gathers a row's columns (prefix over its words) into a
+//                     shared-memory list, then the block shares out the eight
+//                     rows' edges (two per thread for the double integrator);
+//                     out- and in-rows in one launch
 #include <cstdio>
 
 #include "graph_body.cuh"
@@ -186,15 +189,37 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ coun
     scan_rows(count, row, N);
 }
 
-// blockIdx.y = 0: out-rows; 1: in-rows (double integrator, Dubins airplane).
+// Block 0 scans the out-row counts, block 1 the in-row counts.
+__global__ void __launch_bounds__(1024) scan2_kernel(const int* __restrict__ count0, int* __restrict__ row0,
+                                                     const int* __restrict__ count1, int* __restrict__ row1, int N) {
+    if (blockIdx.x == 0) scan_rows(count0, row0, N);
+    else scan_rows(count1, row1, N);
+}
+
+// Persistent blocks take groups of kFillWarps rows from a ticket counter
+// (zeroed with the build's flags): the out-rows' groups, then the in-rows'
+// (double integrator, Dubins airplane).  A direction whose edge count exceeds
+// its arrays' capacity writes nothing (the caller rebuilds).
 template <int KIND, int D>
-__global__ void __launch_bounds__(kFillWarps * 32) fill_kernel(SpaceArgs s, const float* __restrict__ X, FillDir out,
-                                                               FillDir in) {
-    const int v = blockIdx.x * kFillWarps + (threadIdx.x >> 5);
-    const FillDir& f = blockIdx.y == 0 ? out : in;
-    if (f.cap > 0 && (long long)__ldg(&f.row[s.N]) > f.cap) return;  // does not fit: the caller rebuilds
-    if (blockIdx.y == 0) fill_row<KIND, D, false>(s, X, out.mask, out.row, out.col, out.cost, out.tau, out.path, v);
-    else fill_row<KIND, D, true>(s, X, in.mask, in.row, in.col, in.cost, in.tau, in.path, v);
+__global__ void __launch_bounds__(kFillWarps * 32, 4) fill_kernel(SpaceArgs s, const float* __restrict__ X, FillDir out,
+                                                               FillDir in, int* __restrict__ ticket) {
+    __shared__ FillShared sh;
+    const int groups = (s.N + kFillWarps - 1) / kFillWarps;
+    const int ngroups = in.mask ? 2 * groups : groups;
+    const bool out_ok = !(out.cap > 0 && (long long)__ldg(&out.row[s.N]) > out.cap);
+    const bool in_ok = in.mask && !(in.cap > 0 && (long long)__ldg(&in.row[s.N]) > in.cap);
+    for (;;) {
+        if (threadIdx.x == 0) sh.group = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int gi = sh.group;
+        __syncthreads();  // every thread has read the ticket before thread 0 takes the next
+        if (gi >= ngroups) break;
+        if (gi < groups) {
+            if (out_ok) fill_group<KIND, D, false>(s, X, out, gi * kFillWarps, sh);
+        } else if (in_ok) {
+            fill_group<KIND, D, true>(s, X, in, (gi - groups) * kFillWarps, sh);
+        }
+    }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -233,9 +258,22 @@ cudaError_t mask_t(const SpaceArgs& s, const float* X, uint32_t* mask, int* cnt,
     return cudaGetLastError();
 }
 template <int KIND, int D>
-cudaError_t fill_t(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, cudaStream_t st) {
-    const dim3 grid((s.N + kFillWarps - 1) / kFillWarps, in.mask ? 2 : 1);
-    fill_kernel<KIND, D><<<grid, kFillWarps * 32, 0, st>>>(s, X, out, in);
+cudaError_t fill_t(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, int* ticket,
+                   cudaStream_t st) {
+    // as many blocks as fit on the GPU at once (queried once per instantiation)
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_kernel<KIND, D>, kFillWarps * 32, 0);
+        if (e != cudaSuccess) return e;
+        resident = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const long long groups = (long long)((s.N + kFillWarps - 1) / kFillWarps) * (in.mask ? 2 : 1);
+    const int blocks = (int)(groups < resident ? groups : resident);
+    fill_kernel<KIND, D><<<blocks, kFillWarps * 32, 0, st>>>(s, X, out, in, ticket);
     return cudaGetLastError();
 }
 }  // namespace
@@ -314,10 +352,17 @@ cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, cudaStream_t st) {
-    if (s.kind == GMT_COST_DI) return fill_t<GMT_COST_DI, 6>(s, X, out, in, st);
-    if (s.kind == GMT_COST_DUBINS) return fill_t<GMT_COST_DUBINS, 4>(s, X, out, in, st);
-    GMT_EUCLID_DIMS(fill_t, s, X, out, in, st)
+cudaError_t launch_scan2(const int* count0, int* row0, const int* count1, int* row1, int N, cudaStream_t st) {
+    if (!count1) return launch_scan(count0, row0, N, st);
+    scan2_kernel<<<2, 1024, 0, st>>>(count0, row0, count1, row1, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, int* ticket,
+                        cudaStream_t st) {
+    if (s.kind == GMT_COST_DI) return fill_t<GMT_COST_DI, 6>(s, X, out, in, ticket, st);
+    if (s.kind == GMT_COST_DUBINS) return fill_t<GMT_COST_DUBINS, 4>(s, X, out, in, ticket, st);
+    GMT_EUCLID_DIMS(fill_t, s, X, out, in, ticket, st)
 }
 
 }  // namespace gmtk

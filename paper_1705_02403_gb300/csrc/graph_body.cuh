@@ -532,75 +532,115 @@ __device__ __forceinline__ void scan_rows(const int* __restrict__ count, int* __
     if (threadIdx.x == 0) row[N] = carry;
 }
 
-// One warp per row v.  The row's words are read 32 at a time (one per lane),
-// the lanes' bit counts are prefix-summed, and the columns are written, in
-// ascending order, to a per-warp list in shared memory; the lanes then take
-// the listed edges one each, so the cost evaluations keep every lane busy.
-// Out-rows compute c(v, j), in-rows c(j, v), with the same formulas on the
-// same states, so an edge's cost (and arrival time) is the same bits in both
-// CSRs and the two directions need not wait for each other.
+// Fill: the CSR columns and costs from the bit matrix.  A warp reads a row's
+// words 32 at a time (one per lane), prefix-sums the lanes' bit counts and
+// writes the columns, in ascending order, to its list in shared memory; the
+// listed edges are then evaluated.  Out-rows compute c(v, j), in-rows c(j, v),
+// with the same formulas on the same states, so an edge's cost (and arrival
+// time, or shortest word) is the same bits in both CSRs and the two
+// directions need not wait for each other.
 constexpr int kFillWarps = 8;
 constexpr int kFillList = 1024;  // column list per warp (a 32-word chunk holds at most 1024)
 
-// One warp: row v (warp w of a block of kFillWarps warps).
+// The edge between row node v (state xv) and column j, written at CSR position e.
 template <int KIND, int D, bool INCOMING>
-__device__ __forceinline__ void fill_row(const SpaceArgs& s, const float* __restrict__ X,
-                                         const uint32_t* __restrict__ M, const int* __restrict__ row,
-                                         int* __restrict__ col, float* __restrict__ cost, float* __restrict__ tau,
-                                         float* __restrict__ path, int v) {
-    __shared__ int list[kFillWarps][kFillList];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (v >= s.N) return;
-    float xv[D];
+__device__ __forceinline__ void fill_edge(const SpaceArgs& s, const float* __restrict__ X, const float* xv, int j,
+                                          int e, int* __restrict__ col, float* __restrict__ cost,
+                                          float* __restrict__ tau, float* __restrict__ path) {
+    float xj[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) xv[a] = X[(size_t)a * s.pitch + v];
-    const int W = (s.N + 31) / 32;
-    int base = row[v];
-    // Columns are gathered in the warp's list (ascending) and their costs
-    // computed 32 at a time once the list is full or the row ends, so that
-    // the lanes stay busy when a row's edges spread over many words.
-    int cnt = 0;
-    auto flush = [&]() {
-        __syncwarp();
-        for (int t = lane; t < cnt; t += 32) {
-            const int j = list[warp][t];
-            float c, tj = 0.0f;
-            if (KIND == GMT_COST_DUBINS) {
-                float xj[D];
+    for (int a = 0; a < D; ++a) xj[a] = X[(size_t)a * s.pitch + j];
+    const float* from = INCOMING ? xj : xv;
+    const float* to = INCOMING ? xv : xj;
+    float c;
+    if (KIND == GMT_COST_DUBINS) {
+        const DubPath P = dubins_path(from, to, s.rho);
+        c = dubins_length(P, from, to);
+        if (path) reinterpret_cast<float4*>(path)[e] = make_float4(P.t, P.p, P.q, __int_as_float(P.word));
+    } else if (KIND == GMT_COST_DI) {
+        const DICoef k = di_coef(from, to);
+        const float t = di_tau(k, s.r);
+        c = di_J(k, t);
+        tau[e] = t;
+    } else {
+        c = edge_cost<KIND, D>(s, from, to);
+    }
+    col[e] = j;
+    cost[e] = c;
+}
+
+// Two double-integrator edges at once, their root searches interleaved (the
+// second is skipped at the stores when !two).
+template <int D, bool INCOMING>
+__device__ __forceinline__ void fill_edge_di2(const SpaceArgs& s, const float* __restrict__ X, const float* xv0,
+                                              int j0, int e0, const float* xv1, int j1, int e1, bool two,
+                                              int* __restrict__ col, float* __restrict__ cost,
+                                              float* __restrict__ tau) {
+    float x0[D], x1[D];
 #pragma unroll
-                for (int a = 0; a < D; ++a) xj[a] = X[(size_t)a * s.pitch + j];
-                const float* from = INCOMING ? xj : xv;
-                const float* to = INCOMING ? xv : xj;
-                const DubPath P = dubins_path(from, to, s.rho);
-                c = dubins_length(P, from, to);
-                if (path)
-                    reinterpret_cast<float4*>(path)[base + t] = make_float4(P.t, P.p, P.q, __int_as_float(P.word));
-            } else if (KIND == GMT_COST_DI) {
-                // the same formulas on the same states as the edge's out-row:
-                // identical bits in both directions
-                float xj[D];
-#pragma unroll
-                for (int a = 0; a < D; ++a) xj[a] = X[(size_t)a * s.pitch + j];
-                const DICoef k = INCOMING ? di_coef(xj, xv) : di_coef(xv, xj);
-                tj = di_tau(k, s.r);
-                c = di_J(k, tj);
-            } else {
-                float xj[D];
-#pragma unroll
-                for (int a = 0; a < D; ++a) xj[a] = X[(size_t)a * s.pitch + j];
-                c = INCOMING ? edge_cost<KIND, D>(s, xj, xv) : edge_cost<KIND, D>(s, xv, xj);
-            }
-            if (KIND == GMT_COST_DI) tau[base + t] = tj;
-            col[base + t] = j;
-            cost[base + t] = c;
+    for (int a = 0; a < D; ++a) {
+        x0[a] = X[(size_t)a * s.pitch + j0];
+        x1[a] = X[(size_t)a * s.pitch + j1];
+    }
+    const DICoef k0 = INCOMING ? di_coef(x0, xv0) : di_coef(xv0, x0);
+    const DICoef k1 = INCOMING ? di_coef(x1, xv1) : di_coef(xv1, x1);
+    float t0, t1;
+    di_tau2(k0, k1, s.r, t0, t1);
+    col[e0] = j0;
+    cost[e0] = di_J(k0, t0);
+    tau[e0] = t0;
+    if (two) {
+        col[e1] = j1;
+        cost[e1] = di_J(k1, t1);
+        tau[e1] = t1;
+    }
+}
+
+// One warp evaluates the first cnt entries of its list (row v, state xv),
+// written from CSR position base on: one edge per lane, two for the double
+// integrator.
+template <int KIND, int D, bool INCOMING>
+__device__ __forceinline__ void fill_list_warp(const SpaceArgs& s, const float* __restrict__ X, const float* xv,
+                                               const int* list, int cnt, int base, int* __restrict__ col,
+                                               float* __restrict__ cost, float* __restrict__ tau,
+                                               float* __restrict__ path) {
+    const int lane = threadIdx.x & 31;
+    if (KIND == GMT_COST_DI) {
+        for (int t = lane; t < cnt; t += 64) {
+            const bool two = t + 32 < cnt;
+            fill_edge_di2<D, INCOMING>(s, X, xv, list[t], base + t, xv, list[two ? t + 32 : t], base + t + 32, two,
+                                       col, cost, tau);
         }
-        base += cnt;
-        cnt = 0;
-        __syncwarp();
-    };
+    } else {
+        for (int t = lane; t < cnt; t += 32) fill_edge<KIND, D, INCOMING>(s, X, xv, list[t], base + t, col, cost, tau, path);
+    }
+}
+
+// One warp gathers row v's columns into its list (kFillList entries in shared
+// memory).  A list that would overflow is evaluated by the warp on the spot;
+// the entries left in it (the return value) start at CSR position *base.
+template <int KIND, int D, bool INCOMING>
+__device__ __forceinline__ int fill_gather(const SpaceArgs& s, const float* __restrict__ X,
+                                           const uint32_t* __restrict__ M, const float* xv, int v, int* base,
+                                           int* __restrict__ list, int* __restrict__ col, float* __restrict__ cost,
+                                           float* __restrict__ tau, float* __restrict__ path) {
+    const int lane = threadIdx.x & 31;
+    const int W = (s.N + 31) / 32;
+    int cnt = 0;
+    // the row's words are loaded four chunks (128 words) at a time, so that one
+    // latency covers rows of up to 4096 nodes
+    uint32_t wb[4];
     for (int c0 = 0; c0 < W; c0 += 32) {
+        const int u = (c0 >> 5) & 3;
+        if (u == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int wk = c0 + 32 * k + lane;
+                wb[k] = wk < W ? M[(size_t)wk * s.pitch + v] : 0u;
+            }
+        }
         const int w = c0 + lane;
-        uint32_t bits = w < W ? M[(size_t)w * s.pitch + v] : 0u;
+        uint32_t bits = u == 0 ? wb[0] : u == 1 ? wb[1] : u == 2 ? wb[2] : wb[3];
         const int n = __popc(bits);
         int incl = n;
 #pragma unroll
@@ -609,16 +649,113 @@ __device__ __forceinline__ void fill_row(const SpaceArgs& s, const float* __rest
             if (lane >= off) incl += y;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);  // at most 1024
-        if (cnt + total > kFillList) flush();
+        if (cnt + total > kFillList) {
+            __syncwarp();
+            fill_list_warp<KIND, D, INCOMING>(s, X, xv, list, cnt, *base, col, cost, tau, path);
+            *base += cnt;
+            cnt = 0;
+            __syncwarp();
+        }
         int pos = cnt + incl - n;
         while (bits) {
             const int b = __ffs(bits) - 1;
             bits &= bits - 1;
-            list[warp][pos++] = 32 * w + b;
+            list[pos++] = 32 * w + b;
         }
         cnt += total;
     }
-    flush();
+    __syncwarp();
+    return cnt;
+}
+
+// One warp: row v, on its own (the batched build: the warps of a block may
+// belong to different queries).
+template <int KIND, int D, bool INCOMING>
+__device__ __forceinline__ void fill_row(const SpaceArgs& s, const float* __restrict__ X,
+                                         const uint32_t* __restrict__ M, const int* __restrict__ row,
+                                         int* __restrict__ col, float* __restrict__ cost, float* __restrict__ tau,
+                                         float* __restrict__ path, int v, int* __restrict__ list) {
+    if (v >= s.N) return;
+    float xv[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) xv[a] = X[(size_t)a * s.pitch + v];
+    int base = row[v];
+    const int cnt = fill_gather<KIND, D, INCOMING>(s, X, M, xv, v, &base, list, col, cost, tau, path);
+    fill_list_warp<KIND, D, INCOMING>(s, X, xv, list, cnt, base, col, cost, tau, path);
+    __syncwarp();
+}
+
+// One block: a group of kFillWarps consecutive rows of one direction.  Each
+// warp gathers its row; then the block's threads share out all the group's
+// listed edges, so that a row with many edges (the double integrator's slow
+// states reach many more nodes than its fast ones) is spread over the block.
+struct FillShared {
+    int list[kFillWarps][kFillList];
+    float xv[kFillWarps][GMT_MAX_DIM];
+    int cnt[kFillWarps], base[kFillWarps];
+    int group;
+};
+
+template <int KIND, int D, bool INCOMING>
+__device__ __forceinline__ void fill_group(const SpaceArgs& s, const float* __restrict__ X, const FillDir& f,
+                                           int v0, FillShared& sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int v = v0 + warp;
+    int cnt = 0;
+    if (v < s.N) {
+        float xv[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) xv[a] = X[(size_t)a * s.pitch + v];
+        int base = f.row[v];
+        cnt = fill_gather<KIND, D, INCOMING>(s, X, f.mask, xv, v, &base, sh.list[warp], f.col, f.cost, f.tau,
+                                             f.path);
+        if (lane == 0) sh.base[warp] = base;
+        if (lane < D) sh.xv[warp][lane] = X[(size_t)lane * s.pitch + v];
+    }
+    if (lane == 0) sh.cnt[warp] = cnt;
+    __syncthreads();
+    // the group's entries in warp order: entry k is list[w][k - pre[w]]
+    int pre[kFillWarps + 1];
+    pre[0] = 0;
+#pragma unroll
+    for (int w = 0; w < kFillWarps; ++w) pre[w + 1] = pre[w] + sh.cnt[w];
+    const int T = pre[kFillWarps];
+    auto locate = [&](int k, int& w, int& t) {  // selects only: pre[] stays in registers
+        int pw = 0;
+        w = 0;
+#pragma unroll
+        for (int u = 1; u < kFillWarps; ++u)
+            if (k >= pre[u]) { w = u; pw = pre[u]; }
+        t = k - pw;
+    };
+    constexpr int kT = kFillWarps * 32;
+    if (KIND == GMT_COST_DI) {
+        for (int k0 = threadIdx.x; k0 < T; k0 += 2 * kT) {
+            const int k1 = k0 + kT;
+            const bool two = k1 < T;
+            int w0, t0, w1, t1;
+            locate(k0, w0, t0);
+            locate(two ? k1 : k0, w1, t1);
+            float xv0[D], xv1[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                xv0[a] = sh.xv[w0][a];
+                xv1[a] = sh.xv[w1][a];
+            }
+            fill_edge_di2<D, INCOMING>(s, X, xv0, sh.list[w0][t0], sh.base[w0] + t0, xv1, sh.list[w1][t1],
+                                       sh.base[w1] + t1, two, f.col, f.cost, f.tau);
+        }
+    } else {
+        for (int k = threadIdx.x; k < T; k += kT) {
+            int w, t;
+            locate(k, w, t);
+            float xv[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a) xv[a] = sh.xv[w][a];
+            fill_edge<KIND, D, INCOMING>(s, X, xv, sh.list[w][t], sh.base[w] + t, f.col, f.cost, f.tau, f.path);
+        }
+    }
+    __syncthreads();  // the lists are refilled by the next group
 }
 
 }  // namespace gmtk

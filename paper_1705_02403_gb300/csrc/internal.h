@@ -98,6 +98,8 @@ cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask,
 cudaError_t launch_transpose(const SpaceArgs& s, const uint32_t* mask, uint32_t* maskT, int* in_count,
                              cudaStream_t st);
 cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st);
+// Both directions' row offsets in one launch (count1 may be NULL: one scan).
+cudaError_t launch_scan2(const int* count0, int* row0, const int* count1, int* row1, int N, cudaStream_t st);
 // One CSR direction for the fill: the bit matrix rows come from (mask for
 // out-rows, its transpose for in-rows), row offsets, and the outputs; tau
 // (double integrator only, may be NULL) receives each edge's arrival time,
@@ -113,7 +115,9 @@ struct FillDir {
     long long cap;  // > 0: the arrays hold `cap` edges; a larger edge count writes nothing
 };
 // Fills the out-CSR, and the in-CSR in the same launch when in.mask != NULL.
-cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, cudaStream_t st);
+// ticket: one device int, zero at launch (the blocks' work counter).
+cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, int* ticket,
+                        cudaStream_t st);
 
 // Cell-list neighbour search (geometric graphs, 2 or 3 dimensions): a uniform
 // grid over the position bounds whose cell side h is at least 1.01 r, so a
