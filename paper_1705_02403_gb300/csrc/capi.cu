@@ -56,6 +56,9 @@ namespace gmtk {
 void record_error(const char* msg) { g_last_error = msg; }
 }  // namespace gmtk
 
+// Device ints at the front of a graph's count block (see gmt_graph::flags).
+constexpr int kFlagInts = 8;
+
 struct gmt_graph {
     int kind = 0, d = 0, dp = 0, N = 0, pitch = 0;
     long long E = 0;
@@ -68,8 +71,10 @@ struct gmt_graph {
     uint8_t* is_goal = nullptr;    size_t cap_is_goal = 0;
     int* out_row = nullptr;        size_t cap_out_row = 0;
     int* in_row_own = nullptr;     size_t cap_in_row_own = 0;
-    int* out_count = nullptr;      size_t cap_out_count = 0;
-    int* in_count = nullptr;       size_t cap_in_count = 0;
+    // one block, zeroed by one memset per build: [flags: kFlagInts][out_count: N][in_count: N]
+    int* counts = nullptr;         size_t cap_counts = 0;
+    int* out_count = nullptr;      // views into `counts`
+    int* in_count = nullptr;
     int* out_col = nullptr;        size_t cap_out_col = 0;
     float* out_cost = nullptr;     size_t cap_out_cost = 0;
     int* in_col_own = nullptr;     size_t cap_in_col_own = 0;
@@ -79,7 +84,8 @@ struct gmt_graph {
     float* in_path = nullptr;      size_t cap_in_path = 0;   // Dubins airplane: [E][4] (t, p, q, word bits)
     uint32_t* mask = nullptr;      size_t cap_mask = 0;
     uint32_t* maskT = nullptr;     size_t cap_maskT = 0;
-    int* flags = nullptr;          size_t cap_flags = 0;   // [sample flags, max row length, row overflow, fill ticket]
+    // [sample flags, max row length, edge count, fill ticket, cell row overflow, -, -, -]
+    int* flags = nullptr;
     // cell-list neighbour build
     int* cell_of = nullptr;        size_t cap_cell_of = 0;
     int* cell_sorted = nullptr;    size_t cap_cell_sorted = 0;
@@ -137,8 +143,8 @@ struct gmt_graph {
     const float* in_cost() const { return directed() ? in_cost_own : out_cost; }
 
     ~gmt_graph() {
-        void* dev[] = {X, is_goal, out_row, in_row_own, out_count, in_count, out_col, out_cost, in_col_own,
-                       in_cost_own, out_tau, in_tau, in_path, mask, maskT, flags, cell_of, cell_sorted, cell_cnt,
+        void* dev[] = {X, is_goal, out_row, in_row_own, counts, out_col, out_cost, in_col_own,
+                       in_cost_own, out_tau, in_tau, in_path, mask, maskT, cell_of, cell_sorted, cell_cnt,
                        cell_start, grid_cnt, grid_start, grid_list, grid_big, halton, ocost, stamp,
                        lists, ctl};
         for (void* p : dev)
@@ -369,15 +375,16 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
     GROW(X, (size_t)g->d * P);
     GROW(is_goal, P);
     GROW(out_row, N + 1);
-    GROW(out_count, N);
-    GROW(flags, 4);
+    GROW(counts, kFlagInts + 2 * N);
+    g->flags = g->counts;
+    g->out_count = g->counts + kFlagInts;
+    g->in_count = g->counts + kFlagInts + N;
     GROW(ocost, N);
     GROW(stamp, N);
     GROW(lists, kPlanListInts * N);
     GROW(ctl, 1);
     if (g->directed()) {
         GROW(in_row_own, N + 1);
-        GROW(in_count, N);
         GROW(maskT, W * P);
     }
     if (!g->h_ctl && (e = cudaMallocHost((void**)&g->h_ctl, sizeof(PlanCtl))) != cudaSuccess)
@@ -387,9 +394,7 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
 
 #define LAUNCH(call, what) if ((e = (call)) != cudaSuccess) return bail(cuda_fail(e, what))
     for (bool& b : g->stage_ran) b = false;
-    LAUNCH(cudaMemsetAsync(g->flags, 0, 4 * sizeof(int), st), "memset");
-    LAUNCH(cudaMemsetAsync(g->out_count, 0, N * sizeof(int), st), "memset");
-    if (g->directed()) LAUNCH(cudaMemsetAsync(g->in_count, 0, N * sizeof(int), st), "memset");
+    LAUNCH(cudaMemsetAsync(g->counts, 0, (kFlagInts + (g->directed() ? 2 * N : N)) * sizeof(int), st), "memset");
     LAUNCH(g->mark(gmt_graph::kSample, 0, st), "event");
     BoxGridArgs grid;
     LAUNCH(build_box_grid(g, ba, &grid, st), "box grid kernels");
@@ -439,12 +444,11 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
     }
     LAUNCH(g->mark(gmt_graph::kScan, 0, st), "event");
     LAUNCH(launch_scan2(g->out_count, g->out_row, g->directed() ? g->in_count : nullptr,
-                        g->directed() ? g->in_row_own : nullptr, g->N, st),
+                        g->directed() ? g->in_row_own : nullptr, g->N, g->flags + 2, st),
            "scan kernel");
     LAUNCH(g->mark(gmt_graph::kScan, 1, st), "event");
-    LAUNCH(cudaMemcpyAsync(g->h_scalars, g->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
-    LAUNCH(cudaMemcpyAsync(g->h_scalars + 2, g->out_row + N, sizeof(int), cudaMemcpyDeviceToHost, st),
-           "edge count readback");
+    // sample flags, longest cell row and edge count in one copy
+    LAUNCH(cudaMemcpyAsync(g->h_scalars, g->flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
     g->pending = false;
     const long long cap_now = edge_capacity(g);
     if (async && !cells && extra_count == 0 && cap_now > 0) {
@@ -513,7 +517,7 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
     LAUNCH(g->mark(gmt_graph::kFill, 0, st), "event");
     if (cells) {
         LAUNCH(launch_cells_rows(sa, g->X, cg, g->cell_of, g->cell_start, g->cell_sorted, true, nullptr, nullptr,
-                                 g->out_row, g->out_col, g->out_cost, g->flags + 2, st),
+                                 g->out_row, g->out_col, g->out_cost, g->flags + 4, st),
                "cell row kernel");
     } else {
         const FillDir out_dir{g->mask, g->out_row, g->out_col, g->out_cost, di ? g->out_tau : nullptr, nullptr, 0};

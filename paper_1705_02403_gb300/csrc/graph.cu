@@ -1,7 +1,8 @@
 // SampleFree and r-disk neighbour graph construction (Section III-B; the
 // precomputation of Section V-A), as CUDA kernels for sm_103a.
 //
-//   sample_kernel     one thread per node: Philox4x32-10 rejection sampling
+//   sample_kernel     four lanes per node: Philox4x32-10 rejection sampling,
+//                     each attempt's box tests shared out over the lanes
 //   halton_kernel     one block: the free Halton points in order
 //   halton_head_kernel + halton_free_kernel  the same split: nodes 0 and 1
 //                     in one block, the free points over many blocks (chunks
@@ -17,7 +18,8 @@
 //                     root procedure, with per-warp compaction between stages
 //   pair_mask_dubins_kernel  the same for the Dubins airplane: distance
 //                     prefilter, then the shortest-word cost from a queue
-//   scan2_kernel      both directions' row offsets (one block each)
+//   scan2_kernel      both directions' row offsets (one block each) and the
+//                     edge count
 //   fill_kernel       persistent blocks, eight rows at a time: each warp
 //                     gathers a row's columns (prefix over its words) into a
 //                     shared-memory list, then the block shares out the eight
@@ -30,7 +32,8 @@
 namespace gmtk {
 
 // ------------------------------------------------------------------ kernels
-constexpr int kSampleThreads = 64;  // small blocks spread the few thousand nodes over more SMs
+constexpr int kSampleThreads = 128;
+constexpr int kSampleGroup = 4;  // lanes per node: the box tests of an attempt are shared out
 
 // Boxes are staged in shared memory when `staged` (2 * count * DP floats): the
 // rejection loop then tests them without a global-memory round trip per box.
@@ -48,7 +51,8 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(SpaceArgs s, Box
         boxes.lo = sbox;
         boxes.hi = sbox + boxes.count * DP;
     }
-    sample_node<D, DP>(s, boxes, grid, X, is_goal, flags, blockIdx.x * blockDim.x + threadIdx.x);
+    sample_node_group<D, DP, kSampleGroup>(s, boxes, grid, X, is_goal, flags,
+                                           (int)((blockIdx.x * blockDim.x + threadIdx.x) / kSampleGroup));
 }
 
 template <int D, int DP>
@@ -189,11 +193,18 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ coun
     scan_rows(count, row, N);
 }
 
-// Block 0 scans the out-row counts, block 1 the in-row counts.
+// Block 0 scans the out-row counts (and stores the edge count at total0 too,
+// next to the build's flags, so that one copy returns both to the host);
+// block 1, if launched, the in-row counts.
 __global__ void __launch_bounds__(1024) scan2_kernel(const int* __restrict__ count0, int* __restrict__ row0,
-                                                     const int* __restrict__ count1, int* __restrict__ row1, int N) {
-    if (blockIdx.x == 0) scan_rows(count0, row0, N);
-    else scan_rows(count1, row1, N);
+                                                     const int* __restrict__ count1, int* __restrict__ row1, int N,
+                                                     int* __restrict__ total0) {
+    if (blockIdx.x == 0) {
+        const int total = scan_rows(count0, row0, N);
+        if (threadIdx.x == 0 && total0) *total0 = total;
+    } else {
+        scan_rows(count1, row1, N);
+    }
 }
 
 // Persistent blocks take groups of kFillWarps rows from a ticket counter
@@ -246,7 +257,8 @@ cudaError_t sample_t(const SpaceArgs& s, BoxArgs b, const BoxGridArgs& grid, voi
     }
     const int staged = b.count > 0 && b.count <= 4096 / DP;
     const size_t smem = staged ? (size_t)2 * b.count * DP * sizeof(float) : 0;
-    sample_kernel<D, DP><<<(s.N + kSampleThreads - 1) / kSampleThreads, kSampleThreads, smem, st>>>(
+    const long long threads = (long long)s.N * kSampleGroup;
+    sample_kernel<D, DP><<<(unsigned)((threads + kSampleThreads - 1) / kSampleThreads), kSampleThreads, smem, st>>>(
         s, b, grid, X, g, f, staged);
     return cudaGetLastError();
 }
@@ -352,9 +364,9 @@ cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan2(const int* count0, int* row0, const int* count1, int* row1, int N, cudaStream_t st) {
-    if (!count1) return launch_scan(count0, row0, N, st);
-    scan2_kernel<<<2, 1024, 0, st>>>(count0, row0, count1, row1, N);
+cudaError_t launch_scan2(const int* count0, int* row0, const int* count1, int* row1, int N, int* total0,
+                         cudaStream_t st) {
+    scan2_kernel<<<count1 ? 2 : 1, 1024, 0, st>>>(count0, row0, count1, row1, N, total0);
     return cudaGetLastError();
 }
 

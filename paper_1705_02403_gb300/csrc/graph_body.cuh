@@ -65,6 +65,81 @@ __device__ __forceinline__ void sample_node(const SpaceArgs& s, const BoxArgs& b
     is_goal[k] = in_goal_ball(x, s.gd, s.gc, s.grho) ? 1 : 0;
 }
 
+// The same sample drawn by a group of G consecutive lanes (G divides 32):
+// every lane of the group computes the same attempt (the same Philox words),
+// and the box tests of an attempt are dealt round-robin over the group's
+// lanes and ORed with shuffles, so an attempt's chain is about nbox / G box
+// tests long instead of nbox.  Lane `sub` = 0 writes the result.  The
+// accepted attempt, and so the sample, is the one sample_node takes.
+template <int D, int DP, int G>
+__device__ __forceinline__ bool point_in_boxes_group(const float* p, const BoxArgs& boxes, const BoxGridArgs& grid,
+                                                     int sub, unsigned gmask) {
+    bool hit = false;
+    if (grid.use) {
+        const int c = box_grid_cell(grid, p[1], 1) * grid.g + box_grid_cell(grid, p[0], 0);
+        const int e = __ldg(&grid.start[c + 1]);
+        for (int t = __ldg(&grid.start[c]) + sub; t < e; t += G) hit |= in_box<DP>(p, boxes.lo, boxes.hi, __ldg(&grid.list[t]));
+        const int nb = __ldg(grid.nbig);
+        for (int t = sub; t < nb; t += G) hit |= in_box<DP>(p, boxes.lo, boxes.hi, __ldg(&grid.big[t]));
+    } else {
+        for (int b = sub; b < boxes.count; b += G) hit |= in_box<DP>(p, boxes.lo, boxes.hi, b);
+    }
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) hit |= __shfl_xor_sync(gmask, hit ? 1 : 0, off) != 0;
+    return hit;
+}
+
+template <int D, int DP, int G>
+__device__ __forceinline__ void sample_node_group(const SpaceArgs& s, const BoxArgs& boxes, const BoxGridArgs& grid,
+                                                  float* __restrict__ X, uint8_t* __restrict__ is_goal,
+                                                  int* __restrict__ flags, int k) {
+    static_assert(32 % G == 0, "a group lies within one warp");
+    if (k >= s.n_sampled) return;  // uniform over the group
+    const int lane = threadIdx.x & 31, sub = lane % G;
+    const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (lane - sub);
+    float x[D];
+    if (k == 0) {
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            x[a] = s.x0[a];
+            ok = ok && s.lo[a] <= x[a] && x[a] <= s.hi[a];
+        }
+        const bool hit = point_in_boxes_group<D, DP, G>(x, boxes, grid, sub, gmask);
+        if (sub == 0 && (!ok || hit)) atomicOr(flags, kSampleBadInit);
+    } else {
+        bool ok = false;
+        for (int t = 0; t < s.max_attempts && !ok; ++t) {
+            uint32_t w[((D + 3) / 4) * 4];
+#pragma unroll
+            for (int blk = 0; blk < (D + 3) / 4; ++blk) {
+                const Ctr4 c = philox4x32_10(Ctr4{(uint32_t)k, (uint32_t)t, s.stream, (uint32_t)blk}, s.key0, s.key1);
+                w[4 * blk + 0] = c.x; w[4 * blk + 1] = c.y; w[4 * blk + 2] = c.z; w[4 * blk + 3] = c.w;
+            }
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float u = unit_float(w[a]);
+                float l = s.lo[a], h = s.hi[a];
+                if (k == 1 && a < s.gd) { l = s.gc[a] - s.grho; h = s.gc[a] + s.grho; }
+                x[a] = l + u * (h - l);
+            }
+            if (k == 1) {
+                bool inb = true;
+#pragma unroll
+                for (int a = 0; a < D; ++a) inb = inb && s.lo[a] <= x[a] && x[a] <= s.hi[a];
+                if (!inb || !in_goal_ball(x, s.gd, s.gc, s.grho)) continue;
+            }
+            if (point_in_boxes_group<D, DP, G>(x, boxes, grid, sub, gmask)) continue;
+            ok = true;
+        }
+        if (!ok && sub == 0) atomicOr(flags, kSampleExhausted);
+    }
+    if (sub != 0) return;
+#pragma unroll
+    for (int a = 0; a < D; ++a) X[(size_t)a * s.pitch + k] = x[a];
+    is_goal[k] = in_goal_ball(x, s.gd, s.gc, s.grho) ? 1 : 0;
+}
+
 // ------------------------------------------------------------ Halton
 // Radical inverse of k in base p, exactly: the digits of k reversed (R) over
 // p^m (m digits), rounded to double and then to float (R, p^m < 2^35).
@@ -498,9 +573,9 @@ __device__ __forceinline__ void transpose_task(int N, int pitch, const uint32_t*
     }
 }
 
-// Exclusive prefix sum: row[v] = sum_{u < v} count[u], row[N] = total.
-// One block of 1024 threads.
-__device__ __forceinline__ void scan_rows(const int* __restrict__ count, int* __restrict__ row, int N) {
+// Exclusive prefix sum: row[v] = sum_{u < v} count[u], row[N] = total (also
+// returned to every thread).  One block of 1024 threads.
+__device__ __forceinline__ int scan_rows(const int* __restrict__ count, int* __restrict__ row, int N) {
     __shared__ int warp_sum[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int carry = 0;
@@ -530,6 +605,7 @@ __device__ __forceinline__ void scan_rows(const int* __restrict__ count, int* __
         __syncthreads();
     }
     if (threadIdx.x == 0) row[N] = carry;
+    return carry;
 }
 
 // Fill: the CSR columns and costs from the bit matrix.  A warp reads a row's

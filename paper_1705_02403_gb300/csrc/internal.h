@@ -98,8 +98,10 @@ cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask,
 cudaError_t launch_transpose(const SpaceArgs& s, const uint32_t* mask, uint32_t* maskT, int* in_count,
                              cudaStream_t st);
 cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st);
-// Both directions' row offsets in one launch (count1 may be NULL: one scan).
-cudaError_t launch_scan2(const int* count0, int* row0, const int* count1, int* row1, int N, cudaStream_t st);
+// Both directions' row offsets in one launch (count1 may be NULL: one scan);
+// total0 (may be NULL) also receives row0[N].
+cudaError_t launch_scan2(const int* count0, int* row0, const int* count1, int* row1, int N, int* total0,
+                         cudaStream_t st);
 // One CSR direction for the fill: the bit matrix rows come from (mask for
 // out-rows, its transpose for in-rows), row offsets, and the outputs; tau
 // (double integrator only, may be NULL) receives each edge's arrival time,
