@@ -622,7 +622,10 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
         if (blocks < 0) blocks = sms;
         if (blocks > maxb) blocks = maxb;
     }
-    GMT_CUDA(cudaMemsetAsync(g->ctl, 0, sizeof(PlanCtl), st), "memset");
+    // a cooperative grid's software barrier counts in the control block, which
+    // must be zero before its launch; cluster and single-CTA launches clear
+    // their result fields themselves
+    if (!(cluster > 1 || blocks == 1)) GMT_CUDA(cudaMemsetAsync(g->ctl, 0, sizeof(PlanCtl), st), "memset");
     g->stage_ran[gmt_graph::kPlan] = false;
     GMT_CUDA(g->mark(gmt_graph::kPlan, 0, st), "event");
     // many boxes: bin them on a grid over the first two position axes

@@ -56,6 +56,18 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
 
     PlanCtl* ctl = A.ctl;
     const int rank = team.rank(), size = team.size();
+    // The result fields and counters start at zero here, so that a launch
+    // whose barrier keeps no state in the control block needs no memset of it
+    // first (the first team barrier, or the early return below, orders these
+    // stores before every other access).
+    if (rank == 0) {
+        ctl->error = 0;
+        ctl->status = 0;
+        ctl->iters = ctl->final_i = ctl->path_len = 0;
+        ctl->goal_node = -1;
+        ctl->push_edges = ctl->pull_edges = ctl->checks = ctl->failed = ctl->tree_size = 0ull;
+        ctl->checks_computed = 0ull;
+    }
     if (A.check_edges) {
         const long long e = max(__ldcg(&A.out_row[A.N]), __ldcg(&A.in_row[A.N]));
         if (e > A.edge_cap) {  // uniform across the team: every thread reads the same counts
