@@ -41,6 +41,24 @@ cudaError_t grow(T** p, size_t* cap, size_t need) {
     return e;
 }
 
+// Pinned host memory mapped into the device address space (the device writes
+// results there directly; the host reads them after synchronising).
+template <class T>
+cudaError_t alloc_mapped(T** host, T** dev, size_t n) {
+    cudaError_t e = cudaHostAlloc((void**)host, n * sizeof(T), cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+        *host = nullptr;
+        return e;
+    }
+    std::memset(*host, 0, n * sizeof(T));
+    e = cudaHostGetDevicePointer((void**)dev, *host, 0);
+    if (e != cudaSuccess) {
+        cudaFreeHost(*host);
+        *host = nullptr;
+    }
+    return e;
+}
+
 // Smallest float t with sqrtf(t) >= r: for s >= 0, sqrtf(s) < r  <=>  s < t,
 // because correctly rounded square root is monotone.
 float euclid_threshold(float r) {
@@ -84,7 +102,7 @@ struct gmt_graph {
     float* in_path = nullptr;      size_t cap_in_path = 0;   // Dubins airplane: [E][4] (t, p, q, word bits)
     uint32_t* mask = nullptr;      size_t cap_mask = 0;
     uint32_t* maskT = nullptr;     size_t cap_maskT = 0;
-    // [sample flags, max row length, edge count, fill ticket, cell row overflow, -, -, -]
+    // [sample flags, max row length, -, fill ticket, cell row overflow, -, -, -]
     int* flags = nullptr;
     // cell-list neighbour build
     int* cell_of = nullptr;        size_t cap_cell_of = 0;
@@ -104,8 +122,10 @@ struct gmt_graph {
     int* lists = nullptr;          size_t cap_lists = 0;
     PlanCtl* ctl = nullptr;        size_t cap_ctl = 0;
     // pinned host mirrors
-    PlanCtl* h_ctl = nullptr;
+    PlanCtl* h_ctl = nullptr;      // mapped into the device: d_ctl, d_scalars
     int* h_scalars = nullptr;
+    PlanCtl* d_ctl = nullptr;
+    int* d_scalars = nullptr;
     // An asynchronous build (gmt_build_graph_async) not yet confirmed: its fill
     // wrote into the edge arrays of earlier builds (`pending_cap` edges); the
     // flags and edge count are read by the next plan or view, which rebuilds
@@ -387,9 +407,9 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
         GROW(in_row_own, N + 1);
         GROW(maskT, W * P);
     }
-    if (!g->h_ctl && (e = cudaMallocHost((void**)&g->h_ctl, sizeof(PlanCtl))) != cudaSuccess)
+    if (!g->h_ctl && (e = alloc_mapped(&g->h_ctl, &g->d_ctl, 1)) != cudaSuccess)
         return bail(cuda_fail(e, "allocating pinned control block"));
-    if (!g->h_scalars && (e = cudaMallocHost((void**)&g->h_scalars, 4 * sizeof(int))) != cudaSuccess)
+    if (!g->h_scalars && (e = alloc_mapped(&g->h_scalars, &g->d_scalars, 4)) != cudaSuccess)
         return bail(cuda_fail(e, "allocating pinned scalars"));
 
 #define LAUNCH(call, what) if ((e = (call)) != cudaSuccess) return bail(cuda_fail(e, what))
@@ -443,12 +463,12 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
         LAUNCH(g->mark(gmt_graph::kTranspose, 1, st), "event");
     }
     LAUNCH(g->mark(gmt_graph::kScan, 0, st), "event");
+    // the scan also stores the sampling flags, the longest cell row and the
+    // edge count in the pinned scalars (no copy)
     LAUNCH(launch_scan2(g->out_count, g->out_row, g->directed() ? g->in_count : nullptr,
-                        g->directed() ? g->in_row_own : nullptr, g->N, g->flags + 2, st),
+                        g->directed() ? g->in_row_own : nullptr, g->N, g->flags, g->d_scalars, st),
            "scan kernel");
     LAUNCH(g->mark(gmt_graph::kScan, 1, st), "event");
-    // sample flags, longest cell row and edge count in one copy
-    LAUNCH(cudaMemcpyAsync(g->h_scalars, g->flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
     g->pending = false;
     const long long cap_now = edge_capacity(g);
     if (async && !cells && extra_count == 0 && cap_now > 0) {
@@ -586,6 +606,7 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
     a.ocost = g->ocost; a.stamp = g->stamp;
     assign_plan_lists(a, g->lists, (size_t)N);
     a.ctl = g->ctl;
+    a.host_ctl = g->d_ctl;  // the kernel leaves its final control block in h_ctl
     for (int k = 0; k < 3; ++k) { a.pos_lo[k] = g->pos_lo[k]; a.pos_hi[k] = g->pos_hi[k]; }
     if (g->pending) {  // an asynchronous build: the kernel reads the CSR only if its edges fit
         a.check_edges = 1;
@@ -634,7 +655,6 @@ gmt_status gmt_plan(gmt_graph* g, const gmt_boxes* boxes, const gmt_params* para
     GMT_CUDA(g->mark(gmt_graph::kPlan, 1, st), "event");
     g->last_blocks = cluster > 1 ? -cluster : blocks;
     g->last_threads = threads;
-    GMT_CUDA(cudaMemcpyAsync(g->h_ctl, g->ctl, sizeof(PlanCtl), cudaMemcpyDeviceToHost, st), "control readback");
     GMT_CUDA(cudaStreamSynchronize(st), "plan kernel");
     if (g->pending) {
         bool rebuilt = false;

@@ -18,8 +18,8 @@
 //                     root procedure, with per-warp compaction between stages
 //   pair_mask_dubins_kernel  the same for the Dubins airplane: distance
 //                     prefilter, then the shortest-word cost from a queue
-//   scan2_kernel      both directions' row offsets (one block each) and the
-//                     edge count
+//   scan2_kernel      both directions' row offsets (one block each); the
+//                     edge count and sampling flags straight to host memory
 //   fill_kernel       persistent blocks, eight rows at a time: each warp
 //                     gathers a row's columns (prefix over its words) into a
 //                     shared-memory list, then the block shares out the eight
@@ -193,15 +193,20 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ coun
     scan_rows(count, row, N);
 }
 
-// Block 0 scans the out-row counts (and stores the edge count at total0 too,
-// next to the build's flags, so that one copy returns both to the host);
-// block 1, if launched, the in-row counts.
+// Block 0 scans the out-row counts and, when host_out is given (host memory
+// mapped into the device), stores there the build's first two flags (written
+// by the kernels before this one) and the edge count, so that the host needs
+// no copy; block 1, if launched, scans the in-row counts.
 __global__ void __launch_bounds__(1024) scan2_kernel(const int* __restrict__ count0, int* __restrict__ row0,
                                                      const int* __restrict__ count1, int* __restrict__ row1, int N,
-                                                     int* __restrict__ total0) {
+                                                     const int* __restrict__ flags, int* __restrict__ host_out) {
     if (blockIdx.x == 0) {
         const int total = scan_rows(count0, row0, N);
-        if (threadIdx.x == 0 && total0) *total0 = total;
+        if (threadIdx.x == 0 && host_out) {
+            host_out[0] = __ldcg(&flags[0]);
+            host_out[1] = __ldcg(&flags[1]);
+            host_out[2] = total;
+        }
     } else {
         scan_rows(count1, row1, N);
     }
@@ -364,9 +369,9 @@ cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan2(const int* count0, int* row0, const int* count1, int* row1, int N, int* total0,
-                         cudaStream_t st) {
-    scan2_kernel<<<count1 ? 2 : 1, 1024, 0, st>>>(count0, row0, count1, row1, N, total0);
+cudaError_t launch_scan2(const int* count0, int* row0, const int* count1, int* row1, int N, const int* flags,
+                         int* host_out, cudaStream_t st) {
+    scan2_kernel<<<count1 ? 2 : 1, 1024, 0, st>>>(count0, row0, count1, row1, N, flags, host_out);
     return cudaGetLastError();
 }
 

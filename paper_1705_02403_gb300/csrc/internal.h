@@ -98,10 +98,11 @@ cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask,
 cudaError_t launch_transpose(const SpaceArgs& s, const uint32_t* mask, uint32_t* maskT, int* in_count,
                              cudaStream_t st);
 cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st);
-// Both directions' row offsets in one launch (count1 may be NULL: one scan);
-// total0 (may be NULL) also receives row0[N].
-cudaError_t launch_scan2(const int* count0, int* row0, const int* count1, int* row1, int N, int* total0,
-                         cudaStream_t st);
+// Both directions' row offsets in one launch (count1 may be NULL: one scan).
+// host_out (may be NULL; device-mapped host memory) receives flags[0],
+// flags[1] and row0[N].
+cudaError_t launch_scan2(const int* count0, int* row0, const int* count1, int* row1, int N, const int* flags,
+                         int* host_out, cudaStream_t st);
 // One CSR direction for the fill: the bit matrix rows come from (mask for
 // out-rows, its transpose for in-rows), row offsets, and the outputs; tau
 // (double integrator only, may be NULL) receives each edge's arrival time,
@@ -213,6 +214,10 @@ struct PlanArgs {
     int2* list_open[2];   // (node, cost bits) of each open node; N entries each
     int* list_cand;
     PlanCtl* ctl;
+    // Optional device-mapped host copy of the control block: the plan kernel
+    // writes the final control block there once the plan is over, so the
+    // caller needs no device-to-host copy (NULL: not written).
+    PlanCtl* host_ctl;
     // Optional per-edge verdict cache (in-CSR order): 0 unknown, 1 free,
     // 2 collides.  A known verdict answers the check; an unknown one is
     // computed and stored.  Valid only while the obstacles that could change

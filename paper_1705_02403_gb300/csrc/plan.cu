@@ -380,12 +380,24 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
     }
 }
 
+// The first warp copies the final control block to the caller's mapped host
+// copy (src: a block whose writers have all passed a barrier since).
+__device__ __forceinline__ void publish_ctl(PlanCtl* dst, const PlanCtl* src, int rank) {
+    constexpr int n = (int)(sizeof(PlanCtl) / sizeof(int));
+    for (int t = rank; t < n; t += 32)
+        reinterpret_cast<int*>(dst)[t] = __ldcg(reinterpret_cast<const int*>(src) + t);
+}
+
 template <class Team, int KIND, int DP>
 __global__ void __launch_bounds__(1024, 1) plan_kernel(PlanArgs A, Team team) {
     extern __shared__ float sbox[];
     unsigned dyn_smem;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
     plan_body<Team, KIND, DP>(A, team, sbox, dyn_smem);
+    if (A.host_ctl) {
+        team.sync(A.ctl);  // every warp's counters and rank 0's result are in
+        if (team.rank() < 32) publish_ctl(A.host_ctl, A.ctl, team.rank());
+    }
 }
 
 // One CTA whose wavefront state lives in its shared memory: after the region
@@ -412,8 +424,11 @@ __global__ void __launch_bounds__(1024, 1) plan_kernel_smem(PlanArgs A, unsigned
     assign_plan_lists(A, slists, N);
     plan_body<BlockTeam, KIND, DP, true>(A, BlockTeam{}, smem, region0);
     __syncthreads();
-    for (int t = threadIdx.x; t < (int)(sizeof(PlanCtl) / sizeof(int)); t += blockDim.x)
-        reinterpret_cast<int*>(gctl)[t] = reinterpret_cast<const int*>(sctl)[t];
+    for (int t = threadIdx.x; t < (int)(sizeof(PlanCtl) / sizeof(int)); t += blockDim.x) {
+        const int v = reinterpret_cast<const int*>(sctl)[t];
+        reinterpret_cast<int*>(gctl)[t] = v;
+        if (A.host_ctl) reinterpret_cast<int*>(A.host_ctl)[t] = v;
+    }
 }
 
 // Persistent batched wavefront: every team (a CTA, or a cluster) takes the next
