@@ -304,11 +304,68 @@ __device__ __forceinline__ float edge_cost(const SpaceArgs& s, const float* from
     return di_cost(from, to, s.r);
 }
 
+// Euclidean graphs of at most 4 dimensions: the staged columns are float4s
+// (one shared-memory load per pair) and columns past the last node hold +inf
+// (an infinite distance: no edge), so the inner loop tests no bounds; the
+// diagonal pair i = j is cleared once per word.  The squared distance is the
+// same expression as sq_dist (axes in order), so the bits are the same.
+template <int D>
+__device__ __forceinline__ void mask_tile_euclid4(const SpaceArgs& s, const float* __restrict__ X,
+                                                  uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
+                                                  int by) {
+    static_assert(D <= 4, "float4 columns");
+    __shared__ float4 tile[kMaskWords * 32];
+    const int i = bx * kMaskRows + threadIdx.x;
+    const int w0 = by * kMaskWords;
+    const int j0 = w0 * 32;
+    const float INF = f_inf();
+    for (int idx = threadIdx.x; idx < kMaskWords * 32; idx += kMaskRows) {
+        const int j = j0 + idx;
+        float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int a = 0; a < D; ++a) c[a] = j < s.N ? X[(size_t)a * s.pitch + j] : INF;
+        tile[idx] = make_float4(c[0], c[1], c[2], c[3]);
+    }
+    __syncthreads();
+    if (i >= s.N) return;
+    float xi[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int a = 0; a < D; ++a) xi[a] = X[(size_t)a * s.pitch + i];
+    const int W = (s.N + 31) / 32;
+    const float thr = s.r2_threshold;
+    int cnt = 0;
+    for (int ww = 0; ww < kMaskWords; ++ww) {
+        const int w = w0 + ww;
+        if (w >= W) break;
+        uint32_t bits = 0;
+#pragma unroll
+        for (int b = 0; b < 32; ++b) {
+            const float4 q = tile[ww * 32 + b];
+            const float xj[4] = {q.x, q.y, q.z, q.w};
+            float d2 = 0.0f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float t = xj[a] - xi[a];
+                d2 = d2 + t * t;
+            }
+            bits |= (d2 < thr ? 1u : 0u) << b;
+        }
+        if ((i >> 5) == w) bits &= ~(1u << (i & 31));  // no self-loop
+        mask[(size_t)w * s.pitch + i] = bits;
+        cnt += __popc(bits);
+    }
+    if (cnt) atomicAdd(&out_count[i], cnt);
+}
+
 // One block of kMaskRows threads: rows bx*kMaskRows.., words by*kMaskWords..
 template <int KIND, int D>
 __device__ __forceinline__ void mask_tile(const SpaceArgs& s, const float* __restrict__ X,
                                           uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
                                           int by) {
+    if constexpr (KIND == GMT_COST_EUCLID && D <= 4) {
+        mask_tile_euclid4<D>(s, X, mask, out_count, bx, by);
+        return;
+    }
     __shared__ float tile[D][kMaskWords * 32];
     const int i = bx * kMaskRows + threadIdx.x;
     const int w0 = by * kMaskWords;
