@@ -421,8 +421,10 @@ constexpr int kDIWords = GMT_DI_WORDS;  // 32-column words per block (staged col
 __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __restrict__ X,
                                              uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
                                              int by) {
+    static_assert(kDIWords == 1, "the first stage keeps a lane's columns in one 32-bit word");
     __shared__ float tile[6][kDIWords * 32];
     __shared__ uint32_t words[kDIRows / 32][kDIWords][32];
+    __shared__ uint16_t queue0[kDIRows / 32][32 * 32];  // every pair of the warp's tile may pass the first test
     __shared__ uint16_t queue[kDIRows / 32][3][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = bx * kDIRows + threadIdx.x;
@@ -487,8 +489,8 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
             qn2 = shift(2, qn2);
         }
     };
-    auto drain0 = [&](int count) {  // first bound
-        const int e = lane < count ? queue[warp][0][lane] : 0;
+    auto drain0 = [&](int from, int count) {  // first bound, on queue0[from, from + count)
+        const int e = lane < count ? queue0[warp][from + lane] : 0;
         float a_[6], b_[6];
         state(e, a_, b_);
         qn1 = enqueue(1, lane < count && di_may_connect(a_, b_, s.r), e, qn1);
@@ -499,22 +501,39 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
     };
 
     const int jend = min(kDIWords * 32, s.N - j0);
-    for (int jt = 0; jt < jend; ++jt) {
-        const int j = j0 + jt;
-        // velocity test: J >= tau + |v1 - v0|^2 / tau >= 2 |v1 - v0|
-        float A = 0.0f;
+    // velocity test for the lane's row against every staged column, one bit
+    // per column (J >= tau + |v1 - v0|^2 / tau >= 2 |v1 - v0|); the passing
+    // pairs are then queued all at once, so the per-pair cost of the test is
+    // its arithmetic and one bit, with no warp vote per column
+    uint32_t pm = 0;
+    if (row_ok) {
+        const float rr2 = rr * rr;
+#pragma unroll 8
+        for (int jt = 0; jt < jend; ++jt) {
+            float A = 0.0f;
 #pragma unroll
-        for (int a = 3; a < 6; ++a) {
-            const float dv = tile[a][jt] - xi[a];
-            A = A + dv * dv;
+            for (int a = 3; a < 6; ++a) {
+                const float dv = tile[a][jt] - xi[a];
+                A = A + dv * dv;
+            }
+            pm |= (4.0f * A < rr2 ? 1u : 0u) << jt;
         }
-        qn0 = enqueue(0, row_ok && j != i && 4.0f * A < rr * rr, (lane << 8) | jt, qn0);
-        if (qn0 >= 32) {
-            drain0(32);
-            qn0 = shift(0, qn0);
-        }
+        if (i >= j0 && i < j0 + jend) pm &= ~(1u << (i - j0));  // no self pair
     }
-    if (qn0 > 0) drain0(qn0);
+    {
+        const int np = __popc(pm);
+        int incl = np;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        qn0 = __shfl_sync(0xffffffffu, incl, 31);
+        int pos = incl - np;
+        for (uint32_t m = pm; m; m &= m - 1) queue0[warp][pos++] = (uint16_t)((lane << 8) | (__ffs(m) - 1));
+        __syncwarp();
+    }
+    for (int from = 0; from < qn0; from += 32) drain0(from, min(32, qn0 - from));
     if (qn1 > 0) drain1(qn1);
     if (qn2 > 0) drain2(qn2);
     __syncwarp();
