@@ -229,9 +229,9 @@ def run_gpu(args, rank, world, local_rank):
     path = torch.empty(Nn, dtype=torch.int32, device=dev)
     graph = N.Graph()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    # sample, pair filter, (transpose,) row scans (both directions in one
-    # launch), fill, plan
-    launches_per_step = 6 if pb0.kind == N.GMT_COST_DI else 5
+    # sample, pair filter (the double integrator's also writes the transposed
+    # matrix), row scans (both directions in one launch), fill, plan
+    launches_per_step = 5
 
     def step(k, level):
         # the build is queued without a host wait (gmt_plan confirms it; the

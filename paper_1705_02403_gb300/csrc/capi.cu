@@ -454,10 +454,14 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
                "cell row kernel");
     } else {
         GROW(mask, W * P);
-        LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, st), "pair filter kernel");
+        // the double integrator's pair filter also writes the transposed matrix
+        const bool di_t = g->kind == GMT_COST_DI;
+        LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, di_t ? g->maskT : nullptr,
+                                di_t ? g->in_count : nullptr, st),
+               "pair filter kernel");
     }
     LAUNCH(g->mark(gmt_graph::kPair, 1, st), "event");
-    if (g->directed()) {
+    if (g->directed() && g->kind != GMT_COST_DI) {
         LAUNCH(g->mark(gmt_graph::kTranspose, 0, st), "event");
         LAUNCH(launch_transpose(sa, g->mask, g->maskT, g->in_count, st), "transpose kernel");
         LAUNCH(g->mark(gmt_graph::kTranspose, 1, st), "event");
@@ -503,7 +507,7 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
         cells = false;
         GROW(mask, W * P);
         LAUNCH(cudaMemsetAsync(g->out_count, 0, N * sizeof(int), st), "memset");
-        LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, st), "pair filter kernel");
+        LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, nullptr, nullptr, st), "pair filter kernel");
         LAUNCH(launch_scan(g->out_count, g->out_row, g->N, st), "scan kernel");
         LAUNCH(cudaMemcpyAsync(g->h_scalars + 2, g->out_row + N, sizeof(int), cudaMemcpyDeviceToHost, st),
                "edge count readback");

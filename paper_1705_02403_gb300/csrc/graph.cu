@@ -15,7 +15,8 @@
 //   scan_kernel       exclusive prefix sum of the per-row counts -> row_ptr
 //   pair_mask_di_kernel  the same for the double integrator: three
 //                     conservative tests of increasing cost, then the exact
-//                     root procedure, with per-warp compaction between stages
+//                     root procedure, with per-warp compaction between stages;
+//                     it also writes the transposed words and in-row counts
 //   pair_mask_dubins_kernel  the same for the Dubins airplane: distance
 //                     prefilter, then the shortest-word cost from a queue
 //   scan2_kernel      both directions' row offsets (one block each); the
@@ -174,8 +175,10 @@ __global__ void __launch_bounds__(kMaskRows) pair_mask_kernel(SpaceArgs s, const
 
 __global__ void __launch_bounds__(kDIRows, 8) pair_mask_di_kernel(SpaceArgs s, const float* __restrict__ X,
                                                               uint32_t* __restrict__ mask,
-                                                              int* __restrict__ out_count) {
-    mask_di_tile(s, X, mask, out_count, blockIdx.x, blockIdx.y);
+                                                              int* __restrict__ out_count,
+                                                              uint32_t* __restrict__ maskT,
+                                                              int* __restrict__ in_count) {
+    mask_di_tile(s, X, mask, out_count, blockIdx.x, blockIdx.y, maskT, in_count);
 }
 
 __global__ void __launch_bounds__(kDubRows) pair_mask_dubins_kernel(SpaceArgs s, const float* __restrict__ X,
@@ -340,11 +343,12 @@ cudaError_t launch_append(const SpaceArgs& s, BoxArgs b, const float* src, int s
     return cudaGetLastError();
 }
 
-cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* cnt, cudaStream_t st) {
+cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* cnt, uint32_t* maskT,
+                             int* in_count, cudaStream_t st) {
     if (s.kind == GMT_COST_DI) {
         const int W = (s.N + 31) / 32;
         dim3 grid((s.N + kDIRows - 1) / kDIRows, (W + kDIWords - 1) / kDIWords);
-        pair_mask_di_kernel<<<grid, kDIRows, 0, st>>>(s, X, mask, cnt);
+        pair_mask_di_kernel<<<grid, kDIRows, 0, st>>>(s, X, mask, cnt, maskT, in_count);
         return cudaGetLastError();
     }
     if (s.kind == GMT_COST_DUBINS) {

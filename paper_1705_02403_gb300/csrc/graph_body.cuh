@@ -418,9 +418,12 @@ constexpr int kDIRows = GMT_DI_ROWS;    // rows (threads) per block
 constexpr int kDIWords = GMT_DI_WORDS;  // 32-column words per block (staged columns); 1 measured fastest
 
 // One block of kDIRows threads: rows bx*kDIRows.., words by*kDIWords..
+// maskT, in_count (may be NULL): also write the tile's words of the transposed
+// (in-neighbour) matrix and count the in-edges, as transpose_task would.
 __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __restrict__ X,
                                              uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
-                                             int by) {
+                                             int by, uint32_t* __restrict__ maskT = nullptr,
+                                             int* __restrict__ in_count = nullptr) {
     static_assert(kDIWords == 1, "the first stage keeps a lane's columns in one 32-bit word");
     __shared__ float tile[6][kDIWords * 32];
     __shared__ uint32_t words[kDIRows / 32][kDIWords][32];
@@ -537,8 +540,26 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
     if (qn1 > 0) drain1(qn1);
     if (qn2 > 0) drain2(qn2);
     __syncwarp();
-    if (!row_ok) return;
     const int W = (s.N + 31) / 32;
+    if (maskT) {
+        // transposed: for column j0 + jt, the bits of the warp's 32 rows form
+        // word (row chunk, j0 + jt) of the in-neighbour matrix
+        const int chunk = (bx * kDIRows) / 32 + warp;
+        const uint32_t mine = row_ok ? words[warp][0][lane] : 0u;
+        if (chunk < W) {  // uniform over the warp
+            uint32_t tw = 0;  // lane jt keeps column j0 + jt's word
+#pragma unroll
+            for (int jt = 0; jt < 32; ++jt) {
+                const uint32_t t = __ballot_sync(0xffffffffu, (mine >> jt) & 1u);
+                if (lane == jt) tw = t;
+            }
+            if (j0 + lane < s.N) {  // one coalesced store and one atomic per lane
+                maskT[(size_t)chunk * s.pitch + j0 + lane] = tw;
+                if (tw) atomicAdd(&in_count[j0 + lane], __popc(tw));
+            }
+        }
+    }
+    if (!row_ok) return;
     int cnt = 0;
 #pragma unroll
     for (int ww = 0; ww < kDIWords; ++ww) {
