@@ -367,7 +367,7 @@ def run_gpu(args, rank, world, local_rank):
         line["serving"] = bench_serving(local_rank)
         line["dubins"] = bench_dubins(dev, flush)
         line["gpu_launches_extras"] = ("batched: 7 launches per group per batch (replayed CUDA graph); serving: 3 per "
-                                       "request; dubins: 8-9 per build, 1 per plan")
+                                       "request; dubins: 7-8 per build, 1 per plan")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         seeds_cpu = [seeds[args.warmup + j] for j in range(3)]
         rows = 256 if args.workload == "di6" else 1025

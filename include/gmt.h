@@ -523,9 +523,10 @@ gmt_status gmt_plan_static(const gmt_space* space, const gmt_graph_view* graph, 
  * for the recorded events. */
 typedef struct {
     float sample_ms;     /* SampleFree */
-    float pair_ms;       /* all-pairs cost filter (neighbour bit matrix; for the double
-                          * integrator also its transpose, the in-edge bit matrix) */
-    float transpose_ms;  /* in-edge bit matrix (Dubins airplane only) */
+    float pair_ms;       /* all-pairs cost filter (neighbour bit matrix; for directed
+                          * costs also its transpose, the in-edge bit matrix) */
+    float transpose_ms;  /* 0: the pair filter writes the in-edge bit matrix (the field
+                          * keeps the layout of earlier versions) */
     float scan_ms;       /* row offsets */
     float fill_ms;       /* CSR columns and costs */
     float plan_ms;       /* wavefront kernel */

@@ -454,18 +454,13 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
                "cell row kernel");
     } else {
         GROW(mask, W * P);
-        // the double integrator's pair filter also writes the transposed matrix
-        const bool di_t = g->kind == GMT_COST_DI;
-        LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, di_t ? g->maskT : nullptr,
-                                di_t ? g->in_count : nullptr, st),
+        // directed costs: the pair filter also writes the transposed matrix
+        const bool dir = g->directed();
+        LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, dir ? g->maskT : nullptr,
+                                dir ? g->in_count : nullptr, st),
                "pair filter kernel");
     }
     LAUNCH(g->mark(gmt_graph::kPair, 1, st), "event");
-    if (g->directed() && g->kind != GMT_COST_DI) {
-        LAUNCH(g->mark(gmt_graph::kTranspose, 0, st), "event");
-        LAUNCH(launch_transpose(sa, g->mask, g->maskT, g->in_count, st), "transpose kernel");
-        LAUNCH(g->mark(gmt_graph::kTranspose, 1, st), "event");
-    }
     LAUNCH(g->mark(gmt_graph::kScan, 0, st), "event");
     // the scan also stores the sampling flags, the longest cell row and the
     // edge count in the pinned scalars (no copy)

@@ -11,14 +11,14 @@
 //                     c(i, j) < r; rows staged through shared memory; the bit
 //                     matrix is word-major (word w of every row contiguous) so
 //                     that each warp writes 32 consecutive rows' words
-//   transpose_kernel  32x32 bit-block transpose with warp ballots (in-edges)
 //   scan_kernel       exclusive prefix sum of the per-row counts -> row_ptr
 //   pair_mask_di_kernel  the same for the double integrator: three
 //                     conservative tests of increasing cost, then the exact
 //                     root procedure, with per-warp compaction between stages;
 //                     it also writes the transposed words and in-row counts
 //   pair_mask_dubins_kernel  the same for the Dubins airplane: distance
-//                     prefilter, then the shortest-word cost from a queue
+//                     prefilter, then the shortest-word cost from a queue;
+//                     it also writes the transposed words and in-row counts
 //   scan2_kernel      both directions' row offsets (one block each); the
 //                     edge count and sampling flags straight to host memory
 //   fill_kernel       persistent blocks, eight rows at a time: each warp
@@ -183,13 +183,10 @@ __global__ void __launch_bounds__(kDIRows, 8) pair_mask_di_kernel(SpaceArgs s, c
 
 __global__ void __launch_bounds__(kDubRows) pair_mask_dubins_kernel(SpaceArgs s, const float* __restrict__ X,
                                                                   uint32_t* __restrict__ mask,
-                                                                  int* __restrict__ out_count) {
-    mask_dubins_tile(s, X, mask, out_count, blockIdx.x, blockIdx.y);
-}
-
-__global__ void __launch_bounds__(256) transpose_kernel(int N, int pitch, const uint32_t* __restrict__ mask,
-                                                        uint32_t* __restrict__ maskT, int* __restrict__ in_count) {
-    transpose_task(N, pitch, mask, maskT, in_count, ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32);
+                                                                  int* __restrict__ out_count,
+                                                                  uint32_t* __restrict__ maskT,
+                                                                  int* __restrict__ in_count) {
+    mask_dubins_tile(s, X, mask, out_count, blockIdx.x, blockIdx.y, maskT, in_count);
 }
 
 __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ count, int* __restrict__ row, int N) {
@@ -354,18 +351,10 @@ cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask,
     if (s.kind == GMT_COST_DUBINS) {
         const int W = (s.N + 31) / 32;
         dim3 grid((s.N + kDubRows - 1) / kDubRows, (W + kDubWords - 1) / kDubWords);
-        pair_mask_dubins_kernel<<<grid, kDubRows, 0, st>>>(s, X, mask, cnt);
+        pair_mask_dubins_kernel<<<grid, kDubRows, 0, st>>>(s, X, mask, cnt, maskT, in_count);
         return cudaGetLastError();
     }
     GMT_EUCLID_DIMS(mask_t, s, X, mask, cnt, st)
-}
-
-cudaError_t launch_transpose(const SpaceArgs& s, const uint32_t* mask, uint32_t* maskT, int* in_count,
-                             cudaStream_t st) {
-    const long long W = (s.N + 31) / 32;
-    const long long threads = W * W * 32;
-    transpose_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(s.N, s.pitch, mask, maskT, in_count);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st) {

@@ -578,12 +578,16 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
 constexpr int kDubRows = 128;  // rows (threads) per block
 constexpr int kDubWords = 1;   // 32-column words per block
 
+// maskT, in_count (may be NULL): also write the tile's words of the transposed
+// (in-neighbour) matrix and count the in-edges, as transpose_task would.
 __device__ __forceinline__ void mask_dubins_tile(const SpaceArgs& s, const float* __restrict__ X,
                                                  uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
-                                                 int by) {
+                                                 int by, uint32_t* __restrict__ maskT = nullptr,
+                                                 int* __restrict__ in_count = nullptr) {
+    static_assert(kDubWords == 1, "the prefilter keeps a lane's columns in one 32-bit word");
     __shared__ float tile[4][kDubWords * 32];
     __shared__ uint32_t words[kDubRows / 32][kDubWords][32];
-    __shared__ uint16_t queue[kDubRows / 32][64];
+    __shared__ uint16_t queue[kDubRows / 32][32 * 32];  // every pair of the warp's tile may pass the prefilter
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = bx * kDubRows + threadIdx.x;
     const int j0 = by * kDubWords * 32;
@@ -599,9 +603,37 @@ __device__ __forceinline__ void mask_dubins_tile(const SpaceArgs& s, const float
     float xi[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) xi[a] = row_ok ? X[(size_t)a * s.pitch + i] : 0.0f;
-    int qn = 0;
-    auto drain = [&](int count) {
-        const int e = lane < count ? queue[warp][lane] : 0;
+    // prefilter of the lane's row against every staged column, one bit per
+    // column; the passing pairs are then queued all at once and their costs
+    // computed 32 at a time (one per lane)
+    const int jend = min(kDubWords * 32, s.N - j0);
+    uint32_t pm = 0;
+    if (row_ok) {
+        for (int jt = 0; jt < jend; ++jt) {
+            float b_[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) b_[a] = tile[a][jt];
+            pm |= (dubins_near(xi, b_, s.r) ? 1u : 0u) << jt;
+        }
+        if (i >= j0 && i < j0 + jend) pm &= ~(1u << (i - j0));  // no self pair
+    }
+    int qn;
+    {
+        const int np = __popc(pm);
+        int incl = np;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        qn = __shfl_sync(0xffffffffu, incl, 31);
+        int pos = incl - np;
+        for (uint32_t m = pm; m; m &= m - 1) queue[warp][pos++] = (uint16_t)((lane << 8) | (__ffs(m) - 1));
+        __syncwarp();
+    }
+    for (int from = 0; from < qn; from += 32) {
+        const int count = min(32, qn - from);
+        const int e = lane < count ? queue[warp][from + lane] : 0;
         const int src = e >> 8, jt = e & 255;
         float a_[4], b_[4];
 #pragma unroll
@@ -610,30 +642,28 @@ __device__ __forceinline__ void mask_dubins_tile(const SpaceArgs& s, const float
             b_[a] = tile[a][jt];
         }
         if (lane < count && dubins_cost(a_, b_, s.rho) < s.r) atomicOr(&words[warp][jt >> 5][src], 1u << (jt & 31));
-    };
-    const int jend = min(kDubWords * 32, s.N - j0);
-    for (int jt = 0; jt < jend; ++jt) {
-        const int j = j0 + jt;
-        float b_[4];
+    }
+    __syncwarp();
+    const int W = (s.N + 31) / 32;
+    if (maskT) {
+        // transposed: for column j0 + jt, the bits of the warp's 32 rows form
+        // word (row chunk, j0 + jt) of the in-neighbour matrix
+        const int chunk = (bx * kDubRows) / 32 + warp;
+        const uint32_t mine = row_ok ? words[warp][0][lane] : 0u;
+        if (chunk < W) {  // uniform over the warp
+            uint32_t tw = 0;  // lane jt keeps column j0 + jt's word
 #pragma unroll
-        for (int a = 0; a < 4; ++a) b_[a] = tile[a][jt];
-        const bool pass = row_ok && j != i && dubins_near(xi, b_, s.r);
-        const unsigned m = __ballot_sync(0xffffffffu, pass);
-        if (pass) queue[warp][qn + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((lane << 8) | jt);
-        __syncwarp();
-        qn += __popc(m);
-        if (qn >= 32) {
-            drain(32);
-            __syncwarp();
-            if (lane < qn - 32) queue[warp][lane] = queue[warp][32 + lane];
-            __syncwarp();
-            qn -= 32;
+            for (int jt = 0; jt < 32; ++jt) {
+                const uint32_t t = __ballot_sync(0xffffffffu, (mine >> jt) & 1u);
+                if (lane == jt) tw = t;
+            }
+            if (j0 + lane < s.N) {  // one coalesced store and one atomic per lane
+                maskT[(size_t)chunk * s.pitch + j0 + lane] = tw;
+                if (tw) atomicAdd(&in_count[j0 + lane], __popc(tw));
+            }
         }
     }
-    if (qn > 0) drain(qn);
-    __syncwarp();
     if (!row_ok) return;
-    const int W = (s.N + 31) / 32;
     int cnt = 0;
 #pragma unroll
     for (int ww = 0; ww < kDubWords; ++ww) {

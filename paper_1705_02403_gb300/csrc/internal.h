@@ -93,12 +93,11 @@ inline size_t halton_scratch_bytes(long long cap) {
 cudaError_t launch_sample(const SpaceArgs& s, BoxArgs boxes, const BoxGridArgs& grid, void* scratch, float* X,
                           uint8_t* is_goal,
                           int* flags, cudaStream_t st);
-// maskT, in_count (double integrator only; may be NULL): the same launch also
-// writes the transposed bit matrix and the in-row counts (no transpose launch).
+// maskT, in_count (double integrator and Dubins airplane; may be NULL): the
+// same launch also writes the transposed bit matrix and the in-row counts (no
+// transpose launch).
 cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* out_count,
                              uint32_t* maskT, int* in_count, cudaStream_t st);
-cudaError_t launch_transpose(const SpaceArgs& s, const uint32_t* mask, uint32_t* maskT, int* in_count,
-                             cudaStream_t st);
 cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st);
 // Both directions' row offsets in one launch (count1 may be NULL: one scan).
 // host_out (may be NULL; device-mapped host memory) receives flags[0],
