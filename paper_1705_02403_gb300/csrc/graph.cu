@@ -26,6 +26,7 @@
 //                     shared-memory list, then the block shares out the eight
 //                     rows' edges (two per thread for the double integrator);
 //                     out- and in-rows in one launch
+#include <atomic>
 #include <cstdio>
 
 #include "graph_body.cuh"
@@ -277,8 +278,10 @@ cudaError_t mask_t(const SpaceArgs& s, const float* X, uint32_t* mask, int* cnt,
 template <int KIND, int D>
 cudaError_t fill_t(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, int* ticket,
                    cudaStream_t st) {
-    // as many blocks as fit on the GPU at once (queried once per instantiation)
-    static int resident = 0;
+    // as many blocks as fit on the GPU at once (queried once per instantiation;
+    // any count is correct, the blocks take groups until none is left)
+    static std::atomic<int> resident_cache{0};
+    int resident = resident_cache.load(std::memory_order_relaxed);
     if (resident == 0) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaError_t e = cudaGetDevice(&dev);
@@ -287,6 +290,7 @@ cudaError_t fill_t(const SpaceArgs& s, const float* X, const FillDir& out, const
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_kernel<KIND, D>, kFillWarps * 32, 0);
         if (e != cudaSuccess) return e;
         resident = sms * (per_sm > 0 ? per_sm : 1);
+        resident_cache.store(resident, std::memory_order_relaxed);
     }
     const long long groups = (long long)((s.N + kFillWarps - 1) / kFillWarps) * (in.mask ? 2 : 1);
     const int blocks = (int)(groups < resident ? groups : resident);
