@@ -1,6 +1,7 @@
 // Learned sampling proposal: the BF16 tensor-core GEMM launcher and the C ABI
 // entry point that exposes it (gmt_gemm_bf16).  The network, its training and
 // the proposal sampler build on these (proposal.cu).
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -72,12 +73,12 @@ cudaError_t gemm_bf16_tn(int M, int N, int K, const __nv_bfloat16* A, const __nv
                          const float* bias, float* C, __nv_bfloat16* Cb, int ldc, int splits, float* partial,
                          int* error, cudaStream_t st) {
     if (M <= 0 || N <= 0 || K <= 0 || K % 8 != 0) return cudaErrorInvalidValue;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<bool> attr_set{false};  // setting it twice is harmless
+    if (!attr_set.load(std::memory_order_relaxed)) {
         cudaError_t e = cudaFuncSetAttribute(gemm_tn_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kGemmSmemBytes);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set.store(true, std::memory_order_relaxed);
     }
     CUtensorMap ta, tb;
     cudaError_t e = make_map(&ta, A, M, K);
