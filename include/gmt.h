@@ -41,7 +41,7 @@ typedef void* gmt_stream;
 
 typedef enum {
     GMT_OK = 0,
-    GMT_NO_PATH = 1,          /* Alg. 1, Line 12a: V_open became empty */
+    GMT_NO_PATH = 1,          /* Alg. 1's failure outcome: V_open became empty */
     GMT_ERR_INVALID = -1,     /* bad argument, x_init in collision, sampling exhausted */
     GMT_ERR_OOM = -2,         /* device allocation failed or over the memory budget */
     GMT_ERR_CUDA = -3,        /* CUDA runtime error (message in gmt_last_error) */
@@ -224,9 +224,9 @@ typedef struct {
     int32_t path_len;     /* nodes on the path x_init .. goal_node, 0 if none */
     int64_t iters;        /* group expansions (non-empty groups G) */
     int64_t final_i;      /* threshold index i of the last expanded group */
-    int64_t push_edges;   /* out-edges scanned from group nodes (Alg. 1, Line 4) */
-    int64_t pull_edges;   /* in-edges scanned for parent selection (Lines 5-6) */
-    int64_t checks;       /* lazy collision checks (Line 7) */
+    int64_t push_edges;   /* out-edges scanned from group nodes (Alg. 1's frontier push) */
+    int64_t pull_edges;   /* in-edges scanned for parent selection (lazy parent) */
+    int64_t checks;       /* lazy collision checks (Alg. 1) */
     int64_t failed;       /* checks that found a collision */
     int64_t tree_size;    /* nodes with finite cost at termination */
 } gmt_plan_info;
@@ -234,7 +234,7 @@ typedef struct {
 /* Algorithm 1 on a built graph: one persistent kernel runs every wavefront
  * iteration (group selection, frontier push, lazy parent selection, one
  * collision check per candidate, set update, termination test) without host
- * round trips.  V_open in Lines 5-6 is the open set at the start of the
+ * round trips.  V_open in the lazy parent step is the open set at the start of the
  * iteration; a candidate whose check fails stays unexplored.
  *   boxes: obstacles for the collision checks (DEVICE arrays, may differ from
  *          the ones used at build time).
@@ -358,7 +358,7 @@ typedef struct {
     int32_t goal_node;
     float path_cost;
     int64_t iters;
-    int64_t checks;        /* lazy checks (Alg. 1, Line 7) */
+    int64_t checks;        /* lazy checks (Alg. 1) */
     int64_t checks_computed; /* of those, not answered by the verdict cache */
     int64_t edges_checked; /* out-edges pushed + in-edges pulled */
     double queue_ms;       /* submit -> launch */

@@ -449,7 +449,7 @@ R edge_cost(int kind, const R* from, const R* to, int d, R r, R* tau, R rho = 0)
 }
 
 // ---------------------------------------------------------------------------
-// Edge collision check (Alg. 1, Line 7): one connection, checked lazily.
+// Edge collision check (Alg. 1's lazy check, Sec. III-A): one connection.
 // Geometric: m = max(2, ceil(L/spacing)+1) points p_k = y + t_k (x - y),
 //   t_k = k/(m-1), endpoints included; a point in a closed box collides.
 // Double integrator: the minimum-effort trajectory is the cubic Hermite curve
@@ -611,7 +611,8 @@ void finish(const Graph<R>& g, const std::vector<R>& cost, bool success, orc_inf
     info->goal_node = -1;
     info->path_cost = std::numeric_limits<double>::infinity();
     if (!success) { info->status = ORC_NO_PATH; return; }
-    // Result (Alg. 1, Line 12b): the minimum-cost tree node in X_goal, ties by index.
+    // Result (Alg. 1's returned path, Sec. III-A): the minimum-cost tree node in
+    // X_goal, ties by index.
     int best = -1;
     for (int v = 0; v < g.N; ++v)
         if (g.goal[v] && cost[v] < std::numeric_limits<R>::infinity())
@@ -622,25 +623,101 @@ void finish(const Graph<R>& g, const std::vector<R>& cost, bool success, orc_inf
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 1 (Group Marching Tree), literally, one iteration at a time.
-//   Line 1-2: V_open = {x_init}, tree rooted at x_init, i = 0, delta = lambda r.
-//   Line 3:   G = {v in V_open : cost(v) <= theta_i}, theta_i = fl(fl(i)*delta).
-//             (lambda = 0 is the FMT* limit: G = open nodes at the minimum cost.)
-//   Line 4:   every unexplored out-neighbour x of a node of G, once.
-//   Line 5-6: y* = argmin over in-neighbours y in V_open of (cost(y)+c(y,x), y);
-//             V_open is the set at the start of the iteration.
-//   Line 7-9: if the edge y* -> x is collision-free, add it; x leaves
-//             V_unexplored and enters V_open (visible from iteration i+1).
-//             A failed x stays unexplored and may be retried later.
-//   Line 10:  G moves from V_open to V_closed.
-//   Line 12:  stop with success if G held a goal node, with failure if V_open
-//             is empty; otherwise Line 11, i = i + 1.
-// With skip_empty, the iterations whose group would be empty (no-ops) are
-// skipped: the next i is the smallest i' > i with theta_{i'} >= min open cost.
+// Group Marching Tree (Sec. III-A, Algorithm 1), one threshold index at a time.
+//
+// Every node is in one of three sets: unexplored (not yet in the tree), open
+// (in the tree, its out-neighbours not yet expanded) or closed (expanded).
+// The tree starts as x_init alone, open, at cost 0.  At threshold index i the
+// group is every open node whose cost is at most theta_i = fl(fl(i) * delta),
+// delta = fl(lambda r); lambda = 0 is the FMT* limit, where the group is the
+// open nodes at the minimum open cost.  The group's unexplored out-neighbours
+// are the candidates.  Each candidate x looks for its cheapest connection
+// among its open in-neighbours y, by (cost(y) + c(y, x), y) -- "open" as it
+// stood before this index's additions -- and checks only that one edge for
+// collisions (the lazy check).  A free edge puts x in the tree, open from the
+// next index on; a blocked one leaves x unexplored, to be tried again when a
+// later group reaches it.  Then the group closes.  The plan succeeds as soon
+// as a closed group held a goal node and fails once nothing is open.
+// With skip_empty, threshold indices whose group would be empty (no-ops) are
+// skipped: the next index is the smallest i' > i with theta_{i'} >= the
+// minimum open cost.
 // ---------------------------------------------------------------------------
+namespace gmt_steps {
+
+// Open nodes with cost <= theta, ascending.
+template <typename R>
+std::vector<int> open_group(const std::vector<int>& set, const std::vector<R>& cost, R theta) {
+    std::vector<int> grp;
+    for (int v = 0; v < (int)set.size(); ++v)
+        if (set[v] == OPEN && cost[v] <= theta) grp.push_back(v);
+    return grp;
+}
+
+// Smallest cost among open nodes (+inf if none is open).
+template <typename R>
+R min_open_cost(const std::vector<int>& set, const std::vector<R>& cost) {
+    R m = std::numeric_limits<R>::infinity();
+    for (int v = 0; v < (int)set.size(); ++v)
+        if (set[v] == OPEN && cost[v] < m) m = cost[v];
+    return m;
+}
+
+// Unexplored out-neighbours of the group's nodes, each once, ascending.
+template <typename R>
+std::vector<int> candidates_of(const Graph<R>& g, const std::vector<int>& grp, const std::vector<int>& set,
+                               int64_t* scanned) {
+    std::vector<char> seen(g.N, 0);
+    std::vector<int> cand;
+    for (int z : grp) {
+        *scanned += g.out_row[z + 1] - g.out_row[z];
+        for (int e = g.out_row[z]; e < g.out_row[z + 1]; ++e) {
+            const int x = g.out_col[e];
+            if (set[x] == UNEXPLORED && !seen[x]) { seen[x] = 1; cand.push_back(x); }
+        }
+    }
+    std::sort(cand.begin(), cand.end());
+    return cand;
+}
+
+// The lexicographically smallest (cost(y) + c(y, x), y) over open in-neighbours
+// y of x.  Returns y (-1 if none), its connection cost and the edge's cost.
+template <typename R>
+int best_open_parent(const Graph<R>& g, int x, const std::vector<int>& set, const std::vector<R>& cost, R* via,
+                     R* edge, int64_t* scanned) {
+    *scanned += g.in_row[x + 1] - g.in_row[x];
+    int best = -1;
+    R cbest = std::numeric_limits<R>::infinity(), ebest = 0;
+    for (int e = g.in_row[x]; e < g.in_row[x + 1]; ++e) {
+        const int y = g.in_col[e];
+        if (set[y] != OPEN) continue;
+        const R c = cost[y] + g.in_cost[e];
+        if (best < 0 || c < cbest || (c == cbest && y < best)) { best = y; cbest = c; ebest = g.in_cost[e]; }
+    }
+    *via = cbest;
+    *edge = ebest;
+    return best;
+}
+
+// The threshold index after i, given the minimum open cost m > theta_i.  The
+// index stays below 2^24 (exact in FP32); returns -1 beyond that.
+template <typename R>
+int64_t next_index(int64_t i, R m, R delta, bool skip_empty) {
+    if (delta == (R)0) return i + 1;
+    if (!(m / delta < (R)16777216)) return -1;
+    if (!skip_empty) return i + 1;
+    int64_t k = (int64_t)std::ceil(m / delta);
+    if (k < i + 1) k = i + 1;
+    while (k > i + 1 && (R)(k - 1) * delta >= m) --k;
+    while ((R)k * delta < m) ++k;
+    return k;
+}
+
+}  // namespace gmt_steps
+
 template <typename R>
 int gmt_plan(const Graph<R>& g, const PlanCfg& P, int32_t* parent_out, R* cost_out, orc_info* info,
              int64_t* added_i = nullptr, int64_t* closed_i = nullptr) {
+    using namespace gmt_steps;
     const int N = g.N;
     const R INF = std::numeric_limits<R>::infinity();
     std::memset(info, 0, sizeof(*info));
@@ -655,82 +732,45 @@ int gmt_plan(const Graph<R>& g, const PlanCfg& P, int32_t* parent_out, R* cost_o
     int64_t i = 0;
     bool success = false;
     int status = ORC_OK;
-    std::vector<char> is_near(N, 0);
-    struct Add { int x, y; R c; };
+    struct Link { int x, y; R c; };
     for (;;) {
-        // Line 3
-        R theta;
-        if (delta == (R)0) {
-            theta = INF;
-            for (int v = 0; v < N; ++v) if (set[v] == OPEN && cost[v] < theta) theta = cost[v];
-        } else {
-            theta = (R)i * delta;
-        }
-        std::vector<int> G;
-        for (int v = 0; v < N; ++v)
-            if (set[v] == OPEN && cost[v] <= theta) G.push_back(v);
-        if (!G.empty()) {
+        const R theta = delta == (R)0 ? min_open_cost(set, cost) : (R)i * delta;
+        const std::vector<int> grp = open_group(set, cost, theta);
+        if (!grp.empty()) {
             if (info->iters >= P.max_iters) { status = ORC_ERR_ITER_LIMIT; break; }
             info->iters++;
         }
-        // Line 4
-        std::vector<int> Xnear;
-        for (int z : G) {
-            info->push_edges += g.out_row[z + 1] - g.out_row[z];
-            for (int e = g.out_row[z]; e < g.out_row[z + 1]; ++e) {
-                int x = g.out_col[e];
-                if (set[x] == UNEXPLORED && !is_near[x]) { is_near[x] = 1; Xnear.push_back(x); }
-            }
-        }
-        std::sort(Xnear.begin(), Xnear.end());
-        // Lines 5-9
-        std::vector<Add> added;
-        for (int x : Xnear) {
-            is_near[x] = 0;
-            info->pull_edges += g.in_row[x + 1] - g.in_row[x];
-            int ybest = -1;
-            R cbest = INF, ebest = 0;
-            for (int e = g.in_row[x]; e < g.in_row[x + 1]; ++e) {
-                int y = g.in_col[e];
-                if (set[y] != OPEN) continue;
-                R c = cost[y] + g.in_cost[e];
-                if (ybest < 0 || c < cbest || (c == cbest && y < ybest)) { ybest = y; cbest = c; ebest = g.in_cost[e]; }
-            }
-            // x was reached from a node of G, which is open, so ybest exists.
+        // every candidate is decided against the open set as it stands now;
+        // the new tree edges are applied together afterwards
+        std::vector<Link> links;
+        for (int x : candidates_of(g, grp, set, &info->push_edges)) {
+            R via, edge;
+            const int y = best_open_parent(g, x, set, cost, &via, &edge, &info->pull_edges);
+            // x was reached from a node of the group, which is open, so y exists
             info->checks++;
-            if (check_edge(g, ybest, x, ebest, P)) added.push_back({x, ybest, cbest});
+            if (check_edge(g, y, x, edge, P)) links.push_back({x, y, via});
             else info->failed++;
         }
-        for (const Add& a : added) {
-            set[a.x] = OPEN; parent[a.x] = a.y; cost[a.x] = a.c;
-            if (added_i) added_i[a.x] = i;
+        for (const Link& l : links) {
+            set[l.x] = OPEN; parent[l.x] = l.y; cost[l.x] = l.c;
+            if (added_i) added_i[l.x] = i;
         }
-        // Line 10
-        bool goal_in_G = false;
-        for (int z : G) {
+        bool goal_in_group = false;
+        for (int z : grp) {
             set[z] = CLOSED;
-            if (g.goal[z]) goal_in_G = true;
+            if (g.goal[z]) goal_in_group = true;
             if (closed_i) closed_i[z] = i;
         }
-        // Line 12
-        if (goal_in_G) { success = true; break; }
-        R m = INF;
-        for (int v = 0; v < N; ++v) if (set[v] == OPEN && cost[v] < m) m = cost[v];
+        if (goal_in_group) { success = true; break; }
+        const R m = min_open_cost(set, cost);
         if (m == INF) { success = false; break; }
-        // Line 11
-        // The threshold index is kept below 2^24 (exact in FP32); beyond it the
-        // plan stops with an iteration-limit error.
-        if (delta == (R)0 || !P.skip_empty) {
-            i = i + 1;
-            if (delta != (R)0 && !(m / delta < (R)16777216)) { status = ORC_ERR_ITER_LIMIT; break; }
-        } else {
-            if (!(m / delta < (R)16777216)) { status = ORC_ERR_ITER_LIMIT; break; }
-            int64_t k = (int64_t)std::ceil(m / delta);
-            if (k < i + 1) k = i + 1;
-            while (k > i + 1 && (R)(k - 1) * delta >= m) --k;
-            while ((R)k * delta < m) ++k;
-            i = k;
+        const int64_t nxt = next_index(i, m, delta, P.skip_empty);
+        if (nxt < 0) {  // the index would leave the exact FP32 range
+            if (!P.skip_empty) i = i + 1;
+            status = ORC_ERR_ITER_LIMIT;
+            break;
         }
+        i = nxt;
     }
     info->final_i = i;
     int64_t tree = 0;

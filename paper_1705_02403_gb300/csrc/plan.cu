@@ -8,14 +8,14 @@
 //
 //   1  the open-set snapshot `ocost` (cost if open, +inf otherwise) is
 //      brought up to date with the previous iteration (its group closed, the
-//      nodes it opened set to their costs); group selection (Line 3) splits
+//      nodes it opened set to their costs); group selection (Alg. 1's group) splits
 //      the open list into G_i = {v open : cost(v) <= theta_i} and the nodes
 //      that stay open; the warp that selects a node of G_i at once pushes it
-//      (Line 4): it scans the node's out-row and claims every unexplored
+//      (the frontier push): it scans the node's out-row and claims every unexplored
 //      neighbour once per iteration through one atomicMax on its stamp
 //      (INT_MAX marks tree nodes), appending it to the candidate list.
 //      Nothing reads the snapshot in this phase.
-//   2  lazy parent (Lines 5-9): one warp per candidate x scans its in-row,
+//   2  lazy parent, check and commit: one warp per candidate x scans its in-row,
 //      gathers the snapshot and takes argmin of (ocost[y] + c(y, x), y); the
 //      warp checks that single edge (points spread over the lanes) and, if it
 //      is free, commits parent and cost and appends x to the next open list.
@@ -27,7 +27,7 @@
 // stay open at its front and the newly opened nodes at its back, so phase 1
 // of the next iteration finds exactly the nodes the snapshot lacks.
 //
-// After phase 2 every thread reads the same totals and decides (Line 12):
+// After phase 2 every thread reads the same totals and decides (Alg. 1's termination test):
 // success if G_i held a goal node, failure if no node stays open, else the
 // next threshold index is the smallest i' > i with theta_{i'} >= min open cost
 // (iterations whose group would be empty are no-ops and are skipped).  Lists
@@ -85,7 +85,7 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
     const unsigned INF_KEY = 0x7f800000u;
     const int N = A.N;
 
-    // Lines 1-2: x_init is the only open node and the root of the tree.
+    // Initialisation: x_init is the only open node and the root of the tree.
     // stamp[v]: INT_MAX once v is in the tree, else the last iteration that
     // claimed v as a candidate (-1: never)
     for (int v = rank; v < N; v += size) {
@@ -285,7 +285,7 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
                         nxt[N - 1 - s] = make_int2(x, __float_as_int(bc));
                         atomicMin(&ctl->min_new[p], float_key(bc));
                         // a tree node's cost never changes, so the minimum goal
-                        // node over commits is Line 12b's minimum over the tree
+                        // node over commits is the returned path's minimum over the tree
                         ++n_tree;
                         if (x_goal) atomicMin(&ctl->goal_key, ((unsigned long long)float_key(bc) << 32) | (unsigned)x);
                     } else {
@@ -296,7 +296,7 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
         }
         if (!(ok = team.sync(ctl))) break;
 
-        // ---- Line 12 / Line 11: termination test, next threshold
+        // ---- termination test, next threshold
         const int goal = st_i<SM>(&ctl->goal_flag[p]);
         const int n_open = (int)(st_ull<SM>(&ctl->gk[p]) >> 32) + st_i<SM>(&ctl->new_count[p ^ 1]);
         const unsigned mk = min(st_u<SM>(&ctl->min_keep[p]), st_u<SM>(&ctl->min_new[p]));
@@ -341,7 +341,7 @@ __device__ __forceinline__ void plan_body(const PlanArgs& A, const Team& team, f
             atomicAdd(&ctl->tree_size, tree);
         }
     }
-    // Line 12b's path is walked by rank 0 from the goal node back to x_init.
+    // The returned path is walked by rank 0 from the goal node back to x_init.
     // The wavefront is over and the staged boxes are no longer needed, so CTA 0
     // first copies the parent array into that shared memory when it fits:
     // each hop is then a shared-memory read instead of an L2 round trip.

@@ -281,7 +281,7 @@ template <bool SM> __device__ __forceinline__ unsigned long long st_ull(const un
     return __ldcg(p);
 }
 
-// Lazy parent (Alg. 1, Lines 5-6), one lane's share: over the in-row entries
+// Lazy parent (Alg. 1, Sec. III-A), one lane's share: over the in-row entries
 // r0 + lane, r0 + lane + 32, ... the minimum (cost, index) of
 // fl(ocost[y] + in_cost[e]) among open y (ocost < +inf); *be = its edge, -1
 // if none.  (cost, index) is a total order, so the order of the entries does

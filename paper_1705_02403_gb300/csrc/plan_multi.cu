@@ -30,7 +30,7 @@
 // counters) are first gathered per block in shared memory and reach the
 // per-query control blocks once per block and step; list appends are
 // reserved once per block (groups and kept entries with one packed 64-bit
-// atomic).  Then every block evaluates Line 12 / Line 11 for every live
+// atomic).  Then every block evaluates the termination test and the next threshold for every live
 // query: success, failure, or the next threshold index with the skip-ahead
 // over empty groups.
 // Results equal those of the single-query kernel bit for bit (the wavefront's
@@ -70,7 +70,7 @@ __device__ __forceinline__ int find_node_query(const int* base, int nq, int g) {
     return lo;
 }
 
-// Lines 5-9 for one candidate x of query q, run by a whole warp: lazy parent
+// Lazy parent, check and commit for one candidate x of query q, run by a whole warp: lazy parent
 // over the open snapshot, one edge check, commit.  Returns (uniformly across
 // the warp) whether x joined the tree; its cost is then in *out_cost.
 template <int KIND, int DP>
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(1024) plan_lockstep_kernel(const PlanArgs* __r
     if (tid == 0) sm.app = 0;
     __syncthreads();
 
-    // Lines 1-2 for every query: x_init (node 0) is the only open node.
+    // Initialisation for every query: x_init (node 0) is the only open node.
     for (int g = rank; g < M; g += size) {
         const int q = find_node_query(sm.base, nq, g);
         if (sm.status[q] == GMT_ERR_OOM) continue;
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(1024) plan_lockstep_kernel(const PlanArgs* __r
         }
         if (!(ok = team.sync(tc))) break;
 
-        // ---- Line 12 / Line 11 for every live query (same result in every block)
+        // ---- termination test and next threshold for every live query (same result in every block)
         ++it;
         any = 0;
         for (int k = tid; k < nq; k += blockDim.x) {

@@ -1,4 +1,4 @@
-"""Pins of the oracle's lazy edge collision check (Alg. 1, Line 7)."""
+"""Pins of the oracle's lazy edge collision check (Alg. 1, Sec. III-A)."""
 import numpy as np
 
 F = np.float32

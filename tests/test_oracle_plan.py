@@ -1,7 +1,7 @@
 """Pins of the oracle's Algorithm 1 (GMT*), FMT* and Dijkstra.
 
 Hand traces use dyadic coordinates so that every cost is exact in FP32; the
-expected values in the tests were worked out by hand from Alg. 1 (Lines 1-12)
+expected values in the tests were worked out by hand from Alg. 1 (Sec. III-A)
 with the readings: group rule cost <= i*delta, V_open taken at the start of an
 iteration, lazy failures stay unexplored, termination after the group is
 expanded, result = minimum-cost goal node.
