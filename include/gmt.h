@@ -297,15 +297,21 @@ gmt_status gmt_plan_batch(int32_t q, const gmt_query* queries, gmt_batch** batch
 gmt_status gmt_batch_get_view(const gmt_batch* batch, int32_t k, gmt_graph_view* view, int32_t** path);
 
 /* Plan-stage scheme of a batch.
- *   GMT_BATCH_TEAMS: one persistent launch per group; a team (a CTA or a
- *     cluster) runs one query at a time with team barriers.
+ *   GMT_BATCH_TEAMS: one persistent launch for every query of the batch; a
+ *     team (a CTA or a cluster) runs one query at a time, one team barrier per
+ *     Algorithm 1 iteration (double-buffered open-set snapshot; candidates
+ *     are pulled from a team-wide queue as soon as they are claimed).
  *   GMT_BATCH_LOCKSTEP: one cooperative grid runs up to 512 queries at once,
  *     one Algorithm 1 iteration of every live query per grid step (two
  *     bounded grid barriers per step), so small groups of many queries fill
  *     the GPU together.
- *   GMT_BATCH_AUTO: the autotuner's choice; before tuning, lockstep when the
- *     queries average at most 2048 nodes, else teams. */
-typedef enum { GMT_BATCH_AUTO = 0, GMT_BATCH_TEAMS = 1, GMT_BATCH_LOCKSTEP = 2 } gmt_batch_mode;
+ *   GMT_BATCH_POOL: one persistent launch for every query of the batch (all
+ *     kinds); each iteration of each query is split into work items (group
+ *     selection over 32 open entries, the push of one group node, the lazy
+ *     parent and check of one candidate) that any warp may take, so queries
+ *     advance without team barriers and without waiting for one another.
+ *   GMT_BATCH_AUTO: the autotuner's choice; before tuning, teams of 4 CTAs. */
+typedef enum { GMT_BATCH_AUTO = 0, GMT_BATCH_TEAMS = 1, GMT_BATCH_LOCKSTEP = 2, GMT_BATCH_POOL = 3 } gmt_batch_mode;
 gmt_status gmt_batch_set_mode(gmt_batch* batch, int32_t mode);
 
 /* Launch shape of the batched plan stage: cluster = CTAs per team (teams
@@ -422,7 +428,11 @@ typedef struct gmt_model gmt_model;
 
 /* DEVICE pointers into a model (parameters FP32 row-major [out][in], their
  * BF16 copies, the last gradients, logits [B][cells^3] and per-environment
- * losses of the last forward/backward). */
+ * losses of the last forward/backward).  The BF16 activations of the last
+ * pass, row-major with one row per environment (valid for its first B rows):
+ * H1, H2 [B][hidden] (after ReLU), Z [B][z_features] (H2, start, goal, zero
+ * padding), and of the last backward dlog [B][cells^3] ((softmax - target)/B),
+ * dH2, dH1 [B][hidden] (gradients after the ReLU masks). */
 typedef struct {
     int32_t grid, hidden, cells, in_features, z_features, n_cells, max_batch;
     int64_t step;
@@ -431,6 +441,7 @@ typedef struct {
     const void *W1_bf16, *W2_bf16, *W3_bf16;
     const float* logits;
     const float* loss;
+    const void *H1, *H2, *Z, *dlog, *dH2, *dH1;
 } gmt_model_view;
 
 gmt_status gmt_model_create(const gmt_model_config* config, gmt_model** model);
@@ -496,8 +507,7 @@ gmt_status gmt_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const v
  * counterpart).  Runs the same wavefront kernel as gmt_plan, for callers that
  * must not allocate device memory while they plan: a replanning loop inside a
  * control cycle (cudaMalloc/cudaFree can synchronise the device and have no
- * latency bound), code running while a stream is captured into a CUDA graph,
- * or systems whose memory is fixed at start-up.
+ * latency bound), or systems whose memory is fixed at start-up.
  *   space: HOST struct; its position bounds are used by double-integrator
  *          trajectory checks and must match the graph's kind and dimensions.
  *   graph: HOST struct of DEVICE arrays describing the neighbour CSR and the
@@ -508,7 +518,10 @@ gmt_status gmt_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const v
  * The kernel's scratch is one fixed __device__ array inside the library
  * (about 2.4 MB on each GPU that loads it, held until the process exits); no
  * cudaMalloc, cudaFree or other allocating call is made.  The first call on a
- * device looks up that array's address; make it before any stream capture.
+ * device looks up that array's address and the plan kernel's largest resident
+ * cluster; make it before any stream capture.  The launch shape is gmt_plan's
+ * automatic one, but every check scans the boxes linearly (gmt_plan's box grid
+ * for 128 or more boxes needs allocated scratch).
  * Every call on a device shares the array (its contents persist between calls;
  * each call clears the control block it needs), so calls that overlap on the
  * GPU race: serialise them.  Synchronises `stream`; returns info->status. */

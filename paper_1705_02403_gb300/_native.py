@@ -100,7 +100,9 @@ class gmt_model_view(C.Structure):
                 ("gW1", C.c_void_p), ("gb1", C.c_void_p), ("gW2", C.c_void_p), ("gb2", C.c_void_p),
                 ("gW3", C.c_void_p), ("gb3", C.c_void_p),
                 ("W1_bf16", C.c_void_p), ("W2_bf16", C.c_void_p), ("W3_bf16", C.c_void_p),
-                ("logits", C.c_void_p), ("loss", C.c_void_p)]
+                ("logits", C.c_void_p), ("loss", C.c_void_p),
+                ("H1", C.c_void_p), ("H2", C.c_void_p), ("Z", C.c_void_p), ("dlog", C.c_void_p),
+                ("dH2", C.c_void_p), ("dH1", C.c_void_p)]
 
 
 class gmt_server_config(C.Structure):
@@ -326,7 +328,7 @@ def gmt_batch_get_view(batch: Batch, k: int):
     return v, path.value
 
 
-BATCH_AUTO, BATCH_TEAMS, BATCH_LOCKSTEP = 0, 1, 2
+BATCH_AUTO, BATCH_TEAMS, BATCH_LOCKSTEP, BATCH_POOL = 0, 1, 2, 3
 
 
 def gmt_batch_set_mode(batch: Batch, mode: int) -> None:

@@ -2,20 +2,25 @@
 //
 // Some callers cannot allocate device memory when they plan: a replanning
 // loop inside a control cycle (a cudaMalloc or cudaFree may synchronise the
-// whole device and has no latency bound), code running while a stream is being
-// captured into a CUDA graph (allocation calls are not allowed there), or
-// systems that fix their memory at start-up.  This entry point takes the graph
-// as plain device arrays (a gmt_graph_view the caller fills) and runs the same
-// plan kernel as gmt_plan; the kernel's scratch (open-set snapshot, claim
-// stamps, group/open/candidate lists, control block and barrier words) lives
-// in one file-scope __device__ array of fixed size instead of being allocated.
+// whole device and has no latency bound), or systems that fix their memory at
+// start-up.  This entry point takes the graph as plain device arrays (a
+// gmt_graph_view the caller fills) and runs the same plan kernel as gmt_plan;
+// the kernel's scratch (open-set snapshot, claim stamps, group/open/candidate
+// lists, control block and barrier words) lives in one file-scope __device__
+// array of fixed size instead of being allocated.
 //
 //  - Capacity: graphs of at most GMT_STATIC_MAX_NODES nodes; larger ones are
 //    rejected with GMT_ERR_INVALID.  The array takes about 2.4 MB on every GPU
 //    that loads the library, for the life of the process.
 //  - Set-up: the first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress, with that device current) and caches it; make that
-//    first call before any stream capture begins.
+//    (cudaGetSymbolAddress, with that device current) and caches it, together
+//    with the largest resident cluster of the plan kernel; make that first
+//    call before any stream capture begins.
+//  - Launch: the same automatic shape as gmt_plan (one CTA with its state in
+//    shared memory for small 2D graphs, else the largest resident thread-block
+//    cluster, else a cooperative grid).  Obstacles are scanned linearly by
+//    every check: the box grid that gmt_plan builds for 128 or more boxes needs
+//    allocated scratch, so many boxes cost more here than in gmt_plan.
 //  - Sharing: every call on a device uses the same array and the array keeps
 //    the last call's contents; the control block is cleared at the start of
 //    each call.  Calls whose kernels overlap on the GPU (other streams, other
@@ -43,6 +48,10 @@ static __device__ __align__(256) unsigned char g_plan_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 unsigned char* g_scratch_addr[kMaxDevices] = {};
+// plan_max_cluster per device and kernel (double integrator, Dubins, 2D, other
+// geometric) x threads (512, 1024); -1 = not probed yet
+int g_cluster[kMaxDevices][4][2];
+bool g_cluster_init = false;
 
 gmt_status fail(gmt_status s, const std::string& m) {
     record_error(m.c_str());  // readable through gmt_last_error()
@@ -67,6 +76,26 @@ gmt_status scratch_address(unsigned char** out) {
         g_scratch_addr[dev] = (unsigned char*)p;
     }
     *out = g_scratch_addr[dev];
+    return GMT_OK;
+}
+
+// Largest resident cluster of the plan kernel on the current device (cached).
+gmt_status max_cluster(int kind, int dp, int threads, int* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(GMT_ERR_INVALID, "device index out of range");
+    const int k = kind == GMT_COST_DI ? 0 : kind == GMT_COST_DUBINS ? 1 : dp == 2 ? 2 : 3;
+    const int t = threads == 1024 ? 1 : 0;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_cluster_init) {
+        for (auto& d : g_cluster)
+            for (auto& kk : d)
+                for (int& v : kk) v = -1;
+        g_cluster_init = true;
+    }
+    if (g_cluster[dev][k][t] < 0) g_cluster[dev][k][t] = plan_max_cluster(kind, dp, threads);
+    *out = g_cluster[dev][k][t];
     return GMT_OK;
 }
 
@@ -132,20 +161,31 @@ extern "C" gmt_status gmt_plan_static(const gmt_space* space, const gmt_graph_vi
     assign_plan_lists(a, lists, NM);
     a.ctl = ctl;
 
-    int blocks = 1, threads = 1024;
-    if (g->N > 2048) {
-        int dev = 0, sms = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return cuda_fail(e, "device attribute");
-        threads = 512;
-        const int maxb = plan_max_coresident_blocks(g->kind, g->pos_dim, threads);
-        if (maxb <= 0) return fail(GMT_ERR_CUDA, "plan kernel cannot be resident");
-        blocks = sms < maxb ? sms : maxb;
+    // launch shape: as gmt_plan chooses it automatically
+    int blocks = 0, cluster = 0, threads = 0;
+    if (g->kind == GMT_COST_EUCLID && g->pos_dim == 2 && g->N <= 2049) {
+        blocks = 1;  // one CTA, wavefront state in shared memory
+        threads = 1024;
+    } else {
+        threads = g->N <= 2048 ? 512 : 1024;
+        s = max_cluster(g->kind, g->pos_dim, threads, &cluster);
+        if (s != GMT_OK) return s;
+        if (cluster <= 1) {
+            cluster = 0;
+            int dev = 0, sms = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return cuda_fail(e, "device attribute");
+            const int maxb = plan_max_coresident_blocks(g->kind, g->pos_dim, threads);
+            if (maxb <= 0) return fail(GMT_ERR_CUDA, "plan kernel cannot be resident");
+            blocks = sms < maxb ? sms : maxb;
+        }
     }
+    // a cooperative grid's barrier counts live in the control block and must
+    // start at zero; the other launches clear their result fields themselves
     cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(PlanCtl), st);
     if (e != cudaSuccess) return cuda_fail(e, "clearing the control block");
-    e = launch_plan(a, blocks, threads, st);
+    e = launch_plan(a, blocks, threads, st, cluster);
     if (e != cudaSuccess) return cuda_fail(e, "plan kernel launch");
     PlanCtl c;
     e = cudaMemcpyAsync(&c, ctl, sizeof(PlanCtl), cudaMemcpyDeviceToHost, st);

@@ -490,6 +490,7 @@ gmt_status gmt_model_get_view(const gmt_model* m, gmt_model_view* v) {
     v->gW1 = m->gW1; v->gb1 = m->gb1; v->gW2 = m->gW2; v->gb2 = m->gb2; v->gW3 = m->gW3; v->gb3 = m->gb3;
     v->W1_bf16 = m->W1b; v->W2_bf16 = m->W2b; v->W3_bf16 = m->W3b;
     v->logits = m->logits; v->loss = m->loss;
+    v->H1 = m->H1; v->H2 = m->H2; v->Z = m->Z; v->dlog = m->dlog; v->dH2 = m->dH2; v->dH1 = m->dH1p;
     return GMT_OK;
 }
 

@@ -21,10 +21,10 @@ class _CudaArray:
 
 def wrap_device(ptr: int, shape, dtype: str, owner, device=None) -> torch.Tensor:
     """Zero-copy torch view of device memory owned by `owner` (kept alive)."""
-    typestr = {"f4": "<f4", "i4": "<i4", "u1": "|u1"}[dtype]
+    typestr = {"f4": "<f4", "i4": "<i4", "i2": "<i2", "u1": "|u1"}[dtype]
     if int(np.prod(shape)) == 0:
-        return torch.empty(shape, dtype={"f4": torch.float32, "i4": torch.int32, "u1": torch.uint8}[dtype],
-                           device=device or "cuda")
+        return torch.empty(shape, dtype={"f4": torch.float32, "i4": torch.int32, "i2": torch.int16,
+                                         "u1": torch.uint8}[dtype], device=device or "cuda")
     return torch.as_tensor(_CudaArray(ptr, shape, typestr, owner), device=device or "cuda")
 
 

@@ -1,8 +1,9 @@
-"""The replanning server: every request's tree is the same alone and in a mix
-of overlapping requests (bit for bit, verdict cache included; geometric,
-double-integrator and Dubins-airplane sessions with moving boxes), sessions are
-admitted by device memory, and the verdict cache only recomputes what moved
-boxes can change."""
+"""The replanning server: every served tree equals the CPU oracle's plan on the
+session's samples with that request's boxes (and start), bit for bit, with the
+verdict cache warm; it is also the same alone and in a mix of overlapping
+requests (geometric, double-integrator and Dubins-airplane sessions with moving
+boxes); sessions are admitted by device memory, and the verdict cache only
+recomputes what moved boxes can change."""
 import numpy as np
 import pytest
 import torch
@@ -16,6 +17,35 @@ pytestmark = [pytest.mark.gpu,
 def structs(pb):
     from paper_1705_02403_gb300.planner import goal_struct, params_struct, space_struct
     return space_struct(pb), goal_struct(pb), params_struct(pb)
+
+
+def bits(a):
+    return np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+
+
+def oracle_graph(O, pb):
+    """The oracle's samples and r-disk graph of a session's problem (the
+    samples are drawn against the boxes the session was opened with)."""
+    X, goal = O.sample_halton(pb) if pb.sampler == 1 else O.sample(pb)
+    return O.graph_for(pb, X, goal)
+
+
+def session_samples(server, sid):
+    from paper_1705_02403_gb300.planner import wrap_device
+    v = server.session_view(sid)
+    return wrap_device(v.X, (v.dim, v.x_pitch), "f4", server)[:, :v.N].cpu().numpy()
+
+
+def assert_oracle(O, g, pb, lo, hi, r, parent, cost):
+    """A served result against the oracle's plan with the request's boxes."""
+    op, oc, oi = g.plan(lo, hi, pb.lo[:pb.dp], pb.hi[:pb.dp], pb.lam, pb.seg_spacing, pb.traj_points)
+    assert r["status"] == oi["status"] and r["goal_node"] == oi["goal_node"]
+    assert np.array_equal(parent.cpu().numpy(), op), "served parents differ from the oracle's"
+    assert np.array_equal(bits(cost.cpu().numpy()), bits(oc)), "served costs differ from the oracle's"
+    assert r["iters"] == oi["iters"] and r["checks"] == oi["checks"]
+    assert r["edges_checked"] == oi["push_edges"] + oi["pull_edges"]
+    if oi["status"] == O.OK:
+        assert np.float32(r["path_cost"]) == np.float32(oi["path_cost"])
 
 
 def alone(server, sid, pb, lo, hi):
@@ -33,7 +63,7 @@ def alone(server, sid, pb, lo, hi):
     return info, parent, cost
 
 
-def test_same_alone_and_in_the_mix():
+def test_same_alone_and_in_the_mix(O):
     from paper_1705_02403_gb300 import _native as N
     from paper_1705_02403_gb300.serving import MovingBoxes
     pbs = [envgen.di6(seed=1, n=700, r=2.8), envgen.geometric(2, d=2, n=900, nbox=10, r=0.12),
@@ -64,14 +94,21 @@ def test_same_alone_and_in_the_mix():
     torch.cuda.synchronize()
     overlapped = sum(r["queue_ms"] > 0.0 for r in res.values())
     assert overlapped > 0
+    graphs = [oracle_graph(O, pb) for pb in pbs]
+    for k, (pb, sid) in enumerate(zip(pbs, sids)):   # resident samples are the oracle's
+        assert np.array_equal(bits(session_samples(server, sid)), bits(graphs[k].X))
+    warm = 0
     for rid_, k, lo, hi, parent, cost in reqs:
         r = res[rid_]
+        assert_oracle(O, graphs[k], pbs[k], lo, hi, r, parent, cost)
+        warm += r["checks_computed"] < r["checks"]
         info, p2, c2 = alone(server, sids[k], pbs[k], lo, hi)
         assert r["status"] == info["status"] and r["goal_node"] == info["goal_node"]
         assert torch.equal(parent, p2)
         assert torch.equal(cost.view(torch.int32), c2.view(torch.int32))
         if info["status"] == 0:
             assert r["path_cost"] == info["path_cost"]
+    assert warm > 0   # later ticks answered checks from the verdict cache
     server.close()
 
 
@@ -98,29 +135,35 @@ def test_admission_by_device_memory():
     server.close()
 
 
-def test_verdict_cache_reuse():
+def test_verdict_cache_reuse(O):
     from paper_1705_02403_gb300 import _native as N
     pb = envgen.di6(seed=9, n=1500, r=2.6)
+    g = oracle_graph(O, pb)
     server = N.Server(slots=2, cluster=2, max_nodes=1501, max_boxes=30)
     sid, _ = server.open_session(*structs(pb)[:1], pb.x_init, *structs(pb)[1:], pb.box_lo, pb.box_hi)
-    server.submit(sid, 0, pb.box_lo, pb.box_hi)
-    r0 = server.poll(4, 5000)[0]
-    server.submit(sid, 1, pb.box_lo, pb.box_hi)          # nothing moved: every check is cached
-    r1 = server.poll(4, 5000)[0]
+
+    def request(rid, lo, hi):
+        parent = torch.full((pb.N,), -7, dtype=torch.int32, device="cuda")
+        cost = torch.full((pb.N,), -7.0, dtype=torch.float32, device="cuda")
+        server.submit(sid, rid, lo, hi, parent.data_ptr(), cost.data_ptr())
+        r = server.poll(4, 5000)[0]
+        torch.cuda.synchronize()
+        assert_oracle(O, g, pb, lo, hi, r, parent, cost)
+        return r
+
+    r0 = request(0, pb.box_lo, pb.box_hi)
+    r1 = request(1, pb.box_lo, pb.box_hi)                # nothing moved: every check is cached
     assert r1["checks_computed"] == 0 and r1["checks"] == r0["checks"] and r1["path_cost"] == r0["path_cost"]
     lo, hi = pb.box_lo.copy(), pb.box_hi.copy()
     lo[0] += 0.3; hi[0] += 0.3                           # one box moves
     lo[0] = np.clip(lo[0], 0, 0.9); hi[0] = np.clip(hi[0], 0.05, 1.0)
-    server.submit(sid, 2, lo, hi)
-    r2 = server.poll(4, 5000)[0]
+    r2 = request(2, lo, hi)
     assert 0 < r2["checks_computed"] < r2["checks"]
-    info, _, _ = alone(server, sid, pb, lo, hi)
-    assert r2["status"] == info["status"] and r2["goal_node"] == info["goal_node"]
     server.close()
 
 
 @pytest.mark.parametrize("kind", ["di", "dubins"])
-def test_start_move_rebuilds_the_session(kind):
+def test_start_move_rebuilds_the_session(O, kind):
     # After gmt_server_move_start the session plans exactly as a graph built
     # fresh at the new start (same seed, the boxes of its last request) and
     # planned with the request's boxes; a move into a box is refused and the
@@ -155,8 +198,7 @@ def test_start_move_rebuilds_the_session(kind):
         server.move_start(sid, x_bad)
     assert e.value.status == N.GMT_ERR_INVALID
     r, parent, cost = request(1, lo1, hi1)
-    info, p2, c2 = alone(server, sid, pb, lo1, hi1)
-    assert torch.equal(parent, p2) and torch.equal(cost.view(torch.int32), c2.view(torch.int32))
+    assert_oracle(O, oracle_graph(O, pb), pb, lo1, hi1, r, parent, cost)   # still the first start's graph
     # a valid move, then requests with moving boxes
     x_new = None
     for cand in ([0.03, 0.04, 0.3], [0.1, 0.03, 0.2], [0.04, 0.12, 0.1], [0.2, 0.05, 0.05]):
@@ -167,10 +209,15 @@ def test_start_move_rebuilds_the_session(kind):
             break
     assert x_new is not None
     server.move_start(sid, x_new)
-    fresh = Planner(pb.with_(x_init=x_new, box_lo=lo1, box_hi=hi1)).build()
+    # the rebuilt session: the same seed drawn at the new start against the
+    # boxes of its last request
+    moved = pb.with_(x_init=x_new, box_lo=lo1, box_hi=hi1)
+    g_new = oracle_graph(O, moved)
+    fresh = Planner(moved).build()
     for rid in (2, 3):
         lo, hi = mover.step()
         r, parent, cost = request(rid, lo, hi)
+        assert_oracle(O, g_new, moved, lo, hi, r, parent, cost)
         b, keep = boxes_on_device(pb.with_(box_lo=lo, box_hi=hi))
         fresh.boxes = b
         ref = fresh.plan()

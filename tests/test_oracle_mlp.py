@@ -1,5 +1,7 @@
 """Pins of the MLP oracle: FP64 finite differences of its loss on a reduced
-network, its softmax cross-entropy against scipy, and its BF16 rounding."""
+network, its softmax cross-entropy against scipy, its BF16 rounding, and its
+stage checks (another accumulation order passes them, planted mistakes do
+not)."""
 import numpy as np
 from scipy.special import log_softmax
 
@@ -48,3 +50,62 @@ def test_gradients_match_finite_differences():
             fd = (lp - lm) / (2 * eps)
             an = g["g" + name].reshape(-1)[idx]
             assert abs(fd - an) <= 1e-6 + 1e-5 * abs(fd), (name, idx, fd, an)
+
+
+def _stage_case(seed, Din=512, H=64, Nc=64, B=8):
+    rng = np.random.default_rng(seed)
+    P = M.random_params(rng, Din, H, Nc)
+    P = {k: v.astype(np.float32) for k, v in P.items()}
+    X = rng.integers(0, 2, (B, Din)).astype(np.float32)
+    sg = rng.random((B, 6)).astype(np.float32)
+    T = (rng.random((B, Nc)) ** 8).astype(np.float32)
+    T /= T.sum(1, keepdims=True)
+    return P, X, sg, T
+
+
+def _values(P, X, sg, T, acc):
+    """The oracle network's stage values with sums accumulated in `acc`, in
+    the order of a reversed input axis (another implementation)."""
+    perm = np.arange(X.shape[1])[::-1]
+    loss, g, f = M.loss_and_grads(dict(P, W1=P["W1"][:, perm]), X[:, perm], sg, T, rnd=True, acc=acc)
+    g["gW1"] = g["gW1"][:, np.argsort(perm)]
+    V = dict(g, loss=loss, logits=f["logits"], H1=f["H1"], H2=f["H2"], Z=f["Z"], dlog=f["dlog"], dH2=f["dH2"],
+             dH1=f["dH1p"], W1b=M.bf16(P["W1"]), W2b=M.bf16(P["W2"]), W3b=M.bf16(P["W3"]))
+    return V
+
+
+def test_stage_checks_accept_another_accumulation_order():
+    for seed in range(3):
+        P, X, sg, T = _stage_case(seed)
+        for acc in (np.float32, np.float64):
+            V = _values(P, X, sg, T, acc)
+            bad = M.stage_violations(P, X, sg, T, V)
+            assert not any(bad.values()), bad
+            e2e, _ = M.end_to_end_violations(P, X, sg, T, V)
+            assert not any(e2e.values()), e2e
+
+
+def test_stage_checks_catch_planted_mistakes():
+    # one activation two BF16 steps off, a dlog without its 1/B, one gradient
+    # element with the wrong sign, a ReLU mask not applied, a 1% scale error,
+    # rows of an activation swapped: each makes its stage fail
+    P, X, sg, T = _stage_case(5)
+    base = _values(P, X, sg, T, np.float64)
+
+    def fails(name, **over):
+        bad = M.stage_violations(P, X, sg, T, dict(base, **over))
+        assert bad[name] > 0, (name, bad)
+
+    H1 = base["H1"].copy()
+    j = tuple(np.argwhere(H1 > 0)[0])
+    H1[j] = M.bf16(np.array([H1[j] * (1 + 2 ** -6)], np.float32))[0]
+    fails("H1", H1=H1)
+    fails("dlog", dlog=M.bf16((base["dlog"] * X.shape[0]).astype(np.float32)))
+    gW2 = base["gW2"].copy()
+    i = np.unravel_index(np.argmax(np.abs(gW2)), gW2.shape)
+    gW2[i] = -gW2[i]
+    fails("gW2", gW2=gW2)
+    H = base["W2b"].shape[0]
+    fails("dH2", dH2=M.bf16((base["dlog"] @ base["W3b"])[:, :H].astype(np.float32)))
+    fails("gW1", gW1=base["gW1"] * 1.01)
+    fails("H2", H2=base["H2"][::-1].copy())

@@ -1,10 +1,12 @@
 """gmt_plan_static, the allocation-free plan entry point, against gmt_plan.
 
 Callers that must not allocate device memory while planning (a replanning loop
-inside a control cycle, work recorded into a CUDA graph, systems whose memory
-is fixed at start-up) use gmt_plan_static: the same wavefront kernel, with its
-scratch in a fixed array inside the library.  Its results must equal
-gmt_plan's bit for bit, on consecutive calls that share that array.
+inside a control cycle, where an allocation can stall the device; systems
+whose memory is fixed at start-up) use gmt_plan_static: the same wavefront
+kernel, with its scratch in a fixed array inside the library.  Its results must
+equal gmt_plan's bit for bit, on consecutive calls that share that array, up to
+graphs that fill the array; and calls after the first on a device must not
+change the device's free memory or the caching allocator's counts.
 """
 import numpy as np
 import pytest
@@ -48,6 +50,38 @@ def test_static_plan_equals_gmt_plan_on_consecutive_calls():
         for k in ("status", "goal_node", "path_cost", "iters", "final_i", "push_edges", "pull_edges", "checks",
                   "failed", "tree_size"):
             assert info[k] == ref[k], k
+
+
+def test_static_plan_on_large_graphs_and_without_allocation():
+    # A 2D graph of about 20000 nodes (its parent array no longer fits the
+    # shared memory that the path walk reads it from) and one close to the
+    # 65536-node limit, which uses nearly all of the fixed array.
+    from paper_1705_02403_gb300 import _native as N
+    for n in (20000, 65000):
+        pb = envgen.geometric(seed=11, d=2, n=n, nbox=20, r=0.0)
+        ref, rp, rc, rpath, info, parent, cost, path = plan_both(pb)
+        assert torch.equal(parent, rp)
+        assert torch.equal(cost.view(torch.int32), rc.view(torch.int32))
+        for k in ("status", "goal_node", "iters", "push_edges", "pull_edges", "checks", "tree_size"):
+            assert info[k] == ref[k], k
+    # repeated calls allocate nothing: free device memory and the caching
+    # allocator's counters are unchanged (outputs allocated beforehand)
+    from paper_1705_02403_gb300.planner import Planner
+    pl = Planner(envgen.cfg2_di6(4)).build()
+    view = N.gmt_graph_get_view(pl.graph)
+    parent = torch.empty_like(pl.parent)
+    cost = torch.empty_like(pl.cost)
+    N.gmt_plan_static(pl.space, view, pl.boxes, pl.params, parent.data_ptr(), cost.data_ptr(), None)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    stats0 = torch.cuda.memory_stats()
+    for _ in range(3):
+        N.gmt_plan_static(pl.space, view, pl.boxes, pl.params, parent.data_ptr(), cost.data_ptr(), None)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    stats1 = torch.cuda.memory_stats()
+    for k in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current"):
+        assert stats1.get(k, 0) == stats0.get(k, 0), k
 
 
 def test_static_plan_rejects_graphs_beyond_capacity():
