@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgmt.so")
-SOURCES = ["graph.cu", "cells.cu", "plan.cu", "plan_multi.cu", "capi.cu", "plan_static.cu", "batch.cu", "mlp.cu", "proposal.cu", "server.cu"]
+SOURCES = ["graph.cu", "cells.cu", "plan.cu", "plan_multi.cu", "plan_pool.cu", "capi.cu", "plan_static.cu", "batch.cu", "mlp.cu", "proposal.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-fmad=false", "-prec-div=true", "-prec-sqrt=true", "-ftz=false",
          "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", os.path.join(ROOT, "include")]

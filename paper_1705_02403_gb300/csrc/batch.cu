@@ -317,6 +317,7 @@ float euclid_threshold_b(float r) {
 }
 
 constexpr size_t kCtlSlotB = 256;
+static_assert(sizeof(PlanCtl) <= kCtlSlotB, "control block must fit its slot");
 
 struct Group {
     int kind = 0, d = 0, dp = 0;
@@ -350,7 +351,9 @@ struct gmt_batch {
     DevBuf cells, cell_info;
     DevBuf s_ocost, s_stamp, s_lists;
     DevBuf l_open, l_glist, l_ocost, l_stamp, l_ctl;
+    DevBuf p_args, p_order, p_ecum, p_q, p_ctl, p_scratch;  // pool scheme
     int lock_chunks = 0;
+    int max_n = 0;  // largest N of the batch (team scratch slices)
     cudaEvent_t ev_plan[2] = {nullptr, nullptr};  // around the plan stage of every call
     PlanCtl* h_ctl = nullptr;
     int* h_rows = nullptr;
@@ -442,16 +445,27 @@ cudaError_t record_plan_event(cudaEvent_t e, cudaStream_t st) {
                                                : cudaEventRecord(e, st);
 }
 
-// Untuned choice: lockstep pays two grid barriers per step but keeps the whole
-// GPU busy when every query is small; teams win once queries are large enough
-// to fill a team each (measured crossover: a few thousand nodes per query).
-constexpr long long kLockstepMeanNodes = 2048;
-
+// Untuned choice: teams of 4 CTAs x 512 threads (measured fastest on the
+// 256-query uneven batch; the autotuner compares every scheme and shape).
 int plan_mode(const gmt_batch* b) {
     if (b->mode != GMT_BATCH_AUTO) return b->mode;
     if (b->tuned_mode != GMT_BATCH_AUTO) return b->tuned_mode;
-    if (b->node_base.empty()) return GMT_BATCH_LOCKSTEP;
-    return b->node_base.back() <= kLockstepMeanNodes * b->q ? GMT_BATCH_LOCKSTEP : GMT_BATCH_TEAMS;
+    return GMT_BATCH_TEAMS;
+}
+
+// Does the batch hold a double-integrator or Dubins query?
+bool pool_all_kinds(const gmt_batch* b) {
+    for (const Group& g : b->groups)
+        if (g.kind != GMT_COST_EUCLID) return true;
+    return false;
+}
+
+// Pool launch shape: (threads, co-resident blocks).
+void pool_shape(const gmt_batch* b, int* threads, int* blocks) {
+    int t = b->threads > 0 ? b->threads : (b->tuned_threads > 0 ? b->tuned_threads : 256);
+    if (t > 256) t = 256;
+    *threads = t;
+    *blocks = plan_pool_max_blocks(t, pool_all_kinds(b));
 }
 
 // Lockstep launch shape for a group: (threads, co-resident blocks).
@@ -461,14 +475,27 @@ void lock_shape(const gmt_batch* b, const Group& g, int* threads, int* blocks) {
     *blocks = plan_lockstep_max_blocks(g.kind, g.dp, t);
 }
 
-// Plan-stage launch shape for a group: (cluster, threads, teams).
-void plan_shape(const gmt_batch* b, const Group& g, int* cluster, int* threads, int* teams) {
-    int c = b->cluster > 0 ? b->cluster : (b->tuned_cluster > 0 ? b->tuned_cluster : 2);
+// Dynamic shared memory of the batched team kernel: the most any query asks
+// for (its staged boxes, or the parent copy of its path walk).
+size_t batch_smem(const gmt_batch* b) {
+    size_t smem = 16;
+    for (int k = 0; k < b->q; ++k) {
+        const int dp = b->queries[k].space.pos_dim, nb = b->queries[k].boxes.count;
+        smem = std::max(smem, plan_smem_bytes(nb <= smem_box_cap(dp) ? nb : 0, dp, b->N[k]));
+    }
+    return smem;
+}
+
+// Plan-stage launch shape of the teams scheme: (cluster, threads, teams).
+void plan_shape(const gmt_batch* b, int* cluster, int* threads, int* teams) {
+    int c = b->cluster > 0 ? b->cluster : (b->tuned_cluster > 0 ? b->tuned_cluster : 4);
     int t = b->threads > 0 ? b->threads : (b->tuned_threads > 0 ? b->tuned_threads : 512);
-    int n = plan_batch_max_teams(g.kind, g.dp, t, c);
+    const size_t smem = batch_smem(b);
+    const bool all = pool_all_kinds(b);
+    int n = plan_batch_max_teams(t, c, smem, all);
     while (n <= 0 && c > 1) {
         c /= 2;
-        n = plan_batch_max_teams(g.kind, g.dp, t, c);
+        n = plan_batch_max_teams(t, c, smem, all);
     }
     *cluster = c;
     *threads = t;
@@ -515,6 +542,19 @@ gmt_status enqueue_build_back(gmt_batch* b, int32_t* parent, float* cost, cudaSt
     for (cudaEvent_t& e : b->ev_plan)
         if (!e) BCUDA(cudaEventCreate(&e), "event");
     BCUDA(record_plan_event(b->ev_plan[0], st), "event");
+    if (plan_mode(b) == GMT_BATCH_POOL) {
+        int threads, blocks;
+        pool_shape(b, &threads, &blocks);
+        if (blocks <= 0) return bfail(GMT_ERR_CUDA, "pool plan kernel cannot be resident");
+        BCUDA(cudaMemsetAsync(b->p_ctl.p, 0, sizeof(PoolCtl), st), "memset");
+        BCUDA(launch_plan_pool(b->p_args.as<PlanArgs>(), b->p_order.as<int>(), b->p_ecum.as<long long>(), b->q,
+                               b->p_q.as<PoolQ>(), b->p_ctl.as<PoolCtl>(), pool_all_kinds(b), blocks, threads, st),
+              "pool plan kernel");
+        BCUDA(record_plan_event(b->ev_plan[1], st), "event");
+        BCUDA(cudaMemcpyAsync(b->h_ctl, b->ctl.p, (size_t)b->q * kCtlSlotB, cudaMemcpyDeviceToHost, st),
+              "result copy");
+        return GMT_OK;
+    }
     if (plan_mode(b) == GMT_BATCH_LOCKSTEP) {
         BCUDA(cudaMemsetAsync(b->l_ctl.p, 0, b->l_ctl.cap, st), "memset");
         for (Group& g : b->groups) {
@@ -543,21 +583,19 @@ gmt_status enqueue_build_back(gmt_batch* b, int32_t* parent, float* cost, cudaSt
         return GMT_OK;
     }
     BCUDA(cudaMemsetAsync(b->next.p, 0, b->next.cap, st), "memset");
-    int gi = 0;
-    for (Group& g : b->groups) {
+    {
         int cluster, threads, teams;
-        plan_shape(b, g, &cluster, &threads, &teams);
+        plan_shape(b, &cluster, &threads, &teams);
         if (teams <= 0) return bfail(GMT_ERR_CUDA, "batched plan kernel cannot be resident");
+        if ((size_t)teams > b->slot.cap / 4) return bfail(GMT_ERR_CUDA, "batched plan scratch is too small");
         BatchScratch sc;
         sc.ocost = b->s_ocost.as<float>();
         sc.stamp = b->s_stamp.as<int>();
         sc.lists = b->s_lists.as<int>();
-        sc.max_nodes = g.max_n;
-        BCUDA(launch_plan_batch(g.kind, g.dp, g.args.as<PlanArgs>(), g.order.as<int>(), (int)g.members.size(),
-                                b->next.as<int>() + gi, b->slot.as<int>(), sc, teams, threads, cluster, g.max_boxes,
-                                st),
+        sc.max_nodes = b->max_n;
+        BCUDA(launch_plan_batch(b->p_args.as<PlanArgs>(), b->p_order.as<int>(), b->q, b->next.as<int>(),
+                                b->slot.as<int>(), sc, teams, threads, cluster, batch_smem(b), pool_all_kinds(b), st),
               "batched plan kernel");
-        ++gi;
     }
     BCUDA(record_plan_event(b->ev_plan[1], st), "event");
     (void)parent;
@@ -842,6 +880,52 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         BCUDA(cudaStreamSynchronize(st), "upload");
         max_n = std::max(max_n, g.max_n);
     }
+    // pool scheme: every query with its own scratch (two snapshot buffers,
+    // stamps, lists), all queries in one launch, largest edge count first
+    {
+        std::vector<PlanArgs> all(q);
+        for (Group& g : b->groups) {
+            std::vector<PlanArgs> pa(g.members.size());
+            BCUDA(cudaMemcpyAsync(pa.data(), g.args.p, pa.size() * sizeof(PlanArgs), cudaMemcpyDeviceToHost, st),
+                  "download");
+            BCUDA(cudaStreamSynchronize(st), "download");
+            for (size_t i = 0; i < pa.size(); ++i) all[g.members[i]] = pa[i];
+        }
+        size_t words = 0;
+        std::vector<size_t> so(q);
+        for (int k = 0; k < q; ++k) {
+            so[k] = words;
+            const size_t N = (size_t)b->N[k];
+            words += (3 * N + plan_list_stride(N) + 3) / 4 * 4;  // 16-byte aligned slices
+        }
+        BCUDA(b->p_scratch.need(words * 4 + 16), "pool scratch");
+        for (int k = 0; k < q; ++k) {
+            const size_t N = (size_t)b->N[k];
+            int* base = b->p_scratch.as<int>() + so[k];
+            PlanArgs& a = all[k];
+            a.ocost = (float*)base;
+            a.stamp = base + 2 * N;
+            assign_plan_lists(a, base + (3 * N + 3) / 4 * 4, N);
+        }
+        std::vector<int> order(q);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->E[x] > b->E[y]; });
+        std::vector<long long> ecum(q + 1, 0);
+        for (int i = 0; i < q; ++i) ecum[i + 1] = ecum[i] + std::max<long long>(b->E[order[i]], 1);
+        BCUDA(b->p_args.need((size_t)q * sizeof(PlanArgs)), "pool arguments");
+        BCUDA(b->p_order.need((size_t)q * sizeof(int)), "pool arguments");
+        BCUDA(b->p_ecum.need((size_t)(q + 1) * sizeof(long long)), "pool arguments");
+        BCUDA(b->p_q.need((size_t)q * sizeof(PoolQ)), "pool arguments");
+        BCUDA(b->p_ctl.need(sizeof(PoolCtl)), "pool arguments");
+        BCUDA(cudaMemcpyAsync(b->p_args.p, all.data(), (size_t)q * sizeof(PlanArgs), cudaMemcpyHostToDevice, st),
+              "upload");
+        BCUDA(cudaMemcpyAsync(b->p_order.p, order.data(), (size_t)q * sizeof(int), cudaMemcpyHostToDevice, st),
+              "upload");
+        BCUDA(cudaMemcpyAsync(b->p_ecum.p, ecum.data(), (size_t)(q + 1) * sizeof(long long), cudaMemcpyHostToDevice,
+                              st),
+              "upload");
+        BCUDA(cudaStreamSynchronize(st), "upload");
+    }
     // lockstep chunks: up to kLockMaxQueries members per launch
     size_t lock_nodes = 1;
     int chunks = 0;
@@ -877,12 +961,16 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
     b->lock_chunks = chunks;
     // scratch for the most teams any shape can run
     int max_teams = 0;
-    for (Group& g : b->groups)
+    b->max_n = max_n;
+    {
+        const size_t smem = batch_smem(b);
+        const bool all = pool_all_kinds(b);
         for (int c : {1, 2, 4, 8, 16})
-            for (int t : {256, 512, 1024}) max_teams = std::max(max_teams, plan_batch_max_teams(g.kind, g.dp, t, c));
+            for (int t : {256, 512, 1024}) max_teams = std::max(max_teams, plan_batch_max_teams(t, c, smem, all));
+    }
     cudaGetLastError();
     if (max_teams <= 0) return bfail(GMT_ERR_CUDA, "batched plan kernel cannot be resident");
-    BCUDA(b->s_ocost.need((size_t)max_teams * max_n * 4), "scratch");
+    BCUDA(b->s_ocost.need((size_t)max_teams * 2 * max_n * 4), "scratch");
     BCUDA(b->s_stamp.need((size_t)max_teams * max_n * 4), "scratch");
     BCUDA(b->s_lists.need((size_t)max_teams * plan_list_stride(max_n) * 4), "scratch");
     BCUDA(b->slot.need((size_t)max_teams * 4), "scratch");
@@ -969,8 +1057,9 @@ gmt_status gmt_batch_get_view(const gmt_batch* b, int32_t k, gmt_graph_view* v, 
 
 gmt_status gmt_batch_set_mode(gmt_batch* b, int32_t mode) {
     if (!b) return bfail(GMT_ERR_INVALID, "batch is NULL");
-    if (mode != GMT_BATCH_AUTO && mode != GMT_BATCH_TEAMS && mode != GMT_BATCH_LOCKSTEP)
-        return bfail(GMT_ERR_INVALID, "mode must be GMT_BATCH_AUTO, GMT_BATCH_TEAMS or GMT_BATCH_LOCKSTEP");
+    if (mode != GMT_BATCH_AUTO && mode != GMT_BATCH_TEAMS && mode != GMT_BATCH_LOCKSTEP && mode != GMT_BATCH_POOL)
+        return bfail(GMT_ERR_INVALID,
+                     "mode must be GMT_BATCH_AUTO, GMT_BATCH_TEAMS, GMT_BATCH_LOCKSTEP or GMT_BATCH_POOL");
     b->mode = mode;
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -994,11 +1083,14 @@ gmt_status gmt_batch_get_launch(const gmt_batch* b, int32_t* mode, int32_t* clus
     if (!b) return bfail(GMT_ERR_INVALID, "batch is NULL");
     const int m = plan_mode(b);
     int c = 0, t = 0;
-    if (m == GMT_BATCH_LOCKSTEP) {
+    if (m == GMT_BATCH_POOL) {
+        int blocks = 0;
+        pool_shape(b, &t, &blocks);
+    } else if (m == GMT_BATCH_LOCKSTEP) {
         t = b->threads > 0 ? b->threads : (b->tuned_threads > 0 ? b->tuned_threads : 512);
     } else {
-        c = b->cluster > 0 ? b->cluster : (b->tuned_cluster > 0 ? b->tuned_cluster : 2);
-        t = b->threads > 0 ? b->threads : (b->tuned_threads > 0 ? b->tuned_threads : 512);
+        int teams = 0;
+        plan_shape(b, &c, &t, &teams);
     }
     if (mode) *mode = m;
     if (cluster) *cluster = c;
@@ -1018,6 +1110,7 @@ gmt_status gmt_batch_autotune(gmt_batch* b, gmt_stream stream, int32_t* best_clu
     int bm = GMT_BATCH_AUTO, bc = 0, bt = 0;
     struct Shape { int mode, cluster, threads; };
     std::vector<Shape> shapes;
+    for (int t : {128, 256}) shapes.push_back({GMT_BATCH_POOL, 0, t});
     for (int t : {256, 512, 1024}) shapes.push_back({GMT_BATCH_LOCKSTEP, 0, t});
     for (int c : {1, 2, 4, 8, 16})
         for (int t : {256, 512, 1024}) shapes.push_back({GMT_BATCH_TEAMS, c, t});
@@ -1027,14 +1120,20 @@ gmt_status gmt_batch_autotune(gmt_batch* b, gmt_stream stream, int32_t* best_clu
         b->cluster = sh.cluster;
         b->threads = sh.threads;
         bool ok = true;
+        if (sh.mode == GMT_BATCH_POOL) {
+            int tt, blocks;
+            pool_shape(b, &tt, &blocks);
+            if (blocks <= 0) ok = false;
+        }
         for (Group& g : b->groups) {
+            if (sh.mode == GMT_BATCH_POOL) break;
             if (sh.mode == GMT_BATCH_LOCKSTEP) {
                 int tt, blocks;
                 lock_shape(b, g, &tt, &blocks);
                 if (blocks <= 0) ok = false;
             } else {
                 int cc, tt, teams;
-                plan_shape(b, g, &cc, &tt, &teams);
+                plan_shape(b, &cc, &tt, &teams);
                 if (cc != sh.cluster || teams <= 0) ok = false;
             }
         }

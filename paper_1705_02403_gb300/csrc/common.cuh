@@ -332,6 +332,7 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ void st_volatile_i(int* p, int v) { *(volatile int*)p = v; }
 
 // Warp-aggregated append: every lane with `want` gets a distinct slot of
 // list[*count], one atomic per warp.  Returns the slot (or -1).

@@ -186,6 +186,18 @@ struct PlanCtl {
     unsigned long long goal_key;
     unsigned long long push_edges, pull_edges, checks, failed, tree_size;
     unsigned long long checks_computed;  // checks not answered by the verdict cache
+    // The one-barrier wavefront (plan_fused.cuh) keeps its per-iteration
+    // counters in three sets (iteration i uses set i % 3): group entries (low
+    // half) and kept entries (high half), nodes opened, minimum kept and
+    // opened cost (as bits), group held a goal node.
+    unsigned long long gk3[3];
+    int new3[3];
+    unsigned min_keep3[3], min_new3[3];
+    int goal3[3];
+    // ... and its candidate queue, by parity: cand_count[j] reserves entries,
+    // ticket[j] deals them out, pushed[j] counts the warps done pushing.
+    int ticket[2];
+    unsigned pushed[2];
 };
 
 struct PlanArgs {
@@ -243,9 +255,21 @@ __host__ __device__ inline void assign_plan_lists(PlanArgs& a, int* base, size_t
     a.list_cand = base + 6 * M;
 }
 
+// Largest box count staged in shared memory (2 * count * DP floats).
+__host__ __device__ constexpr int smem_box_cap(int dp) { return 4096 / dp; }
+// Dynamic shared memory of a plan launch: the staged boxes, or, when it is
+// larger and within 48 KB, the parent array of N nodes (read for the path
+// walk once the wavefront is over).
+inline size_t plan_smem_bytes(int staged_boxes, int dp, int N) {
+    const size_t boxes = (size_t)2 * staged_boxes * dp * sizeof(float);
+    const size_t parents = (size_t)N * sizeof(int);
+    return parents <= 48 * 1024 && parents > boxes ? parents : boxes;
+}
+
 // Per-team scratch of the batched wavefront: team t uses the slices
-// [t * max_nodes, (t+1) * max_nodes) of ocost and stamp and
-// [t * kPlanListInts max_nodes, (t+1) * kPlanListInts max_nodes) of lists.
+// [2 t max_nodes, 2 (t+1) max_nodes) of ocost (two snapshot buffers),
+// [t max_nodes, (t+1) max_nodes) of stamp and
+// [t plan_list_stride(max_nodes), (t+1) plan_list_stride(max_nodes)) of lists.
 struct BatchScratch {
     float* ocost;
     int* stamp;
@@ -281,6 +305,44 @@ struct LockScratch {
     int nodes;        // base[nq]
 };
 
+// Pool scheme of the batched wavefront (plan_pool.cu): per-query scheduling
+// state.  The claim word packs the current stage, its item count and the
+// items claimed; done counts the stage's completed items.  The iteration
+// fields are written before the stage that reads them is published.  A
+// query's PlanArgs.ocost holds 2 N floats (the two snapshot buffers).
+struct PoolIter {
+    int it;        // iterations begun (the parity of the current one is it & 1)
+    int ncur;      // entries of the open list
+    int nk;        // of those, kept entries at its front (the rest at its back)
+    int ng_prev;   // nodes of the previous group
+    float theta;   // group threshold of this iteration
+    int ng;        // nodes of this iteration's group (PUSH stage)
+    long long i;   // threshold index
+    int nc;        // candidates of this iteration (PULL stage)
+    int pad;
+};
+struct __align__(64) PoolQ {
+    unsigned long long word;
+    int done;
+    int live;
+    PoolIter iter;
+};
+static_assert(sizeof(PoolQ) == 64, "one PoolQ per 64-byte line");
+struct PoolCtl {
+    int finished;  // queries done
+    int error;     // GMT_ERR_TIMEOUT if a bounded wait ran out
+};
+// Runs the queries args[order[0 .. nq)] (largest first) in one persistent
+// launch of `blocks` x `threads` (after a per-query initialisation launch).
+// ecum: nq + 1 running sums of the queries' edge counts in that order (warps
+// are dealt to queries in proportion); qs: nq entries; pool: zeroed before the
+// call.  all_kinds = false: every query is geometric (a kernel with fewer
+// registers).
+cudaError_t launch_plan_pool(const PlanArgs* args, const int* order, const long long* ecum, int nq, PoolQ* qs,
+                             PoolCtl* pool, bool all_kinds, int blocks, int threads, cudaStream_t st);
+// Co-resident blocks of the pool kernel with `threads` threads (0 if none).
+int plan_pool_max_blocks(int threads, bool all_kinds);
+
 // mlp.cu: C = A . B^T on the tensor cores (BF16 in, FP32 accumulate);
 // epilogue 0 = FP32 store, 1 = BF16 relu(x + bias), 2 = FP32 x + bias.
 cudaError_t gemm_bf16_tn(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* B, int epilogue,
@@ -304,13 +366,16 @@ void record_error(const char* msg);
 cudaError_t launch_plan(const PlanArgs& a, int blocks, int threads, cudaStream_t st, int cluster = 0);
 int plan_max_coresident_blocks(int kind, int dp, int threads);
 int plan_max_cluster(int kind, int dp, int threads);
-// Persistent batched wavefront over `nq` queries of one (kind, dp) group, taken
-// in the order `order` from the device counter `next` (zeroed by the caller);
-// `slot` holds one int per team.  cluster <= 1: teams are single CTAs.
-cudaError_t launch_plan_batch(int kind, int dp, const PlanArgs* queries, const int* order, int nq, int* next,
-                              int* slot, const BatchScratch& scratch, int teams, int threads, int cluster,
-                              int max_boxes, cudaStream_t st);
-int plan_batch_max_teams(int kind, int dp, int threads, int cluster);
+// Persistent batched wavefront (one barrier per iteration) over the `nq`
+// queries queries[order[0 .. nq)] of any kinds, taken in that order from the
+// device counter `next` (zeroed by the caller); `slot` holds one int per team.
+// cluster <= 1: teams are single CTAs.  smem: dynamic shared memory per CTA
+// (the largest plan_smem_bytes of the queries).  all_kinds = false: every
+// query is geometric (a kernel with fewer registers).
+cudaError_t launch_plan_batch(const PlanArgs* queries, const int* order, int nq, int* next, int* slot,
+                              const BatchScratch& scratch, int teams, int threads, int cluster, size_t smem,
+                              bool all_kinds, cudaStream_t st);
+int plan_batch_max_teams(int threads, int cluster, size_t smem, bool all_kinds);
 // plan_multi.cu: one cooperative grid of `blocks` CTAs advances all `nq`
 // queries of one (kind, dp) group together (nq <= kLockMaxQueries).  The
 // queries' PlanCtl blocks must be zeroed before the launch.

@@ -35,6 +35,7 @@
 // compaction of Section IV.  Counters are double-buffered by parity so that
 // resets need no extra barrier.
 #include "plan_core.cuh"
+#include "plan_fused.cuh"
 
 namespace gmtk {
 
@@ -432,11 +433,12 @@ __global__ void __launch_bounds__(1024, 1) plan_kernel_smem(PlanArgs A, unsigned
 }
 
 // Persistent batched wavefront: every team (a CTA, or a cluster) takes the next
-// query from a device queue (queries ordered by decreasing size), runs the
-// plan body on it with its own scratch slice, and repeats until the queue is
-// empty.  Queries never wait for each other, so teams need no co-scheduling
-// beyond their own CTAs.
-template <class Team, int KIND, int DP>
+// query from a device queue (every query of the batch, of any kind, ordered by
+// decreasing size), runs the one-barrier wavefront on it with its own scratch
+// slice, and repeats until the queue is empty.  Queries never wait for each
+// other, so teams need no co-scheduling beyond their own CTAs.  ALL_KINDS =
+// false: a lean instantiation for batches of geometric queries only.
+template <class Team, bool ALL_KINDS>
 __global__ void __launch_bounds__(1024, 1) plan_batch_kernel(const PlanArgs* __restrict__ queries,
                                                           const int* __restrict__ order, int nq,
                                                           int* __restrict__ next, int* __restrict__ slot,
@@ -450,12 +452,16 @@ __global__ void __launch_bounds__(1024, 1) plan_batch_kernel(const PlanArgs* __r
         if (k >= nq) break;
         PlanArgs A = queries[order[k]];
         const size_t nm = (size_t)scratch.max_nodes;
-        A.ocost = scratch.ocost + team_id * nm;
+        A.ocost = scratch.ocost + team_id * 2 * nm;
         A.stamp = scratch.stamp + team_id * nm;
         assign_plan_lists(A, scratch.lists + team_id * plan_list_stride(nm), nm);
         unsigned dyn_smem;
         asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
-        plan_body<Team, KIND, DP>(A, team, sbox, dyn_smem);
+        if (ALL_KINDS && A.kind == GMT_COST_DI) plan_body_fused<Team, GMT_COST_DI, 3>(A, team, sbox, dyn_smem);
+        else if (ALL_KINDS && A.kind == GMT_COST_DUBINS)
+            plan_body_fused<Team, GMT_COST_DUBINS, 3>(A, team, sbox, dyn_smem);
+        else if (A.dp == 2) plan_body_fused<Team, GMT_COST_EUCLID, 2>(A, team, sbox, dyn_smem);
+        else plan_body_fused<Team, GMT_COST_EUCLID, 3>(A, team, sbox, dyn_smem);
         team.sync(nullptr);
     }
 }
@@ -566,19 +572,20 @@ int plan_max_cluster(int kind, int dp, int threads) {
 }
 
 namespace {
-template <int KIND, int DP>
+template <bool ALL_KINDS>
 cudaError_t plan_batch_t(const PlanArgs* queries, const int* order, int nq, int* next, int* slot,
-                         const BatchScratch& scratch, int teams, int threads, int cluster, int max_boxes,
+                         const BatchScratch& scratch, int teams, int threads, int cluster, size_t smem,
                          cudaStream_t st) {
-    const int nbs = max_boxes <= smem_box_cap(DP) ? max_boxes : 0;
-    const size_t smem = plan_smem_bytes(nbs, DP, scratch.max_nodes);
     if (cluster <= 1) {
-        plan_batch_kernel<BlockTeam, KIND, DP><<<teams, threads, smem, st>>>(queries, order, nq, next, slot,
-                                                                             scratch, BlockTeam{});
+        auto kern = plan_batch_kernel<BlockTeam, ALL_KINDS>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<teams, threads, smem, st>>>(queries, order, nq, next, slot, scratch, BlockTeam{});
         return cudaGetLastError();
     }
-    auto kern = plan_batch_kernel<ClusterTeam, KIND, DP>;
+    auto kern = plan_batch_kernel<ClusterTeam, ALL_KINDS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(teams * cluster);
@@ -595,19 +602,27 @@ cudaError_t plan_batch_t(const PlanArgs* queries, const int* order, int nq, int*
     return cudaLaunchKernelEx(&cfg, kern, queries, order, nq, next, slot, scratch, ClusterTeam{});
 }
 
-template <int KIND, int DP>
-int batch_teams_t(int threads, int cluster) {
+template <bool ALL_KINDS>
+int batch_teams_t(int threads, int cluster, size_t smem) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = plan_smem_bytes(smem_box_cap(DP), DP, 12 * 1024);  // the most a launch asks for
     if (cluster <= 1) {
+        auto kern = plan_batch_kernel<BlockTeam, ALL_KINDS>;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_batch_kernel<BlockTeam, KIND, DP>, threads, smem);
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
         return per_sm * sms;
     }
-    auto kern = plan_batch_kernel<ClusterTeam, KIND, DP>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+    auto kern = plan_batch_kernel<ClusterTeam, ALL_KINDS>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cluster);
     cfg.blockDim = dim3(threads);
@@ -628,31 +643,15 @@ int batch_teams_t(int threads, int cluster) {
 }
 }  // namespace
 
-// The batched path supports the double integrator, the Dubins airplane and
-// 2D/3D geometric queries.
-cudaError_t launch_plan_batch(int kind, int dp, const PlanArgs* queries, const int* order, int nq, int* next,
-                              int* slot, const BatchScratch& scratch, int teams, int threads, int cluster,
-                              int max_boxes, cudaStream_t st) {
-    if (kind == GMT_COST_DI)
-        return plan_batch_t<GMT_COST_DI, 3>(queries, order, nq, next, slot, scratch, teams, threads, cluster, max_boxes, st);
-    if (kind == GMT_COST_DUBINS)
-        return plan_batch_t<GMT_COST_DUBINS, 3>(queries, order, nq, next, slot, scratch, teams, threads, cluster,
-                                                max_boxes, st);
-    if (dp == 2)
-        return plan_batch_t<GMT_COST_EUCLID, 2>(queries, order, nq, next, slot, scratch, teams, threads, cluster,
-                                                max_boxes, st);
-    if (dp == 3)
-        return plan_batch_t<GMT_COST_EUCLID, 3>(queries, order, nq, next, slot, scratch, teams, threads, cluster,
-                                                max_boxes, st);
-    return cudaErrorInvalidValue;
+cudaError_t launch_plan_batch(const PlanArgs* queries, const int* order, int nq, int* next, int* slot,
+                              const BatchScratch& scratch, int teams, int threads, int cluster, size_t smem,
+                              bool all_kinds, cudaStream_t st) {
+    return all_kinds ? plan_batch_t<true>(queries, order, nq, next, slot, scratch, teams, threads, cluster, smem, st)
+                     : plan_batch_t<false>(queries, order, nq, next, slot, scratch, teams, threads, cluster, smem, st);
 }
 
-int plan_batch_max_teams(int kind, int dp, int threads, int cluster) {
-    if (kind == GMT_COST_DI) return batch_teams_t<GMT_COST_DI, 3>(threads, cluster);
-    if (kind == GMT_COST_DUBINS) return batch_teams_t<GMT_COST_DUBINS, 3>(threads, cluster);
-    if (dp == 2) return batch_teams_t<GMT_COST_EUCLID, 2>(threads, cluster);
-    if (dp == 3) return batch_teams_t<GMT_COST_EUCLID, 3>(threads, cluster);
-    return 0;
+int plan_batch_max_teams(int threads, int cluster, size_t smem, bool all_kinds) {
+    return all_kinds ? batch_teams_t<true>(threads, cluster, smem) : batch_teams_t<false>(threads, cluster, smem);
 }
 
 int plan_max_coresident_blocks(int kind, int dp, int threads) {

@@ -318,16 +318,6 @@ __device__ __forceinline__ void lane_parent_min(const int* __restrict__ in_col, 
     *be_out = be;
 }
 
-// Largest box count staged in shared memory (2 * count * DP floats).
-__host__ __device__ constexpr int smem_box_cap(int dp) { return 4096 / dp; }
-// Dynamic shared memory of a plan launch: the staged boxes, or, when it is
-// larger and within 48 KB, the parent array of N nodes (read for the path
-// walk once the wavefront is over).
-inline size_t plan_smem_bytes(int staged_boxes, int dp, int N) {
-    const size_t boxes = (size_t)2 * staged_boxes * dp * sizeof(float);
-    const size_t parents = (size_t)N * sizeof(int);
-    return parents <= 48 * 1024 && parents > boxes ? parents : boxes;
-}
 
 // Shared-memory layout of the single-CTA kernel that keeps the wavefront state
 // on chip (plan_kernel_smem): region0 (boxes / parent copy), the control

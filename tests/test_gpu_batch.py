@@ -3,8 +3,8 @@
 Every query of a mixed batch (2D and 3D geometric, double integrator; uneven
 n, own seeds, own boxes, Theorem 1 radii) must produce the same samples, CSR,
 parents, costs and counters as the oracle on that query alone; a repeated call
-(replayed from the captured CUDA graph) must give the same bits again; both
-plan-stage schemes (teams, lockstep) and every launch shape give the same
+(replayed from the captured CUDA graph) must give the same bits again; every
+plan-stage scheme (pool, teams, lockstep) and every launch shape give the same
 trees.
 """
 import numpy as np
@@ -95,6 +95,23 @@ def test_every_team_shape_gives_the_same_trees(O, shape):
         check_query(O, bp, k, infos)
 
 
+@pytest.mark.parametrize("threads", [128, 256])
+def test_every_pool_shape_gives_the_same_trees(O, threads):
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import BatchPlanner
+    bp = BatchPlanner(mixed_batch(seed=5, q=12))
+    bp.plan()
+    N.gmt_batch_set_mode(bp.batch, N.BATCH_POOL)
+    N.gmt_batch_set_launch(bp.batch, 0, threads)
+    assert N.gmt_batch_get_launch(bp.batch) == (N.BATCH_POOL, 0, threads)
+    for rep in range(3):   # prepared, then replayed twice from the captured graph
+        bp.parent.fill_(-9)
+        bp.cost.fill_(-9.0)
+        infos = bp.plan()
+        for k in range(len(bp.problems)):
+            check_query(O, bp, k, infos)
+
+
 @pytest.mark.parametrize("threads", [256, 512, 1024])
 def test_every_lockstep_shape_gives_the_same_trees(O, threads):
     from paper_1705_02403_gb300 import _native as N
@@ -109,23 +126,23 @@ def test_every_lockstep_shape_gives_the_same_trees(O, threads):
         check_query(O, bp, k, infos)
 
 
-def test_lockstep_and_teams_agree_bit_for_bit(O):
+def test_pool_lockstep_and_teams_agree_bit_for_bit(O):
     from paper_1705_02403_gb300 import _native as N
     from paper_1705_02403_gb300.planner import BatchPlanner
     bp = BatchPlanner(mixed_batch(seed=3, q=16))
-    N_ = N
-    infos_l = bp.plan()
-    assert N_.gmt_batch_get_launch(bp.batch)[0] == N.BATCH_LOCKSTEP   # the untuned default for small queries
+    infos_p = bp.plan()
+    assert N.gmt_batch_get_launch(bp.batch)[0] == N.BATCH_TEAMS   # the untuned default
     for k in range(len(bp.problems)):
-        check_query(O, bp, k, infos_l)
-    p_l, c_l = bp.parent.clone(), bp.cost.clone()
-    N.gmt_batch_set_mode(bp.batch, N.BATCH_TEAMS)
-    bp.parent.fill_(-9)
-    bp.cost.fill_(-9.0)
-    infos_t = bp.plan()
-    assert infos_t == infos_l
-    assert torch.equal(bp.parent, p_l)
-    assert torch.equal(bp.cost.view(torch.int32), c_l.view(torch.int32))
+        check_query(O, bp, k, infos_p)
+    p_p, c_p = bp.parent.clone(), bp.cost.clone()
+    for mode in (N.BATCH_POOL, N.BATCH_LOCKSTEP):
+        N.gmt_batch_set_mode(bp.batch, mode)
+        bp.parent.fill_(-9)
+        bp.cost.fill_(-9.0)
+        infos = bp.plan()
+        assert infos == infos_p
+        assert torch.equal(bp.parent, p_p)
+        assert torch.equal(bp.cost.view(torch.int32), c_p.view(torch.int32))
 
 
 @pytest.mark.parametrize("flags", ["cells", "cells_list", "pairs"])
@@ -164,7 +181,7 @@ def test_halton_queries_in_a_batch(O):
         check_query(O, bp, k, infos)
 
 
-@pytest.mark.parametrize("mode", ["teams", "lockstep"])
+@pytest.mark.parametrize("mode", ["pool", "teams", "lockstep"])
 def test_dubins_queries_in_a_batch(O, mode):
     # Dubins airplane queries (Philox and Halton, 30 to 500 boxes, two turning
     # radii) next to geometric and double-integrator ones, under both plan-stage
@@ -178,7 +195,7 @@ def test_dubins_queries_in_a_batch(O, mode):
            envgen.dubins_forest(34, n=64, r=0.6, trunks=2)]
     bp = BatchPlanner(qs)
     bp.plan()
-    N.gmt_batch_set_mode(bp.batch, N.BATCH_TEAMS if mode == "teams" else N.BATCH_LOCKSTEP)
+    N.gmt_batch_set_mode(bp.batch, {"pool": N.BATCH_POOL, "teams": N.BATCH_TEAMS, "lockstep": N.BATCH_LOCKSTEP}[mode])
     infos = bp.plan()
     for k in range(len(qs)):
         check_query(O, bp, k, infos)
@@ -186,20 +203,27 @@ def test_dubins_queries_in_a_batch(O, mode):
     assert v.turn_radius == np.float32(qs[-1].rho) and v.in_path is not None
 
 
-def test_lockstep_runs_more_than_512_queries_in_chunks(O):
-    # 600 small queries: the lockstep scheme runs them as two launches
+@pytest.mark.parametrize("mode", ["pool", "lockstep"])
+def test_600_small_queries(O, mode):
+    # 600 small queries: the lockstep scheme runs them as two launches, the
+    # pool scheme in one
+    from paper_1705_02403_gb300 import _native as N
     from paper_1705_02403_gb300.planner import BatchPlanner
     qs = envgen.batch_queries(seed=5, q=600, n_min=16, n_max=200)
     bp = BatchPlanner(qs)
+    bp.plan()
+    N.gmt_batch_set_mode(bp.batch, N.BATCH_POOL if mode == "pool" else N.BATCH_LOCKSTEP)
     infos = bp.plan()
     for k in range(len(qs)):
         check_query(O, bp, k, infos)
 
 
-def test_lockstep_candidate_queue_overflow(O):
+@pytest.mark.parametrize("mode", ["pool", "lockstep"])
+def test_nearly_complete_graphs_in_a_batch(O, mode):
     # Nearly complete graphs: x_init alone claims more candidates in its first
-    # iteration than a block's shared-memory queue holds, so the pushing warp
-    # pulls the rest itself.
+    # iteration than a lockstep block's shared-memory queue holds (the pushing
+    # warp pulls the rest itself), and in the pool scheme one group node
+    # produces over a thousand PULL items.
     from paper_1705_02403_gb300 import _native as N
     from paper_1705_02403_gb300.planner import BatchPlanner
     qs = [envgen.geometric(600 + k, d=2, n=1500, nbox=4, r=1.0) for k in range(2)]
@@ -207,14 +231,14 @@ def test_lockstep_candidate_queue_overflow(O):
     qs += envgen.batch_queries(seed=6, q=5, n_min=200, n_max=800)
     bp = BatchPlanner(qs)
     bp.plan()
-    N.gmt_batch_set_mode(bp.batch, N.BATCH_LOCKSTEP)
+    N.gmt_batch_set_mode(bp.batch, N.BATCH_POOL if mode == "pool" else N.BATCH_LOCKSTEP)
     infos = bp.plan()
     for k in range(len(qs)):
         check_query(O, bp, k, infos)
     assert max(bp.view(k)["E"] / qs[k].N for k in range(3)) > 1024
 
 
-@pytest.mark.parametrize("mode", ["lockstep", "teams"])
+@pytest.mark.parametrize("mode", ["lockstep", "teams", "pool"])
 def test_iteration_limit_per_query(O, mode):
     from paper_1705_02403_gb300 import _native as N
     from paper_1705_02403_gb300.planner import BatchPlanner
@@ -224,7 +248,7 @@ def test_iteration_limit_per_query(O, mode):
     for k, m in limits.items():
         bp.queries[k].params.max_iters = m
     bp.plan(allow_errors=True)
-    N.gmt_batch_set_mode(bp.batch, N.BATCH_LOCKSTEP if mode == "lockstep" else N.BATCH_TEAMS)
+    N.gmt_batch_set_mode(bp.batch, {"pool": N.BATCH_POOL, "teams": N.BATCH_TEAMS, "lockstep": N.BATCH_LOCKSTEP}[mode])
     infos = bp.plan(allow_errors=True)
     for k, pb in enumerate(qs):
         X, goal = O.sample(pb)
@@ -247,15 +271,15 @@ def test_autotune_keeps_results(O):
     infos = bp.plan()
     c, t, ms = N.gmt_batch_autotune(bp.batch)
     mode, c2, t2 = N.gmt_batch_get_launch(bp.batch)
-    assert mode in (N.BATCH_TEAMS, N.BATCH_LOCKSTEP) and t2 == t and c2 == c
-    assert (c == 0) == (mode == N.BATCH_LOCKSTEP)
-    assert c in (0, 1, 2, 4, 8, 16) and t in (256, 512, 1024) and ms > 0
+    assert mode in (N.BATCH_TEAMS, N.BATCH_LOCKSTEP, N.BATCH_POOL) and t2 == t and c2 == c
+    assert (c == 0) == (mode in (N.BATCH_LOCKSTEP, N.BATCH_POOL))
+    assert c in (0, 1, 2, 4, 8, 16) and t in (128, 256, 512, 1024) and ms > 0
     infos2 = bp.plan()
     for k in range(len(bp.problems)):
         check_query(O, bp, k, infos2)
 
 
-@pytest.mark.parametrize("mode", ["default", "lockstep"])
+@pytest.mark.parametrize("mode", ["pool", "teams", "lockstep"])
 def test_full_size_batch_sampled_queries(O, mode):
     # The 256-query workload (n up to 16384): every query's tree is checked for
     # the paper's invariants on the GPU result, and a sample of queries, the
@@ -265,9 +289,11 @@ def test_full_size_batch_sampled_queries(O, mode):
     qs = envgen.batch_queries(seed=0, q=256)
     bp = BatchPlanner(qs)
     infos = bp.plan()
-    if mode == "lockstep":
-        N.gmt_batch_set_mode(bp.batch, N.BATCH_LOCKSTEP)
+    if mode != "teams":
+        N.gmt_batch_set_mode(bp.batch, N.BATCH_LOCKSTEP if mode == "lockstep" else N.BATCH_POOL)
         infos = bp.plan()
+    assert N.gmt_batch_get_launch(bp.batch)[0] == {"pool": N.BATCH_POOL, "teams": N.BATCH_TEAMS,
+                                                   "lockstep": N.BATCH_LOCKSTEP}[mode]
     sizes = np.array([pb.n for pb in qs])
     pick = sorted(set([int(np.argmax(sizes)), int(np.argmin(sizes))] + list(range(0, 256, 37))))
     for k in pick:
