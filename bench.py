@@ -17,8 +17,9 @@ the flush is outside the per-step CUDA-event timings.
 Under torchrun (N > 1) each rank plans its own seeds (replicas, no collective
 on the data path); value = edges of all ranks / the slowest rank's time.
 
---impl reference times the CPU oracle (oracle/) as the reference arm on a
-bounded sample of the same workload, on the host cores, single-threaded.
+--impl reference times the CPU oracle (oracle/) as the reference arm: one full
+oracle step (SampleFree, all-pairs CSR, wavefront) per step, on the GPU arm's
+seeds, on one host core.
 """
 from __future__ import annotations
 
@@ -126,65 +127,61 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- oracle
-class OracleProblem:
-    """A problem with its oracle graph built once (untimed setup)."""
-
-    def __init__(self, O, pb):
-        self.pb = pb
-        self.X, self.goal = O.sample(pb)
-        self.g = O.Graph(pb.kind, pb.d, pb.dp, self.X, self.goal, pb.r)
-
-
-def oracle_step(O, prob, rows_per_step):
-    """One bounded oracle sample of a step: SampleFree of all nodes, the
-    neighbour test of `rows_per_step` rows (time scaled to all N rows) and the
-    full wavefront on the full graph.  Returns (seconds for one full step,
-    edges checked)."""
-    pb = prob.pb
+def oracle_step(O, pb):
+    """One full oracle step on one problem, timed: SampleFree, the all-pairs
+    neighbour CSR and the wavefront.  Returns (seconds, edges checked)."""
     t0 = time.perf_counter()
-    O.sample(pb)
-    t1 = time.perf_counter()
-    rows = min(rows_per_step, pb.N)
-    O.count_edges_rows(pb, prob.X, 0, rows)
-    t2 = time.perf_counter()
-    _, _, info = prob.g.plan(pb.box_lo, pb.box_hi, pb.lo[:pb.dp], pb.hi[:pb.dp], pb.lam, pb.seg_spacing,
-                             pb.traj_points)
-    t3 = time.perf_counter()
-    sec = (t1 - t0) + (t2 - t1) * (pb.N / rows) + (t3 - t2)
+    X, goal = O.sample(pb)
+    g = O.Graph(pb.kind, pb.d, pb.dp, X, goal, pb.r)
+    _, _, info = g.plan(pb.box_lo, pb.box_hi, pb.lo[:pb.dp], pb.hi[:pb.dp], pb.lam, pb.seg_spacing, pb.traj_points)
+    sec = time.perf_counter() - t0
     return sec, info["push_edges"] + info["pull_edges"]
 
 
-def cpu_baseline(workload, seeds, rows_per_step):
+def cpu_baseline(workload, seeds):
+    """The oracle, one full step per seed (single thread).  Returns
+    (edges/s, seconds per step)."""
     from oracle import oracle as O
     O.build()
     tot_s, tot_e = 0.0, 0
     for s in seeds:
-        sec, edges = oracle_step(O, OracleProblem(O, make_problem(workload, s)), rows_per_step)
+        sec, edges = oracle_step(O, make_problem(workload, s))
         tot_s += sec
         tot_e += edges
     return tot_e / tot_s, tot_s / len(seeds)
+
+
+def plan_bytes(info, d, N):
+    """Algorithmic bytes of one wavefront: 4 B per pushed out-edge (its column),
+    12 B per scanned in-edge (column, cost, gathered snapshot cost), both end
+    states of every collision check (2 d floats), the open/closed/unexplored and
+    group masks touched once per iteration (5 N / 8 B) and the cost and parent
+    writes (8 B per node)."""
+    return (4 * info["push_edges"] + 12 * info["pull_edges"] + 8 * d * info["checks"] + info["iters"] * 5 * N / 8
+            + 8 * N)
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     cfg = workload_config(args.workload)
-    rows = 64 if args.workload == "di6" else 1025
     from oracle import oracle as O
     O.build()
-    pool = [OracleProblem(O, make_problem(args.workload, args.seed_base + k)) for k in range(3)]
     secs, edges = [], []
-    for k in range(args.warmup + args.steps):
-        sec, e = oracle_step(O, pool[k % len(pool)], rows)
+    # the GPU arm's seeds: warm-up steps first, then one seed per timed step
+    seeds = [args.seed_base + k for k in range(args.warmup + args.steps)]
+    for k, s in enumerate(seeds):
+        sec, e = oracle_step(O, make_problem(args.workload, s))
         if k >= args.warmup:
             secs.append(sec); edges.append(e)
     value = float(np.sum(edges) / np.sum(secs))
-    sample = (f"per step: SampleFree of all nodes, the neighbour test of {rows} rows scaled to all N rows, and "
-              f"the full wavefront; problems cycle over seeds {args.seed_base}..{args.seed_base + 2}")
+    sample = (f"every step one full oracle step (SampleFree, all-pairs neighbour CSR, wavefront) on one problem; "
+              f"seeds {seeds[args.warmup]}..{seeds[-1]} timed, as in the GPU arm; single thread")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": cfg,
+            "data": "synthetic",
+            "config": dict(cfg, seeds=f"{seeds[args.warmup]}..{seeds[-1]} (one seed per step)"),
             "ms_per_plan": {"p50": 1e3 * pct(secs, 50), "p99": 1e3 * pct(secs, 99)},
             "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -328,13 +325,12 @@ def run_gpu(args, rank, world, local_rank):
     except Exception:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    d = pb0.d
-    plan_bytes = [8 * i["push_edges"] + 12 * i["pull_edges"] + 8 * d * i["checks"] + 16 * Nn for i in infos]
+    pbytes = [plan_bytes(i, pb0.d, Nn) for i in infos]
     roof = {"kernel": "plan_kernel (wavefront, Alg. 1)", "bound": "hbm",
-            "achieved": float(np.mean(plan_bytes)) / (kern["plan_ms"] / 1e3) / 1e9,
+            "achieved": float(np.mean(pbytes)) / (kern["plan_ms"] / 1e3) / 1e9,
             "peak": hbm, "unit": "GB/s", "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "traffic": PLAN_KERNEL_DRAM_BYTES.get(args.workload),
-            "algorithmic_bytes_per_launch": float(np.mean(plan_bytes)),
+            "algorithmic_bytes_per_launch": float(np.mean(pbytes)),
             "launch_ms": kern["plan_ms"]}
     roof["frac"] = roof["achieved"] / roof["peak"]
     if dominant != "plan_ms":
@@ -366,30 +362,53 @@ def run_gpu(args, rank, world, local_rank):
         line["batched"] = bench_batched(dev, flush)
         line["serving"] = bench_serving(local_rank)
         line["dubins"] = bench_dubins(dev, flush)
+        line["learned"] = bench_learned()
         line["gpu_launches_extras"] = ("batched: 7 launches per group per batch (replayed CUDA graph); serving: 3 per "
                                        "request; dubins: 7-8 per build, 1 per plan")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        seeds_cpu = [seeds[args.warmup + j] for j in range(3)]
-        rows = 256 if args.workload == "di6" else 1025
-        v, sec = cpu_baseline(args.workload, seeds_cpu, rows)
+        nb = min(args.steps, 8 if args.workload == "di6" else 20)
+        seeds_cpu = [seeds[args.warmup + j] for j in range(nb)]
+        v, sec = cpu_baseline(args.workload, seeds_cpu)
         line["cpu_baseline"] = {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                                "sample": f"3 plans (seeds {seeds_cpu}); per plan: SampleFree, neighbour test of "
-                                          f"{rows} rows scaled to all N rows, full wavefront; "
-                                          f"{1e3 * sec:.0f} ms per full plan"}
+                                "sample": f"the first {nb} timed seeds ({seeds_cpu[0]}..{seeds_cpu[-1]}), one full "
+                                          f"oracle step each (SampleFree, all-pairs CSR, wavefront), measured, not "
+                                          f"scaled; {1e3 * sec:.0f} ms per step"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def bench_batched(dev, flush, reps=5):
+# DRAM bytes (read + write) of one launch of the batched plan kernel on the
+# 256-query batch in its autotuned shape, from the ncu capture summarised in
+# profiles/plan_batch_kernel_uneven_256.md.  None until that kernel is
+# captured again after a change.
+PLAN_BATCH_DRAM_BYTES = None
+
+
+def bench_batched(dev, flush, reps=5, cpu_queries=8):
     """The 256-query uneven batch (2D/3D, n log-uniform in [512, 16384], 5-80
-    boxes, Theorem 1 radii): prepared once, team shape autotuned, then whole
-    batches (sampling + CSR + wavefront) replayed from the captured CUDA graph."""
+    boxes, Theorem 1 radii): prepared once, plan-stage scheme and shape
+    autotuned, then whole batches (sampling + CSR + wavefront) replayed from
+    the captured CUDA graph, L2 flushed before each.  End to end: the boxes of
+    every query are copied from pinned host memory before each batch and
+    every parent and cost array back after it, inside the timed region.  CPU
+    baseline: the oracle's full step on `cpu_queries` of the queries."""
     import torch
     from paper_1705_02403_gb300 import _native as N
     from paper_1705_02403_gb300 import envgen
     from paper_1705_02403_gb300.planner import BatchPlanner
     qs = envgen.batch_queries(seed=0, q=256)
     bp = BatchPlanner(qs, device=dev)
+    # every query's boxes in one device buffer (one host-to-device copy per batch)
+    counts = [pb.nbox * pb.dp for pb in qs]
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    h_lo = torch.as_tensor(np.concatenate([np.ascontiguousarray(pb.box_lo, np.float32).ravel() for pb in qs]))
+    h_hi = torch.as_tensor(np.concatenate([np.ascontiguousarray(pb.box_hi, np.float32).ravel() for pb in qs]))
+    h_lo, h_hi = h_lo.pin_memory(), h_hi.pin_memory()
+    d_lo, d_hi = h_lo.to(dev), h_hi.to(dev)
+    for k in range(len(qs)):
+        if counts[k]:
+            bp.queries[k].boxes.lo = d_lo.data_ptr() + 4 * int(off[k])
+            bp.queries[k].boxes.hi = d_hi.data_ptr() + 4 * int(off[k])
     infos = bp.plan()
     N.gmt_batch_autotune(bp.batch)
     mode, cluster, threads = N.gmt_batch_get_launch(bp.batch)
@@ -407,6 +426,24 @@ def bench_batched(dev, flush, reps=5):
     edges = sum(i["push_edges"] + i["pull_edges"] for i in infos)
     t = float(np.median(ms))
     tp = float(np.median(plan_ms))
+    # end to end: host boxes in, parent and cost arrays out
+    h_parent = torch.empty(bp.parent.numel(), dtype=torch.int32).pin_memory()
+    h_cost = torch.empty(bp.cost.numel(), dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        d_lo.copy_(h_lo, non_blocking=True)
+        d_hi.copy_(h_hi, non_blocking=True)
+        infos_e = bp.plan()
+        h_parent.copy_(bp.parent, non_blocking=True)
+        h_cost.copy_(bp.cost, non_blocking=True)
+        b.record(st)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    assert [i["status"] for i in infos_e] == [i["status"] for i in infos]
+    te = float(np.median(e2e_ms))
     # plan-stage roofline: algorithmic bytes of every query's wavefront (the
     # per-plan formula of the main line) over the plan-stage time
     peaks = {}
@@ -416,18 +453,73 @@ def bench_batched(dev, flush, reps=5):
     except (OSError, ValueError):
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    plan_bytes = sum(8 * i["push_edges"] + 12 * i["pull_edges"] + 8 * pb.d * i["checks"] + 16 * pb.N
-                     for i, pb in zip(infos, qs))
-    achieved = plan_bytes / (tp / 1e3) / 1e9
+    pbytes = sum(plan_bytes(i, pb.d, pb.N) for i, pb in zip(infos, qs))
+    achieved = pbytes / (tp / 1e3) / 1e9
+    # CPU baseline: the oracle's full step (SampleFree, all-pairs CSR,
+    # wavefront) on queries spread over the sizes, single thread
+    from oracle import oracle as O
+    O.build()
+    pick = sorted(range(len(qs)), key=lambda k: qs[k].n)[::max(1, len(qs) // cpu_queries)][:cpu_queries]
+    cpu_s, cpu_e = 0.0, 0
+    for k in pick:
+        pb = qs[k]
+        t0 = time.perf_counter()
+        X, goal = O.sample(pb)
+        g = O.Graph(pb.kind, pb.d, pb.dp, X, goal, np.float32(O.radius_thm1(pb.n, pb.d)))
+        _, _, oi = g.plan(pb.box_lo, pb.box_hi, pb.lo[:pb.dp], pb.hi[:pb.dp], pb.lam, pb.seg_spacing,
+                          pb.traj_points)
+        cpu_s += time.perf_counter() - t0
+        cpu_e += oi["push_edges"] + oi["pull_edges"]
+        assert oi["push_edges"] == infos[k]["push_edges"] and oi["pull_edges"] == infos[k]["pull_edges"]
+    scheme = {N.BATCH_TEAMS: "teams", N.BATCH_LOCKSTEP: "lockstep", N.BATCH_POOL: "pool"}.get(mode, str(mode))
     return {"workload": "256 uneven 2D/3D geometric queries, n log-uniform in [512, 16384], 5-80 boxes",
             "ms_per_batch_p50": t, "plans_per_s": 256 / (t / 1e3), "edges_checked_per_s": edges / (t / 1e3),
             "sum_nodes": int(sum(pb.N for pb in qs)), "edges_checked_per_batch": int(edges),
             "success_rate": float(np.mean([i["status"] == 0 for i in infos])),
             "plan_stage_ms_p50": tp,
-            "autotuned": {"scheme": {N.BATCH_TEAMS: "teams", N.BATCH_LOCKSTEP: "lockstep"}.get(mode, str(mode)),
-                          "cluster": cluster, "threads": threads},
+            "autotuned": {"scheme": scheme, "cluster": cluster, "threads": threads},
+            "gpu_launches_per_batch": "build kernels per (kind, dimension) group, then one plan-stage launch",
             "plan_stage_roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                                    "frac": achieved / hbm, "algorithmic_bytes": plan_bytes, "traffic": None}}
+                                    "frac": achieved / hbm, "algorithmic_bytes": pbytes,
+                                    "traffic": PLAN_BATCH_DRAM_BYTES},
+            "e2e": {"value": edges / (te / 1e3), "unit": "edges/s", "ms_per_batch_p50": te,
+                    "h2d_bytes_per_step": int(h_lo.numel() * 8), "d2h_bytes_per_step": int(bp.parent.numel() * 8)},
+            "cpu_baseline": {"value": cpu_e / cpu_s, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(pick)} of the 256 queries (n {min(qs[k].n for k in pick)}.."
+                                       f"{max(qs[k].n for k in pick)}), one full oracle step each (SampleFree, "
+                                       f"all-pairs CSR, wavefront); {1e3 * cpu_s / len(pick):.0f} ms per query"}}
+
+
+def bench_learned(train_envs=3000, test_envs=200, epochs=20):
+    """The learned proposal against uniform sampling at equal path cost (3D box
+    environments, 30 boxes, Theorem 1 radii): the network is trained on the
+    plain-GMT* solutions (n = 16384) of `train_envs` seeded environments, then
+    every arm plans `test_envs` held-out environments at n in 512 .. 4096; per
+    arm the smallest n within 2% of uniform sampling's mean cost at n = 4096,
+    with its p50 step and plan times."""
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300 import learned
+    t0 = time.time()
+    X, SG, T, kept = learned.generate_dataset([1_000_000 + k for k in range(train_envs)], n=16384, log=None)
+    t_data = time.time() - t0
+    model = N.Model(learned.GRID, learned.HIDDEN, learned.CELLS, 256, seed=7)
+    t1 = time.time()
+    losses = learned.train(model, X, SG, T, epochs=epochs, log=None)
+    t_train = time.time() - t1
+    test = [2_000_000 + k for k in range(test_envs)]
+    Xt, SGt, Tt, _ = learned.generate_dataset(test, n=16384, log=None)
+    held_out = learned.mean_loss(model, Xt, SGt, Tt)
+    ev = learned.evaluate(model, test, log=None)
+    cross = ev["within_2pct_of_reference"]
+    return {"workload": f"3D boxes, {train_envs} training / {test_envs} held-out environments, n in {list(learned.NS)}",
+            "reference": ev["reference"], "within_2pct_of_reference": cross,
+            "cost_vs_reference": {arm: {n: ev[arm][n]["cost_vs_uniform_ref"] for n in ev[arm]}
+                                  for arm in ("uniform", "mixture", "uniform_mixture_radius")},
+            "success": {arm: {n: ev[arm][n]["success"] for n in ev[arm]}
+                        for arm in ("uniform", "mixture", "uniform_mixture_radius")},
+            "training": {"solved_envs": len(kept), "epochs": epochs, "dataset_s": t_data, "train_s": t_train,
+                         "final_loss": losses[-1], "held_out_loss": held_out,
+                         "uniform_cell_loss": float(np.log(learned.CELLS ** 3))}}
 
 
 def bench_dubins(dev, flush, reps=20):

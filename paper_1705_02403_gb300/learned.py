@@ -106,13 +106,43 @@ def mean_loss(model: N.Model, X, SG, T, batch=256):
     return tot / cnt
 
 
-def plan_uniform(pbs):
-    bp = BatchPlanner(pbs)
-    return [(i["status"], i["path_cost"]) for i in bp.plan()]
+def _timed(fn):
+    """Runs fn() (which queues device work on the current stream and returns
+    (info dict, graph)); returns (info, step ms from the first queued kernel to
+    the plan's end, plan-kernel ms)."""
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    info, g = fn()
+    b.record(st)
+    b.synchronize()
+    plan_ms = N.gmt_graph_get_profile(g)["plan_ms"]
+    return info, a.elapsed_time(b), plan_ms, g
+
+
+def plan_uniform(pb: envgen.Problem, graph: N.Graph | None = None):
+    """SampleFree + CSR + wavefront for one environment (single-plan API).
+    Returns ((status, cost), step ms, plan ms, graph)."""
+    space, goal = space_struct(pb), goal_struct(pb)
+    boxes, keep = boxes_on_device(pb)
+    params = params_struct(pb)
+    g = graph if graph is not None else N.Graph()
+    parent = torch.empty(pb.N, dtype=torch.int32, device="cuda")
+    cost = torch.empty(pb.N, dtype=torch.float32, device="cuda")
+
+    def run():
+        N.gmt_build_graph_async(space, boxes, [float(v) for v in pb.x_init], goal, params, g)
+        N.gmt_graph_set_profiling(g, 2)
+        return N.gmt_plan(g, boxes, params, parent.data_ptr(), cost.data_ptr()).as_dict(), g
+
+    info, step_ms, plan_ms, g = _timed(run)
+    return (info["status"], info["path_cost"]), step_ms, plan_ms, g
 
 
 def plan_mixture(model: N.Model, pb: envgen.Problem, graph: N.Graph | None = None):
-    """n/2 uniform (SampleFree) + n/2 learned samples, radius for n/2."""
+    """n/2 uniform (SampleFree) + n/2 learned samples, radius for n/2: the
+    proposal's forward pass and draws, the CSR and the wavefront.  Returns
+    ((status, cost), step ms, plan ms, graph)."""
     n_u = pb.n // 2
     n_l = pb.n - n_u
     r = np.float32(N.gmt_connection_radius(n_u, 3, 0.0, 1.0))
@@ -121,49 +151,80 @@ def plan_mixture(model: N.Model, pb: envgen.Problem, graph: N.Graph | None = Non
     boxes, keep = boxes_on_device(upb)
     params = params_struct(upb)
     samples = torch.empty(3, n_l, dtype=torch.float32, device="cuda")
-    N.gmt_propose(model, space, boxes, upb.x_init, upb.goal_center, n_l, int(pb.seed) ^ 0x5A5A5A5A, samples.data_ptr(),
-                  n_l)
-    g = N.gmt_build_graph_ex(space, boxes, [float(v) for v in upb.x_init], goal, params, samples.data_ptr(), n_l, n_l,
-                             graph)
     Nn = n_u + 1 + n_l
     parent = torch.empty(Nn, dtype=torch.int32, device="cuda")
     cost = torch.empty(Nn, dtype=torch.float32, device="cuda")
-    info = N.gmt_plan(g, boxes, params, parent.data_ptr(), cost.data_ptr()).as_dict()
-    return (info["status"], info["path_cost"]), g
+
+    def run():
+        N.gmt_propose(model, space, boxes, upb.x_init, upb.goal_center, n_l, int(pb.seed) ^ 0x5A5A5A5A,
+                      samples.data_ptr(), n_l)
+        g = N.gmt_build_graph_ex(space, boxes, [float(v) for v in upb.x_init], goal, params, samples.data_ptr(), n_l,
+                                 n_l, graph)
+        N.gmt_graph_set_profiling(g, 2)
+        return N.gmt_plan(g, boxes, params, parent.data_ptr(), cost.data_ptr()).as_dict(), g
+
+    info, step_ms, plan_ms, g = _timed(run)
+    return (info["status"], info["path_cost"]), step_ms, plan_ms, g
 
 
-def evaluate(model: N.Model, seeds, ns=(1024, 2048, 4096), n_ref=4096, log=print):
-    """Mean path cost of uniform and mixture sampling at each n, over the
-    environments every method solves, relative to uniform at n_ref.  The
-    control arm "uniform_mixture_radius" samples uniformly with the mixture's
-    (larger, n/2) radius, which isolates what the learned samples add."""
-    res = {"uniform": {}, "mixture": {}, "uniform_mixture_radius": {}}
+NS = (256, 384, 512, 640, 768, 1024, 1365, 2048, 4096)
+
+
+def evaluate(model: N.Model, seeds, ns=NS, n_ref=4096, log=print):
+    """Mean path cost of three arms at each n, over the environments every arm
+    solves at every n, relative to uniform sampling at n_ref:
+      uniform                 SampleFree with Theorem 1's radius for n;
+      mixture                 n/2 SampleFree + n/2 learned, Theorem 1's radius for n/2;
+      uniform_mixture_radius  SampleFree with the mixture's radius (n/2), which
+                              isolates what the learned samples add.
+    Per arm: the smallest n whose mean cost is within 2% of the reference (and
+    whose success rate is within 2 points of it), with the p50 step and plan
+    times there (CUDA events; the step includes sampling, the proposal's
+    forward pass and draws, and the CSR)."""
+    arms = ("uniform", "mixture", "uniform_mixture_radius")
     per = {}
-    for n in sorted(set(ns) | {n_ref}):
-        per[("uniform", n)] = plan_uniform([env(s, n) for s in seeds])
-    for n in ns:
-        r_half = float(np.float32(N.gmt_connection_radius(n // 2, 3, 0.0, 1.0)))
-        per[("uniform_mixture_radius", n)] = plan_uniform([env(s, n).with_(r=r_half) for s in seeds])
     g = None
-    for n in ns:
-        out = []
-        for s in seeds:
-            r, g = plan_mixture(model, env(s, n), g)
-            out.append(r)
-        per[("mixture", n)] = out
+    for n in sorted(set(ns) | {n_ref}):
+        r_half = float(np.float32(N.gmt_connection_radius(n // 2, 3, 0.0, 1.0)))
+        for arm in arms:
+            if arm != "uniform" and n not in ns:
+                continue
+            out = []
+            for s in seeds:
+                pb = env(s, n)
+                if arm == "mixture":
+                    r, step, plan, g = plan_mixture(model, pb, g)
+                else:
+                    r, step, plan, g = plan_uniform(pb.with_(r=r_half) if arm != "uniform" else pb, g)
+                out.append((r[0], r[1], step, plan))
+            per[(arm, n)] = out
     keys = list(per)
     both = [i for i in range(len(seeds)) if all(per[k][i][0] == 0 for k in keys)]
-    ref = float(np.mean([per[("uniform", n_ref)][i][1] for i in both])) if both else float("nan")
-    for (kind, n), rr in per.items():
-        costs = [rr[i][1] for i in both]
-        res[kind][str(n)] = {"success": float(np.mean([x[0] == 0 for x in rr])),
-                             "mean_cost": float(np.mean(costs)) if costs else None,
-                             "cost_vs_uniform_ref": (float(np.mean(costs)) / ref) if costs else None}
-    res["reference"] = {"n": n_ref, "mean_cost": ref, "environments_compared": len(both)}
-    within = [n for n in ns if res["mixture"][str(n)]["cost_vs_uniform_ref"] is not None
-              and res["mixture"][str(n)]["cost_vs_uniform_ref"] <= 1.02]
-    res["smallest_mixture_n_within_2pct"] = min(within) if within else None
-    res["sample_reduction_at_equal_cost"] = (n_ref / min(within)) if within else None
+    ref_rows = per[("uniform", n_ref)]
+    ref = float(np.mean([ref_rows[i][1] for i in both])) if both else float("nan")
+    ref_success = float(np.mean([x[0] == 0 for x in ref_rows]))
+    res = {arm: {} for arm in arms}
+    for (arm, n), rows in per.items():
+        costs = [rows[i][1] for i in both]
+        res[arm][str(n)] = {"success": float(np.mean([x[0] == 0 for x in rows])),
+                            "mean_cost": float(np.mean(costs)) if costs else None,
+                            "cost_vs_uniform_ref": (float(np.mean(costs)) / ref) if costs else None,
+                            "step_ms_p50": float(np.median([x[2] for x in rows])),
+                            "plan_ms_p50": float(np.median([x[3] for x in rows]))}
+    res["reference"] = {"arm": "uniform", "n": n_ref, "mean_cost": ref, "success": ref_success,
+                        "environments_compared": len(both), "environments": len(seeds),
+                        "step_ms_p50": res["uniform"][str(n_ref)]["step_ms_p50"],
+                        "plan_ms_p50": res["uniform"][str(n_ref)]["plan_ms_p50"]}
+    crossing = {}
+    for arm in arms:
+        ok = [n for n in ns if res[arm][str(n)]["cost_vs_uniform_ref"] is not None
+              and res[arm][str(n)]["cost_vs_uniform_ref"] <= 1.02
+              and res[arm][str(n)]["success"] >= ref_success - 0.02]
+        n0 = min(ok) if ok else None
+        crossing[arm] = {"n": n0, "sample_reduction": (n_ref / n0) if n0 else None,
+                         "step_ms_p50": res[arm][str(n0)]["step_ms_p50"] if n0 else None,
+                         "plan_ms_p50": res[arm][str(n0)]["plan_ms_p50"] if n0 else None}
+    res["within_2pct_of_reference"] = crossing
     if log:
         log(json.dumps(res, indent=1))
     return res

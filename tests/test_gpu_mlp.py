@@ -176,7 +176,7 @@ def test_mixture_graph_appends_learned_samples(O):
     from paper_1705_02403_gb300 import learned
     m = N.Model(G, H, C, 4, seed=6)
     pb = learned.env(21, 600)
-    res, g = learned.plan_mixture(m, pb)
+    res, _, _, g = learned.plan_mixture(m, pb)
     v = N.gmt_graph_get_view(g)
     X = dev(v.X, (3, v.x_pitch), "f4", g)[:, :v.N].cpu().numpy()
     goal = dev(v.is_goal, (v.N,), "u1", g).cpu().numpy()
