@@ -516,7 +516,7 @@ gmt_status gmt_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, const v
  *          GMT_ERR_INVALID.
  *   boxes, params, parent, cost, path, info, stream: as for gmt_plan.
  * The kernel's scratch is one fixed __device__ array inside the library
- * (about 2.4 MB on each GPU that loads it, held until the process exits); no
+ * (about 2.6 MB on each GPU that loads it, held until the process exits); no
  * cudaMalloc, cudaFree or other allocating call is made.  The first call on a
  * device looks up that array's address and the plan kernel's largest resident
  * cluster; make it before any stream capture.  The launch shape is gmt_plan's

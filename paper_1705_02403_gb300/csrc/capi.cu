@@ -399,7 +399,7 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
     g->flags = g->counts;
     g->out_count = g->counts + kFlagInts;
     g->in_count = g->counts + kFlagInts + N;
-    GROW(ocost, N);
+    GROW(ocost, 2 * (size_t)N);  // two open-set snapshot buffers
     GROW(stamp, N);
     GROW(lists, kPlanListInts * N);
     GROW(ctl, 1);

@@ -7,13 +7,17 @@
 //   - warp 0 allocates 128 TMEM columns (the FP32 accumulator: 128 lanes x 128
 //     columns) and frees them at the end;
 //   - one thread of warp 0 is the TMA producer: 64-wide K-blocks of A and B are
-//     loaded with cp.async.bulk.tensor into a 4-stage ring of shared-memory
-//     buffers in the 128-byte-swizzled K-major layout the MMA reads;
+//     loaded with cp.async.bulk.tensor into a ring of STAGES shared-memory
+//     buffers in the 128-byte-swizzled K-major layout the MMA reads (6 for
+//     deep K; 3 for short K, so that two CTAs share an SM and one's epilogue
+//     overlaps the other's loads);
 //   - one thread of warp 1 issues tcgen05.mma (kind::f16, M = 128, N = 128,
 //     K = 16 per instruction, 4 per K-block) and returns each stage to the
 //     producer with tcgen05.commit on the stage's "empty" mbarrier;
 //   - after the last commit, all four warps read their 32 accumulator lanes
-//     with tcgen05.ld (32 columns at a time) and apply the epilogue.
+//     with tcgen05.ld (32 columns at a time) into the ring's shared memory,
+//     which the MMAs no longer read, and each warp then writes its 32 rows
+//     128 bytes at a time (one row segment per warp store) with the epilogue.
 // Every mbarrier wait is bounded: a wait that runs out sets an error flag and
 // the CTA stops issuing work, waits (bounded) for copies it issued, releases
 // its TMEM and returns.
@@ -26,9 +30,17 @@
 
 namespace gmtk {
 
-constexpr int kGemmBM = 128, kGemmBN = 128, kGemmBK = 64, kGemmStages = 4;
+constexpr int kGemmBM = 128, kGemmBN = 128, kGemmBK = 64;
+constexpr int kGemmStagesDeep = 6, kGemmStagesShort = 3;
+// Epilogue staging: each row of the FP32 tile padded to 129 floats, so the 32
+// lanes of a warp (32 rows) write one column in 32 different banks.
+constexpr int kGemmStagePitch = kGemmBN + 1;
 constexpr int kGemmTileBytes = kGemmBM * kGemmBK * 2;  // 16 KB per operand tile
-constexpr int kGemmSmemBytes = 2 * kGemmStages * kGemmTileBytes + 1024 /*align*/ + 256 /*barriers*/;
+__host__ __device__ constexpr int gemm_smem_bytes(int stages) {
+    return 2 * stages * kGemmTileBytes + 1024 /*align*/ + 256 /*barriers*/;
+}
+static_assert(kGemmBM * kGemmStagePitch * 4 <= 2 * kGemmStagesShort * kGemmTileBytes,
+              "the epilogue staging fits the operand ring");
 constexpr long long kGemmSpinLimit = 1ll << 26;
 
 enum GemmEpilogue { kEpiStoreF32 = 0, kEpiBiasReluBF16 = 1, kEpiBiasF32 = 2, kEpiPartialF32 = 3 };
@@ -139,8 +151,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+template <int STAGES>
 __global__ void __launch_bounds__(128, 1) gemm_tn_bf16_kernel(const __grid_constant__ CUtensorMap tmA,
                                                              const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
+    constexpr int kGemmStages = STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = base;
@@ -214,32 +228,32 @@ __global__ void __launch_bounds__(128, 1) gemm_tn_bf16_kernel(const __grid_const
     const bool waited = nkb > 0 && mbar_wait(done, 0, g.error);
     const bool have = __all_sync(0xffffffffu, waited && *(volatile int*)g.error == 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int row = m0 + warp * 32 + lane;
     if (have) {
+        // the warp's 32 accumulator rows into shared memory (row-major, padded) ...
+        float* stage = reinterpret_cast<float*>(base) + warp * 32 * kGemmStagePitch;
         for (int c = 0; c < kGemmBN; c += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            if (row >= g.M) continue;
-            const int col0 = n0 + c;
-            if (g.epilogue == kEpiPartialF32) {
-                float* dst = g.C + (size_t)blockIdx.z * g.M * g.ldc + (size_t)row * g.ldc + col0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (col0 + j < g.N) dst[j] = v[j];
-            } else if (g.epilogue == kEpiBiasReluBF16) {
-                __nv_bfloat16* dst = g.Cb + (size_t)row * g.ldc + col0;
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (col0 + j < g.N) {
-                        const float x = fmaxf(v[j] + (g.bias ? g.bias[col0 + j] : 0.0f), 0.0f);
-                        dst[j] = __float2bfloat16_rn(x);
-                    }
-            } else {
-                float* dst = g.C + (size_t)row * g.ldc + col0;
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (col0 + j < g.N)
-                        dst[j] = v[j] + ((g.epilogue == kEpiBiasF32 && g.bias) ? g.bias[col0 + j] : 0.0f);
+            for (int j = 0; j < 32; ++j) stage[lane * kGemmStagePitch + c + j] = v[j];
+        }
+        __syncwarp();
+        // ... then out, one 32-column row segment per warp store
+        const float* biasp = g.bias;
+        for (int r = 0; r < 32; ++r) {
+            const int row = m0 + warp * 32 + r;
+            if (row >= g.M) break;
+            for (int c = 0; c < kGemmBN; c += 32) {
+                const int col = n0 + c + lane;
+                if (col >= g.N) continue;
+                const float x = stage[r * kGemmStagePitch + c + lane];
+                if (g.epilogue == kEpiPartialF32) {
+                    g.C[(size_t)blockIdx.z * g.M * g.ldc + (size_t)row * g.ldc + col] = x;
+                } else if (g.epilogue == kEpiBiasReluBF16) {
+                    g.Cb[(size_t)row * g.ldc + col] = __float2bfloat16_rn(fmaxf(x + (biasp ? biasp[col] : 0.0f), 0.0f));
+                } else {
+                    g.C[(size_t)row * g.ldc + col] = x + ((g.epilogue == kEpiBiasF32 && biasp) ? biasp[col] : 0.0f);
+                }
             }
         }
     }

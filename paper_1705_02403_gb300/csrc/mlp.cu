@@ -75,8 +75,12 @@ cudaError_t gemm_bf16_tn(int M, int N, int K, const __nv_bfloat16* A, const __nv
     if (M <= 0 || N <= 0 || K <= 0 || K % 8 != 0) return cudaErrorInvalidValue;
     static std::atomic<bool> attr_set{false};  // setting it twice is harmless
     if (!attr_set.load(std::memory_order_relaxed)) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_tn_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kGemmSmemBytes);
+        cudaError_t e = cudaFuncSetAttribute(gemm_tn_bf16_kernel<kGemmStagesDeep>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             gemm_smem_bytes(kGemmStagesDeep));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(gemm_tn_bf16_kernel<kGemmStagesShort>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem_bytes(kGemmStagesShort));
         if (e != cudaSuccess) return e;
         attr_set.store(true, std::memory_order_relaxed);
     }
@@ -93,14 +97,22 @@ cudaError_t gemm_bf16_tn(int M, int N, int K, const __nv_bfloat16* A, const __nv
     std::memset(&g, 0, sizeof(g));
     g.M = M; g.N = N; g.K = K; g.k_blocks_per_split = per; g.error = error; g.bias = bias; g.ldc = ldc;
     dim3 grid((M + kGemmBM - 1) / kGemmBM, (N + kGemmBN - 1) / kGemmBN, splits);
+    // short K: a shallow ring, two CTAs per SM
+    const bool shallow = per <= 2 * kGemmStagesShort;
+    auto launch = [&](const GemmArgs& a) {
+        if (shallow)
+            gemm_tn_bf16_kernel<kGemmStagesShort><<<grid, 128, gemm_smem_bytes(kGemmStagesShort), st>>>(ta, tb, a);
+        else
+            gemm_tn_bf16_kernel<kGemmStagesDeep><<<grid, 128, gemm_smem_bytes(kGemmStagesDeep), st>>>(ta, tb, a);
+    };
     if (splits == 1) {
         g.epilogue = epilogue; g.C = C; g.Cb = Cb;
-        gemm_tn_bf16_kernel<<<grid, 128, kGemmSmemBytes, st>>>(ta, tb, g);
+        launch(g);
         return cudaGetLastError();
     }
     if (!partial) return cudaErrorInvalidValue;
     g.epilogue = kEpiPartialF32; g.C = partial; g.ldc = N;
-    gemm_tn_bf16_kernel<<<grid, 128, kGemmSmemBytes, st>>>(ta, tb, g);
+    launch(g);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long total = (long long)M * N;

@@ -389,12 +389,14 @@ __device__ __forceinline__ void publish_ctl(PlanCtl* dst, const PlanCtl* src, in
         reinterpret_cast<int*>(dst)[t] = __ldcg(reinterpret_cast<const int*>(src) + t);
 }
 
+// One plan on a team that spans several SMs (or one CTA whose state does not
+// fit its shared memory): the one-barrier wavefront (A.ocost holds 2 N floats).
 template <class Team, int KIND, int DP>
 __global__ void __launch_bounds__(1024, 1) plan_kernel(PlanArgs A, Team team) {
     extern __shared__ float sbox[];
     unsigned dyn_smem;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
-    plan_body<Team, KIND, DP>(A, team, sbox, dyn_smem);
+    plan_body_fused<Team, KIND, DP>(A, team, sbox, dyn_smem);
     if (A.host_ctl) {
         team.sync(A.ctl);  // every warp's counters and rank 0's result are in
         if (team.rank() < 32) publish_ctl(A.host_ctl, A.ctl, team.rank());

@@ -10,7 +10,7 @@
 // array of fixed size instead of being allocated.
 //
 //  - Capacity: graphs of at most GMT_STATIC_MAX_NODES nodes; larger ones are
-//    rejected with GMT_ERR_INVALID.  The array takes about 2.4 MB on every GPU
+//    rejected with GMT_ERR_INVALID.  The array takes about 2.6 MB on every GPU
 //    that loads the library, for the life of the process.
 //  - Set-up: the first call on a device looks up the array's device address
 //    (cudaGetSymbolAddress, with that device current) and caches it, together
@@ -39,9 +39,10 @@ namespace {
 constexpr size_t kCtlSlot = 256;
 static_assert(sizeof(PlanCtl) <= kCtlSlot, "control block must fit its slot");
 constexpr size_t kNodes = GMT_STATIC_MAX_NODES;
-// [control block][ocost: kNodes floats][stamp: kNodes ints][lists: kPlanListInts kNodes ints]
+// [control block][ocost: 2 kNodes floats (two snapshot buffers)][stamp: kNodes ints]
+// [lists: kPlanListInts kNodes ints]
 constexpr size_t kScratchBytes =
-    kCtlSlot + kNodes * sizeof(float) + kNodes * sizeof(int) + (size_t)kPlanListInts * kNodes * sizeof(int);
+    kCtlSlot + 2 * kNodes * sizeof(float) + kNodes * sizeof(int) + (size_t)kPlanListInts * kNodes * sizeof(int);
 
 static __device__ __align__(256) unsigned char g_plan_scratch[kScratchBytes];
 
@@ -135,7 +136,7 @@ extern "C" gmt_status gmt_plan_static(const gmt_space* space, const gmt_graph_vi
     const size_t NM = kNodes;
     PlanCtl* ctl = (PlanCtl*)base;
     float* ocost = (float*)(base + kCtlSlot);
-    int* stamp = (int*)(base + kCtlSlot + NM * sizeof(float));
+    int* stamp = (int*)(base + kCtlSlot + 2 * NM * sizeof(float));
     int* lists = stamp + NM;
 
     PlanArgs a;

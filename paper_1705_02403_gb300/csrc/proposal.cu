@@ -14,6 +14,7 @@
 // master weights, BF16 copies refreshed after every step.
 #include <cmath>
 #include <cstdio>
+#include <atomic>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -141,12 +142,24 @@ __global__ void relu_back_kernel(const float* __restrict__ d, int ld, const bf16
 }
 
 // g[c] = sum_b d[b, c] (d BF16 [B, N] or FP32).
-__global__ void colsum_bf16_kernel(const bf16* __restrict__ d, int B, int N, float* __restrict__ g) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
+// Column sums of a BF16 matrix [B][N] in FP32: a block of 32 x 8 threads takes
+// 32 columns, each thread a strided eighth of the rows, then the 8 partial
+// sums are added in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) colsum_bf16_kernel(const bf16* __restrict__ d, int B, int N,
+                                                         float* __restrict__ g) {
+    __shared__ float part[8][33];
+    const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + cx;
     float s = 0.0f;
-    for (int b = 0; b < B; ++b) s += __bfloat162float(d[(size_t)b * N + c]);
-    g[c] = s;
+    if (c < N)
+        for (int b = ry; b < B; b += 8) s += __bfloat162float(d[(size_t)b * N + c]);
+    part[ry][cx] = s;
+    __syncthreads();
+    if (ry == 0 && c < N) {
+        float t = part[0][cx];
+        for (int k = 1; k < 8; ++k) t += part[k][cx];
+        g[c] = t;
+    }
 }
 
 // AdamW (decoupled weight decay) on FP32 master weights; refreshes the BF16 copy.
@@ -179,11 +192,29 @@ __global__ void init_normal_kernel(float* __restrict__ p, long long n, float std
 
 // Normalised histogram over cells^3 of points every `spacing` along a path of
 // sample indices (positions are the first three coordinates), plus eps.
-__global__ void path_hist_kernel(const float* __restrict__ X, int pitch, const int* __restrict__ path, int len,
-                                 int cells, float spacing, float* __restrict__ hist) {
-    // one thread walks the whole path (paths are short); cost grows with length/spacing
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int s = 0; s + 1 < len; ++s) {
+// Path histogram in one block: points every `spacing` along the path (each
+// segment from its start, m = max(1, ceil(L / spacing)) points at t = k/m,
+// then the last node), counted per cell in shared memory (the counts are whole
+// numbers, so the order of the additions does not matter), then
+// normalised: (count + eps) / (total + eps cells^3).
+__global__ void __launch_bounds__(256) path_hist_kernel(const float* __restrict__ X, int pitch,
+                                                        const int* __restrict__ path, int len, int cells,
+                                                        float spacing, float eps, float* __restrict__ hist) {
+    extern __shared__ float h[];
+    __shared__ float red[256];
+    const int n = cells * cells * cells;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = 0.0f;
+    __syncthreads();
+    auto cell_of = [&](const float* x) {
+        int idx = 0;
+        for (int d = 0; d < 3; ++d) {
+            int ci = (int)(x[d] * (float)cells);
+            ci = min(max(ci, 0), cells - 1);
+            idx = idx * cells + ci;
+        }
+        return idx;
+    };
+    for (int s = threadIdx.x; s + 1 < len; s += blockDim.x) {
         const int a = path[s], b = path[s + 1];
         float pa[3], pb[3];
         for (int d = 0; d < 3; ++d) { pa[d] = X[(size_t)d * pitch + a]; pb[d] = X[(size_t)d * pitch + b]; }
@@ -192,37 +223,29 @@ __global__ void path_hist_kernel(const float* __restrict__ X, int pitch, const i
         const int m = max(1, (int)ceilf(L / spacing));
         for (int k = 0; k < m; ++k) {
             const float t = (float)k / (float)m;
-            int idx = 0;
-            for (int d = 0; d < 3; ++d) {
-                const float x = pa[d] + t * (pb[d] - pa[d]);
-                int ci = (int)(x * (float)cells);
-                ci = min(max(ci, 0), cells - 1);
-                idx = idx * cells + ci;
-            }
-            hist[idx] += 1.0f;
+            float x[3];
+            for (int d = 0; d < 3; ++d) x[d] = pa[d] + t * (pb[d] - pa[d]);
+            atomicAdd(&h[cell_of(x)], 1.0f);
         }
     }
-    if (len >= 1) {
+    if (threadIdx.x == 0 && len >= 1) {
         const int e = path[len - 1];
-        int idx = 0;
-        for (int d = 0; d < 3; ++d) {
-            int ci = (int)(X[(size_t)d * pitch + e] * (float)cells);
-            ci = min(max(ci, 0), cells - 1);
-            idx = idx * cells + ci;
-        }
-        hist[idx] += 1.0f;
-    }
-}
-
-__global__ void normalise_kernel(float* __restrict__ h, int n, float eps) {
-    __shared__ float tot;
-    if (threadIdx.x == 0) {
-        float s = 0.0f;
-        for (int i = 0; i < n; ++i) s += h[i];
-        tot = s + eps * (float)n;
+        float x[3];
+        for (int d = 0; d < 3; ++d) x[d] = X[(size_t)d * pitch + e];
+        atomicAdd(&h[cell_of(x)], 1.0f);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = (h[i] + eps) / tot;
+    // total count: whole numbers below 2^24, exact in any order
+    float s = 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += h[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const float tot = red[0] + eps * (float)n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) hist[i] = (h[i] + eps) / tot;
 }
 
 // Draws `count` samples: a cell from the softmax of `logits` (inverse CDF,
@@ -351,12 +374,24 @@ cudaError_t transpose(const bf16* in, int R, int C, bf16* out, cudaStream_t st) 
     return cudaGetLastError();
 }
 
+// Split-K factor: enough K-slices that the CTAs cover the SMs once (each
+// slice at least 4 K-blocks deep).
 int splits_for(int M, int N, int K) {
+    static std::atomic<int> sms_cached{0};
+    int sms = sms_cached.load(std::memory_order_relaxed);
+    if (sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 148;
+        sms_cached.store(sms, std::memory_order_relaxed);
+    }
     const int tiles = ((M + 127) / 128) * ((N + 127) / 128);
     const int kb = (K + 63) / 64;
-    int s = 1;
-    while (tiles * s * 2 <= 148 && s * 2 <= kb / 4) s *= 2;
-    return s;
+    if (tiles >= sms) return 1;
+    int s = sms / tiles;
+    if (s > kb / 4) s = kb / 4;
+    return s < 1 ? 1 : s;
 }
 
 cudaError_t gemm(gmt_model* m, int M, int N, int K, const bf16* A, const bf16* B, int epi, const float* bias,
@@ -393,7 +428,7 @@ gmt_status backward(gmt_model* m, int B, const bf16* X, const float* target, cud
     MCUDA(transpose(m->dlog, B, m->Nc, m->dlogt, st), "transpose");
     MCUDA(transpose(m->Z, B, m->Dz, m->Zt, st), "transpose");
     MCUDA(gemm(m, m->Nc, m->Dz, B, m->dlogt, m->Zt, 0, nullptr, m->gW3, nullptr, st), "dW3 GEMM");
-    colsum_bf16_kernel<<<blocks_for(m->Nc, 256), 256, 0, st>>>(m->dlog, B, m->Nc, m->gb3);
+    colsum_bf16_kernel<<<blocks_for(m->Nc, 32), 256, 0, st>>>(m->dlog, B, m->Nc, m->gb3);
     MCUDA(gemm(m, B, m->Dz, m->Nc, m->dlog, m->W3tb, 0, nullptr, m->dZ, nullptr, st), "dZ GEMM");
     // layer 2
     relu_back_kernel<<<blocks_for((long long)B * m->H, 256), 256, 0, st>>>(m->dZ, m->Dz, m->H2, B, m->H, m->dH2);
@@ -401,7 +436,7 @@ gmt_status backward(gmt_model* m, int B, const bf16* X, const float* target, cud
     MCUDA(transpose(m->dH2, B, m->H, m->dH2t, st), "transpose");
     MCUDA(transpose(m->H1, B, m->H, m->H1t, st), "transpose");
     MCUDA(gemm(m, m->H, m->H, B, m->dH2t, m->H1t, 0, nullptr, m->gW2, nullptr, st), "dW2 GEMM");
-    colsum_bf16_kernel<<<blocks_for(m->H, 256), 256, 0, st>>>(m->dH2, B, m->H, m->gb2);
+    colsum_bf16_kernel<<<blocks_for(m->H, 32), 256, 0, st>>>(m->dH2, B, m->H, m->gb2);
     MCUDA(gemm(m, B, m->H, m->H, m->dH2, m->W2tb, 0, nullptr, m->dH1, nullptr, st), "dH1 GEMM");
     // layer 1
     relu_back_kernel<<<blocks_for((long long)B * m->H, 256), 256, 0, st>>>(m->dH1, m->H, m->H1, B, m->H, m->dH1p);
@@ -409,7 +444,7 @@ gmt_status backward(gmt_model* m, int B, const bf16* X, const float* target, cud
     MCUDA(transpose(m->dH1p, B, m->H, m->dH1pt, st), "transpose");
     MCUDA(transpose(X, B, m->Din, m->Xt, st), "transpose");
     MCUDA(gemm(m, m->H, m->Din, B, m->dH1pt, m->Xt, 0, nullptr, m->gW1, nullptr, st), "dW1 GEMM");
-    colsum_bf16_kernel<<<blocks_for(m->H, 256), 256, 0, st>>>(m->dH1p, B, m->H, m->gb1);
+    colsum_bf16_kernel<<<blocks_for(m->H, 32), 256, 0, st>>>(m->dH1p, B, m->H, m->gb1);
     MCUDA(cudaGetLastError(), "bias gradients");
     return GMT_OK;
 }
@@ -635,10 +670,16 @@ gmt_status gmt_path_histogram(const float* X, int32_t pitch, const int32_t* path
         return mfail(GMT_ERR_INVALID, "bad histogram arguments");
     cudaStream_t st = (cudaStream_t)stream;
     const int n = cells * cells * cells;
-    MCUDA(cudaMemsetAsync(hist, 0, n * sizeof(float), st), "memset");
-    path_hist_kernel<<<1, 32, 0, st>>>(X, pitch, path, len, cells, spacing, hist);
-    normalise_kernel<<<1, 256, 0, st>>>(hist, n, eps);
-    MCUDA(cudaGetLastError(), "histogram kernels");
+    const size_t smem = (size_t)n * sizeof(float);
+    if (smem > 200 * 1024) return mfail(GMT_ERR_INVALID, "cells^3 too large for the histogram kernel");
+    static std::atomic<bool> attr_set{false};
+    if (!attr_set.load(std::memory_order_relaxed)) {
+        MCUDA(cudaFuncSetAttribute(path_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
+              "histogram kernel attribute");
+        attr_set.store(true, std::memory_order_relaxed);
+    }
+    path_hist_kernel<<<1, 256, smem, st>>>(X, pitch, path, len, cells, spacing, eps, hist);
+    MCUDA(cudaGetLastError(), "histogram kernel");
     return GMT_OK;
 }
 

@@ -384,7 +384,7 @@ gmt_status gmt_server_create(const gmt_server_config* cfg, gmt_server** out) {
         auto sl = std::make_unique<Slot>();
         sl->cv = &sv->cv;
         e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaMalloc(&sl->ocost, M * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&sl->ocost, 2 * M * 4);  // two snapshot buffers
         if (e == cudaSuccess) e = cudaMalloc(&sl->stamp, M * 4);
         if (e == cudaSuccess) e = cudaMalloc(&sl->lists, M * kPlanListInts * 4);
         if (e == cudaSuccess) e = cudaMalloc(&sl->ctl, 256);

@@ -14,7 +14,8 @@ def ref(A, B, bias=None):
 
 @pytest.mark.parametrize("M,N,K,splits", [(128, 128, 64, 1), (256, 512, 1024, 1), (130, 70, 200, 1),
                                           (1, 4096, 528, 1), (256, 512, 32768, 16), (512, 4096, 528, 3),
-                                          (300, 200, 4096, 7)])
+                                          (300, 200, 4096, 7), (512, 32768, 256, 1), (1024, 512, 32768, 4),
+                                          (77, 1000, 96, 1)])
 def test_gemm_matches_fp32_reference(M, N, K, splits):
     from paper_1705_02403_gb300 import _native as N_
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N + K)
