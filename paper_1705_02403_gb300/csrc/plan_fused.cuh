@@ -217,12 +217,18 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
             const int t = t0 + nctas * wpc * lane;
             bool in_g = false, keep = false;
             int2 e = make_int2(-1, 0);
+            int row0 = 0, row1 = 0;  // out-row of a group node, loaded while the warp reserves its slots
             if (t < ncur) {
                 e = __ldcg(&cur[t < nk ? t : N - 1 - (t - nk)]);
                 in_g = __int_as_float(e.y) <= theta;
                 keep = !in_g;
-                if (in_g) onext[e.x] = INF;                            // G_i closes
-                else if (t >= nk) onext[e.x] = __int_as_float(e.y);    // opened in i - 1, stays open
+                if (in_g) {
+                    row0 = __ldg(&A.out_row[e.x]);
+                    row1 = __ldg(&A.out_row[e.x + 1]);
+                    onext[e.x] = INF;                                  // G_i closes
+                } else if (t >= nk) {
+                    onext[e.x] = __int_as_float(e.y);                  // opened in i - 1, stays open
+                }
                 if (in_g && A.is_goal[e.x]) ctl->goal3[set] = 1;
             }
             const unsigned mg = __ballot_sync(0xffffffffu, in_g), mkeep = __ballot_sync(0xffffffffu, keep);
@@ -241,8 +247,8 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
             // push each group node of the warp: its unexplored out-neighbours are
             // claimed for this iteration and queued
             for (unsigned gm = mg; gm; gm &= gm - 1) {
-                const int z = __shfl_sync(0xffffffffu, e.x, __ffs(gm) - 1);
-                const int e0 = __ldg(&A.out_row[z]), e1 = __ldg(&A.out_row[z + 1]);
+                const int src = __ffs(gm) - 1;
+                const int e0 = __shfl_sync(0xffffffffu, row0, src), e1 = __shfl_sync(0xffffffffu, row1, src);
                 if (lane == 0) cnt.push += (unsigned long long)(e1 - e0);
                 for (int eb = e0; eb < e1; eb += 4 * 32) {
                     int xs[4];
