@@ -41,7 +41,7 @@ METRIC = "ms/plan p50/p99 & edges checked/s; learned+batched vs plain at equal p
 # ncu captures summarised in profiles/plan_kernel_double_integrator_6d_n4096.md
 # and profiles/plan_kernel_geometric_2d_n1024.md.
 # Set to None whenever plan_kernel changes until it is captured again.
-PLAN_KERNEL_DRAM_BYTES = {"di6": 2223872, "geo2d": None}
+PLAN_KERNEL_DRAM_BYTES = {"di6": 2224128, "geo2d": None}
 
 
 def parse():
@@ -496,7 +496,9 @@ def bench_learned(train_envs=3000, test_envs=200, epochs=20):
     plain-GMT* solutions (n = 16384) of `train_envs` seeded environments, then
     every arm plans `test_envs` held-out environments at n in 512 .. 4096; per
     arm the smallest n within 2% of uniform sampling's mean cost at n = 4096,
-    with its p50 step and plan times."""
+    with its p50 step and plan times; then the mixture in batched form (all
+    held-out environments in one gmt_propose_batch + gmt_plan_batch call per
+    n) against plain uniform sampling at n = 4096, batched and single-plan."""
     from paper_1705_02403_gb300 import _native as N
     from paper_1705_02403_gb300 import learned
     t0 = time.time()
@@ -511,8 +513,17 @@ def bench_learned(train_envs=3000, test_envs=200, epochs=20):
     held_out = learned.mean_loss(model, Xt, SGt, Tt)
     ev = learned.evaluate(model, test, log=None)
     cross = ev["within_2pct_of_reference"]
+    evb = learned.evaluate_batched(model, test, ns=(384, 512, 640, 768, 1024), n_ref=4096,
+                                   plain_step_ms_p50=ev["reference"]["step_ms_p50"], log=None)
     return {"workload": f"3D boxes, {train_envs} training / {test_envs} held-out environments, n in {list(learned.NS)}",
             "reference": ev["reference"], "within_2pct_of_reference": cross,
+            "batched": {"workload": f"all {test_envs} held-out environments as one batch per arm "
+                                    "(gmt_propose_batch + gmt_plan_batch, autotuned, graph-replayed)",
+                        "within_2pct_of_plain": evb["within_2pct_of_plain"],
+                        "plain_batched": evb["plain_batched"],
+                        "plain_single_step_ms_p50": evb["plain_single_step_ms_p50"],
+                        "environments_compared": evb["environments_compared"],
+                        "mixture_batched": evb["mixture_batched"]},
             "cost_vs_reference": {arm: {n: ev[arm][n]["cost_vs_uniform_ref"] for n in ev[arm]}
                                   for arm in ("uniform", "mixture", "uniform_mixture_radius")},
             "success": {arm: {n: ev[arm][n]["success"] for n in ev[arm]}

@@ -266,14 +266,23 @@ typedef struct {
     float x_init[GMT_MAX_DIM];
     gmt_goal goal;
     gmt_params params;           /* r <= 0: Theorem 1 radius for this query's n and dim */
+    /* Optional caller samples appended after the n + 1 SampleFree nodes, as
+     * in gmt_build_graph_ex (nodes n+1 .. n+extra_count; each must lie in X
+     * and outside X_obs, else the call fails with GMT_ERR_INVALID, or, on a
+     * replay, that query's info.status is GMT_ERR_INVALID).  extra: DEVICE
+     * [dim][extra_pitch], read on every call (also on replays), or NULL with
+     * extra_count 0.  The radius stays Theorem 1's for params.n when r <= 0. */
+    const float* extra;
+    int32_t extra_count;
+    int32_t extra_pitch;
 } gmt_query;
 
 typedef struct gmt_batch gmt_batch;
 
 /* Samples, builds the neighbour CSR of, and plans every query.
  *   queries: HOST array [q].
- *   parent, cost: DEVICE outputs of sum_k (n_k + 1) entries; query k's nodes
- *     start at offset sum_{j<k} (n_j + 1).
+ *   parent, cost: DEVICE outputs of sum_k N_k entries, N_k = n_k + 1 +
+ *     extra_count_k; query k's nodes start at offset sum_{j<k} N_j.
  *   infos: HOST output [q].
  *   *batch: NULL to create a handle, or the handle of an earlier call, whose
  *     arena is reused.  If the queries (compared by value, including the box
@@ -486,6 +495,23 @@ gmt_status gmt_path_histogram(const float* X, int32_t pitch, const int32_t* path
 gmt_status gmt_propose(gmt_model* model, const gmt_space* space, const gmt_boxes* boxes, const float* start,
                        const float* goal, int32_t count, uint64_t seed, float* samples, int32_t pitch,
                        gmt_stream stream);
+
+/* gmt_propose for B problems at once: the voxelisation, one forward pass and
+ * one sampling launch (one CTA per problem) per `max_batch` problems, and one
+ * host synchronisation for the whole call.  Problem b draws `count` samples
+ * exactly as gmt_propose would with seed seeds[b], from the logits of a
+ * forward pass over its chunk of problems (the GEMMs' FP32 summation order
+ * may depend on the chunk size, so a sample can differ from a single call's
+ * where a draw lies within rounding of a cell boundary of the CDF).
+ *   spaces, boxes: HOST arrays [B] (box arrays DEVICE, 3D geometric spaces).
+ *   start_goal: HOST FP32 [B][6] (start xyz, goal xyz).
+ *   seeds: HOST [B].
+ *   samples: DEVICE FP32 [B][3][pitch], pitch >= count; problem b's rows
+ *     start at samples + 3 b pitch (the layout gmt_query.extra takes).
+ * Errors: GMT_ERR_INVALID (arguments; a sample exhausted its attempts). */
+gmt_status gmt_propose_batch(gmt_model* model, int32_t B, const gmt_space* spaces, const gmt_boxes* boxes,
+                             const float* start_goal, int32_t count, const uint64_t* seeds, float* samples,
+                             int32_t pitch, gmt_stream stream);
 
 /* ---------------------------------------------------------------- tensor cores
  * BF16 GEMM on the 5th-generation tensor cores (tcgen05, TMEM accumulator,

@@ -84,7 +84,8 @@ class gmt_profile(C.Structure):
 
 class gmt_query(C.Structure):
     _fields_ = [("space", gmt_space), ("boxes", gmt_boxes), ("x_init", C.c_float * GMT_MAX_DIM),
-                ("goal", gmt_goal), ("params", gmt_params)]
+                ("goal", gmt_goal), ("params", gmt_params), ("extra", C.c_void_p), ("extra_count", C.c_int32),
+                ("extra_pitch", C.c_int32)]
 
 
 class gmt_model_config(C.Structure):
@@ -158,6 +159,8 @@ SIGNATURES = {
     "gmt_model_load": (_I32, [_P, C.c_char_p]),
     "gmt_path_histogram": (_I32, [_P, _I32, _P, _I32, _I32, _F32, _F32, _P, _P]),
     "gmt_propose": (_I32, [_P, C.POINTER(gmt_space), C.POINTER(gmt_boxes), _P, _P, _I32, _U64, _P, _I32, _P]),
+    "gmt_propose_batch": (_I32, [_P, _I32, C.POINTER(gmt_space), C.POINTER(gmt_boxes), _P, _I32, _P, _P, _I32,
+                                 _P]),
     "gmt_server_create": (_I32, [C.POINTER(gmt_server_config), C.POINTER(C.c_void_p)]),
     "gmt_server_free": (None, [_P]),
     "gmt_server_open_session": (_I32, [_P, C.POINTER(gmt_space), _P, C.POINTER(gmt_goal), C.POINTER(gmt_params), _I32,
@@ -433,6 +436,18 @@ def gmt_propose(model: Model, space: gmt_space, boxes: gmt_boxes, start, goal, c
     g3 = (C.c_float * 3)(*[float(v) for v in goal[:3]])
     _check(lib.gmt_propose(model.handle, C.byref(space), C.byref(boxes), C.cast(s3, C.c_void_p),
                            C.cast(g3, C.c_void_p), count, seed, C.c_void_p(samples_ptr), pitch, _stream(stream)))
+
+
+def gmt_propose_batch(model: Model, spaces, boxes, start_goal, count, seeds, samples_ptr, pitch, stream=None):
+    """spaces, boxes: sequences of B structs; start_goal: [B][6] floats; seeds:
+    B integers; samples: DEVICE [B][3][pitch]."""
+    B = len(spaces)
+    sp = (gmt_space * B)(*spaces)
+    bx = (gmt_boxes * B)(*boxes)
+    sg = (C.c_float * (6 * B))(*[float(v) for row in start_goal for v in row[:6]])
+    sd = (C.c_uint64 * B)(*[int(v) & 0xFFFFFFFFFFFFFFFF for v in seeds])
+    _check(lib.gmt_propose_batch(model.handle, B, sp, bx, C.cast(sg, C.c_void_p), count, C.cast(sd, C.c_void_p),
+                                 C.c_void_p(samples_ptr), pitch, _stream(stream)))
 
 
 def gmt_build_graph_ex(space, boxes, x_init, goal, params, extra_ptr, extra_count, extra_pitch,

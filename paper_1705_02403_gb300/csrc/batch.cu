@@ -49,6 +49,9 @@ struct QueryDev {
     int* cell_cnt;
     int* cell_start;
     int* cell_info;  // [longest row, a row overflowed the fill's list]
+    // caller samples appended after the n_sampled SampleFree nodes
+    const float* extra;
+    int extra_pitch;
 };
 
 // index k with off[k] <= t < off[k+1] (off has nq+1 entries, off[0] = 0)
@@ -68,9 +71,15 @@ __global__ void __launch_bounds__(128) batch_sample_kernel(const QueryDev* __res
     if (t >= off[nq]) return;
     const int k = find_query(off, nq, t);
     const QueryDev& q = Q[k];
+    const int v = (int)(t - off[k]);
+    if (v >= q.s.n_sampled) {  // an appended sample
+        append_node<D, DP>(q.s, q.boxes, q.extra, q.extra_pitch, q.s.n_sampled, q.X, q.is_goal, q.flags,
+                           v - q.s.n_sampled);
+        return;
+    }
     if (q.s.sampler == GMT_SAMPLER_HALTON) return;  // batch_halton_kernel
     const BoxGridArgs no_grid{};
-    sample_node<D, DP>(q.s, q.boxes, no_grid, q.X, q.is_goal, q.flags, (int)(t - off[k]));
+    sample_node<D, DP>(q.s, q.boxes, no_grid, q.X, q.is_goal, q.flags, v);
 }
 
 // One block per query of the group; queries that sample with Philox return.
@@ -356,7 +365,7 @@ struct gmt_batch {
     int max_n = 0;  // largest N of the batch (team scratch slices)
     cudaEvent_t ev_plan[2] = {nullptr, nullptr};  // around the plan stage of every call
     PlanCtl* h_ctl = nullptr;
-    int* h_rows = nullptr;
+    int* h_rows = nullptr;  // [q] edge counts, then [q] sampling flags
     size_t h_cap = 0;
     // scheme and launch shape of the plan stage
     int mode = GMT_BATCH_AUTO;
@@ -413,6 +422,10 @@ gmt_status check_query(const gmt_query& Qh, int k) {
     if (!(p.seg_spacing > 0.0f) || p.traj_points < 2)
         return bfail(GMT_ERR_INVALID, "seg_spacing must be > 0 and traj_points >= 2" + at);
     if (!(Qh.goal.radius >= 0.0f)) return bfail(GMT_ERR_INVALID, "goal radius must be >= 0" + at);
+    if (Qh.extra_count < 0 || Qh.extra_count > (1 << 24) ||
+        (Qh.extra_count > 0 && (!Qh.extra || Qh.extra_pitch < Qh.extra_count)))
+        return bfail(GMT_ERR_INVALID, "appended samples need a DEVICE array [dim][extra_pitch], "
+                                      "extra_pitch >= extra_count, extra_count in [0, 2^24]" + at);
     return GMT_OK;
 }
 
@@ -538,6 +551,9 @@ gmt_status enqueue_build_back(gmt_batch* b, int32_t* parent, float* cost, cudaSt
             BCUDA(batch_cells_fill(g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, g.cell_words, st),
                   "batched cells");
     }
+    // sampling flags of this call (appended samples are read on replays too)
+    BCUDA(cudaMemcpyAsync(b->h_rows + b->q, b->flags.p, (size_t)b->q * 4, cudaMemcpyDeviceToHost, st),
+          "flag readback");
     BCUDA(cudaMemsetAsync(b->ctl.p, 0, b->ctl.cap, st), "memset");
     for (cudaEvent_t& e : b->ev_plan)
         if (!e) BCUDA(cudaEventCreate(&e), "event");
@@ -638,7 +654,7 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
     b->node_base[0] = 0;
     for (int k = 0; k < q; ++k) {
         const gmt_query& Qh = queries[k];
-        const int N = Qh.params.n + 1;
+        const int N = Qh.params.n + 1 + Qh.extra_count;
         const int P = (N + 31) / 32 * 32, W = (N + 31) / 32;
         b->N[k] = N; b->pitch[k] = P;
         b->node_base[k + 1] = b->node_base[k] + N;
@@ -692,7 +708,7 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         std::memset(&d, 0, sizeof(d));
         SpaceArgs& s = d.s;
         s.kind = Qh.space.kind; s.d = Qh.space.dim; s.dp = Qh.space.pos_dim; s.N = b->N[k]; s.pitch = b->pitch[k];
-        s.n_sampled = s.N;
+        s.n_sampled = Qh.params.n + 1;
         for (int a = 0; a < s.d; ++a) {
             s.lo[a] = Qh.space.lo[a]; s.hi[a] = Qh.space.hi[a];
             s.x0[a] = Qh.x_init[a]; s.gc[a] = Qh.goal.center[a];
@@ -704,11 +720,13 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         s.stream = 0;
         s.max_attempts = Qh.params.max_attempts > 0 ? Qh.params.max_attempts : 65536;
         s.sampler = Qh.params.sampler;
-        s.halton_cap = (long long)s.max_attempts + 64LL * s.N;
+        s.halton_cap = (long long)s.max_attempts + 64LL * s.n_sampled;
         s.r = b->r[k];
         s.r2_threshold = euclid_threshold_b(s.r);
         s.rho = s.kind == GMT_COST_DUBINS ? Qh.params.turn_radius : 0.0f;
         d.boxes = BoxArgs{Qh.boxes.count, Qh.boxes.lo, Qh.boxes.hi};
+        d.extra = Qh.extra_count > 0 ? Qh.extra : nullptr;
+        d.extra_pitch = Qh.extra_pitch;
         d.X = b->X.as<float>() + xo[k];
         d.is_goal = b->goal.as<uint8_t>() + go[k];
         d.flags = b->flags.as<int>() + k;
@@ -801,6 +819,9 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
             return bfail(GMT_ERR_INVALID, "x_init outside X or in an obstacle (query " + std::to_string(k) + ")");
         if (flags[k] & kSampleExhausted)
             return bfail(GMT_ERR_INVALID, "sampling exhausted max_attempts (query " + std::to_string(k) + ")");
+        if (flags[k] & kSampleBadAppend)
+            return bfail(GMT_ERR_INVALID,
+                         "an appended sample is outside X or in X_obs (query " + std::to_string(k) + ")");
     }
     // edge slices: ints (columns) and floats; a Dubins query's float slice
     // starts with its in-edge words (4 floats each), kept 16-byte aligned
@@ -993,7 +1014,8 @@ gmt_status finish(gmt_batch* b, gmt_plan_info* infos, cudaStream_t st) {
     for (int k = 0; k < b->q; ++k) {
         const PlanCtl& c = *(const PlanCtl*)((const unsigned char*)b->h_ctl + (size_t)k * kCtlSlotB);
         info_from_ctl(c, &infos[k]);
-        if (c.status < 0 && worst == GMT_OK) worst = (gmt_status)c.status;
+        if (b->h_rows[b->q + k] & kSampleBadAppend) infos[k].status = GMT_ERR_INVALID;
+        if (infos[k].status < 0 && worst == GMT_OK) worst = (gmt_status)infos[k].status;
     }
     if (worst != GMT_OK) return bfail(worst, "at least one query failed (see its info.status)");
     return GMT_OK;

@@ -248,44 +248,88 @@ __global__ void __launch_bounds__(256) path_hist_kernel(const float* __restrict_
     for (int i = threadIdx.x; i < n; i += blockDim.x) hist[i] = (h[i] + eps) / tot;
 }
 
-// Draws `count` samples: a cell from the softmax of `logits` (inverse CDF,
-// Philox counter (k, attempt, 2, 0)), a uniform point inside it (same draw),
-// rejected if it lies in a box; velocity-free 3D positions.
+// One environment of a proposal launch: its obstacle boxes, position bounds,
+// Philox key and output rows (3 x pitch floats).
+struct ProposalEnv {
+    int box_count;
+    const float* box_lo;
+    const float* box_hi;
+    float lo[3], hi[3];
+    uint32_t k0, k1;
+    float* out;
+};
+
+// One block per environment (blockIdx.x; its logits are row blockIdx.x of
+// `logits`).  Draws `count` samples: a cell from the softmax of the logits
+// (inverse CDF, Philox counter (k, attempt, 2, 0)), a uniform point inside it
+// (same draw), rejected while it lies in a box; velocity-free 3D positions.
+// The CDF is a block-wide scan: each thread sums a contiguous run of cells,
+// the run totals are scanned across warps, and each thread writes its run's
+// running sums from its offset.
 __global__ void __launch_bounds__(1024) proposal_sample_kernel(const float* __restrict__ logits, int Nc, int cells,
-                                                               BoxArgs boxes, const float* lo, const float* hi,
-                                                               int count, uint32_t k0, uint32_t k1, int max_attempts,
-                                                               float* __restrict__ out, int pitch,
+                                                               const ProposalEnv* __restrict__ envs, int count,
+                                                               int max_attempts, int pitch,
                                                                int* __restrict__ flags) {
     extern __shared__ float cdf[];
     __shared__ float red[32];
     __shared__ float blo[3], bhi[3];
-    if (threadIdx.x < 3) { blo[threadIdx.x] = lo[threadIdx.x]; bhi[threadIdx.x] = hi[threadIdx.x]; }
+    const ProposalEnv& E = envs[blockIdx.x];
+    const float* lg = logits + (size_t)blockIdx.x * Nc;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    if (threadIdx.x < 3) { blo[threadIdx.x] = E.lo[threadIdx.x]; bhi[threadIdx.x] = E.hi[threadIdx.x]; }
     float mx = -INFINITY;
-    for (int c = threadIdx.x; c < Nc; c += blockDim.x) mx = fmaxf(mx, logits[c]);
+    for (int c = threadIdx.x; c < Nc; c += blockDim.x) mx = fmaxf(mx, lg[c]);
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    if (lane == 0) red[wid] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
         float v = -INFINITY;
-        for (int w = 0; w < (int)(blockDim.x / 32); ++w) v = fmaxf(v, red[w]);
+        for (int w = 0; w < nw; ++w) v = fmaxf(v, red[w]);
         red[0] = v;
     }
     __syncthreads();
     mx = red[0];
-    for (int c = threadIdx.x; c < Nc; c += blockDim.x) cdf[c] = expf(logits[c] - mx);
+    __syncthreads();  // red is reused by the scan
+    // this thread's run of cells [c0, c1)
+    const int per = (Nc + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int c0 = min(Nc, (int)threadIdx.x * per), c1 = min(Nc, c0 + per);
+    float run = 0.0f;
+    for (int c = c0; c < c1; ++c) {
+        const float v = expf(lg[c] - mx);
+        cdf[c] = v;
+        run += v;
+    }
+    float inc = run;  // inclusive scan of the run totals within the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const float t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) red[wid] = inc;
     __syncthreads();
-    if (threadIdx.x == 0) {  // inclusive prefix sum (Nc is small)
-        float s = 0.0f;
-        for (int c = 0; c < Nc; ++c) { s += cdf[c]; cdf[c] = s; }
+    if (wid == 0) {
+        float w = lane < nw ? red[lane] : 0.0f;
+        for (int o = 1; o < 32; o <<= 1) {
+            const float t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < nw) red[lane] = w;
+    }
+    __syncthreads();
+    const float excl = __shfl_up_sync(0xffffffffu, inc, 1);
+    float acc = (wid > 0 ? red[wid - 1] : 0.0f) + (lane > 0 ? excl : 0.0f);
+    for (int c = c0; c < c1; ++c) {
+        acc += cdf[c];
+        cdf[c] = acc;
     }
     __syncthreads();
     const float total = cdf[Nc - 1];
     const float w = 1.0f / (float)cells;
+    const BoxArgs boxes{E.box_count, E.box_lo, E.box_hi};
     for (int k = threadIdx.x; k < count; k += blockDim.x) {
         bool ok = false;
         float p[3] = {0, 0, 0};
         for (int t = 0; t < max_attempts && !ok; ++t) {
-            const Ctr4 r = philox4x32_10(Ctr4{(uint32_t)k, (uint32_t)t, 2u, 0u}, k0, k1);
+            const Ctr4 r = philox4x32_10(Ctr4{(uint32_t)k, (uint32_t)t, 2u, 0u}, E.k0, E.k1);
             const float u = unit_float(r.x) * total;
             int lo_i = 0, hi_i = Nc - 1;
             while (lo_i < hi_i) {
@@ -302,7 +346,7 @@ __global__ void __launch_bounds__(1024) proposal_sample_kernel(const float* __re
             ok = !in_any_box<3>(p, boxes.lo, boxes.hi, boxes.count);
         }
         if (!ok) atomicOr(flags, 1);
-        for (int d = 0; d < 3; ++d) out[(size_t)d * pitch + k] = p[d];
+        for (int d = 0; d < 3; ++d) E.out[(size_t)d * pitch + k] = p[d];
     }
 }
 
@@ -330,7 +374,8 @@ struct gmt_model {
     // proposal scratch
     bf16* pvox = nullptr;
     float* psg = nullptr;
-    EnvBoxes* envs = nullptr;
+    EnvBoxes* envs = nullptr;       // grow-only descriptor arrays of proposal calls
+    ProposalEnv* penv = nullptr;
     int envs_cap = 0;
     std::vector<void*> owned;
 
@@ -342,6 +387,8 @@ struct gmt_model {
     float* grad(int i) { float* p[6] = {gW1, gb1, gW2, gb2, gW3, gb3}; return p[i]; }
     ~gmt_model() {
         for (void* p : owned) cudaFree(p);
+        if (envs) cudaFree(envs);
+        if (penv) cudaFree(penv);
     }
 };
 
@@ -460,9 +507,80 @@ gmt_status check_err(gmt_model* m, cudaStream_t st) {
     return GMT_OK;
 }
 
+// Proposal draws for B environments: descriptors uploaded once, then per
+// chunk of at most maxB environments the voxelisation, one batched forward
+// pass and one sampling launch (one block per environment); one host
+// synchronisation at the end reads the exhausted-attempts flag.
+gmt_status propose_impl(gmt_model* m, int B, const gmt_space* spaces, const gmt_boxes* boxes, const float* sg,
+                        int count, const uint64_t* seeds, float* samples, int pitch, gmt_stream stream) {
+    if (!m || B < 1 || !spaces || !boxes || !sg || !seeds || !samples || count < 1 || pitch < count)
+        return mfail(GMT_ERR_INVALID, "bad proposal arguments");
+    const size_t smem = (size_t)m->Nc * sizeof(float);  // at most 32^3 cells: 128 KB
+    static std::atomic<bool> attr_set{false};
+    if (smem > 48 * 1024 && !attr_set.load(std::memory_order_relaxed)) {
+        MCUDA(cudaFuncSetAttribute(proposal_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   128 * 1024),
+              "proposal kernel attribute");
+        attr_set.store(true, std::memory_order_relaxed);
+    }
+    std::vector<EnvBoxes> eb(B);
+    std::vector<ProposalEnv> pe(B);
+    for (int b = 0; b < B; ++b) {
+        const gmt_space& sp = spaces[b];
+        if (sp.kind != GMT_COST_EUCLID || sp.dim != 3)
+            return mfail(GMT_ERR_INVALID, "the learned proposal supports 3D geometric spaces");
+        if (boxes[b].count < 0 || (boxes[b].count > 0 && (!boxes[b].lo || !boxes[b].hi)))
+            return mfail(GMT_ERR_INVALID, "bad box arrays");
+        eb[b] = EnvBoxes{boxes[b].count, boxes[b].lo, boxes[b].hi};
+        ProposalEnv& e = pe[b];
+        e.box_count = boxes[b].count; e.box_lo = boxes[b].lo; e.box_hi = boxes[b].hi;
+        for (int a = 0; a < 3; ++a) { e.lo[a] = sp.lo[a]; e.hi[a] = sp.hi[a]; }
+        e.k0 = (uint32_t)(seeds[b] & 0xffffffffu);
+        e.k1 = (uint32_t)(seeds[b] >> 32);
+        e.out = samples + (size_t)b * 3 * pitch;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (m->envs_cap < B) {
+        MCUDA(cudaStreamSynchronize(st), "proposal descriptors");  // earlier calls may still read them
+        if (m->envs) cudaFree(m->envs);
+        if (m->penv) cudaFree(m->penv);
+        m->envs = nullptr; m->penv = nullptr; m->envs_cap = 0;
+        MCUDA(cudaMalloc((void**)&m->envs, (size_t)B * sizeof(EnvBoxes)), "proposal descriptors");
+        MCUDA(cudaMalloc((void**)&m->penv, (size_t)B * sizeof(ProposalEnv)), "proposal descriptors");
+        m->envs_cap = B;
+    }
+    MCUDA(cudaMemcpyAsync(m->envs, eb.data(), (size_t)B * sizeof(EnvBoxes), cudaMemcpyHostToDevice, st),
+          "proposal descriptors");
+    MCUDA(cudaMemcpyAsync(m->penv, pe.data(), (size_t)B * sizeof(ProposalEnv), cudaMemcpyHostToDevice, st),
+          "proposal descriptors");
+    const int G3 = m->G * m->G * m->G;
+    for (int b0 = 0; b0 < B; b0 += m->maxB) {
+        const int nb = std::min(m->maxB, B - b0);
+        MCUDA(cudaMemcpyAsync(m->psg, sg + (size_t)b0 * 6, (size_t)nb * 6 * sizeof(float), cudaMemcpyHostToDevice,
+                              st),
+              "start/goal upload");
+        voxelize_kernel<<<dim3(blocks_for(G3, 256), nb), 256, 0, st>>>(m->envs + b0, m->G, m->pvox);
+        MCUDA(cudaGetLastError(), "voxelize kernel");
+        gmt_status s = forward(m, nb, m->pvox, m->psg, st);
+        if (s != GMT_OK) return s;
+        proposal_sample_kernel<<<nb, 1024, smem, st>>>(m->logits, m->Nc, m->C, m->penv + b0, count,
+                                                                       65536, pitch, m->err);
+        MCUDA(cudaGetLastError(), "proposal kernel");
+    }
+    int h = 0;
+    MCUDA(cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
+    MCUDA(cudaStreamSynchronize(st), "proposal");
+    if (h) {
+        cudaMemset(m->err, 0, sizeof(int));
+        return mfail(GMT_ERR_INVALID, "a proposal sample exhausted its attempts (or a GEMM wait ran out)");
+    }
+    return GMT_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
 
 gmt_status gmt_model_create(const gmt_model_config* cfg, gmt_model** out) {
     if (!cfg || !out) return mfail(GMT_ERR_INVALID, "config and out must be non-NULL");
@@ -492,8 +610,8 @@ gmt_status gmt_model_create(const gmt_model_config* cfg, gmt_model** out) {
     m->ws_floats = (size_t)16 * std::max((size_t)B * m->H, (size_t)B * m->Dz) + (size_t)4 * B * m->Nc;
     MK(ws, m->ws_floats);
     MK(err, 1);
-    MK(pvox, (size_t)m->Din);
-    MK(psg, 8);
+    MK(pvox, (size_t)B * m->Din);
+    MK(psg, (size_t)B * 6);
 #undef MK
     cudaStream_t st = 0;
     const uint32_t k0 = (uint32_t)(m->seed & 0xffffffffu), k1 = (uint32_t)(m->seed >> 32);
@@ -686,35 +804,16 @@ gmt_status gmt_path_histogram(const float* X, int32_t pitch, const int32_t* path
 gmt_status gmt_propose(gmt_model* m, const gmt_space* space, const gmt_boxes* boxes, const float* start,
                        const float* goal, int32_t count, uint64_t seed, float* samples, int32_t pitch,
                        gmt_stream stream) {
-    if (!m || !space || !boxes || !start || !goal || !samples || count < 1 || pitch < count)
-        return mfail(GMT_ERR_INVALID, "bad proposal arguments");
-    if (space->kind != GMT_COST_EUCLID || space->dim != 3)
-        return mfail(GMT_ERR_INVALID, "the learned proposal supports 3D geometric spaces");
-    cudaStream_t st = (cudaStream_t)stream;
-    gmt_status s = gmt_voxelize(1, boxes, m->G, m->pvox, stream);
-    if (s != GMT_OK) return s;
-    const float sg[6] = {start[0], start[1], start[2], goal[0], goal[1], goal[2]};
-    MCUDA(cudaMemcpyAsync(m->psg, sg, sizeof(sg), cudaMemcpyHostToDevice, st), "start/goal upload");
-    s = forward(m, 1, m->pvox, m->psg, st);
-    if (s != GMT_OK) return s;
-    int* flags = m->err;  // reuse: set to 1 on exhausted attempts, checked below
-    float* lo = m->psg;   // position bounds next to start/goal (6 floats used, 8 allocated -> use ws)
-    float bounds[6] = {space->lo[0], space->lo[1], space->lo[2], space->hi[0], space->hi[1], space->hi[2]};
-    float* dbounds = m->ws;
-    MCUDA(cudaMemcpyAsync(dbounds, bounds, sizeof(bounds), cudaMemcpyHostToDevice, st), "bounds upload");
-    (void)lo;
-    proposal_sample_kernel<<<1, 1024, m->Nc * sizeof(float), st>>>(
-        m->logits, m->Nc, m->C, BoxArgs{boxes->count, boxes->lo, boxes->hi}, dbounds, dbounds + 3, count,
-        (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), 65536, samples, pitch, flags);
-    MCUDA(cudaGetLastError(), "proposal kernel");
-    int h = 0;
-    MCUDA(cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, st), "flag readback");
-    MCUDA(cudaStreamSynchronize(st), "proposal");
-    if (h) {
-        cudaMemset(m->err, 0, sizeof(int));
-        return mfail(GMT_ERR_INVALID, "a proposal sample exhausted its attempts (or a GEMM wait ran out)");
-    }
-    return GMT_OK;
+    if (!space || !start || !goal) return mfail(GMT_ERR_INVALID, "bad proposal arguments");
+    float sg[6];
+    for (int a = 0; a < 3; ++a) { sg[a] = start[a]; sg[3 + a] = goal[a]; }
+    return propose_impl(m, 1, space, boxes, sg, count, &seed, samples, pitch, stream);
+}
+
+gmt_status gmt_propose_batch(gmt_model* m, int32_t B, const gmt_space* spaces, const gmt_boxes* boxes,
+                             const float* start_goal, int32_t count, const uint64_t* seeds, float* samples,
+                             int32_t pitch, gmt_stream stream) {
+    return propose_impl(m, B, spaces, boxes, start_goal, count, seeds, samples, pitch, stream);
 }
 
 }  // extern "C"

@@ -167,6 +167,104 @@ def plan_mixture(model: N.Model, pb: envgen.Problem, graph: N.Graph | None = Non
     return (info["status"], info["path_cost"]), step_ms, plan_ms, g
 
 
+class MixtureBatch:
+    """The mixture planned for many environments at once: gmt_propose_batch
+    draws every environment's n/2 learned samples (one forward pass per
+    max_batch environments, one sampling launch, one host synchronisation),
+    and gmt_plan_batch plans every query with its learned samples appended
+    after its n/2 + 1 SampleFree nodes (replayed from its CUDA graph from the
+    second call on).  Every query's tree equals a single gmt_plan on the same
+    sample set."""
+
+    def __init__(self, model: N.Model, problems):
+        self.model = model
+        n = problems[0].n
+        assert all(pb.n == n for pb in problems)
+        self.n_u = n // 2
+        self.n_l = n - self.n_u
+        r = float(np.float32(N.gmt_connection_radius(self.n_u, 3, 0.0, 1.0)))
+        self.upbs = [pb.with_(n=self.n_u, r=r) for pb in problems]
+        self.spaces = [space_struct(u) for u in self.upbs]
+        self._keep = [boxes_on_device(u) for u in self.upbs]
+        self.boxes = [k[0] for k in self._keep]
+        self.sg = [np.concatenate([u.x_init[:3], u.goal_center[:3]]) for u in self.upbs]
+        self.seeds = [int(pb.seed) ^ 0x5A5A5A5A for pb in problems]
+        self.samples = torch.empty(len(problems), 3, self.n_l, dtype=torch.float32, device="cuda")
+        self.planner = BatchPlanner(self.upbs, extra=self.samples, extra_count=self.n_l)
+
+    def run(self, allow_errors=True):
+        N.gmt_propose_batch(self.model, self.spaces, self.boxes, self.sg, self.n_l, self.seeds,
+                            self.samples.data_ptr(), self.n_l)
+        return self.planner.plan(allow_errors=allow_errors)
+
+
+def _batch_timed(run, reps):
+    """p50 of CUDA-event times around run() (which synchronises), and the
+    infos of the last call."""
+    st = torch.cuda.current_stream()
+    times, infos = [], None
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        infos = run()
+        b.record(st)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return float(np.median(times)), infos
+
+
+def evaluate_batched(model: N.Model, seeds, ns, n_ref=4096, reps=5, plain_step_ms_p50=None, log=print):
+    """The mixture in batched form against plain GMT* at equal path cost.
+    For every n in ns, all environments as one batch (gmt_propose_batch +
+    gmt_plan_batch, autotuned, then graph-replayed): batch time p50
+    over reps calls and mean path cost; the plain method is uniform sampling
+    at n_ref, both batched (gmt_plan_batch) and, if given, the single-plan p50
+    step time.  Costs are compared over the environments every arm solves.
+    The crossing is the smallest n whose mean cost is within 2% of plain
+    uniform@n_ref and whose success rate is within 2 points of it."""
+    pbs_ref = [env(s, n_ref) for s in seeds]
+    plain = BatchPlanner(pbs_ref)
+    plain.plan(allow_errors=True)
+    N.gmt_batch_autotune(plain.batch)
+    plain_ms, plain_infos = _batch_timed(lambda: plain.plan(allow_errors=True), reps + 1)
+    arms = {}
+    for n in ns:
+        mb = MixtureBatch(model, [env(s, n) for s in seeds])
+        mb.run()
+        N.gmt_batch_autotune(mb.planner.batch)
+        ms, infos = _batch_timed(mb.run, reps + 1)
+        arms[n] = (ms, infos)
+    B = len(seeds)
+    both = [i for i in range(B) if plain_infos[i]["status"] == 0 and all(a[1][i]["status"] == 0 for a in arms.values())]
+    ref = float(np.mean([plain_infos[i]["path_cost"] for i in both])) if both else float("nan")
+    ref_success = float(np.mean([x["status"] == 0 for x in plain_infos]))
+    res = {"environments": B, "environments_compared": len(both),
+           "plain_batched": {"n": n_ref, "batch_ms_p50": plain_ms, "ms_per_plan": plain_ms / B,
+                             "mean_cost": ref, "success": ref_success},
+           "plain_single_step_ms_p50": plain_step_ms_p50, "mixture_batched": {}}
+    for n, (ms, infos) in arms.items():
+        costs = [infos[i]["path_cost"] for i in both]
+        res["mixture_batched"][str(n)] = {
+            "batch_ms_p50": ms, "ms_per_plan": ms / B,
+            "success": float(np.mean([x["status"] == 0 for x in infos])),
+            "mean_cost": float(np.mean(costs)) if costs else None,
+            "cost_vs_plain": (float(np.mean(costs)) / ref) if costs else None}
+    ok = [n for n in ns if res["mixture_batched"][str(n)]["cost_vs_plain"] is not None
+          and res["mixture_batched"][str(n)]["cost_vs_plain"] <= 1.02
+          and res["mixture_batched"][str(n)]["success"] >= ref_success - 0.02]
+    n0 = min(ok) if ok else None
+    cross = {"n": n0, "sample_reduction": (n_ref / n0) if n0 else None}
+    if n0:
+        mpp = res["mixture_batched"][str(n0)]["ms_per_plan"]
+        cross["ms_per_plan"] = mpp
+        cross["speedup_vs_plain_batched"] = res["plain_batched"]["ms_per_plan"] / mpp
+        cross["speedup_vs_plain_single_p50"] = (plain_step_ms_p50 / mpp) if plain_step_ms_p50 else None
+    res["within_2pct_of_plain"] = cross
+    if log:
+        log(json.dumps(res, indent=1))
+    return res
+
+
 NS = (256, 384, 512, 640, 768, 1024, 1365, 2048, 4096)
 
 

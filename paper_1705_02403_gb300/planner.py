@@ -122,10 +122,13 @@ class Planner:
 
 
 class BatchPlanner:
-    """A batch of problems planned with gmt_plan_batch (one handle, reusable)."""
+    """A batch of problems planned with gmt_plan_batch (one handle, reusable).
+    extra: optional DEVICE tensor [q, d, pitch] of samples appended to every
+    query (its first extra_count columns; e.g. gmt_propose_batch's output)."""
 
-    def __init__(self, problems, device="cuda"):
+    def __init__(self, problems, device="cuda", extra=None, extra_count=0):
         self.problems = list(problems)
+        self.extra = extra
         self.device = device
         self._keep = []
         self.queries = (N.gmt_query * len(self.problems))()
@@ -139,7 +142,14 @@ class BatchPlanner:
                 qd.x_init[a] = float(pb.x_init[a])
             qd.goal = goal_struct(pb)
             qd.params = params_struct(pb)
-        self.offsets = np.concatenate([[0], np.cumsum([pb.N for pb in self.problems])]).astype(np.int64)
+            if extra is not None and extra_count > 0:
+                assert extra.is_contiguous() and extra.dtype == torch.float32 and extra.shape[0] == len(self.problems)
+                qd.extra = extra[k].data_ptr()
+                qd.extra_count = extra_count
+                qd.extra_pitch = extra.shape[2]
+        self.extra_count = extra_count if extra is not None else 0
+        self.offsets = np.concatenate(
+            [[0], np.cumsum([pb.N + self.extra_count for pb in self.problems])]).astype(np.int64)
         total = int(self.offsets[-1])
         self.parent = torch.empty(total, dtype=torch.int32, device=device)
         self.cost = torch.empty(total, dtype=torch.float32, device=device)

@@ -313,3 +313,80 @@ def test_invalid_batch_arguments(O):
     with pytest.raises(N.GmtError) as e:
         bp.plan()
     assert e.value.status == N.GMT_ERR_INVALID
+
+
+def free_points(pb, count, seed):
+    """`count` seeded uniform states of X outside every box: [d][count]."""
+    rng = np.random.default_rng([seed, 1705, 77])
+    out = []
+    while len(out) < count:
+        x = rng.uniform(pb.lo, pb.hi).astype(np.float32)
+        p = x[:pb.dp]
+        if len(pb.box_lo) and np.any(np.all((pb.box_lo <= p) & (p <= pb.box_hi), axis=1)):
+            continue
+        out.append(x)
+    return np.stack(out, 1)
+
+
+def appended_oracle(O, pb, extra):
+    """The oracle on SampleFree's n + 1 nodes followed by `extra` [d][m]."""
+    X, goal = O.sample_halton(pb) if pb.sampler == 1 else O.sample(pb)
+    gd = pb.dp if pb.goal_pos_only else pb.d
+    g_extra = np.array([O.in_goal(extra[:, j], gd, pb.goal_center, pb.goal_radius) for j in range(extra.shape[1])],
+                       np.uint8)
+    X = np.concatenate([X, extra], 1)
+    goal = np.concatenate([goal, g_extra])
+    r0 = O.radius_halton(pb.n, pb.d) if pb.sampler == 1 else O.radius_thm1(pb.n, pb.d)
+    r = pb.r if pb.r > 0 else np.float32(r0)
+    g = O.Graph(pb.kind, pb.d, pb.dp, X, goal, r, rho=pb.rho)
+    parent, cost, info = g.plan(pb.box_lo, pb.box_hi, pb.lo[:pb.dp], pb.hi[:pb.dp], pb.lam, pb.seg_spacing,
+                                pb.traj_points)
+    return X, goal, g, parent, cost, info
+
+
+def test_appended_samples_match_oracle_and_replay(O):
+    # gmt_query.extra: caller samples appended after each query's n + 1
+    # SampleFree nodes (the batched form of the learned mixture) give the
+    # oracle's samples, CSR, tree and counters on the same node set; a replay
+    # reads the appended samples again, so contents rewritten in place plan
+    # anew, and a replayed sample in an obstacle fails only its own query.
+    from paper_1705_02403_gb300 import learned
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300.planner import BatchPlanner
+    qs = [learned.env(900 + k, 300 + 41 * k).with_(r=0.0) for k in range(3)]
+    qs += [envgen.geometric(910, d=2, n=350, nbox=8, r=0.0), envgen.geometric(911, d=2, n=257, nbox=8, r=0.0)
+           .with_(sampler=1)]
+    qs += [envgen.di6(seed=920 + k, n=280 + 53 * k, r=2.8) for k in range(2)]
+    m, pitch = 150, 160
+    ext = np.zeros((len(qs), 6, pitch), np.float32)
+    for k, pb in enumerate(qs):
+        ext[k, :pb.d, :m] = free_points(pb, m, k)
+    extra = torch.tensor(ext, device="cuda")
+    bp = BatchPlanner(qs, extra=extra, extra_count=m)
+    infos = bp.plan()
+    for k, pb in enumerate(qs):
+        check_query(O, bp, k, infos, ref=appended_oracle(O, pb, ext[k, :pb.d, :m]))
+    # appended samples rewritten in place (permuted: the same edge count, so
+    # the replayed arena still fits; new node indices, so new CSR order and
+    # tie-breaks): the replay plans the new contents
+    for k, pb in enumerate(qs):
+        perm = np.random.default_rng(k).permutation(m)
+        ext[k, :pb.d, :m] = ext[k, :pb.d, :m][:, perm]
+    extra.copy_(torch.tensor(ext))
+    bp.parent.fill_(-9)
+    infos2 = bp.plan()
+    for k, pb in enumerate(qs):
+        check_query(O, bp, k, infos2, ref=appended_oracle(O, pb, ext[k, :pb.d, :m]))
+    # an appended sample inside a box of query 0: that query reports the error
+    pb0 = qs[0]
+    inside = (pb0.box_lo[0] + pb0.box_hi[0]) / 2
+    bad = ext.copy()
+    bad[0, :3, 7] = inside
+    extra.copy_(torch.tensor(bad))
+    infos3 = bp.plan(allow_errors=True)
+    assert infos3[0]["status"] == N.GMT_ERR_INVALID
+    assert all(infos3[k]["status"] in (0, N.GMT_NO_PATH) for k in range(1, len(qs)))
+    # the same call on a fresh handle fails before planning
+    bp2 = BatchPlanner(qs, extra=extra, extra_count=m)
+    with pytest.raises(RuntimeError):
+        bp2.plan()

@@ -169,6 +169,89 @@ def test_proposal_samples_follow_the_softmax():
     assert not inside.any()
 
 
+def test_batched_proposal_follows_each_softmax_and_agrees_with_single_calls():
+    # gmt_propose_batch: every environment's samples follow the softmax of its
+    # own logits row (chi^2 over 64 groups of cells), stay in X and out of its
+    # boxes, and agree with one gmt_propose call per environment (same seed)
+    # except where a draw falls within rounding of a CDF cell boundary; 6
+    # environments with max_batch 4 take two chunks.
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300 import learned
+    from paper_1705_02403_gb300.planner import boxes_on_device, space_struct
+    m = N.Model(G, H, C, 4, seed=8)
+    empty = np.zeros((0, 3), np.float32)
+    pbs = [learned.env(40 + k, 100).with_(box_lo=empty, box_hi=empty) for k in range(3)]
+    keep = [boxes_on_device(pb) for pb in pbs]
+    n = 200000
+    S = torch.empty(3, 3, n, device="cuda")
+    sg = [np.concatenate([pb.x_init, pb.goal_center]) for pb in pbs]
+    N.gmt_propose_batch(m, [space_struct(pb) for pb in pbs], [k[0] for k in keep], sg, n, [5, 6, 7], S.data_ptr(), n)
+    logits = dev(m.view().logits, (3, C ** 3), "f4", m).cpu().numpy().astype(np.float64)
+    for b in range(3):
+        p = np.exp(logits[b] - logits[b].max()); p /= p.sum()
+        s = S[b].cpu().numpy()
+        assert s.min() >= 0.0 and s.max() <= 1.0
+        c = np.clip((s * C).astype(int), 0, C - 1)
+        counts = np.bincount((c[0] * C + c[1]) * C + c[2], minlength=C ** 3)
+        obs = counts.reshape(64, -1).sum(1); exp = n * p.reshape(64, -1).sum(1)
+        assert ((obs - exp) ** 2 / exp).sum() < 120.0, b
+    # different environments give different logits rows
+    assert np.abs(logits[0] - logits[1]).max() > 1e-3
+    # with boxes, two chunks, against single calls
+    pbs = [learned.env(60 + k, 100) for k in range(6)]
+    keep = [boxes_on_device(pb) for pb in pbs]
+    cnt, pitch = 3000, 3008
+    S = torch.full((6, 3, pitch), -1.0, device="cuda")
+    seeds = [1000 + 3 * k for k in range(6)]
+    N.gmt_propose_batch(m, [space_struct(pb) for pb in pbs], [k[0] for k in keep],
+                        [np.concatenate([pb.x_init, pb.goal_center]) for pb in pbs], cnt, seeds, S.data_ptr(), pitch)
+    Sb = S.cpu().numpy()
+    assert np.all(Sb[:, :, cnt:] == -1.0)          # nothing past count is written
+    for b, pb in enumerate(pbs):
+        one = torch.empty(3, cnt, device="cuda")
+        N.gmt_propose(m, space_struct(pb), keep[b][0], pb.x_init, pb.goal_center, cnt, seeds[b], one.data_ptr(), cnt)
+        P = Sb[b, :, :cnt].T
+        assert P.min() >= 0.0 and P.max() <= 1.0
+        inside = np.any(np.all((pb.box_lo[None] <= P[:, None]) & (P[:, None] <= pb.box_hi[None]), axis=2), axis=1)
+        assert not inside.any(), b
+        same = np.all(one.cpu().numpy().T == P, axis=1).mean()
+        assert same >= 0.99, (b, same)
+
+
+def test_batched_mixture_plans_equal_single_plans():
+    # The mixture in batched form (gmt_propose_batch + gmt_plan_batch with the
+    # learned samples appended to every query) gives each environment the
+    # tree that gmt_build_graph_ex + gmt_plan give on the same sample set, and
+    # a replay (same seeds) gives the same bits again.
+    from paper_1705_02403_gb300 import _native as N
+    from paper_1705_02403_gb300 import learned
+    m = N.Model(G, H, C, 4, seed=9)
+    pbs = [learned.env(80 + k, 500) for k in range(5)]
+    mb = learned.MixtureBatch(m, pbs)
+    infos = mb.run(allow_errors=False)
+    for k, upb in enumerate(mb.upbs):
+        v = mb.planner.view(k)
+        assert v["N"] == upb.n + 1 + mb.n_l
+        X = v["X"].cpu().numpy()
+        assert np.array_equal(X[:, upb.n + 1:], mb.samples[k].cpu().numpy())
+        g = N.gmt_build_graph_ex(learned.space_struct(upb), mb.boxes[k], [float(x) for x in upb.x_init],
+                                 learned.goal_struct(upb), learned.params_struct(upb), mb.samples[k].data_ptr(),
+                                 mb.n_l, mb.n_l)
+        parent = torch.empty(v["N"], dtype=torch.int32, device="cuda")
+        cost = torch.empty(v["N"], dtype=torch.float32, device="cuda")
+        info = N.gmt_plan(g, mb.boxes[k], learned.params_struct(upb), parent.data_ptr(), cost.data_ptr(),
+                          allow_errors=True).as_dict()
+        p, c = mb.planner.result(k)
+        assert np.array_equal(p.cpu().numpy(), parent.cpu().numpy()), k
+        assert np.array_equal(c.cpu().numpy().view(np.uint32), cost.cpu().numpy().view(np.uint32)), k
+        assert infos[k]["status"] == info["status"] and infos[k]["path_cost"] == info["path_cost"]
+    p0 = mb.planner.parent.clone()
+    mb.planner.parent.fill_(-9)
+    infos2 = mb.run(allow_errors=False)
+    assert torch.equal(mb.planner.parent, p0)
+    assert [i["path_cost"] for i in infos2] == [i["path_cost"] for i in infos]
+
+
 def test_mixture_graph_appends_learned_samples(O):
     # gmt_build_graph_ex: the appended samples become nodes n+1.. and the graph
     # and tree equal the oracle's on the same sample set.
