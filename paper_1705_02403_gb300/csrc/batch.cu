@@ -162,25 +162,25 @@ __global__ void __launch_bounds__(256) batch_cells_scatter_kernel(const QueryDev
     if (q.use_cells) cell_scatter_node(q.s.N, q.cell_of, q.cell_start, q.cell_cnt, q.cell_sorted, (int)(t - off[k]));
 }
 
-// One warp per (query, row).  Fill pass: a query whose longest row outgrew
-// the sort list (only possible if a replayed batch's inputs changed in place)
-// gets an edge count its plan rejects (GMT_ERR_OOM); so does one whose edge
-// count outgrew its slice.
+// One CTA per (query, cell) of the cell-list queries (off: cumulative cell
+// counts, 0 for the other queries).  Fill pass: a query whose longest row
+// outgrew the sort list (only possible if a replayed batch's inputs changed in
+// place) gets an edge count its plan rejects (GMT_ERR_OOM); so does one whose
+// edge count outgrew its slice.
 template <int D, bool FILL>
-__global__ void __launch_bounds__(kCellWarps * 32) batch_cells_rows_kernel(const QueryDev* __restrict__ Q,
+__global__ void __launch_bounds__(kCellWarps * 32) batch_cells_tile_kernel(const QueryDev* __restrict__ Q,
                                                                            const long long* __restrict__ off, int nq,
                                                                            int words) {
     extern __shared__ int cell_buf[];
-    const long long w = (long long)blockIdx.x * kCellWarps + (threadIdx.x >> 5);
-    if (w >= off[nq]) return;
-    const int k = find_query(off, nq, w);
+    const long long c = blockIdx.x;
+    if (c >= off[nq]) return;
+    const int k = find_query(off, nq, c);
     const QueryDev& q = Q[k];
     if (!q.use_cells) return;
     if (FILL && (long long)q.out_row[q.s.N] > q.edge_cap) return;
-    cell_row<D, FILL>(q.s, q.X, q.cg, q.cell_of, q.cell_start, q.cell_sorted, q.out_count, q.cell_info, q.out_row,
-                      q.out_col, q.out_cost, q.cell_info + 1, cell_buf + (threadIdx.x >> 5) * words,
-                      (int)(w - off[k]));
-    if (FILL && (threadIdx.x & 31) == 0 && __ldcg(&q.cell_info[1]) != 0) q.out_row[q.s.N] = INT_MAX;
+    cell_tile<D, FILL>(q.s, q.X, q.cg, q.cell_start, q.cell_sorted, q.out_count, q.cell_info, q.out_row, q.out_col,
+                       q.out_cost, q.cell_info + 1, cell_buf, words, (int)(c - off[k]));
+    if (FILL && threadIdx.x == 0 && __ldcg(&q.cell_info[1]) != 0) q.out_row[q.s.N] = INT_MAX;
 }
 
 // One warp per (query, row).  A query whose edge count exceeds the slice it was
@@ -245,26 +245,30 @@ cudaError_t batch_mask(int kind, int d, const QueryDev* Q, const long long* off,
     return cudaGetLastError();
 }
 // Cell-list stages before the row scan: cell counts, per-query cell scan,
-// scatter, row counts (queries without use_cells return at once).
-cudaError_t batch_cells_front(int d, const QueryDev* Q, const long long* off, int nq, long long nodes,
-                              cudaStream_t st) {
-    const unsigned tb = (unsigned)((nodes + 255) / 256), wb = (unsigned)((nodes + kCellWarps - 1) / kCellWarps);
+// scatter, row counts (queries without use_cells return at once).  off:
+// cumulative node counts; off_cells: cumulative cell counts (cells: their total).
+cudaError_t batch_cells_front(int d, const QueryDev* Q, const long long* off, const long long* off_cells, int nq,
+                              long long nodes, long long cells, cudaStream_t st) {
+    const unsigned tb = (unsigned)((nodes + 255) / 256);
     if (d == 2) batch_cells_count_kernel<2><<<tb, 256, 0, st>>>(Q, off, nq);
     else if (d == 3) batch_cells_count_kernel<3><<<tb, 256, 0, st>>>(Q, off, nq);
     else return cudaErrorInvalidValue;
     batch_cells_scan_kernel<<<nq, 1024, 0, st>>>(Q);
     batch_cells_scatter_kernel<<<tb, 256, 0, st>>>(Q, off, nq);
-    if (d == 2) batch_cells_rows_kernel<2, false><<<wb, kCellWarps * 32, 0, st>>>(Q, off, nq, 0);
-    else batch_cells_rows_kernel<3, false><<<wb, kCellWarps * 32, 0, st>>>(Q, off, nq, 0);
+    if (cells > 0) {
+        const size_t smem = cell_tile_smem(d, 0);
+        if (d == 2) batch_cells_tile_kernel<2, false><<<(unsigned)cells, kCellWarps * 32, smem, st>>>(Q, off_cells, nq, 0);
+        else batch_cells_tile_kernel<3, false><<<(unsigned)cells, kCellWarps * 32, smem, st>>>(Q, off_cells, nq, 0);
+    }
     return cudaGetLastError();
 }
 // words: the largest cell_fill_words of the group's cell-list queries
-cudaError_t batch_cells_fill(int d, const QueryDev* Q, const long long* off, int nq, long long rows, int words,
+cudaError_t batch_cells_fill(int d, const QueryDev* Q, const long long* off_cells, int nq, long long cells, int words,
                              cudaStream_t st) {
-    const unsigned wb = (unsigned)((rows + kCellWarps - 1) / kCellWarps);
-    const size_t smem = (size_t)kCellWarps * words * sizeof(int);
-    if (d == 2) batch_cells_rows_kernel<2, true><<<wb, kCellWarps * 32, smem, st>>>(Q, off, nq, words);
-    else if (d == 3) batch_cells_rows_kernel<3, true><<<wb, kCellWarps * 32, smem, st>>>(Q, off, nq, words);
+    if (cells <= 0) return cudaSuccess;
+    const size_t smem = cell_tile_smem(d, words);
+    if (d == 2) batch_cells_tile_kernel<2, true><<<(unsigned)cells, kCellWarps * 32, smem, st>>>(Q, off_cells, nq, words);
+    else if (d == 3) batch_cells_tile_kernel<3, true><<<(unsigned)cells, kCellWarps * 32, smem, st>>>(Q, off_cells, nq, words);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -331,9 +335,9 @@ static_assert(sizeof(PlanCtl) <= kCtlSlotB, "control block must fit its slot");
 struct Group {
     int kind = 0, d = 0, dp = 0;
     std::vector<int> members;          // query indices
-    long long nodes = 0, tiles = 0, tasks = 0;
+    long long nodes = 0, tiles = 0, tasks = 0, cells = 0;
     int max_n = 0, max_boxes = 0;
-    DevBuf desc, off_nodes, off_tiles, off_tasks, off_rows, order, args;
+    DevBuf desc, off_nodes, off_tiles, off_tasks, off_rows, off_cells, order, args;
     std::vector<int> order_h;
     // lockstep scheme: members [chunk_start[c], chunk_start[c] + chunk_count[c])
     // run in one launch; their node offsets start at lock_base + chunk_base[c]
@@ -529,7 +533,10 @@ gmt_status enqueue_build_front(gmt_batch* b, cudaStream_t st) {
         BCUDA(batch_sample(g.kind, g.d, Q, g.off_nodes.as<long long>(), nq, g.nodes, g.any_halton, st),
               "batched sample kernel");
         BCUDA(batch_mask(g.kind, g.d, Q, g.off_tiles.as<long long>(), nq, g.tiles, st), "batched pair filter");
-        if (g.any_cells) BCUDA(batch_cells_front(g.d, Q, g.off_nodes.as<long long>(), nq, g.nodes, st), "batched cells");
+        if (g.any_cells)
+            BCUDA(batch_cells_front(g.d, Q, g.off_nodes.as<long long>(), g.off_cells.as<long long>(), nq, g.nodes,
+                                    g.cells, st),
+                  "batched cells");
         if (g.kind != GMT_COST_EUCLID) {  // directed costs: the in-neighbour bit matrix and rows
             const long long warps = g.tasks;
             batch_transpose_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(Q, g.off_tasks.as<long long>(), nq);
@@ -548,7 +555,7 @@ gmt_status enqueue_build_back(gmt_batch* b, int32_t* parent, float* cost, cudaSt
         const QueryDev* Q = g.desc.as<QueryDev>();
         BCUDA(batch_fill(g.kind, g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, st), "batched fill");
         if (g.any_cells)
-            BCUDA(batch_cells_fill(g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, g.cell_words, st),
+            BCUDA(batch_cells_fill(g.d, Q, g.off_cells.as<long long>(), nq, g.cells, g.cell_words, st),
                   "batched cells");
     }
     // sampling flags of this call (appended samples are read on replays too)
@@ -665,7 +672,7 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         bool pays = false;
         const unsigned dbg = Qh.params.debug_flags;
         const bool applies = make_cell_grid(Qh.space.kind, Qh.space.dim, Qh.space.lo, Qh.space.hi, b->r[k], N,
-                                            &cgs[k], &pays);
+                                            true, &cgs[k], &pays);
         if (dbg & GMT_DEBUG_CELLS_LIST) cgs[k].list_only = 1;
         use_cells[k] = applies && !(dbg & GMT_DEBUG_PAIRS_ALL) && (pays || (dbg & GMT_DEBUG_PAIRS_CELLS)) &&
                        !(k < (int)force_pairs.size() && force_pairs[k]);
@@ -751,7 +758,7 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
     // per-group work offsets and descriptors
     for (Group& g : b->groups) {
         const int nq = (int)g.members.size();
-        std::vector<long long> on(nq + 1, 0), ot(nq + 1, 0), ow(nq + 1, 0);
+        std::vector<long long> on(nq + 1, 0), ot(nq + 1, 0), ow(nq + 1, 0), oc(nq + 1, 0);
         std::vector<QueryDev> dq(nq);
         g.max_n = 0; g.max_boxes = 0;
         g.any_cells = false;
@@ -771,23 +778,26 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
                     ? (long long)((N + kDubRows - 1) / kDubRows) * ((W + kDubWords - 1) / kDubWords)
                     : (long long)((N + kMaskRows - 1) / kMaskRows) * ((W + kMaskWords - 1) / kMaskWords);
             on[i + 1] = on[i] + N;
+            oc[i + 1] = oc[i] + (use_cells[k] ? cgs[k].ncells : 0);
             ot[i + 1] = ot[i] + tiles;
             ow[i + 1] = ow[i] + (long long)W * W;
             g.max_n = std::max(g.max_n, N);
             g.max_boxes = std::max(g.max_boxes, queries[k].boxes.count);
             dq[i] = b->qd[k];
         }
-        g.nodes = on[nq]; g.tiles = ot[nq]; g.tasks = ow[nq];
+        g.nodes = on[nq]; g.tiles = ot[nq]; g.tasks = ow[nq]; g.cells = oc[nq];
         BCUDA(g.desc.need(nq * sizeof(QueryDev)), "descriptors");
         BCUDA(g.off_nodes.need((nq + 1) * 8), "descriptors");
         BCUDA(g.off_tiles.need((nq + 1) * 8), "descriptors");
         BCUDA(g.off_tasks.need((nq + 1) * 8), "descriptors");
         BCUDA(g.off_rows.need((nq + 1) * 8), "descriptors");
+        BCUDA(g.off_cells.need((nq + 1) * 8), "descriptors");
         BCUDA(cudaMemcpyAsync(g.desc.p, dq.data(), nq * sizeof(QueryDev), cudaMemcpyHostToDevice, st), "upload");
         BCUDA(cudaMemcpyAsync(g.off_nodes.p, on.data(), (nq + 1) * 8, cudaMemcpyHostToDevice, st), "upload");
         BCUDA(cudaMemcpyAsync(g.off_tiles.p, ot.data(), (nq + 1) * 8, cudaMemcpyHostToDevice, st), "upload");
         BCUDA(cudaMemcpyAsync(g.off_tasks.p, ow.data(), (nq + 1) * 8, cudaMemcpyHostToDevice, st), "upload");
         BCUDA(cudaMemcpyAsync(g.off_rows.p, on.data(), (nq + 1) * 8, cudaMemcpyHostToDevice, st), "upload");
+        BCUDA(cudaMemcpyAsync(g.off_cells.p, oc.data(), (nq + 1) * 8, cudaMemcpyHostToDevice, st), "upload");
         BCUDA(cudaStreamSynchronize(st), "upload");  // host vectors go out of scope
     }
     gmt_status s = enqueue_build_front(b, st);

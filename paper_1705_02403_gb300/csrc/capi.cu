@@ -434,7 +434,7 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
     // (or when forced), else all pairs; both give the same CSR
     CellGrid cg;
     bool cells_pay = false;
-    bool cells = make_cell_grid(g->kind, g->d, space->lo, space->hi, g->r, g->N, &cg, &cells_pay);
+    bool cells = make_cell_grid(g->kind, g->d, space->lo, space->hi, g->r, g->N, false, &cg, &cells_pay);
     if (params->debug_flags & GMT_DEBUG_CELLS_LIST) cg.list_only = 1;
     if (params->debug_flags & GMT_DEBUG_PAIRS_ALL) cells = false;
     else if (!(params->debug_flags & GMT_DEBUG_PAIRS_CELLS)) cells = cells && cells_pay;

@@ -18,9 +18,8 @@ __global__ void __launch_bounds__(256) cells_scatter_kernel(int N, const int* __
 }
 
 template <int D, bool FILL>
-__global__ void __launch_bounds__(kCellWarps * 32) cells_rows_kernel(SpaceArgs s, const float* __restrict__ X,
-                                                                     CellGrid cg, const int* __restrict__ cell_of,
-                                                                     const int* __restrict__ start,
+__global__ void __launch_bounds__(kCellWarps * 32) cells_tile_kernel(SpaceArgs s, const float* __restrict__ X,
+                                                                     CellGrid cg, const int* __restrict__ start,
                                                                      const int* __restrict__ sorted,
                                                                      int* __restrict__ out_count,
                                                                      int* __restrict__ max_deg,
@@ -28,8 +27,8 @@ __global__ void __launch_bounds__(kCellWarps * 32) cells_rows_kernel(SpaceArgs s
                                                                      int* __restrict__ col, float* __restrict__ cost,
                                                                      int* __restrict__ overflow, int words) {
     extern __shared__ int cell_buf[];
-    cell_row<D, FILL>(s, X, cg, cell_of, start, sorted, out_count, max_deg, row, col, cost, overflow,
-                      cell_buf + (threadIdx.x >> 5) * words, blockIdx.x * kCellWarps + (threadIdx.x >> 5));
+    cell_tile<D, FILL>(s, X, cg, start, sorted, out_count, max_deg, row, col, cost, overflow, cell_buf, words,
+                       blockIdx.x);
 }
 
 // ---- box grid (checks against many boxes)
@@ -89,7 +88,8 @@ cudaError_t launch_box_grid(int dp, BoxArgs boxes, const BoxGridArgs& grid, int*
     return cudaGetLastError();
 }
 
-bool make_cell_grid(int kind, int d, const float* lo, const float* hi, float r, int N, CellGrid* cg, bool* pays) {
+bool make_cell_grid(int kind, int d, const float* lo, const float* hi, float r, int N, bool batched, CellGrid* cg,
+                    bool* pays) {
     if (kind != GMT_COST_EUCLID || (d != 2 && d != 3) || !(r > 0.0f)) return false;
     // cell side: at least 1.01 r, and coarse enough for at most 2^16 cells
     double h = (double)r * 1.01;
@@ -116,26 +116,28 @@ bool make_cell_grid(int kind, int d, const float* lo, const float* hi, float r, 
     while ((double)r * 1.01 * (double)cg->inv_h > 1.0) cg->inv_h = std::nextafter(cg->inv_h, 0.0f);
     cg->ncells = (int)ncells;
     cg->list_only = 0;
-    // measured on one GB300 (Theorem 1 radii): in 2D the cell list overtakes
-    // the all-pairs test near 4096 nodes; in 3D, with 27 cells of candidates
-    // per row, only beyond 16384
-    *pays = frac <= 0.25 && N >= (d == 2 ? 4096 : 32768);
+    // measured on one GB300 (Theorem 1 radii, cell tiles): in 2D the cell
+    // list ties with the all-pairs test at 8192 nodes and wins 2x at 16384 on
+    // one graph, and in a batch (where the cell stages' short launches overlap
+    // other queries' work) already pays from 4096; in 3D, with 27 cells of
+    // candidates to sort per tile, it loses at 16384 and wins 2.3x at 32768
+    *pays = frac <= 0.25 && N >= (d == 2 ? (batched ? 4096 : 8192) : 32768);
     return true;
 }
 
 namespace {
 template <int D>
-cudaError_t rows_t(const SpaceArgs& s, const float* X, const CellGrid& cg, const int* cell_of, const int* start,
-                   const int* sorted, bool fill, int* out_count, int* max_deg, const int* row, int* col, float* cost,
-                   int* overflow, cudaStream_t st) {
-    const int blocks = (s.N + kCellWarps - 1) / kCellWarps;
-    const int words = cell_fill_words(cg, s.N);
+cudaError_t rows_t(const SpaceArgs& s, const float* X, const CellGrid& cg, const int* start, const int* sorted,
+                   bool fill, int* out_count, int* max_deg, const int* row, int* col, float* cost, int* overflow,
+                   cudaStream_t st) {
+    const int words = fill ? cell_fill_words(cg, s.N) : 0;
+    const size_t smem = cell_tile_smem(D, words);
     if (fill)
-        cells_rows_kernel<D, true><<<blocks, kCellWarps * 32, (size_t)kCellWarps * words * sizeof(int), st>>>(
-            s, X, cg, cell_of, start, sorted, out_count, max_deg, row, col, cost, overflow, words);
+        cells_tile_kernel<D, true><<<cg.ncells, kCellWarps * 32, smem, st>>>(s, X, cg, start, sorted, out_count,
+                                                                             max_deg, row, col, cost, overflow, words);
     else
-        cells_rows_kernel<D, false><<<blocks, kCellWarps * 32, 0, st>>>(s, X, cg, cell_of, start, sorted, out_count,
-                                                                         max_deg, row, col, cost, overflow, 0);
+        cells_tile_kernel<D, false><<<cg.ncells, kCellWarps * 32, smem, st>>>(s, X, cg, start, sorted, out_count,
+                                                                              max_deg, row, col, cost, overflow, 0);
     return cudaGetLastError();
 }
 }  // namespace
@@ -158,10 +160,9 @@ cudaError_t launch_cells_scatter(int N, const int* cell_of, const int* cell_star
 cudaError_t launch_cells_rows(const SpaceArgs& s, const float* X, const CellGrid& cg, const int* cell_of,
                               const int* cell_start, const int* sorted, bool fill, int* out_count, int* max_deg,
                               const int* row, int* col, float* cost, int* overflow, cudaStream_t st) {
-    if (s.d == 2)
-        return rows_t<2>(s, X, cg, cell_of, cell_start, sorted, fill, out_count, max_deg, row, col, cost, overflow, st);
-    if (s.d == 3)
-        return rows_t<3>(s, X, cg, cell_of, cell_start, sorted, fill, out_count, max_deg, row, col, cost, overflow, st);
+    (void)cell_of;
+    if (s.d == 2) return rows_t<2>(s, X, cg, cell_start, sorted, fill, out_count, max_deg, row, col, cost, overflow, st);
+    if (s.d == 3) return rows_t<3>(s, X, cg, cell_start, sorted, fill, out_count, max_deg, row, col, cost, overflow, st);
     return cudaErrorInvalidValue;
 }
 

@@ -4,16 +4,25 @@
 // counting-sorted by grid cell; a row's candidates are the nodes of the 3^d
 // cells around its own, which lie in 3^(d-1) runs of consecutive cells along
 // axis 0.  Every candidate takes the same FP32 edge predicate as the all-pairs
-// build, and each row's columns come out in ascending order (a bitmap of the
-// row in shared memory, or a bitonic sort for graphs beyond 32768 nodes), so
-// the CSR is the same bits.
+// build, and each row's columns come out in ascending order, so the CSR is the
+// same bits.
+//
+// One CTA per cell (a cell tile): the cell's candidates (the same for every
+// row of the cell) are loaded into shared memory once, with their
+// coordinates, and for the fill sorted by node index (bitonic); then each warp
+// takes rows of the cell and tests 32 candidates per step, so a row's passing
+// candidates come out in ascending order from a ballot and are written
+// straight into the CSR.  A cell with more than kTileCand candidates takes the
+// row-by-row path instead (one warp per row, candidates gathered from global
+// memory, columns ordered through a bitmap of the row or a sorted list).
 #pragma once
 
 #include "graph_body.cuh"
 
 namespace gmtk {
 
-constexpr int kCellWarps = 8;  // rows (one per warp) per block
+constexpr int kCellWarps = 8;    // warps per cell tile
+constexpr int kTileCand = 2048;  // candidates a cell tile holds in shared memory
 
 template <int D>
 __device__ __forceinline__ int cell_index(const CellGrid& cg, const float* x) {
@@ -47,38 +56,32 @@ __device__ __forceinline__ void cell_scatter_node(int N, const int* __restrict__
     sorted[start[c] + atomicSub(&cnt[c], 1) - 1] = v;
 }
 
-// Words of the fill's per-warp shared-memory buffer for a graph of N nodes.
+// Words of the row-by-row fill's per-warp buffer for a graph of N nodes.
 __host__ __device__ inline int cell_fill_words(const CellGrid& cg, int N) {
     const int W = (N + 31) / 32;
     return !cg.list_only && W <= kCellList ? W : kCellList;
 }
 
-// One warp: row v.  Count pass (FILL = false) or fill pass, whose warp buffer
-// `list` holds cell_fill_words(cg, N) words (only what the row needs, so that
-// the rest of the SM's L1 keeps caching the samples).
-template <int D, bool FILL>
-__device__ __forceinline__ void cell_row(const SpaceArgs& s, const float* __restrict__ X, const CellGrid& cg,
-                                         const int* __restrict__ cell_of, const int* __restrict__ start,
-                                         const int* __restrict__ sorted, int* __restrict__ out_count,
-                                         int* __restrict__ max_deg, const int* __restrict__ row,
-                                         int* __restrict__ col, float* __restrict__ cost, int* __restrict__ overflow,
-                                         int* list, int v) {
-    constexpr int NR = D == 3 ? 9 : 3;  // runs of up to 3 cells along axis 0
-    const int lane = threadIdx.x & 31;
-    if (v >= s.N) return;
-    float xv[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) xv[a] = X[(size_t)a * s.pitch + v];
+// Dynamic shared memory of a cell tile: the candidate tile or, for a cell
+// with too many candidates, the row-by-row buffers of its warps.
+__host__ __device__ inline size_t cell_tile_smem(int D, int words) {
+    const size_t tile = (size_t)kTileCand * (1 + D) * sizeof(int);
+    const size_t rows = (size_t)kCellWarps * words * sizeof(int);
+    return tile > rows ? tile : rows;
+}
+
+// The candidate runs of cell `cell`: up to 3^(d-1) runs of consecutive cells
+// along axis 0 ([rs, re) in the cell-sorted node order).  Returns their total.
+template <int D>
+__device__ __forceinline__ int cell_runs(const CellGrid& cg, const int* __restrict__ start, int cell, int* rs,
+                                         int* re) {
+    constexpr int NR = D == 3 ? 9 : 3;
     int c[3] = {0, 0, 0};
-    {
-        int idx = cell_of[v];
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            c[a] = idx % cg.g[a];
-            idx /= cg.g[a];
-        }
+    for (int a = 0; a < D; ++a) {
+        c[a] = cell % cg.g[a];
+        cell /= cg.g[a];
     }
-    int rs[NR], re[NR];
     int T = 0;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
@@ -90,27 +93,51 @@ __device__ __forceinline__ void cell_row(const SpaceArgs& s, const float* __rest
         re[k] = ok ? start[base + x1 + 1] : 0;
         T += re[k] - rs[k];
     }
+    return T;
+}
+
+// Candidate t of the runs (t < their total).
+template <int D>
+__device__ __forceinline__ int run_candidate(const int* __restrict__ sorted, const int* rs, const int* re, int t) {
+    constexpr int NR = D == 3 ? 9 : 3;
+    int j = -1, off = t;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int len = re[k] - rs[k];
+        if (j < 0 && off >= 0 && off < len) j = sorted[rs[k] + off];
+        off -= len;
+    }
+    return j;
+}
+
+// Row-by-row path, one warp: row v with candidates in the given runs.  Count
+// pass (FILL = false) or fill pass, whose warp buffer `list` holds
+// cell_fill_words(cg, N) words.
+template <int D, bool FILL>
+__device__ __forceinline__ void cell_row(const SpaceArgs& s, const float* __restrict__ X, const CellGrid& cg,
+                                         const int* __restrict__ sorted, const int* rs, const int* re, int T,
+                                         int* __restrict__ out_count, int* __restrict__ max_deg,
+                                         const int* __restrict__ row, int* __restrict__ col, float* __restrict__ cost,
+                                         int* __restrict__ overflow, int* list, int v) {
+    const int lane = threadIdx.x & 31;
+    float xv[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) xv[a] = X[(size_t)a * s.pitch + v];
     // Fill: with N <= 32 kCellList the warp's buffer holds a bitmap of the
     // row's columns, which yields them in ascending order; larger graphs keep
     // a list of columns and sort it (bitonic).
     const int W = (s.N + 31) / 32;
     const bool bitmap = FILL && W <= kCellList && !cg.list_only;
     if (bitmap) {
-        for (int w = lane; w < W; w += 32) list[w] = 0;
+        for (int q = lane; q < W; q += 32) list[q] = 0;
         __syncwarp();
     }
     int n = 0;
     for (int t0 = 0; t0 < T; t0 += 32) {
         const int t = t0 + lane;
-        int j = -1, off = t;
-#pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            const int len = re[k] - rs[k];
-            if (j < 0 && off >= 0 && off < len) j = sorted[rs[k] + off];
-            off -= len;
-        }
+        const int j = t < T ? run_candidate<D>(sorted, rs, re, t) : -1;
         bool pass = false;
-        if (t < T && j >= 0 && j != v) {
+        if (j >= 0 && j != v) {
             float xj[D];
 #pragma unroll
             for (int a = 0; a < D; ++a) xj[a] = X[(size_t)a * s.pitch + j];
@@ -137,8 +164,8 @@ __device__ __forceinline__ void cell_row(const SpaceArgs& s, const float* __rest
         __syncwarp();
         int done = 0;
         for (int c0 = 0; c0 < W; c0 += 32) {
-            const int w = c0 + lane;
-            unsigned bits = w < W ? (unsigned)list[w] : 0u;
+            const int wd = c0 + lane;
+            unsigned bits = wd < W ? (unsigned)list[wd] : 0u;
             const int cnt = __popc(bits);
             int incl = cnt;
 #pragma unroll
@@ -148,7 +175,7 @@ __device__ __forceinline__ void cell_row(const SpaceArgs& s, const float* __rest
             }
             int pos = b + done + incl - cnt;
             while (bits) {
-                const int j = 32 * w + __ffs(bits) - 1;
+                const int j = 32 * wd + __ffs(bits) - 1;
                 bits &= bits - 1;
                 float xj[D];
 #pragma unroll
@@ -195,6 +222,95 @@ __device__ __forceinline__ void cell_row(const SpaceArgs& s, const float* __rest
         cost[b + t] = edge_cost<GMT_COST_EUCLID, D>(s, xv, xj);
     }
     __syncwarp();
+}
+
+// One CTA of kCellWarps warps: every row of cell `cell`.  smem:
+// cell_tile_smem(D, words) bytes; words = cell_fill_words(cg, N) (fill).
+template <int D, bool FILL>
+__device__ __forceinline__ void cell_tile(const SpaceArgs& s, const float* __restrict__ X, const CellGrid& cg,
+                                          const int* __restrict__ start, const int* __restrict__ sorted,
+                                          int* __restrict__ out_count, int* __restrict__ max_deg,
+                                          const int* __restrict__ row, int* __restrict__ col,
+                                          float* __restrict__ cost, int* __restrict__ overflow, int* smem, int words,
+                                          int cell) {
+    constexpr int NR = D == 3 ? 9 : 3;
+    const int r0 = start[cell], R = start[cell + 1] - r0;
+    if (R <= 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int rs[NR], re[NR];
+    const int T = cell_runs<D>(cg, start, cell, rs, re);
+    if (T > kTileCand) {
+        for (int r = warp; r < R; r += kCellWarps)
+            cell_row<D, FILL>(s, X, cg, sorted, rs, re, T, out_count, max_deg, row, col, cost, overflow,
+                              smem + warp * words, sorted[r0 + r]);
+        return;
+    }
+    int* cand = smem;
+    float* xs = (float*)(smem + kTileCand);  // xs[a * kTileCand + t]
+    int L = T;
+    if (FILL) {  // sort the candidates by node index (bitonic, padded with INT_MAX)
+        L = 1;
+        while (L < T) L <<= 1;
+    }
+    for (int t = threadIdx.x; t < L; t += blockDim.x)
+        cand[t] = t < T ? run_candidate<D>(sorted, rs, re, t) : INT_MAX;
+    __syncthreads();
+    if (FILL) {
+        for (int k = 2; k <= L; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int i = threadIdx.x; i < L; i += blockDim.x) {
+                    const int ix = i ^ jj;
+                    if (ix > i) {
+                        const int a = cand[i], b2 = cand[ix];
+                        if ((a > b2) == ((i & k) == 0)) {
+                            cand[i] = b2;
+                            cand[ix] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        const int j = cand[t];
+#pragma unroll
+        for (int a = 0; a < D; ++a) xs[a * kTileCand + t] = X[(size_t)a * s.pitch + j];
+    }
+    __syncthreads();
+    int longest = 0;
+    for (int r = warp; r < R; r += kCellWarps) {
+        const int v = sorted[r0 + r];
+        float xv[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) xv[a] = X[(size_t)a * s.pitch + v];
+        const int b = FILL ? row[v] : 0, e = FILL ? row[v + 1] : 0;
+        int n = 0;
+        for (int t0 = 0; t0 < T; t0 += 32) {
+            const int t = t0 + lane;
+            bool pass = false;
+            int j = -1;
+            float xj[D];
+            if (t < T) {
+                j = cand[t];
+#pragma unroll
+                for (int a = 0; a < D; ++a) xj[a] = xs[a * kTileCand + t];
+                pass = j != v && connects<GMT_COST_EUCLID, D>(s, xv, xj);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            if (FILL && pass) {
+                const int pos = b + n + __popc(m & ((1u << lane) - 1u));
+                if (pos < e) {
+                    col[pos] = j;
+                    cost[pos] = edge_cost<GMT_COST_EUCLID, D>(s, xv, xj);
+                }
+            }
+            n += __popc(m);
+        }
+        if (!FILL && lane == 0) out_count[v] = n;
+        longest = max(longest, n);
+    }
+    if (!FILL && lane == 0 && longest > 0) atomicMax(max_deg, longest);
 }
 
 }  // namespace gmtk

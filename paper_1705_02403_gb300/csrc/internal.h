@@ -147,7 +147,8 @@ constexpr int kCellList = 1024;
 // Returns false when the cell list does not apply (not a 2D/3D geometric
 // graph); *pays is false when the 3^d cells around a node would hold more than
 // a quarter of the domain.
-bool make_cell_grid(int kind, int d, const float* lo, const float* hi, float r, int N, CellGrid* cg, bool* pays);
+bool make_cell_grid(int kind, int d, const float* lo, const float* hi, float r, int N, bool batched, CellGrid* cg,
+                    bool* pays);
 cudaError_t launch_cells_count(const SpaceArgs& s, const float* X, const CellGrid& cg, int* cell_of, int* cell_cnt,
                                cudaStream_t st);
 // cell_cnt returns to zero.

@@ -37,16 +37,30 @@ struct EnvBoxes {
 };
 
 // X[b, (i G + j) G + k] = 1 if the centre of voxel (i, j, k) lies in a box of env b.
-__global__ void voxelize_kernel(const EnvBoxes* __restrict__ envs, int G, bf16* __restrict__ X) {
+constexpr int kVoxBoxes = 256;  // boxes staged in shared memory per pass
+
+// Block (x, b): voxels of environment b; its boxes pass through shared memory.
+__global__ void __launch_bounds__(256) voxelize_kernel(const EnvBoxes* __restrict__ envs, int G,
+                                                       bf16* __restrict__ X) {
+    __shared__ float slo[kVoxBoxes * 3], shi[kVoxBoxes * 3];
     const int b = blockIdx.y;
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     const int G3 = G * G * G;
-    if (v >= G3) return;
     const int i = v / (G * G), j = (v / G) % G, k = v % G;
     const float p[3] = {((float)i + 0.5f) / (float)G, ((float)j + 0.5f) / (float)G, ((float)k + 0.5f) / (float)G};
     const EnvBoxes e = envs[b];
-    const bool occ = in_any_box<3>(p, e.lo, e.hi, e.count);
-    X[(size_t)b * G3 + v] = __float2bfloat16_rn(occ ? 1.0f : 0.0f);
+    bool occ = false;
+    for (int b0 = 0; b0 < e.count; b0 += kVoxBoxes) {
+        const int nb = min(kVoxBoxes, e.count - b0);
+        __syncthreads();  // the previous pass's boxes are no longer read
+        for (int t = threadIdx.x; t < nb * 3; t += blockDim.x) {
+            slo[t] = e.lo[(size_t)b0 * 3 + t];
+            shi[t] = e.hi[(size_t)b0 * 3 + t];
+        }
+        __syncthreads();
+        occ = occ || in_any_box<3>(p, slo, shi, nb);
+    }
+    if (v < G3) X[(size_t)b * G3 + v] = __float2bfloat16_rn(occ ? 1.0f : 0.0f);
 }
 
 // Z = [H2, start/goal (6), zeros] in BF16.
@@ -377,6 +391,9 @@ struct gmt_model {
     EnvBoxes* envs = nullptr;       // grow-only descriptor arrays of proposal calls
     ProposalEnv* penv = nullptr;
     int envs_cap = 0;
+    unsigned char* pin = nullptr;   // pinned staging of those descriptors and start/goal
+    size_t pin_cap = 0;
+    cudaEvent_t pin_ev = nullptr;   // recorded after the copies out of `pin`
     std::vector<void*> owned;
 
     long long n(int i) const {
@@ -389,6 +406,8 @@ struct gmt_model {
         for (void* p : owned) cudaFree(p);
         if (envs) cudaFree(envs);
         if (penv) cudaFree(penv);
+        if (pin) cudaFreeHost(pin);
+        if (pin_ev) cudaEventDestroy(pin_ev);
     }
 };
 
@@ -523,8 +542,23 @@ gmt_status propose_impl(gmt_model* m, int B, const gmt_space* spaces, const gmt_
               "proposal kernel attribute");
         attr_set.store(true, std::memory_order_relaxed);
     }
-    std::vector<EnvBoxes> eb(B);
-    std::vector<ProposalEnv> pe(B);
+    // pinned staging: [B] EnvBoxes, [B] ProposalEnv, [B][6] start/goal
+    const size_t eb_bytes = (size_t)B * sizeof(EnvBoxes), pe_bytes = (size_t)B * sizeof(ProposalEnv);
+    const size_t pe_off = (eb_bytes + 15) / 16 * 16, sg_off = pe_off + (pe_bytes + 15) / 16 * 16;
+    const size_t need = sg_off + (size_t)B * 6 * sizeof(float);
+    if (!m->pin_ev) MCUDA(cudaEventCreateWithFlags(&m->pin_ev, cudaEventDisableTiming), "proposal event");
+    MCUDA(cudaEventSynchronize(m->pin_ev), "proposal staging");  // earlier copies out of `pin` are done
+    if (m->pin_cap < need) {
+        if (m->pin) cudaFreeHost(m->pin);
+        m->pin = nullptr;
+        m->pin_cap = 0;
+        MCUDA(cudaMallocHost((void**)&m->pin, need), "proposal staging");
+        m->pin_cap = need;
+    }
+    EnvBoxes* eb = (EnvBoxes*)m->pin;
+    ProposalEnv* pe = (ProposalEnv*)(m->pin + pe_off);
+    float* hsg = (float*)(m->pin + sg_off);
+    std::memcpy(hsg, sg, (size_t)B * 6 * sizeof(float));
     for (int b = 0; b < B; ++b) {
         const gmt_space& sp = spaces[b];
         if (sp.kind != GMT_COST_EUCLID || sp.dim != 3)
@@ -549,16 +583,15 @@ gmt_status propose_impl(gmt_model* m, int B, const gmt_space* spaces, const gmt_
         MCUDA(cudaMalloc((void**)&m->penv, (size_t)B * sizeof(ProposalEnv)), "proposal descriptors");
         m->envs_cap = B;
     }
-    MCUDA(cudaMemcpyAsync(m->envs, eb.data(), (size_t)B * sizeof(EnvBoxes), cudaMemcpyHostToDevice, st),
-          "proposal descriptors");
-    MCUDA(cudaMemcpyAsync(m->penv, pe.data(), (size_t)B * sizeof(ProposalEnv), cudaMemcpyHostToDevice, st),
-          "proposal descriptors");
+    MCUDA(cudaMemcpyAsync(m->envs, eb, eb_bytes, cudaMemcpyHostToDevice, st), "proposal descriptors");
+    MCUDA(cudaMemcpyAsync(m->penv, pe, pe_bytes, cudaMemcpyHostToDevice, st), "proposal descriptors");
     const int G3 = m->G * m->G * m->G;
     for (int b0 = 0; b0 < B; b0 += m->maxB) {
         const int nb = std::min(m->maxB, B - b0);
-        MCUDA(cudaMemcpyAsync(m->psg, sg + (size_t)b0 * 6, (size_t)nb * 6 * sizeof(float), cudaMemcpyHostToDevice,
-                              st),
+        MCUDA(cudaMemcpyAsync(m->psg, hsg + (size_t)b0 * 6, (size_t)nb * 6 * sizeof(float),
+                              cudaMemcpyHostToDevice, st),
               "start/goal upload");
+        MCUDA(cudaEventRecord(m->pin_ev, st), "proposal event");  // covers every copy out of `pin` so far
         voxelize_kernel<<<dim3(blocks_for(G3, 256), nb), 256, 0, st>>>(m->envs + b0, m->G, m->pvox);
         MCUDA(cudaGetLastError(), "voxelize kernel");
         gmt_status s = forward(m, nb, m->pvox, m->psg, st);

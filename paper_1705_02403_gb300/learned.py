@@ -191,16 +191,21 @@ class MixtureBatch:
         self.seeds = [int(pb.seed) ^ 0x5A5A5A5A for pb in problems]
         self.samples = torch.empty(len(problems), 3, self.n_l, dtype=torch.float32, device="cuda")
         self.planner = BatchPlanner(self.upbs, extra=self.samples, extra_count=self.n_l)
+        self.args = N.ProposeBatchArgs(self.spaces, self.boxes, self.sg, self.seeds)
 
-    def run(self, allow_errors=True):
-        N.gmt_propose_batch(self.model, self.spaces, self.boxes, self.sg, self.n_l, self.seeds,
-                            self.samples.data_ptr(), self.n_l)
-        return self.planner.plan(allow_errors=allow_errors)
+    def propose(self):
+        N.gmt_propose_batch(self.model, None, None, None, self.n_l, None, self.samples.data_ptr(), self.n_l,
+                            args=self.args)
+
+    def run(self, allow_errors=True, raw=False):
+        self.propose()
+        return self.planner.plan(allow_errors=allow_errors, raw=raw)
 
 
 def _batch_timed(run, reps):
-    """p50 of CUDA-event times around run() (which synchronises), and the
-    infos of the last call."""
+    """p50 of CUDA-event times around run() (which synchronises and returns
+    the ctypes info array, or None), and the info dicts of the last call
+    (converted outside the timed region)."""
     st = torch.cuda.current_stream()
     times, infos = [], None
     for _ in range(reps):
@@ -210,14 +215,15 @@ def _batch_timed(run, reps):
         b.record(st)
         b.synchronize()
         times.append(a.elapsed_time(b))
-    return float(np.median(times)), infos
+    return float(np.median(times)), (N.infos_as_dicts(infos) if infos is not None else None)
 
 
 def evaluate_batched(model: N.Model, seeds, ns, n_ref=4096, reps=5, plain_step_ms_p50=None, log=print):
     """The mixture in batched form against plain GMT* at equal path cost.
     For every n in ns, all environments as one batch (gmt_propose_batch +
     gmt_plan_batch, autotuned, then graph-replayed): batch time p50
-    over reps calls and mean path cost; the plain method is uniform sampling
+    over reps calls (and of the proposal and the batched plan alone) and mean
+    path cost; the plain method is uniform sampling
     at n_ref, both batched (gmt_plan_batch) and, if given, the single-plan p50
     step time.  Costs are compared over the environments every arm solves.
     The crossing is the smallest n whose mean cost is within 2% of plain
@@ -226,14 +232,16 @@ def evaluate_batched(model: N.Model, seeds, ns, n_ref=4096, reps=5, plain_step_m
     plain = BatchPlanner(pbs_ref)
     plain.plan(allow_errors=True)
     N.gmt_batch_autotune(plain.batch)
-    plain_ms, plain_infos = _batch_timed(lambda: plain.plan(allow_errors=True), reps + 1)
+    plain_ms, plain_infos = _batch_timed(lambda: plain.plan(allow_errors=True, raw=True), reps + 1)
     arms = {}
     for n in ns:
         mb = MixtureBatch(model, [env(s, n) for s in seeds])
         mb.run()
         N.gmt_batch_autotune(mb.planner.batch)
-        ms, infos = _batch_timed(mb.run, reps + 1)
-        arms[n] = (ms, infos)
+        ms, infos = _batch_timed(lambda: mb.run(raw=True), reps + 1)
+        prop_ms, _ = _batch_timed(mb.propose, reps + 1)
+        plan_ms, _ = _batch_timed(lambda: mb.planner.plan(allow_errors=True, raw=True), reps + 1)
+        arms[n] = (ms, infos, prop_ms, plan_ms)
     B = len(seeds)
     both = [i for i in range(B) if plain_infos[i]["status"] == 0 and all(a[1][i]["status"] == 0 for a in arms.values())]
     ref = float(np.mean([plain_infos[i]["path_cost"] for i in both])) if both else float("nan")
@@ -242,10 +250,10 @@ def evaluate_batched(model: N.Model, seeds, ns, n_ref=4096, reps=5, plain_step_m
            "plain_batched": {"n": n_ref, "batch_ms_p50": plain_ms, "ms_per_plan": plain_ms / B,
                              "mean_cost": ref, "success": ref_success},
            "plain_single_step_ms_p50": plain_step_ms_p50, "mixture_batched": {}}
-    for n, (ms, infos) in arms.items():
+    for n, (ms, infos, prop_ms, plan_ms) in arms.items():
         costs = [infos[i]["path_cost"] for i in both]
         res["mixture_batched"][str(n)] = {
-            "batch_ms_p50": ms, "ms_per_plan": ms / B,
+            "batch_ms_p50": ms, "ms_per_plan": ms / B, "propose_ms_p50": prop_ms, "plan_batch_ms_p50": plan_ms,
             "success": float(np.mean([x["status"] == 0 for x in infos])),
             "mean_cost": float(np.mean(costs)) if costs else None,
             "cost_vs_plain": (float(np.mean(costs)) / ref) if costs else None}

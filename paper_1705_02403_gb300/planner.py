@@ -155,9 +155,10 @@ class BatchPlanner:
         self.cost = torch.empty(total, dtype=torch.float32, device=device)
         self.batch = N.Batch()
 
-    def plan(self, stream=None, allow_errors=False):
+    def plan(self, stream=None, allow_errors=False, raw=False):
+        """Info dicts, or (raw=True) the ctypes info array (N.infos_as_dicts)."""
         return N.gmt_plan_batch(self.queries, self.batch, self.parent.data_ptr(), self.cost.data_ptr(), stream,
-                                allow_errors)
+                                allow_errors, raw)
 
     def result(self, k):
         a, b = int(self.offsets[k]), int(self.offsets[k + 1])
