@@ -94,10 +94,30 @@ struct ClusterTeam {
     }
 };
 
+// ------------------------------------------------------------- lane groups
+// A group of W lanes (W = 32: the warp; W = 16: half a warp) working on one
+// edge: its lane index, its lanes' mask, and votes whose bit i is lane i of
+// the group.  Two groups of one warp may call these at the same time with
+// their own masks.
+template <int W>
+struct LaneGroup {
+    static_assert(W == 32 || W == 16 || W == 8, "lane groups of 8, 16 or 32 lanes");
+    __device__ __forceinline__ static int base() { return (int)(threadIdx.x & 31) & ~(W - 1); }
+    __device__ __forceinline__ static int lane() { return (int)threadIdx.x & (W - 1); }
+    __device__ __forceinline__ static unsigned mask() {
+        return W == 32 ? 0xffffffffu : ((1u << (W & 31)) - 1u) << base();
+    }
+    __device__ __forceinline__ static unsigned ballot(bool p) {
+        const unsigned b = __ballot_sync(mask(), p);
+        return W == 32 ? b : (b >> base()) & ((1u << (W & 31)) - 1u);
+    }
+    __device__ __forceinline__ static bool any(bool p) { return __any_sync(mask(), p); }
+};
+
 // ---------------------------------------------------------------- edge check
 // Both checks first keep only the boxes that meet an axis-aligned bound of
-// every point the check will evaluate (one box per lane, 32 at a time), then
-// test the points against those boxes alone.  The bound is inflated by far
+// every point the check will evaluate (one box per lane, a lane group's width
+// at a time), then test the points against those boxes alone.  The bound is inflated by far
 // more than the rounding of the point formulas, so a box that holds one of
 // the computed points is never dropped: the verdict equals testing every
 // point against every box.
@@ -115,16 +135,17 @@ __device__ __forceinline__ bool box_meets(const float* blo, const float* bhi, in
 // Geometric edge y -> x of length L: m = max(2, ceil(L/spacing) + 1) points
 // p_k = y + t_k (x - y), t_k = k/(m-1); collision if one lies in a closed box.
 // Without the grid, boxes that do not meet the segment's bounding box (every
-// computed p_k lies within a few ulps of it) are set aside 32 at a time first.
-template <int DP>
+// computed p_k lies within a few ulps of it) are set aside W at a time first.
+template <int DP, int W = 32>
 __device__ __forceinline__ bool segment_free_warp(const float* y, const float* x, float L, float spacing, const float* blo,
                                   const float* bhi, int nbox, const BoxGridArgs& grid) {
-    const int lane = threadIdx.x & 31;
+    using LG = LaneGroup<W>;
+    const int lane = LG::lane();
     int m = (int)ceilf(L / spacing) + 1;
     if (m < 2) m = 2;
     const float denom = (float)(m - 1);
     if (grid.use) {
-        for (int k0 = 0; k0 < m; k0 += 32) {
+        for (int k0 = 0; k0 < m; k0 += W) {
             const int k = k0 + lane;
             bool hit = false;
             if (k < m) {
@@ -134,7 +155,7 @@ __device__ __forceinline__ bool segment_free_warp(const float* y, const float* x
                 for (int a = 0; a < DP; ++a) p[a] = y[a] + t * (x[a] - y[a]);
                 hit = in_any_box_grid<DP>(p, blo, bhi, grid);
             }
-            if (__any_sync(0xffffffffu, hit)) return false;
+            if (LG::any(hit)) return false;
         }
         return true;
     }
@@ -145,11 +166,11 @@ __device__ __forceinline__ bool segment_free_warp(const float* y, const float* x
         lo[a] = fminf(x[a], y[a]) - e;
         hi[a] = fmaxf(x[a], y[a]) + e;
     }
-    for (int b0 = 0; b0 < nbox; b0 += 32) {
+    for (int b0 = 0; b0 < nbox; b0 += W) {
         const int b = b0 + lane;
-        const unsigned near = __ballot_sync(0xffffffffu, b < nbox && box_meets<DP>(blo, bhi, b, lo, hi));
+        const unsigned near = LG::ballot(b < nbox && box_meets<DP>(blo, bhi, b, lo, hi));
         if (!near) continue;
-        for (int k0 = 0; k0 < m; k0 += 32) {
+        for (int k0 = 0; k0 < m; k0 += W) {
             const int k = k0 + lane;
             bool hit = false;
             if (k < m) {
@@ -159,7 +180,7 @@ __device__ __forceinline__ bool segment_free_warp(const float* y, const float* x
                 for (int a = 0; a < DP; ++a) p[a] = y[a] + t * (x[a] - y[a]);
                 for (unsigned w = near; w; w &= w - 1) hit = hit || in_box<DP>(p, blo, bhi, b0 + __ffs(w) - 1);
             }
-            if (__any_sync(0xffffffffu, hit)) return false;
+            if (LG::any(hit)) return false;
         }
     }
     return true;
@@ -170,13 +191,15 @@ __device__ __forceinline__ bool segment_free_warp(const float* y, const float* x
 // bounds.  Without the grid, the boxes are first filtered against the
 // bounding box of the cubic's Bezier control points p0, p0 + tau v0 / 3,
 // p1 - tau v1 / 3, p1 (the curve lies in their convex hull), inflated.
+template <int W = 32>
 __device__ __forceinline__ bool trajectory_free_warp(const float* y, const float* x, float tau, int points, const float* plo,
                                             const float* phi, const float* blo, const float* bhi, int nbox,
                                             const BoxGridArgs& grid) {
-    const int lane = threadIdx.x & 31;
+    using LG = LaneGroup<W>;
+    const int lane = LG::lane();
     const float denom = (float)(points - 1);
     float lo[3], hi[3];
-    unsigned near_first = 0;  // boxes 0..31, reused by the first chunk of points
+    unsigned near_first = 0;  // boxes 0..W-1, reused by the first chunk of points
     if (!grid.use) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -186,9 +209,9 @@ __device__ __forceinline__ bool trajectory_free_warp(const float* y, const float
             lo[a] = fminf(fminf(y[a], x[a]), fminf(c1, c2)) - e;
             hi[a] = fmaxf(fmaxf(y[a], x[a]), fmaxf(c1, c2)) + e;
         }
-        if (nbox > 0) near_first = __ballot_sync(0xffffffffu, lane < nbox && box_meets<3>(blo, bhi, lane, lo, hi));
+        if (nbox > 0) near_first = LG::ballot(lane < nbox && box_meets<3>(blo, bhi, lane, lo, hi));
     }
-    for (int k0 = 0; k0 < points; k0 += 32) {
+    for (int k0 = 0; k0 < points; k0 += W) {
         const int k = k0 + lane;
         bool hit = false;
         float p[3];
@@ -200,15 +223,15 @@ __device__ __forceinline__ bool trajectory_free_warp(const float* y, const float
             if (grid.use && !hit) hit = in_any_box_grid<3>(p, blo, bhi, grid);
         }
         if (!grid.use) {
-            for (int b0 = 0; b0 < nbox; b0 += 32) {
+            for (int b0 = 0; b0 < nbox; b0 += W) {
                 const unsigned near =
                     b0 == 0 ? near_first
-                            : __ballot_sync(0xffffffffu, b0 + lane < nbox && box_meets<3>(blo, bhi, b0 + lane, lo, hi));
+                            : LG::ballot(b0 + lane < nbox && box_meets<3>(blo, bhi, b0 + lane, lo, hi));
                 if (k < points)
                     for (unsigned w = near; w; w &= w - 1) hit = hit || in_box<3>(p, blo, bhi, b0 + __ffs(w) - 1);
             }
         }
-        if (__any_sync(0xffffffffu, hit)) return false;
+        if (LG::any(hit)) return false;
     }
     return true;
 }
@@ -221,11 +244,13 @@ __device__ __forceinline__ bool trajectory_free_warp(const float* y, const float
 // part stays within c/2 of the midpoint of y and x (a point at arc length l is
 // within l of y and L - l of x, L <= c), its altitude between the two end
 // altitudes.
+template <int W = 32>
 __device__ __forceinline__ bool dubins_free_warp(const float* y, const float* x, const DubPath& P, float c,
                                                  float spacing, float rho, const float* plo, const float* phi,
                                                  const float* blo, const float* bhi, int nbox,
                                                  const BoxGridArgs& grid) {
-    const int lane = threadIdx.x & 31;
+    using LG = LaneGroup<W>;
+    const int lane = LG::lane();
     if (P.word >= kDubNone) return false;  // no word: never an edge (its cost would be +inf)
     const DubSegs G = dubins_segments(y, P, rho);
     int m = (int)ceilf(c / spacing) + 1;
@@ -243,9 +268,9 @@ __device__ __forceinline__ bool dubins_free_warp(const float* y, const float* x,
         }
         lo[2] = fminf(y[2], x[2]) - e;
         hi[2] = fmaxf(y[2], x[2]) + e;
-        if (nbox > 0) near_first = __ballot_sync(0xffffffffu, lane < nbox && box_meets<3>(blo, bhi, lane, lo, hi));
+        if (nbox > 0) near_first = LG::ballot(lane < nbox && box_meets<3>(blo, bhi, lane, lo, hi));
     }
-    for (int k0 = 0; k0 < m; k0 += 32) {
+    for (int k0 = 0; k0 < m; k0 += W) {
         const int k = k0 + lane;
         bool hit = false;
         float p[3];
@@ -256,15 +281,15 @@ __device__ __forceinline__ bool dubins_free_warp(const float* y, const float* x,
             if (grid.use && !hit) hit = in_any_box_grid<3>(p, blo, bhi, grid);
         }
         if (!grid.use) {
-            for (int b0 = 0; b0 < nbox; b0 += 32) {
+            for (int b0 = 0; b0 < nbox; b0 += W) {
                 const unsigned near =
                     b0 == 0 ? near_first
-                            : __ballot_sync(0xffffffffu, b0 + lane < nbox && box_meets<3>(blo, bhi, b0 + lane, lo, hi));
+                            : LG::ballot(b0 + lane < nbox && box_meets<3>(blo, bhi, b0 + lane, lo, hi));
                 if (k < m)
                     for (unsigned w = near; w; w &= w - 1) hit = hit || in_box<3>(p, blo, bhi, b0 + __ffs(w) - 1);
             }
         }
-        if (__any_sync(0xffffffffu, hit)) return false;
+        if (LG::any(hit)) return false;
     }
     return true;
 }
@@ -281,25 +306,25 @@ template <bool SM> __device__ __forceinline__ unsigned long long st_ull(const un
     return __ldcg(p);
 }
 
-// Lazy parent (Alg. 1, Sec. III-A), one lane's share: over the in-row entries
-// r0 + lane, r0 + lane + 32, ... the minimum (cost, index) of
+// Lazy parent (Alg. 1, Sec. III-A), one lane's share of a group of W lanes:
+// over the in-row entries r0 + lane, r0 + lane + W, ... the minimum (cost, index) of
 // fl(ocost[y] + in_cost[e]) among open y (ocost < +inf); *be = its edge, -1
 // if none.  (cost, index) is a total order, so the order of the entries does
-// not matter: four chunks of 32 are taken at a time, their column and cost
+// not matter: four chunks of W are taken at a time, their column and cost
 // loads issued together, then their snapshot gathers.
-template <bool SM>
+template <bool SM, int W = 32>
 __device__ __forceinline__ void lane_parent_min(const int* __restrict__ in_col, const float* __restrict__ in_cost,
                                                 const float* ocost, int r0, int r1, int lane, float* bc_out,
                                                 int* by_out, int* be_out) {
     const float INF = f_inf();
     float bc = INF;
     int by = INT_MAX, be = -1;
-    for (int eb = r0; eb < r1; eb += 4 * 32) {
+    for (int eb = r0; eb < r1; eb += 4 * W) {
         int ys[4];
         float ic[4], oc[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int e = eb + 32 * u + lane;
+            const int e = eb + W * u + lane;
             ys[u] = e < r1 ? __ldg(&in_col[e]) : -1;
             ic[u] = e < r1 ? __ldg(&in_cost[e]) : 0.0f;
         }
@@ -309,7 +334,7 @@ __device__ __forceinline__ void lane_parent_min(const int* __restrict__ in_col, 
         for (int u = 0; u < 4; ++u) {
             if (oc[u] < INF) {
                 const float c = oc[u] + ic[u];
-                if (c < bc || (c == bc && ys[u] < by)) { bc = c; by = ys[u]; be = eb + 32 * u + lane; }
+                if (c < bc || (c == bc && ys[u] < by)) { bc = c; by = ys[u]; be = eb + W * u + lane; }
             }
         }
     }

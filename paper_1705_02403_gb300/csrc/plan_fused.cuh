@@ -33,13 +33,17 @@ struct FusedCounts {
 
 // Lazy parent (minimum (cost, index) over x's in-neighbours open in the
 // snapshot ocur), one collision check of that edge, and, if it is free, the
-// commit: x joins the tree and opens in the next snapshot.  Whole warp.
-template <int KIND, int DP>
+// commit: x joins the tree and opens in the next snapshot.  One group of W
+// lanes (the whole warp, or half of it: then the warp's two halves pull two
+// candidates side by side).
+template <int KIND, int DP, int W>
 __device__ __forceinline__ void fused_pull(const PlanArgs& A, int x, const float* ocur, float* onext, int2* nxt,
                                            int set, int p, const float* blo, const float* bhi, int nbox,
                                            FusedCounts& cnt) {
     constexpr int D = KIND == GMT_COST_DI ? 6 : (KIND == GMT_COST_DUBINS ? 4 : DP);
-    const int lane = threadIdx.x & 31;
+    using LG = LaneGroup<W>;
+    const int lane = LG::lane();
+    const unsigned gmask = LG::mask();
     PlanCtl* ctl = A.ctl;
     const int N = A.N;
     const int r0 = __ldg(&A.in_row[x]), r1 = __ldg(&A.in_row[x + 1]);
@@ -49,12 +53,12 @@ __device__ __forceinline__ void fused_pull(const PlanArgs& A, int x, const float
     for (int a = 0; a < D; ++a) sx[a] = __ldg(&A.X[(size_t)a * A.pitch + x]);
     float bc;
     int by, be;
-    lane_parent_min<false>(A.in_col, A.in_cost, ocur, r0, r1, lane, &bc, &by, &be);
+    lane_parent_min<false, W>(A.in_col, A.in_cost, ocur, r0, r1, lane, &bc, &by, &be);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const float oc = __shfl_xor_sync(0xffffffffu, bc, off);
-        const int oy = __shfl_xor_sync(0xffffffffu, by, off);
-        const int oe = __shfl_xor_sync(0xffffffffu, be, off);
+    for (int off = W / 2; off > 0; off >>= 1) {
+        const float oc = __shfl_xor_sync(gmask, bc, off);
+        const int oy = __shfl_xor_sync(gmask, by, off);
+        const int oe = __shfl_xor_sync(gmask, be, off);
         if (oc < bc || (oc == bc && oy < by)) { bc = oc; by = oy; be = oe; }
     }
     // the group node that pushed x is an open in-neighbour, so be >= 0; the
@@ -72,7 +76,8 @@ __device__ __forceinline__ void fused_pull(const PlanArgs& A, int x, const float
         free_edge = cached == 1;
     } else {
         if (KIND == GMT_COST_EUCLID) {
-            free_edge = segment_free_warp<DP>(sy, sx, __ldg(&A.in_cost[be]), A.seg_spacing, blo, bhi, nbox, A.grid);
+            free_edge =
+                segment_free_warp<DP, W>(sy, sx, __ldg(&A.in_cost[be]), A.seg_spacing, blo, bhi, nbox, A.grid);
         } else if (KIND == GMT_COST_DUBINS) {
             DubPath P;
             if (A.in_path) {
@@ -81,11 +86,12 @@ __device__ __forceinline__ void fused_pull(const PlanArgs& A, int x, const float
             } else {
                 P = dubins_path(sy, sx, A.rho);
             }
-            free_edge = dubins_free_warp(sy, sx, P, __ldg(&A.in_cost[be]), A.seg_spacing, A.rho, A.pos_lo, A.pos_hi,
-                                         blo, bhi, nbox, A.grid);
+            free_edge = dubins_free_warp<W>(sy, sx, P, __ldg(&A.in_cost[be]), A.seg_spacing, A.rho, A.pos_lo,
+                                            A.pos_hi, blo, bhi, nbox, A.grid);
         } else {
             const float tau = A.in_tau ? __ldg(&A.in_tau[be]) : di_tau(di_coef(sy, sx), A.r);
-            free_edge = trajectory_free_warp(sy, sx, tau, A.traj_points, A.pos_lo, A.pos_hi, blo, bhi, nbox, A.grid);
+            free_edge =
+                trajectory_free_warp<W>(sy, sx, tau, A.traj_points, A.pos_lo, A.pos_hi, blo, bhi, nbox, A.grid);
         }
         if (lane == 0) {
             ++cnt.computed;
@@ -113,8 +119,9 @@ __device__ __forceinline__ void fused_pull(const PlanArgs& A, int x, const float
 }
 
 // sbox_bytes: shared memory at sbox for staged boxes and, once the wavefront is
-// over, the copy of the parent array.  A.ocost holds 2 N floats.
-template <class Team, int KIND, int DP>
+// over, the copy of the parent array.  A.ocost holds 2 N floats.  W: lanes
+// per candidate pull (32, or 16 for two pulls per warp).
+template <class Team, int KIND, int DP, int W = 32>
 __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& team, float* sbox, size_t sbox_bytes) {
     const int nbs = A.boxes.count <= smem_box_cap(DP) ? A.boxes.count : 0;
     for (int t = threadIdx.x; t < nbs * DP; t += blockDim.x) {
@@ -291,7 +298,7 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
         }
         for (;;) {
             int x = -1;
-            if (lane == 0) {
+            if ((lane & (W - 1)) == 0) {
                 const int t = atomicAdd(&ctl->ticket[p], 1);
                 if (t < N) {
                     for (int spins = 0;; ++spins) {
@@ -308,10 +315,11 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
                     if (x >= 0) A.list_cand[t] = -1;  // free for a later iteration
                 }
             }
-            x = __shfl_sync(0xffffffffu, x, 0);
+            x = __shfl_sync(LaneGroup<W>::mask(), x, 0, W);
             if (x < 0) break;
-            fused_pull<KIND, DP>(A, x, ocur, onext, nxt, set, p, blo, bhi, nbox, cnt);
+            fused_pull<KIND, DP, W>(A, x, ocur, onext, nxt, set, p, blo, bhi, nbox, cnt);
         }
+        __syncwarp();  // the lane groups leave the queue apart; the barrier wants whole warps
         if (!(ok = team.sync(ctl))) break;
 
         // termination test (Alg. 1), next threshold
