@@ -304,33 +304,71 @@ __device__ __forceinline__ float edge_cost(const SpaceArgs& s, const float* from
     return di_cost(from, to, s.r);
 }
 
-// Euclidean graphs of at most 4 dimensions: the staged columns are float4s
-// (one shared-memory load per pair) and columns past the last node hold +inf
-// (an infinite distance: no edge), so the inner loop tests no bounds; the
-// diagonal pair i = j is cleared once per word.  The squared distance is the
-// same expression as sq_dist (axes in order), so the bits are the same.
+// Packed FP32 pairs (two IEEE round-to-nearest operations per instruction,
+// each lane of the pair rounded on its own: the same bits as two scalar ops).
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+// Euclidean graphs of 2 to 4 dimensions: columns are staged in pairs (float4
+// (x_j, x_j+1, y_j, y_j+1), then (z_j, z_j+1, w_j, w_j+1)), and each lane
+// tests its row against two columns per step with packed FP32 arithmetic:
+// t = x_j - x_i, then d2 = t_0^2 + t_1^2 + ... in axis order, which is the
+// expression of sq_dist (0 + t_0^2 = t_0^2 exactly), so the bits are the same.
+// Columns past the last node hold +inf (an infinite distance: no edge), so
+// the inner loop tests no bounds; the diagonal pair i = j is cleared once per
+// word.
 template <int D>
 __device__ __forceinline__ void mask_tile_euclid4(const SpaceArgs& s, const float* __restrict__ X,
                                                   uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
                                                   int by) {
-    static_assert(D <= 4, "float4 columns");
-    __shared__ float4 tile[kMaskWords * 32];
+    static_assert(D >= 2 && D <= 4, "two to four axes in two float4s per column pair");
+    constexpr int kPairs = kMaskWords * 16;
+    __shared__ float4 tab[kPairs];                  // axes 0 and 1
+    __shared__ float4 tcd[D > 2 ? kPairs : 1];      // axes 2 and 3
     const int i = bx * kMaskRows + threadIdx.x;
     const int w0 = by * kMaskWords;
     const int j0 = w0 * 32;
     const float INF = f_inf();
-    for (int idx = threadIdx.x; idx < kMaskWords * 32; idx += kMaskRows) {
-        const int j = j0 + idx;
-        float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int idx = threadIdx.x; idx < kPairs; idx += kMaskRows) {
+        const int ja = j0 + 2 * idx, jb = ja + 1;
+        float c[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
 #pragma unroll
-        for (int a = 0; a < D; ++a) c[a] = j < s.N ? X[(size_t)a * s.pitch + j] : INF;
-        tile[idx] = make_float4(c[0], c[1], c[2], c[3]);
+        for (int a = 0; a < D; ++a) {
+            c[0][a] = ja < s.N ? X[(size_t)a * s.pitch + ja] : INF;
+            c[1][a] = jb < s.N ? X[(size_t)a * s.pitch + jb] : INF;
+        }
+        tab[idx] = make_float4(c[0][0], c[1][0], c[0][1], c[1][1]);
+        if (D > 2) tcd[idx] = make_float4(c[0][2], c[1][2], c[0][3], c[1][3]);
     }
     __syncthreads();
     if (i >= s.N) return;
-    float xi[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    unsigned long long xi2[4];
 #pragma unroll
-    for (int a = 0; a < D; ++a) xi[a] = X[(size_t)a * s.pitch + i];
+    for (int a = 0; a < D; ++a) {
+        const float v = X[(size_t)a * s.pitch + i];
+        xi2[a] = f2_pack(v, v);
+    }
     const int W = (s.N + 31) / 32;
     const float thr = s.r2_threshold;
     int cnt = 0;
@@ -339,16 +377,24 @@ __device__ __forceinline__ void mask_tile_euclid4(const SpaceArgs& s, const floa
         if (w >= W) break;
         uint32_t bits = 0;
 #pragma unroll
-        for (int b = 0; b < 32; ++b) {
-            const float4 q = tile[ww * 32 + b];
-            const float xj[4] = {q.x, q.y, q.z, q.w};
-            float d2 = 0.0f;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                const float t = xj[a] - xi[a];
-                d2 = d2 + t * t;
+        for (int b = 0; b < 32; b += 2) {
+            const float4 q = tab[ww * 16 + (b >> 1)];
+            const unsigned long long t0 = f2_sub(f2_pack(q.x, q.y), xi2[0]);
+            const unsigned long long t1 = f2_sub(f2_pack(q.z, q.w), xi2[1]);
+            unsigned long long d2 = f2_add(f2_mul(t0, t0), f2_mul(t1, t1));
+            if (D > 2) {
+                const float4 r = tcd[ww * 16 + (b >> 1)];
+                const unsigned long long t2 = f2_sub(f2_pack(r.x, r.y), xi2[2]);
+                d2 = f2_add(d2, f2_mul(t2, t2));
+                if (D > 3) {
+                    const unsigned long long t3 = f2_sub(f2_pack(r.z, r.w), xi2[3]);
+                    d2 = f2_add(d2, f2_mul(t3, t3));
+                }
             }
-            bits |= (d2 < thr ? 1u : 0u) << b;
+            float da, db;
+            f2_unpack(d2, da, db);
+            bits |= (da < thr ? 1u : 0u) << b;
+            bits |= (db < thr ? 1u : 0u) << (b + 1);
         }
         if ((i >> 5) == w) bits &= ~(1u << (i & 31));  // no self-loop
         mask[(size_t)w * s.pitch + i] = bits;
@@ -362,7 +408,7 @@ template <int KIND, int D>
 __device__ __forceinline__ void mask_tile(const SpaceArgs& s, const float* __restrict__ X,
                                           uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
                                           int by) {
-    if constexpr (KIND == GMT_COST_EUCLID && D <= 4) {
+    if constexpr (KIND == GMT_COST_EUCLID && D >= 2 && D <= 4) {
         mask_tile_euclid4<D>(s, X, mask, out_count, bx, by);
         return;
     }
