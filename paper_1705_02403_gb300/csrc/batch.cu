@@ -52,6 +52,8 @@ struct QueryDev {
     // caller samples appended after the n_sampled SampleFree nodes
     const float* extra;
     int extra_pitch;
+    // tiled fill (all-pairs Euclidean queries): per-tile row counts [tile][pitch]
+    int* tile_cnt;
 };
 
 // index k with off[k] <= t < off[k+1] (off has nq+1 entries, off[0] = 0)
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(kMaskRows) batch_mask_kernel(const QueryDev* _
     const QueryDev& q = Q[k];
     const int rb = (q.s.N + kMaskRows - 1) / kMaskRows;
     const int t = (int)(b - off[k]);
-    mask_tile<KIND, D>(q.s, q.X, q.mask, q.out_count, t % rb, t / rb);
+    mask_tile<KIND, D>(q.s, q.X, q.mask, q.out_count, t % rb, t / rb, q.tile_cnt);
 }
 
 __global__ void __launch_bounds__(kDIRows, 8) batch_mask_di_kernel(const QueryDev* __restrict__ Q,
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(kFillWarps * 32) batch_fill_kernel(const Query
     if (w >= off[nq]) return;
     const int k = find_query(off, nq, w);
     const QueryDev& q = Q[k];
-    if (q.use_cells) return;
+    if (q.use_cells || q.tile_cnt) return;
     const bool incoming = blockIdx.y == 1;  // in-rows (double integrator, Dubins airplane)
     const int* row = incoming ? q.in_row : q.out_row;
     if ((long long)row[q.s.N] > q.edge_cap) return;
@@ -204,6 +206,35 @@ __global__ void __launch_bounds__(kFillWarps * 32) batch_fill_kernel(const Query
     else
         fill_row<KIND, D, false>(q.s, q.X, q.mask, q.out_row, q.out_col, q.out_cost, q.out_tau, nullptr,
                                  (int)(w - off[k]), list[threadIdx.x >> 5]);
+}
+
+// Tiled fill of the all-pairs Euclidean queries: after the pair filter, the
+// per-tile counts become prefixes (one thread per row; off: cumulative node
+// counts); the fill, one block per mask tile (off: cumulative mask tiles),
+// then only reads them, so the build's back half can run again (the
+// autotuner does).  A query whose edge count exceeds its slice writes
+// nothing; its plan then reports GMT_ERR_OOM.
+__global__ void __launch_bounds__(256) batch_tile_prefix_kernel(const QueryDev* __restrict__ Q,
+                                                                const long long* __restrict__ off, int nq) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= off[nq]) return;
+    const int k = find_query(off, nq, t);
+    const QueryDev& q = Q[k];
+    if (!q.tile_cnt) return;
+    const int W = (q.s.N + 31) / 32;
+    tile_prefix_row(q.tile_cnt, q.s.pitch, (W + kMaskWords - 1) / kMaskWords, (int)(t - off[k]));
+}
+
+template <int D>
+__global__ void __launch_bounds__(kMaskRows) batch_fill_tile_kernel(const QueryDev* __restrict__ Q,
+                                                                    const long long* __restrict__ off, int nq) {
+    const long long b = blockIdx.x;
+    const int k = find_query(off, nq, b);
+    const QueryDev& q = Q[k];
+    if (!q.tile_cnt || (long long)q.out_row[q.s.N] > q.edge_cap) return;
+    const int rb = (q.s.N + kMaskRows - 1) / kMaskRows;
+    const int t = (int)(b - off[k]);
+    fill_tile_euclid<D>(q.s, q.X, q.mask, q.out_row, q.tile_cnt, q.out_col, q.out_cost, t % rb, t / rb);
 }
 
 namespace {
@@ -269,6 +300,19 @@ cudaError_t batch_cells_fill(int d, const QueryDev* Q, const long long* off_cell
     const size_t smem = cell_tile_smem(d, words);
     if (d == 2) batch_cells_tile_kernel<2, true><<<(unsigned)cells, kCellWarps * 32, smem, st>>>(Q, off_cells, nq, words);
     else if (d == 3) batch_cells_tile_kernel<3, true><<<(unsigned)cells, kCellWarps * 32, smem, st>>>(Q, off_cells, nq, words);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+cudaError_t batch_tile_prefix(const QueryDev* Q, const long long* off_nodes, int nq, long long nodes,
+                              cudaStream_t st) {
+    batch_tile_prefix_kernel<<<(unsigned)((nodes + 255) / 256), 256, 0, st>>>(Q, off_nodes, nq);
+    return cudaGetLastError();
+}
+cudaError_t batch_fill_tiles(int d, const QueryDev* Q, const long long* off_tiles, int nq, long long tiles,
+                             cudaStream_t st) {
+    if (tiles <= 0) return cudaSuccess;
+    if (d == 2) batch_fill_tile_kernel<2><<<(unsigned)tiles, kMaskRows, 0, st>>>(Q, off_tiles, nq);
+    else if (d == 3) batch_fill_tile_kernel<3><<<(unsigned)tiles, kMaskRows, 0, st>>>(Q, off_tiles, nq);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -344,6 +388,7 @@ struct Group {
     std::vector<int> chunk_start, chunk_count, chunk_nodes, chunk_base, chunk_ctl;
     DevBuf lock_base;
     bool any_cells = false;  // some member builds its neighbours with the cell list
+    bool any_tiles = false;  // some member fills its CSR by mask tiles
     int cell_words = 0;      // largest fill buffer (words per warp) of those members
     bool any_halton = false; // some member samples with the Halton sequence
 };
@@ -360,7 +405,7 @@ struct gmt_batch {
     std::vector<float> r;
     std::vector<Group> groups;
     // arena
-    DevBuf X, goal, flags, mask, maskT, counts, rows, edges_i, edges_f, path, ctl, next, slot;
+    DevBuf X, goal, flags, mask, maskT, counts, rows, edges_i, edges_f, path, ctl, next, slot, tcnt;
     DevBuf cells, cell_info;
     DevBuf s_ocost, s_stamp, s_lists;
     DevBuf l_open, l_glist, l_ocost, l_stamp, l_ctl;
@@ -533,6 +578,8 @@ gmt_status enqueue_build_front(gmt_batch* b, cudaStream_t st) {
         BCUDA(batch_sample(g.kind, g.d, Q, g.off_nodes.as<long long>(), nq, g.nodes, g.any_halton, st),
               "batched sample kernel");
         BCUDA(batch_mask(g.kind, g.d, Q, g.off_tiles.as<long long>(), nq, g.tiles, st), "batched pair filter");
+        if (g.any_tiles)
+            BCUDA(batch_tile_prefix(Q, g.off_nodes.as<long long>(), nq, g.nodes, st), "batched tile prefixes");
         if (g.any_cells)
             BCUDA(batch_cells_front(g.d, Q, g.off_nodes.as<long long>(), g.off_cells.as<long long>(), nq, g.nodes,
                                     g.cells, st),
@@ -553,7 +600,12 @@ gmt_status enqueue_build_back(gmt_batch* b, int32_t* parent, float* cost, cudaSt
     for (Group& g : b->groups) {
         const int nq = (int)g.members.size();
         const QueryDev* Q = g.desc.as<QueryDev>();
-        BCUDA(batch_fill(g.kind, g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, st), "batched fill");
+        if (g.kind == GMT_COST_EUCLID) {  // every all-pairs geometric query fills by mask tiles
+            if (g.any_tiles)
+                BCUDA(batch_fill_tiles(g.d, Q, g.off_tiles.as<long long>(), nq, g.tiles, st), "batched tiled fill");
+        } else {
+            BCUDA(batch_fill(g.kind, g.d, Q, g.off_rows.as<long long>(), nq, g.nodes, st), "batched fill");
+        }
         if (g.any_cells)
             BCUDA(batch_cells_fill(g.d, Q, g.off_cells.as<long long>(), nq, g.cells, g.cell_words, st),
                   "batched cells");
@@ -654,8 +706,9 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         g->members.push_back(k);
     }
     // sizes and offsets
-    size_t xs = 0, gs = 0, ms = 0, mts = 0, cs = 0, rs = 0, ps = 0, cls = 0;
-    std::vector<size_t> xo(q), go(q), mo(q), mto(q), co(q), ro(q), po(q), clo(q);
+    size_t xs = 0, gs = 0, ms = 0, mts = 0, cs = 0, rs = 0, ps = 0, cls = 0, ts = 0;
+    std::vector<size_t> xo(q), go(q), mo(q), mto(q), co(q), ro(q), po(q), clo(q), to(q);
+    std::vector<char> use_tiles(q, 0);
     std::vector<CellGrid> cgs(q);
     std::vector<char> use_cells(q, 0);
     b->node_base[0] = 0;
@@ -683,6 +736,10 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
             cls += 2 * (size_t)N + 2 * (size_t)cgs[k].ncells + 1;
         } else {
             mo[k] = ms; ms += (size_t)W * P;
+            if (fill_tiles_apply(Qh.space.kind, Qh.space.dim, N, true)) {
+                use_tiles[k] = 1;
+                to[k] = ts; ts += (size_t)fill_tiles_per_row(N) * P;
+            }
         }
         if (Qh.space.kind != GMT_COST_EUCLID) { mto[k] = mts; mts += (size_t)W * P; }
         co[k] = cs; cs += 2 * (size_t)N;
@@ -693,6 +750,7 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
     BCUDA(b->goal.need(gs), "arena");
     BCUDA(b->flags.need((size_t)q * 4), "arena");
     BCUDA(b->mask.need(ms * 4 + 4), "arena");
+    BCUDA(b->tcnt.need(ts * 4 + 4), "arena");
     BCUDA(b->cells.need(cls * 4 + 4), "arena");
     BCUDA(b->cell_info.need((size_t)q * 2 * 4), "arena");
     BCUDA(b->maskT.need(mts * 4 + 4), "arena");
@@ -738,6 +796,7 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         d.is_goal = b->goal.as<uint8_t>() + go[k];
         d.flags = b->flags.as<int>() + k;
         d.mask = use_cells[k] ? nullptr : b->mask.as<uint32_t>() + mo[k];
+        d.tile_cnt = use_tiles[k] ? b->tcnt.as<int>() + to[k] : nullptr;
         d.use_cells = use_cells[k];
         d.cg = cgs[k];
         if (use_cells[k]) {
@@ -762,12 +821,14 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         std::vector<QueryDev> dq(nq);
         g.max_n = 0; g.max_boxes = 0;
         g.any_cells = false;
+        g.any_tiles = false;
         g.cell_words = 0;
         g.any_halton = false;
         for (int i = 0; i < nq; ++i) {
             const int k = g.members[i];
             const int N = b->N[k], W = (N + 31) / 32;
             g.any_cells = g.any_cells || use_cells[k];
+            g.any_tiles = g.any_tiles || b->qd[k].tile_cnt != nullptr;
             g.any_halton = g.any_halton || queries[k].params.sampler == GMT_SAMPLER_HALTON;
             if (use_cells[k]) g.cell_words = std::max(g.cell_words, cell_fill_words(cgs[k], N));
             const long long tiles =

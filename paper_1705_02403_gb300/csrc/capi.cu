@@ -102,6 +102,7 @@ struct gmt_graph {
     float* in_path = nullptr;      size_t cap_in_path = 0;   // Dubins airplane: [E][4] (t, p, q, word bits)
     uint32_t* mask = nullptr;      size_t cap_mask = 0;
     uint32_t* maskT = nullptr;     size_t cap_maskT = 0;
+    int* tile_cnt = nullptr;       size_t cap_tile_cnt = 0;  // per-tile row counts of the tiled fill
     // [sample flags, max row length, -, fill ticket, cell row overflow, -, -, -]
     int* flags = nullptr;
     // cell-list neighbour build
@@ -164,7 +165,7 @@ struct gmt_graph {
 
     ~gmt_graph() {
         void* dev[] = {X, is_goal, out_row, in_row_own, counts, out_col, out_cost, in_col_own,
-                       in_cost_own, out_tau, in_tau, in_path, mask, maskT, cell_of, cell_sorted, cell_cnt,
+                       in_cost_own, out_tau, in_tau, in_path, mask, maskT, tile_cnt, cell_of, cell_sorted, cell_cnt,
                        cell_start, grid_cnt, grid_start, grid_list, grid_big, halton, ocost, stamp,
                        lists, ctl};
         for (void* p : dev)
@@ -438,6 +439,8 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
     if (params->debug_flags & GMT_DEBUG_CELLS_LIST) cg.list_only = 1;
     if (params->debug_flags & GMT_DEBUG_PAIRS_ALL) cells = false;
     else if (!(params->debug_flags & GMT_DEBUG_PAIRS_CELLS)) cells = cells && cells_pay;
+    // Euclidean graphs of 2 to 4 dimensions fill their CSR by mask tiles
+    const bool tiles = fill_tiles_apply(g->kind, g->d, g->N, false);
     LAUNCH(g->mark(gmt_graph::kPair, 0, st), "event");
     if (cells) {
         GROW(cell_of, N);
@@ -454,10 +457,13 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
                "cell row kernel");
     } else {
         GROW(mask, W * P);
+        if (tiles) {
+            GROW(tile_cnt, (size_t)fill_tiles_per_row(N) * P);
+        }
         // directed costs: the pair filter also writes the transposed matrix
         const bool dir = g->directed();
         LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, dir ? g->maskT : nullptr,
-                                dir ? g->in_count : nullptr, st),
+                                dir ? g->in_count : nullptr, st, tiles ? g->tile_cnt : nullptr),
                "pair filter kernel");
     }
     LAUNCH(g->mark(gmt_graph::kPair, 1, st), "event");
@@ -481,7 +487,11 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
                                                        di_a ? g->in_tau : nullptr, dub_a ? g->in_path : nullptr,
                                                        cap_now}
                                              : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
-        LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, g->flags + 3, st), "fill kernel");
+        if (tiles) {
+            LAUNCH(launch_fill_tiles(sa, g->X, out_dir, g->tile_cnt, st), "fill kernel");
+        } else {
+            LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, g->flags + 3, st), "fill kernel");
+        }
         LAUNCH(g->mark(gmt_graph::kFill, 1, st), "event");
         g->used_cells = false;
         g->E = -1;
@@ -501,8 +511,12 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
         // a row too long to sort in shared memory: the all-pairs test instead
         cells = false;
         GROW(mask, W * P);
+        if (tiles) {
+            GROW(tile_cnt, (size_t)fill_tiles_per_row(N) * P);
+        }
         LAUNCH(cudaMemsetAsync(g->out_count, 0, N * sizeof(int), st), "memset");
-        LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, nullptr, nullptr, st), "pair filter kernel");
+        LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, nullptr, nullptr, st, tiles ? g->tile_cnt : nullptr),
+               "pair filter kernel");
         LAUNCH(launch_scan(g->out_count, g->out_row, g->N, st), "scan kernel");
         LAUNCH(cudaMemcpyAsync(g->h_scalars + 2, g->out_row + N, sizeof(int), cudaMemcpyDeviceToHost, st),
                "edge count readback");
@@ -543,7 +557,11 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
         const FillDir in_dir = directed ? FillDir{g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own,
                                                   di ? g->in_tau : nullptr, dubins ? g->in_path : nullptr, 0}
                                         : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
-        LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, g->flags + 3, st), "fill kernel");
+        if (tiles) {
+            LAUNCH(launch_fill_tiles(sa, g->X, out_dir, g->tile_cnt, st), "fill kernel");
+        } else {
+            LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, g->flags + 3, st), "fill kernel");
+        }
     }
     LAUNCH(g->mark(gmt_graph::kFill, 1, st), "event");
 #undef GROW

@@ -116,12 +116,14 @@ bool make_cell_grid(int kind, int d, const float* lo, const float* hi, float r, 
     while ((double)r * 1.01 * (double)cg->inv_h > 1.0) cg->inv_h = std::nextafter(cg->inv_h, 0.0f);
     cg->ncells = (int)ncells;
     cg->list_only = 0;
-    // measured on one GB300 (Theorem 1 radii, cell tiles): in 2D the cell
-    // list ties with the all-pairs test at 8192 nodes and wins 2x at 16384 on
-    // one graph, and in a batch (where the cell stages' short launches overlap
-    // other queries' work) already pays from 4096; in 3D, with 27 cells of
-    // candidates to sort per tile, it loses at 16384 and wins 2.3x at 32768
-    *pays = frac <= 0.25 && N >= (d == 2 ? (batched ? 4096 : 8192) : 32768);
+    // measured on one GB300 (Theorem 1 radii, cell tiles against the packed
+    // all-pairs test and the tiled fill): on one graph in 2D the cell list
+    // loses at 8192 nodes (0.055 against 0.040 ms) and wins at 16384 (0.069
+    // against 0.087); in a batch (where the cell stages' short launches
+    // overlap other queries' work) it already pays from 4096; in 3D, with 27
+    // cells of candidates to sort per tile, it loses at 16384 (0.216 against
+    // 0.113 ms) and wins at 32768 (0.280 against 0.388)
+    *pays = frac <= 0.25 && N >= (d == 2 ? (batched ? 4096 : 12000) : 32768);
     return true;
 }
 

@@ -170,8 +170,25 @@ __global__ void __launch_bounds__(128) append_kernel(SpaceArgs s, BoxArgs boxes,
 template <int KIND, int D>
 __global__ void __launch_bounds__(kMaskRows) pair_mask_kernel(SpaceArgs s, const float* __restrict__ X,
                                                               uint32_t* __restrict__ mask,
-                                                              int* __restrict__ out_count) {
-    mask_tile<KIND, D>(s, X, mask, out_count, blockIdx.x, blockIdx.y);
+                                                              int* __restrict__ out_count,
+                                                              int* __restrict__ tile_cnt) {
+    mask_tile<KIND, D>(s, X, mask, out_count, blockIdx.x, blockIdx.y, tile_cnt);
+}
+
+__global__ void __launch_bounds__(256) tile_prefix_kernel(int N, int pitch, int nb, int* __restrict__ tile_cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) tile_prefix_row(tile_cnt, pitch, nb, i);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kMaskRows) fill_tile_kernel(SpaceArgs s, const float* __restrict__ X,
+                                                              const uint32_t* __restrict__ mask,
+                                                              const int* __restrict__ row,
+                                                              const int* __restrict__ tile_pre,
+                                                              int* __restrict__ col, float* __restrict__ cost,
+                                                              long long cap) {
+    if (cap > 0 && (long long)__ldg(&row[s.N]) > cap) return;  // uniform: the caller rebuilds
+    fill_tile_euclid<D>(s, X, mask, row, tile_pre, col, cost, blockIdx.x, blockIdx.y);
 }
 
 __global__ void __launch_bounds__(kDIRows, 8) pair_mask_di_kernel(SpaceArgs s, const float* __restrict__ X,
@@ -269,10 +286,20 @@ cudaError_t sample_t(const SpaceArgs& s, BoxArgs b, const BoxGridArgs& grid, voi
     return cudaGetLastError();
 }
 template <int KIND, int D>
-cudaError_t mask_t(const SpaceArgs& s, const float* X, uint32_t* mask, int* cnt, cudaStream_t st) {
-    const int W = (s.N + 31) / 32;
-    dim3 grid((s.N + kMaskRows - 1) / kMaskRows, (W + kMaskWords - 1) / kMaskWords);
-    pair_mask_kernel<KIND, D><<<grid, kMaskRows, 0, st>>>(s, X, mask, cnt);
+cudaError_t mask_t(const SpaceArgs& s, const float* X, uint32_t* mask, int* cnt, int* tile_cnt, cudaStream_t st) {
+    const int W = (s.N + 31) / 32, nb = (W + kMaskWords - 1) / kMaskWords;
+    dim3 grid((s.N + kMaskRows - 1) / kMaskRows, nb);
+    pair_mask_kernel<KIND, D><<<grid, kMaskRows, 0, st>>>(s, X, mask, cnt, tile_cnt);
+    // the per-tile counts become prefixes here, so the fill reads them only
+    // (and a fill run again on the same mask writes the same CSR)
+    if (tile_cnt) tile_prefix_kernel<<<(s.N + 255) / 256, 256, 0, st>>>(s.N, s.pitch, nb, tile_cnt);
+    return cudaGetLastError();
+}
+template <int D>
+cudaError_t fill_tiles_t(const SpaceArgs& s, const float* X, const FillDir& out, int* tile_cnt, cudaStream_t st) {
+    const int W = (s.N + 31) / 32, nb = (W + kMaskWords - 1) / kMaskWords;
+    dim3 grid((s.N + kMaskRows - 1) / kMaskRows, nb);
+    fill_tile_kernel<D><<<grid, kMaskRows, 0, st>>>(s, X, out.mask, out.row, tile_cnt, out.col, out.cost, out.cap);
     return cudaGetLastError();
 }
 template <int KIND, int D>
@@ -345,7 +372,7 @@ cudaError_t launch_append(const SpaceArgs& s, BoxArgs b, const float* src, int s
 }
 
 cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* cnt, uint32_t* maskT,
-                             int* in_count, cudaStream_t st) {
+                             int* in_count, cudaStream_t st, int* tile_cnt) {
     if (s.kind == GMT_COST_DI) {
         const int W = (s.N + 31) / 32;
         dim3 grid((s.N + kDIRows - 1) / kDIRows, (W + kDIWords - 1) / kDIWords);
@@ -358,7 +385,20 @@ cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask,
         pair_mask_dubins_kernel<<<grid, kDubRows, 0, st>>>(s, X, mask, cnt, maskT, in_count);
         return cudaGetLastError();
     }
-    GMT_EUCLID_DIMS(mask_t, s, X, mask, cnt, st)
+    GMT_EUCLID_DIMS(mask_t, s, X, mask, cnt, s.d >= 2 && s.d <= 4 ? tile_cnt : nullptr, st)
+}
+
+int fill_tiles_per_row(int N) {
+    const int W = (N + 31) / 32;
+    return (W + kMaskWords - 1) / kMaskWords;
+}
+
+cudaError_t launch_fill_tiles(const SpaceArgs& s, const float* X, const FillDir& out, int* tile_cnt,
+                              cudaStream_t st) {
+    if (s.d == 2) return fill_tiles_t<2>(s, X, out, tile_cnt, st);
+    if (s.d == 3) return fill_tiles_t<3>(s, X, out, tile_cnt, st);
+    if (s.d == 4) return fill_tiles_t<4>(s, X, out, tile_cnt, st);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st) {

@@ -337,11 +337,12 @@ __device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsig
 // expression of sq_dist (0 + t_0^2 = t_0^2 exactly), so the bits are the same.
 // Columns past the last node hold +inf (an infinite distance: no edge), so
 // the inner loop tests no bounds; the diagonal pair i = j is cleared once per
-// word.
+// word.  tile_cnt (or NULL): receives the row's edge count in this tile's
+// columns at [by * pitch + i], for the tiled fill.
 template <int D>
 __device__ __forceinline__ void mask_tile_euclid4(const SpaceArgs& s, const float* __restrict__ X,
                                                   uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
-                                                  int by) {
+                                                  int by, int* __restrict__ tile_cnt) {
     static_assert(D >= 2 && D <= 4, "two to four axes in two float4s per column pair");
     constexpr int kPairs = kMaskWords * 16;
     __shared__ float4 tab[kPairs];                  // axes 0 and 1
@@ -401,15 +402,85 @@ __device__ __forceinline__ void mask_tile_euclid4(const SpaceArgs& s, const floa
         cnt += __popc(bits);
     }
     if (cnt) atomicAdd(&out_count[i], cnt);
+    if (tile_cnt) tile_cnt[(size_t)by * s.pitch + i] = cnt;
+}
+
+// Tiled fill of a Euclidean graph of 2 to 4 dimensions (after
+// mask_tile_euclid4 with tile_cnt and the row scan): tile_prefix_row turns a
+// row's per-tile counts into exclusive prefixes (nb tiles of kMaskWords words
+// each); then fill_tile_euclid, one block per mask tile with the tile's
+// columns staged in shared memory, writes each row's columns of the tile, in
+// ascending order, from row[i] + prefix, with cost sqrt(d2) of the same
+// expression as edge_cost (so the same bits), and no gather of the samples
+// per edge.
+__device__ __forceinline__ void tile_prefix_row(int* __restrict__ tile_cnt, int pitch, int nb, int i) {
+    constexpr int kChunk = 16;  // loads issued together, then the chunk's prefixes stored
+    int acc = 0;
+    for (int b0 = 0; b0 < nb; b0 += kChunk) {
+        int c[kChunk];
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) c[u] = b0 + u < nb ? tile_cnt[(size_t)(b0 + u) * pitch + i] : 0;
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+            if (b0 + u < nb) tile_cnt[(size_t)(b0 + u) * pitch + i] = acc;
+            acc += c[u];
+        }
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void fill_tile_euclid(const SpaceArgs& s, const float* __restrict__ X,
+                                                 const uint32_t* __restrict__ mask, const int* __restrict__ row,
+                                                 const int* __restrict__ tile_pre, int* __restrict__ col,
+                                                 float* __restrict__ cost, int bx, int by) {
+    static_assert(D >= 2 && D <= 4, "float4 columns");
+    __shared__ float4 tile[kMaskWords * 32];
+    const int i = bx * kMaskRows + threadIdx.x;
+    const int w0 = by * kMaskWords;
+    const int j0 = w0 * 32;
+    for (int idx = threadIdx.x; idx < kMaskWords * 32; idx += kMaskRows) {
+        const int j = j0 + idx;
+        float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int a = 0; a < D; ++a) c[a] = j < s.N ? X[(size_t)a * s.pitch + j] : 0.0f;
+        tile[idx] = make_float4(c[0], c[1], c[2], c[3]);
+    }
+    __syncthreads();
+    if (i >= s.N) return;
+    float xi[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int a = 0; a < D; ++a) xi[a] = X[(size_t)a * s.pitch + i];
+    const int W = (s.N + 31) / 32;
+    int pos = row[i] + tile_pre[(size_t)by * s.pitch + i];
+    uint32_t words[kMaskWords];  // all loads of the row's words issued at once
+#pragma unroll
+    for (int ww = 0; ww < kMaskWords; ++ww) words[ww] = w0 + ww < W ? mask[(size_t)(w0 + ww) * s.pitch + i] : 0u;
+#pragma unroll
+    for (int ww = 0; ww < kMaskWords; ++ww) {
+        for (uint32_t bits = words[ww]; bits; bits &= bits - 1) {
+            const int jt = ww * 32 + __ffs(bits) - 1;
+            const float4 q = tile[jt];
+            const float xj[4] = {q.x, q.y, q.z, q.w};
+            float d2 = 0.0f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float t = xj[a] - xi[a];
+                d2 = d2 + t * t;
+            }
+            col[pos] = j0 + jt;
+            cost[pos] = __fsqrt_rn(d2);
+            ++pos;
+        }
+    }
 }
 
 // One block of kMaskRows threads: rows bx*kMaskRows.., words by*kMaskWords..
 template <int KIND, int D>
 __device__ __forceinline__ void mask_tile(const SpaceArgs& s, const float* __restrict__ X,
                                           uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
-                                          int by) {
+                                          int by, int* __restrict__ tile_cnt = nullptr) {
     if constexpr (KIND == GMT_COST_EUCLID && D >= 2 && D <= 4) {
-        mask_tile_euclid4<D>(s, X, mask, out_count, bx, by);
+        mask_tile_euclid4<D>(s, X, mask, out_count, bx, by, tile_cnt);
         return;
     }
     __shared__ float tile[D][kMaskWords * 32];

@@ -96,8 +96,19 @@ cudaError_t launch_sample(const SpaceArgs& s, BoxArgs boxes, const BoxGridArgs& 
 // maskT, in_count (double integrator and Dubins airplane; may be NULL): the
 // same launch also writes the transposed bit matrix and the in-row counts (no
 // transpose launch).
+// tile_cnt (Euclidean graphs of 2 to 4 dimensions, may be NULL): receives,
+// for launch_fill_tiles, the number of each row's edges in the tiles of
+// kMaskWords mask words before each tile, [tile][pitch].
 cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* out_count,
-                             uint32_t* maskT, int* in_count, cudaStream_t st);
+                             uint32_t* maskT, int* in_count, cudaStream_t st, int* tile_cnt = nullptr);
+// Does the tiled fill apply (Euclidean, 2 to 4 dimensions; on one graph from
+// 4096 nodes, below which its extra prefix launch costs more than it saves;
+// in a batch always, one launch serving every query), and how many tiles of
+// mask words a row has.
+inline bool fill_tiles_apply(int kind, int d, int N, bool batched) {
+    return kind == GMT_COST_EUCLID && d >= 2 && d <= 4 && (batched || N >= 4096);
+}
+int fill_tiles_per_row(int N);
 cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st);
 // Both directions' row offsets in one launch (count1 may be NULL: one scan).
 // host_out (may be NULL; device-mapped host memory) receives flags[0],
@@ -122,6 +133,12 @@ struct FillDir {
 // ticket: one device int, zero at launch (the blocks' work counter).
 cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, int* ticket,
                         cudaStream_t st);
+// The out-CSR of a Euclidean graph of 2 to 4 dimensions from the mask and the
+// per-tile prefixes of launch_pair_mask: one block per mask tile, columns
+// staged in shared memory.  Reads its inputs only, so it may run again.  A
+// graph whose edge count exceeds out.cap (> 0) writes nothing.
+cudaError_t launch_fill_tiles(const SpaceArgs& s, const float* X, const FillDir& out, int* tile_cnt,
+                              cudaStream_t st);
 
 // Cell-list neighbour search (geometric graphs, 2 or 3 dimensions): a uniform
 // grid over the position bounds whose cell side h is at least 1.01 r, so a

@@ -265,18 +265,29 @@ def test_iteration_limit_per_query(O, mode):
 
 
 def test_autotune_keeps_results(O):
+    # The autotuner times every scheme and shape on the prepared batch; its
+    # runs leave the CSR and the later trees equal to the oracle's.
     from paper_1705_02403_gb300 import _native as N
     from paper_1705_02403_gb300.planner import BatchPlanner
     bp = BatchPlanner(mixed_batch(seed=2, q=12))
     infos = bp.plan()
+    refs = [oracle_of(O, pb) for pb in bp.problems]
     c, t, ms = N.gmt_batch_autotune(bp.batch)
+    # the autotuner ran the build's back half (fill, plan) many times on the
+    # same samples and masks: the CSR it leaves is still the oracle's
+    for k in range(len(bp.problems)):
+        v = bp.view(k)
+        g = refs[k][2].csr()
+        assert v["E"] == refs[k][2].num_edges, k
+        assert np.array_equal(v["out_col"].cpu().numpy(), g.out_col), k
+        assert np.array_equal(bits(v["out_cost"].cpu().numpy()), bits(g.out_cost)), k
     mode, c2, t2 = N.gmt_batch_get_launch(bp.batch)
     assert mode in (N.BATCH_TEAMS, N.BATCH_LOCKSTEP, N.BATCH_POOL) and t2 == t and c2 == c
     assert (c == 0) == (mode in (N.BATCH_LOCKSTEP, N.BATCH_POOL))
     assert c in (0, 1, 2, 4, 8, 16) and t in (128, 256, 512, 1024) and ms > 0
     infos2 = bp.plan()
     for k in range(len(bp.problems)):
-        check_query(O, bp, k, infos2)
+        check_query(O, bp, k, infos2, ref=refs[k])
 
 
 @pytest.mark.parametrize("mode", ["pool", "teams", "lockstep"])

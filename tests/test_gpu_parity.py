@@ -131,13 +131,14 @@ def same_csr(a, b):
 
 
 @pytest.mark.parametrize("case", ["2d_small_r", "2d_ragged", "3d_thm1", "3d_boxes", "2d_dense_fallback",
-                                  "3d_dense_fallback", "2d_two_nodes"])
+                                  "3d_dense_fallback", "2d_two_nodes", "2d_tiled_fill", "3d_tiled_fill"])
 def test_cell_list_and_all_pairs_give_the_oracle_csr(O, P, case):
     # The 2D/3D geometric neighbour build picks a cell list when the radius is
     # small against the domain.  Forced either way, and with either way of
     # ordering a row (bitmap or sorted list), it must give the oracle's CSR bit
     # for bit; rows longer than the list (dense graphs) fall back to the
-    # all-pairs test.
+    # all-pairs test.  All-pairs builds of at least 4096 nodes fill the CSR
+    # by mask tiles (per-tile prefixes), smaller ones row by row.
     from paper_1705_02403_gb300 import _native as N
     pb = {"2d_small_r": envgen.geometric(51, d=2, n=3000, nbox=8, r=0.03),
           "2d_ragged": envgen.geometric(52, d=2, n=1777, nbox=5, r=0.05),
@@ -145,7 +146,10 @@ def test_cell_list_and_all_pairs_give_the_oracle_csr(O, P, case):
           "3d_boxes": envgen.geometric(54, d=3, n=2500, nbox=40, r=0.11),
           "2d_dense_fallback": DENSE[0],
           "3d_dense_fallback": DENSE[1],
-          "2d_two_nodes": envgen.geometric(55, d=2, n=1, nbox=0, r=0.05)}[case]
+          "2d_two_nodes": envgen.geometric(55, d=2, n=1, nbox=0, r=0.05),
+          # all-pairs builds of at least 4096 nodes fill the CSR by mask tiles
+          "2d_tiled_fill": envgen.geometric(57, d=2, n=6100, nbox=10, r=0.0),
+          "3d_tiled_fill": envgen.geometric(58, d=3, n=4500, nbox=20, r=0.0)}[case]
     cells = csr_of(P, pb, N.GMT_DEBUG_PAIRS_CELLS)
     listed = csr_of(P, pb, N.GMT_DEBUG_PAIRS_CELLS | N.GMT_DEBUG_CELLS_LIST)
     pairs = csr_of(P, pb, N.GMT_DEBUG_PAIRS_ALL)
@@ -446,6 +450,27 @@ def test_asynchronous_builds(O, P):
         G = {"parent": pl.parent.cpu().numpy(), "cost": pl.cost.cpu().numpy(), "info": info,
              "path": pl.path.cpu().numpy()[:info["path_len"]]}
         v = pl.view()
+        G.update(X=v.X.cpu().numpy(), goal=v.is_goal.cpu().numpy(), E=v.E, out_row=v.out_row.cpu().numpy(),
+                 out_col=v.out_col.cpu().numpy(), out_cost=v.out_cost.cpu().numpy(), in_row=v.in_row.cpu().numpy(),
+                 in_col=v.in_col.cpu().numpy(), in_cost=v.in_cost.cpu().numpy())
+        assert_same(O, G, *oracle_run(O, pb))
+    # the same with all-pairs geometric graphs filled by mask tiles (3D, at
+    # least 4096 nodes): a growing graph is rebuilt by the plan, a smaller one fits
+    t_small = envgen.geometric(35, d=3, n=4200, nbox=12, r=0.0)
+    t_big = envgen.geometric(36, d=3, n=6000, nbox=12, r=0.0)
+    pt = P.Planner(t_small).build()
+    for pb in (t_big, t_small):
+        pt.pb = pb
+        pt.space, pt.goal, pt.params = P.space_struct(pb), P.goal_struct(pb), P.params_struct(pb)
+        pt.boxes, pt._box_tensors = P.boxes_on_device(pb)
+        pt.parent = torch.empty(pb.N, dtype=torch.int32, device="cuda")
+        pt.cost = torch.empty(pb.N, dtype=torch.float32, device="cuda")
+        pt.path = torch.empty(pb.N, dtype=torch.int32, device="cuda")
+        pt.build(asynchronous=True)
+        info = pt.plan()
+        G = {"parent": pt.parent.cpu().numpy(), "cost": pt.cost.cpu().numpy(), "info": info,
+             "path": pt.path.cpu().numpy()[:info["path_len"]]}
+        v = pt.view()
         G.update(X=v.X.cpu().numpy(), goal=v.is_goal.cpu().numpy(), E=v.E, out_row=v.out_row.cpu().numpy(),
                  out_col=v.out_col.cpu().numpy(), out_cost=v.out_cost.cpu().numpy(), in_row=v.in_row.cpu().numpy(),
                  in_col=v.in_col.cpu().numpy(), in_cost=v.in_cost.cpu().numpy())
