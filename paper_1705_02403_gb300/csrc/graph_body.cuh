@@ -412,7 +412,9 @@ __device__ __forceinline__ void mask_tile_euclid4(const SpaceArgs& s, const floa
 // columns staged in shared memory, writes each row's columns of the tile, in
 // ascending order, from row[i] + prefix, with cost sqrt(d2) of the same
 // expression as edge_cost (so the same bits), and no gather of the samples
-// per edge.
+// per edge.  Each lane loads its row's words; a warp whose rows hold many
+// columns in the tile (small graphs) then writes them row by row with a lane
+// per column (coalesced stores), else each lane writes its own row.
 __device__ __forceinline__ void tile_prefix_row(int* __restrict__ tile_cnt, int pitch, int nb, int i) {
     constexpr int kChunk = 16;  // loads issued together, then the chunk's prefixes stored
     int acc = 0;
@@ -428,6 +430,20 @@ __device__ __forceinline__ void tile_prefix_row(int* __restrict__ tile_cnt, int 
     }
 }
 
+// The tiled fill's warps write row by row, a lane per column, when their rows
+// average at least this many columns in the tile; else each lane its own row.
+constexpr int kFillTileCoop = 48;
+
+// Position of the m-th (from 0) set bit of x (x has more than m set bits):
+// the largest p with fewer than m + 1 set bits below it, by binary search.
+__device__ __forceinline__ int select_bit(uint32_t x, int m) {
+    int p = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+        if (__popc(x & ((1u << (p + step)) - 1u)) <= m) p += step;
+    return p;
+}
+
 template <int D>
 __device__ __forceinline__ void fill_tile_euclid(const SpaceArgs& s, const float* __restrict__ X,
                                                  const uint32_t* __restrict__ mask, const int* __restrict__ row,
@@ -435,6 +451,7 @@ __device__ __forceinline__ void fill_tile_euclid(const SpaceArgs& s, const float
                                                  float* __restrict__ cost, int bx, int by) {
     static_assert(D >= 2 && D <= 4, "float4 columns");
     __shared__ float4 tile[kMaskWords * 32];
+    const int lane = threadIdx.x & 31;
     const int i = bx * kMaskRows + threadIdx.x;
     const int w0 = by * kMaskWords;
     const int j0 = w0 * 32;
@@ -446,30 +463,79 @@ __device__ __forceinline__ void fill_tile_euclid(const SpaceArgs& s, const float
         tile[idx] = make_float4(c[0], c[1], c[2], c[3]);
     }
     __syncthreads();
-    if (i >= s.N) return;
-    float xi[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-    for (int a = 0; a < D; ++a) xi[a] = X[(size_t)a * s.pitch + i];
+    // each lane loads its row's words of the tile (coalesced over the rows)
+    const bool row_ok = i < s.N;
     const int W = (s.N + 31) / 32;
-    int pos = row[i] + tile_pre[(size_t)by * s.pitch + i];
-    uint32_t words[kMaskWords];  // all loads of the row's words issued at once
-#pragma unroll
-    for (int ww = 0; ww < kMaskWords; ++ww) words[ww] = w0 + ww < W ? mask[(size_t)(w0 + ww) * s.pitch + i] : 0u;
+    uint32_t words[kMaskWords];
+    int cnt = 0;
 #pragma unroll
     for (int ww = 0; ww < kMaskWords; ++ww) {
-        for (uint32_t bits = words[ww]; bits; bits &= bits - 1) {
-            const int jt = ww * 32 + __ffs(bits) - 1;
+        words[ww] = row_ok && w0 + ww < W ? mask[(size_t)(w0 + ww) * s.pitch + i] : 0u;
+        cnt += __popc(words[ww]);
+    }
+    float xi[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) xi[a] = row_ok ? X[(size_t)a * s.pitch + i] : 0.0f;
+    const int base = cnt > 0 ? row[i] + tile_pre[(size_t)by * s.pitch + i] : 0;
+    const unsigned live0 = __ballot_sync(0xffffffffu, cnt > 0);
+    int sum = cnt;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if (sum < kFillTileCoop * __popc(live0)) {
+        // few columns per row (large graphs): each lane writes its own row
+        int pos = base;
+#pragma unroll
+        for (int ww = 0; ww < kMaskWords; ++ww) {
+            for (uint32_t bits = words[ww]; bits; bits &= bits - 1) {
+                const int jt = ww * 32 + __ffs(bits) - 1;
+                const float4 q = tile[jt];
+                const float xj[4] = {q.x, q.y, q.z, q.w};
+                float d2 = 0.0f;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const float tt = xj[a] - xi[a];
+                    d2 = d2 + tt * tt;
+                }
+                col[pos] = j0 + jt;
+                cost[pos] = __fsqrt_rn(d2);
+                ++pos;
+            }
+        }
+        return;
+    }
+    // ...else the warp writes the rows that have edges here one after the
+    // other, a lane per column: consecutive lanes, consecutive positions
+    for (unsigned live = live0; live; live &= live - 1) {
+        const int src = __ffs(live) - 1;
+        uint32_t wv[kMaskWords];
+        int ex[kMaskWords + 1];
+        ex[0] = 0;
+#pragma unroll
+        for (int ww = 0; ww < kMaskWords; ++ww) {
+            wv[ww] = __shfl_sync(0xffffffffu, words[ww], src);
+            ex[ww + 1] = ex[ww] + __popc(wv[ww]);
+        }
+        const int b0 = __shfl_sync(0xffffffffu, base, src);
+        float xr[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) xr[a] = __shfl_sync(0xffffffffu, xi[a], src);
+        for (int t = lane; t < ex[kMaskWords]; t += 32) {
+            int k = 0, m = t;
+            uint32_t wk = wv[0];
+#pragma unroll
+            for (int ww = 1; ww < kMaskWords; ++ww)
+                if (t >= ex[ww]) { k = ww; wk = wv[ww]; m = t - ex[ww]; }
+            const int jt = k * 32 + select_bit(wk, m);
             const float4 q = tile[jt];
             const float xj[4] = {q.x, q.y, q.z, q.w};
             float d2 = 0.0f;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                const float t = xj[a] - xi[a];
-                d2 = d2 + t * t;
+                const float tt = xj[a] - xr[a];
+                d2 = d2 + tt * tt;
             }
-            col[pos] = j0 + jt;
-            cost[pos] = __fsqrt_rn(d2);
-            ++pos;
+            col[b0 + t] = j0 + jt;
+            cost[b0 + t] = __fsqrt_rn(d2);
         }
     }
 }
