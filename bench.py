@@ -381,7 +381,7 @@ def run_gpu(args, rank, world, local_rank):
 # 256-query batch in its autotuned shape, from the ncu capture summarised in
 # profiles/plan_batch_kernel_uneven_256.md.  None until that kernel is
 # captured again after a change.
-PLAN_BATCH_DRAM_BYTES = 1_727_480_576
+PLAN_BATCH_DRAM_BYTES = 1_712_954_624
 
 
 def bench_batched(dev, flush, reps=5, cpu_queries=8):
