@@ -412,9 +412,9 @@ __device__ __forceinline__ void mask_tile_euclid4(const SpaceArgs& s, const floa
 // columns staged in shared memory, writes each row's columns of the tile, in
 // ascending order, from row[i] + prefix, with cost sqrt(d2) of the same
 // expression as edge_cost (so the same bits), and no gather of the samples
-// per edge.  Each lane loads its row's words; a warp whose rows hold many
-// columns in the tile (small graphs) then writes them row by row with a lane
-// per column (coalesced stores), else each lane writes its own row.
+// per edge.  Each lane loads its row's words; the warp then deals all its
+// rows' columns of the tile to its lanes in order, so no lane idles while
+// another walks a long row, and a row's columns go to consecutive lanes.
 __device__ __forceinline__ void tile_prefix_row(int* __restrict__ tile_cnt, int pitch, int nb, int i) {
     constexpr int kChunk = 16;  // loads issued together, then the chunk's prefixes stored
     int acc = 0;
@@ -429,10 +429,6 @@ __device__ __forceinline__ void tile_prefix_row(int* __restrict__ tile_cnt, int 
         }
     }
 }
-
-// The tiled fill's warps write row by row, a lane per column, when their rows
-// average at least this many columns in the tile; else each lane its own row.
-constexpr int kFillTileCoop = 48;
 
 // Position of the m-th (from 0) set bit of x (x has more than m set bits):
 // the largest p with fewer than m + 1 set bits below it, by binary search.
@@ -450,8 +446,13 @@ __device__ __forceinline__ void fill_tile_euclid(const SpaceArgs& s, const float
                                                  const int* __restrict__ tile_pre, int* __restrict__ col,
                                                  float* __restrict__ cost, int bx, int by) {
     static_assert(D >= 2 && D <= 4, "float4 columns");
+    constexpr int kWarps = kMaskRows / 32;
     __shared__ float4 tile[kMaskWords * 32];
-    const int lane = threadIdx.x & 31;
+    __shared__ uint32_t swords[kWarps][32][kMaskWords];  // each row's words of the tile
+    __shared__ int sex[kWarps][33];                       // exclusive prefix of the rows' column counts
+    __shared__ int sbase[kWarps][32];                     // each row's first position for the tile
+    __shared__ float4 sxi[kWarps][32];                    // each row's coordinates
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = bx * kMaskRows + threadIdx.x;
     const int w0 = by * kMaskWords;
     const int j0 = w0 * 32;
@@ -462,81 +463,60 @@ __device__ __forceinline__ void fill_tile_euclid(const SpaceArgs& s, const float
         for (int a = 0; a < D; ++a) c[a] = j < s.N ? X[(size_t)a * s.pitch + j] : 0.0f;
         tile[idx] = make_float4(c[0], c[1], c[2], c[3]);
     }
-    __syncthreads();
     // each lane loads its row's words of the tile (coalesced over the rows)
     const bool row_ok = i < s.N;
     const int W = (s.N + 31) / 32;
-    uint32_t words[kMaskWords];
     int cnt = 0;
 #pragma unroll
     for (int ww = 0; ww < kMaskWords; ++ww) {
-        words[ww] = row_ok && w0 + ww < W ? mask[(size_t)(w0 + ww) * s.pitch + i] : 0u;
-        cnt += __popc(words[ww]);
+        const uint32_t w = row_ok && w0 + ww < W ? mask[(size_t)(w0 + ww) * s.pitch + i] : 0u;
+        swords[warp][lane][ww] = w;
+        cnt += __popc(w);
     }
-    float xi[D];
+    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int a = 0; a < D; ++a) xi[a] = row_ok ? X[(size_t)a * s.pitch + i] : 0.0f;
-    const int base = cnt > 0 ? row[i] + tile_pre[(size_t)by * s.pitch + i] : 0;
-    const unsigned live0 = __ballot_sync(0xffffffffu, cnt > 0);
-    int sum = cnt;
+    for (int a = 0; a < D; ++a) c[a] = row_ok ? X[(size_t)a * s.pitch + i] : 0.0f;
+    sxi[warp][lane] = make_float4(c[0], c[1], c[2], c[3]);
+    sbase[warp][lane] = cnt > 0 ? row[i] + tile_pre[(size_t)by * s.pitch + i] : 0;
+    int incl = cnt;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-    if (sum < kFillTileCoop * __popc(live0)) {
-        // few columns per row (large graphs): each lane writes its own row
-        int pos = base;
-#pragma unroll
-        for (int ww = 0; ww < kMaskWords; ++ww) {
-            for (uint32_t bits = words[ww]; bits; bits &= bits - 1) {
-                const int jt = ww * 32 + __ffs(bits) - 1;
-                const float4 q = tile[jt];
-                const float xj[4] = {q.x, q.y, q.z, q.w};
-                float d2 = 0.0f;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const float tt = xj[a] - xi[a];
-                    d2 = d2 + tt * tt;
-                }
-                col[pos] = j0 + jt;
-                cost[pos] = __fsqrt_rn(d2);
-                ++pos;
-            }
-        }
-        return;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
     }
-    // ...else the warp writes the rows that have edges here one after the
-    // other, a lane per column: consecutive lanes, consecutive positions
-    for (unsigned live = live0; live; live &= live - 1) {
-        const int src = __ffs(live) - 1;
-        uint32_t wv[kMaskWords];
-        int ex[kMaskWords + 1];
-        ex[0] = 0;
+    sex[warp][lane] = incl - cnt;
+    if (lane == 31) sex[warp][32] = incl;
+    __syncthreads();  // the staged columns; the warp's row tables
+    // the warp's columns in (row, word, bit) order, dealt to its lanes: entry
+    // e of row r goes to position sbase[r] + (e - sex[r]), so each row's
+    // columns come out ascending and consecutive lanes write consecutive
+    // positions of a row
+    const int total = sex[warp][32];
+    for (int e = lane; e < total; e += 32) {
+        int r = 0;  // the row: the last one whose prefix is <= e
 #pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+            if (sex[warp][r + step] <= e) r += step;
+        int m = e - sex[warp][r], k = 0;
+        uint32_t wk = swords[warp][r][0];
         for (int ww = 0; ww < kMaskWords; ++ww) {
-            wv[ww] = __shfl_sync(0xffffffffu, words[ww], src);
-            ex[ww + 1] = ex[ww] + __popc(wv[ww]);
+            wk = swords[warp][r][ww];
+            const int cw = __popc(wk);
+            if (m < cw) { k = ww; break; }
+            m -= cw;
         }
-        const int b0 = __shfl_sync(0xffffffffu, base, src);
-        float xr[D];
+        const int jt = k * 32 + select_bit(wk, m);
+        const float4 q = tile[jt], p = sxi[warp][r];
+        const float xj[4] = {q.x, q.y, q.z, q.w}, xr[4] = {p.x, p.y, p.z, p.w};
+        float d2 = 0.0f;
 #pragma unroll
-        for (int a = 0; a < D; ++a) xr[a] = __shfl_sync(0xffffffffu, xi[a], src);
-        for (int t = lane; t < ex[kMaskWords]; t += 32) {
-            int k = 0, m = t;
-            uint32_t wk = wv[0];
-#pragma unroll
-            for (int ww = 1; ww < kMaskWords; ++ww)
-                if (t >= ex[ww]) { k = ww; wk = wv[ww]; m = t - ex[ww]; }
-            const int jt = k * 32 + select_bit(wk, m);
-            const float4 q = tile[jt];
-            const float xj[4] = {q.x, q.y, q.z, q.w};
-            float d2 = 0.0f;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                const float tt = xj[a] - xr[a];
-                d2 = d2 + tt * tt;
-            }
-            col[b0 + t] = j0 + jt;
-            cost[b0 + t] = __fsqrt_rn(d2);
+        for (int a = 0; a < D; ++a) {
+            const float tt = xj[a] - xr[a];
+            d2 = d2 + tt * tt;
         }
+        const int pos = sbase[warp][r] + (e - sex[warp][r]);
+        col[pos] = j0 + jt;
+        cost[pos] = __fsqrt_rn(d2);
     }
 }
 
