@@ -66,14 +66,18 @@ __device__ __forceinline__ int find_query(const long long* __restrict__ off, int
     return lo;
 }
 
+// SampleFree of a group's nodes, one thread per node (any queries): the
+// draws of sample_node, with the box test of an attempt taken over every box
+// without early exit (one uniform loop per warp instead of lanes leaving it at
+// different boxes).  Each node's sample is sample_node's.
 template <int D, int DP>
 __global__ void __launch_bounds__(128) batch_sample_kernel(const QueryDev* __restrict__ Q,
                                                            const long long* __restrict__ off, int nq) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= off[nq]) return;
-    const int k = find_query(off, nq, t);
+    const long long tn = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tn >= off[nq]) return;
+    const int k = find_query(off, nq, tn);
     const QueryDev& q = Q[k];
-    const int v = (int)(t - off[k]);
+    const int v = (int)(tn - off[k]);
     if (v >= q.s.n_sampled) {  // an appended sample
         append_node<D, DP>(q.s, q.boxes, q.extra, q.extra_pitch, q.s.n_sampled, q.X, q.is_goal, q.flags,
                            v - q.s.n_sampled);
@@ -81,7 +85,17 @@ __global__ void __launch_bounds__(128) batch_sample_kernel(const QueryDev* __res
     }
     if (q.s.sampler == GMT_SAMPLER_HALTON) return;  // batch_halton_kernel
     const BoxGridArgs no_grid{};
-    sample_node<D, DP>(q.s, q.boxes, no_grid, q.X, q.is_goal, q.flags, v);
+    if (v == 0) {
+        sample_node<D, DP>(q.s, q.boxes, no_grid, q.X, q.is_goal, q.flags, 0);
+        return;
+    }
+    float x[D];
+    bool ok = false;
+    for (int t = 0; t < q.s.max_attempts && !ok; ++t) ok = sample_attempt<D, DP, true>(q.s, q.boxes, no_grid, v, t, x);
+    if (!ok) atomicOr(q.flags, kSampleExhausted);
+#pragma unroll
+    for (int a = 0; a < D; ++a) q.X[(size_t)a * q.s.pitch + v] = x[a];
+    q.is_goal[v] = in_goal_ball(x, q.s.gd, q.s.gc, q.s.grho) ? 1 : 0;
 }
 
 // One block per query of the group; queries that sample with Philox return.

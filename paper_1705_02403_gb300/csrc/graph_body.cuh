@@ -65,6 +65,47 @@ __device__ __forceinline__ void sample_node(const SpaceArgs& s, const BoxArgs& b
     is_goal[k] = in_goal_ball(x, s.gd, s.gc, s.grho) ? 1 : 0;
 }
 
+// Attempt t of SampleFree for node k >= 1 (the draws of sample_node): x
+// receives the attempt's state; returns whether it is accepted (node 1: in
+// the goal region and in X; every node: outside every box).  FLAT: the box
+// test visits every box with no early exit and no short-circuit (the same
+// answer, no divergence inside it).
+template <int D, int DP, bool FLAT>
+__device__ __forceinline__ bool sample_attempt(const SpaceArgs& s, const BoxArgs& boxes, const BoxGridArgs& grid,
+                                               int k, int t, float* x) {
+    uint32_t w[((D + 3) / 4) * 4];
+#pragma unroll
+    for (int blk = 0; blk < (D + 3) / 4; ++blk) {
+        const Ctr4 c = philox4x32_10(Ctr4{(uint32_t)k, (uint32_t)t, s.stream, (uint32_t)blk}, s.key0, s.key1);
+        w[4 * blk + 0] = c.x; w[4 * blk + 1] = c.y; w[4 * blk + 2] = c.z; w[4 * blk + 3] = c.w;
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const float u = unit_float(w[a]);
+        float l = s.lo[a], h = s.hi[a];
+        if (k == 1 && a < s.gd) { l = s.gc[a] - s.grho; h = s.gc[a] + s.grho; }
+        x[a] = l + u * (h - l);
+    }
+    if (k == 1) {
+        bool inb = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) inb = inb && s.lo[a] <= x[a] && x[a] <= s.hi[a];
+        if (!inb || !in_goal_ball(x, s.gd, s.gc, s.grho)) return false;
+    }
+    if (FLAT && !grid.use) {
+        bool hit = false;
+        for (int b = 0; b < boxes.count; ++b) {
+            bool in = true;
+#pragma unroll
+            for (int a = 0; a < DP; ++a)
+                in = in & (boxes.lo[b * DP + a] <= x[a]) & (x[a] <= boxes.hi[b * DP + a]);
+            hit = hit | in;
+        }
+        return !hit;
+    }
+    return !point_in_boxes<DP>(x, boxes, grid);
+}
+
 // The same sample drawn by a group of G consecutive lanes (G divides 32):
 // every lane of the group computes the same attempt (the same Philox words),
 // and the box tests of an attempt are dealt round-robin over the group's
