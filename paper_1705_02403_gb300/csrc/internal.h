@@ -276,12 +276,14 @@ __host__ __device__ inline void assign_plan_lists(PlanArgs& a, int* base, size_t
 // Largest box count staged in shared memory (2 * count * DP floats).
 __host__ __device__ constexpr int smem_box_cap(int dp) { return 4096 / dp; }
 // Dynamic shared memory of a plan launch: the staged boxes, or, when it is
-// larger and within 48 KB, the parent array of N nodes (read for the path
-// walk once the wavefront is over).
+// larger and fits within 48 KB beside the kernel's own static shared memory
+// (at most kPlanStaticSmem bytes), the parent array of N nodes (read for the
+// path walk once the wavefront is over).
+constexpr size_t kPlanStaticSmem = 256;
 inline size_t plan_smem_bytes(int staged_boxes, int dp, int N) {
     const size_t boxes = (size_t)2 * staged_boxes * dp * sizeof(float);
     const size_t parents = (size_t)N * sizeof(int);
-    return parents <= 48 * 1024 && parents > boxes ? parents : boxes;
+    return parents + kPlanStaticSmem <= 48 * 1024 && parents > boxes ? parents : boxes;
 }
 
 // Per-team scratch of the batched wavefront: team t uses the slices

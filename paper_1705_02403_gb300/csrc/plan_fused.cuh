@@ -322,12 +322,24 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
         __syncwarp();  // the lane groups leave the queue apart; the barrier wants whole warps
         if (!(ok = team.sync(ctl))) break;
 
-        // termination test (Alg. 1), next threshold
-        const int goal = __ldcg(&ctl->goal3[set]);
-        const unsigned long long gk = __ldcg(&ctl->gk3[set]);
-        const int kept = (int)(gk >> 32), ngrp = (int)(gk & 0xffffffffu);
-        const int opened = __ldcg(&ctl->new3[set]);
-        const unsigned mk = min(__ldcg(&ctl->min_keep3[set]), __ldcg(&ctl->min_new3[set]));
+        // termination test (Alg. 1), next threshold: one thread per CTA reads
+        // the iteration's counters and shares them through shared memory (a
+        // read by every warp of the team would queue hundreds of requests on
+        // the same L2 line)
+        __shared__ unsigned term[5];
+        if (threadIdx.x == 0) {
+            const unsigned long long gk = __ldcg(&ctl->gk3[set]);
+            term[0] = (unsigned)__ldcg(&ctl->goal3[set]);
+            term[1] = (unsigned)(gk >> 32);
+            term[2] = (unsigned)(gk & 0xffffffffu);
+            term[3] = (unsigned)__ldcg(&ctl->new3[set]);
+            term[4] = min(__ldcg(&ctl->min_keep3[set]), __ldcg(&ctl->min_new3[set]));
+        }
+        __syncthreads();
+        const int goal = (int)term[0];
+        const int kept = (int)term[1], ngrp = (int)term[2];
+        const int opened = (int)term[3];
+        const unsigned mk = term[4];
         ++it;
         if (goal) { status = GMT_OK; break; }
         if (kept + opened == 0) { status = GMT_NO_PATH; break; }
