@@ -279,7 +279,7 @@ __host__ __device__ constexpr int smem_box_cap(int dp) { return 4096 / dp; }
 // larger and fits within 48 KB beside the kernel's own static shared memory
 // (at most kPlanStaticSmem bytes), the parent array of N nodes (read for the
 // path walk once the wavefront is over).
-constexpr size_t kPlanStaticSmem = 256;
+constexpr size_t kPlanStaticSmem = 512;
 inline size_t plan_smem_bytes(int staged_boxes, int dp, int N) {
     const size_t boxes = (size_t)2 * staged_boxes * dp * sizeof(float);
     const size_t parents = (size_t)N * sizeof(int);

@@ -467,12 +467,15 @@ __global__ void __launch_bounds__(1024, 1) plan_batch_kernel(const PlanArgs* __r
         assign_plan_lists(A, scratch.lists + team_id * plan_list_stride(nm), nm);
         unsigned dyn_smem;
         asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
+        // counters in the control block: in this kernel (four bodies inlined)
+        // the shared copy cost registers and measured no faster
         constexpr int W = kBatchPullLanes;
-        if (ALL_KINDS && A.kind == GMT_COST_DI) plan_body_fused<Team, GMT_COST_DI, 3, W>(A, team, sbox, dyn_smem);
+        constexpr bool SH = false;
+        if (ALL_KINDS && A.kind == GMT_COST_DI) plan_body_fused<Team, GMT_COST_DI, 3, W, SH>(A, team, sbox, dyn_smem);
         else if (ALL_KINDS && A.kind == GMT_COST_DUBINS)
-            plan_body_fused<Team, GMT_COST_DUBINS, 3, W>(A, team, sbox, dyn_smem);
-        else if (A.dp == 2) plan_body_fused<Team, GMT_COST_EUCLID, 2, W>(A, team, sbox, dyn_smem);
-        else plan_body_fused<Team, GMT_COST_EUCLID, 3, W>(A, team, sbox, dyn_smem);
+            plan_body_fused<Team, GMT_COST_DUBINS, 3, W, SH>(A, team, sbox, dyn_smem);
+        else if (A.dp == 2) plan_body_fused<Team, GMT_COST_EUCLID, 2, W, SH>(A, team, sbox, dyn_smem);
+        else plan_body_fused<Team, GMT_COST_EUCLID, 3, W, SH>(A, team, sbox, dyn_smem);
         team.sync(nullptr);
     }
 }

@@ -19,6 +19,7 @@ __device__ __forceinline__ float ldcg_f(const float* p) { return __ldcg(p); }
 // Every team also names its CTAs (cta() in [0, ctas())), so that work can be
 // dealt to CTAs round-robin.
 struct BlockTeam {
+    static constexpr bool kSharedCtl = true;  // the team's counters can live in shared memory
     __device__ __forceinline__ int id() const { return blockIdx.x; }
     __device__ __forceinline__ int cta() const { return 0; }
     __device__ __forceinline__ int ctas() const { return 1; }
@@ -35,6 +36,7 @@ struct BlockTeam {
 // the wait gives up, records GMT_ERR_TIMEOUT and returns false, so the kernel
 // ends with an error status instead of hanging.
 struct GridTeam {
+    static constexpr bool kSharedCtl = false;
     unsigned expected;
     int spin_limit;
     __device__ __forceinline__ int id() const { return 0; }
@@ -73,6 +75,7 @@ struct GridTeam {
 // scope); it cannot wait forever because every thread of the cluster reaches
 // every barrier (all exits from the iteration loop are uniform).
 struct ClusterTeam {
+    static constexpr bool kSharedCtl = true;
     __device__ __forceinline__ static unsigned cta_rank() {
         unsigned r;
         asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -113,6 +116,119 @@ struct LaneGroup {
     }
     __device__ __forceinline__ static bool any(bool p) { return __any_sync(mask(), p); }
 };
+
+// ------------------------------------------------------------ team counters
+// The wavefront's team-wide counters (PlanCtl's group, queue and commit
+// words): in the control block in global memory (SH = false), or in a copy in
+// the shared memory of the team's first CTA (SH = true: a CTA or a cluster),
+// reached through the cluster's shared window, where a dependent atomic takes
+// about a third of a global one's latency (measured on GB300: 261 against 707
+// cycles; a load 219 against 307).  Field addresses are those of the control
+// block; `base` maps them into the copy.  The ordering of the memory model
+// holds in both: barrier.cluster (or __syncthreads) orders the copy's
+// accesses across the team, and the fences of the global path also order the
+// queue's global entries against these counters (acquire/release at cluster
+// scope covers both state spaces).
+template <bool SH>
+struct TeamCtl {
+    PlanCtl* g;
+    unsigned base;  // SH: shared::cluster address of the copy in CTA 0
+    template <class T>
+    __device__ __forceinline__ unsigned at(const T* f) const {
+        return base + (unsigned)((const char*)f - (const char*)g);
+    }
+    __device__ __forceinline__ int add(int* f, int v) const {
+        if (!SH) return atomicAdd(f, v);
+        int r;
+        asm volatile("atom.shared::cluster.add.u32 %0, [%1], %2;" : "=r"(r) : "r"(at(f)), "r"(v) : "memory");
+        return r;
+    }
+    __device__ __forceinline__ unsigned add(unsigned* f, unsigned v) const {
+        if (!SH) return atomicAdd(f, v);
+        unsigned r;
+        asm volatile("atom.shared::cluster.add.u32 %0, [%1], %2;" : "=r"(r) : "r"(at(f)), "r"(v) : "memory");
+        return r;
+    }
+    __device__ __forceinline__ unsigned long long add(unsigned long long* f, unsigned long long v) const {
+        if (!SH) return atomicAdd(f, v);
+        unsigned long long r;
+        asm volatile("atom.shared::cluster.add.u64 %0, [%1], %2;" : "=l"(r) : "r"(at(f)), "l"(v) : "memory");
+        return r;
+    }
+    __device__ __forceinline__ void min(unsigned* f, unsigned v) const {
+        if (!SH) { atomicMin(f, v); return; }
+        unsigned r;
+        asm volatile("atom.shared::cluster.min.u32 %0, [%1], %2;" : "=r"(r) : "r"(at(f)), "r"(v) : "memory");
+    }
+    // 64-bit minimum: a compare-and-swap loop in the copy (on GB300 the
+    // native 64-bit atomic minimum through the cluster's shared window lost
+    // updates under contention in a test of 16 CTAs, while 64-bit add and CAS
+    // were exact); every failed CAS returns a smaller value, so the loop ends.
+    __device__ __forceinline__ void min(unsigned long long* f, unsigned long long v) const {
+        if (!SH) { atomicMin(f, v); return; }
+        const unsigned a = at(f);
+        unsigned long long cur;
+        asm volatile("ld.relaxed.cluster.shared::cluster.u64 %0, [%1];" : "=l"(cur) : "r"(a) : "memory");
+        while (v < cur) {
+            unsigned long long prev;
+            asm volatile("atom.shared::cluster.cas.b64 %0, [%1], %2, %3;" : "=l"(prev) : "r"(a), "l"(cur), "l"(v) : "memory");
+            if (prev == cur) break;
+            cur = prev;
+        }
+    }
+    __device__ __forceinline__ void cas(int* f, int cmp, int v) const {
+        if (!SH) { atomicCAS(f, cmp, v); return; }
+        int r;
+        asm volatile("atom.shared::cluster.cas.b32 %0, [%1], %2, %3;" : "=r"(r) : "r"(at(f)), "r"(cmp), "r"(v) : "memory");
+    }
+    // relaxed (volatile) load; acquire load at cluster scope
+    __device__ __forceinline__ int ld(const int* f) const {
+        if (!SH) return ld_volatile(f);
+        int r;
+        asm volatile("ld.relaxed.cluster.shared::cluster.u32 %0, [%1];" : "=r"(r) : "r"(at(f)) : "memory");
+        return r;
+    }
+    __device__ __forceinline__ unsigned ld(const unsigned* f) const {
+        if (!SH) return __ldcg(f);
+        unsigned r;
+        asm volatile("ld.relaxed.cluster.shared::cluster.u32 %0, [%1];" : "=r"(r) : "r"(at(f)) : "memory");
+        return r;
+    }
+    __device__ __forceinline__ unsigned long long ld(const unsigned long long* f) const {
+        if (!SH) return __ldcg(f);
+        unsigned long long r;
+        asm volatile("ld.relaxed.cluster.shared::cluster.u64 %0, [%1];" : "=l"(r) : "r"(at(f)) : "memory");
+        return r;
+    }
+    __device__ __forceinline__ unsigned ld_acq(const unsigned* f) const {
+        if (!SH) return ld_acquire(f);
+        unsigned r;
+        asm volatile("ld.acquire.cluster.shared::cluster.u32 %0, [%1];" : "=r"(r) : "r"(at(f)) : "memory");
+        return r;
+    }
+    // plain stores (the writer then passes a team barrier before any reader)
+    __device__ __forceinline__ void st(int* f, int v) const {
+        if (!SH) { *f = v; return; }
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(at(f)), "r"(v) : "memory");
+    }
+    __device__ __forceinline__ void st(unsigned* f, unsigned v) const {
+        if (!SH) { *f = v; return; }
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(at(f)), "r"(v) : "memory");
+    }
+    __device__ __forceinline__ void st(unsigned long long* f, unsigned long long v) const {
+        if (!SH) { *f = v; return; }
+        asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(at(f)), "l"(v) : "memory");
+    }
+};
+
+// The shared::cluster address of `p` (this CTA's shared memory) in CTA `rank`
+// of the cluster (a launch without clusters is a cluster of one CTA).
+__device__ __forceinline__ unsigned cluster_map(const void* p, unsigned rank) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
 
 // ---------------------------------------------------------------- edge check
 // Both checks first keep only the boxes that meet an axis-aligned bound of

@@ -26,6 +26,13 @@
 
 namespace gmtk {
 
+// Shared memory of the fused body, one allocation per kernel however many
+// instantiations of the body it inlines: the copy of the team's counters
+// (read by the team through the cluster's shared window) and the counters of
+// the termination test shared within a CTA.
+static __shared__ PlanCtl fused_team_ctl;
+static __shared__ unsigned fused_term[5];
+
 struct FusedCounts {
     unsigned long long push = 0, pull = 0;
     unsigned checks = 0, failed = 0, computed = 0, tree = 0;
@@ -36,10 +43,10 @@ struct FusedCounts {
 // commit: x joins the tree and opens in the next snapshot.  One group of W
 // lanes (the whole warp, or half of it: then the warp's two halves pull two
 // candidates side by side).
-template <int KIND, int DP, int W>
-__device__ __forceinline__ void fused_pull(const PlanArgs& A, int x, const float* ocur, float* onext, int2* nxt,
-                                           int set, int p, const float* blo, const float* bhi, int nbox,
-                                           FusedCounts& cnt) {
+template <int KIND, int DP, int W, bool SH>
+__device__ __forceinline__ void fused_pull(const PlanArgs& A, const TeamCtl<SH>& tc, int x, const float* ocur,
+                                           float* onext, int2* nxt, int set, int p, const float* blo,
+                                           const float* bhi, int nbox, FusedCounts& cnt) {
     constexpr int D = KIND == GMT_COST_DI ? 6 : (KIND == GMT_COST_DUBINS ? 4 : DP);
     using LG = LaneGroup<W>;
     const int lane = LG::lane();
@@ -64,7 +71,7 @@ __device__ __forceinline__ void fused_pull(const PlanArgs& A, int x, const float
     // the group node that pushed x is an open in-neighbour, so be >= 0; the
     // guard keeps a broken invariant from reading out of bounds
     if (be < 0) {
-        if (lane == 0) { ++cnt.checks; ++cnt.failed; atomicCAS(&ctl->error, 0, (int)GMT_ERR_CUDA); }
+        if (lane == 0) { ++cnt.checks; ++cnt.failed; tc.cas(&ctl->error, 0, (int)GMT_ERR_CUDA); }
         return;
     }
     float sy[D];
@@ -106,11 +113,11 @@ __device__ __forceinline__ void fused_pull(const PlanArgs& A, int x, const float
             A.parent[x] = by;
             A.stamp[x] = INT_MAX;
             onext[x] = bc;
-            const int s = atomicAdd(&ctl->new3[set], 1);
+            const int s = tc.add(&ctl->new3[set], 1);
             nxt[N - 1 - s] = make_int2(x, __float_as_int(bc));
-            atomicMin(&ctl->min_new3[set], float_key(bc));
+            tc.min(&ctl->min_new3[set], float_key(bc));
             ++cnt.tree;
-            if (x_goal) atomicMin(&ctl->goal_key, ((unsigned long long)float_key(bc) << 32) | (unsigned)x);
+            if (x_goal) tc.min(&ctl->goal_key, ((unsigned long long)float_key(bc) << 32) | (unsigned)x);
         } else {
             ++cnt.failed;
         }
@@ -120,9 +127,12 @@ __device__ __forceinline__ void fused_pull(const PlanArgs& A, int x, const float
 
 // sbox_bytes: shared memory at sbox for staged boxes and, once the wavefront is
 // over, the copy of the parent array.  A.ocost holds 2 N floats.  W: lanes
-// per candidate pull (32, or 16 for two pulls per warp).
-template <class Team, int KIND, int DP, int W = 32>
+// per candidate pull (32, or 16 for two pulls per warp).  SH: the team's
+// counters in a copy in CTA 0's shared memory (a CTA or a cluster) rather
+// than in the control block.
+template <class Team, int KIND, int DP, int W = 32, bool SH = Team::kSharedCtl>
 __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& team, float* sbox, size_t sbox_bytes) {
+    static_assert(!SH || Team::kSharedCtl, "shared counters need a CTA or a cluster team");
     const int nbs = A.boxes.count <= smem_box_cap(DP) ? A.boxes.count : 0;
     for (int t = threadIdx.x; t < nbs * DP; t += blockDim.x) {
         sbox[t] = A.boxes.lo[t];
@@ -134,6 +144,9 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
     const int nbox = A.boxes.count;
 
     PlanCtl* ctl = A.ctl;
+    // the team's counters: a copy in CTA 0's shared memory for a CTA or a
+    // cluster, else the control block
+    const TeamCtl<SH> tc{ctl, SH ? cluster_map(&fused_team_ctl, 0) : 0u};
     const int rank = team.rank(), size = team.size();
     if (rank == 0) {
         ctl->error = 0;
@@ -174,17 +187,20 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
     }
     if (rank == 0) {
         A.list_open[0][0] = make_int2(0, __float_as_int(0.0f));
+        tc.st(&ctl->error, 0);
         for (int k = 0; k < 2; ++k) {
-            ctl->cand_count[k] = ctl->ticket[k] = 0;
-            ctl->pushed[k] = 0u;
+            tc.st(&ctl->cand_count[k], 0);
+            tc.st(&ctl->ticket[k], 0);
+            tc.st(&ctl->pushed[k], 0u);
         }
         for (int k = 0; k < 3; ++k) {
-            ctl->gk3[k] = 0ull;
-            ctl->new3[k] = 0;
-            ctl->min_keep3[k] = ctl->min_new3[k] = INF_KEY;
-            ctl->goal3[k] = 0;
+            tc.st(&ctl->gk3[k], 0ull);
+            tc.st(&ctl->new3[k], 0);
+            tc.st(&ctl->min_keep3[k], INF_KEY);
+            tc.st(&ctl->min_new3[k], INF_KEY);
+            tc.st(&ctl->goal3[k], 0);
         }
-        ctl->goal_key = A.is_goal[0] ? 0ull : ~0ull;
+        tc.st(&ctl->goal_key, A.is_goal[0] ? 0ull : ~0ull);
     }
     bool ok = team.sync(ctl);
 
@@ -206,14 +222,16 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
         const float* ocur = A.ocost + (size_t)p * N;
         float* onext = A.ocost + (size_t)(p ^ 1) * N;
         if (rank == 0) {
-            ctl->gk3[set1] = 0ull;
-            ctl->new3[set1] = 0;
-            ctl->min_keep3[set1] = ctl->min_new3[set1] = INF_KEY;
-            ctl->goal3[set1] = 0;
+            tc.st(&ctl->gk3[set1], 0ull);
+            tc.st(&ctl->new3[set1], 0);
+            tc.st(&ctl->min_keep3[set1], INF_KEY);
+            tc.st(&ctl->min_new3[set1], INF_KEY);
+            tc.st(&ctl->goal3[set1], 0);
             // the next iteration's queue (its previous user, iteration i - 1,
             // finished with it before the last barrier)
-            ctl->cand_count[p ^ 1] = ctl->ticket[p ^ 1] = 0;
-            ctl->pushed[p ^ 1] = 0u;
+            tc.st(&ctl->cand_count[p ^ 1], 0);
+            tc.st(&ctl->ticket[p ^ 1], 0);
+            tc.st(&ctl->pushed[p ^ 1], 0u);
         }
         // the previous group is closed from the next iteration on (it still
         // was open in the buffer being rebuilt)
@@ -236,20 +254,20 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
                 } else if (t >= nk) {
                     onext[e.x] = __int_as_float(e.y);                  // opened in i - 1, stays open
                 }
-                if (in_g && A.is_goal[e.x]) ctl->goal3[set] = 1;
+                if (in_g && A.is_goal[e.x]) tc.st(&ctl->goal3[set], 1);
             }
             const unsigned mg = __ballot_sync(0xffffffffu, in_g), mkeep = __ballot_sync(0xffffffffu, keep);
             const unsigned below = (1u << lane) - 1u;
             if (mg | mkeep) {
                 unsigned long long base = 0;
                 if (lane == 0)
-                    base = atomicAdd(&ctl->gk3[set], ((unsigned long long)__popc(mkeep) << 32) | __popc(mg));
+                    base = tc.add(&ctl->gk3[set], ((unsigned long long)__popc(mkeep) << 32) | __popc(mg));
                 base = __shfl_sync(0xffffffffu, base, 0);
                 if (in_g) G[(int)(base & 0xffffffffu) + __popc(mg & below)] = e.x;
                 if (keep) nxt[(int)(base >> 32) + __popc(mkeep & below)] = e;
                 const unsigned kmin =
                     __reduce_min_sync(0xffffffffu, keep ? float_key(__int_as_float(e.y)) : INF_KEY);
-                if (lane == 0 && kmin != INF_KEY) atomicMin(&ctl->min_keep3[set], kmin);
+                if (lane == 0 && kmin != INF_KEY) tc.min(&ctl->min_keep3[set], kmin);
             }
             // push each group node of the warp: its unexplored out-neighbours are
             // claimed for this iteration and queued
@@ -279,7 +297,7 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
                     }
                     if (total == 0) continue;
                     int slot = 0;
-                    if (lane == 0) slot = atomicAdd(&ctl->cand_count[p], total);
+                    if (lane == 0) slot = tc.add(&ctl->cand_count[p], total);
                     slot = __shfl_sync(0xffffffffu, slot, 0);
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
@@ -294,20 +312,20 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
         __syncwarp();
         if (lane == 0) {
             __threadfence();
-            atomicAdd(&ctl->pushed[p], 1u);
+            tc.add(&ctl->pushed[p], 1u);
         }
         for (;;) {
             int x = -1;
             if ((lane & (W - 1)) == 0) {
-                const int t = atomicAdd(&ctl->ticket[p], 1);
+                const int t = tc.add(&ctl->ticket[p], 1);
                 if (t < N) {
                     for (int spins = 0;; ++spins) {
                         x = ld_volatile(&A.list_cand[t]);
                         if (x >= 0) break;
                         // the queue is complete once every warp has pushed
-                        if (ld_acquire(&ctl->pushed[p]) == nwarps && t >= ld_volatile(&ctl->cand_count[p])) break;
+                        if (tc.ld_acq(&ctl->pushed[p]) == nwarps && t >= tc.ld(&ctl->cand_count[p])) break;
                         if (spins > spin_limit) {
-                            atomicCAS(&ctl->error, 0, (int)GMT_ERR_TIMEOUT);
+                            tc.cas(&ctl->error, 0, (int)GMT_ERR_TIMEOUT);
                             break;
                         }
                         __nanosleep(32);
@@ -317,7 +335,7 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
             }
             x = __shfl_sync(LaneGroup<W>::mask(), x, 0, W);
             if (x < 0) break;
-            fused_pull<KIND, DP, W>(A, x, ocur, onext, nxt, set, p, blo, bhi, nbox, cnt);
+            fused_pull<KIND, DP, W, SH>(A, tc, x, ocur, onext, nxt, set, p, blo, bhi, nbox, cnt);
         }
         __syncwarp();  // the lane groups leave the queue apart; the barrier wants whole warps
         if (!(ok = team.sync(ctl))) break;
@@ -326,14 +344,14 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
         // the iteration's counters and shares them through shared memory (a
         // read by every warp of the team would queue hundreds of requests on
         // the same L2 line)
-        __shared__ unsigned term[5];
+        unsigned* term = fused_term;
         if (threadIdx.x == 0) {
-            const unsigned long long gk = __ldcg(&ctl->gk3[set]);
-            term[0] = (unsigned)__ldcg(&ctl->goal3[set]);
+            const unsigned long long gk = tc.ld(&ctl->gk3[set]);
+            term[0] = (unsigned)tc.ld(&ctl->goal3[set]);
             term[1] = (unsigned)(gk >> 32);
             term[2] = (unsigned)(gk & 0xffffffffu);
-            term[3] = (unsigned)__ldcg(&ctl->new3[set]);
-            term[4] = min(__ldcg(&ctl->min_keep3[set]), __ldcg(&ctl->min_new3[set]));
+            term[3] = (unsigned)tc.ld(&ctl->new3[set]);
+            term[4] = min(tc.ld(&ctl->min_keep3[set]), tc.ld(&ctl->min_new3[set]));
         }
         __syncthreads();
         const int goal = (int)term[0];
@@ -361,6 +379,10 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
             theta = (float)i * A.delta;
         }
     }
+
+    // the copy of the counters in CTA 0 has been read for the last time by
+    // every CTA before any of them leaves
+    if (SH) team.sync(ctl);
 
     // ---- result: counters (every commit happened before the last barrier),
     // the returned path
@@ -393,14 +415,15 @@ __device__ __forceinline__ void plan_body_fused(const PlanArgs& A, const Team& t
         __syncthreads();
     }
     if (rank == 0) {
-        const int err = ld_volatile(&ctl->error);
+        const int err = tc.ld(&ctl->error);
         ctl->status = err ? err : status;
+        ctl->goal_key = tc.ld(&ctl->goal_key);  // the host reads the goal's cost from it
         ctl->iters = it;
         ctl->final_i = (int)i;
         ctl->goal_node = -1;
         ctl->path_len = 0;
         if (ok && status == GMT_OK) {
-            const int g = (int)(ctl->goal_key & 0xffffffffu);
+            const int g = (int)(tc.ld(&ctl->goal_key) & 0xffffffffu);
             ctl->goal_node = g;
             auto parent_of = [&](int v) { return par_in_smem ? spar[v] : ldcg_i(&A.parent[v]); };
             int len = 1, v = g;
