@@ -41,7 +41,7 @@ METRIC = "ms/plan p50/p99 & edges checked/s; learned+batched vs plain at equal p
 # ncu captures summarised in profiles/plan_kernel_double_integrator_6d_n4096.md
 # and profiles/plan_kernel_geometric_2d_n1024.md.
 # Set to None whenever plan_kernel changes until it is captured again.
-PLAN_KERNEL_DRAM_BYTES = {"di6": 2224128, "geo2d": None}
+PLAN_KERNEL_DRAM_BYTES = {"di6": 2224640, "geo2d": None}
 
 
 def parse():
@@ -381,7 +381,7 @@ def run_gpu(args, rank, world, local_rank):
 # 256-query batch in its autotuned shape, from the ncu capture summarised in
 # profiles/plan_batch_kernel_uneven_256.md.  None until that kernel is
 # captured again after a change.
-PLAN_BATCH_DRAM_BYTES = 1_712_954_624
+PLAN_BATCH_DRAM_BYTES = 1_712_398_848
 
 
 def bench_batched(dev, flush, reps=5, cpu_queries=8):
