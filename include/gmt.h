@@ -309,7 +309,11 @@ gmt_status gmt_batch_get_view(const gmt_batch* batch, int32_t k, gmt_graph_view*
  *   GMT_BATCH_TEAMS: one persistent launch for every query of the batch; a
  *     team (a CTA or a cluster) runs one query at a time, one team barrier per
  *     Algorithm 1 iteration (double-buffered open-set snapshot; candidates
- *     are pulled from a team-wide queue as soon as they are claimed).
+ *     are pulled from a team-wide queue as soon as they are claimed).  With
+ *     one-CTA teams, when the largest query's wavefront state fits in a CTA's
+ *     shared memory (about 36 bytes per node), each CTA keeps its query's
+ *     whole state there (two barriers per iteration, every step but the CSR
+ *     and sample reads on chip).
  *   GMT_BATCH_LOCKSTEP: one cooperative grid runs up to 512 queries at once,
  *     one Algorithm 1 iteration of every live query per grid step (two
  *     bounded grid barriers per step), so small groups of many queries fill

@@ -568,10 +568,10 @@ void plan_shape(const gmt_batch* b, int* cluster, int* threads, int* teams) {
     int t = b->threads > 0 ? b->threads : (b->tuned_threads > 0 ? b->tuned_threads : 512);
     const size_t smem = batch_smem(b);
     const bool all = pool_all_kinds(b);
-    int n = plan_batch_max_teams(t, c, smem, all);
+    int n = plan_batch_max_teams(t, c, smem, b->max_n, true, all);
     while (n <= 0 && c > 1) {
         c /= 2;
-        n = plan_batch_max_teams(t, c, smem, all);
+        n = plan_batch_max_teams(t, c, smem, b->max_n, true, all);
     }
     *cluster = c;
     *threads = t;
@@ -683,7 +683,8 @@ gmt_status enqueue_build_back(gmt_batch* b, int32_t* parent, float* cost, cudaSt
         sc.lists = b->s_lists.as<int>();
         sc.max_nodes = b->max_n;
         BCUDA(launch_plan_batch(b->p_args.as<PlanArgs>(), b->p_order.as<int>(), b->q, b->next.as<int>(),
-                                b->slot.as<int>(), sc, teams, threads, cluster, batch_smem(b), pool_all_kinds(b), st),
+                                b->slot.as<int>(), sc, teams, threads, cluster, batch_smem(b), b->max_n,
+                                pool_all_kinds(b), st),
               "batched plan kernel");
     }
     BCUDA(record_plan_event(b->ev_plan[1], st), "event");
@@ -1072,7 +1073,8 @@ gmt_status prepare(gmt_batch* b, int q, const gmt_query* queries, int32_t* paren
         const size_t smem = batch_smem(b);
         const bool all = pool_all_kinds(b);
         for (int c : {1, 2, 4, 8, 16})
-            for (int t : {256, 512, 1024}) max_teams = std::max(max_teams, plan_batch_max_teams(t, c, smem, all));
+            for (int t : {256, 512, 1024})
+                max_teams = std::max(max_teams, plan_batch_max_teams(t, c, smem, max_n, false, all));
     }
     cudaGetLastError();
     if (max_teams <= 0) return bfail(GMT_ERR_CUDA, "batched plan kernel cannot be resident");

@@ -389,13 +389,19 @@ int plan_max_cluster(int kind, int dp, int threads);
 // Persistent batched wavefront (one barrier per iteration) over the `nq`
 // queries queries[order[0 .. nq)] of any kinds, taken in that order from the
 // device counter `next` (zeroed by the caller); `slot` holds one int per team.
-// cluster <= 1: teams are single CTAs.  smem: dynamic shared memory per CTA
-// (the largest plan_smem_bytes of the queries).  all_kinds = false: every
-// query is geometric (a kernel with fewer registers).
+// cluster <= 1: teams are single CTAs, which keep the whole wavefront state
+// in shared memory when the largest query (max_n nodes) fits
+// (batch_state_fits; no scratch used), else use the scratch.  smem: dynamic
+// shared memory per CTA (the largest plan_smem_bytes of the queries).
+// all_kinds = false: every query is geometric (a kernel with fewer
+// registers).  plan_batch_max_teams: resident teams of a shape; with
+// smem_state = false, of the scratch-using kernels only (for sizing the
+// scratch).
 cudaError_t launch_plan_batch(const PlanArgs* queries, const int* order, int nq, int* next, int* slot,
                               const BatchScratch& scratch, int teams, int threads, int cluster, size_t smem,
-                              bool all_kinds, cudaStream_t st);
-int plan_batch_max_teams(int threads, int cluster, size_t smem, bool all_kinds);
+                              int max_n, bool all_kinds, cudaStream_t st);
+int plan_batch_max_teams(int threads, int cluster, size_t smem, int max_n, bool smem_state, bool all_kinds);
+bool batch_state_fits(size_t smem, int max_n);
 // plan_multi.cu: one cooperative grid of `blocks` CTAs advances all `nq`
 // queries of one (kind, dp) group together (nq <= kLockMaxQueries).  The
 // queries' PlanCtl blocks must be zeroed before the launch.

@@ -480,6 +480,50 @@ __global__ void __launch_bounds__(1024, 1) plan_batch_kernel(const PlanArgs* __r
     }
 }
 
+// Persistent batched wavefront with one CTA per query whose state lives in
+// its shared memory (the batch's one-CTA teams when the largest query fits):
+// the CTA takes the next query from the device queue and runs the body of
+// plan_kernel_smem on it (control block, snapshot, stamps and lists after
+// region0 bytes of staged boxes / parent copy), then copies the control block
+// out.
+template <bool ALL_KINDS>
+__global__ void __launch_bounds__(1024, 1) plan_batch_smem_kernel(const PlanArgs* __restrict__ queries,
+                                                               const int* __restrict__ order, int nq,
+                                                               int* __restrict__ next, unsigned region0) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int kq;
+    unsigned char* base = reinterpret_cast<unsigned char*>(smem);
+    PlanCtl* sctl = reinterpret_cast<PlanCtl*>(base + region0);
+    for (;;) {
+        if (threadIdx.x == 0) kq = atomicAdd(next, 1);
+        __syncthreads();
+        const int k = kq;
+        if (k >= nq) break;
+        PlanArgs A = queries[order[k]];
+        const size_t N = (size_t)A.N;
+        PlanCtl* gctl = A.ctl;
+        float* socost = reinterpret_cast<float*>(base + region0 + kSmemCtlBytes);
+        int* sstamp = reinterpret_cast<int*>(socost + N);
+        int* slists = reinterpret_cast<int*>(base + region0 + kSmemCtlBytes + smem_round16(8 * N));
+        for (int t = threadIdx.x; t < (int)(sizeof(PlanCtl) / sizeof(int)); t += blockDim.x)
+            reinterpret_cast<int*>(sctl)[t] = 0;
+        __syncthreads();
+        A.ctl = sctl;
+        A.ocost = socost;
+        A.stamp = sstamp;
+        assign_plan_lists(A, slists, N);
+        if (ALL_KINDS && A.kind == GMT_COST_DI) plan_body<BlockTeam, GMT_COST_DI, 3, true>(A, BlockTeam{}, smem, region0);
+        else if (ALL_KINDS && A.kind == GMT_COST_DUBINS)
+            plan_body<BlockTeam, GMT_COST_DUBINS, 3, true>(A, BlockTeam{}, smem, region0);
+        else if (A.dp == 2) plan_body<BlockTeam, GMT_COST_EUCLID, 2, true>(A, BlockTeam{}, smem, region0);
+        else plan_body<BlockTeam, GMT_COST_EUCLID, 3, true>(A, BlockTeam{}, smem, region0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < (int)(sizeof(PlanCtl) / sizeof(int)); t += blockDim.x)
+            reinterpret_cast<int*>(gctl)[t] = reinterpret_cast<const int*>(sctl)[t];
+        __syncthreads();  // the next query reuses the shared memory
+    }
+}
+
 // ----------------------------------------------------------------- launcher
 namespace {
 template <int KIND, int DP>
@@ -589,7 +633,15 @@ namespace {
 template <bool ALL_KINDS>
 cudaError_t plan_batch_t(const PlanArgs* queries, const int* order, int nq, int* next, int* slot,
                          const BatchScratch& scratch, int teams, int threads, int cluster, size_t smem,
-                         cudaStream_t st) {
+                         int max_n, cudaStream_t st) {
+    if (cluster <= 1 && batch_state_fits(smem, max_n)) {
+        const size_t region0 = smem_round16(smem), total = plan_smem_state_bytes(region0, max_n);
+        auto kern = plan_batch_smem_kernel<ALL_KINDS>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total);
+        if (e != cudaSuccess) return e;
+        kern<<<teams, threads, total, st>>>(queries, order, nq, next, (unsigned)region0);
+        return cudaGetLastError();
+    }
     if (cluster <= 1) {
         auto kern = plan_batch_kernel<BlockTeam, ALL_KINDS>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -617,10 +669,21 @@ cudaError_t plan_batch_t(const PlanArgs* queries, const int* order, int nq, int*
 }
 
 template <bool ALL_KINDS>
-int batch_teams_t(int threads, int cluster, size_t smem) {
+int batch_teams_t(int threads, int cluster, size_t smem, int max_n) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cluster <= 1 && batch_state_fits(smem, max_n)) {
+        const size_t total = plan_smem_state_bytes(smem_round16(smem), max_n);
+        auto kern = plan_batch_smem_kernel<ALL_KINDS>;
+        int per_sm = 0;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, total) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return per_sm * sms;
+    }
     if (cluster <= 1) {
         auto kern = plan_batch_kernel<BlockTeam, ALL_KINDS>;
         int per_sm = 0;
@@ -659,13 +722,24 @@ int batch_teams_t(int threads, int cluster, size_t smem) {
 
 cudaError_t launch_plan_batch(const PlanArgs* queries, const int* order, int nq, int* next, int* slot,
                               const BatchScratch& scratch, int teams, int threads, int cluster, size_t smem,
-                              bool all_kinds, cudaStream_t st) {
-    return all_kinds ? plan_batch_t<true>(queries, order, nq, next, slot, scratch, teams, threads, cluster, smem, st)
-                     : plan_batch_t<false>(queries, order, nq, next, slot, scratch, teams, threads, cluster, smem, st);
+                              int max_n, bool all_kinds, cudaStream_t st) {
+    return all_kinds ? plan_batch_t<true>(queries, order, nq, next, slot, scratch, teams, threads, cluster, smem,
+                                          max_n, st)
+                     : plan_batch_t<false>(queries, order, nq, next, slot, scratch, teams, threads, cluster, smem,
+                                           max_n, st);
 }
 
-int plan_batch_max_teams(int threads, int cluster, size_t smem, bool all_kinds) {
-    return all_kinds ? batch_teams_t<true>(threads, cluster, smem) : batch_teams_t<false>(threads, cluster, smem);
+int plan_batch_max_teams(int threads, int cluster, size_t smem, int max_n, bool smem_state, bool all_kinds) {
+    const int mn = smem_state ? max_n : INT_MAX;  // INT_MAX nodes never fit: the scratch kernels
+    return all_kinds ? batch_teams_t<true>(threads, cluster, smem, mn) : batch_teams_t<false>(threads, cluster, smem, mn);
+}
+
+bool batch_state_fits(size_t smem, int max_n) {
+    if (max_n <= 0 || max_n > (1 << 24)) return false;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return plan_smem_state_bytes(smem_round16(smem), max_n) + kPlanStaticSmem <= (size_t)optin;
 }
 
 int plan_max_coresident_blocks(int kind, int dp, int threads) {
