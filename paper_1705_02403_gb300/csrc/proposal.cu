@@ -38,18 +38,24 @@ struct EnvBoxes {
 
 // X[b, (i G + j) G + k] = 1 if the centre of voxel (i, j, k) lies in a box of env b.
 constexpr int kVoxBoxes = 256;  // boxes staged in shared memory per pass
+constexpr int kVoxRows = 256;   // voxel rows (i, j) per block
 
-// Block (x, b): voxels of environment b; its boxes pass through shared memory.
-__global__ void __launch_bounds__(256) voxelize_kernel(const EnvBoxes* __restrict__ envs, int G,
-                                                       bf16* __restrict__ X) {
+// Block (x, b): rows (i, j) of environment b's voxel grid, one thread per row
+// of G voxels along k; its boxes pass through shared memory.  A box is tested
+// against the row's centre in x and y once, and only then against the G
+// centres in z, so a voxel is occupied exactly when its centre lies in a box
+// (the same comparisons as testing every voxel against every box).
+__global__ void __launch_bounds__(kVoxRows) voxelize_kernel(const EnvBoxes* __restrict__ envs, int G,
+                                                            bf16* __restrict__ X) {
     __shared__ float slo[kVoxBoxes * 3], shi[kVoxBoxes * 3];
+    __shared__ float pz[64];
     const int b = blockIdx.y;
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    const int G3 = G * G * G;
-    const int i = v / (G * G), j = (v / G) % G, k = v % G;
-    const float p[3] = {((float)i + 0.5f) / (float)G, ((float)j + 0.5f) / (float)G, ((float)k + 0.5f) / (float)G};
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = row / G, j = row % G;
+    const float px = ((float)i + 0.5f) / (float)G, py = ((float)j + 0.5f) / (float)G;
+    if (threadIdx.x < G) pz[threadIdx.x] = ((float)threadIdx.x + 0.5f) / (float)G;
     const EnvBoxes e = envs[b];
-    bool occ = false;
+    unsigned long long occ = 0ull;
     for (int b0 = 0; b0 < e.count; b0 += kVoxBoxes) {
         const int nb = min(kVoxBoxes, e.count - b0);
         __syncthreads();  // the previous pass's boxes are no longer read
@@ -58,9 +64,31 @@ __global__ void __launch_bounds__(256) voxelize_kernel(const EnvBoxes* __restric
             shi[t] = e.hi[(size_t)b0 * 3 + t];
         }
         __syncthreads();
-        occ = occ || in_any_box<3>(p, slo, shi, nb);
+        for (int q = 0; q < nb; ++q) {
+            if (slo[3 * q] <= px && px <= shi[3 * q] && slo[3 * q + 1] <= py && py <= shi[3 * q + 1]) {
+                const float zl = slo[3 * q + 2], zh = shi[3 * q + 2];
+                for (int k = 0; k < G; ++k)
+                    if (zl <= pz[k] && pz[k] <= zh) occ |= 1ull << k;
+            }
+        }
     }
-    if (v < G3) X[(size_t)b * G3 + v] = __float2bfloat16_rn(occ ? 1.0f : 0.0f);
+    if (row >= G * G) return;
+    bf16* out = X + (size_t)b * G * G * G + (size_t)row * G;
+    const unsigned short one = 0x3F80u;  // BF16 1.0
+    if (G % 8 == 0 && ((uintptr_t)out & 15u) == 0) {
+        for (int k0 = 0; k0 < G; k0 += 8) {
+            unsigned w[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const unsigned lo = (occ >> (k0 + 2 * h)) & 1ull ? one : 0u;
+                const unsigned hi = (occ >> (k0 + 2 * h + 1)) & 1ull ? one : 0u;
+                w[h] = lo | (hi << 16);
+            }
+            *reinterpret_cast<uint4*>(out + k0) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    } else {
+        for (int k = 0; k < G; ++k) out[k] = __float2bfloat16_rn((occ >> k) & 1ull ? 1.0f : 0.0f);
+    }
 }
 
 // Z = [H2, start/goal (6), zeros] in BF16.
@@ -585,14 +613,14 @@ gmt_status propose_impl(gmt_model* m, int B, const gmt_space* spaces, const gmt_
     }
     MCUDA(cudaMemcpyAsync(m->envs, eb, eb_bytes, cudaMemcpyHostToDevice, st), "proposal descriptors");
     MCUDA(cudaMemcpyAsync(m->penv, pe, pe_bytes, cudaMemcpyHostToDevice, st), "proposal descriptors");
-    const int G3 = m->G * m->G * m->G;
     for (int b0 = 0; b0 < B; b0 += m->maxB) {
         const int nb = std::min(m->maxB, B - b0);
         MCUDA(cudaMemcpyAsync(m->psg, hsg + (size_t)b0 * 6, (size_t)nb * 6 * sizeof(float),
                               cudaMemcpyHostToDevice, st),
               "start/goal upload");
         MCUDA(cudaEventRecord(m->pin_ev, st), "proposal event");  // covers every copy out of `pin` so far
-        voxelize_kernel<<<dim3(blocks_for(G3, 256), nb), 256, 0, st>>>(m->envs + b0, m->G, m->pvox);
+        voxelize_kernel<<<dim3(blocks_for((long long)m->G * m->G, kVoxRows), nb), kVoxRows, 0, st>>>(m->envs + b0, m->G,
+                                                                                               m->pvox);
         MCUDA(cudaGetLastError(), "voxelize kernel");
         gmt_status s = forward(m, nb, m->pvox, m->psg, st);
         if (s != GMT_OK) return s;
@@ -692,8 +720,7 @@ gmt_status gmt_voxelize(int32_t B, const gmt_boxes* boxes, int32_t grid, void* v
     EnvBoxes* d = nullptr;
     MCUDA(cudaMallocAsync((void**)&d, B * sizeof(EnvBoxes), st), "voxelize descriptors");
     MCUDA(cudaMemcpyAsync(d, h.data(), B * sizeof(EnvBoxes), cudaMemcpyHostToDevice, st), "voxelize descriptors");
-    const int G3 = grid * grid * grid;
-    voxelize_kernel<<<dim3(blocks_for(G3, 256), B), 256, 0, st>>>(d, grid, (bf16*)voxels);
+    voxelize_kernel<<<dim3(blocks_for((long long)grid * grid, kVoxRows), B), kVoxRows, 0, st>>>(d, grid, (bf16*)voxels);
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(d, st);
     MCUDA(e, "voxelize kernel");
