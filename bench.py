@@ -24,6 +24,7 @@ seeds, on one host core.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import subprocess
@@ -253,6 +254,10 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    # no Python garbage collection inside the timed region (a collection is a
+    # host pause of milliseconds during which the GPU would idle between steps)
+    gc.collect()
+    gc.disable()
     clocks.start()
     t_wall = time.perf_counter()
     for j in range(args.steps):
@@ -267,6 +272,7 @@ def run_gpu(args, rank, world, local_rank):
     wall = time.perf_counter() - t_wall
     if world > 1:
         torch.distributed.barrier()
+    gc.enable()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     edges = [i["push_edges"] + i["pull_edges"] for i in infos]
