@@ -1,5 +1,7 @@
 // C ABI of the planner (include/gmt.h): argument checks, device buffers of the
 // opaque handles, and the launch sequence of every entry point.
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -103,7 +105,12 @@ struct gmt_graph {
     uint32_t* mask = nullptr;      size_t cap_mask = 0;
     uint32_t* maskT = nullptr;     size_t cap_maskT = 0;
     int* tile_cnt = nullptr;       size_t cap_tile_cnt = 0;  // per-tile row counts of the tiled fill
-    // [sample flags, max row length, -, fill ticket, cell row overflow, -, -, -]
+    // double integrator: the pair filter's edge list (row, column, cost,
+    // arrival time) and the word prefixes of mask and maskT that place it
+    int4* elist = nullptr;         size_t cap_elist = 0;
+    int* wpre = nullptr;           size_t cap_wpre = 0;
+    int* wpreT = nullptr;          size_t cap_wpreT = 0;
+    // [sample flags, max row length, -, fill ticket, cell row overflow, edge list count, -, -]
     int* flags = nullptr;
     // cell-list neighbour build
     int* cell_of = nullptr;        size_t cap_cell_of = 0;
@@ -165,7 +172,8 @@ struct gmt_graph {
 
     ~gmt_graph() {
         void* dev[] = {X, is_goal, out_row, in_row_own, counts, out_col, out_cost, in_col_own,
-                       in_cost_own, out_tau, in_tau, in_path, mask, maskT, tile_cnt, cell_of, cell_sorted, cell_cnt,
+                       in_cost_own, out_tau, in_tau, in_path, mask, maskT, tile_cnt, elist, wpre, wpreT,
+                       cell_of, cell_sorted, cell_cnt,
                        cell_start, grid_cnt, grid_start, grid_list, grid_big, halton, ocost, stamp,
                        lists, ctl};
         for (void* p : dev)
@@ -408,6 +416,16 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
         GROW(in_row_own, N + 1);
         GROW(maskT, W * P);
     }
+    // Double integrator, once earlier builds have sized the edge arrays: the
+    // pair filter lists each edge with its cost and arrival time, and the fill
+    // places the listed edges by rank instead of solving for them again.
+    const bool di_list = g->kind == GMT_COST_DI && edge_capacity(g) > 0;
+    if (di_list) {
+        GROW(elist, (size_t)edge_capacity(g));
+        GROW(wpre, W * P);
+        GROW(wpreT, W * P);
+    }
+    const int list_cap = di_list ? (int)std::min<size_t>(g->cap_elist, (size_t)INT_MAX) : 0;
     if (!g->h_ctl && (e = alloc_mapped(&g->h_ctl, &g->d_ctl, 1)) != cudaSuccess)
         return bail(cuda_fail(e, "allocating pinned control block"));
     if (!g->h_scalars && (e = alloc_mapped(&g->h_scalars, &g->d_scalars, 4)) != cudaSuccess)
@@ -463,7 +481,8 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
         // directed costs: the pair filter also writes the transposed matrix
         const bool dir = g->directed();
         LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, dir ? g->maskT : nullptr,
-                                dir ? g->in_count : nullptr, st, tiles ? g->tile_cnt : nullptr),
+                                dir ? g->in_count : nullptr, st, tiles ? g->tile_cnt : nullptr,
+                                di_list ? g->elist : nullptr, g->flags + 5, list_cap),
                "pair filter kernel");
     }
     LAUNCH(g->mark(gmt_graph::kPair, 1, st), "event");
@@ -471,7 +490,8 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
     // the scan also stores the sampling flags, the longest cell row and the
     // edge count in the pinned scalars (no copy)
     LAUNCH(launch_scan2(g->out_count, g->out_row, g->directed() ? g->in_count : nullptr,
-                        g->directed() ? g->in_row_own : nullptr, g->N, g->flags, g->d_scalars, st),
+                        g->directed() ? g->in_row_own : nullptr, g->N, g->flags, g->d_scalars, st,
+                        di_list ? g->mask : nullptr, g->wpre, di_list ? g->maskT : nullptr, g->wpreT, g->pitch),
            "scan kernel");
     LAUNCH(g->mark(gmt_graph::kScan, 1, st), "event");
     g->pending = false;
@@ -487,7 +507,9 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
                                                        di_a ? g->in_tau : nullptr, dub_a ? g->in_path : nullptr,
                                                        cap_now}
                                              : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
-        if (tiles) {
+        if (di_list && list_cap >= cap_now) {  // the list holds every edge the arrays can
+            LAUNCH(launch_fill_list(sa, g->elist, list_cap, out_dir, in_dir, g->wpre, g->wpreT, st), "fill kernel");
+        } else if (tiles) {
             LAUNCH(launch_fill_tiles(sa, g->X, out_dir, g->tile_cnt, st), "fill kernel");
         } else {
             LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, g->flags + 3, st), "fill kernel");
@@ -557,7 +579,9 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
         const FillDir in_dir = directed ? FillDir{g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own,
                                                   di ? g->in_tau : nullptr, dubins ? g->in_path : nullptr, 0}
                                         : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
-        if (tiles) {
+        if (di_list && (long long)E <= (long long)list_cap) {  // the list holds every edge
+            LAUNCH(launch_fill_list(sa, g->elist, list_cap, out_dir, in_dir, g->wpre, g->wpreT, st), "fill kernel");
+        } else if (tiles) {
             LAUNCH(launch_fill_tiles(sa, g->X, out_dir, g->tile_cnt, st), "fill kernel");
         } else {
             LAUNCH(launch_fill(sa, g->X, out_dir, in_dir, g->flags + 3, st), "fill kernel");

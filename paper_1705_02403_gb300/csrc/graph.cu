@@ -21,6 +21,9 @@
 //                     it also writes the transposed words and in-row counts
 //   scan2_kernel      both directions' row offsets (one block each); the
 //                     edge count and sampling flags straight to host memory
+//   fill_list_kernel  double integrator: the edges the pair filter listed
+//                     with their costs, placed in both CSRs by rank (word
+//                     prefixes from scan2_kernel's extra blocks)
 //   fill_kernel       persistent blocks, eight rows at a time: each warp
 //                     gathers a row's columns (prefix over its words) into a
 //                     shared-memory list, then the block shares out the eight
@@ -195,8 +198,9 @@ __global__ void __launch_bounds__(kDIRows, 8) pair_mask_di_kernel(SpaceArgs s, c
                                                               uint32_t* __restrict__ mask,
                                                               int* __restrict__ out_count,
                                                               uint32_t* __restrict__ maskT,
-                                                              int* __restrict__ in_count) {
-    mask_di_tile(s, X, mask, out_count, blockIdx.x, blockIdx.y, maskT, in_count);
+                                                              int* __restrict__ in_count, int4* __restrict__ elist,
+                                                              int* __restrict__ elist_n, int elist_cap) {
+    mask_di_tile(s, X, mask, out_count, blockIdx.x, blockIdx.y, maskT, in_count, elist, elist_n, elist_cap);
 }
 
 __global__ void __launch_bounds__(kDubRows) pair_mask_dubins_kernel(SpaceArgs s, const float* __restrict__ X,
@@ -214,10 +218,22 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ coun
 // Block 0 scans the out-row counts and, when host_out is given (host memory
 // mapped into the device), stores there the build's first two flags (written
 // by the kernels before this one) and the edge count, so that the host needs
-// no copy; block 1, if launched, scans the in-row counts.
+// no copy; block 1, if count1 is given, scans the in-row counts.  The blocks
+// after them, if launched, write the word prefixes of m0 into pre0 and of m1
+// into pre1, 32 rows per block (m0's row blocks first).
 __global__ void __launch_bounds__(1024) scan2_kernel(const int* __restrict__ count0, int* __restrict__ row0,
                                                      const int* __restrict__ count1, int* __restrict__ row1, int N,
-                                                     const int* __restrict__ flags, int* __restrict__ host_out) {
+                                                     const int* __restrict__ flags, int* __restrict__ host_out,
+                                                     const uint32_t* __restrict__ m0, int* __restrict__ pre0,
+                                                     const uint32_t* __restrict__ m1, int* __restrict__ pre1,
+                                                     int pitch) {
+    const int nscan = count1 ? 2 : 1;
+    if ((int)blockIdx.x >= nscan) {
+        const int tb = (int)blockIdx.x - nscan, rb = (N + 31) / 32;
+        if (tb < rb) word_prefix_block(m0, pre0, N, pitch, 32 * tb);
+        else if (m1 && tb < 2 * rb) word_prefix_block(m1, pre1, N, pitch, 32 * (tb - rb));
+        return;
+    }
     if (blockIdx.x == 0) {
         const int total = scan_rows(count0, row0, N);
         if (threadIdx.x == 0 && host_out) {
@@ -228,6 +244,20 @@ __global__ void __launch_bounds__(1024) scan2_kernel(const int* __restrict__ cou
     } else {
         scan_rows(count1, row1, N);
     }
+}
+
+// Double integrator: the edges the pair filter listed (with cost and arrival
+// time), placed in the out- and in-CSR by their ranks (place_listed_edge).
+// Writes nothing when the edge count exceeds the arrays' capacity (cap > 0:
+// the caller rebuilds) or the list's.
+__global__ void __launch_bounds__(256) fill_list_kernel(int N, int pitch, const int4* __restrict__ elist,
+                                                        int list_cap, FillDir out, FillDir in,
+                                                        const int* __restrict__ pre_out,
+                                                        const int* __restrict__ pre_in) {
+    const int E = __ldg(&out.row[N]);
+    if ((out.cap > 0 && (long long)E > out.cap) || E > list_cap || __ldg(&in.row[N]) != E) return;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < E; t += gridDim.x * blockDim.x)
+        place_listed_edge(pitch, __ldg(&elist[t]), out, in, pre_out, pre_in);
 }
 
 // Persistent blocks take groups of kFillWarps rows from a ticket counter
@@ -372,11 +402,12 @@ cudaError_t launch_append(const SpaceArgs& s, BoxArgs b, const float* src, int s
 }
 
 cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* cnt, uint32_t* maskT,
-                             int* in_count, cudaStream_t st, int* tile_cnt) {
+                             int* in_count, cudaStream_t st, int* tile_cnt, int4* elist, int* elist_n,
+                             int elist_cap) {
     if (s.kind == GMT_COST_DI) {
         const int W = (s.N + 31) / 32;
         dim3 grid((s.N + kDIRows - 1) / kDIRows, (W + kDIWords - 1) / kDIWords);
-        pair_mask_di_kernel<<<grid, kDIRows, 0, st>>>(s, X, mask, cnt, maskT, in_count);
+        pair_mask_di_kernel<<<grid, kDIRows, 0, st>>>(s, X, mask, cnt, maskT, in_count, elist, elist_n, elist_cap);
         return cudaGetLastError();
     }
     if (s.kind == GMT_COST_DUBINS) {
@@ -407,8 +438,21 @@ cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st) {
 }
 
 cudaError_t launch_scan2(const int* count0, int* row0, const int* count1, int* row1, int N, const int* flags,
-                         int* host_out, cudaStream_t st) {
-    scan2_kernel<<<count1 ? 2 : 1, 1024, 0, st>>>(count0, row0, count1, row1, N, flags, host_out);
+                         int* host_out, cudaStream_t st, const uint32_t* m0, int* pre0, const uint32_t* m1,
+                         int* pre1, int pitch) {
+    const int nscan = count1 ? 2 : 1;
+    const int ntab = m0 && pre0 ? (m1 && pre1 ? 2 : 1) * ((N + 31) / 32) : 0;  // 32 rows per block
+    scan2_kernel<<<nscan + ntab, 1024, 0, st>>>(count0, row0, count1, row1, N, flags, host_out, m0, pre0,
+                                                m1 && pre1 ? m1 : nullptr, pre1, pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_list(const SpaceArgs& s, const int4* elist, int list_cap, const FillDir& out,
+                             const FillDir& in, const int* pre_out, const int* pre_in, cudaStream_t st) {
+    long long blocks = ((long long)list_cap + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 4096) blocks = 4096;
+    fill_list_kernel<<<(unsigned)blocks, 256, 0, st>>>(s.N, s.pitch, elist, list_cap, out, in, pre_out, pre_in);
     return cudaGetLastError();
 }
 

@@ -624,10 +624,15 @@ constexpr int kDIWords = GMT_DI_WORDS;  // 32-column words per block (staged col
 // One block of kDIRows threads: rows bx*kDIRows.., words by*kDIWords..
 // maskT, in_count (may be NULL): also write the tile's words of the transposed
 // (in-neighbour) matrix and count the in-edges, as transpose_task would.
+// elist (may be NULL): every edge found is also listed as (row, column, cost
+// bits, arrival-time bits) at a slot taken from *elist_n (slots at or past
+// elist_cap are counted but not written), so the CSR fill need not solve for
+// the arrival time again.
 __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __restrict__ X,
                                              uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
                                              int by, uint32_t* __restrict__ maskT = nullptr,
-                                             int* __restrict__ in_count = nullptr) {
+                                             int* __restrict__ in_count = nullptr, int4* __restrict__ elist = nullptr,
+                                             int* __restrict__ elist_n = nullptr, int elist_cap = 0) {
     static_assert(kDIWords == 1, "the first stage keeps a lane's columns in one 32-bit word");
     __shared__ float tile[6][kDIWords * 32];
     __shared__ uint32_t words[kDIRows / 32][kDIWords][32];
@@ -679,12 +684,30 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
         __syncwarp();
         return qn - 32;
     };
-    auto drain2 = [&](int count) {  // exact test
+    auto drain2 = [&](int count) {  // exact test (the steps of di_cost)
         const int e = lane < count ? queue[warp][2][lane] : 0;
         float a_[6], b_[6];
         state(e, a_, b_);
         const int src = e >> 8, jt = e & 255;
-        if (lane < count && di_cost(a_, b_, s.r) < s.r) atomicOr(&words[warp][jt >> 5][src], 1u << (jt & 31));
+        float J = f_inf(), t = f_inf();
+        if (lane < count) {
+            const DICoef k = di_coef(a_, b_);
+            t = di_tau(k, s.r);
+            if (t != f_inf()) J = di_J(k, t);
+        }
+        const bool edge = J < s.r;
+        if (edge) atomicOr(&words[warp][jt >> 5][src], 1u << (jt & 31));
+        if (elist) {
+            const unsigned m = __ballot_sync(0xffffffffu, edge);
+            if (m) {
+                int slot = 0;
+                if (lane == 0) slot = atomicAdd(elist_n, __popc(m));
+                slot = __shfl_sync(0xffffffffu, slot, 0) + __popc(m & ((1u << lane) - 1u));
+                if (edge && slot < elist_cap)
+                    elist[slot] = make_int4(bx * kDIRows + warp * 32 + src, j0 + jt, __float_as_int(J),
+                                            __float_as_int(t));
+            }
+        }
     };
     auto drain1 = [&](int count) {  // second bound
         const int e = lane < count ? queue[warp][1][lane] : 0;
@@ -878,6 +901,65 @@ __device__ __forceinline__ void mask_dubins_tile(const SpaceArgs& s, const float
         cnt += __popc(bits);
     }
     if (cnt) atomicAdd(&out_count[i], cnt);
+}
+
+// Word prefixes of a word-major bit matrix (word w of row i at w * pitch + i):
+// pre[w * pitch + i] = the set bits of row i's words 0 .. w-1.  One block of
+// 1024 threads takes 32 rows (rows0 ..): lane = row, and warp k the k-th
+// run of ceil(W / 32) words, so every load is one row-contiguous line.  Each
+// warp sums its run, the runs' totals meet in shared memory, and each warp then
+// writes its run's prefixes from the sum of the runs before it.
+__device__ __forceinline__ void word_prefix_block(const uint32_t* __restrict__ M, int* __restrict__ pre, int N,
+                                                  int pitch, int row0) {
+    __shared__ int run_total[32][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int W = (N + 31) / 32, seg = (W + 31) / 32;
+    const int i = row0 + lane;
+    const int wa = min(W, warp * seg), wb = min(W, wa + seg);
+    const bool row_ok = i < N;
+    int sum = 0;
+    for (int w0 = wa; w0 < wb; w0 += 8) {
+        uint32_t b[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) b[k] = row_ok && w0 + k < wb ? __ldcg(&M[(size_t)(w0 + k) * pitch + i]) : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sum += __popc(b[k]);
+    }
+    run_total[warp][lane] = sum;
+    __syncthreads();
+    int run = 0;
+    for (int k = 0; k < warp; ++k) run += run_total[k][lane];
+    for (int w0 = wa; w0 < wb; w0 += 8) {
+        uint32_t b[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) b[k] = row_ok && w0 + k < wb ? __ldcg(&M[(size_t)(w0 + k) * pitch + i]) : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (row_ok && w0 + k < wb) pre[(size_t)(w0 + k) * pitch + i] = run;
+            run += __popc(b[k]);
+        }
+    }
+}
+
+// A double-integrator edge (i, j) listed by the pair filter (with its cost and
+// arrival-time bits), written to both CSRs at its rank: in the out-row of i
+// after row[i] + pre[w][i] + the bits of word w = j / 32 below j, in the
+// in-row of j the same in the transposed matrix.  The ranks are those the
+// row-by-row fill gives, so the CSRs are the same arrays.
+__device__ __forceinline__ void place_listed_edge(int pitch, int4 q, const FillDir& out, const FillDir& in,
+                                                  const int* __restrict__ pre_out, const int* __restrict__ pre_in) {
+    const int i = q.x, j = q.y;
+    const size_t oi = (size_t)(j >> 5) * pitch + i, ij = (size_t)(i >> 5) * pitch + j;
+    const int po =
+        __ldg(&out.row[i]) + __ldg(&pre_out[oi]) + __popc(__ldg(&out.mask[oi]) & ((1u << (j & 31)) - 1u));
+    const int pi = __ldg(&in.row[j]) + __ldg(&pre_in[ij]) + __popc(__ldg(&in.mask[ij]) & ((1u << (i & 31)) - 1u));
+    const float J = __int_as_float(q.z), t = __int_as_float(q.w);
+    out.col[po] = j;
+    out.cost[po] = J;
+    out.tau[po] = t;
+    in.col[pi] = i;
+    in.cost[pi] = J;
+    in.tau[pi] = t;
 }
 
 // maskT[u][j] bit l = mask[j/32][32u + l] bit (j%32): the in-neighbour rows.

@@ -99,8 +99,13 @@ cudaError_t launch_sample(const SpaceArgs& s, BoxArgs boxes, const BoxGridArgs& 
 // tile_cnt (Euclidean graphs of 2 to 4 dimensions, may be NULL): receives,
 // for launch_fill_tiles, the number of each row's edges in the tiles of
 // kMaskWords mask words before each tile, [tile][pitch].
+// elist, elist_n (double integrator, may be NULL): every edge is also listed
+// as (row, column, cost bits, arrival-time bits) at a slot counted by
+// *elist_n (zero at launch; slots at or past elist_cap are not written), for
+// launch_fill_list.
 cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* out_count,
-                             uint32_t* maskT, int* in_count, cudaStream_t st, int* tile_cnt = nullptr);
+                             uint32_t* maskT, int* in_count, cudaStream_t st, int* tile_cnt = nullptr,
+                             int4* elist = nullptr, int* elist_n = nullptr, int elist_cap = 0);
 // Does the tiled fill apply (Euclidean, 2 to 4 dimensions; on one graph from
 // 4096 nodes, below which its extra prefix launch costs more than it saves;
 // in a batch always, one launch serving every query), and how many tiles of
@@ -112,9 +117,12 @@ int fill_tiles_per_row(int N);
 cudaError_t launch_scan(const int* count, int* row, int N, cudaStream_t st);
 // Both directions' row offsets in one launch (count1 may be NULL: one scan).
 // host_out (may be NULL; device-mapped host memory) receives flags[0],
-// flags[1] and row0[N].
+// flags[1] and row0[N].  m0/pre0 and m1/pre1 (may be NULL): the same launch
+// writes the word prefixes of those word-major bit matrices ([W][pitch] each:
+// the set bits of a row's words before each word), for launch_fill_list.
 cudaError_t launch_scan2(const int* count0, int* row0, const int* count1, int* row1, int N, const int* flags,
-                         int* host_out, cudaStream_t st);
+                         int* host_out, cudaStream_t st, const uint32_t* m0 = nullptr, int* pre0 = nullptr,
+                         const uint32_t* m1 = nullptr, int* pre1 = nullptr, int pitch = 0);
 // One CSR direction for the fill: the bit matrix rows come from (mask for
 // out-rows, its transpose for in-rows), row offsets, and the outputs; tau
 // (double integrator only, may be NULL) receives each edge's arrival time,
@@ -133,6 +141,12 @@ struct FillDir {
 // ticket: one device int, zero at launch (the blocks' work counter).
 cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, int* ticket,
                         cudaStream_t st);
+// Double integrator: both CSRs from the edge list of launch_pair_mask (list_cap
+// slots) and the word prefixes of launch_scan2 (pre_out for out.mask, pre_in
+// for in.mask), with no cost evaluated again.  Writes nothing if the edge
+// count exceeds out.cap (> 0) or list_cap.
+cudaError_t launch_fill_list(const SpaceArgs& s, const int4* elist, int list_cap, const FillDir& out,
+                             const FillDir& in, const int* pre_out, const int* pre_in, cudaStream_t st);
 // The out-CSR of a Euclidean graph of 2 to 4 dimensions from the mask and the
 // per-tile prefixes of launch_pair_mask: one block per mask tile, columns
 // staged in shared memory.  Reads its inputs only, so it may run again.  A

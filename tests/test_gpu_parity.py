@@ -492,6 +492,53 @@ def test_asynchronous_builds(O, P):
 
 
 
+def _retarget(P, pl, pb):
+    """Points a planner (and its graph handle) at another problem."""
+    pl.pb = pb
+    pl.space, pl.goal, pl.params = P.space_struct(pb), P.goal_struct(pb), P.params_struct(pb)
+    pl.boxes, pl._box_tensors = P.boxes_on_device(pb)
+    pl.parent = torch.empty(pb.N, dtype=torch.int32, device="cuda")
+    pl.cost = torch.empty(pb.N, dtype=torch.float32, device="cuda")
+    pl.path = torch.empty(pb.N, dtype=torch.int32, device="cuda")
+
+
+def test_double_integrator_listed_edges(O, P):
+    # A rebuild of a double-integrator graph on a handle whose edge arrays are
+    # already sized takes its costs and arrival times from the pair filter's
+    # edge list (placed by rank) instead of solving for them again, in the
+    # synchronous and the asynchronous build; CSR, costs, arrival times and the
+    # tree must equal the oracle's bit for bit.  The last problem has more
+    # edges than the list holds: the synchronous rebuild then fills row by row.
+    from paper_1705_02403_gb300.planner import wrap_device
+    first = envgen.cfg2_di6(20)
+    pl = P.Planner(first).build()
+    cases = [(envgen.cfg2_di6(21), False), (envgen.cfg2_di6(22), True), (envgen.di6(seed=23, n=600, r=2.8), False),
+             (envgen.di6(seed=24, n=4500, r=2.5), True)]
+    for pb, asynchronous in cases:
+        _retarget(P, pl, pb)
+        pl.build(asynchronous=asynchronous)
+        info = pl.plan()
+        v = pl.view()
+        G = {"parent": pl.parent.cpu().numpy(), "cost": pl.cost.cpu().numpy(), "info": info,
+             "path": pl.path.cpu().numpy()[:info["path_len"]], "X": v.X.cpu().numpy(),
+             "goal": v.is_goal.cpu().numpy(), "E": v.E, "out_row": v.out_row.cpu().numpy(),
+             "out_col": v.out_col.cpu().numpy(), "out_cost": v.out_cost.cpu().numpy(),
+             "in_row": v.in_row.cpu().numpy(), "in_col": v.in_col.cpu().numpy(), "in_cost": v.in_cost.cpu().numpy()}
+        X, goal, g, parent, cost, oinfo = oracle_run(O, pb)
+        assert_same(O, G, X, goal, g, parent, cost, oinfo)
+        out_tau = wrap_device(v.raw.out_tau, (v.E,), "f4", pl.graph).cpu().numpy()
+        in_tau = wrap_device(v.raw.in_tau, (v.E,), "f4", pl.graph).cpu().numpy()
+        r = np.float32(pb.r)
+        for y in range(0, pb.N, 97):
+            for e in range(G["out_row"][y], G["out_row"][y + 1]):
+                J, tau = O.cost_di(X[:, y], X[:, G["out_col"][e]], r)
+                assert bits(tau) == bits(out_tau[e])
+        for x in range(0, pb.N, 97):
+            for e in range(G["in_row"][x], G["in_row"][x + 1]):
+                J, tau = O.cost_di(X[:, G["in_col"][e]], X[:, x], r)
+                assert bits(tau) == bits(in_tau[e])
+
+
 def test_large_graph(O, P):
     # 40001 nodes in 2D (Theorem 1 radius, 5.4 M edges, about 100 group
     # expansions): the cell-list build, a wavefront over a large graph and the
