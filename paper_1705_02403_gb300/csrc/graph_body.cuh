@@ -371,6 +371,56 @@ __device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsig
     return r;
 }
 
+// di_may_connect for two pairs at once (s0a -> s1a and s0b -> s1b): the same
+// operations in the same order, the additions and multiplications packed two
+// to an instruction, so each verdict is the scalar function's.
+__device__ __forceinline__ void di_may_connect_x2(const float* s0a, const float* s1a, const float* s0b,
+                                                  const float* s1b, float r, bool& pass_a, bool& pass_b) {
+    const float rr = r * 1.01f;
+    const unsigned long long two = f2_pack(2.0f, 2.0f);
+    unsigned long long A = f2_pack(0.0f, 0.0f), qs = A, ss = A, q[3], sv[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const unsigned long long v0 = f2_pack(s0a[3 + ax], s0b[3 + ax]), v1 = f2_pack(s1a[3 + ax], s1b[3 + ax]);
+        const unsigned long long dv = f2_sub(v1, v0);
+        A = f2_add(A, f2_mul(dv, dv));
+        q[ax] = f2_mul(two, f2_sub(f2_pack(s1a[ax], s1b[ax]), f2_pack(s0a[ax], s0b[ax])));
+        sv[ax] = f2_add(v0, v1);
+        qs = f2_add(qs, f2_mul(q[ax], sv[ax]));
+        ss = f2_add(ss, f2_mul(sv[ax], sv[ax]));
+    }
+    float Aa, Ab, qsa, qsb, ssa, ssb;
+    f2_unpack(A, Aa, Ab);
+    f2_unpack(qs, qsa, qsb);
+    f2_unpack(ss, ssa, ssb);
+    float ta = ssa > 0.0f ? __fdividef(qsa, ssa) : 0.0f, tb = ssb > 0.0f ? __fdividef(qsb, ssb) : 0.0f;
+    ta = fminf(fmaxf(ta, 0.0f), rr);
+    tb = fminf(fmaxf(tb, 0.0f), rr);
+    const unsigned long long t = f2_pack(ta, tb);
+    unsigned long long D2 = f2_pack(0.0f, 0.0f);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const unsigned long long e = f2_sub(q[ax], f2_mul(t, sv[ax]));
+        D2 = f2_add(D2, f2_mul(e, e));
+    }
+    const unsigned long long B = f2_mul(f2_pack(3.0f, 3.0f), D2);
+    const unsigned long long disc = f2_add(f2_mul(A, A), f2_mul(f2_pack(12.0f, 12.0f), B));
+    float da, db;
+    f2_unpack(disc, da, db);
+    const unsigned long long h = f2_mul(f2_pack(0.5f, 0.5f), f2_add(A, f2_pack(approx_sqrt(da), approx_sqrt(db))));
+    float ha, hb;
+    f2_unpack(h, ha, hb);
+    const float taua = fminf(approx_sqrt(ha), rr), taub = fminf(approx_sqrt(hb), rr);
+    const unsigned long long tau = f2_pack(taua, taub), inv = f2_pack(approx_rcp(taua), approx_rcp(taub));
+    const unsigned long long f =
+        f2_add(f2_add(tau, f2_mul(A, inv)), f2_mul(B, f2_mul(f2_mul(inv, inv), inv)));
+    float fa, fb;
+    f2_unpack(f, fa, fb);
+    const float rr2 = rr * rr;
+    pass_a = !(4.0f * Aa >= rr2) && (!(taua > 0.0f) || fa < rr);
+    pass_b = !(4.0f * Ab >= rr2) && (!(taub > 0.0f) || fb < rr);
+}
+
 // Euclidean graphs of 2 to 4 dimensions: columns are staged in pairs (float4
 // (x_j, x_j+1, y_j, y_j+1), then (z_j, z_j+1, w_j, w_j+1)), and each lane
 // tests its row against two columns per step with packed FP32 arithmetic:
@@ -634,7 +684,7 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
                                              int* __restrict__ in_count = nullptr, int4* __restrict__ elist = nullptr,
                                              int* __restrict__ elist_n = nullptr, int elist_cap = 0) {
     static_assert(kDIWords == 1, "the first stage keeps a lane's columns in one 32-bit word");
-    __shared__ float tile[6][kDIWords * 32];
+    __shared__ __align__(16) float tile[6][kDIWords * 32];  // float2 reads of column pairs
     __shared__ uint32_t words[kDIRows / 32][kDIWords][32];
     __shared__ uint16_t queue0[kDIRows / 32][32 * 32];  // every pair of the warp's tile may pass the first test
     __shared__ uint16_t queue[kDIRows / 32][3][64];
@@ -719,11 +769,22 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
             qn2 = shift(2, qn2);
         }
     };
-    auto drain0 = [&](int from, int count) {  // first bound, on queue0[from, from + count)
-        const int e = lane < count ? queue0[warp][from + lane] : 0;
-        float a_[6], b_[6];
-        state(e, a_, b_);
-        qn1 = enqueue(1, lane < count && di_may_connect(a_, b_, s.r), e, qn1);
+    // first bound, on queue0[from, from + count) (count <= 64): each lane
+    // takes two entries, evaluated together with packed arithmetic
+    auto drain0 = [&](int from, int count) {
+        const int ea = lane < count ? queue0[warp][from + lane] : 0;
+        const int eb = lane + 32 < count ? queue0[warp][from + 32 + lane] : 0;
+        float a0[6], b0[6], a1[6], b1[6];
+        state(ea, a0, b0);
+        state(eb, a1, b1);
+        bool pa, pb;
+        di_may_connect_x2(a0, b0, a1, b1, s.r, pa, pb);
+        qn1 = enqueue(1, lane < count && pa, ea, qn1);
+        if (qn1 >= 32) {
+            drain1(32);
+            qn1 = shift(1, qn1);
+        }
+        qn1 = enqueue(1, lane + 32 < count && pb, eb, qn1);
         if (qn1 >= 32) {
             drain1(32);
             qn1 = shift(1, qn1);
@@ -738,16 +799,25 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
     uint32_t pm = 0;
     if (row_ok) {
         const float rr2 = rr * rr;
-#pragma unroll 8
-        for (int jt = 0; jt < jend; ++jt) {
-            float A = 0.0f;
+        // two columns per step with packed arithmetic (the staged tile holds 32
+        // columns, zero past the last node; bits from jend on are cleared)
+        unsigned long long xv2[3];
 #pragma unroll
-            for (int a = 3; a < 6; ++a) {
-                const float dv = tile[a][jt] - xi[a];
-                A = A + dv * dv;
+        for (int a = 0; a < 3; ++a) xv2[a] = f2_pack(xi[3 + a], xi[3 + a]);
+#pragma unroll 4
+        for (int jt = 0; jt < jend; jt += 2) {
+            unsigned long long A = f2_pack(0.0f, 0.0f);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float2 c = *reinterpret_cast<const float2*>(&tile[3 + a][jt]);
+                const unsigned long long dv = f2_sub(f2_pack(c.x, c.y), xv2[a]);
+                A = f2_add(A, f2_mul(dv, dv));
             }
-            pm |= (4.0f * A < rr2 ? 1u : 0u) << jt;
+            float A0, A1;
+            f2_unpack(A, A0, A1);
+            pm |= ((4.0f * A0 < rr2 ? 1u : 0u) | (4.0f * A1 < rr2 ? 2u : 0u)) << jt;
         }
+        if (jend < 32) pm &= (1u << jend) - 1u;
         if (i >= j0 && i < j0 + jend) pm &= ~(1u << (i - j0));  // no self pair
     }
     {
@@ -763,7 +833,7 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
         for (uint32_t m = pm; m; m &= m - 1) queue0[warp][pos++] = (uint16_t)((lane << 8) | (__ffs(m) - 1));
         __syncwarp();
     }
-    for (int from = 0; from < qn0; from += 32) drain0(from, min(32, qn0 - from));
+    for (int from = 0; from < qn0; from += 64) drain0(from, min(64, qn0 - from));
     if (qn1 > 0) drain1(qn1);
     if (qn2 > 0) drain2(qn2);
     __syncwarp();
