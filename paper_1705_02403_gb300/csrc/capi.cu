@@ -105,9 +105,11 @@ struct gmt_graph {
     uint32_t* mask = nullptr;      size_t cap_mask = 0;
     uint32_t* maskT = nullptr;     size_t cap_maskT = 0;
     int* tile_cnt = nullptr;       size_t cap_tile_cnt = 0;  // per-tile row counts of the tiled fill
-    // double integrator: the pair filter's edge list (row, column, cost,
-    // arrival time) and the word prefixes of mask and maskT that place it
+    // directed costs: the pair filter's edge list (row, column, cost, arrival
+    // time), the Dubins words at the same slots, and the word prefixes of mask
+    // and maskT that place them
     int4* elist = nullptr;         size_t cap_elist = 0;
+    float4* epath = nullptr;       size_t cap_epath = 0;
     int* wpre = nullptr;           size_t cap_wpre = 0;
     int* wpreT = nullptr;          size_t cap_wpreT = 0;
     // [sample flags, max row length, -, fill ticket, cell row overflow, edge list count, -, -]
@@ -172,7 +174,7 @@ struct gmt_graph {
 
     ~gmt_graph() {
         void* dev[] = {X, is_goal, out_row, in_row_own, counts, out_col, out_cost, in_col_own,
-                       in_cost_own, out_tau, in_tau, in_path, mask, maskT, tile_cnt, elist, wpre, wpreT,
+                       in_cost_own, out_tau, in_tau, in_path, mask, maskT, tile_cnt, elist, epath, wpre, wpreT,
                        cell_of, cell_sorted, cell_cnt,
                        cell_start, grid_cnt, grid_start, grid_list, grid_big, halton, ocost, stamp,
                        lists, ctl};
@@ -416,16 +418,20 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
         GROW(in_row_own, N + 1);
         GROW(maskT, W * P);
     }
-    // Double integrator, once earlier builds have sized the edge arrays: the
-    // pair filter lists each edge with its cost and arrival time, and the fill
-    // places the listed edges by rank instead of solving for them again.
-    const bool di_list = g->kind == GMT_COST_DI && edge_capacity(g) > 0;
-    if (di_list) {
+    // Directed costs (double integrator, Dubins airplane), once earlier builds
+    // have sized the edge arrays: the pair filter lists each edge with its cost
+    // and arrival time (or shortest word), and the fill places the listed
+    // edges by rank instead of solving for them again.
+    const bool listed = g->directed() && edge_capacity(g) > 0;
+    if (listed) {
         GROW(elist, (size_t)edge_capacity(g));
+        if (g->kind == GMT_COST_DUBINS) GROW(epath, (size_t)edge_capacity(g));
         GROW(wpre, W * P);
         GROW(wpreT, W * P);
     }
-    const int list_cap = di_list ? (int)std::min<size_t>(g->cap_elist, (size_t)INT_MAX) : 0;
+    size_t list_slots = listed ? g->cap_elist : 0;
+    if (listed && g->kind == GMT_COST_DUBINS) list_slots = std::min(list_slots, g->cap_epath);
+    const int list_cap = (int)std::min<size_t>(list_slots, (size_t)INT_MAX);
     if (!g->h_ctl && (e = alloc_mapped(&g->h_ctl, &g->d_ctl, 1)) != cudaSuccess)
         return bail(cuda_fail(e, "allocating pinned control block"));
     if (!g->h_scalars && (e = alloc_mapped(&g->h_scalars, &g->d_scalars, 4)) != cudaSuccess)
@@ -482,7 +488,8 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
         const bool dir = g->directed();
         LAUNCH(launch_pair_mask(sa, g->X, g->mask, g->out_count, dir ? g->maskT : nullptr,
                                 dir ? g->in_count : nullptr, st, tiles ? g->tile_cnt : nullptr,
-                                di_list ? g->elist : nullptr, g->flags + 5, list_cap),
+                                listed ? g->elist : nullptr, g->flags + 5, list_cap,
+                                listed && g->kind == GMT_COST_DUBINS ? g->epath : nullptr),
                "pair filter kernel");
     }
     LAUNCH(g->mark(gmt_graph::kPair, 1, st), "event");
@@ -491,7 +498,7 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
     // edge count in the pinned scalars (no copy)
     LAUNCH(launch_scan2(g->out_count, g->out_row, g->directed() ? g->in_count : nullptr,
                         g->directed() ? g->in_row_own : nullptr, g->N, g->flags, g->d_scalars, st,
-                        di_list ? g->mask : nullptr, g->wpre, di_list ? g->maskT : nullptr, g->wpreT, g->pitch),
+                        listed ? g->mask : nullptr, g->wpre, listed ? g->maskT : nullptr, g->wpreT, g->pitch),
            "scan kernel");
     LAUNCH(g->mark(gmt_graph::kScan, 1, st), "event");
     g->pending = false;
@@ -507,8 +514,9 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
                                                        di_a ? g->in_tau : nullptr, dub_a ? g->in_path : nullptr,
                                                        cap_now}
                                              : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
-        if (di_list && list_cap >= cap_now) {  // the list holds every edge the arrays can
-            LAUNCH(launch_fill_list(sa, g->elist, list_cap, out_dir, in_dir, g->wpre, g->wpreT, st), "fill kernel");
+        if (listed && list_cap >= cap_now) {  // the list holds every edge the arrays can
+            LAUNCH(launch_fill_list(sa, g->elist, g->epath, list_cap, out_dir, in_dir, g->wpre, g->wpreT, st),
+                   "fill kernel");
         } else if (tiles) {
             LAUNCH(launch_fill_tiles(sa, g->X, out_dir, g->tile_cnt, st), "fill kernel");
         } else {
@@ -579,8 +587,9 @@ gmt_status build_impl(const gmt_space* space, const gmt_boxes* boxes, const floa
         const FillDir in_dir = directed ? FillDir{g->maskT, g->in_row_own, g->in_col_own, g->in_cost_own,
                                                   di ? g->in_tau : nullptr, dubins ? g->in_path : nullptr, 0}
                                         : FillDir{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
-        if (di_list && (long long)E <= (long long)list_cap) {  // the list holds every edge
-            LAUNCH(launch_fill_list(sa, g->elist, list_cap, out_dir, in_dir, g->wpre, g->wpreT, st), "fill kernel");
+        if (listed && (long long)E <= (long long)list_cap) {  // the list holds every edge
+            LAUNCH(launch_fill_list(sa, g->elist, g->epath, list_cap, out_dir, in_dir, g->wpre, g->wpreT, st),
+                   "fill kernel");
         } else if (tiles) {
             LAUNCH(launch_fill_tiles(sa, g->X, out_dir, g->tile_cnt, st), "fill kernel");
         } else {

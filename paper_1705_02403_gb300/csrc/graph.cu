@@ -21,9 +21,10 @@
 //                     it also writes the transposed words and in-row counts
 //   scan2_kernel      both directions' row offsets (one block each); the
 //                     edge count and sampling flags straight to host memory
-//   fill_list_kernel  double integrator: the edges the pair filter listed
-//                     with their costs, placed in both CSRs by rank (word
-//                     prefixes from scan2_kernel's extra blocks)
+//   fill_list_kernel  double integrator, Dubins airplane: the edges the pair
+//                     filter listed with their costs (and arrival times or
+//                     words), placed in both CSRs by rank (word prefixes
+//                     from scan2_kernel's extra blocks)
 //   fill_kernel       persistent blocks, eight rows at a time: each warp
 //                     gathers a row's columns (prefix over its words) into a
 //                     shared-memory list, then the block shares out the eight
@@ -207,8 +208,12 @@ __global__ void __launch_bounds__(kDubRows) pair_mask_dubins_kernel(SpaceArgs s,
                                                                   uint32_t* __restrict__ mask,
                                                                   int* __restrict__ out_count,
                                                                   uint32_t* __restrict__ maskT,
-                                                                  int* __restrict__ in_count) {
-    mask_dubins_tile(s, X, mask, out_count, blockIdx.x, blockIdx.y, maskT, in_count);
+                                                                  int* __restrict__ in_count,
+                                                                  int4* __restrict__ elist,
+                                                                  float4* __restrict__ epath,
+                                                                  int* __restrict__ elist_n, int elist_cap) {
+    mask_dubins_tile(s, X, mask, out_count, blockIdx.x, blockIdx.y, maskT, in_count, elist, epath, elist_n,
+                     elist_cap);
 }
 
 __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ count, int* __restrict__ row, int N) {
@@ -246,18 +251,20 @@ __global__ void __launch_bounds__(1024) scan2_kernel(const int* __restrict__ cou
     }
 }
 
-// Double integrator: the edges the pair filter listed (with cost and arrival
-// time), placed in the out- and in-CSR by their ranks (place_listed_edge).
-// Writes nothing when the edge count exceeds the arrays' capacity (cap > 0:
-// the caller rebuilds) or the list's.
+// Directed costs: the edges the pair filter listed (with cost and arrival
+// time, or shortest word), placed in the out- and in-CSR by their ranks
+// (place_listed_edge).  Writes nothing when the edge count exceeds the
+// arrays' capacity (cap > 0: the caller rebuilds) or the list's.
+template <int KIND>
 __global__ void __launch_bounds__(256) fill_list_kernel(int N, int pitch, const int4* __restrict__ elist,
-                                                        int list_cap, FillDir out, FillDir in,
-                                                        const int* __restrict__ pre_out,
+                                                        const float4* __restrict__ epath, int list_cap, FillDir out,
+                                                        FillDir in, const int* __restrict__ pre_out,
                                                         const int* __restrict__ pre_in) {
     const int E = __ldg(&out.row[N]);
     if ((out.cap > 0 && (long long)E > out.cap) || E > list_cap || __ldg(&in.row[N]) != E) return;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < E; t += gridDim.x * blockDim.x)
-        place_listed_edge(pitch, __ldg(&elist[t]), out, in, pre_out, pre_in);
+        place_listed_edge<KIND>(pitch, __ldg(&elist[t]), KIND == GMT_COST_DUBINS ? epath + t : nullptr, out, in,
+                                pre_out, pre_in);
 }
 
 // Persistent blocks take groups of kFillWarps rows from a ticket counter
@@ -403,7 +410,7 @@ cudaError_t launch_append(const SpaceArgs& s, BoxArgs b, const float* src, int s
 
 cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* cnt, uint32_t* maskT,
                              int* in_count, cudaStream_t st, int* tile_cnt, int4* elist, int* elist_n,
-                             int elist_cap) {
+                             int elist_cap, float4* epath) {
     if (s.kind == GMT_COST_DI) {
         const int W = (s.N + 31) / 32;
         dim3 grid((s.N + kDIRows - 1) / kDIRows, (W + kDIWords - 1) / kDIWords);
@@ -413,7 +420,8 @@ cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask,
     if (s.kind == GMT_COST_DUBINS) {
         const int W = (s.N + 31) / 32;
         dim3 grid((s.N + kDubRows - 1) / kDubRows, (W + kDubWords - 1) / kDubWords);
-        pair_mask_dubins_kernel<<<grid, kDubRows, 0, st>>>(s, X, mask, cnt, maskT, in_count);
+        pair_mask_dubins_kernel<<<grid, kDubRows, 0, st>>>(s, X, mask, cnt, maskT, in_count, epath ? elist : nullptr,
+                                                           epath, elist_n, elist_cap);
         return cudaGetLastError();
     }
     GMT_EUCLID_DIMS(mask_t, s, X, mask, cnt, s.d >= 2 && s.d <= 4 ? tile_cnt : nullptr, st)
@@ -447,12 +455,20 @@ cudaError_t launch_scan2(const int* count0, int* row0, const int* count1, int* r
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill_list(const SpaceArgs& s, const int4* elist, int list_cap, const FillDir& out,
-                             const FillDir& in, const int* pre_out, const int* pre_in, cudaStream_t st) {
+cudaError_t launch_fill_list(const SpaceArgs& s, const int4* elist, const float4* epath, int list_cap,
+                             const FillDir& out, const FillDir& in, const int* pre_out, const int* pre_in,
+                             cudaStream_t st) {
     long long blocks = ((long long)list_cap + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (blocks > 4096) blocks = 4096;
-    fill_list_kernel<<<(unsigned)blocks, 256, 0, st>>>(s.N, s.pitch, elist, list_cap, out, in, pre_out, pre_in);
+    if (s.kind == GMT_COST_DI)
+        fill_list_kernel<GMT_COST_DI>
+            <<<(unsigned)blocks, 256, 0, st>>>(s.N, s.pitch, elist, nullptr, list_cap, out, in, pre_out, pre_in);
+    else if (s.kind == GMT_COST_DUBINS && epath && in.path)
+        fill_list_kernel<GMT_COST_DUBINS>
+            <<<(unsigned)blocks, 256, 0, st>>>(s.N, s.pitch, elist, epath, list_cap, out, in, pre_out, pre_in);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

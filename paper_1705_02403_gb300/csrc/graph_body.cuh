@@ -877,10 +877,17 @@ constexpr int kDubWords = 1;   // 32-column words per block
 
 // maskT, in_count (may be NULL): also write the tile's words of the transposed
 // (in-neighbour) matrix and count the in-edges, as transpose_task would.
+// elist, epath (may be NULL): every edge is also listed as (row, column, cost
+// bits, 0) with its shortest word (t, p, q, word bits) at the same slot of
+// epath, slots taken from *elist_n (those at or past elist_cap are counted but
+// not written), so the CSR fill need not solve for the word again.
 __device__ __forceinline__ void mask_dubins_tile(const SpaceArgs& s, const float* __restrict__ X,
                                                  uint32_t* __restrict__ mask, int* __restrict__ out_count, int bx,
                                                  int by, uint32_t* __restrict__ maskT = nullptr,
-                                                 int* __restrict__ in_count = nullptr) {
+                                                 int* __restrict__ in_count = nullptr,
+                                                 int4* __restrict__ elist = nullptr,
+                                                 float4* __restrict__ epath = nullptr,
+                                                 int* __restrict__ elist_n = nullptr, int elist_cap = 0) {
     static_assert(kDubWords == 1, "the prefilter keeps a lane's columns in one 32-bit word");
     __shared__ float tile[4][kDubWords * 32];
     __shared__ uint32_t words[kDubRows / 32][kDubWords][32];
@@ -938,7 +945,23 @@ __device__ __forceinline__ void mask_dubins_tile(const SpaceArgs& s, const float
             a_[a] = __shfl_sync(0xffffffffu, xi[a], src);
             b_[a] = tile[a][jt];
         }
-        if (lane < count && dubins_cost(a_, b_, s.rho) < s.r) atomicOr(&words[warp][jt >> 5][src], 1u << (jt & 31));
+        // the steps of dubins_cost
+        const DubPath P = dubins_path(a_, b_, s.rho);
+        const float c = dubins_length(P, a_, b_);
+        const bool edge = lane < count && c < s.r;
+        if (edge) atomicOr(&words[warp][jt >> 5][src], 1u << (jt & 31));
+        if (elist) {
+            const unsigned m = __ballot_sync(0xffffffffu, edge);
+            if (m) {
+                int slot = 0;
+                if (lane == 0) slot = atomicAdd(elist_n, __popc(m));
+                slot = __shfl_sync(0xffffffffu, slot, 0) + __popc(m & ((1u << lane) - 1u));
+                if (edge && slot < elist_cap) {
+                    elist[slot] = make_int4(bx * kDubRows + warp * 32 + src, j0 + jt, __float_as_int(c), 0);
+                    epath[slot] = make_float4(P.t, P.p, P.q, __int_as_float(P.word));
+                }
+            }
+        }
     }
     __syncwarp();
     const int W = (s.N + 31) / 32;
@@ -1011,25 +1034,32 @@ __device__ __forceinline__ void word_prefix_block(const uint32_t* __restrict__ M
     }
 }
 
-// A double-integrator edge (i, j) listed by the pair filter (with its cost and
-// arrival-time bits), written to both CSRs at its rank: in the out-row of i
-// after row[i] + pre[w][i] + the bits of word w = j / 32 below j, in the
+// An edge (i, j) listed by a directed pair filter (with its cost bits and, for
+// the double integrator, its arrival-time bits; for the Dubins airplane its
+// shortest word in `path`), written to both CSRs at its rank: in the out-row
+// of i after row[i] + pre[w][i] + the bits of word w = j / 32 below j, in the
 // in-row of j the same in the transposed matrix.  The ranks are those the
 // row-by-row fill gives, so the CSRs are the same arrays.
-__device__ __forceinline__ void place_listed_edge(int pitch, int4 q, const FillDir& out, const FillDir& in,
-                                                  const int* __restrict__ pre_out, const int* __restrict__ pre_in) {
+template <int KIND>
+__device__ __forceinline__ void place_listed_edge(int pitch, int4 q, const float4* path, const FillDir& out,
+                                                  const FillDir& in, const int* __restrict__ pre_out,
+                                                  const int* __restrict__ pre_in) {
     const int i = q.x, j = q.y;
     const size_t oi = (size_t)(j >> 5) * pitch + i, ij = (size_t)(i >> 5) * pitch + j;
     const int po =
         __ldg(&out.row[i]) + __ldg(&pre_out[oi]) + __popc(__ldg(&out.mask[oi]) & ((1u << (j & 31)) - 1u));
     const int pi = __ldg(&in.row[j]) + __ldg(&pre_in[ij]) + __popc(__ldg(&in.mask[ij]) & ((1u << (i & 31)) - 1u));
-    const float J = __int_as_float(q.z), t = __int_as_float(q.w);
+    const float c = __int_as_float(q.z);
     out.col[po] = j;
-    out.cost[po] = J;
-    out.tau[po] = t;
+    out.cost[po] = c;
     in.col[pi] = i;
-    in.cost[pi] = J;
-    in.tau[pi] = t;
+    in.cost[pi] = c;
+    if (KIND == GMT_COST_DI) {
+        out.tau[po] = __int_as_float(q.w);
+        in.tau[pi] = __int_as_float(q.w);
+    } else {
+        reinterpret_cast<float4*>(in.path)[pi] = *path;
+    }
 }
 
 // maskT[u][j] bit l = mask[j/32][32u + l] bit (j%32): the in-neighbour rows.

@@ -99,13 +99,15 @@ cudaError_t launch_sample(const SpaceArgs& s, BoxArgs boxes, const BoxGridArgs& 
 // tile_cnt (Euclidean graphs of 2 to 4 dimensions, may be NULL): receives,
 // for launch_fill_tiles, the number of each row's edges in the tiles of
 // kMaskWords mask words before each tile, [tile][pitch].
-// elist, elist_n (double integrator, may be NULL): every edge is also listed
-// as (row, column, cost bits, arrival-time bits) at a slot counted by
-// *elist_n (zero at launch; slots at or past elist_cap are not written), for
-// launch_fill_list.
+// elist, elist_n (double integrator, Dubins airplane; may be NULL): every
+// edge is also listed as (row, column, cost bits, arrival-time bits or 0) at a
+// slot counted by *elist_n (zero at launch; slots at or past elist_cap are
+// not written), for launch_fill_list; a Dubins airplane list needs epath too
+// (the edge's shortest word (t, p, q, word bits) at the same slot).
 cudaError_t launch_pair_mask(const SpaceArgs& s, const float* X, uint32_t* mask, int* out_count,
                              uint32_t* maskT, int* in_count, cudaStream_t st, int* tile_cnt = nullptr,
-                             int4* elist = nullptr, int* elist_n = nullptr, int elist_cap = 0);
+                             int4* elist = nullptr, int* elist_n = nullptr, int elist_cap = 0,
+                             float4* epath = nullptr);
 // Does the tiled fill apply (Euclidean, 2 to 4 dimensions; on one graph from
 // 4096 nodes, below which its extra prefix launch costs more than it saves;
 // in a batch always, one launch serving every query), and how many tiles of
@@ -141,12 +143,14 @@ struct FillDir {
 // ticket: one device int, zero at launch (the blocks' work counter).
 cudaError_t launch_fill(const SpaceArgs& s, const float* X, const FillDir& out, const FillDir& in, int* ticket,
                         cudaStream_t st);
-// Double integrator: both CSRs from the edge list of launch_pair_mask (list_cap
-// slots) and the word prefixes of launch_scan2 (pre_out for out.mask, pre_in
-// for in.mask), with no cost evaluated again.  Writes nothing if the edge
-// count exceeds out.cap (> 0) or list_cap.
-cudaError_t launch_fill_list(const SpaceArgs& s, const int4* elist, int list_cap, const FillDir& out,
-                             const FillDir& in, const int* pre_out, const int* pre_in, cudaStream_t st);
+// Double integrator, Dubins airplane: both CSRs from the edge list of
+// launch_pair_mask (list_cap slots; epath: the Dubins words, NULL for the
+// double integrator) and the word prefixes of launch_scan2 (pre_out for
+// out.mask, pre_in for in.mask), with no cost evaluated again.  Writes nothing
+// if the edge count exceeds out.cap (> 0) or list_cap.
+cudaError_t launch_fill_list(const SpaceArgs& s, const int4* elist, const float4* epath, int list_cap,
+                             const FillDir& out, const FillDir& in, const int* pre_out, const int* pre_in,
+                             cudaStream_t st);
 // The out-CSR of a Euclidean graph of 2 to 4 dimensions from the mask and the
 // per-tile prefixes of launch_pair_mask: one block per mask tile, columns
 // staged in shared memory.  Reads its inputs only, so it may run again.  A

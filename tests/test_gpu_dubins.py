@@ -176,3 +176,35 @@ def test_aligned_states_and_recomputed_words(O, P):
         assert np.array_equal(parent.cpu().numpy(), ref_parent)
         assert np.array_equal(bits(cost.cpu().numpy()), bits(ref_cost))
         assert info["checks"] == ref_info["checks"] and info["failed"] == ref_info["failed"]
+
+
+def test_rebuilds_take_listed_words(O, P):
+    # Rebuilds on a handle whose edge arrays are already sized take each edge's
+    # cost and shortest word from the pair filter's list (placed by rank), in
+    # the synchronous and the asynchronous build; a graph with more edges than
+    # the list holds is rebuilt row by row.  CSR, stored words, tree and path
+    # must equal the oracle's.
+    from test_gpu_parity import _retarget
+    pl = P.Planner(envgen.dubins_forest(30, n=1500, r=0.3)).build()
+    for pb, asynchronous in ((envgen.dubins_forest(31, n=1500, r=0.3), False),
+                             (envgen.dubins_forest(32, n=1400, r=0.3), True),
+                             (envgen.dubins_forest(33, n=2500, r=0.35), True)):
+        _retarget(P, pl, pb)
+        pl.build(asynchronous=asynchronous)
+        info = pl.plan()
+        v = pl.view()
+        G = {"parent": pl.parent.cpu().numpy(), "cost": pl.cost.cpu().numpy(), "info": info,
+             "path": pl.path.cpu().numpy()[:info["path_len"]], "X": v.X.cpu().numpy(),
+             "goal": v.is_goal.cpu().numpy(), "E": v.E, "out_row": v.out_row.cpu().numpy(),
+             "out_col": v.out_col.cpu().numpy(), "out_cost": v.out_cost.cpu().numpy(),
+             "in_row": v.in_row.cpu().numpy(), "in_col": v.in_col.cpu().numpy(), "in_cost": v.in_cost.cpu().numpy()}
+        ref = oracle_run(O, pb)
+        assert_same(O, G, *ref)
+        X = G["X"]
+        words = P.wrap_device(v.raw.in_path, (v.E, 4), "f4", pl.graph).cpu().numpy()
+        wid = words[:, 3].copy().view(np.int32)
+        for x in range(0, pb.N, 37):
+            for e in range(G["in_row"][x], G["in_row"][x + 1]):
+                y = int(G["in_col"][e])
+                w, best = O.dubins_words(X[:, y], X[:, x], pb.rho, precision=32)
+                assert wid[e] == best and np.array_equal(bits(words[e, :3]), bits(w[best, 1:4]))
