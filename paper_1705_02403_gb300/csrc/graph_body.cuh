@@ -687,7 +687,7 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
     __shared__ __align__(16) float tile[6][kDIWords * 32];  // float2 reads of column pairs
     __shared__ uint32_t words[kDIRows / 32][kDIWords][32];
     __shared__ uint16_t queue0[kDIRows / 32][32 * 32];  // every pair of the warp's tile may pass the first test
-    __shared__ uint16_t queue[kDIRows / 32][3][64];
+    __shared__ uint16_t queue[kDIRows / 32][3][96];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = bx * kDIRows + threadIdx.x;
     const int w0 = by * kDIWords;
@@ -728,13 +728,18 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
         __syncwarp();
         return qn + __popc(m);
     };
-    auto shift = [&](int k, int qn) {  // drops the 32 entries just taken
+    // drops the first c (<= 32) of the qn (<= 96) entries of queue k
+    auto shift = [&](int k, int qn, int c) {
         __syncwarp();
-        if (lane < qn - 32) queue[warp][k][lane] = queue[warp][k][32 + lane];
+        const uint16_t m0 = lane + c < qn ? queue[warp][k][lane + c] : (uint16_t)0;
+        const uint16_t m1 = lane + 32 + c < qn ? queue[warp][k][lane + 32 + c] : (uint16_t)0;
         __syncwarp();
-        return qn - 32;
+        if (lane < qn - c) queue[warp][k][lane] = m0;
+        if (lane + 32 < qn - c) queue[warp][k][lane + 32] = m1;
+        __syncwarp();
+        return qn - c;
     };
-    auto drain2 = [&](int count) {  // exact test (the steps of di_cost)
+    auto drain2 = [&](int count) {  // exact test (the steps of di_cost) on queue 2's first count entries
         const int e = lane < count ? queue[warp][2][lane] : 0;
         float a_[6], b_[6];
         state(e, a_, b_);
@@ -759,18 +764,14 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
             }
         }
     };
-    auto drain1 = [&](int count) {  // second bound
+    auto drain1 = [&](int count) {  // second bound on queue 1's first count entries, into queue 2
         const int e = lane < count ? queue[warp][1][lane] : 0;
         float a_[6], b_[6];
         state(e, a_, b_);
         qn2 = enqueue(2, lane < count && di_bern_may_connect(a_, b_, s.r), e, qn2);
-        if (qn2 >= 32) {
-            drain2(32);
-            qn2 = shift(2, qn2);
-        }
     };
-    // first bound, on queue0[from, from + count) (count <= 64): each lane
-    // takes two entries, evaluated together with packed arithmetic
+    // first bound on queue0[from, from + count) (count <= 64), into queue 1:
+    // each lane takes two entries, evaluated together with packed arithmetic
     auto drain0 = [&](int from, int count) {
         const int ea = lane < count ? queue0[warp][from + lane] : 0;
         const int eb = lane + 32 < count ? queue0[warp][from + 32 + lane] : 0;
@@ -780,15 +781,7 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
         bool pa, pb;
         di_may_connect_x2(a0, b0, a1, b1, s.r, pa, pb);
         qn1 = enqueue(1, lane < count && pa, ea, qn1);
-        if (qn1 >= 32) {
-            drain1(32);
-            qn1 = shift(1, qn1);
-        }
         qn1 = enqueue(1, lane + 32 < count && pb, eb, qn1);
-        if (qn1 >= 32) {
-            drain1(32);
-            qn1 = shift(1, qn1);
-        }
     };
 
     const int jend = min(kDIWords * 32, s.N - j0);
@@ -833,9 +826,30 @@ __device__ __forceinline__ void mask_di_tile(const SpaceArgs& s, const float* __
         for (uint32_t m = pm; m; m &= m - 1) queue0[warp][pos++] = (uint16_t)((lane << 8) | (__ffs(m) - 1));
         __syncwarp();
     }
-    for (int from = 0; from < qn0; from += 64) drain0(from, min(64, qn0 - from));
-    if (qn1 > 0) drain1(qn1);
-    if (qn2 > 0) drain2(qn2);
+    // The stages as one loop with a single call site each (the instruction
+    // cache then holds all of them): a stage runs only when the next one has
+    // fewer than 32 entries, so queue 1 holds at most 31 + 64 entries and
+    // queue 2 at most 31 + 32; once queue 0 is used up, what is left in
+    // queues 1 and 2 is drained.  Every condition is uniform over the warp.
+    int from = 0;
+#pragma unroll 1
+    for (;;) {
+        const bool rest = from >= qn0;
+        if (qn2 >= 32 || (rest && qn1 == 0 && qn2 > 0)) {
+            const int c = min(32, qn2);
+            drain2(c);
+            qn2 = shift(2, qn2, c);
+        } else if (qn1 >= 32 || (rest && qn1 > 0)) {
+            const int c = min(32, qn1);
+            drain1(c);
+            qn1 = shift(1, qn1, c);
+        } else if (!rest) {
+            drain0(from, min(64, qn0 - from));
+            from += 64;
+        } else {
+            break;
+        }
+    }
     __syncwarp();
     const int W = (s.N + 31) / 32;
     if (maskT) {
