@@ -42,7 +42,7 @@ METRIC = "ms/plan p50/p99 & edges checked/s; learned+batched vs plain at equal p
 # ncu captures summarised in profiles/plan_kernel_double_integrator_6d_n4096.md
 # and profiles/plan_kernel_geometric_2d_n1024.md.
 # Set to None whenever plan_kernel changes until it is captured again.
-PLAN_KERNEL_DRAM_BYTES = {"di6": 2224640, "geo2d": None}
+PLAN_KERNEL_DRAM_BYTES = {"di6": 2225408, "geo2d": None}
 
 
 def parse():

@@ -70,6 +70,31 @@ __device__ __forceinline__ bool in_box(const float* p, const float* lo, const fl
     return inside;
 }
 
+// Does p lie in one of the boxes b0 + i, i a set bit of `near`?  Four boxes per
+// step with every comparison evaluated (no short circuit), so their loads
+// issue together; the answer is that of testing them one by one.
+template <int DP>
+__device__ __forceinline__ bool in_near_boxes(const float* p, const float* lo, const float* hi, int b0,
+                                              unsigned near) {
+    bool hit = false;
+    for (unsigned w = near; w;) {
+        const int first = b0 + __ffs(w) - 1;
+        bool h = false;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool valid = w != 0u;
+            const int b = valid ? b0 + __ffs(w) - 1 : first;
+            w &= w - 1u;
+            bool inside = valid;
+#pragma unroll
+            for (int a = 0; a < DP; ++a) inside = inside & (lo[b * DP + a] <= p[a]) & (p[a] <= hi[b * DP + a]);
+            h = h | inside;
+        }
+        hit = hit | h;
+    }
+    return hit;
+}
+
 template <int DP>
 __device__ __forceinline__ bool in_any_box(const float* p, const float* lo, const float* hi, int nbox) {
     for (int b = 0; b < nbox; ++b)

@@ -344,7 +344,7 @@ __device__ __forceinline__ bool trajectory_free_warp(const float* y, const float
                     b0 == 0 ? near_first
                             : LG::ballot(b0 + lane < nbox && box_meets<3>(blo, bhi, b0 + lane, lo, hi));
                 if (k < points)
-                    for (unsigned w = near; w; w &= w - 1) hit = hit || in_box<3>(p, blo, bhi, b0 + __ffs(w) - 1);
+                    if (!hit && near) hit = in_near_boxes<3>(p, blo, bhi, b0, near);
             }
         }
         if (LG::any(hit)) return false;
@@ -402,7 +402,7 @@ __device__ __forceinline__ bool dubins_free_warp(const float* y, const float* x,
                     b0 == 0 ? near_first
                             : LG::ballot(b0 + lane < nbox && box_meets<3>(blo, bhi, b0 + lane, lo, hi));
                 if (k < m)
-                    for (unsigned w = near; w; w &= w - 1) hit = hit || in_box<3>(p, blo, bhi, b0 + __ffs(w) - 1);
+                    if (!hit && near) hit = in_near_boxes<3>(p, blo, bhi, b0, near);
             }
         }
         if (LG::any(hit)) return false;
