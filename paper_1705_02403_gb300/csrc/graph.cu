@@ -1,8 +1,9 @@
 // SampleFree and r-disk neighbour graph construction (Section III-B; the
 // precomputation of Section V-A), as CUDA kernels for sm_103a.
 //
-//   sample_kernel     four lanes per node: Philox4x32-10 rejection sampling,
-//                     each attempt's box tests shared out over the lanes
+//   sample_kernel     sixteen lanes per node: Philox4x32-10 rejection sampling,
+//                     four attempts at once, each attempt's box tests shared
+//                     out over four lanes, the first accepted one kept
 //   halton_kernel     one block: the free Halton points in order
 //   halton_head_kernel + halton_free_kernel  the same split: nodes 0 and 1
 //                     in one block, the free points over many blocks (chunks
@@ -39,7 +40,9 @@ namespace gmtk {
 
 // ------------------------------------------------------------------ kernels
 constexpr int kSampleThreads = 128;
-constexpr int kSampleGroup = 4;  // lanes per node: the box tests of an attempt are shared out
+constexpr int kSampleLanes = 4;     // lanes per attempt: its box tests are shared out
+constexpr int kSampleParallel = 4;  // attempts of one node at once
+constexpr int kSampleGroup = kSampleLanes * kSampleParallel;  // lanes per node
 
 // Boxes are staged in shared memory when `staged` (2 * count * DP floats): the
 // rejection loop then tests them without a global-memory round trip per box.
@@ -57,7 +60,7 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(SpaceArgs s, Box
         boxes.lo = sbox;
         boxes.hi = sbox + boxes.count * DP;
     }
-    sample_node_group<D, DP, kSampleGroup>(s, boxes, grid, X, is_goal, flags,
+    sample_node_group<D, DP, kSampleLanes, kSampleParallel>(s, boxes, grid, X, is_goal, flags,
                                            (int)((blockIdx.x * blockDim.x + threadIdx.x) / kSampleGroup));
 }
 

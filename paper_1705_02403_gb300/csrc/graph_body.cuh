@@ -130,15 +130,21 @@ __device__ __forceinline__ bool point_in_boxes_group(const float* p, const BoxAr
     return hit;
 }
 
-template <int D, int DP, int G>
+// SampleFree for node k on a group of Q * P lanes of one warp: P attempts at
+// once (attempts t0 .. t0 + P - 1), each on Q lanes that share out its box
+// tests.  The node takes the first accepted attempt in attempt order, the one
+// the sequential rejection loop would take.
+template <int D, int DP, int Q, int P>
 __device__ __forceinline__ void sample_node_group(const SpaceArgs& s, const BoxArgs& boxes, const BoxGridArgs& grid,
                                                   float* __restrict__ X, uint8_t* __restrict__ is_goal,
                                                   int* __restrict__ flags, int k) {
+    constexpr int G = Q * P;
     static_assert(32 % G == 0, "a group lies within one warp");
     if (k >= s.n_sampled) return;  // uniform over the group
-    const int lane = threadIdx.x & 31, sub = lane % G;
-    const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (lane - sub);
-    float x[D];
+    const int lane = threadIdx.x & 31, sub = lane % G, q = sub % Q, first = lane - sub;
+    const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << first;
+    const unsigned qmask = ((1u << Q) - 1u) << (lane - q);
+    float x[D] = {};
     if (k == 0) {
         bool ok = true;
 #pragma unroll
@@ -149,31 +155,43 @@ __device__ __forceinline__ void sample_node_group(const SpaceArgs& s, const BoxA
         const bool hit = point_in_boxes_group<D, DP, G>(x, boxes, grid, sub, gmask);
         if (sub == 0 && (!ok || hit)) atomicOr(flags, kSampleBadInit);
     } else {
-        bool ok = false;
-        for (int t = 0; t < s.max_attempts && !ok; ++t) {
-            uint32_t w[((D + 3) / 4) * 4];
+        bool found = false;
+        for (int t0 = 0; t0 < s.max_attempts && !found; t0 += P) {  // uniform over the group
+            const int t = t0 + sub / Q;
+            bool acc = false;
+            if (t < s.max_attempts) {  // uniform over the attempt's Q lanes
+                uint32_t w[((D + 3) / 4) * 4];
 #pragma unroll
-            for (int blk = 0; blk < (D + 3) / 4; ++blk) {
-                const Ctr4 c = philox4x32_10(Ctr4{(uint32_t)k, (uint32_t)t, s.stream, (uint32_t)blk}, s.key0, s.key1);
-                w[4 * blk + 0] = c.x; w[4 * blk + 1] = c.y; w[4 * blk + 2] = c.z; w[4 * blk + 3] = c.w;
-            }
+                for (int blk = 0; blk < (D + 3) / 4; ++blk) {
+                    const Ctr4 c =
+                        philox4x32_10(Ctr4{(uint32_t)k, (uint32_t)t, s.stream, (uint32_t)blk}, s.key0, s.key1);
+                    w[4 * blk + 0] = c.x; w[4 * blk + 1] = c.y; w[4 * blk + 2] = c.z; w[4 * blk + 3] = c.w;
+                }
 #pragma unroll
-            for (int a = 0; a < D; ++a) {
-                const float u = unit_float(w[a]);
-                float l = s.lo[a], h = s.hi[a];
-                if (k == 1 && a < s.gd) { l = s.gc[a] - s.grho; h = s.gc[a] + s.grho; }
-                x[a] = l + u * (h - l);
-            }
-            if (k == 1) {
-                bool inb = true;
+                for (int a = 0; a < D; ++a) {
+                    const float u = unit_float(w[a]);
+                    float l = s.lo[a], h = s.hi[a];
+                    if (k == 1 && a < s.gd) { l = s.gc[a] - s.grho; h = s.gc[a] + s.grho; }
+                    x[a] = l + u * (h - l);
+                }
+                acc = true;
+                if (k == 1) {
 #pragma unroll
-                for (int a = 0; a < D; ++a) inb = inb && s.lo[a] <= x[a] && x[a] <= s.hi[a];
-                if (!inb || !in_goal_ball(x, s.gd, s.gc, s.grho)) continue;
+                    for (int a = 0; a < D; ++a) acc = acc && s.lo[a] <= x[a] && x[a] <= s.hi[a];
+                    acc = acc && in_goal_ball(x, s.gd, s.gc, s.grho);
+                }
+                if (acc) acc = !point_in_boxes_group<D, DP, Q>(x, boxes, grid, q, qmask);
             }
-            if (point_in_boxes_group<D, DP, G>(x, boxes, grid, sub, gmask)) continue;
-            ok = true;
+            // the first accepted attempt of the round (one vote per attempt)
+            const unsigned m = (__ballot_sync(gmask, acc && q == 0) >> first) & (G == 32 ? 0xffffffffu : ((1u << G) - 1u));
+            if (m) {
+                found = true;
+                const int src = first + __ffs(m) - 1;
+#pragma unroll
+                for (int a = 0; a < D; ++a) x[a] = __shfl_sync(gmask, x[a], src);
+            }
         }
-        if (!ok && sub == 0) atomicOr(flags, kSampleExhausted);
+        if (!found && sub == 0) atomicOr(flags, kSampleExhausted);
     }
     if (sub != 0) return;
 #pragma unroll
