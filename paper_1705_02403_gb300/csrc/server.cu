@@ -358,10 +358,13 @@ void worker_loop(gmt_server* sv) {
 size_t session_bytes_estimate(int N, int kind) {
     const size_t P = (size_t)(N + 31) / 32 * 32, W = (size_t)(N + 31) / 32;
     const size_t E = (size_t)N * 256;  // upper estimate of edges per node
-    const size_t mask = W * P * 4 * (kind == GMT_COST_EUCLID ? 1 : 2);
+    // bit matrices (and, for directed costs, the transpose and both matrices'
+    // word prefixes of a rebuild that places listed edges)
+    const size_t mask = W * P * 4 * (kind == GMT_COST_EUCLID ? 1 : 4);
     // per edge: CSR columns and costs (both directions for directed costs),
-    // arrival times (DI) or stored words (Dubins), point box, verdict
-    return mask + E * (kind == GMT_COST_DI ? 44 : kind == GMT_COST_DUBINS ? 57 : 33) + (size_t)N * 64;
+    // arrival times (DI) or stored words (Dubins), point box, verdict, and the
+    // pair filter's edge list of a rebuild (16 B, and 16 B of words for Dubins)
+    return mask + E * (kind == GMT_COST_DI ? 60 : kind == GMT_COST_DUBINS ? 89 : 33) + (size_t)N * 64;
 }
 
 }  // namespace

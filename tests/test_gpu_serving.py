@@ -113,12 +113,13 @@ def test_same_alone_and_in_the_mix(O):
 
 
 def test_admission_by_device_memory():
-    # A 60 MB budget holds two sessions of n = 2000 (each estimated at about
-    # 24 MB: bit matrices plus CSR space for up to 256 edges per node); the
-    # third is refused with GMT_ERR_ADMISSION, and fits again after a close.
+    # An 80 MiB budget holds two sessions of n = 2000 (each estimated at about
+    # 33 MB: bit matrices and their word prefixes plus CSR and edge-list space
+    # for up to 256 edges per node); the third is refused with
+    # GMT_ERR_ADMISSION, and fits again after a close.
     from paper_1705_02403_gb300 import _native as N
     pbs = [envgen.di6(seed=20 + k, n=2000, r=2.6) for k in range(4)]
-    server = N.Server(slots=1, cluster=0, max_nodes=2001, max_boxes=30, memory_budget=60 << 20)
+    server = N.Server(slots=1, cluster=0, max_nodes=2001, max_boxes=30, memory_budget=80 << 20)
     opened = []
     for pb in pbs[:3]:
         sid, st = server.open_session(*structs(pb)[:1], pb.x_init, *structs(pb)[1:], pb.box_lo, pb.box_hi,
